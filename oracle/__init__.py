@@ -1,0 +1,229 @@
+"""CPU FP64 oracle for the QFT->FFT method (Markidis et al.).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+benchmark's ``cpu_baseline`` / ``--impl reference`` legs are the only callers.
+The GPU library never imports this package and shares no code with it.
+
+The arithmetic lives in ``qft_oracle.c`` (plain C, FP64, OpenMP parallel-for
+over amplitudes).  This module compiles it with gcc on first use (or when
+``build()`` is called) and wraps it with ctypes for numpy complex128 arrays.
+
+Conventions (paper Sec. 2-3): qubit q_j is bit j of the array index (LSB q_0);
+sign = -1 is the forward transform with omega_N = e^{-2 pi i/N}; the circuit is
+the unitary U = DFT_N / sqrt(N); the final swaps give the natural output order.
+
+Functions:
+  encode(x)                    Sec. 3 step 1
+  circuit(psi, n, k, sign)     Sec. 3 steps 2-3, Fig. 1 (+ Sec. 2 AQFT cutoff)
+  decode(psi, scale_in, mode)  Sec. 3 step 4
+  qft(x, k, sign, mode)        encode -> circuit -> decode
+  dft(x, sign)                 Sec. 2 DFT definition, O(N^2)
+  aqft_direct(x, k, sign)      closed-form matrix elements of the range-k AQFT
+  aqft_bins(x, ys, k, sign)    a few output bins by O(N) direct summation
+  gate_counts(n, k)            Table 2
+  gate_list(n, k)              Fig. 1
+  fidelity(a, b), leakage(...) Sec. 4 accuracy measures
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qft_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SCALE_STATE, SCALE_UNITARY, SCALE_UNNORM, SCALE_INV_N = 0, 1, 2, 3
+FORWARD, INVERSE = -1, +1
+
+
+def build(force: bool = False) -> str:
+    """Compile qft_oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_encode.argtypes = [ctypes.c_int, dp, dp]
+        lib.oracle_encode.restype = ctypes.c_double
+        lib.oracle_circuit.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        lib.oracle_circuit.restype = None
+        lib.oracle_decode.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, dp]
+        lib.oracle_decode.restype = None
+        lib.oracle_dft.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.oracle_dft.restype = None
+        lib.oracle_aqft_direct.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.oracle_aqft_direct.restype = None
+        lib.oracle_aqft_bins.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, i64p,
+                                         ctypes.c_int, dp]
+        lib.oracle_aqft_bins.restype = None
+        lib.oracle_gate_counts.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
+        lib.oracle_gate_counts.restype = None
+        lib.oracle_gate_list.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int]
+        lib.oracle_gate_list.restype = ctypes.c_int
+        lib.oracle_bit_reverse.argtypes = [ctypes.c_int64, ctypes.c_int]
+        lib.oracle_bit_reverse.restype = ctypes.c_int64
+        lib.oracle_num_threads.argtypes = []
+        lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_num_threads.restype = None
+        _lib = lib
+        return lib
+
+
+def _as_c128(x) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+    return a
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _log2_exact(N: int) -> int:
+    n = int(N).bit_length() - 1
+    if N <= 0 or (1 << n) != N:
+        raise ValueError(f"length {N} is not a power of two")
+    return n
+
+
+def num_threads() -> int:
+    return _load().oracle_num_threads()
+
+
+def set_num_threads(t: int) -> None:
+    _load().oracle_set_num_threads(int(t))
+
+
+def encode(x):
+    """Sec. 3 step 1: returns (psi = x / ||x||_2, scale_in = ||x||_2)."""
+    lib = _load()
+    x = _as_c128(x)
+    n = _log2_exact(x.size)
+    psi = np.empty_like(x)
+    s = lib.oracle_encode(n, _dptr(x), _dptr(psi))
+    return psi, s
+
+
+def circuit(psi, k: int = -1, sign: int = FORWARD, natural_order: bool = True) -> np.ndarray:
+    """Apply the range-k (A)QFT circuit gate by gate; returns a new array."""
+    lib = _load()
+    out = _as_c128(psi).copy()
+    n = _log2_exact(out.size)
+    lib.oracle_circuit(n, int(k), int(sign), 1 if natural_order else 0, _dptr(out))
+    return out
+
+
+def decode(psi, scale_in: float, mode: int = SCALE_STATE) -> np.ndarray:
+    """Sec. 3 step 4: rescale the final state to FFT units."""
+    lib = _load()
+    psi = _as_c128(psi)
+    n = _log2_exact(psi.size)
+    out = np.empty_like(psi)
+    lib.oracle_decode(n, _dptr(psi), float(scale_in), int(mode), _dptr(out))
+    return out
+
+
+def qft(x, k: int = -1, sign: int = FORWARD, mode: int = SCALE_STATE, natural_order: bool = True):
+    """encode -> circuit -> decode.  Returns (output, scale_in)."""
+    psi, s = encode(x)
+    return decode(circuit(psi, k, sign, natural_order), s, mode), s
+
+
+def dft(x, sign: int = FORWARD) -> np.ndarray:
+    """Unnormalised DFT by its definition (Sec. 2), O(N^2)."""
+    lib = _load()
+    x = _as_c128(x)
+    n = _log2_exact(x.size)
+    out = np.empty_like(x)
+    lib.oracle_dft(n, int(sign), _dptr(x), _dptr(out))
+    return out
+
+
+def aqft_direct(x, k: int = -1, sign: int = FORWARD) -> np.ndarray:
+    """U_k x (natural order, swaps included) from closed-form matrix elements, O(N^2)."""
+    lib = _load()
+    x = _as_c128(x)
+    n = _log2_exact(x.size)
+    out = np.empty_like(x)
+    lib.oracle_aqft_direct(n, int(k), int(sign), _dptr(x), _dptr(out))
+    return out
+
+
+def aqft_bins(x, ys, k: int = -1, sign: int = FORWARD) -> np.ndarray:
+    """Selected output bins <y|U_k|x> by O(N) direct summation each."""
+    lib = _load()
+    x = _as_c128(x)
+    n = _log2_exact(x.size)
+    ys = np.ascontiguousarray(np.asarray(ys, dtype=np.int64))
+    out = np.empty(ys.size, dtype=np.complex128)
+    lib.oracle_aqft_bins(n, int(k), int(sign), _dptr(x),
+                         ys.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(ys.size), _dptr(out))
+    return out
+
+
+def gate_counts(n: int, k: int = -1):
+    """(n_H, n_CP, n_swap) of the range-k circuit (Table 2)."""
+    lib = _load()
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib.oracle_gate_counts(int(n), int(k), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return a.value, b.value, c.value
+
+
+def gate_list(n: int, k: int = -1, natural_order: bool = True):
+    """The gate sequence (Fig. 1): list of ('H', t) / ('CR', control, target, m) / ('SWAP', a, b)."""
+    lib = _load()
+    cap = n + n * n + n
+    buf = (ctypes.c_int * (4 * cap))()
+    g = lib.oracle_gate_list(int(n), int(k), 1 if natural_order else 0, buf, cap)
+    out = []
+    for i in range(g):
+        kind, a, b, m = buf[4 * i: 4 * i + 4]
+        if kind == 0:
+            out.append(("H", a))
+        elif kind == 1:
+            out.append(("CR", a, b, m))
+        else:
+            out.append(("SWAP", a, b))
+    return out
+
+
+def bit_reverse(i: int, n: int) -> int:
+    return _load().oracle_bit_reverse(int(i), int(n))
+
+
+def fidelity(a, b) -> float:
+    """Sec. 4: squared, normalised inner product |<a,b>|^2 / (||a||^2 ||b||^2)."""
+    a = np.asarray(a, dtype=np.complex128).ravel()
+    b = np.asarray(b, dtype=np.complex128).ravel()
+    num = abs(np.vdot(a, b)) ** 2
+    den = np.vdot(a, a).real * np.vdot(b, b).real
+    return float(num / den) if den > 0 else 1.0
+
+
+def leakage(approx, exact) -> float:
+    """Sec. 4 top-bin leakage: 1 - |approx[y*]|^2 / ||approx||^2, y* = argmax |exact|."""
+    approx = np.asarray(approx, dtype=np.complex128).ravel()
+    ystar = int(np.argmax(np.abs(np.asarray(exact).ravel())))
+    tot = np.vdot(approx, approx).real
+    return float(1.0 - abs(approx[ystar]) ** 2 / tot) if tot > 0 else 0.0
