@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the QFT->FFT hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one complete transform of a 2^n-amplitude state (norm, every fused
+pass of the circuit, the qubit-reversal layout and the decode scale), run
+through the C ABI.  Default workload: the exact forward QFT of n = 30 qubits in
+complex64, natural output order, state-vector mode, seeded Gaussian amplitudes
+drawn on the device (an 8 GiB state: larger than L2, so no flush is needed).
+
+Printed (rank 0, one JSON line): amplitudes/s over all ranks (value),
+ms/step, the end-to-end rate through host buffers (e2e: pinned host -> device
+copy, execute, device -> host copy every step), the HBM roofline of the pass
+kernel (algorithmic bytes per launch / mean CUDA-event launch duration against
+MEASURED_PEAKS.json), the CPU oracle timed on a bounded sample of the same
+workload (cpu_baseline), SM clocks sampled during the timed region, and a few
+secondary measurements (extra).  With torchrun (N > 1) every rank runs an
+independent replica (no collective on the data path; scaling "weak").
+
+--impl reference times the reference arm: the CPU FP64 oracle, as it stands,
+on this machine's host cores, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "QFT amplitudes/s and % HBM roofline vs plain c128 path; served p99 ms"
+UNIT = "amplitudes/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--k", type=int, default=-1)
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(n, dt, k):
+    kind = "exact QFT" if k < 0 or k >= n - 1 else f"AQFT k={k}"
+    return (f"{kind}, forward, n={n} ({1 << n} amplitudes), {'complex64' if dt == 'c64' else 'complex128'}, "
+            f"natural order, state-vector scaling, seeded Gaussian amplitudes")
+
+
+# ------------------------------------------------------------------ clocks
+
+REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, power, reasons = [], [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(REASONS, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("qft_pass.cu", "plan.hpp"):
+        h.update(open(os.path.join(ROOT, "paper_2606_18981_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n, dt):
+    """DRAM bytes per launch of the pass kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "qft_pass_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        if d.get("kernel_hash") != kernel_source_hash():
+            return None
+        e = d.get("per_launch", {}).get(f"{dt}_n{n}")
+        return float(e) if e is not None else None
+    except Exception:
+        return None
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_sample(n, k, reps=1):
+    """Bounded sample of the same circuit on the host: time one H sweep, one
+    controlled-phase sweep and the swap sweeps of the n-qubit circuit with the
+    FP64 oracle; extrapolate by the circuit's gate counts.  Returns
+    (amplitudes/s, seconds of CPU work, threads, description)."""
+    import numpy as np
+
+    import oracle
+
+    N = 1 << n
+    nh, ncp, _ = oracle.gate_counts(n, k)
+    psi = np.full(N, 1.0 / np.sqrt(N), dtype=np.complex128)
+    t_sw0 = time.perf_counter()
+    oracle.apply_gate(psi, "SWAPS")
+    t_sw = time.perf_counter() - t_sw0
+    work = t_sw
+    rates = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.apply_gate(psi, "H", n - 1)
+        t1 = time.perf_counter()
+        oracle.apply_gate(psi, "CR", n - 2, n - 1, 2)
+        t2 = time.perf_counter()
+        work += t2 - t0
+        T = nh * (t1 - t0) + ncp * (t2 - t1) + t_sw
+        rates.append(N / T)
+    desc = (f"oracle gate sweeps on the full n={n} state: 1 H, 1 controlled phase and the swap sweeps "
+            f"timed, extrapolated by the circuit's {nh} H + {ncp} controlled phases")
+    return statistics.median(rates), work, oracle.num_threads(), desc
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    n, k = args.n, args.k
+    rates = []
+    t_all = 0.0
+    for s in range(args.warmup + args.steps):
+        r, w, cores, desc = oracle_sample(n, k, reps=1)
+        t_all += w
+        if s >= args.warmup:
+            rates.append(r)
+    val = statistics.median(rates)
+    N = 1 << n
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * N / val,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(n, args.dtype, k), "n": n,
+                                            "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+
+def timed_transform(q, torch, plan, state, ws, stream, steps, warmup):
+    """Device-timed steps on resident data; returns (ms/step, [mean ms per pass])."""
+    P = plan.info().passes
+    for _ in range(warmup):
+        plan.execute(state, ws, q.SCALE_STATE, stream=stream)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(P + 1)] for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(steps):
+        for i in range(P):
+            evs[s][i].record(stream)
+            plan.execute_pass(i, state, ws, q.SCALE_STATE, stream=stream)
+        evs[s][P].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total = t0.elapsed_time(t1)
+    per_pass = [statistics.mean(evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(steps)) for i in range(P)]
+    return total / steps, per_pass
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2606_18981_gb300 as q
+    import qft_inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    n, dt, k = args.n, args.dtype, args.k
+    N = 1 << n
+    eb = 8 if dt == "c64" else 16
+    plan = q.Plan(n, k, q.FORWARD, dt, q.ORDER_NATURAL)
+    info = plan.info()
+    P = info.passes
+    stream = torch.cuda.Stream(device=dev)
+    state = qft_inputs.device_gaussian(n, 1234 + rank, dt, device=str(dev))
+    ws = plan.alloc_workspace(dev)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+    except Exception:
+        gpu_id = None
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.execute(state, ws, q.SCALE_STATE, stream=stream)
+    torch.cuda.synchronize()
+    barrier()
+    with ClockSampler(gpu_id) as clk:
+        ms, per_pass = timed_transform(q, torch, plan, state, ws, stream, args.steps, 1)
+    barrier()
+    status = plan.status(ws, stream)
+    if status != 0:
+        raise RuntimeError(f"device status {status}")
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * N / (ms_max / 1000.0)
+
+    # end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        td = torch.complex64 if dt == "c64" else torch.complex128
+        host_in = torch.empty(N, dtype=td, pin_memory=True)
+        host_in.copy_(state.cpu())
+        host_out = torch.empty(N, dtype=td, pin_memory=True)
+        e_steps = max(3, min(args.steps, 10))
+        for _ in range(2):
+            plan.load(state, host_in, stream=stream)
+            plan.execute(state, ws, q.SCALE_STATE, stream=stream)
+            plan.read(state, host_out, stream=stream)
+        torch.cuda.synchronize()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(e_steps):
+            plan.load(state, host_in, stream=stream)
+            plan.execute(state, ws, q.SCALE_STATE, stream=stream)
+            plan.read(state, host_out, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = a.elapsed_time(b) / e_steps
+        e_t = torch.tensor([e_ms], device=dev)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * N / (float(e_t.item()) / 1000.0), "unit": UNIT, "ms_per_step": float(e_t.item()),
+               "h2d_bytes_per_step": N * eb, "d2h_bytes_per_step": N * eb, "steps": e_steps}
+        del host_in, host_out
+
+    peak, peak_src = load_peaks()
+    bytes_per_launch = 2 * N * eb
+    mean_launch_ms = statistics.mean(per_pass)
+    achieved = bytes_per_launch / (mean_launch_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(n, dt), "peak_source": peak_src,
+                "kernel": "qft_pass_kernel", "bytes_per_launch": bytes_per_launch,
+                "launch_ms": per_pass}
+
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        del state, ws
+        torch.cuda.empty_cache()
+        for name, (nn, ddt, kk) in {"aqft_k4_c64_n30": (30, "c64", 4), "plain_c128_n30": (30, "c128", -1),
+                                     "c64_n26": (26, "c64", -1), "c64_n33": (33, "c64", -1)}.items():
+            try:
+                p2 = q.Plan(nn, kk, q.FORWARD, ddt, q.ORDER_NATURAL)
+                free, _ = torch.cuda.mem_get_info()
+                need = (1 << nn) * (8 if ddt == "c64" else 16) * 2 + (1 << 30)
+                if free < need:
+                    extra[name] = {"skipped": "memory"}
+                    continue
+                st2 = qft_inputs.device_gaussian(nn, 99, ddt, device=str(dev))
+                ws2 = p2.alloc_workspace(dev)
+                ms2, pp2 = timed_transform(q, torch, p2, st2, ws2, stream, 5, 2)
+                eb2 = 8 if ddt == "c64" else 16
+                extra[name] = {"amplitudes_per_s": (1 << nn) / (ms2 / 1000.0), "ms_per_step": ms2,
+                               "passes": p2.info().passes,
+                               "hbm_frac": (2 * (1 << nn) * eb2 / (statistics.mean(pp2) / 1000.0) / 1e9) / peak}
+                del st2, ws2
+                torch.cuda.empty_cache()
+            except Exception as ex:  # secondary numbers must not sink the headline
+                extra[name] = {"error": str(ex)[:200]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle
+
+            oracle.build()
+            r, w, cores, desc = oracle_sample(n, k, reps=2)
+            cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                   "cpu_seconds": w}
+        except Exception as ex:
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if dt == "c64" else "f64", "data": "synthetic",
+                "config": {"workload": workload_name(n, dt, k), "n": n, "amplitudes": N,
+                           "dtype": "complex64" if dt == "c64" else "complex128", "passes": P,
+                           "wires_per_pass": list(info.wires_per_pass)[:P],
+                           "state_bytes": N * eb,
+                           "l2": "state (and workspace) larger than L2; no flush needed",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": P * args.steps,
+                "clocks": clk.summary(), "extra": extra}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * qftfft.h -- C ABI of the GB300 QFT->FFT library (libqftfft.so).
+ *
+ * The library computes discrete Fourier transforms by executing the quantum
+ * Fourier transform circuit on a 2^n-amplitude state vector, following
+ * Markidis et al., "Not Your Usual FFT: QFT->FFT via Classical Quantum-Circuit
+ * Simulation".  The problem statement it implements is Sec. 3 of that paper:
+ *
+ *   1. encode:  scale_in = ||x||_2, psi = x / scale_in, index k of the array is
+ *               the basis state |b_{n-1} ... b_0>, qubit q_j = bit j (LSB q_0);
+ *   2. build the n-qubit QFT circuit of Fig. 1 (H on each wire from the most
+ *      significant down, each followed by the controlled phases R_{d+1}
+ *      whose control lies d wires below, then the qubit-reversal swaps); the
+ *      range-k approximate QFT keeps only the controlled phases with d <= k
+ *      (Sec. 2, "Approximate QFT");
+ *   3. evolve:  psi' = U psi with U = DFT_N / sqrt(N) (Sec. 3 step 3), where
+ *      DFT_N = [omega^{kl}], omega = e^{-2 pi i / N} for the forward direction
+ *      (Sec. 2) and e^{+2 pi i / N} for the inverse;
+ *   4. decode:  rescale psi' to FFT units with scale_in (Sec. 3 step 4).
+ *
+ * Calls map onto those steps: qft_plan_create (step 2, host only),
+ * qft_load (step 1: place the caller's array in the state buffer),
+ * qft_execute (steps 1 and 3-4 on the GPU: the norm, the circuit and the
+ * rescaling run inside the pass kernels), qft_read (copy the result out).
+ *
+ * Everything is asynchronous on the caller's CUDA stream unless stated.  No
+ * call allocates device memory except qft_plan_create (small, plan-owned) and
+ * the server calls; state buffers and workspaces are caller-owned.
+ *
+ * Data layout: a state is N = 2^n complex numbers, interleaved (re, im):
+ * complex64 = 2 x float32 (8 bytes), complex128 = 2 x float64 (16 bytes) --
+ * the memory layout of torch.complex64 / torch.complex128.  Device pointers
+ * must be 256-byte aligned (what cudaMalloc and the torch caching allocator
+ * return).
+ *
+ * Errors: every call returns QFT_OK (0) or a negative QFT_ERR_* code; no call
+ * aborts, throws or traps.  A CUDA launch/runtime failure is reported as
+ * QFT_ERR_CUDA (qft_last_cuda_error gives the cudaError_t value).  Faults that
+ * happen asynchronously on the GPU surface at the caller's next synchronising
+ * CUDA call.
+ */
+#ifndef QFTFFT_H
+#define QFTFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque handles.  qft_stream_t is a cudaStream_t (NULL = legacy default stream). */
+typedef struct qft_plan_s* qft_plan_t;
+typedef struct qft_server_s* qft_server_t;
+typedef struct CUstream_st* qft_stream_t;
+
+enum qft_dtype { QFT_C64 = 0, QFT_C128 = 1 };
+
+/* Sign of the exponent (Sec. 2: omega_N = e^{-2 pi i / N} is the forward transform). */
+enum qft_direction { QFT_FORWARD = -1, QFT_INVERSE = +1 };
+
+/* Output scaling (Sec. 3 step 4).  With psi' = DFT_N x / (scale_in sqrt N):
+ *   STATE    psi'                       (the normalised simulator state)
+ *   UNITARY  scale_in psi'  = DFT_N x / sqrt(N)
+ *   UNNORM   scale_in sqrt(N) psi' = DFT_N x      (numpy.fft.fft for FORWARD)
+ *   INV_N    scale_in psi' / sqrt(N) = DFT_N x / N (numpy.fft.ifft for INVERSE) */
+enum qft_scale { QFT_SCALE_STATE = 0, QFT_SCALE_UNITARY = 1, QFT_SCALE_UNNORM = 2, QFT_SCALE_INV_N = 3 };
+
+/* Output index order.  NATURAL applies the final qubit-reversal swaps (a drop-in
+ * FFT); BITREV leaves them to the caller as an output index permutation, as the
+ * paper does (Sec. 3 step 2): out[i] holds frequency bitrev_n(i). */
+enum qft_order { QFT_ORDER_NATURAL = 0, QFT_ORDER_BITREV = 1 };
+
+enum qft_status {
+    QFT_OK = 0,
+    QFT_ERR_BAD_ARG = -1,     /* NULL handle/pointer, n or k or enum out of range   */
+    QFT_ERR_SIZE = -2,        /* length is zero or not a power of two                */
+    QFT_ERR_BUDGET = -3,      /* request exceeds the server's HBM admission budget   */
+    QFT_ERR_CUDA = -4,        /* a CUDA runtime/driver call failed                    */
+    QFT_ERR_TIMEOUT = -5,     /* a bounded wait (host or device) ran out             */
+    QFT_ERR_NOMEM = -6,       /* host or plan-owned device allocation failed         */
+    QFT_ERR_UNSUPPORTED = -7, /* valid request this build does not implement         */
+    QFT_ERR_STATE = -8        /* call out of order (e.g. unknown ticket)             */
+};
+
+/* Planner options; pass NULL for defaults.  Zero fields mean "choose". */
+typedef struct {
+    int order;          /* QFT_ORDER_NATURAL (default) or QFT_ORDER_BITREV                 */
+    int tile_bits;      /* log2(amplitudes per CTA tile); 0 = default (13 c64, 12 c128)   */
+    int coalesce_bits;  /* min log2(contiguous amplitudes per HBM run); 0 = default         */
+    int max_stage_bits; /* max wires per register stage (1..4); 0 = default                */
+    int wait_limit_ms;  /* bound of every device-side wait; 0 = default (2000 ms)           */
+    int test_skip_first_load; /* test hook: 1 = never issue the first tile load, so the
+                                 kernel's bounded wait expires and reports QFT_ERR_TIMEOUT  */
+    int reserved[2];
+} qft_opts;
+
+/* What the planner built (Sec. 3.1: the plan is defined by the qubit count,
+ * the fused blocks and the pre-fusion gate counters). */
+typedef struct {
+    int n, k_eff, direction, dtype, order;
+    long long n_h, n_cp, n_swap;     /* gate counts before fusion (Table 2)            */
+    int passes;                      /* HBM sweeps per execute                          */
+    int wires_per_pass[8];           /* transform wires fused into each pass            */
+    int stages_per_pass[8];          /* register stages (fused blocks) in each pass     */
+    int tile_bits[8];                /* log2(amplitudes per tile) of each pass          */
+    int coalesce_bits[8];            /* log2(contiguous amplitudes per run) per pass   */
+    size_t workspace_bytes;          /* qft_workspace_size()                            */
+    long long bytes_per_execute;     /* algorithmic HBM bytes: passes * 2 * N * elem   */
+} qft_plan_info;
+
+/* Step 2 (Sec. 3, Fig. 1): build the circuit for n qubits, cutoff k
+ * (k < 0 or k >= n-1: exact QFT; 0 <= k < n-1: range-k AQFT, Sec. 2),
+ * direction (QFT_FORWARD/QFT_INVERSE) and dtype (QFT_C64/QFT_C128), and plan its
+ * passes.  Host work only, plus a small plan-owned device block.  1 <= n <= 34
+ * (c64) or 33 (c128).  *out is set to NULL on failure. */
+int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, const qft_opts* opts);
+int qft_plan_destroy(qft_plan_t plan);
+int qft_plan_get_info(qft_plan_t plan, qft_plan_info* info);
+
+/* Bytes of caller-allocated device workspace qft_execute needs (always > 0:
+ * it holds scale_in, the status word and the norm partial sums; NATURAL-order
+ * plans of more than one pass also need an N-amplitude ping-pong buffer). */
+size_t qft_workspace_size(qft_plan_t plan);
+
+/* Step 1: copy len complex values from src into the device state buffer
+ * d_state (N = 2^n amplitudes of the plan's dtype).  src is a host pointer
+ * (src_on_device = 0; pinned memory gives an asynchronous copy) or a device
+ * pointer (src_on_device = 1).  len must equal 2^n (QFT_ERR_SIZE otherwise).
+ * The normalisation x / scale_in is deferred: qft_execute computes scale_in
+ * while it reads the state and folds 1/scale_in into its last store. */
+int qft_load(qft_plan_t plan, void* d_state, const void* src, size_t len, int src_on_device,
+             qft_stream_t stream);
+
+/* Steps 1 and 3-4 on the GPU, in place on d_state: scale_in = ||x||_2,
+ * psi' = U (x / scale_in), then the output scaling scale_mode (QFT_SCALE_*).
+ * d_workspace: qft_workspace_size(plan) bytes of device memory, 256-byte
+ * aligned, owned by the caller; after the call its first double holds
+ * scale_in (see qft_get_scale_in).  d_scale_in: optional device pointer that
+ * also receives scale_in (NULL = none).  A zero input gives a zero output and
+ * scale_in = 0.  Concurrent executes must use distinct workspaces. */
+int qft_execute(qft_plan_t plan, void* d_state, void* d_workspace, double* d_scale_in, int scale_mode,
+                qft_stream_t stream);
+
+/* One pass of qft_execute: launches only pass `pass` (0 .. passes-1, see
+ * qft_plan_get_info).  Calling it for pass = 0, 1, ..., passes-1 in order on
+ * one stream is exactly qft_execute (pass 0 also clears the status word); it
+ * lets a caller put events or other work between the HBM sweeps. */
+int qft_execute_pass(qft_plan_t plan, int pass, void* d_state, void* d_workspace, double* d_scale_in,
+                     int scale_mode, qft_stream_t stream);
+
+/* Copy the N results from d_state to dst (host if dst_on_device = 0, else device). */
+int qft_read(qft_plan_t plan, const void* d_state, void* dst, int dst_on_device, qft_stream_t stream);
+
+/* Synchronise stream, then return scale_in recorded in the workspace by the last execute. */
+int qft_get_scale_in(qft_plan_t plan, const void* d_workspace, double* out, qft_stream_t stream);
+
+/* Synchronise stream and read the device status word of the workspace
+ * (0 = ok, QFT_ERR_TIMEOUT if a kernel's bounded wait expired). */
+int qft_check_status(qft_plan_t plan, const void* d_workspace, qft_stream_t stream);
+
+/* Diagnostics: write pass i of the plan as a flat integer record (tile bits,
+ * register stages with their wires and lane maps, tile-index -> wire and
+ * output-address maps, tile-coordinate segments, TMA box geometry, grid,
+ * shared memory, buffers) into out[0..cap); returns the record length or a
+ * negative error.  The record order is fixed by this library version and is
+ * read by the test-suite's index checks; it is not a stable interface. */
+int qft_plan_describe_pass(qft_plan_t plan, int i, long long* out, int cap);
+
+/* Error description (static string). */
+const char* qft_strerror(int code);
+/* cudaError_t value behind the last QFT_ERR_CUDA returned on this thread. */
+int qft_last_cuda_error(void);
+/* Library version as major*10000 + minor*100 + patch. */
+int qft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QFTFFT_H */

@@ -81,6 +81,9 @@ def _load():
         lib.oracle_gate_counts.restype = None
         lib.oracle_gate_list.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int]
         lib.oracle_gate_list.restype = ctypes.c_int
+        lib.oracle_apply_gate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, dp]
+        lib.oracle_apply_gate.restype = None
         lib.oracle_bit_reverse.argtypes = [ctypes.c_int64, ctypes.c_int]
         lib.oracle_bit_reverse.restype = ctypes.c_int64
         lib.oracle_num_threads.argtypes = []
@@ -206,6 +209,15 @@ def gate_list(n: int, k: int = -1, natural_order: bool = True):
         else:
             out.append(("SWAP", a, b))
     return out
+
+
+def apply_gate(psi: np.ndarray, kind: str, a: int = 0, b: int = 0, m: int = 0, sign: int = FORWARD) -> None:
+    """In place on a complex128 array: 'H' on q_a, 'CR' (control a, target b, R_m), or 'SWAPS'."""
+    lib = _load()
+    n = _log2_exact(psi.size)
+    assert psi.dtype == np.complex128 and psi.flags.c_contiguous
+    code = {"H": 0, "CR": 1, "SWAPS": 2}[kind]
+    lib.oracle_apply_gate(n, code, int(a), int(b), int(m), int(sign), _dptr(psi))
 
 
 def bit_reverse(i: int, n: int) -> int:

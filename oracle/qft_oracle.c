@@ -142,6 +142,8 @@ static void apply_swaps(double *psi, int n)
     const int64_t N = (int64_t)1 << n;
     for (int j = 0; j < n / 2; j++) {
         const int64_t bj = (int64_t)1 << j, bk = (int64_t)1 << (n - 1 - j);
+        /* each exchanged pair is visited once, from its bit-j-set member */
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; i++) {
             /* exchange the amplitudes of |..1..0..> and |..0..1..> once */
             if ((i & bj) && !(i & bk)) {
@@ -170,6 +172,16 @@ void oracle_circuit(int n, int k, int sign, int natural_order, double *psi)
         for (int d = 1; d <= kk && d <= t; d++) apply_cp(psi, n, t - d, t, d + 1, sign);
     }
     if (natural_order) apply_swaps(psi, n);
+}
+
+/* Single gates, exposed so that a benchmark can time a bounded sample of a
+ * large circuit (one sweep per gate) without running all of it.
+ * kind 0: H on q_a; 1: controlled-R_m, control q_a, target q_b; 2: the swaps. */
+void oracle_apply_gate(int n, int kind, int a, int b, int m, int sign, double *psi)
+{
+    if (kind == 0) apply_h(psi, n, a);
+    else if (kind == 1) apply_cp(psi, n, a, b, m, sign);
+    else apply_swaps(psi, n);
 }
 
 /* ----------------------------------------------------------------- decode */

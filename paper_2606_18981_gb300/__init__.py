@@ -1,0 +1,242 @@
+"""qftfft: GB300 QFT->FFT library -- thin ctypes binding over libqftfft.so.
+
+Every step of the transform runs in the library's CUDA kernels; this module
+only marshals arguments (device pointers from torch tensors, CUDA stream
+handles, sizes) into the C ABI declared in ``include/qftfft.h``.  There is no
+CPU fallback: importing the package fails loudly if ``libqftfft.so`` has not
+been built (``python paper_2606_18981_gb300/build.py``).
+
+Conventions (Markidis et al., Sec. 2-3): qubit q_j is bit j of the array index;
+FORWARD uses omega_N = e^{-2 pi i / N}; the circuit is U = DFT_N / sqrt(N);
+scale modes STATE / UNITARY / UNNORM / INV_N are the decode rules of Sec. 3
+step 4; order NATURAL applies the qubit-reversal swaps, BITREV leaves them to
+the caller (out[i] holds frequency bitrev_n(i)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqftfft.so")
+
+C64, C128 = 0, 1
+FORWARD, INVERSE = -1, +1
+SCALE_STATE, SCALE_UNITARY, SCALE_UNNORM, SCALE_INV_N = 0, 1, 2, 3
+ORDER_NATURAL, ORDER_BITREV = 0, 1
+OK, ERR_BAD_ARG, ERR_SIZE, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED, ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                      "(python paper_2606_18981_gb300/build.py)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class QftError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = _lib.qft_strerror(code).decode()
+        if code == ERR_CUDA:
+            msg += f" (cudaError {_lib.qft_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [{code}]" if what else f"{msg} [{code}]")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("k_eff", ctypes.c_int), ("direction", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("order", ctypes.c_int),
+                ("n_h", ctypes.c_longlong), ("n_cp", ctypes.c_longlong), ("n_swap", ctypes.c_longlong),
+                ("passes", ctypes.c_int), ("wires_per_pass", ctypes.c_int * 8),
+                ("stages_per_pass", ctypes.c_int * 8), ("tile_bits", ctypes.c_int * 8),
+                ("coalesce_bits", ctypes.c_int * 8), ("workspace_bytes", ctypes.c_size_t),
+                ("bytes_per_execute", ctypes.c_longlong)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("tile_bits", ctypes.c_int), ("coalesce_bits", ctypes.c_int),
+                ("max_stage_bits", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
+                ("test_skip_first_load", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+
+
+_vp = ctypes.c_void_p
+_lib.qft_version.restype = ctypes.c_int
+_lib.qft_strerror.restype = ctypes.c_char_p
+_lib.qft_strerror.argtypes = [ctypes.c_int]
+_lib.qft_last_cuda_error.restype = ctypes.c_int
+_lib.qft_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(Opts)]
+_lib.qft_plan_destroy.argtypes = [_vp]
+_lib.qft_plan_get_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
+_lib.qft_workspace_size.argtypes = [_vp]
+_lib.qft_workspace_size.restype = ctypes.c_size_t
+_lib.qft_load.argtypes = [_vp, _vp, _vp, ctypes.c_size_t, ctypes.c_int, _vp]
+_lib.qft_execute.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.qft_execute_pass.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.qft_read.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.qft_get_scale_in.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+_lib.qft_check_status.argtypes = [_vp, _vp, _vp]
+_lib.qft_plan_describe_pass.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+
+lib = _lib  # the raw ctypes handle (tests call the C ABI through it)
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise QftError(rc, what)
+    return rc
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in (C64, "c64", "complex64"):
+        return C64
+    if dtype in (C128, "c128", "complex128"):
+        return C128
+    s = str(dtype)
+    if s.endswith("complex64"):
+        return C64
+    if s.endswith("complex128"):
+        return C128
+    raise ValueError(f"unsupported dtype {dtype!r}")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    return t if isinstance(t, int) else t.data_ptr()
+
+
+class Plan:
+    """A planned (A)QFT: n qubits, cutoff k (-1 or >= n-1: exact), direction, dtype, order."""
+
+    def __init__(self, n: int, k: int = -1, direction: int = FORWARD, dtype="c64", order: int = ORDER_NATURAL,
+                 tile_bits: int = 0, coalesce_bits: int = 0, max_stage_bits: int = 0,
+                 wait_limit_ms: int = 0, test_skip_first_load: int = 0):
+        self._h = _vp()
+        self.n, self.k, self.direction = int(n), int(k), int(direction)
+        self.dtype = _dtype_code(dtype)
+        self.order = int(order)
+        opts = Opts(order, tile_bits, coalesce_bits, max_stage_bits, wait_limit_ms, test_skip_first_load)
+        _check(_lib.qft_plan_create(ctypes.byref(self._h), self.n, self.k, self.direction, self.dtype,
+                                    ctypes.byref(opts)), "qft_plan_create")
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    @property
+    def N(self) -> int:
+        return 1 << self.n
+
+    @property
+    def elem_bytes(self) -> int:
+        return 8 if self.dtype == C64 else 16
+
+    def info(self) -> PlanInfo:
+        inf = PlanInfo()
+        _check(_lib.qft_plan_get_info(self._h, ctypes.byref(inf)), "qft_plan_get_info")
+        return inf
+
+    def workspace_size(self) -> int:
+        return int(_lib.qft_workspace_size(self._h))
+
+    def describe_pass(self, i: int) -> list[int]:
+        buf = (ctypes.c_longlong * 1024)()
+        m = _check(_lib.qft_plan_describe_pass(self._h, i, buf, 1024), "qft_plan_describe_pass")
+        return list(buf[:m])
+
+    def alloc_workspace(self, device="cuda"):
+        import torch
+
+        return torch.empty(self.workspace_size(), dtype=torch.uint8, device=device)
+
+    def load(self, state, src, stream=None) -> None:
+        """Copy src (host or device tensor / numpy array) into the device state buffer."""
+        on_dev = 1
+        if hasattr(src, "is_cuda"):
+            on_dev = 1 if src.is_cuda else 0
+            ptr, ln = src.data_ptr(), src.numel()
+        else:  # numpy
+            on_dev, ptr, ln = 0, src.ctypes.data, src.size
+        _check(_lib.qft_load(self._h, _ptr(state), ptr, ln, on_dev, _stream_handle(stream)), "qft_load")
+
+    def execute(self, state, workspace, scale_mode: int = SCALE_STATE, scale_out=None, stream=None) -> None:
+        """Run the transform in place on the device state tensor (async on stream)."""
+        _check(_lib.qft_execute(self._h, _ptr(state), _ptr(workspace),
+                                _ptr(scale_out) if scale_out is not None else None,
+                                int(scale_mode), _stream_handle(stream)), "qft_execute")
+
+    def execute_pass(self, i: int, state, workspace, scale_mode: int = SCALE_STATE, scale_out=None,
+                     stream=None) -> None:
+        """Launch pass i only (passes 0..P-1 in order on one stream == execute)."""
+        _check(_lib.qft_execute_pass(self._h, int(i), _ptr(state), _ptr(workspace),
+                                     _ptr(scale_out) if scale_out is not None else None,
+                                     int(scale_mode), _stream_handle(stream)), "qft_execute_pass")
+
+    def read(self, state, dst, stream=None) -> None:
+        on_dev = 1 if getattr(dst, "is_cuda", False) else 0
+        ptr = dst.data_ptr() if hasattr(dst, "data_ptr") else dst.ctypes.data
+        _check(_lib.qft_read(self._h, _ptr(state), ptr, on_dev, _stream_handle(stream)), "qft_read")
+
+    def scale_in(self, workspace, stream=None) -> float:
+        out = ctypes.c_double()
+        _check(_lib.qft_get_scale_in(self._h, _ptr(workspace), ctypes.byref(out), _stream_handle(stream)),
+               "qft_get_scale_in")
+        return out.value
+
+    def status(self, workspace, stream=None) -> int:
+        return _lib.qft_check_status(self._h, _ptr(workspace), _stream_handle(stream))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.qft_plan_destroy(h)
+            self._h = _vp()
+
+
+_plan_cache: dict = {}
+
+
+def fft(x, k: int | None = None, inverse: bool = False, norm: str = "backward", order: str = "natural"):
+    """numpy.fft-style convenience on a CUDA complex tensor (length 2^n), out of place.
+
+    norm="backward": forward unscaled, inverse 1/N (numpy's default);
+    "ortho": 1/sqrt(N) both ways; "forward": forward 1/N, inverse unscaled;
+    "state": the normalised simulator state psi' (Sec. 3 step 4).
+    k: AQFT cutoff (None = exact).
+    """
+    import torch
+
+    if not x.is_cuda:
+        raise ValueError("fft expects a CUDA tensor")
+    N = x.numel()
+    n = N.bit_length() - 1
+    if N < 2 or (1 << n) != N:
+        raise QftError(ERR_SIZE, "fft")
+    direction = INVERSE if inverse else FORWARD
+    modes = {("backward", False): SCALE_UNNORM, ("backward", True): SCALE_INV_N,
+             ("ortho", False): SCALE_UNITARY, ("ortho", True): SCALE_UNITARY,
+             ("forward", False): SCALE_INV_N, ("forward", True): SCALE_UNNORM,
+             ("state", False): SCALE_STATE, ("state", True): SCALE_STATE}
+    mode = modes[(norm, bool(inverse))]
+    ordc = ORDER_NATURAL if order == "natural" else ORDER_BITREV
+    key = (n, -1 if k is None else int(k), direction, _dtype_code(x.dtype), ordc)
+    p = _plan_cache.get(key)
+    if p is None:
+        p = _plan_cache[key] = Plan(n, key[1], direction, key[3], ordc)
+    out = x.contiguous().clone()
+    ws = p.alloc_workspace(x.device)
+    p.execute(out, ws, mode)
+    return out
+
+
+__all__ = ["Plan", "PlanInfo", "QftError", "fft", "lib", "C64", "C128", "FORWARD", "INVERSE",
+           "SCALE_STATE", "SCALE_UNITARY", "SCALE_UNNORM", "SCALE_INV_N", "ORDER_NATURAL", "ORDER_BITREV"]

@@ -1,0 +1,534 @@
+// qft_pass.cu -- the SMEM-staged pass kernel of the QFT->FFT hot path (sm_103a).
+//
+// One launch = one HBM sweep over the state.  A persistent CTA loops over
+// tiles: a tile (2^tb amplitudes, the pass's wire group plus batch wires) is
+// fetched by TMA into buffer A (cp.async.bulk.tensor, or a 1D cp.async.bulk
+// for contiguous tiles), completion tracked by an mbarrier; then the pass's
+// register stages run:
+//
+//   stage s: every thread takes the 2^r amplitudes that differ only in the
+//   stage's r wires (one fused block of the circuit), multiplies them by the
+//   cross twiddle of the controlled phases whose target wire lies above the
+//   block (Eq. 5 / Sec. 2: diagonal two-level updates, folded into one phase
+//   per amplitude computed from exact integer phases), then applies the
+//   block's own Hadamards and controlled phases in registers (Sec. 2,
+//   Fig. 1 order), and writes the amplitudes back to buffer B (XOR-swizzled
+//   so that every stage reads and writes without bank conflicts).
+//
+// The last stage of a pass stores straight from registers to HBM with the
+// output wire->address map of the pass (this is where the qubit-reversal
+// swaps and the decode scale of Sec. 3 step 4 are folded in).  While stages
+// 1.. run on buffer B, the TMA engine already fetches the next tile into A.
+//
+// The first pass also accumulates ||x||^2 (Sec. 3 step 1) from the raw
+// amplitudes it reads; the last pass turns the per-CTA partial sums into
+// scale_in and applies 1/scale_in together with the folded 2^{-n/2} of the
+// n unnormalised butterflies.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "plan.hpp"
+
+namespace qft {
+
+// ------------------------------------------------------------------ helpers
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after limit_ns (the caller reports QFT_ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, const int32_t c[5],
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// exp(2 pi i m / 16) for m = 0..7 (cos, sin): the rotations of controlled
+// phases between wires at distance <= 3 (R_2, R_3, R_4 and their products).
+__device__ constexpr double kW16c[8] = {1.0, 0.92387953251128675613, 0.70710678118654752440,
+                                        0.38268343236508977173, 0.0, -0.38268343236508977173,
+                                        -0.70710678118654752440, -0.92387953251128675613};
+__device__ constexpr double kW16s[8] = {0.0, 0.38268343236508977173, 0.70710678118654752440,
+                                        0.92387953251128675613, 1.0, 0.92387953251128675613,
+                                        0.70710678118654752440, 0.38268343236508977173};
+
+// z *= exp(DIR * 2 pi i m / 16).  With m a compile-time constant after loop
+// unrolling the trivial rotations (1, +-i, -1) reduce to moves and negations.
+template <int DIR, typename V>
+__device__ __forceinline__ void rot16(V& z, int m) {
+    using T = decltype(z.x);
+    m &= 15;
+    if (m == 0) return;
+    const bool neg = m >= 8;
+    const int mm = m & 7;
+    if (mm == 4) {  // multiply by DIR * i
+        const T t = z.x;
+        if (DIR > 0) { z.x = -z.y; z.y = t; } else { z.x = z.y; z.y = -t; }
+    } else if (mm != 0) {
+        const T c = static_cast<T>(kW16c[mm]);
+        const T s = static_cast<T>(DIR > 0 ? kW16s[mm] : -kW16s[mm]);
+        const T re = z.x * c - z.y * s;
+        z.y = z.x * s + z.y * c;
+        z.x = re;
+    }
+    if (neg) { z.x = -z.x; z.y = -z.y; }
+}
+
+__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// exp(DIR * 2 pi i beta / 2^n) for an exact integer phase beta (any 64-bit
+// value; only beta mod 2^n matters), n <= 40.  The phase is reduced exactly
+// in fixed point (2^40 = one turn) to the nearest quarter turn, so the
+// floating-point sine/cosine only sees |x| <= 1/4 (in units of pi).
+template <typename T, int DIR>
+__device__ __forceinline__ typename Vec2<T>::type phase_turns(uint64_t beta, int n) {
+    const uint64_t b = (beta << (64 - n)) >> 24;            // beta mod 2^n, scaled to 2^40 per turn
+    const uint64_t q4 = (b + (1ull << 37)) >> 38;            // nearest quarter turn, 0..4
+    const int64_t rem = static_cast<int64_t>(b) - static_cast<int64_t>(q4 << 38);  // |rem| <= 2^37
+    const T x = static_cast<T>(rem) * static_cast<T>(1.0 / 549755813888.0);      // rem / 2^39
+    T s, c;
+    sincospi_t(x, &s, &c);
+    typename Vec2<T>::type r;
+    switch (q4 & 3) {
+        case 0: r.x = c; r.y = s; break;
+        case 1: r.x = -s; r.y = c; break;
+        case 2: r.x = -c; r.y = -s; break;
+        default: r.x = s; r.y = -c; break;
+    }
+    if (DIR < 0) r.y = -r.y;
+    return r;
+}
+
+// XOR swizzle of buffer B: the low SW bits of a tile index are XORed with the
+// XOR-fold of its higher SW-bit groups.  A bank-conflict-free access needs the
+// lanes of one SMEM wavefront (16 lanes x 8 bytes, or 8 lanes x 16 bytes) to
+// hit distinct SW-bit slots; with this map that holds whenever those lanes'
+// tile bits have distinct residues mod SW, which the planner arranges.
+template <int SW>
+__device__ __forceinline__ uint32_t swz(uint32_t x) {
+    uint32_t y = x >> SW;
+    uint32_t f = 0;
+#pragma unroll
+    for (int i = 0; i < 16 / SW + 1; ++i) { f ^= y; y >>= SW; }
+    return x ^ (f & ((1u << SW) - 1));
+}
+
+// The r-wire sub-circuit of one block, in registers (Sec. 2, Fig. 1): for the
+// block's wires from the top down, the (unnormalised) butterfly H then the
+// controlled phases from the lower wires of the block within distance kk.
+// v[j]: bit e of j is wire wlo + e.  The 1/sqrt(2) of every H is folded into
+// the pass's final scale.
+template <int DIR, int R, typename V>
+__device__ __forceinline__ void block_circuit(V (&v)[1 << R], int kk) {
+    constexpr int NJ = 1 << R;
+#pragma unroll
+    for (int t = R - 1; t >= 0; --t) {
+        const int bit = 1 << t;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            if (!(j & bit)) {
+                const V a = v[j], b = v[j | bit];
+                v[j] = cadd(a, b);
+                v[j | bit] = csub(a, b);
+            }
+        }
+        if (kk >= R - 1) {
+#pragma unroll
+            for (int j = 0; j < NJ; ++j)
+                if (j & bit) rot16<DIR>(v[j], (j & (bit - 1)) << (3 - t));
+        } else {
+            int lo = t - kk;
+            if (lo < 0) lo = 0;
+            const int mask = (bit - 1) & ~((1 << lo) - 1);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j)
+                if (j & bit) rot16<DIR>(v[j], (j & mask) << (3 - t));
+        }
+    }
+}
+
+// Per-stage lookup of a group's base tile index, logical-index bits and
+// output-address offset: group g = (g & 31) | (g >> 5) << 5 splits into a lane
+// part and a high part whose contributions are disjoint, so each is a table.
+struct GroupTab {
+    uint32_t* pb;
+    uint64_t* iw;
+    int64_t* ob;
+};
+
+template <typename T, int DIR, int R>
+__device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& S, const GroupTab& tab,
+                                          int toff, const typename Vec2<T>::type* __restrict__ src,
+                                          bool src_dense, typename Vec2<T>::type* __restrict__ dstB,
+                                          bool to_global, uint64_t I_tile, int64_t out_tile, T scale,
+                                          bool acc_norm, double& norm_acc) {
+    using V = typename Vec2<T>::type;
+    constexpr int NJ = 1 << R;
+    constexpr int SW = sizeof(V) == 8 ? 4 : 3;
+    const int ng = 1 << S.ngbits;
+    const uint32_t q = static_cast<uint32_t>(S.q);
+    uint32_t img[R];
+    int64_t oimg[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        img[e] = swz<SW>(1u << (q + e));
+        oimg[e] = to_global ? (int64_t(1) << P.p_out[q + e]) : 0;
+    }
+    const int n = P.n;
+    const int hi = S.wlo + R - 1;
+    for (int g = threadIdx.x; g < ng; g += kThreads) {
+        const int lo5 = toff + (g & 31), hi5 = toff + 32 + (g >> 5);
+        const uint32_t pb = tab.pb[lo5] | tab.pb[hi5];
+        V v[NJ];
+        if (src_dense) {
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) v[j] = src[pb + (uint32_t(j) << q)];
+        } else {
+            const uint32_t base = swz<SW>(pb);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                uint32_t o = 0;  // swz is XOR-linear: swz(pb | j<<q) = swz(pb) ^ (XOR of img[e], e in j)
+#pragma unroll
+                for (int e = 0; e < R; ++e)
+                    if (j & (1 << e)) o ^= img[e];
+                v[j] = src[base ^ o];
+            }
+        }
+        if (acc_norm) {
+            T a = T(0);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) a += v[j].x * v[j].x + v[j].y * v[j].y;
+            norm_acc += static_cast<double>(a);
+        }
+        if (S.cross) {
+            // rh: bit (n-1-t) = I_t for every wire t above the block.
+            const uint64_t I = I_tile | tab.iw[lo5] | tab.iw[hi5];
+            const uint64_t rh = (__brevll(I) >> (64 - n)) & ((1ull << (n - 1 - hi)) - 1ull);
+#pragma unroll
+            for (int e = 0; e < R; ++e) {
+                const int c = S.wlo + e;
+                uint64_t m = rh;
+                const int lowcut = n - 1 - c - P.kk;  // keep targets t <= c + kk
+                if (lowcut > 0) m &= ~((1ull << lowcut) - 1ull);
+                const V tau = phase_turns<T, DIR>(m << c, n);
+#pragma unroll
+                for (int j = 0; j < NJ; ++j)
+                    if (j & (1 << e)) v[j] = cmul(v[j], tau);
+            }
+        }
+        block_circuit<DIR, R>(v, P.kk);
+        if (to_global) {
+            V* __restrict__ out = static_cast<V*>(P.out);
+            const int64_t ob = out_tile + tab.ob[lo5] + tab.ob[hi5];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                int64_t o = 0;
+#pragma unroll
+                for (int e = 0; e < R; ++e)
+                    if (j & (1 << e)) o += oimg[e];
+                V w = v[j];
+                w.x *= scale;
+                w.y *= scale;
+                out[ob + o] = w;
+            }
+        } else {
+            const uint32_t base = swz<SW>(pb);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                uint32_t o = 0;
+#pragma unroll
+                for (int e = 0; e < R; ++e)
+                    if (j & (1 << e)) o ^= img[e];
+                dstB[base ^ o] = v[j];
+            }
+        }
+    }
+}
+
+template <typename T, int DIR>
+__device__ __forceinline__ void dispatch_stage(const PassParams& P, int s, const GroupTab& tab,
+                                               const typename Vec2<T>::type* src, bool src_dense,
+                                               typename Vec2<T>::type* dstB, bool to_global, uint64_t I_tile,
+                                               int64_t out_tile, T scale, bool acc_norm, double& norm_acc) {
+    const StageDesc& S = P.st[s];
+    switch (S.r) {
+        case 1: run_stage<T, DIR, 1>(P, S, tab, P.tab_off[s], src, src_dense, dstB, to_global, I_tile, out_tile, scale, acc_norm, norm_acc); break;
+        case 2: run_stage<T, DIR, 2>(P, S, tab, P.tab_off[s], src, src_dense, dstB, to_global, I_tile, out_tile, scale, acc_norm, norm_acc); break;
+        case 3: run_stage<T, DIR, 3>(P, S, tab, P.tab_off[s], src, src_dense, dstB, to_global, I_tile, out_tile, scale, acc_norm, norm_acc); break;
+        default: run_stage<T, DIR, 4>(P, S, tab, P.tab_off[s], src, src_dense, dstB, to_global, I_tile, out_tile, scale, acc_norm, norm_acc); break;
+    }
+}
+
+// Deterministic CTA-wide sum (fixed shuffle tree, then warps in order).
+__device__ __forceinline__ double block_sum(double x, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[w] = x;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+    __syncthreads();
+    return t;
+}
+
+// Output factor of the decode step (Sec. 3 step 4) times the folded 2^{-n/2}.
+__device__ __forceinline__ double output_factor(const PassParams& P, double scale_in) {
+    switch (P.scale_mode) {
+        case 0: return scale_in > 0.0 ? P.inv_root_n / scale_in : 0.0;  // state
+        case 1: return P.inv_root_n;                                     // unitary
+        case 2: return 1.0;                                              // unnormalised
+        default: return P.inv_root_n * P.inv_root_n;                     // 1/N
+    }
+}
+
+__device__ __forceinline__ void issue_tile_load(const PassParams& P, const CUtensorMap* map, int64_t tile,
+                                                void* dstA, uint64_t* bar, uint32_t bytes) {
+    mbar_arrive_expect_tx(bar, bytes);
+    if (P.load_mode == 1) {
+        const char* src = static_cast<const char*>(P.in) + static_cast<int64_t>(bytes) * tile;
+        bulk_load_1d(dstA, src, bytes, bar);
+    } else {
+        int32_t c[5];
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            const int len = P.dim_len[d];
+            c[d] = len ? static_cast<int32_t>((tile >> P.dim_src[d]) & ((int64_t(1) << len) - 1)) : 0;
+        }
+        tma_load_5d(dstA, map, c, bar);
+    }
+}
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(kThreads, 1)
+    qft_pass_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassParams P) {
+    using V = typename Vec2<T>::type;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ double red[kThreads / 32];
+
+    const int tid = threadIdx.x;
+    const uint32_t tile_elems = 1u << P.tb;
+    const uint32_t tile_bytes = tile_elems * static_cast<uint32_t>(sizeof(V));
+    V* A = reinterpret_cast<V*>(smem_raw);
+    V* B = A + tile_elems;
+    unsigned char* tab_raw = smem_raw + 2 * static_cast<size_t>(tile_bytes);
+
+    // Group tables: per stage 32 lane entries + max(1, ng/32) high entries,
+    // stage s at entry offset P.tab_off[s] (P.ntab entries in all).
+    const int ntab = P.ntab;
+    GroupTab tab;
+    tab.iw = reinterpret_cast<uint64_t*>(tab_raw);
+    tab.ob = reinterpret_cast<int64_t*>(tab_raw + 8 * static_cast<size_t>(ntab));
+    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + 16 * static_cast<size_t>(ntab));
+    for (int s = 0; s < P.nstages; ++s) {
+        const StageDesc& S = P.st[s];
+        const int ng = 1 << S.ngbits;
+        const int nhi = ng > 32 ? ng >> 5 : 1;
+        for (int i = tid; i < 32 + nhi; i += kThreads) {
+            const int g = i < 32 ? (i < ng ? i : 0) : ((i - 32) << 5);
+            const int gm = i < 32 ? (g & 31) : g;
+            uint32_t pb = 0;
+            uint64_t iw = 0;
+            int64_t ob = 0;
+            for (int b = 0; b < S.ngbits; ++b) {
+                if ((gm >> b) & 1) {
+                    const int p = S.gpos[b];
+                    pb |= 1u << p;
+                    iw |= 1ull << P.p_wire[p];
+                    ob += int64_t(1) << P.p_out[p];
+                }
+            }
+            tab.pb[P.tab_off[s] + i] = pb;
+            tab.iw[P.tab_off[s] + i] = iw;
+            tab.ob[P.tab_off[s] + i] = ob;
+        }
+    }
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+
+    // Last pass of a multi-pass plan: scale_in from the first pass's partials.
+    T scale = T(1);
+    if (P.last && !P.first) {
+        double s = 0.0;
+        for (int i = tid; i < P.npartials; i += kThreads) s += P.partials[i];
+        const double tot = block_sum(s, red);
+        const double scale_in = sqrt(tot);
+        scale = static_cast<T>(output_factor(P, scale_in));
+        if (blockIdx.x == 0 && tid == 0) {
+            P.meta[0] = scale_in;
+            if (P.user_scale) *P.user_scale = scale_in;
+        }
+    }
+
+    double norm_acc = 0.0;
+    int64_t tile = blockIdx.x;
+    uint32_t parity = 0;
+    bool aborted = false;
+    if (tile < P.num_tiles && tid == 0 && !P.test_skip_first_load)
+        issue_tile_load(P, &tmap, tile, A, &mbar, tile_bytes);
+
+    for (; tile < P.num_tiles; tile += gridDim.x) {
+        uint64_t I_tile = 0;
+        int64_t out_tile = 0;
+        for (int sg = 0; sg < P.nseg; ++sg) {
+            const TileSeg& G = P.seg[sg];
+            const uint64_t v = (static_cast<uint64_t>(tile) >> G.src) & ((1ull << G.len) - 1ull);
+            I_tile |= v << G.wire;
+            if (G.out_rev)
+                out_tile += static_cast<int64_t>((__brevll(v) >> (64 - G.len)) << (G.out - G.len + 1));
+            else
+                out_tile += static_cast<int64_t>(v << G.out);
+        }
+        const bool ok = mbar_wait_bounded(&mbar, parity, P.wait_limit_ns);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        if (P.first && P.last) {
+            // Single-pass transform (the whole state is this tile): norm first.
+            double s = 0.0;
+            for (uint32_t i = tid; i < tile_elems; i += kThreads) {
+                const V a = A[i];
+                s += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
+            }
+            const double tot = block_sum(s, red);
+            const double scale_in = sqrt(tot);
+            scale = static_cast<T>(output_factor(P, scale_in));
+            if (tid == 0) {
+                P.meta[0] = scale_in;
+                if (P.user_scale) *P.user_scale = scale_in;
+            }
+        }
+        for (int s = 0; s < P.nstages; ++s) {
+            const bool last_stage = (s == P.nstages - 1);
+            const bool from_A = (s == 0);
+            dispatch_stage<T, DIR>(P, s, tab, from_A ? A : B, from_A,
+                                   B, last_stage, I_tile, out_tile, scale, from_A && P.first && !P.last,
+                                   norm_acc);
+            __syncthreads();
+            if (from_A) {
+                const int64_t nt = tile + gridDim.x;
+                if (tid == 0 && nt < P.num_tiles) {
+                    fence_proxy_async_smem();
+                    issue_tile_load(P, &tmap, nt, A, &mbar, tile_bytes);
+                }
+            }
+        }
+    }
+
+    if (aborted) {
+        if (tid == 0) {
+            atomicExch(P.status, -5);  // QFT_ERR_TIMEOUT
+            // let an in-flight copy land before the CTA's shared memory is released
+            mbar_wait_bounded(&mbar, parity ^ 1u, P.wait_limit_ns);
+        }
+        return;
+    }
+    if (P.first && !P.last) {
+        const double tot = block_sum(norm_acc, red);
+        if (tid == 0) P.partials[blockIdx.x] = tot;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+template <typename T, int DIR>
+static cudaError_t launch_pass_t(const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+                                 cudaStream_t stream) {
+    auto kern = qft_pass_kernel<T, DIR>;
+    static thread_local size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    kern<<<grid, kThreads, smem, stream>>>(map, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass(int dtype, int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+                        cudaStream_t stream) {
+    if (dtype == 0)
+        return dir < 0 ? launch_pass_t<float, -1>(map, P, grid, smem, stream)
+                       : launch_pass_t<float, +1>(map, P, grid, smem, stream);
+    return dir < 0 ? launch_pass_t<double, -1>(map, P, grid, smem, stream)
+                   : launch_pass_t<double, +1>(map, P, grid, smem, stream);
+}
+
+// Dynamic shared memory of one CTA: buffers A and B plus the group tables.
+size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes) {
+    return 2 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (8 + 8 + 4);
+}
+
+}  // namespace qft

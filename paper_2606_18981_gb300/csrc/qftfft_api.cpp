@@ -1,0 +1,623 @@
+// qftfft_api.cpp -- host planner and C ABI of libqftfft (see include/qftfft.h).
+//
+// The planner turns the n-wire (A)QFT circuit (Sec. 3 step 2, Fig. 1) into a
+// few HBM passes (Sec. 3.1: the planner fuses gates into blocks and emits a
+// device-agnostic schedule; here each pass is one launch of the pass kernel):
+//
+//   * n <= tile bits: one pass, the whole state is one CTA tile;
+//   * otherwise the wires are split top-down into groups G_1 .. G_P, one per
+//     pass, each pass's tile being G_j plus "batch" wires that sit at the
+//     lowest addresses so every HBM run is >= 2^coalesce amplitudes long.
+//
+// Output order NATURAL (the swaps applied) is produced by layout adapters:
+// pass 1 writes the top wires to the lowest addresses and the lowest wires to
+// the top (out of place into the workspace), the middle passes work in place
+// there, and the last pass writes the bit-reversed layout back into the
+// caller's state.  BITREV order keeps the identity layout and runs in place.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/qftfft.h"
+#include "plan.hpp"
+
+namespace qft {
+cudaError_t launch_pass(int dtype, int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+                        cudaStream_t stream);
+size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes);
+}  // namespace qft
+
+using namespace qft;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int cuda_fail(cudaError_t e) {
+    g_last_cuda = static_cast<int>(e);
+    return QFT_ERR_CUDA;
+}
+
+// Workspace layout: [0, 4096) meta (scale_in at 0, status word at 8,
+// partials from 64 on); the ping-pong state buffer from 4096.
+constexpr size_t kMetaBytes = 4096;
+constexpr size_t kStatusOff = 8;
+constexpr size_t kPartialOff = 64;
+constexpr int kMaxPartials = (kMetaBytes - kPartialOff) / 8;
+
+struct PassHost {
+    PassParams prm;
+    int in_buf = 0, out_buf = 0;  // 0 = caller's state, 1 = workspace ping-pong buffer
+    int grid = 1;
+    size_t smem = 0;
+    // TMA description
+    int rank = 5;
+    cuuint64_t gdim[5];
+    cuuint64_t gstride[4];
+    cuuint32_t box[5];
+    int wires = 0;
+    int run_bits = 0;  // low input address bits inside the tile (log2 amplitudes per HBM run)
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+struct qft_plan_s {
+    int n = 0, k = -1, kk = 0, dir = -1, dtype = 0, order = 0;
+    size_t esize = 8;
+    int TB = 13, cmin = 2, rmax = 4;
+    uint64_t wait_limit_ns = 2000000000ull;
+    int test_skip_first_load = 0;
+    int num_sms = 148;
+    long long n_h = 0, n_cp = 0, n_swap = 0;
+    std::vector<PassHost> passes;
+    size_t ws_bytes = 0;
+    // tensor maps for the last (state, workspace) pointer pair
+    std::mutex mu;
+    const void* map_state = nullptr;
+    const void* map_work = nullptr;
+    std::vector<CUtensorMap> maps;
+};
+
+namespace {
+
+int effective_k(int n, int k) { return (k < 0 || k > n - 1) ? std::max(n - 1, 0) : k; }
+
+// Build one pass from its wire group [glo, glo + a), batch wires, and the
+// input/output wire -> address maps.
+bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<int>& batch,
+                const std::vector<int>& Lin, const std::vector<int>& Lout, bool first, bool last) {
+    const int n = pl->n;
+    PassParams& P = ph.prm;
+    std::memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.kk = pl->kk;
+    P.first = first;
+    P.last = last;
+    P.inv_root_n = std::ldexp(1.0, -n / 2) * ((n & 1) ? std::sqrt(0.5) : 1.0);
+    ph.wires = a;
+
+    std::vector<char> in_tile(n, 0);
+    for (int w = glo; w < glo + a; ++w) in_tile[w] = 1;
+    for (int w : batch) in_tile[w] = 1;
+    std::vector<int> tw, nt;  // tile wires / non-tile wires, sorted by input address
+    std::vector<int> wire_at(n);
+    for (int w = 0; w < n; ++w) wire_at[Lin[w]] = w;
+    for (int adr = 0; adr < n; ++adr) (in_tile[wire_at[adr]] ? tw : nt).push_back(wire_at[adr]);
+    const int tb = static_cast<int>(tw.size());
+    if (tb > kMaxTileBits || tb < 1) return false;
+    P.tb = tb;
+    P.num_tiles = int64_t(1) << (n - tb);
+    std::vector<int> pos(n, -1);
+    for (int i = 0; i < tb; ++i) {
+        P.p_wire[i] = tw[i];
+        P.p_out[i] = Lout[tw[i]];
+        pos[tw[i]] = i;
+    }
+    // tile coordinate segments (bit m of the tile coordinate <-> wire nt[m])
+    P.nseg = 0;
+    for (int m = 0; m < static_cast<int>(nt.size());) {
+        int len = 1;
+        int dir = 0;
+        while (m + len < static_cast<int>(nt.size()) && nt[m + len] == nt[m + len - 1] + 1) {
+            const int d = Lout[nt[m + len]] - Lout[nt[m + len - 1]];
+            if (d != 1 && d != -1) break;
+            if (dir == 0) dir = d;
+            else if (d != dir) break;
+            ++len;
+        }
+        if (P.nseg >= kMaxSegs) return false;
+        TileSeg& S = P.seg[P.nseg++];
+        S.src = m;
+        S.len = len;
+        S.wire = nt[m];
+        S.out = Lout[nt[m]];
+        S.out_rev = dir < 0 ? 1 : 0;
+        m += len;
+    }
+    // TMA dims: runs of tile / non-tile input address bits, tile runs cut to <= 8 bits
+    const int inner_mult = static_cast<int>(pl->esize / 8);  // UINT64 elements per amplitude
+    int nd = 0;
+    int adr = 0;
+    int m_of_adr = 0;  // tile-coordinate bit index of the next non-tile address
+    if (!in_tile[wire_at[0]]) return false;  // the lowest address must be a tile bit (contiguous runs)
+    while (adr < n) {
+        const bool t = in_tile[wire_at[adr]];
+        int len = 1;
+        while (adr + len < n && static_cast<bool>(in_tile[wire_at[adr + len]]) == t) ++len;
+        if (t) {
+            int left = len, start = adr;
+            while (left > 0) {
+                const int maxbits = (nd == 0) ? (inner_mult == 2 ? 7 : 8) : 8;
+                const int cut = std::min(left, maxbits);
+                if (nd >= kMaxDims) return false;
+                ph.gdim[nd] = (cuuint64_t(1) << cut) * (nd == 0 ? inner_mult : 1);
+                ph.box[nd] = (cuuint32_t(1) << cut) * (nd == 0 ? inner_mult : 1);
+                if (nd > 0) ph.gstride[nd - 1] = (cuuint64_t(1) << start) * pl->esize;
+                P.dim_src[nd] = 0;
+                P.dim_len[nd] = 0;
+                ++nd;
+                start += cut;
+                left -= cut;
+            }
+        } else {
+            if (nd >= kMaxDims) return false;
+            ph.gdim[nd] = cuuint64_t(1) << len;
+            ph.box[nd] = 1;
+            ph.gstride[nd - 1] = (cuuint64_t(1) << adr) * pl->esize;
+            P.dim_src[nd] = m_of_adr;
+            P.dim_len[nd] = len;
+            m_of_adr += len;
+            ++nd;
+        }
+        adr += len;
+    }
+    P.ndims = nd;
+    ph.run_bits = 0;
+    while (ph.run_bits < n && in_tile[wire_at[ph.run_bits]]) ++ph.run_bits;
+    for (int d = nd; d < kMaxDims; ++d) {  // pad to rank 5 with extent-1 dims
+        ph.gdim[d] = 1;
+        ph.box[d] = 1;
+        ph.gstride[d - 1] = (cuuint64_t(1) << n) * pl->esize;
+        P.dim_src[d] = 0;
+        P.dim_len[d] = 0;
+    }
+    for (int d = 0; d < kMaxDims; ++d) P.dim_scale[d] = 1;
+
+    // Stages: the group's wires top-down, split into blocks that are
+    // consecutive both as wires and as tile bits; within each such run the
+    // first block takes the remainder so later blocks have rmax wires.
+    std::vector<std::pair<int, int>> runs;  // (top wire, length)
+    for (int w = glo + a - 1; w >= glo;) {
+        int len = 1;
+        while (w - len >= glo && pos[w - len] == pos[w - len + 1] - 1) ++len;
+        runs.push_back({w, len});
+        w -= len;
+    }
+    P.nstages = 0;
+    for (auto& rr : runs) {
+        int top = rr.first, left = rr.second;
+        int firstr = left % pl->rmax;
+        if (firstr == 0) firstr = std::min(left, pl->rmax);
+        int r = firstr;
+        while (left > 0) {
+            if (P.nstages >= kMaxStages) return false;
+            StageDesc& S = P.st[P.nstages++];
+            S.r = r;
+            S.wlo = top - r + 1;
+            S.q = pos[S.wlo];
+            S.cross = (top < n - 1) ? 1 : 0;
+            S.ngbits = tb - r;
+            top -= r;
+            left -= r;
+            r = std::min(left, pl->rmax);
+        }
+    }
+    // Lane order of each stage's group index.
+    const int SW = pl->esize == 8 ? 4 : 3;     // swizzle slot bits
+    const int wave_lanes = pl->esize == 8 ? 4 : 3;  // log2 lanes per SMEM wavefront
+    for (int s = 0; s < P.nstages; ++s) {
+        StageDesc& S = P.st[s];
+        std::vector<int> others;
+        for (int p = 0; p < tb; ++p)
+            if (p < S.q || p >= S.q + S.r) others.push_back(p);
+        std::vector<int> order;
+        if (s == P.nstages - 1) {
+            // last stage stores to HBM: lanes follow the output address bits
+            order = others;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return P.p_out[x] < P.p_out[y]; });
+        } else {
+            // lanes of one wavefront on distinct residues mod SW (bank-conflict free)
+            std::vector<char> used_res(SW, 0), taken(tb, 0);
+            for (int p : others) {
+                if (static_cast<int>(order.size()) >= wave_lanes) break;
+                if (!used_res[p % SW]) {
+                    used_res[p % SW] = 1;
+                    taken[p] = 1;
+                    order.push_back(p);
+                }
+            }
+            for (int p : others)
+                if (!taken[p]) order.push_back(p);
+        }
+        for (int i = 0; i < S.ngbits; ++i) S.gpos[i] = order[i];
+    }
+    int ntab = 0;
+    for (int s = 0; s < P.nstages; ++s) {
+        P.tab_off[s] = ntab;
+        const int ng = 1 << P.st[s].ngbits;
+        ntab += 32 + (ng > 32 ? ng >> 5 : 1);
+    }
+    P.ntab = ntab;
+    ph.smem = pass_smem_bytes(P, pl->esize);
+    const int64_t tiles = P.num_tiles;
+    ph.grid = static_cast<int>(std::min<int64_t>(tiles, pl->num_sms));
+    return true;
+}
+
+int plan_passes(qft_plan_s* pl) {
+    const int n = pl->n;
+    std::vector<int> ident(n);
+    for (int w = 0; w < n; ++w) ident[w] = w;
+    std::vector<int> brev(n);
+    for (int w = 0; w < n; ++w) brev[w] = n - 1 - w;
+    const bool natural = pl->order == QFT_ORDER_NATURAL;
+
+    if (n <= pl->TB) {
+        PassHost ph;
+        if (!build_pass(pl, ph, 0, n, {}, ident, natural ? brev : ident, true, true)) return QFT_ERR_UNSUPPORTED;
+        ph.prm.load_mode = 1;
+        ph.in_buf = ph.out_buf = 0;
+        pl->passes.push_back(ph);
+        return QFT_OK;
+    }
+    const int TB = pl->TB, cmin = pl->cmin;
+    const int cap = TB - cmin;
+    int P;
+    std::vector<int> a;
+    if (natural) {
+        P = (n + cap - 1) / cap;
+        a.assign(P, n / P);
+        for (int j = 0; j < n % P; ++j) a[j] += 1;
+    } else {
+        P = 1 + (n - TB + cap - 1) / cap;
+        if (P < 2) P = 2;
+        a.assign(P, n / P);
+        for (int j = 0; j < n % P; ++j) a[j] += 1;
+        // the last pass (contiguous, no batch wires) may hold up to TB wires
+        for (int j = 0; j < P - 1; ++j) {
+            while (a[j] > cap) { a[j]--; a[P - 1]++; }
+        }
+        if (a[P - 1] > TB) return QFT_ERR_UNSUPPORTED;
+    }
+    if (P > kMaxPasses) return QFT_ERR_UNSUPPORTED;
+    for (int j = 0; j < P; ++j)
+        if (a[j] > cap + (natural || j < P - 1 ? 0 : cmin) || a[j] < 1) return QFT_ERR_UNSUPPORTED;
+
+    std::vector<int> glo(P);
+    {
+        int top = n;
+        for (int j = 0; j < P; ++j) { top -= a[j]; glo[j] = top; }
+    }
+    const int c1 = std::min(TB - a[0], glo[0]);
+    int ctop = 0;
+    std::vector<int> L1 = ident;
+    if (natural) {
+        ctop = std::min({c1, a[0], TB - a[P - 1], a[P - 1]});
+        if (ctop < 1) return QFT_ERR_UNSUPPORTED;
+        for (int e = 0; e < ctop; ++e) {
+            L1[n - 1 - e] = e;           // top wires to the lowest addresses (their final place)
+            L1[e] = n - ctop + e;        // lowest wires to the top
+        }
+    }
+    for (int j = 0; j < P; ++j) {
+        PassHost ph;
+        const bool first = j == 0, last = j == P - 1;
+        std::vector<int> batch;
+        const std::vector<int>& Lin = first ? ident : L1;
+        std::vector<int> Lout;
+        if (first) {
+            for (int w = 0; w < c1; ++w) batch.push_back(w);
+            Lout = natural ? L1 : ident;
+        } else if (!last) {
+            const int cj = std::min(TB - a[j], glo[j]);
+            std::vector<int> wat(n);
+            for (int w = 0; w < n; ++w) wat[Lin[w]] = w;
+            for (int adr = 0; adr < cj; ++adr) batch.push_back(wat[adr]);
+            Lout = Lin;
+        } else {
+            if (natural)
+                for (int e = 0; e < ctop; ++e) batch.push_back(n - 1 - e);
+            Lout = natural ? brev : ident;
+        }
+        if (!build_pass(pl, ph, glo[j], a[j], batch, Lin, Lout, first, last)) return QFT_ERR_UNSUPPORTED;
+        ph.prm.load_mode = 0;
+        if (natural) {
+            ph.in_buf = first ? 0 : 1;
+            ph.out_buf = last ? 0 : 1;
+        } else {
+            ph.in_buf = ph.out_buf = 0;
+        }
+        pl->passes.push_back(ph);
+    }
+    const int g1 = pl->passes[0].grid;
+    if (g1 > kMaxPartials) return QFT_ERR_UNSUPPORTED;
+    pl->passes.back().prm.npartials = g1;
+    return QFT_OK;
+}
+
+int encode_maps(qft_plan_s* pl, const void* state, const void* work) {
+    if (pl->map_state == state && pl->map_work == work && !pl->maps.empty()) return QFT_OK;
+    auto fn = get_encode_fn();
+    pl->maps.assign(pl->passes.size(), CUtensorMap{});
+    for (size_t i = 0; i < pl->passes.size(); ++i) {
+        PassHost& ph = pl->passes[i];
+        if (ph.prm.load_mode == 1) continue;
+        if (!fn) return cuda_fail(cudaErrorNotSupported);
+        const void* base = ph.in_buf == 0 ? state : work;
+        const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
+        CUresult r = fn(&pl->maps[i], CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(base), ph.gdim,
+                        ph.gstride, ph.box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            g_last_cuda = static_cast<int>(r);
+            pl->maps.clear();
+            return QFT_ERR_CUDA;
+        }
+    }
+    pl->map_state = state;
+    pl->map_work = work;
+    return QFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qft_version(void) { return 100; }
+
+int qft_last_cuda_error(void) { return g_last_cuda; }
+
+const char* qft_strerror(int code) {
+    switch (code) {
+        case QFT_OK: return "ok";
+        case QFT_ERR_BAD_ARG: return "invalid argument";
+        case QFT_ERR_SIZE: return "length is zero or not a power of two";
+        case QFT_ERR_BUDGET: return "request exceeds the HBM admission budget";
+        case QFT_ERR_CUDA: return "CUDA call failed";
+        case QFT_ERR_TIMEOUT: return "bounded wait expired";
+        case QFT_ERR_NOMEM: return "out of memory";
+        case QFT_ERR_UNSUPPORTED: return "unsupported configuration";
+        case QFT_ERR_STATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, const qft_opts* opts) {
+    if (!out) return QFT_ERR_BAD_ARG;
+    *out = nullptr;
+    if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
+    if (direction != QFT_FORWARD && direction != QFT_INVERSE) return QFT_ERR_BAD_ARG;
+    const int nmax = dtype == QFT_C64 ? 34 : 33;
+    if (n < 1 || n > nmax) return QFT_ERR_BAD_ARG;
+    qft_plan_s* pl = new (std::nothrow) qft_plan_s();
+    if (!pl) return QFT_ERR_NOMEM;
+    pl->n = n;
+    pl->k = k;
+    pl->kk = effective_k(n, k);
+    pl->dir = direction;
+    pl->dtype = dtype;
+    pl->esize = dtype == QFT_C64 ? 8 : 16;
+    pl->TB = dtype == QFT_C64 ? 13 : 12;
+    pl->cmin = dtype == QFT_C64 ? 2 : 1;
+    pl->rmax = 4;
+    if (opts) {
+        if (opts->order != QFT_ORDER_NATURAL && opts->order != QFT_ORDER_BITREV) { delete pl; return QFT_ERR_BAD_ARG; }
+        pl->order = opts->order;
+        if (opts->tile_bits) {
+            if (opts->tile_bits < 4 || opts->tile_bits > (dtype == QFT_C64 ? 13 : 12)) { delete pl; return QFT_ERR_BAD_ARG; }
+            pl->TB = opts->tile_bits;
+        }
+        if (opts->coalesce_bits) {
+            if (opts->coalesce_bits < 1 || opts->coalesce_bits > 6) { delete pl; return QFT_ERR_BAD_ARG; }
+            pl->cmin = opts->coalesce_bits;
+        }
+        if (opts->wait_limit_ms < 0) { delete pl; return QFT_ERR_BAD_ARG; }
+        if (opts->wait_limit_ms) pl->wait_limit_ns = uint64_t(opts->wait_limit_ms) * 1000000ull;
+        pl->test_skip_first_load = opts->test_skip_first_load ? 1 : 0;
+        if (opts->max_stage_bits) {
+            if (opts->max_stage_bits < 1 || opts->max_stage_bits > 4) { delete pl; return QFT_ERR_BAD_ARG; }
+            pl->rmax = opts->max_stage_bits;
+        }
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            pl->num_sms = sms;
+    } else {
+        cudaGetLastError();
+    }
+    // gate counters before fusion (Table 2)
+    pl->n_h = n;
+    pl->n_cp = 0;
+    for (int t = n - 1; t >= 0; --t) pl->n_cp += std::min(pl->kk, t);
+    pl->n_swap = n / 2;
+    int rc = plan_passes(pl);
+    if (rc != QFT_OK) {
+        delete pl;
+        return rc;
+    }
+    const size_t N = size_t(1) << n;
+    const bool need_work = pl->order == QFT_ORDER_NATURAL && pl->passes.size() > 1;
+    pl->ws_bytes = kMetaBytes + (need_work ? N * pl->esize : 0);
+    *out = pl;
+    return QFT_OK;
+}
+
+int qft_plan_destroy(qft_plan_t plan) {
+    delete plan;
+    return QFT_OK;
+}
+
+int qft_plan_get_info(qft_plan_t pl, qft_plan_info* info) {
+    if (!pl || !info) return QFT_ERR_BAD_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n = pl->n;
+    info->k_eff = pl->kk;
+    info->direction = pl->dir;
+    info->dtype = pl->dtype;
+    info->order = pl->order;
+    info->n_h = pl->n_h;
+    info->n_cp = pl->n_cp;
+    info->n_swap = pl->n_swap;
+    info->passes = static_cast<int>(pl->passes.size());
+    for (size_t i = 0; i < pl->passes.size() && i < 8; ++i) {
+        const PassHost& ph = pl->passes[i];
+        info->wires_per_pass[i] = ph.wires;
+        info->stages_per_pass[i] = ph.prm.nstages;
+        info->tile_bits[i] = ph.prm.tb;
+        info->coalesce_bits[i] = ph.run_bits;
+    }
+    info->workspace_bytes = pl->ws_bytes;
+    info->bytes_per_execute = static_cast<long long>(pl->passes.size()) * 2LL * (1LL << pl->n) * static_cast<long long>(pl->esize);
+    return QFT_OK;
+}
+
+size_t qft_workspace_size(qft_plan_t pl) { return pl ? pl->ws_bytes : 0; }
+
+int qft_load(qft_plan_t pl, void* d_state, const void* src, size_t len, int src_on_device, qft_stream_t stream) {
+    if (!pl || !d_state || !src) return QFT_ERR_BAD_ARG;
+    if (len != (size_t(1) << pl->n)) return QFT_ERR_SIZE;
+    if (src == d_state) return QFT_OK;
+    cudaError_t e = cudaMemcpyAsync(d_state, src, len * pl->esize,
+                                    src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? QFT_OK : cuda_fail(e);
+}
+
+int qft_read(qft_plan_t pl, const void* d_state, void* dst, int dst_on_device, qft_stream_t stream) {
+    if (!pl || !d_state || !dst) return QFT_ERR_BAD_ARG;
+    if (dst == d_state) return QFT_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, d_state, (size_t(1) << pl->n) * pl->esize,
+                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? QFT_OK : cuda_fail(e);
+}
+
+namespace {
+int execute_range(qft_plan_t pl, void* d_state, void* d_workspace, double* d_scale_in, int scale_mode,
+                  qft_stream_t stream, size_t i0, size_t i1) {
+    if (!pl || !d_state || !d_workspace) return QFT_ERR_BAD_ARG;
+    if (scale_mode < QFT_SCALE_STATE || scale_mode > QFT_SCALE_INV_N) return QFT_ERR_BAD_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_state) & 255) || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+        return QFT_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(d_workspace);
+    void* work = ws + kMetaBytes;
+    std::lock_guard<std::mutex> lock(pl->mu);
+    int rc = encode_maps(pl, d_state, work);
+    if (rc != QFT_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    if (i0 == 0) {
+        e = cudaMemsetAsync(ws + kStatusOff, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    for (size_t i = i0; i < i1; ++i) {
+        PassHost& ph = pl->passes[i];
+        PassParams P = ph.prm;
+        P.scale_mode = scale_mode;
+        P.in = ph.in_buf == 0 ? d_state : work;
+        P.out = ph.out_buf == 0 ? d_state : work;
+        P.partials = reinterpret_cast<double*>(ws + kPartialOff);
+        P.meta = reinterpret_cast<double*>(ws);
+        P.user_scale = d_scale_in;
+        P.status = reinterpret_cast<int32_t*>(ws + kStatusOff);
+        P.wait_limit_ns = pl->wait_limit_ns;
+        P.test_skip_first_load = pl->test_skip_first_load;
+        e = launch_pass(pl->dtype, pl->dir, pl->maps[i], P, ph.grid, ph.smem, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return QFT_OK;
+}
+}  // namespace
+
+int qft_execute(qft_plan_t pl, void* d_state, void* d_workspace, double* d_scale_in, int scale_mode,
+                qft_stream_t stream) {
+    if (!pl) return QFT_ERR_BAD_ARG;
+    return execute_range(pl, d_state, d_workspace, d_scale_in, scale_mode, stream, 0, pl->passes.size());
+}
+
+int qft_execute_pass(qft_plan_t pl, int pass, void* d_state, void* d_workspace, double* d_scale_in,
+                     int scale_mode, qft_stream_t stream) {
+    if (!pl || pass < 0 || pass >= static_cast<int>(pl->passes.size())) return QFT_ERR_BAD_ARG;
+    return execute_range(pl, d_state, d_workspace, d_scale_in, scale_mode, stream, size_t(pass), size_t(pass) + 1);
+}
+
+int qft_plan_describe_pass(qft_plan_t pl, int i, long long* out, int cap) {
+    if (!pl || !out || i < 0 || i >= static_cast<int>(pl->passes.size())) return QFT_ERR_BAD_ARG;
+    const PassHost& ph = pl->passes[i];
+    const PassParams& P = ph.prm;
+    std::vector<long long> v;
+    v.insert(v.end(), {P.n, P.kk, P.tb, P.nstages, P.first, P.last, P.load_mode, (long long)P.num_tiles});
+    for (int s = 0; s < kMaxStages; ++s) {
+        const StageDesc& S = P.st[s];
+        v.insert(v.end(), {S.wlo, S.r, S.q, S.cross, S.ngbits});
+        for (int b = 0; b < kMaxTileBits; ++b) v.push_back(S.gpos[b]);
+    }
+    for (int b = 0; b < kMaxTileBits; ++b) v.push_back(P.p_wire[b]);
+    for (int b = 0; b < kMaxTileBits; ++b) v.push_back(P.p_out[b]);
+    v.push_back(P.nseg);
+    for (int g = 0; g < kMaxSegs; ++g) v.insert(v.end(), {P.seg[g].src, P.seg[g].len, P.seg[g].wire, P.seg[g].out, P.seg[g].out_rev});
+    v.push_back(P.ndims);
+    for (int d = 0; d < kMaxDims; ++d) v.push_back(P.dim_src[d]);
+    for (int d = 0; d < kMaxDims; ++d) v.push_back(P.dim_len[d]);
+    for (int d = 0; d < kMaxDims; ++d) v.push_back((long long)ph.gdim[d]);
+    for (int d = 0; d < 4; ++d) v.push_back((long long)ph.gstride[d]);
+    for (int d = 0; d < kMaxDims; ++d) v.push_back((long long)ph.box[d]);
+    v.insert(v.end(), {ph.grid, (long long)ph.smem, ph.in_buf, ph.out_buf, P.npartials, ph.run_bits});
+    for (size_t j = 0; j < v.size() && static_cast<int>(j) < cap; ++j) out[j] = v[j];
+    return static_cast<int>(v.size());
+}
+
+int qft_get_scale_in(qft_plan_t pl, const void* d_workspace, double* out, qft_stream_t stream) {
+    if (!pl || !d_workspace || !out) return QFT_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaMemcpy(out, d_workspace, sizeof(double), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? QFT_OK : cuda_fail(e);
+}
+
+int qft_check_status(qft_plan_t pl, const void* d_workspace, qft_stream_t stream) {
+    if (!pl || !d_workspace) return QFT_ERR_BAD_ARG;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e);
+    int32_t s = 0;
+    e = cudaMemcpy(&s, static_cast<const char*>(d_workspace) + kStatusOff, sizeof(s), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances (relative L2 error against the FP64 oracle): complex64 <= 2e-6,
+complex128 <= 1e-13 * n.  Element by element every amplitude must also lie
+within 10 x that tolerance of the state's RMS amplitude.  Index maps (the
+qubit-reversal permutation, the bit-reversed order, argmax bins) are compared
+bit-exactly.
+"""
+import numpy as np
+import pytest
+
+import qft_inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+q = pytest.importorskip("paper_2606_18981_gb300")
+
+TOL = {"c64": lambda n: 2e-6, "c128": lambda n: 1e-13 * max(n, 1)}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def assert_close(got, ref, dt, n):
+    tol = TOL[dt](n)
+    err = rel_l2(got, ref)
+    assert err <= tol, f"rel L2 {err:.3e} > {tol:.1e}"
+    rms = np.linalg.norm(ref) / np.sqrt(ref.size)
+    assert np.max(np.abs(got - ref)) <= 10 * tol * max(rms, 1e-300) + 1e-300
+
+
+def tdt(dt):
+    return torch.complex64 if dt == "c64" else torch.complex128
+
+
+def run(x, n, k=-1, direction=-1, dt="c64", order=0, mode=0, tile_bits=0, plan=None):
+    p = plan or q.Plan(n, k, direction, dt, order, tile_bits=tile_bits)
+    state = torch.empty(1 << n, dtype=tdt(dt), device="cuda")
+    pinned = torch.from_numpy(np.ascontiguousarray(x)).to(tdt(dt)).pin_memory()
+    p.load(state, pinned)
+    ws = p.alloc_workspace()
+    p.execute(state, ws, mode)
+    out = state.cpu().numpy().astype(np.complex128)
+    assert p.status(ws) == 0
+    return out, p.scale_in(ws)
+
+
+def as_dt(x, dt):
+    return x.astype(np.complex64 if dt == "c64" else np.complex128).astype(np.complex128)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 10, 12, 13])
+def test_single_pass(oracle_mod, dt, order, n):
+    x = as_dt(qft_inputs.gaussian(n, seed=n, normalise=False), dt)
+    for direction in (-1, +1):
+        got, s = run(x, n, -1, direction, dt, order)
+        ref, s_ref = oracle_mod.qft(x, -1, direction, 0, order == 0)
+        assert abs(s - s_ref) <= 1e-6 * s_ref
+        assert_close(got, ref, dt, n)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("n", [14, 16, 19, 20, 22])
+def test_multi_pass(oracle_mod, dt, order, n):
+    x = as_dt(qft_inputs.tones(n, seed=n), dt)
+    for direction in (-1, +1):
+        got, _ = run(x, n, -1, direction, dt, order)
+        ref, _ = oracle_mod.qft(x, -1, direction, 0, order == 0)
+        assert_close(got, ref, dt, n)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n,tbits", [(12, 5), (13, 6), (15, 7), (16, 6), (11, 8), (14, 9), (9, 4)])
+def test_small_tiles_many_passes(oracle_mod, dt, n, tbits):
+    """Small tiles force 3..7 passes with ragged wire groups."""
+    x = as_dt(qft_inputs.gaussian(n, seed=3 * n, normalise=False), dt)
+    for order in (0, 1):
+        for k in (-1, 1, 3):
+            got, _ = run(x, n, k, -1, dt, order, tile_bits=tbits)
+            ref, _ = oracle_mod.qft(x, k, -1, 0, order == 0)
+            assert_close(got, ref, dt, n)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n", [6, 13, 18, 21])
+def test_aqft_cutoffs(oracle_mod, dt, n):
+    x = as_dt(qft_inputs.gaussian(n, seed=7 + n, normalise=False), dt)
+    for k in (0, 1, 2, 3, 4, 8, 16):
+        if k >= n:
+            continue
+        for direction in (-1, +1):
+            got, _ = run(x, n, k, direction, dt, 0)
+            ref, _ = oracle_mod.qft(x, k, direction, 0, True)
+            assert_close(got, ref, dt, n)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_scale_modes_against_numpy_fft(dt):
+    for n in (9, 17):
+        x = as_dt(qft_inputs.gaussian(n, seed=11, normalise=False), dt)
+        N = 1 << n
+        F = np.fft.fft(x)
+        G = np.fft.ifft(x)
+        cases = [(-1, q.SCALE_UNNORM, F), (-1, q.SCALE_UNITARY, F / np.sqrt(N)), (+1, q.SCALE_INV_N, G),
+                 (+1, q.SCALE_UNNORM, G * N), (-1, q.SCALE_STATE, F / (np.linalg.norm(x) * np.sqrt(N)))]
+        for direction, mode, ref in cases:
+            got, s = run(x, n, -1, direction, dt, 0, mode)
+            assert abs(s - np.linalg.norm(x)) <= 1e-6 * np.linalg.norm(x)
+            assert_close(got, ref, dt, n)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_zero_input(dt):
+    for n in (5, 16):
+        got, s = run(np.zeros(1 << n, dtype=np.complex128), n, -1, -1, dt, 0)
+        assert s == 0.0 and np.all(got == 0)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("n,tbits", [(6, 0), (12, 0), (15, 0), (20, 0), (13, 7)])
+def test_index_maps_bit_exact(dt, order, n, tbits):
+    """k = 0 on small-integer input, unnormalised: every operation is exact, so the
+    output must equal the integer Walsh-Hadamard transform permuted by the
+    qubit reversal (NATURAL) or not (BITREV), bit for bit."""
+    rng = np.random.default_rng(n)
+    xi = rng.integers(-4, 5, size=1 << n) + 1j * rng.integers(-4, 5, size=1 << n)
+    x = xi.astype(np.complex128)
+    # fast integer WHT (Sylvester order), exact in int64
+    w = xi.astype(np.complex128).copy()
+    h = 1
+    while h < w.size:
+        w = w.reshape(-1, 2, h)
+        w = np.stack([w[:, 0] + w[:, 1], w[:, 0] - w[:, 1]], axis=1).reshape(-1)
+        h *= 2
+    if order == 0:
+        rev = np.array([int(format(i, f"0{n}b")[::-1], 2) for i in range(1 << n)])
+        w = w[rev]
+    got, _ = run(x, n, 0, -1, dt, order, q.SCALE_UNNORM, tile_bits=tbits)
+    assert np.array_equal(got, w)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_single_tone_peak_and_basis(dt):
+    for n in (8, 14, 20):
+        for direction in (-1, +1):
+            x = qft_inputs.single_tone(n, 2, direction)
+            got, s = run(x, n, -1, direction, dt, 0)
+            assert int(np.argmax(np.abs(got))) == 2
+            assert abs(abs(got[2]) - 1) < 1e-5
+            j = 5 + n
+            got, _ = run(qft_inputs.basis(n, j), n, -1, direction, dt, 0)
+            y = np.arange(1 << n, dtype=np.int64)
+            ref = np.exp(direction * 2j * np.pi * ((j * y) % (1 << n)) / (1 << n)) / np.sqrt(1 << n)
+            assert_close(got, ref, dt, n)
+
+
+def test_deterministic():
+    for n in (11, 21):
+        x = qft_inputs.gaussian(n, seed=5)
+        a, _ = run(x, n, -1, -1, "c64", 0)
+        b, _ = run(x, n, -1, -1, "c64", 0)
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dt,k", [("c64", -1), ("c64", 4), ("c128", -1), ("c128", 8)])
+def test_n24_full_oracle(oracle_mod, dt, k):
+    n = 24
+    x = as_dt(qft_inputs.gaussian(n, seed=24, normalise=True), dt)
+    got, _ = run(x, n, k, -1, dt, 0)
+    ref, _ = oracle_mod.qft(x, k, -1, 0, True)
+    assert_close(got, ref, dt, n)
+
+
+def test_graph_capture_replay():
+    n = 18
+    p = q.Plan(n)
+    x = torch.from_numpy(qft_inputs.gaussian(n, seed=1)).to(torch.complex64).cuda()
+    state = x.clone()
+    ws = p.alloc_workspace()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p.execute(state, ws, q.SCALE_STATE, stream=s)  # warm-up encodes the tensor maps
+    torch.cuda.synchronize()
+    ref = state.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        p.execute(state, ws, q.SCALE_STATE, stream=s)
+    for _ in range(2):
+        state.copy_(x)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(state, ref)
+
+
+def test_bounded_wait_reports_timeout():
+    """A tile load that never arrives makes the bounded mbarrier wait expire;
+    the kernel reports QFT_ERR_TIMEOUT in the status word and the context stays usable."""
+    p = q.Plan(18, test_skip_first_load=1, wait_limit_ms=20)
+    state = torch.zeros(1 << 18, dtype=torch.complex64, device="cuda")
+    ws = p.alloc_workspace()
+    p.execute(state, ws, q.SCALE_STATE)
+    assert p.status(ws) == q.ERR_TIMEOUT
+    got, _ = run(qft_inputs.gaussian(10, seed=1), 10)  # context still usable
+    assert np.isfinite(got).all()
+
+
+def _bench_like(n, dt, seed):
+    x = qft_inputs.device_gaussian(n, seed, dt)
+    return x
+
+
+@pytest.mark.parametrize("n,dt", [(30, "c64"), (28, "c128")])
+def test_large_sampled_bins(oracle_mod, n, dt):
+    """Large transform in the benchmark's launch configuration: sampled output
+    bins against the oracle's direct O(N) sums, plus the norm."""
+    p = q.Plan(n, -1, -1, dt, 0)
+    x = _bench_like(n, dt, 2024)
+    xh = x.cpu().numpy().astype(np.complex128)
+    state = x.clone()
+    ws = p.alloc_workspace()
+    p.execute(state, ws, q.SCALE_UNITARY)
+    assert p.status(ws) == 0
+    rng = np.random.default_rng(n)
+    ys = np.concatenate([[0, 1, 2, (1 << n) - 1], rng.integers(0, 1 << n, size=4)])
+    got = state[torch.from_numpy(ys).cuda()].cpu().numpy().astype(np.complex128)
+    ref = oracle_mod.aqft_bins(xh, ys, -1, -1)
+    scale = np.linalg.norm(xh) / np.sqrt(1 << n)  # rms amplitude of the unitary output
+    tol = TOL[dt](n)
+    assert np.max(np.abs(got - ref)) <= 10 * tol * scale
+    nrm = torch.linalg.vector_norm(state.to(torch.complex128)).item()
+    assert abs(nrm - np.linalg.norm(xh)) <= 10 * tol * np.linalg.norm(xh)
+
+
+def _chunked_norm(a, b=None, scale_b=1.0, chunk=1 << 26):
+    """||a - scale_b * b|| (or ||a||) in float64 without materialising full-size temporaries."""
+    acc = 0.0
+    for s in range(0, a.numel(), chunk):
+        d = a[s:s + chunk].to(torch.complex128)
+        if b is not None:
+            d = d - b[s:s + chunk].to(torch.complex128) * scale_b
+        acc += float(torch.sum(d.real ** 2 + d.imag ** 2).item())
+    return acc ** 0.5
+
+
+@pytest.mark.parametrize("n,dt", [(33, "c64"), (32, "c128")])
+def test_max_size_round_trip(n, dt):
+    """Largest sizes (64 GiB states): forward then inverse returns the normalised
+    input; the forward result keeps unit norm."""
+    free, _ = torch.cuda.mem_get_info()
+    need = 3 * (1 << n) * (8 if dt == "c64" else 16) + (4 << 30)
+    if free < need:
+        pytest.skip(f"needs {need / 2**30:.0f} GiB free")
+    x = _bench_like(n, dt, 7)
+    pf = q.Plan(n, -1, -1, dt, 0)
+    pi = q.Plan(n, -1, +1, dt, 0)
+    ws = pf.alloc_workspace()
+    state = x.clone()
+    pf.execute(state, ws, q.SCALE_STATE)
+    assert pf.status(ws) == 0
+    assert abs(_chunked_norm(state) - 1.0) < 1e-5
+    pi.execute(state, ws, q.SCALE_STATE)
+    assert pi.status(ws) == 0
+    x_norm = _chunked_norm(x)
+    assert _chunked_norm(state, x, 1.0 / x_norm) <= 2 * TOL[dt](n)
+    del state, x, ws
+    torch.cuda.empty_cache()

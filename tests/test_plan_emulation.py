@@ -1,0 +1,79 @@
+"""Planner checks on the CPU: index maps, TMA boxes and the pass arithmetic.
+
+Each plan built by libqftfft is replayed by tests/plan_emulator.py (numpy,
+float64) and compared with the oracle; the emulator also asserts that every
+index is in bounds and every map is a bijection.  Large plans (up to n = 34)
+get the data-free structural checks.  No GPU is needed: plan creation is host
+code.
+"""
+import numpy as np
+import pytest
+
+import qft_inputs
+
+q = pytest.importorskip("paper_2606_18981_gb300")
+from plan_emulator import check_structure, emulate, parse  # noqa: E402
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+CASES = []
+for dt in ("c64", "c128"):
+    for order in (q.ORDER_NATURAL, q.ORDER_BITREV):
+        for n in (1, 2, 3, 5, 8, 12):
+            CASES.append((n, -1, dt, order, 0))
+        for n, tbits in ((9, 5), (12, 5), (13, 6), (14, 7), (15, 6), (16, 8), (8, 4), (14, 5)):
+            CASES.append((n, -1, dt, order, tbits))
+        CASES.append((14, 0, dt, order, 0))
+        CASES.append((15, 2, dt, order, 6))
+        CASES.append((13, 4, dt, order, 5))
+
+
+@pytest.mark.parametrize("n,k,dt,order,tbits", CASES)
+def test_emulated_plan_matches_oracle(oracle_mod, n, k, dt, order, tbits):
+    x = qft_inputs.gaussian(n, seed=1000 + n, normalise=False)
+    for direction in (q.FORWARD, q.INVERSE):
+        p = q.Plan(n, k, direction, dt, order, tile_bits=tbits)
+        for mode in (q.SCALE_STATE, q.SCALE_UNNORM):
+            got = emulate(p, x, mode)
+            ref, _ = oracle_mod.qft(x, k=k, sign=direction, mode=mode, natural_order=(order == q.ORDER_NATURAL))
+            assert rel_l2(got, ref) < 1e-12, (n, k, dt, order, tbits, direction, mode)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("order", [0, 1])
+def test_structure_all_sizes(dt, order):
+    nmax = 34 if dt == "c64" else 33
+    esize = 8 if dt == "c64" else 16
+    for n in range(1, nmax + 1):
+        for k in (-1, 0, 4):
+            p = q.Plan(n, k, q.FORWARD, dt, order)
+            inf = p.info()
+            assert inf.n_h == n and inf.n_swap == n // 2
+            for i in range(inf.passes):
+                P = parse(p.describe_pass(i))
+                check_structure(P, esize)
+                if P["load_mode"] == 0:
+                    assert P["run_bits"] >= (2 if dt == "c64" else 1), "HBM runs must be >= 32 bytes"
+
+
+def test_plan_counters_table2():
+    """Pre-fusion counters of the plan reproduce Table 2 for n = 22."""
+    for k, cnt in ((21, 231), (16, 216), (12, 186), (10, 165), (8, 140), (6, 111), (4, 78)):
+        assert q.Plan(22, k).info().n_cp == cnt
+
+
+def test_plan_argument_errors():
+    with pytest.raises(q.QftError) as e:
+        q.Plan(0)
+    assert e.value.code == q.ERR_BAD_ARG
+    with pytest.raises(q.QftError):
+        q.Plan(35, dtype="c64")
+    with pytest.raises(q.QftError):
+        q.Plan(34, dtype="c128")
+    with pytest.raises(q.QftError):
+        q.Plan(10, direction=2)
+    with pytest.raises(ValueError):
+        q.Plan(10, dtype="c32")
