@@ -39,6 +39,8 @@ struct StageDesc {
     int32_t q;      // tile index bit that holds wire wlo; the block occupies tile bits [q, q + r)
     int32_t cross;  // 1 if some wire above the block exists (cross twiddle (a) is not identity)
     int32_t ngbits; // tb - r: bits of the group index
+    int32_t tile_above;  // 1 if a tile-coordinate wire lies above the block (per-tile twiddle U needed)
+    int32_t uoff;        // offset of this stage's r per-tile twiddles in the U table
     int32_t gpos[kMaxTileBits];  // group-index bit i -> tile index bit (lanes use the low group bits)
 };
 
@@ -63,6 +65,7 @@ struct PassParams {
     StageDesc st[kMaxStages];
     int32_t tab_off[kMaxStages];   // group-table entry offset of each stage (32 lane + high entries)
     int32_t ntab;                  // total group-table entries
+    int32_t nU;                    // per-tile twiddles of all stages (sum of r)
     int32_t p_wire[kMaxTileBits];  // tile index bit -> logical wire
     int32_t p_out[kMaxTileBits];   // tile index bit -> output address bit
     int32_t nseg;

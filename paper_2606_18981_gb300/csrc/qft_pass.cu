@@ -216,35 +216,58 @@ __device__ __forceinline__ void block_circuit(V (&v)[1 << R], int kk) {
     }
 }
 
-// Per-stage lookup of a group's base tile index, logical-index bits and
-// output-address offset: group g = (g & 31) | (g >> 5) << 5 splits into a lane
-// part and a high part whose contributions are disjoint, so each is a table.
+// Per-stage group tables.  A group g (the 2^r amplitudes one thread holds in a
+// stage) splits as g = (g & 31) | (g >> 5) << 5 into a lane part and a high
+// part whose tile bits are disjoint, so every per-group quantity that is
+// additive over disjoint bits is the combination of one lane entry (index
+// g & 31) and one high entry (index 32 + (g >> 5)):
+//   pb  tile index bits (OR),  ob  output address offset (sum),
+//   V   the cross-twiddle factors exp(s 2 pi i beta_e / 2^n) of the group's
+//       tile wires above the block, one per block wire e (product).
+// The tile coordinate's share of the cross twiddle, U_e, is computed once per
+// tile.  beta_e is additive over disjoint wire sets, so the full cross twiddle
+// of block wire e is U_e * V_e(lane entry) * V_e(high entry).
+template <typename V>
 struct GroupTab {
     uint32_t* pb;
-    uint64_t* iw;
     int64_t* ob;
+    V* tw;  // [entry][4]
 };
 
+// Integer phase beta_e of block wire c = wlo + e for the logical bits I (only
+// wires above hi = wlo + r - 1 matter): the controlled phases CP(c, t) with
+// t > hi, t - c <= kk, in units of 2^-n turns (Eq. 5 / Sec. 2).
+__device__ __forceinline__ uint64_t cross_phase(uint64_t I, int n, int hi, int c, int kk) {
+    const uint64_t rh = (__brevll(I) >> (64 - n)) & ((1ull << (n - 1 - hi)) - 1ull);
+    uint64_t m = rh;
+    const int lowcut = n - 1 - c - kk;  // keep targets t <= c + kk
+    if (lowcut > 0) m &= ~((1ull << lowcut) - 1ull);
+    return m << c;
+}
+
 template <typename T, int DIR, int R>
-__device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& S, const GroupTab& tab,
+__device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& S, const GroupTab<typename Vec2<T>::type>& tab,
                                           int toff, const typename Vec2<T>::type* __restrict__ src,
                                           bool src_dense, typename Vec2<T>::type* __restrict__ dstB,
-                                          bool to_global, uint64_t I_tile, int64_t out_tile, T scale,
-                                          bool acc_norm, double& norm_acc) {
+                                          bool to_global, int64_t out_tile, T scale,
+                                          const typename Vec2<T>::type* __restrict__ U, bool acc_norm,
+                                          double& norm_acc) {
     using V = typename Vec2<T>::type;
     constexpr int NJ = 1 << R;
     constexpr int SW = sizeof(V) == 8 ? 4 : 3;
     const int ng = 1 << S.ngbits;
     const uint32_t q = static_cast<uint32_t>(S.q);
-    uint32_t img[R];
-    int64_t oimg[R];
+    // swizzled offsets of the register bits (swz is XOR-linear), built by Gray steps
+    uint32_t soff[NJ];
+    soff[0] = 0;
 #pragma unroll
-    for (int e = 0; e < R; ++e) {
-        img[e] = swz<SW>(1u << (q + e));
-        oimg[e] = to_global ? (int64_t(1) << P.p_out[q + e]) : 0;
+    for (int j = 1; j < NJ; ++j) soff[j] = soff[j & (j - 1)] ^ swz<SW>(1u << (q + (__ffs(j) - 1)));
+    V u[R];
+    const bool use_u = S.cross && S.tile_above;
+    if (use_u) {
+#pragma unroll
+        for (int e = 0; e < R; ++e) u[e] = U[e];
     }
-    const int n = P.n;
-    const int hi = S.wlo + R - 1;
     for (int g = threadIdx.x; g < ng; g += kThreads) {
         const int lo5 = toff + (g & 31), hi5 = toff + 32 + (g >> 5);
         const uint32_t pb = tab.pb[lo5] | tab.pb[hi5];
@@ -255,13 +278,7 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
         } else {
             const uint32_t base = swz<SW>(pb);
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                uint32_t o = 0;  // swz is XOR-linear: swz(pb | j<<q) = swz(pb) ^ (XOR of img[e], e in j)
-#pragma unroll
-                for (int e = 0; e < R; ++e)
-                    if (j & (1 << e)) o ^= img[e];
-                v[j] = src[base ^ o];
-            }
+            for (int j = 0; j < NJ; ++j) v[j] = src[base ^ soff[j]];
         }
         if (acc_norm) {
             T a = T(0);
@@ -270,16 +287,12 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
             norm_acc += static_cast<double>(a);
         }
         if (S.cross) {
-            // rh: bit (n-1-t) = I_t for every wire t above the block.
-            const uint64_t I = I_tile | tab.iw[lo5] | tab.iw[hi5];
-            const uint64_t rh = (__brevll(I) >> (64 - n)) & ((1ull << (n - 1 - hi)) - 1ull);
+            const V* tl = tab.tw + 4 * lo5;
+            const V* th = tab.tw + 4 * hi5;
 #pragma unroll
             for (int e = 0; e < R; ++e) {
-                const int c = S.wlo + e;
-                uint64_t m = rh;
-                const int lowcut = n - 1 - c - P.kk;  // keep targets t <= c + kk
-                if (lowcut > 0) m &= ~((1ull << lowcut) - 1ull);
-                const V tau = phase_turns<T, DIR>(m << c, n);
+                V tau = cmul(tl[e], th[e]);
+                if (use_u) tau = cmul(tau, u[e]);
 #pragma unroll
                 for (int j = 0; j < NJ; ++j)
                     if (j & (1 << e)) v[j] = cmul(v[j], tau);
@@ -287,44 +300,42 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
         }
         block_circuit<DIR, R>(v, P.kk);
         if (to_global) {
-            V* __restrict__ out = static_cast<V*>(P.out);
-            const int64_t ob = out_tile + tab.ob[lo5] + tab.ob[hi5];
+            V* __restrict__ out = static_cast<V*>(P.out) + (out_tile + tab.ob[lo5] + tab.ob[hi5]);
+            int64_t oo[R];
+#pragma unroll
+            for (int e = 0; e < R; ++e) oo[e] = int64_t(1) << P.p_out[q + e];
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
                 int64_t o = 0;
 #pragma unroll
                 for (int e = 0; e < R; ++e)
-                    if (j & (1 << e)) o += oimg[e];
+                    if (j & (1 << e)) o += oo[e];
                 V w = v[j];
                 w.x *= scale;
                 w.y *= scale;
-                out[ob + o] = w;
+                out[o] = w;
             }
         } else {
             const uint32_t base = swz<SW>(pb);
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                uint32_t o = 0;
-#pragma unroll
-                for (int e = 0; e < R; ++e)
-                    if (j & (1 << e)) o ^= img[e];
-                dstB[base ^ o] = v[j];
-            }
+            for (int j = 0; j < NJ; ++j) dstB[base ^ soff[j]] = v[j];
         }
     }
 }
 
 template <typename T, int DIR>
-__device__ __forceinline__ void dispatch_stage(const PassParams& P, int s, const GroupTab& tab,
+__device__ __forceinline__ void dispatch_stage(const PassParams& P, int s, const GroupTab<typename Vec2<T>::type>& tab,
                                                const typename Vec2<T>::type* src, bool src_dense,
-                                               typename Vec2<T>::type* dstB, bool to_global, uint64_t I_tile,
-                                               int64_t out_tile, T scale, bool acc_norm, double& norm_acc) {
+                                               typename Vec2<T>::type* dstB, bool to_global, int64_t out_tile,
+                                               T scale, const typename Vec2<T>::type* U, bool acc_norm,
+                                               double& norm_acc) {
     const StageDesc& S = P.st[s];
+    const int toff = P.tab_off[s];
     switch (S.r) {
-        case 1: run_stage<T, DIR, 1>(P, S, tab, P.tab_off[s], src, src_dense, dstB, to_global, I_tile, out_tile, scale, acc_norm, norm_acc); break;
-        case 2: run_stage<T, DIR, 2>(P, S, tab, P.tab_off[s], src, src_dense, dstB, to_global, I_tile, out_tile, scale, acc_norm, norm_acc); break;
-        case 3: run_stage<T, DIR, 3>(P, S, tab, P.tab_off[s], src, src_dense, dstB, to_global, I_tile, out_tile, scale, acc_norm, norm_acc); break;
-        default: run_stage<T, DIR, 4>(P, S, tab, P.tab_off[s], src, src_dense, dstB, to_global, I_tile, out_tile, scale, acc_norm, norm_acc); break;
+        case 1: run_stage<T, DIR, 1>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
+        case 2: run_stage<T, DIR, 2>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
+        case 3: run_stage<T, DIR, 3>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
+        default: run_stage<T, DIR, 4>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
     }
 }
 
@@ -368,52 +379,96 @@ __device__ __forceinline__ void issue_tile_load(const PassParams& P, const CUten
     }
 }
 
+// Logical bits of the tile coordinate and its output address offset.
+__device__ __forceinline__ void tile_coords(const PassParams& P, int64_t tile, uint64_t& I_tile, int64_t& out_tile) {
+    I_tile = 0;
+    out_tile = 0;
+    for (int sg = 0; sg < P.nseg; ++sg) {
+        const TileSeg& G = P.seg[sg];
+        const uint64_t v = (static_cast<uint64_t>(tile) >> G.src) & ((1ull << G.len) - 1ull);
+        I_tile |= v << G.wire;
+        if (G.out_rev)
+            out_tile += static_cast<int64_t>((__brevll(v) >> (64 - G.len)) << (G.out - G.len + 1));
+        else
+            out_tile += static_cast<int64_t>(v << G.out);
+    }
+}
+
+// U_e for every stage of one tile: thread i < nU computes entry i.
+template <typename T, int DIR>
+__device__ __forceinline__ void compute_tile_twiddles(const PassParams& P, int64_t tile,
+                                                      typename Vec2<T>::type* Ubuf) {
+    const int i = threadIdx.x;
+    if (i >= P.nU || tile >= P.num_tiles) return;
+    int s = 0;
+    while (s + 1 < P.nstages && P.st[s + 1].uoff <= i) ++s;
+    const StageDesc& S = P.st[s];
+    const int e = i - S.uoff;
+    uint64_t I_tile;
+    int64_t dummy;
+    tile_coords(P, tile, I_tile, dummy);
+    const uint64_t beta = cross_phase(I_tile, P.n, S.wlo + S.r - 1, S.wlo + e, P.kk);
+    Ubuf[i] = phase_turns<T, DIR>(beta, P.n);
+}
+
 template <typename T, int DIR>
 __global__ void __launch_bounds__(kThreads, 1)
     qft_pass_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassParams P) {
     using V = typename Vec2<T>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ double red[kThreads / 32];
+    __shared__ __align__(16) V Ubuf[2][4 * kMaxStages];
 
     const int tid = threadIdx.x;
     const uint32_t tile_elems = 1u << P.tb;
     const uint32_t tile_bytes = tile_elems * static_cast<uint32_t>(sizeof(V));
-    V* A = reinterpret_cast<V*>(smem_raw);
-    V* B = A + tile_elems;
-    unsigned char* tab_raw = smem_raw + 2 * static_cast<size_t>(tile_bytes);
-
-    // Group tables: per stage 32 lane entries + max(1, ng/32) high entries,
-    // stage s at entry offset P.tab_off[s] (P.ntab entries in all).
+    // buffer B first, then the two TMA load buffers, then the group tables
+    V* B = reinterpret_cast<V*>(smem_raw);
+    V* A[2] = {B + tile_elems, B + 2 * tile_elems};
+    unsigned char* tab_raw = smem_raw + 3 * static_cast<size_t>(tile_bytes);
     const int ntab = P.ntab;
-    GroupTab tab;
-    tab.iw = reinterpret_cast<uint64_t*>(tab_raw);
-    tab.ob = reinterpret_cast<int64_t*>(tab_raw + 8 * static_cast<size_t>(ntab));
-    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + 16 * static_cast<size_t>(ntab));
+    GroupTab<V> tab;
+    tab.tw = reinterpret_cast<V*>(tab_raw);
+    tab.ob = reinterpret_cast<int64_t*>(tab_raw + 4 * sizeof(V) * static_cast<size_t>(ntab));
+    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (4 * sizeof(V) + 8) * static_cast<size_t>(ntab));
+
+    // Build the group tables (pb, ob, cross-twiddle factors of the group's tile wires).
     for (int s = 0; s < P.nstages; ++s) {
         const StageDesc& S = P.st[s];
         const int ng = 1 << S.ngbits;
         const int nhi = ng > 32 ? ng >> 5 : 1;
         for (int i = tid; i < 32 + nhi; i += kThreads) {
             const int g = i < 32 ? (i < ng ? i : 0) : ((i - 32) << 5);
-            const int gm = i < 32 ? (g & 31) : g;
             uint32_t pb = 0;
             uint64_t iw = 0;
             int64_t ob = 0;
             for (int b = 0; b < S.ngbits; ++b) {
-                if ((gm >> b) & 1) {
+                if ((g >> b) & 1) {
                     const int p = S.gpos[b];
                     pb |= 1u << p;
                     iw |= 1ull << P.p_wire[p];
                     ob += int64_t(1) << P.p_out[p];
                 }
             }
-            tab.pb[P.tab_off[s] + i] = pb;
-            tab.iw[P.tab_off[s] + i] = iw;
-            tab.ob[P.tab_off[s] + i] = ob;
+            const int idx = P.tab_off[s] + i;
+            tab.pb[idx] = pb;
+            tab.ob[idx] = ob;
+            for (int e = 0; e < 4; ++e) {
+                V w;
+                w.x = T(1);
+                w.y = T(0);
+                if (S.cross && e < S.r) w = phase_turns<T, DIR>(cross_phase(iw, P.n, S.wlo + S.r - 1, S.wlo + e, P.kk), P.n);
+                tab.tw[4 * idx + e] = w;
+            }
         }
     }
-    if (tid == 0) mbar_init(&mbar, 1);
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+    }
+    int64_t tile = blockIdx.x;
+    compute_tile_twiddles<T, DIR>(P, tile, Ubuf[0]);
     __syncthreads();
 
     // Last pass of a multi-pass plan: scale_in from the first pass's partials.
@@ -431,26 +486,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     double norm_acc = 0.0;
-    int64_t tile = blockIdx.x;
-    uint32_t parity = 0;
+    uint32_t parity[2] = {0u, 0u};
     bool aborted = false;
-    if (tile < P.num_tiles && tid == 0 && !P.test_skip_first_load)
-        issue_tile_load(P, &tmap, tile, A, &mbar, tile_bytes);
+    if (tid == 0 && !P.test_skip_first_load) {
+        if (tile < P.num_tiles) issue_tile_load(P, &tmap, tile, A[0], &mbar[0], tile_bytes);
+        if (tile + gridDim.x < P.num_tiles) issue_tile_load(P, &tmap, tile + gridDim.x, A[1], &mbar[1], tile_bytes);
+    }
 
-    for (; tile < P.num_tiles; tile += gridDim.x) {
-        uint64_t I_tile = 0;
-        int64_t out_tile = 0;
-        for (int sg = 0; sg < P.nseg; ++sg) {
-            const TileSeg& G = P.seg[sg];
-            const uint64_t v = (static_cast<uint64_t>(tile) >> G.src) & ((1ull << G.len) - 1ull);
-            I_tile |= v << G.wire;
-            if (G.out_rev)
-                out_tile += static_cast<int64_t>((__brevll(v) >> (64 - G.len)) << (G.out - G.len + 1));
-            else
-                out_tile += static_cast<int64_t>(v << G.out);
-        }
-        const bool ok = mbar_wait_bounded(&mbar, parity, P.wait_limit_ns);
-        parity ^= 1u;
+    for (int k = 0; tile < P.num_tiles; tile += gridDim.x, ++k) {
+        const int buf = k & 1;
+        uint64_t I_tile;
+        int64_t out_tile;
+        tile_coords(P, tile, I_tile, out_tile);
+        const bool ok = mbar_wait_bounded(&mbar[buf], parity[buf], P.wait_limit_ns);
+        parity[buf] ^= 1u;
         if (__syncthreads_or(!ok)) {
             aborted = true;
             break;
@@ -459,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // Single-pass transform (the whole state is this tile): norm first.
             double s = 0.0;
             for (uint32_t i = tid; i < tile_elems; i += kThreads) {
-                const V a = A[i];
+                const V a = A[buf][i];
                 s += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
             }
             const double tot = block_sum(s, red);
@@ -470,18 +519,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (P.user_scale) *P.user_scale = scale_in;
             }
         }
+        const V* Ucur = Ubuf[buf];
         for (int s = 0; s < P.nstages; ++s) {
             const bool last_stage = (s == P.nstages - 1);
             const bool from_A = (s == 0);
-            dispatch_stage<T, DIR>(P, s, tab, from_A ? A : B, from_A,
-                                   B, last_stage, I_tile, out_tile, scale, from_A && P.first && !P.last,
-                                   norm_acc);
+            dispatch_stage<T, DIR>(P, s, tab, from_A ? A[buf] : B, from_A, B, last_stage, out_tile, scale,
+                                   Ucur + P.st[s].uoff, from_A && P.first && !P.last, norm_acc);
+            if (last_stage) compute_tile_twiddles<T, DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1]);
             __syncthreads();
             if (from_A) {
-                const int64_t nt = tile + gridDim.x;
+                // A[buf] is consumed: fetch the tile after next into it.
+                const int64_t nt = tile + 2 * static_cast<int64_t>(gridDim.x);
                 if (tid == 0 && nt < P.num_tiles) {
                     fence_proxy_async_smem();
-                    issue_tile_load(P, &tmap, nt, A, &mbar, tile_bytes);
+                    issue_tile_load(P, &tmap, nt, A[buf], &mbar[buf], tile_bytes);
                 }
             }
         }
@@ -490,8 +541,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (aborted) {
         if (tid == 0) {
             atomicExch(P.status, -5);  // QFT_ERR_TIMEOUT
-            // let an in-flight copy land before the CTA's shared memory is released
-            mbar_wait_bounded(&mbar, parity ^ 1u, P.wait_limit_ns);
+            // let in-flight copies land before the CTA's shared memory is released
+            for (int b = 0; b < 2; ++b) mbar_wait_bounded(&mbar[b], parity[b], P.wait_limit_ns);
         }
         return;
     }
@@ -526,9 +577,10 @@ cudaError_t launch_pass(int dtype, int dir, const CUtensorMap& map, const PassPa
                    : launch_pass_t<double, +1>(map, P, grid, smem, stream);
 }
 
-// Dynamic shared memory of one CTA: buffers A and B plus the group tables.
+// Dynamic shared memory of one CTA: buffer B, the two TMA load buffers and
+// the group tables (4 twiddle factors + output offset + tile bits per entry).
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes) {
-    return 2 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (8 + 8 + 4);
+    return 3 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (4 * elem_bytes + 8 + 4);
 }
 
 }  // namespace qft

@@ -105,7 +105,7 @@ int effective_k(int n, int k) { return (k < 0 || k > n - 1) ? std::max(n - 1, 0)
 
 // Build one pass from its wire group [glo, glo + a), batch wires, and the
 // input/output wire -> address maps.
-bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<int>& batch,
+bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<int>& batch_in,
                 const std::vector<int>& Lin, const std::vector<int>& Lout, bool first, bool last) {
     const int n = pl->n;
     PassParams& P = ph.prm;
@@ -119,10 +119,25 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
 
     std::vector<char> in_tile(n, 0);
     for (int w = glo; w < glo + a; ++w) in_tile[w] = 1;
+    std::vector<int> batch = batch_in;
     for (int w : batch) in_tile[w] = 1;
-    std::vector<int> tw, nt;  // tile wires / non-tile wires, sorted by input address
     std::vector<int> wire_at(n);
     for (int w = 0; w < n; ++w) wire_at[Lin[w]] = w;
+    // Fill the tile to the full tile width with the lowest-address non-tile
+    // wires: more batch wires only lengthen the HBM runs and keep every
+    // thread of the CTA busy in every stage.
+    {
+        int have = a + static_cast<int>(batch.size());
+        for (int adr = 0; adr < n && have < std::min(pl->TB, n); ++adr) {
+            const int w = wire_at[adr];
+            if (!in_tile[w]) {
+                in_tile[w] = 1;
+                batch.push_back(w);
+                ++have;
+            }
+        }
+    }
+    std::vector<int> tw, nt;  // tile wires / non-tile wires, sorted by input address
     for (int adr = 0; adr < n; ++adr) (in_tile[wire_at[adr]] ? tw : nt).push_back(wire_at[adr]);
     const int tb = static_cast<int>(tw.size());
     if (tb > kMaxTileBits || tb < 1) return false;
@@ -228,6 +243,9 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
             S.q = pos[S.wlo];
             S.cross = (top < n - 1) ? 1 : 0;
             S.ngbits = tb - r;
+            S.tile_above = 0;
+            for (int w : nt)
+                if (w > top) S.tile_above = 1;
             top -= r;
             left -= r;
             r = std::min(left, pl->rmax);
@@ -262,14 +280,18 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
         }
         for (int i = 0; i < S.ngbits; ++i) S.gpos[i] = order[i];
     }
-    int ntab = 0;
+    int ntab = 0, nU = 0;
     for (int s = 0; s < P.nstages; ++s) {
+        P.st[s].uoff = nU;
+        nU += P.st[s].r;
         P.tab_off[s] = ntab;
         const int ng = 1 << P.st[s].ngbits;
         ntab += 32 + (ng > 32 ? ng >> 5 : 1);
     }
     P.ntab = ntab;
+    P.nU = nU;
     ph.smem = pass_smem_bytes(P, pl->esize);
+    if (ph.smem > 227 * 1024 - 4096) return false;
     const int64_t tiles = P.num_tiles;
     ph.grid = static_cast<int>(std::min<int64_t>(tiles, pl->num_sms));
     return true;
@@ -583,7 +605,7 @@ int qft_plan_describe_pass(qft_plan_t pl, int i, long long* out, int cap) {
     v.insert(v.end(), {P.n, P.kk, P.tb, P.nstages, P.first, P.last, P.load_mode, (long long)P.num_tiles});
     for (int s = 0; s < kMaxStages; ++s) {
         const StageDesc& S = P.st[s];
-        v.insert(v.end(), {S.wlo, S.r, S.q, S.cross, S.ngbits});
+        v.insert(v.end(), {S.wlo, S.r, S.q, S.cross, S.ngbits, S.tile_above, S.uoff});
         for (int b = 0; b < kMaxTileBits; ++b) v.push_back(S.gpos[b]);
     }
     for (int b = 0; b < kMaxTileBits; ++b) v.push_back(P.p_wire[b]);

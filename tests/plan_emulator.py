@@ -23,7 +23,7 @@ def parse(rec):
     P = {k: nx() for k in ("n", "kk", "tb", "nstages", "first", "last", "load_mode", "num_tiles")}
     st = []
     for _ in range(K_MAX_STAGES):
-        s = {k: nx() for k in ("wlo", "r", "q", "cross", "ngbits")}
+        s = {k: nx() for k in ("wlo", "r", "q", "cross", "ngbits", "tile_above", "uoff")}
         s["gpos"] = [nx() for _ in range(K_MAX_TILE_BITS)]
         st.append(s)
     P["st"] = st[:P["nstages"]]
@@ -71,6 +71,13 @@ def check_structure(P, esize):
             assert P["p_wire"][s["q"] + e] == s["wlo"] + e, "stage block must be consecutive wires on consecutive tile bits"
         others = sorted(s["gpos"][:s["ngbits"]])
         assert others == [p for p in range(tb) if not (s["q"] <= p < s["q"] + s["r"])]
+    seg_wires = [s["wire"] + i for s in P["seg"] for i in range(s["len"])]
+    uoff = 0
+    for s in P["st"]:
+        hi = s["wlo"] + s["r"] - 1
+        assert s["tile_above"] == int(any(w > hi for w in seg_wires)), "per-tile twiddle flag"
+        assert s["uoff"] == uoff
+        uoff += s["r"]
     # blocks processed top-down and covering each wire once
     blocks = [(s["wlo"], s["r"]) for s in P["st"]]
     for a, b in zip(blocks, blocks[1:]):
