@@ -30,17 +30,19 @@ constexpr int kMaxTileBits = 14;
 constexpr int kMaxSegs = 8;
 constexpr int kMaxPasses = 8;
 constexpr int kMaxDims = 5;
-constexpr int kThreads = 512;  // threads per CTA of the pass kernel
+constexpr int kThreads = 256;  // threads per CTA of the pass kernel
+constexpr int kMaxR = 5;       // wires per register stage (32 amplitudes per thread)
 
 // One register stage (one fused block of wires).
 struct StageDesc {
     int32_t wlo;    // lowest logical wire of the block
-    int32_t r;      // wires in the block (1..4); the block is wires [wlo, wlo + r)
+    int32_t r;      // wires in the block (1..kMaxR); the block is wires [wlo, wlo + r)
     int32_t q;      // tile index bit that holds wire wlo; the block occupies tile bits [q, q + r)
     int32_t cross;  // 1 if some wire above the block exists (cross twiddle (a) is not identity)
     int32_t ngbits; // tb - r: bits of the group index
     int32_t tile_above;  // 1 if a tile-coordinate wire lies above the block (per-tile twiddle U needed)
     int32_t uoff;        // offset of this stage's r per-tile twiddles in the U table
+    int32_t img[kMaxR];  // swizzled buffer-B offset of each register bit (1 << (q + e) mapped)
     int32_t gpos[kMaxTileBits];  // group-index bit i -> tile index bit (lanes use the low group bits)
 };
 

@@ -111,30 +111,35 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
     return r;
 }
 
-// exp(2 pi i m / 16) for m = 0..7 (cos, sin): the rotations of controlled
-// phases between wires at distance <= 3 (R_2, R_3, R_4 and their products).
-__device__ constexpr double kW16c[8] = {1.0, 0.92387953251128675613, 0.70710678118654752440,
-                                        0.38268343236508977173, 0.0, -0.38268343236508977173,
-                                        -0.70710678118654752440, -0.92387953251128675613};
-__device__ constexpr double kW16s[8] = {0.0, 0.38268343236508977173, 0.70710678118654752440,
-                                        0.92387953251128675613, 1.0, 0.92387953251128675613,
-                                        0.70710678118654752440, 0.38268343236508977173};
+// exp(2 pi i m / 32) for m = 0..15 (cos, sin): the rotations of controlled
+// phases between wires at distance <= 4 inside one register block
+// (R_2 .. R_5 and their products).
+__device__ constexpr double kW32c[16] = {
+    1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+    0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173, 0.19509032201612826785,
+    0.0, -0.19509032201612826785, -0.38268343236508977173, -0.55557023301960222474,
+    -0.70710678118654752440, -0.83146961230254523708, -0.92387953251128675613, -0.98078528040323044913};
+__device__ constexpr double kW32s[16] = {
+    0.0, 0.19509032201612826785, 0.38268343236508977173, 0.55557023301960222474,
+    0.70710678118654752440, 0.83146961230254523708, 0.92387953251128675613, 0.98078528040323044913,
+    1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+    0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173, 0.19509032201612826785};
 
-// z *= exp(DIR * 2 pi i m / 16).  With m a compile-time constant after loop
+// z *= exp(DIR * 2 pi i m / 32).  With m a compile-time constant after loop
 // unrolling the trivial rotations (1, +-i, -1) reduce to moves and negations.
 template <int DIR, typename V>
-__device__ __forceinline__ void rot16(V& z, int m) {
+__device__ __forceinline__ void rot32(V& z, int m) {
     using T = decltype(z.x);
-    m &= 15;
+    m &= 31;
     if (m == 0) return;
-    const bool neg = m >= 8;
-    const int mm = m & 7;
-    if (mm == 4) {  // multiply by DIR * i
+    const bool neg = m >= 16;
+    const int mm = m & 15;
+    if (mm == 8) {  // multiply by DIR * i
         const T t = z.x;
         if (DIR > 0) { z.x = -z.y; z.y = t; } else { z.x = z.y; z.y = -t; }
     } else if (mm != 0) {
-        const T c = static_cast<T>(kW16c[mm]);
-        const T s = static_cast<T>(DIR > 0 ? kW16s[mm] : -kW16s[mm]);
+        const T c = static_cast<T>(kW32c[mm]);
+        const T s = static_cast<T>(DIR > 0 ? kW32s[mm] : -kW32s[mm]);
         const T re = z.x * c - z.y * s;
         z.y = z.x * s + z.y * c;
         z.x = re;
@@ -204,14 +209,14 @@ __device__ __forceinline__ void block_circuit(V (&v)[1 << R], int kk) {
         if (kk >= R - 1) {
 #pragma unroll
             for (int j = 0; j < NJ; ++j)
-                if (j & bit) rot16<DIR>(v[j], (j & (bit - 1)) << (3 - t));
+                if (j & bit) rot32<DIR>(v[j], (j & (bit - 1)) << (4 - t));
         } else {
             int lo = t - kk;
             if (lo < 0) lo = 0;
             const int mask = (bit - 1) & ~((1 << lo) - 1);
 #pragma unroll
             for (int j = 0; j < NJ; ++j)
-                if (j & bit) rot16<DIR>(v[j], (j & mask) << (3 - t));
+                if (j & bit) rot32<DIR>(v[j], (j & mask) << (4 - t));
         }
     }
 }
@@ -231,7 +236,8 @@ template <typename V>
 struct GroupTab {
     uint32_t* pb;
     int64_t* ob;
-    V* tw;  // [entry][4]
+    V* tw;  // [e][entry], e < kMaxR: plane e holds factor e of every entry (lane reads are consecutive)
+    int ntab;
 };
 
 // Integer phase beta_e of block wire c = wlo + e for the logical bits I (only
@@ -261,7 +267,7 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
     uint32_t soff[NJ];
     soff[0] = 0;
 #pragma unroll
-    for (int j = 1; j < NJ; ++j) soff[j] = soff[j & (j - 1)] ^ swz<SW>(1u << (q + (__ffs(j) - 1)));
+    for (int j = 1; j < NJ; ++j) soff[j] = soff[j & (j - 1)] ^ static_cast<uint32_t>(S.img[__ffs(j) - 1]);
     V u[R];
     const bool use_u = S.cross && S.tile_above;
     if (use_u) {
@@ -287,15 +293,28 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
             norm_acc += static_cast<double>(a);
         }
         if (S.cross) {
-            const V* tl = tab.tw + 4 * lo5;
-            const V* th = tab.tw + 4 * hi5;
+            // tau_e for each block wire, then the diagonal prod_e tau_e^{j_e}
+            // applied as (low 2 bits) x (high bits) products.
+            V tau[R];
 #pragma unroll
             for (int e = 0; e < R; ++e) {
-                V tau = cmul(tl[e], th[e]);
-                if (use_u) tau = cmul(tau, u[e]);
+                tau[e] = cmul(tab.tw[e * tab.ntab + lo5], tab.tw[e * tab.ntab + hi5]);
+                if (use_u) tau[e] = cmul(tau[e], u[e]);
+            }
+            constexpr int LB = R < 2 ? R : 2;
+            constexpr int HB = R - LB;
+            V tl[1 << LB], th[1 << HB];
 #pragma unroll
-                for (int j = 0; j < NJ; ++j)
-                    if (j & (1 << e)) v[j] = cmul(v[j], tau);
+            for (int a = 1; a < (1 << LB); ++a)
+                tl[a] = (a & (a - 1)) ? cmul(tl[a & (a - 1)], tau[__ffs(a) - 1]) : tau[__ffs(a) - 1];
+#pragma unroll
+            for (int b = 1; b < (1 << HB); ++b)
+                th[b] = (b & (b - 1)) ? cmul(th[b & (b - 1)], tau[LB + __ffs(b) - 1]) : tau[LB + __ffs(b) - 1];
+#pragma unroll
+            for (int j = 1; j < NJ; ++j) {
+                const int a = j & ((1 << LB) - 1), b = j >> LB;
+                if (a) v[j] = cmul(v[j], tl[a]);
+                if (b) v[j] = cmul(v[j], th[b]);
             }
         }
         block_circuit<DIR, R>(v, P.kk);
@@ -335,7 +354,8 @@ __device__ __forceinline__ void dispatch_stage(const PassParams& P, int s, const
         case 1: run_stage<T, DIR, 1>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
         case 2: run_stage<T, DIR, 2>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
         case 3: run_stage<T, DIR, 3>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
-        default: run_stage<T, DIR, 4>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
+        case 4: run_stage<T, DIR, 4>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
+        default: run_stage<T, DIR, 5>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
     }
 }
 
@@ -418,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ double red[kThreads / 32];
-    __shared__ __align__(16) V Ubuf[2][4 * kMaxStages];
+    __shared__ __align__(16) V Ubuf[2][kMaxR * kMaxStages];
 
     const int tid = threadIdx.x;
     const uint32_t tile_elems = 1u << P.tb;
@@ -429,9 +449,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* tab_raw = smem_raw + 3 * static_cast<size_t>(tile_bytes);
     const int ntab = P.ntab;
     GroupTab<V> tab;
+    tab.ntab = ntab;
     tab.tw = reinterpret_cast<V*>(tab_raw);
-    tab.ob = reinterpret_cast<int64_t*>(tab_raw + 4 * sizeof(V) * static_cast<size_t>(ntab));
-    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (4 * sizeof(V) + 8) * static_cast<size_t>(ntab));
+    tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * sizeof(V) * static_cast<size_t>(ntab));
+    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * sizeof(V) + 8) * static_cast<size_t>(ntab));
 
     // Build the group tables (pb, ob, cross-twiddle factors of the group's tile wires).
     for (int s = 0; s < P.nstages; ++s) {
@@ -454,12 +475,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int idx = P.tab_off[s] + i;
             tab.pb[idx] = pb;
             tab.ob[idx] = ob;
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < kMaxR; ++e) {
                 V w;
                 w.x = T(1);
                 w.y = T(0);
                 if (S.cross && e < S.r) w = phase_turns<T, DIR>(cross_phase(iw, P.n, S.wlo + S.r - 1, S.wlo + e, P.kk), P.n);
-                tab.tw[4 * idx + e] = w;
+                tab.tw[e * ntab + idx] = w;
             }
         }
     }
@@ -578,9 +599,9 @@ cudaError_t launch_pass(int dtype, int dir, const CUtensorMap& map, const PassPa
 }
 
 // Dynamic shared memory of one CTA: buffer B, the two TMA load buffers and
-// the group tables (4 twiddle factors + output offset + tile bits per entry).
+// the group tables (kMaxR twiddle factors + output offset + tile bits per entry).
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes) {
-    return 3 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (4 * elem_bytes + 8 + 4);
+    return 3 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (kMaxR * elem_bytes + 8 + 4);
 }
 
 }  // namespace qft

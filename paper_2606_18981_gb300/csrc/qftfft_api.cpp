@@ -101,6 +101,16 @@ struct qft_plan_s {
 
 namespace {
 
+// Host copy of the kernel's buffer-B swizzle: the low SW bits of a tile index
+// XORed with the XOR-fold of its higher SW-bit groups (SW = 4 for 8-byte,
+// 3 for 16-byte amplitudes).
+uint32_t swizzle(uint32_t x, size_t esize) {
+    const int SW = esize == 8 ? 4 : 3;
+    uint32_t y = x >> SW, f = 0;
+    for (int i = 0; i < 16 / SW + 1; ++i) { f ^= y; y >>= SW; }
+    return x ^ (f & ((1u << SW) - 1));
+}
+
 int effective_k(int n, int k) { return (k < 0 || k > n - 1) ? std::max(n - 1, 0) : k; }
 
 // Build one pass from its wire group [glo, glo + a), batch wires, and the
@@ -231,11 +241,12 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
     }
     P.nstages = 0;
     for (auto& rr : runs) {
-        int top = rr.first, left = rr.second;
-        int firstr = left % pl->rmax;
-        if (firstr == 0) firstr = std::min(left, pl->rmax);
-        int r = firstr;
-        while (left > 0) {
+        // as few stages as rmax allows, sizes as equal as possible (larger first)
+        const int len = rr.second;
+        const int nst = (len + pl->rmax - 1) / pl->rmax;
+        int top = rr.first;
+        for (int i = 0; i < nst; ++i) {
+            const int r = len / nst + (i < len % nst ? 1 : 0);
             if (P.nstages >= kMaxStages) return false;
             StageDesc& S = P.st[P.nstages++];
             S.r = r;
@@ -246,9 +257,8 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
             S.tile_above = 0;
             for (int w : nt)
                 if (w > top) S.tile_above = 1;
+            for (int e = 0; e < kMaxR; ++e) S.img[e] = e < r ? static_cast<int32_t>(swizzle(1u << (S.q + e), pl->esize)) : 0;
             top -= r;
-            left -= r;
-            r = std::min(left, pl->rmax);
         }
     }
     // Lane order of each stage's group index.
@@ -452,8 +462,8 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
     pl->dtype = dtype;
     pl->esize = dtype == QFT_C64 ? 8 : 16;
     pl->TB = dtype == QFT_C64 ? 13 : 12;
-    pl->cmin = dtype == QFT_C64 ? 2 : 1;
-    pl->rmax = 4;
+    pl->cmin = dtype == QFT_C64 ? 4 : 3;  // HBM runs of >= 128 bytes
+    pl->rmax = kMaxR;
     if (opts) {
         if (opts->order != QFT_ORDER_NATURAL && opts->order != QFT_ORDER_BITREV) { delete pl; return QFT_ERR_BAD_ARG; }
         pl->order = opts->order;
@@ -461,6 +471,8 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
             if (opts->tile_bits < 4 || opts->tile_bits > (dtype == QFT_C64 ? 13 : 12)) { delete pl; return QFT_ERR_BAD_ARG; }
             pl->TB = opts->tile_bits;
         }
+        // small tiles keep at least 3 transform wires per pass unless told otherwise
+        if (opts->tile_bits && !opts->coalesce_bits) pl->cmin = std::min(pl->cmin, std::max(1, pl->TB - 3));
         if (opts->coalesce_bits) {
             if (opts->coalesce_bits < 1 || opts->coalesce_bits > 6) { delete pl; return QFT_ERR_BAD_ARG; }
             pl->cmin = opts->coalesce_bits;
@@ -469,7 +481,7 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
         if (opts->wait_limit_ms) pl->wait_limit_ns = uint64_t(opts->wait_limit_ms) * 1000000ull;
         pl->test_skip_first_load = opts->test_skip_first_load ? 1 : 0;
         if (opts->max_stage_bits) {
-            if (opts->max_stage_bits < 1 || opts->max_stage_bits > 4) { delete pl; return QFT_ERR_BAD_ARG; }
+            if (opts->max_stage_bits < 1 || opts->max_stage_bits > kMaxR) { delete pl; return QFT_ERR_BAD_ARG; }
             pl->rmax = opts->max_stage_bits;
         }
     }
@@ -606,6 +618,7 @@ int qft_plan_describe_pass(qft_plan_t pl, int i, long long* out, int cap) {
     for (int s = 0; s < kMaxStages; ++s) {
         const StageDesc& S = P.st[s];
         v.insert(v.end(), {S.wlo, S.r, S.q, S.cross, S.ngbits, S.tile_above, S.uoff});
+        for (int e = 0; e < kMaxR; ++e) v.push_back(S.img[e]);
         for (int b = 0; b < kMaxTileBits; ++b) v.push_back(S.gpos[b]);
     }
     for (int b = 0; b < kMaxTileBits; ++b) v.push_back(P.p_wire[b]);

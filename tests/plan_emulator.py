@@ -14,7 +14,7 @@ from __future__ import annotations
 
 import numpy as np
 
-K_MAX_STAGES, K_MAX_TILE_BITS, K_MAX_SEGS, K_MAX_DIMS = 8, 14, 8, 5
+K_MAX_STAGES, K_MAX_TILE_BITS, K_MAX_SEGS, K_MAX_DIMS, K_MAX_R = 8, 14, 8, 5, 5
 
 
 def parse(rec):
@@ -24,6 +24,7 @@ def parse(rec):
     st = []
     for _ in range(K_MAX_STAGES):
         s = {k: nx() for k in ("wlo", "r", "q", "cross", "ngbits", "tile_above", "uoff")}
+        s["img"] = [nx() for _ in range(K_MAX_R)]
         s["gpos"] = [nx() for _ in range(K_MAX_TILE_BITS)]
         st.append(s)
     P["st"] = st[:P["nstages"]]
@@ -65,7 +66,7 @@ def check_structure(P, esize):
     assert sum(s["len"] for s in P["seg"]) == n - tb
     assert P["num_tiles"] == 1 << (n - tb)
     for s in P["st"]:
-        assert 1 <= s["r"] <= 4 and s["ngbits"] == tb - s["r"]
+        assert 1 <= s["r"] <= K_MAX_R and s["ngbits"] == tb - s["r"]
         assert 0 <= s["q"] and s["q"] + s["r"] <= tb
         for e in range(s["r"]):
             assert P["p_wire"][s["q"] + e] == s["wlo"] + e, "stage block must be consecutive wires on consecutive tile bits"
@@ -121,7 +122,7 @@ def _gather_tma(P, src_u64, tiles):
     return addr
 
 
-W16 = np.exp(2j * np.pi * np.arange(16) / 16)
+W32 = np.exp(2j * np.pi * np.arange(32) / 32)
 
 
 def _block_circuit(v, R, kk, sign):
@@ -137,8 +138,8 @@ def _block_circuit(v, R, kk, sign):
         mask = (bit - 1) & ~((1 << lo) - 1)
         for j in range(1 << R):
             if j & bit:
-                m = ((j & mask) << (3 - t)) & 15
-                v[..., j] *= W16[m] if sign > 0 else np.conj(W16[m])
+                m = ((j & mask) << (4 - t)) & 31
+                v[..., j] *= W32[m] if sign > 0 else np.conj(W32[m])
     return v
 
 
