@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--n", type=int, default=30)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--k", type=int, default=-1)
+    ap.add_argument("--threads", type=int, default=0, help="pass-kernel CTA size (256 or 512; 0 = default)")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -263,7 +264,7 @@ def run_ours(args, world, rank, local):
     n, dt, k = args.n, args.dtype, args.k
     N = 1 << n
     eb = 8 if dt == "c64" else 16
-    plan = q.Plan(n, k, q.FORWARD, dt, q.ORDER_NATURAL)
+    plan = q.Plan(n, k, q.FORWARD, dt, q.ORDER_NATURAL, threads=args.threads)
     info = plan.info()
     P = info.passes
     stream = torch.cuda.Stream(device=dev)

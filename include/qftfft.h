@@ -92,7 +92,9 @@ typedef struct {
     int wait_limit_ms;  /* bound of every device-side wait; 0 = default (2000 ms)           */
     int test_skip_first_load; /* test hook: 1 = never issue the first tile load, so the
                                  kernel's bounded wait expires and reports QFT_ERR_TIMEOUT  */
-    int reserved[2];
+    int threads;        /* CTA size of the pass kernel: 256 (stages <= 5 wires) or 512
+                           (stages <= 4 wires); 0 = default                                 */
+    int reserved[1];
 } qft_opts;
 
 /* What the planner built (Sec. 3.1: the plan is defined by the qubit count,

@@ -56,7 +56,8 @@ class PlanInfo(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("tile_bits", ctypes.c_int), ("coalesce_bits", ctypes.c_int),
                 ("max_stage_bits", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
-                ("test_skip_first_load", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("test_skip_first_load", ctypes.c_int), ("threads", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 _vp = ctypes.c_void_p
@@ -119,12 +120,12 @@ class Plan:
 
     def __init__(self, n: int, k: int = -1, direction: int = FORWARD, dtype="c64", order: int = ORDER_NATURAL,
                  tile_bits: int = 0, coalesce_bits: int = 0, max_stage_bits: int = 0,
-                 wait_limit_ms: int = 0, test_skip_first_load: int = 0):
+                 wait_limit_ms: int = 0, test_skip_first_load: int = 0, threads: int = 0):
         self._h = _vp()
         self.n, self.k, self.direction = int(n), int(k), int(direction)
         self.dtype = _dtype_code(dtype)
         self.order = int(order)
-        opts = Opts(order, tile_bits, coalesce_bits, max_stage_bits, wait_limit_ms, test_skip_first_load)
+        opts = Opts(order, tile_bits, coalesce_bits, max_stage_bits, wait_limit_ms, test_skip_first_load, threads)
         _check(_lib.qft_plan_create(ctypes.byref(self._h), self.n, self.k, self.direction, self.dtype,
                                     ctypes.byref(opts)), "qft_plan_create")
 

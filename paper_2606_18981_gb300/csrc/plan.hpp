@@ -30,8 +30,9 @@ constexpr int kMaxTileBits = 14;
 constexpr int kMaxSegs = 8;
 constexpr int kMaxPasses = 8;
 constexpr int kMaxDims = 5;
-constexpr int kThreads = 256;  // threads per CTA of the pass kernel
-constexpr int kMaxR = 5;       // wires per register stage (32 amplitudes per thread)
+constexpr int kMaxR = 5;  // wires per register stage (32 amplitudes per thread)
+// The pass kernel runs with 256 threads per CTA (register stages of up to 5
+// wires) or 512 threads (stages of up to 4 wires).
 
 // One register stage (one fused block of wires).
 struct StageDesc {

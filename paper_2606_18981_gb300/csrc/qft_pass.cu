@@ -251,48 +251,68 @@ __device__ __forceinline__ uint64_t cross_phase(uint64_t I, int n, int hi, int c
     return m << c;
 }
 
-template <typename T, int DIR, int R>
-__device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& S, const GroupTab<typename Vec2<T>::type>& tab,
-                                          int toff, const typename Vec2<T>::type* __restrict__ src,
-                                          bool src_dense, typename Vec2<T>::type* __restrict__ dstB,
-                                          bool to_global, int64_t out_tile, T scale,
+// Stage kinds: where a stage reads its amplitudes and where it writes them.
+enum StageKind { K_FIRST = 0, K_MID = 1, K_LAST = 2, K_ONLY = 3 };
+//   K_FIRST  TMA buffer A (dense tile order) -> swizzled buffer B
+//   K_MID    B -> B
+//   K_LAST   B -> HBM through the pass's output address map (with the output scale)
+//   K_ONLY   A -> HBM (a pass of a single stage)
+
+template <typename T, int DIR, int R, int KIND, int NT>
+__device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& S,
+                                          const GroupTab<typename Vec2<T>::type>& tab, int toff,
+                                          const typename Vec2<T>::type* __restrict__ A,
+                                          typename Vec2<T>::type* __restrict__ Bb, int64_t out_tile, T scale,
                                           const typename Vec2<T>::type* __restrict__ U, bool acc_norm,
                                           double& norm_acc) {
     using V = typename Vec2<T>::type;
     constexpr int NJ = 1 << R;
     constexpr int SW = sizeof(V) == 8 ? 4 : 3;
+    constexpr bool kFromA = (KIND == K_FIRST || KIND == K_ONLY);
+    constexpr bool kToGlobal = (KIND == K_LAST || KIND == K_ONLY);
     const int ng = 1 << S.ngbits;
     const uint32_t q = static_cast<uint32_t>(S.q);
-    // swizzled offsets of the register bits (swz is XOR-linear), built by Gray steps
+    // swizzled offsets of the register bits (the swizzle is XOR-linear), by Gray steps
     uint32_t soff[NJ];
     soff[0] = 0;
 #pragma unroll
     for (int j = 1; j < NJ; ++j) soff[j] = soff[j & (j - 1)] ^ static_cast<uint32_t>(S.img[__ffs(j) - 1]);
+    const bool cross = S.cross != 0;
+    const bool use_u = cross && S.tile_above;
     V u[R];
-    const bool use_u = S.cross && S.tile_above;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        u[e].x = T(1);
+        u[e].y = T(0);
+    }
     if (use_u) {
 #pragma unroll
         for (int e = 0; e < R; ++e) u[e] = U[e];
     }
-    for (int g = threadIdx.x; g < ng; g += kThreads) {
+    int64_t oo[R];
+    if (kToGlobal) {
+#pragma unroll
+        for (int e = 0; e < R; ++e) oo[e] = int64_t(1) << P.p_out[q + e];
+    }
+    for (int g = threadIdx.x; g < ng; g += NT) {
         const int lo5 = toff + (g & 31), hi5 = toff + 32 + (g >> 5);
         const uint32_t pb = tab.pb[lo5] | tab.pb[hi5];
         V v[NJ];
-        if (src_dense) {
+        if (kFromA) {
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) v[j] = src[pb + (uint32_t(j) << q)];
+            for (int j = 0; j < NJ; ++j) v[j] = A[pb + (uint32_t(j) << q)];
         } else {
             const uint32_t base = swz<SW>(pb);
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) v[j] = src[base ^ soff[j]];
+            for (int j = 0; j < NJ; ++j) v[j] = Bb[base ^ soff[j]];
         }
-        if (acc_norm) {
+        if (kFromA && acc_norm) {
             T a = T(0);
 #pragma unroll
             for (int j = 0; j < NJ; ++j) a += v[j].x * v[j].x + v[j].y * v[j].y;
             norm_acc += static_cast<double>(a);
         }
-        if (S.cross) {
+        if (cross) {
             // tau_e for each block wire, then the diagonal prod_e tau_e^{j_e}
             // applied as (low 2 bits) x (high bits) products.
             V tau[R];
@@ -318,11 +338,8 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
             }
         }
         block_circuit<DIR, R>(v, P.kk);
-        if (to_global) {
+        if (kToGlobal) {
             V* __restrict__ out = static_cast<V*>(P.out) + (out_tile + tab.ob[lo5] + tab.ob[hi5]);
-            int64_t oo[R];
-#pragma unroll
-            for (int e = 0; e < R; ++e) oo[e] = int64_t(1) << P.p_out[q + e];
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
                 int64_t o = 0;
@@ -337,29 +354,44 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
         } else {
             const uint32_t base = swz<SW>(pb);
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) dstB[base ^ soff[j]] = v[j];
+            for (int j = 0; j < NJ; ++j) Bb[base ^ soff[j]] = v[j];
         }
     }
 }
 
-template <typename T, int DIR>
-__device__ __forceinline__ void dispatch_stage(const PassParams& P, int s, const GroupTab<typename Vec2<T>::type>& tab,
-                                               const typename Vec2<T>::type* src, bool src_dense,
-                                               typename Vec2<T>::type* dstB, bool to_global, int64_t out_tile,
-                                               T scale, const typename Vec2<T>::type* U, bool acc_norm,
-                                               double& norm_acc) {
+template <typename T, int DIR, int KIND, int NT>
+__device__ __forceinline__ void dispatch_r(const PassParams& P, int s, const GroupTab<typename Vec2<T>::type>& tab,
+                                           const typename Vec2<T>::type* A, typename Vec2<T>::type* Bb,
+                                           int64_t out_tile, T scale, const typename Vec2<T>::type* U,
+                                           bool acc_norm, double& norm_acc) {
     const StageDesc& S = P.st[s];
     const int toff = P.tab_off[s];
     switch (S.r) {
-        case 1: run_stage<T, DIR, 1>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
-        case 2: run_stage<T, DIR, 2>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
-        case 3: run_stage<T, DIR, 3>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
-        case 4: run_stage<T, DIR, 4>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
-        default: run_stage<T, DIR, 5>(P, S, tab, toff, src, src_dense, dstB, to_global, out_tile, scale, U, acc_norm, norm_acc); break;
+        case 1: run_stage<T, DIR, 1, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
+        case 2: run_stage<T, DIR, 2, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
+        case 3: run_stage<T, DIR, 3, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
+        case 4: run_stage<T, DIR, 4, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
+        default:
+            if constexpr (NT <= 256)
+                run_stage<T, DIR, 5, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
+            break;
     }
 }
 
+template <typename T, int DIR, int NT>
+__device__ __forceinline__ void dispatch_stage(const PassParams& P, int s, const GroupTab<typename Vec2<T>::type>& tab,
+                                               const typename Vec2<T>::type* A, typename Vec2<T>::type* Bb,
+                                               int64_t out_tile, T scale, const typename Vec2<T>::type* U,
+                                               bool acc_norm, double& norm_acc) {
+    const bool first = (s == 0), last = (s == P.nstages - 1);
+    if (first && last) dispatch_r<T, DIR, K_ONLY, NT>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
+    else if (first) dispatch_r<T, DIR, K_FIRST, NT>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
+    else if (last) dispatch_r<T, DIR, K_LAST, NT>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
+    else dispatch_r<T, DIR, K_MID, NT>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
+}
+
 // Deterministic CTA-wide sum (fixed shuffle tree, then warps in order).
+template <int NT>
 __device__ __forceinline__ double block_sum(double x, double* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -367,7 +399,7 @@ __device__ __forceinline__ double block_sum(double x, double* red) {
     if ((threadIdx.x & 31) == 0) red[w] = x;
     __syncthreads();
     double t = 0.0;
-    for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+    for (int i = 0; i < NT / 32; ++i) t += red[i];
     __syncthreads();
     return t;
 }
@@ -431,13 +463,13 @@ __device__ __forceinline__ void compute_tile_twiddles(const PassParams& P, int64
     Ubuf[i] = phase_turns<T, DIR>(beta, P.n);
 }
 
-template <typename T, int DIR>
-__global__ void __launch_bounds__(kThreads, 1)
+template <typename T, int DIR, int NT>
+__global__ void __launch_bounds__(NT, 1)
     qft_pass_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassParams P) {
     using V = typename Vec2<T>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ double red[kThreads / 32];
+    __shared__ double red[NT / 32];
     __shared__ __align__(16) V Ubuf[2][kMaxR * kMaxStages];
 
     const int tid = threadIdx.x;
@@ -445,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tile_bytes = tile_elems * static_cast<uint32_t>(sizeof(V));
     // buffer B first, then the two TMA load buffers, then the group tables
     V* B = reinterpret_cast<V*>(smem_raw);
-    V* A[2] = {B + tile_elems, B + 2 * tile_elems};
+    V* const A0 = B + tile_elems;  // load buffer k & 1 is A0 + (k & 1) * tile_elems
     unsigned char* tab_raw = smem_raw + 3 * static_cast<size_t>(tile_bytes);
     const int ntab = P.ntab;
     GroupTab<V> tab;
@@ -459,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const StageDesc& S = P.st[s];
         const int ng = 1 << S.ngbits;
         const int nhi = ng > 32 ? ng >> 5 : 1;
-        for (int i = tid; i < 32 + nhi; i += kThreads) {
+        for (int i = tid; i < 32 + nhi; i += NT) {
             const int g = i < 32 ? (i < ng ? i : 0) : ((i - 32) << 5);
             uint32_t pb = 0;
             uint64_t iw = 0;
@@ -496,8 +528,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     T scale = T(1);
     if (P.last && !P.first) {
         double s = 0.0;
-        for (int i = tid; i < P.npartials; i += kThreads) s += P.partials[i];
-        const double tot = block_sum(s, red);
+        for (int i = tid; i < P.npartials; i += NT) s += P.partials[i];
+        const double tot = block_sum<NT>(s, red);
         const double scale_in = sqrt(tot);
         scale = static_cast<T>(output_factor(P, scale_in));
         if (blockIdx.x == 0 && tid == 0) {
@@ -507,20 +539,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     double norm_acc = 0.0;
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t parity = 0u;  // bit b: phase parity of mbar[b]
     bool aborted = false;
     if (tid == 0 && !P.test_skip_first_load) {
-        if (tile < P.num_tiles) issue_tile_load(P, &tmap, tile, A[0], &mbar[0], tile_bytes);
-        if (tile + gridDim.x < P.num_tiles) issue_tile_load(P, &tmap, tile + gridDim.x, A[1], &mbar[1], tile_bytes);
+        if (tile < P.num_tiles) issue_tile_load(P, &tmap, tile, A0, &mbar[0], tile_bytes);
+        if (tile + gridDim.x < P.num_tiles)
+            issue_tile_load(P, &tmap, tile + gridDim.x, A0 + tile_elems, &mbar[1], tile_bytes);
     }
 
     for (int k = 0; tile < P.num_tiles; tile += gridDim.x, ++k) {
         const int buf = k & 1;
+        V* const Ab = A0 + (buf ? tile_elems : 0u);
         uint64_t I_tile;
         int64_t out_tile;
         tile_coords(P, tile, I_tile, out_tile);
-        const bool ok = mbar_wait_bounded(&mbar[buf], parity[buf], P.wait_limit_ns);
-        parity[buf] ^= 1u;
+        const bool ok = mbar_wait_bounded(&mbar[buf], (parity >> buf) & 1u, P.wait_limit_ns);
+        parity ^= 1u << buf;
         if (__syncthreads_or(!ok)) {
             aborted = true;
             break;
@@ -528,11 +562,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (P.first && P.last) {
             // Single-pass transform (the whole state is this tile): norm first.
             double s = 0.0;
-            for (uint32_t i = tid; i < tile_elems; i += kThreads) {
-                const V a = A[buf][i];
+            for (uint32_t i = tid; i < tile_elems; i += NT) {
+                const V a = Ab[i];
                 s += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
             }
-            const double tot = block_sum(s, red);
+            const double tot = block_sum<NT>(s, red);
             const double scale_in = sqrt(tot);
             scale = static_cast<T>(output_factor(P, scale_in));
             if (tid == 0) {
@@ -544,8 +578,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < P.nstages; ++s) {
             const bool last_stage = (s == P.nstages - 1);
             const bool from_A = (s == 0);
-            dispatch_stage<T, DIR>(P, s, tab, from_A ? A[buf] : B, from_A, B, last_stage, out_tile, scale,
-                                   Ucur + P.st[s].uoff, from_A && P.first && !P.last, norm_acc);
+            dispatch_stage<T, DIR, NT>(P, s, tab, Ab, B, out_tile, scale, Ucur + P.st[s].uoff,
+                                       P.first && !P.last, norm_acc);
             if (last_stage) compute_tile_twiddles<T, DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1]);
             __syncthreads();
             if (from_A) {
@@ -553,7 +587,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t nt = tile + 2 * static_cast<int64_t>(gridDim.x);
                 if (tid == 0 && nt < P.num_tiles) {
                     fence_proxy_async_smem();
-                    issue_tile_load(P, &tmap, nt, A[buf], &mbar[buf], tile_bytes);
+                    issue_tile_load(P, &tmap, nt, Ab, &mbar[buf], tile_bytes);
                 }
             }
         }
@@ -563,39 +597,46 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tid == 0) {
             atomicExch(P.status, -5);  // QFT_ERR_TIMEOUT
             // let in-flight copies land before the CTA's shared memory is released
-            for (int b = 0; b < 2; ++b) mbar_wait_bounded(&mbar[b], parity[b], P.wait_limit_ns);
+            for (int b = 0; b < 2; ++b) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, P.wait_limit_ns);
         }
         return;
     }
     if (P.first && !P.last) {
-        const double tot = block_sum(norm_acc, red);
+        const double tot = block_sum<NT>(norm_acc, red);
         if (tid == 0) P.partials[blockIdx.x] = tot;
     }
 }
 
 // ------------------------------------------------------------- launchers
 
-template <typename T, int DIR>
+template <typename T, int DIR, int NT>
 static cudaError_t launch_pass_t(const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                                  cudaStream_t stream) {
-    auto kern = qft_pass_kernel<T, DIR>;
+    auto kern = qft_pass_kernel<T, DIR, NT>;
     static thread_local size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    kern<<<grid, kThreads, smem, stream>>>(map, P);
+    kern<<<grid, NT, smem, stream>>>(map, P);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pass(int dtype, int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
-                        cudaStream_t stream) {
+template <int NT>
+static cudaError_t launch_nt(int dtype, int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+                             cudaStream_t stream) {
     if (dtype == 0)
-        return dir < 0 ? launch_pass_t<float, -1>(map, P, grid, smem, stream)
-                       : launch_pass_t<float, +1>(map, P, grid, smem, stream);
-    return dir < 0 ? launch_pass_t<double, -1>(map, P, grid, smem, stream)
-                   : launch_pass_t<double, +1>(map, P, grid, smem, stream);
+        return dir < 0 ? launch_pass_t<float, -1, NT>(map, P, grid, smem, stream)
+                       : launch_pass_t<float, +1, NT>(map, P, grid, smem, stream);
+    return dir < 0 ? launch_pass_t<double, -1, NT>(map, P, grid, smem, stream)
+                   : launch_pass_t<double, +1, NT>(map, P, grid, smem, stream);
+}
+
+cudaError_t launch_pass(int dtype, int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid,
+                        size_t smem, cudaStream_t stream) {
+    if (threads == 512) return launch_nt<512>(dtype, dir, map, P, grid, smem, stream);
+    return launch_nt<256>(dtype, dir, map, P, grid, smem, stream);
 }
 
 // Dynamic shared memory of one CTA: buffer B, the two TMA load buffers and

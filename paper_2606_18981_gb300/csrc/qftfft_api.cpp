@@ -29,8 +29,8 @@
 #include "plan.hpp"
 
 namespace qft {
-cudaError_t launch_pass(int dtype, int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
-                        cudaStream_t stream);
+cudaError_t launch_pass(int dtype, int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid,
+                        size_t smem, cudaStream_t stream);
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes);
 }  // namespace qft
 
@@ -86,6 +86,7 @@ struct qft_plan_s {
     int n = 0, k = -1, kk = 0, dir = -1, dtype = 0, order = 0;
     size_t esize = 8;
     int TB = 13, cmin = 2, rmax = 4;
+    int threads = 256;  // CTA size of the pass kernel (256: stages of <= 5 wires; 512: <= 4)
     uint64_t wait_limit_ns = 2000000000ull;
     int test_skip_first_load = 0;
     int num_sms = 148;
@@ -464,6 +465,7 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
     pl->TB = dtype == QFT_C64 ? 13 : 12;
     pl->cmin = dtype == QFT_C64 ? 4 : 3;  // HBM runs of >= 128 bytes
     pl->rmax = kMaxR;
+    pl->threads = 256;
     if (opts) {
         if (opts->order != QFT_ORDER_NATURAL && opts->order != QFT_ORDER_BITREV) { delete pl; return QFT_ERR_BAD_ARG; }
         pl->order = opts->order;
@@ -480,8 +482,16 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
         if (opts->wait_limit_ms < 0) { delete pl; return QFT_ERR_BAD_ARG; }
         if (opts->wait_limit_ms) pl->wait_limit_ns = uint64_t(opts->wait_limit_ms) * 1000000ull;
         pl->test_skip_first_load = opts->test_skip_first_load ? 1 : 0;
+        if (opts->threads) {
+            if (opts->threads != 256 && opts->threads != 512) { delete pl; return QFT_ERR_BAD_ARG; }
+            pl->threads = opts->threads;
+            if (pl->threads == 512) pl->rmax = 4;
+        }
         if (opts->max_stage_bits) {
-            if (opts->max_stage_bits < 1 || opts->max_stage_bits > kMaxR) { delete pl; return QFT_ERR_BAD_ARG; }
+            if (opts->max_stage_bits < 1 || opts->max_stage_bits > (pl->threads == 512 ? 4 : kMaxR)) {
+                delete pl;
+                return QFT_ERR_BAD_ARG;
+            }
             pl->rmax = opts->max_stage_bits;
         }
     }
@@ -590,7 +600,7 @@ int execute_range(qft_plan_t pl, void* d_state, void* d_workspace, double* d_sca
         P.status = reinterpret_cast<int32_t*>(ws + kStatusOff);
         P.wait_limit_ns = pl->wait_limit_ns;
         P.test_skip_first_load = pl->test_skip_first_load;
-        e = launch_pass(pl->dtype, pl->dir, pl->maps[i], P, ph.grid, ph.smem, st);
+        e = launch_pass(pl->dtype, pl->dir, pl->threads, pl->maps[i], P, ph.grid, ph.smem, st);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return QFT_OK;
