@@ -44,6 +44,8 @@ struct StageDesc {
     int32_t tile_above;  // 1 if a tile-coordinate wire lies above the block (per-tile twiddle U needed)
     int32_t uoff;        // offset of this stage's r per-tile twiddles in the U table
     int32_t img[kMaxR];  // swizzled buffer-B offset of each register bit (1 << (q + e) mapped)
+    int32_t lo_tw;       // 1 if a lane-part tile bit lies above the block (its twiddle table is not all 1)
+    int32_t hi_tw;       // 1 if a high-part tile bit lies above the block
     int32_t gpos[kMaxTileBits];  // group-index bit i -> tile index bit (lanes use the low group bits)
 };
 

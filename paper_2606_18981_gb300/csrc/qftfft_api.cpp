@@ -290,6 +290,11 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
                 if (!taken[p]) order.push_back(p);
         }
         for (int i = 0; i < S.ngbits; ++i) S.gpos[i] = order[i];
+        const int hi_w = S.wlo + S.r - 1;
+        S.lo_tw = S.hi_tw = 0;
+        for (int i = 0; i < S.ngbits; ++i)
+            if (P.p_wire[S.gpos[i]] > hi_w) (i < 5 ? S.lo_tw : S.hi_tw) = 1;
+        if (!S.lo_tw && !S.hi_tw) S.hi_tw = 1;  // keep one (all-ones) factor so tau is defined
     }
     int ntab = 0, nU = 0;
     for (int s = 0; s < P.nstages; ++s) {
@@ -629,6 +634,8 @@ int qft_plan_describe_pass(qft_plan_t pl, int i, long long* out, int cap) {
         const StageDesc& S = P.st[s];
         v.insert(v.end(), {S.wlo, S.r, S.q, S.cross, S.ngbits, S.tile_above, S.uoff});
         for (int e = 0; e < kMaxR; ++e) v.push_back(S.img[e]);
+        v.push_back(S.lo_tw);
+        v.push_back(S.hi_tw);
         for (int b = 0; b < kMaxTileBits; ++b) v.push_back(S.gpos[b]);
     }
     for (int b = 0; b < kMaxTileBits; ++b) v.push_back(P.p_wire[b]);

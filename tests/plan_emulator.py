@@ -25,6 +25,8 @@ def parse(rec):
     for _ in range(K_MAX_STAGES):
         s = {k: nx() for k in ("wlo", "r", "q", "cross", "ngbits", "tile_above", "uoff")}
         s["img"] = [nx() for _ in range(K_MAX_R)]
+        s["lo_tw"] = nx()
+        s["hi_tw"] = nx()
         s["gpos"] = [nx() for _ in range(K_MAX_TILE_BITS)]
         st.append(s)
     P["st"] = st[:P["nstages"]]
@@ -78,6 +80,9 @@ def check_structure(P, esize):
         hi = s["wlo"] + s["r"] - 1
         assert s["tile_above"] == int(any(w > hi for w in seg_wires)), "per-tile twiddle flag"
         assert s["uoff"] == uoff
+        lanes_above = any(P["p_wire"][s["gpos"][i]] > hi for i in range(min(5, s["ngbits"])))
+        high_above = any(P["p_wire"][s["gpos"][i]] > hi for i in range(5, s["ngbits"]))
+        assert s["lo_tw"] == int(lanes_above) and s["hi_tw"] == int(high_above or not lanes_above)
         uoff += s["r"]
     # blocks processed top-down and covering each wire once
     blocks = [(s["wlo"], s["r"]) for s in P["st"]]
