@@ -294,7 +294,6 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
 #pragma unroll
         for (int e = 0; e < R; ++e) oo[e] = int64_t(1) << P.p_out[q + e];
     }
-#pragma unroll 2
     for (int g = threadIdx.x; g < ng; g += NT) {
         const int lo5 = toff + (g & 31), hi5 = toff + 32 + (g >> 5);
         const uint32_t pb = tab.pb[lo5] | tab.pb[hi5];
@@ -344,16 +343,16 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
         block_circuit<DIR, R>(v, P.kk);
         if (kToGlobal) {
             V* __restrict__ out = static_cast<V*>(P.out) + (out_tile + tab.ob[lo5] + tab.ob[hi5]);
-            V* op[NJ];  // element pointers by Gray steps: one 64-bit add each
-            op[0] = out;
-#pragma unroll
-            for (int j = 1; j < NJ; ++j) op[j] = op[j & (j - 1)] + oo[__ffs(j) - 1];
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
+                int64_t o = 0;
+#pragma unroll
+                for (int e = 0; e < R; ++e)
+                    if (j & (1 << e)) o += oo[e];
                 V w = v[j];
                 w.x *= scale;
                 w.y *= scale;
-                *op[j] = w;
+                out[o] = w;
             }
         } else {
             const uint32_t base = swz<SW>(pb);
