@@ -151,6 +151,25 @@ int qft_execute(qft_plan_t plan, void* d_state, void* d_workspace, double* d_sca
 int qft_execute_pass(qft_plan_t plan, int pass, void* d_state, void* d_workspace, double* d_scale_in,
                      int scale_mode, qft_stream_t stream);
 
+/* qft_execute without a caller-provided workspace, for callers that cannot
+ * allocate device memory: code that runs while a stream is being captured into
+ * a CUDA graph (cudaMalloc is not allowed during capture), host runtimes that
+ * own the device heap and give libraries no allocator, and latency-critical
+ * loops that must never enter an allocator.  The paper has no counterpart;
+ * this is a library convenience.
+ *
+ * The workspace comes from a fixed scratch array in the library's device image
+ * (32 MiB + 4 KiB, held on every GPU that loads the library until the process
+ * exits).  Plans whose qft_workspace_size() exceeds it are rejected with
+ * QFT_ERR_SIZE: BITREV plans and single-pass plans always fit; NATURAL-order
+ * multi-pass plans fit up to n = 22 (complex64) / n = 21 (complex128).
+ * Allocates nothing.  The first call on a device looks up the scratch address
+ * for that device (it must be the current device) and caches it, so make the
+ * first call before any stream capture.  All calls share the scratch and it
+ * keeps the last call's contents; calls whose kernels overlap on the GPU race.
+ * scale_in is returned only through d_scale_in (device pointer, may be NULL). */
+int qft_execute_noalloc(qft_plan_t plan, void* d_state, double* d_scale_in, int scale_mode, qft_stream_t stream);
+
 /* Copy the N results from d_state to dst (host if dst_on_device = 0, else device). */
 int qft_read(qft_plan_t plan, const void* d_state, void* dst, int dst_on_device, qft_stream_t stream);
 

@@ -75,6 +75,7 @@ _lib.qft_load.argtypes = [_vp, _vp, _vp, ctypes.c_size_t, ctypes.c_int, _vp]
 _lib.qft_execute.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_execute_pass.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_read.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.qft_execute_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_get_scale_in.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.qft_check_status.argtypes = [_vp, _vp, _vp]
 _lib.qft_plan_describe_pass.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
@@ -181,6 +182,11 @@ class Plan:
         _check(_lib.qft_execute_pass(self._h, int(i), _ptr(state), _ptr(workspace),
                                      _ptr(scale_out) if scale_out is not None else None,
                                      int(scale_mode), _stream_handle(stream)), "qft_execute_pass")
+
+    def execute_noalloc(self, state, scale_mode: int = SCALE_STATE, scale_out=None, stream=None) -> None:
+        """Run the transform with the library's fixed device scratch (no allocation)."""
+        _check(_lib.qft_execute_noalloc(self._h, _ptr(state), _ptr(scale_out) if scale_out is not None else None,
+                                        int(scale_mode), _stream_handle(stream)), "qft_execute_noalloc")
 
     def read(self, state, dst, stream=None) -> None:
         on_dev = 1 if getattr(dst, "is_cuda", False) else 0
