@@ -151,6 +151,36 @@ int qft_execute(qft_plan_t plan, void* d_state, void* d_workspace, double* d_sca
 int qft_execute_pass(qft_plan_t plan, int pass, void* d_state, void* d_workspace, double* d_scale_in,
                      int scale_mode, qft_stream_t stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many transforms of different sizes and cutoffs in one persistent launch.
+ * (Batching is not in the paper, which times one transform at a time; it is
+ * the same circuit per transform.)  All plans of a batch must share dtype and
+ * direction.  Each transform's result, scale handling and accuracy are those
+ * of qft_execute with the same plan. */
+typedef struct qft_batch_s* qft_batch_t;
+
+/* Bytes of caller-owned device workspace a batch of these plans needs
+ * (per transform: scale_in and norm partial sums, plus the ping-pong buffer of
+ * natural-order multi-pass plans).  0 on bad arguments. */
+size_t qft_batch_workspace_size(const qft_plan_t* plans, int count);
+
+/* Bind transform i = plans[i] on d_states[i] (2^n amplitudes each, 256-byte
+ * aligned) for i < count.  d_workspace: qft_batch_workspace_size bytes,
+ * 256-byte aligned, caller-owned.  d_scale_in: optional device array of count
+ * doubles that receives each scale_in (NULL = none).  scale_mode: QFT_SCALE_*
+ * for every transform.  Allocates the batch's small device tables (work list,
+ * pass descriptors, tensor maps); the plans must outlive the batch. */
+int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_states, int count, void* d_workspace,
+                     size_t workspace_bytes, double* d_scale_in, int scale_mode);
+
+/* Run every transform of the batch in place: two memsets and one kernel launch
+ * on stream (capturable into a CUDA graph).  Asynchronous. */
+int qft_batch_execute(qft_batch_t batch, qft_stream_t stream);
+
+/* Synchronise stream and read the batch's device status word (0 or QFT_ERR_TIMEOUT). */
+int qft_batch_status(qft_batch_t batch, qft_stream_t stream);
+int qft_batch_destroy(qft_batch_t batch);
+
 /* qft_execute without a caller-provided workspace, for callers that cannot
  * allocate device memory: code that runs while a stream is being captured into
  * a CUDA graph (cudaMalloc is not allowed during capture), host runtimes that

@@ -80,6 +80,14 @@ _lib.qft_get_scale_in.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp
 _lib.qft_check_status.argtypes = [_vp, _vp, _vp]
 _lib.qft_plan_describe_pass.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
 
+_lib.qft_batch_workspace_size.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+_lib.qft_batch_workspace_size.restype = ctypes.c_size_t
+_lib.qft_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp,
+                                  ctypes.c_size_t, _vp, ctypes.c_int]
+_lib.qft_batch_execute.argtypes = [_vp, _vp]
+_lib.qft_batch_status.argtypes = [_vp, _vp]
+_lib.qft_batch_destroy.argtypes = [_vp]
+
 lib = _lib  # the raw ctypes handle (tests call the C ABI through it)
 
 
@@ -209,6 +217,39 @@ class Plan:
             self._h = _vp()
 
 
+class Batch:
+    """Many transforms (plans[i] on device tensors states[i]) run by one persistent launch."""
+
+    def __init__(self, plans, states, scale_mode: int = SCALE_STATE, scale_out=None, device="cuda"):
+        import torch
+
+        n = len(plans)
+        self.plans = list(plans)  # keep the plans alive
+        self.states = list(states)
+        parr = (_vp * n)(*[p.handle for p in plans])
+        sarr = (_vp * n)(*[_ptr(s) for s in states])
+        size = int(_lib.qft_batch_workspace_size(parr, n))
+        if size == 0:
+            raise QftError(ERR_BAD_ARG, "qft_batch_workspace_size")
+        self.workspace = torch.empty(size, dtype=torch.uint8, device=device)
+        self._h = _vp()
+        _check(_lib.qft_batch_create(ctypes.byref(self._h), parr, sarr, n, self.workspace.data_ptr(), size,
+                                     _ptr(scale_out) if scale_out is not None else None, int(scale_mode)),
+               "qft_batch_create")
+
+    def execute(self, stream=None) -> None:
+        _check(_lib.qft_batch_execute(self._h, _stream_handle(stream)), "qft_batch_execute")
+
+    def status(self, stream=None) -> int:
+        return _lib.qft_batch_status(self._h, _stream_handle(stream))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.qft_batch_destroy(h)
+            self._h = _vp()
+
+
 _plan_cache: dict = {}
 
 
@@ -245,5 +286,5 @@ def fft(x, k: int | None = None, inverse: bool = False, norm: str = "backward", 
     return out
 
 
-__all__ = ["Plan", "PlanInfo", "QftError", "fft", "lib", "C64", "C128", "FORWARD", "INVERSE",
+__all__ = ["Plan", "Batch", "PlanInfo", "QftError", "fft", "lib", "C64", "C128", "FORWARD", "INVERSE",
            "SCALE_STATE", "SCALE_UNITARY", "SCALE_UNNORM", "SCALE_INV_N", "ORDER_NATURAL", "ORDER_BITREV"]

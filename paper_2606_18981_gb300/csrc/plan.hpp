@@ -91,4 +91,15 @@ struct PassParams {
     int32_t test_skip_first_load;  // test hook: never issue the first load (the wait must expire)
 };
 
+// One tile of one pass of one transform in a batched launch.
+struct BatchItem {
+    int32_t desc;         // index of the transform's PassParams for this pass
+    int32_t shape;        // passes with equal shape ids share group tables
+    int64_t tile;         // tile index within the pass
+    int32_t wait_ctr;     // counter to wait on before loading (-1: none)
+    int32_t wait_target;  // value that counter must reach
+    int32_t signal_ctr;   // counter to increment when this tile is stored (-1: none)
+    int32_t map;          // index of the tensor map (-1: 1D bulk load)
+};
+
 }  // namespace qft

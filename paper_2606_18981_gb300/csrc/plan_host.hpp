@@ -1,0 +1,63 @@
+// plan_host.hpp -- host-side plan structures shared by the C ABI files
+// (qftfft_api.cpp, qft_batch.cpp).  Internal to libqftfft.
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "plan.hpp"
+
+namespace qft {
+
+cudaError_t launch_pass(int dtype, int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid,
+                        size_t smem, cudaStream_t stream);
+size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes);
+
+// Workspace layout of one transform: [0, 4096) metadata (scale_in at 0,
+// status word at 8, norm partial sums from 64); the ping-pong state buffer
+// from 4096.
+constexpr size_t kMetaBytes = 4096;
+constexpr size_t kStatusOff = 8;
+constexpr size_t kPartialOff = 64;
+constexpr int kMaxPartials = (kMetaBytes - kPartialOff) / 8;
+
+struct PassHost {
+    PassParams prm;
+    int in_buf = 0, out_buf = 0;  // 0 = caller's state, 1 = workspace ping-pong buffer
+    int grid = 1;
+    size_t smem = 0;
+    // TMA description
+    int rank = 5;
+    cuuint64_t gdim[5];
+    cuuint64_t gstride[4];
+    cuuint32_t box[5];
+    int wires = 0;
+    int run_bits = 0;  // low input address bits inside the tile (log2 amplitudes per HBM run)
+};
+
+int set_cuda_error(cudaError_t e);           // records e for qft_last_cuda_error, returns QFT_ERR_CUDA
+void set_cuda_error_code(int e);
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn();
+
+}  // namespace qft
+
+struct qft_plan_s {
+    int n = 0, k = -1, kk = 0, dir = -1, dtype = 0, order = 0;
+    size_t esize = 8;
+    int TB = 13, cmin = 2, rmax = 4;
+    int threads = 256;  // CTA size of the pass kernel (256: stages of <= 5 wires; 512: <= 4)
+    uint64_t wait_limit_ns = 2000000000ull;
+    int test_skip_first_load = 0;
+    int num_sms = 148;
+    long long n_h = 0, n_cp = 0, n_swap = 0;
+    std::vector<qft::PassHost> passes;
+    size_t ws_bytes = 0;
+    // tensor maps for the last (state, workspace) pointer pair
+    std::mutex mu;
+    const void* map_state = nullptr;
+    const void* map_work = nullptr;
+    std::vector<CUtensorMap> maps;
+};

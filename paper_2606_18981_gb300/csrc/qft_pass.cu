@@ -466,30 +466,13 @@ __device__ __forceinline__ void compute_tile_twiddles(const PassParams& P, int64
     Ubuf[i] = phase_turns<T, DIR>(beta, P.n);
 }
 
+// Build the group tables (pb, ob, cross-twiddle factors of the group's tile
+// wires) of every stage of pass P into shared memory.
 template <typename T, int DIR, int NT>
-__global__ void __launch_bounds__(NT, 1)
-    qft_pass_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassParams P) {
+__device__ __forceinline__ void build_group_tables(const PassParams& P, GroupTab<typename Vec2<T>::type>& tab) {
     using V = typename Vec2<T>::type;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ double red[NT / 32];
-    __shared__ __align__(16) V Ubuf[2][kMaxR * kMaxStages];
-
     const int tid = threadIdx.x;
-    const uint32_t tile_elems = 1u << P.tb;
-    const uint32_t tile_bytes = tile_elems * static_cast<uint32_t>(sizeof(V));
-    // buffer B first, then the two TMA load buffers, then the group tables
-    V* B = reinterpret_cast<V*>(smem_raw);
-    V* const A0 = B + tile_elems;  // load buffer k & 1 is A0 + (k & 1) * tile_elems
-    unsigned char* tab_raw = smem_raw + 3 * static_cast<size_t>(tile_bytes);
-    const int ntab = P.ntab;
-    GroupTab<V> tab;
-    tab.ntab = ntab;
-    tab.tw = reinterpret_cast<V*>(tab_raw);
-    tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * sizeof(V) * static_cast<size_t>(ntab));
-    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * sizeof(V) + 8) * static_cast<size_t>(ntab));
-
-    // Build the group tables (pb, ob, cross-twiddle factors of the group's tile wires).
+    const int ntab = tab.ntab;
     for (int s = 0; s < P.nstages; ++s) {
         const StageDesc& S = P.st[s];
         const int ng = 1 << S.ngbits;
@@ -519,6 +502,32 @@ __global__ void __launch_bounds__(NT, 1)
             }
         }
     }
+}
+
+template <typename T, int DIR, int NT>
+__global__ void __launch_bounds__(NT, 1)
+    qft_pass_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassParams P) {
+    using V = typename Vec2<T>::type;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ double red[NT / 32];
+    __shared__ __align__(16) V Ubuf[2][kMaxR * kMaxStages];
+
+    const int tid = threadIdx.x;
+    const uint32_t tile_elems = 1u << P.tb;
+    const uint32_t tile_bytes = tile_elems * static_cast<uint32_t>(sizeof(V));
+    // buffer B first, then the two TMA load buffers, then the group tables
+    V* B = reinterpret_cast<V*>(smem_raw);
+    V* const A0 = B + tile_elems;  // load buffer k & 1 is A0 + (k & 1) * tile_elems
+    unsigned char* tab_raw = smem_raw + 3 * static_cast<size_t>(tile_bytes);
+    const int ntab = P.ntab;
+    GroupTab<V> tab;
+    tab.ntab = ntab;
+    tab.tw = reinterpret_cast<V*>(tab_raw);
+    tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * sizeof(V) * static_cast<size_t>(ntab));
+    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * sizeof(V) + 8) * static_cast<size_t>(ntab));
+
+    build_group_tables<T, DIR, NT>(P, tab);
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
@@ -608,6 +617,170 @@ __global__ void __launch_bounds__(NT, 1)
         const double tot = block_sum<NT>(norm_acc, red);
         if (tid == 0) P.partials[blockIdx.x] = tot;
     }
+}
+
+// ------------------------------------------------------------ batched launch
+//
+// One persistent launch over a list of tile work items drawn from many
+// transforms of different sizes and plans.  Each CTA claims items in order
+// from an atomic counter; an item is one tile of one pass of one transform.
+// Items are ordered transform by transform, so the second pass of a
+// transform runs right after its first (its intermediate is still in L2).
+// A second-pass item waits (bounded) until every first-pass tile of its
+// transform has signalled completion; the producers were claimed earlier by
+// running CTAs and never wait themselves, so the waits always end.
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+template <typename T, int DIR, int NT>
+__global__ void __launch_bounds__(NT, 1)
+    qft_batch_kernel(const BatchItem* __restrict__ items, int nitems, const PassParams* __restrict__ descs,
+                     const CUtensorMap* __restrict__ maps, int* counters, int* next, int* status,
+                     uint64_t wait_ns, int max_tb, int max_ntab) {
+    using V = typename Vec2<T>::type;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ double red[NT / 32];
+    __shared__ __align__(16) V Ubuf[kMaxR * kMaxStages];
+    __shared__ int s_item;
+
+    const int tid = threadIdx.x;
+    const uint32_t max_elems = 1u << max_tb;
+    V* B = reinterpret_cast<V*>(smem_raw);
+    V* A = B + max_elems;
+    unsigned char* tab_raw = smem_raw + 2 * static_cast<size_t>(max_elems) * sizeof(V);
+    GroupTab<V> tab;
+    tab.ntab = max_ntab;
+    tab.tw = reinterpret_cast<V*>(tab_raw);
+    tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * sizeof(V) * static_cast<size_t>(max_ntab));
+    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * sizeof(V) + 8) * static_cast<size_t>(max_ntab));
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    uint32_t parity = 0;
+    int cached_shape = -1;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(next, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        const BatchItem it = items[item];
+        const PassParams& P = descs[it.desc];
+        if (it.shape != cached_shape) {
+            build_group_tables<T, DIR, NT>(P, tab);
+            cached_shape = it.shape;
+        }
+        bool ok = true;
+        if (tid == 0) {
+            if (it.wait_ctr >= 0) {
+                const uint64_t t0 = global_timer_ns();
+                while (ld_acquire_gpu(counters + it.wait_ctr) < it.wait_target) {
+                    if (global_timer_ns() - t0 > wait_ns) { ok = false; break; }
+                }
+                fence_proxy_async_global();  // the first pass's stores before this pass's TMA reads
+            }
+            if (ok) {
+                const uint32_t bytes = (1u << P.tb) * static_cast<uint32_t>(sizeof(V));
+                issue_tile_load(P, maps + (it.map >= 0 ? it.map : 0), it.tile, A, &mbar, bytes);
+            }
+        }
+        compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(status, -5);  // QFT_ERR_TIMEOUT
+            return;
+        }
+        const bool okw = mbar_wait_bounded(&mbar, parity, wait_ns);
+        parity ^= 1u;
+        if (__syncthreads_or(!okw)) {
+            if (tid == 0) {
+                atomicExch(status, -5);
+                mbar_wait_bounded(&mbar, parity ^ 1u, wait_ns);
+            }
+            return;
+        }
+        uint64_t I_tile;
+        int64_t out_tile;
+        tile_coords(P, it.tile, I_tile, out_tile);
+        T scale = T(1);
+        if (P.first && P.last) {
+            double s = 0.0;
+            for (uint32_t i = tid; i < (1u << P.tb); i += NT) {
+                const V a = A[i];
+                s += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
+            }
+            const double scale_in = sqrt(block_sum<NT>(s, red));
+            scale = static_cast<T>(output_factor(P, scale_in));
+            if (tid == 0) {
+                P.meta[0] = scale_in;
+                if (P.user_scale) *P.user_scale = scale_in;
+            }
+        } else if (P.last) {
+            double s = 0.0;
+            for (int i = tid; i < P.npartials; i += NT) s += P.partials[i];
+            const double scale_in = sqrt(block_sum<NT>(s, red));
+            scale = static_cast<T>(output_factor(P, scale_in));
+            if (tid == 0 && it.tile == 0) {
+                P.meta[0] = scale_in;
+                if (P.user_scale) *P.user_scale = scale_in;
+            }
+        }
+        double norm_acc = 0.0;
+        for (int s = 0; s < P.nstages; ++s) {
+            dispatch_stage<T, DIR, NT>(P, s, tab, A, B, out_tile, scale, Ubuf + P.st[s].uoff,
+                                       P.first && !P.last, norm_acc);
+            __syncthreads();
+        }
+        if (P.first && !P.last) {
+            const double tot = block_sum<NT>(norm_acc, red);
+            if (tid == 0) P.partials[it.tile] = tot;  // one partial per first-pass tile
+        }
+        if (it.signal_ctr >= 0) {
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicAdd(counters + it.signal_ctr, 1);
+        }
+        fence_proxy_async_smem();  // this item's shared-memory reads before the next item's TMA write
+    }
+}
+
+template <typename T, int DIR, int NT>
+static cudaError_t launch_batch_t(const BatchItem* items, int nitems, const PassParams* descs,
+                                  const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
+                                  int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
+    auto kern = qft_batch_kernel<T, DIR, NT>;
+    static thread_local size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    kern<<<grid, NT, smem, stream>>>(items, nitems, descs, maps, counters, next, status, wait_ns, max_tb, max_ntab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(int dtype, int dir, const BatchItem* items, int nitems, const PassParams* descs,
+                         const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
+                         int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
+    if (dtype == 0)
+        return dir < 0 ? launch_batch_t<float, -1, 256>(items, nitems, descs, maps, counters, next, status, wait_ns,
+                                                         max_tb, max_ntab, grid, smem, stream)
+                       : launch_batch_t<float, +1, 256>(items, nitems, descs, maps, counters, next, status, wait_ns,
+                                                         max_tb, max_ntab, grid, smem, stream);
+    return dir < 0 ? launch_batch_t<double, -1, 256>(items, nitems, descs, maps, counters, next, status, wait_ns,
+                                                      max_tb, max_ntab, grid, smem, stream)
+                   : launch_batch_t<double, +1, 256>(items, nitems, descs, maps, counters, next, status, wait_ns,
+                                                      max_tb, max_ntab, grid, smem, stream);
+}
+
+size_t batch_smem_bytes(int max_tb, int max_ntab, size_t elem_bytes) {
+    return 2 * (size_t(1) << max_tb) * elem_bytes + size_t(max_ntab) * (kMaxR * elem_bytes + 8 + 4);
 }
 
 // ------------------------------------------------------------- launchers

@@ -26,45 +26,21 @@
 #include <vector>
 
 #include "../../include/qftfft.h"
-#include "plan.hpp"
+#include "plan_host.hpp"
 
-namespace qft {
-cudaError_t launch_pass(int dtype, int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid,
-                        size_t smem, cudaStream_t stream);
-size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes);
-}  // namespace qft
 
 using namespace qft;
 
-namespace {
+namespace qft {
 
 thread_local int g_last_cuda = 0;
 
-int cuda_fail(cudaError_t e) {
+int set_cuda_error(cudaError_t e) {
     g_last_cuda = static_cast<int>(e);
     return QFT_ERR_CUDA;
 }
 
-// Workspace layout: [0, 4096) meta (scale_in at 0, status word at 8,
-// partials from 64 on); the ping-pong state buffer from 4096.
-constexpr size_t kMetaBytes = 4096;
-constexpr size_t kStatusOff = 8;
-constexpr size_t kPartialOff = 64;
-constexpr int kMaxPartials = (kMetaBytes - kPartialOff) / 8;
-
-struct PassHost {
-    PassParams prm;
-    int in_buf = 0, out_buf = 0;  // 0 = caller's state, 1 = workspace ping-pong buffer
-    int grid = 1;
-    size_t smem = 0;
-    // TMA description
-    int rank = 5;
-    cuuint64_t gdim[5];
-    cuuint64_t gstride[4];
-    cuuint32_t box[5];
-    int wires = 0;
-    int run_bits = 0;  // low input address bits inside the tile (log2 amplitudes per HBM run)
-};
+void set_cuda_error_code(int e) { g_last_cuda = e; }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -80,25 +56,11 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     return fn;
 }
 
-}  // namespace
+}  // namespace qft
 
-struct qft_plan_s {
-    int n = 0, k = -1, kk = 0, dir = -1, dtype = 0, order = 0;
-    size_t esize = 8;
-    int TB = 13, cmin = 2, rmax = 4;
-    int threads = 256;  // CTA size of the pass kernel (256: stages of <= 5 wires; 512: <= 4)
-    uint64_t wait_limit_ns = 2000000000ull;
-    int test_skip_first_load = 0;
-    int num_sms = 148;
-    long long n_h = 0, n_cp = 0, n_swap = 0;
-    std::vector<PassHost> passes;
-    size_t ws_bytes = 0;
-    // tensor maps for the last (state, workspace) pointer pair
-    std::mutex mu;
-    const void* map_state = nullptr;
-    const void* map_work = nullptr;
-    std::vector<CUtensorMap> maps;
-};
+namespace {
+int cuda_fail(cudaError_t e) { return qft::set_cuda_error(e); }
+}  // namespace
 
 namespace {
 
@@ -419,7 +381,7 @@ int encode_maps(qft_plan_s* pl, const void* state, const void* work) {
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
-            g_last_cuda = static_cast<int>(r);
+            qft::set_cuda_error_code(static_cast<int>(r));
             pl->maps.clear();
             return QFT_ERR_CUDA;
         }
@@ -435,7 +397,7 @@ extern "C" {
 
 int qft_version(void) { return 100; }
 
-int qft_last_cuda_error(void) { return g_last_cuda; }
+int qft_last_cuda_error(void) { return qft::g_last_cuda; }
 
 const char* qft_strerror(int code) {
     switch (code) {

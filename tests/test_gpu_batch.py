@@ -1,0 +1,98 @@
+"""Batched execution on the GPU: one persistent launch over many uneven transforms.
+
+Every transform of a mixed batch must give the result it gives alone
+(qft_execute with the same plan), within the parity tolerances; a sample is
+also checked against the CPU oracle.  Graph capture and replay of the batch
+launch must reproduce the same results.
+"""
+import numpy as np
+import pytest
+
+import qft_inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+q = pytest.importorskip("paper_2606_18981_gb300")
+
+TOL = {"c64": lambda n: 2e-6, "c128": lambda n: 1e-13 * n}
+
+
+def rel(a, b):
+    a = a.to(torch.complex128)
+    b = b.to(torch.complex128)
+    return float(torch.linalg.vector_norm(a - b) / max(torch.linalg.vector_norm(b), 1e-300))
+
+
+def make_batch(count, nmin, nmax, dt, order, seed, direction=q.FORWARD):
+    rng = np.random.default_rng(seed)
+    td = torch.complex64 if dt == "c64" else torch.complex128
+    plans, xs, ks = {}, [], []
+    specs = []
+    for i in range(count):
+        n = int(rng.integers(nmin, nmax + 1))
+        k = int(rng.choice([4, 8, n]))
+        kind = qft_inputs.KINDS[i % 3]
+        specs.append((n, k, kind))
+    for i, (n, k, kind) in enumerate(specs):
+        key = (n, k)
+        if key not in plans:
+            plans[key] = q.Plan(n, k, direction, dt, order)
+        xs.append(torch.from_numpy(qft_inputs.make(kind, n, seed * 1000 + i)).to(td).cuda())
+    return specs, plans, xs
+
+
+@pytest.mark.parametrize("dt,order", [("c64", 0), ("c64", 1), ("c128", 0)])
+def test_batch_matches_single_transforms(oracle_mod, dt, order):
+    specs, plans, xs = make_batch(96, 3, 17, dt, order, seed=7)
+    states = [x.clone() for x in xs]
+    scales = torch.zeros(len(xs), dtype=torch.float64, device="cuda")
+    b = q.Batch([plans[(n, k)] for n, k, _ in specs], states, q.SCALE_STATE, scale_out=scales)
+    b.execute()
+    assert b.status() == 0
+    for i, (n, k, _) in enumerate(specs):
+        p = plans[(n, k)]
+        ref = xs[i].clone()
+        ws = p.alloc_workspace()
+        p.execute(ref, ws, q.SCALE_STATE)
+        torch.cuda.synchronize()
+        assert rel(states[i], ref) <= TOL[dt](n), (i, n, k)
+        assert abs(scales[i].item() - p.scale_in(ws)) <= 1e-6 * max(p.scale_in(ws), 1e-300)
+    for i in (0, 1, 2, 50, 95):
+        n, k, _ = specs[i]
+        want, _ = oracle_mod.qft(xs[i].cpu().numpy().astype(np.complex128), k, -1, 0, order == 0)
+        got = states[i].cpu().numpy().astype(np.complex128)
+        err = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert err <= TOL[dt](n)
+
+
+def test_batch_graph_capture_replay():
+    specs, plans, xs = make_batch(64, 8, 18, "c64", 0, seed=11)
+    states = [x.clone() for x in xs]
+    b = q.Batch([plans[(n, k)] for n, k, _ in specs], states, q.SCALE_STATE)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.execute(stream=s)
+    torch.cuda.synchronize()
+    first = [st.clone() for st in states]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.execute(stream=s)
+    for _ in range(2):
+        for st, x in zip(states, xs):
+            st.copy_(x)
+        g.replay()
+        torch.cuda.synchronize()
+        for st, f in zip(states, first):
+            assert torch.equal(st, f)
+
+
+def test_batch_inverse_round_trip():
+    specs, plans, xs = make_batch(40, 5, 16, "c64", 0, seed=3)
+    inv = {key: q.Plan(key[0], key[1], q.INVERSE, "c64", 0) for key in plans}
+    states = [x.clone() for x in xs]
+    q.Batch([plans[(n, k)] for n, k, _ in specs], states, q.SCALE_UNITARY).execute()
+    q.Batch([inv[(n, k)] for n, k, _ in specs], states, q.SCALE_UNITARY).execute()
+    torch.cuda.synchronize()
+    for st, x, (n, _, _) in zip(states, xs, specs):
+        assert rel(st, x) <= 4e-6
