@@ -227,6 +227,99 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------ ours
 
+def device_input(torch, kind, n, seed, dt, device):
+    """One synthetic input of the given kind drawn on the device (seeded)."""
+    import qft_inputs
+
+    N = 1 << n
+    td = torch.complex64 if dt == "c64" else torch.complex128
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    if kind == "basis":
+        x = torch.zeros(N, dtype=td, device=device)
+        x[int(torch.randint(0, N, (1,), generator=g, device=device).item())] = 1
+        return x
+    if kind == "tones":
+        j = torch.arange(N, device=device, dtype=torch.int64)
+        x = torch.zeros(N, dtype=torch.complex128, device=device)
+        cnt = int(torch.randint(1, 9, (1,), generator=g, device=device).item())
+        for _ in range(cnt):
+            f = int(torch.randint(0, N, (1,), generator=g, device=device).item())
+            a = 0.1 + 0.9 * float(torch.rand(1, generator=g, device=device).item())
+            ph = 2 * 3.141592653589793 * float(torch.rand(1, generator=g, device=device).item())
+            x += a * torch.exp(1j * (2 * 3.141592653589793 * ((f * j) % N).to(torch.float64) / N + ph))
+        x += 1e-3 * torch.randn(N, dtype=torch.complex128, generator=g, device=device)
+        return x.to(td)
+    return qft_inputs.device_gaussian(n, seed, dt, device=str(device))
+
+
+def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
+    """The batched configuration: count transforms, n ~ U{8..18}, complex64,
+    input kinds ~ U{Gaussian, tones, basis}, AQFT k ~ U{4, 8, n}, forward,
+    natural order; one persistent launch captured in a CUDA graph.  Also times
+    the same transforms one by one on the plain complex128 path."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        n = int(rng.integers(8, 19))
+        specs.append((n, int(rng.choice([4, 8, n])), ("gaussian", "tones", "basis")[int(rng.integers(0, 3))]))
+    amps = sum(1 << n for n, _, _ in specs)
+    plans = {}
+    for n, k, _ in specs:
+        if (n, k) not in plans:
+            plans[(n, k)] = q.Plan(n, k, q.FORWARD, "c64", q.ORDER_NATURAL)
+    pool = torch.empty(amps + 64 * count, dtype=torch.complex64, device=dev)
+    states, off = [], 0
+    for i, (n, k, kind) in enumerate(specs):
+        st = pool[off:off + (1 << n)]
+        st.copy_(device_input(torch, kind, n, seed * 100000 + i, "c64", dev))
+        states.append(st)
+        off += (1 << n) + ((-(1 << n)) % 32)
+    batch = q.Batch([plans[(n, k)] for n, k, _ in specs], states, q.SCALE_STATE, device=dev)
+    with torch.cuda.stream(stream):
+        batch.execute(stream=stream)
+        batch.execute(stream=stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batch.execute(stream=stream)
+    g.replay()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    bb = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        g.replay()
+    bb.record(stream)
+    torch.cuda.synchronize()
+    status = batch.status(stream)
+    ms = a.elapsed_time(bb) / reps
+    out = {"transforms": count, "amplitudes": amps, "ms_per_batch": ms, "transforms_per_s": count / (ms / 1e3),
+           "amplitudes_per_s": amps / (ms / 1e3), "status": status, "launches_per_batch": 1,
+           "graph": True}
+    del batch, states, pool, g
+    torch.cuda.empty_cache()
+    # the plain single-transform complex128 path on the same transforms
+    p128 = {key: q.Plan(key[0], key[1], q.FORWARD, "c128", q.ORDER_NATURAL) for key in plans}
+    ws = {key: p.alloc_workspace(dev) for key, p in p128.items()}
+    buf = torch.empty(1 << 18, dtype=torch.complex128, device=dev)
+    sub = specs[:1024]
+    for n, k, _ in sub[:16]:
+        p128[(n, k)].execute(buf[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for n, k, _ in sub:
+        p128[(n, k)].execute(buf[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
+    bb.record(stream)
+    torch.cuda.synchronize()
+    ms128 = a.elapsed_time(bb)
+    out["plain_c128_single"] = {"transforms": len(sub), "ms": ms128, "transforms_per_s": len(sub) / (ms128 / 1e3)}
+    out["speedup_vs_plain_c128_single"] = out["transforms_per_s"] / out["plain_c128_single"]["transforms_per_s"]
+    return out
+
+
 def timed_transform(q, torch, plan, state, ws, stream, steps, warmup):
     """Device-timed steps on resident data; returns (ms/step, [mean ms per pass])."""
     P = plan.info().passes
@@ -350,6 +443,10 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_extra:
         del state, ws
         torch.cuda.empty_cache()
+        try:
+            extra["batched_4096_n8to18_c64"] = batched_workload(q, torch, dev, stream)
+        except Exception as ex:
+            extra["batched_4096_n8to18_c64"] = {"error": str(ex)[:300]}
         for name, (nn, ddt, kk) in {"aqft_k4_c64_n30": (30, "c64", 4), "plain_c128_n30": (30, "c128", -1),
                                      "c64_n26": (26, "c64", -1), "c64_n33": (33, "c64", -1)}.items():
             try:

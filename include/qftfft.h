@@ -181,6 +181,48 @@ int qft_batch_execute(qft_batch_t batch, qft_stream_t stream);
 int qft_batch_status(qft_batch_t batch, qft_stream_t stream);
 int qft_batch_destroy(qft_batch_t batch);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop for transforms of mixed n, cutoff, direction and dtype
+ * (not in the paper; each request runs the circuit of Sec. 3 exactly as
+ * qft_execute does).  A worker thread admits requests in arrival order as
+ * soon as their device bytes (state + workspace) fit in the HBM budget next
+ * to everything in flight and an in-flight slot is free, runs each on the
+ * least-loaded of its streams (copy in, execute, copy out), so new requests
+ * overlap with running ones, and records each request's latency from submit
+ * to completion.  The server allocates and pools its own device buffers and
+ * caches one plan per (n, k, direction, dtype, order). */
+typedef struct {
+    int n, k, direction, dtype, order, scale_mode; /* as qft_plan_create / qft_execute        */
+    const void* input;                             /* 2^n complex values, host or device     */
+    int input_on_device;
+    void* output;                                  /* 2^n complex values, host or device     */
+    int output_on_device;
+    double* scale_in_out;                          /* optional host double receiving scale_in */
+} qft_request;
+
+typedef struct {
+    long long completed, failed, pending, in_flight;
+    size_t bytes_in_use, bytes_pooled;
+    double p50_ms, p99_ms, max_ms;                 /* submit-to-completion latency           */
+    double requests_per_s;                         /* completed / (last completion - first submit) */
+} qft_server_stats;
+
+/* Start a server on the current device.  hbm_budget_bytes bounds the device
+ * memory of admitted requests; streams (0 = 8) and max_inflight (0 = 64). */
+int qft_server_create(qft_server_t* out, size_t hbm_budget_bytes, int streams, int max_inflight);
+/* Queue a request (its buffers must stay valid until it completes); *ticket identifies it.
+ * Requests larger than the budget fail with QFT_ERR_BUDGET. */
+int qft_server_submit(qft_server_t server, const qft_request* request, uint64_t* ticket);
+/* *done = 1 once finished; returns the request's status if finished, else QFT_OK. */
+int qft_server_poll(qft_server_t server, uint64_t ticket, int* done);
+/* Block until the request finishes (timeout_ms < 0: no limit; QFT_ERR_TIMEOUT when it
+ * expires) and return its status; *latency_ms (optional) gets its latency.  Forgets the ticket. */
+int qft_server_wait(qft_server_t server, uint64_t ticket, int timeout_ms, double* latency_ms);
+int qft_server_get_stats(qft_server_t server, qft_server_stats* out);
+int qft_server_reset_stats(qft_server_t server);
+/* Finish every queued request, then stop the worker and free the server's memory. */
+int qft_server_destroy(qft_server_t server);
+
 /* qft_execute without a caller-provided workspace, for callers that cannot
  * allocate device memory: code that runs while a stream is being captured into
  * a CUDA graph (cudaMalloc is not allowed during capture), host runtimes that

@@ -88,6 +88,27 @@ _lib.qft_batch_execute.argtypes = [_vp, _vp]
 _lib.qft_batch_status.argtypes = [_vp, _vp]
 _lib.qft_batch_destroy.argtypes = [_vp]
 
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("k", ctypes.c_int), ("direction", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("order", ctypes.c_int), ("scale_mode", ctypes.c_int), ("input", _vp), ("input_on_device", ctypes.c_int),
+                ("output", _vp), ("output_on_device", ctypes.c_int), ("scale_in_out", ctypes.POINTER(ctypes.c_double))]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("pending", ctypes.c_longlong),
+                ("in_flight", ctypes.c_longlong), ("bytes_in_use", ctypes.c_size_t), ("bytes_pooled", ctypes.c_size_t),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("requests_per_s", ctypes.c_double)]
+
+
+_lib.qft_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int]
+_lib.qft_server_submit.argtypes = [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+_lib.qft_server_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+_lib.qft_server_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+_lib.qft_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
+_lib.qft_server_reset_stats.argtypes = [_vp]
+_lib.qft_server_destroy.argtypes = [_vp]
+
 lib = _lib  # the raw ctypes handle (tests call the C ABI through it)
 
 
@@ -250,6 +271,56 @@ class Batch:
             self._h = _vp()
 
 
+class Server:
+    """Continuous-batching request loop (C++ worker thread inside the library)."""
+
+    def __init__(self, hbm_budget_bytes: int, streams: int = 0, max_inflight: int = 0):
+        self._h = _vp()
+        _check(_lib.qft_server_create(ctypes.byref(self._h), int(hbm_budget_bytes), int(streams), int(max_inflight)),
+               "qft_server_create")
+        self._keep = {}
+
+    def submit(self, x, out, n: int, k: int = -1, direction: int = FORWARD, dtype="c64", order: int = ORDER_NATURAL,
+               scale_mode: int = SCALE_STATE) -> int:
+        """Queue a transform of x into out (torch tensors or numpy arrays; keep them alive)."""
+        def ptr_loc(t):
+            if hasattr(t, "data_ptr"):
+                return t.data_ptr(), 1 if t.is_cuda else 0
+            return t.ctypes.data, 0
+        ip, il = ptr_loc(x)
+        op, ol = ptr_loc(out)
+        scale = ctypes.c_double(0.0)
+        req = Request(int(n), int(k), int(direction), _dtype_code(dtype), int(order), int(scale_mode), ip, il, op, ol,
+                      ctypes.pointer(scale))
+        t = ctypes.c_uint64()
+        _check(_lib.qft_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "qft_server_submit")
+        self._keep[t.value] = (x, out, scale)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Returns (status, latency_ms, scale_in)."""
+        lat = ctypes.c_double()
+        rc = _lib.qft_server_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(lat))
+        keep = self._keep.pop(ticket, None)
+        return rc, lat.value, keep[2].value if keep else None
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(_lib.qft_server_get_stats(self._h, ctypes.byref(st)), "qft_server_get_stats")
+        return st
+
+    def reset_stats(self) -> None:
+        _lib.qft_server_reset_stats(self._h)
+
+    def close(self) -> None:
+        if self._h.value:
+            _lib.qft_server_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        self.close()
+
+
 _plan_cache: dict = {}
 
 
@@ -286,5 +357,5 @@ def fft(x, k: int | None = None, inverse: bool = False, norm: str = "backward", 
     return out
 
 
-__all__ = ["Plan", "Batch", "PlanInfo", "QftError", "fft", "lib", "C64", "C128", "FORWARD", "INVERSE",
+__all__ = ["Plan", "Batch", "Server", "PlanInfo", "QftError", "fft", "lib", "C64", "C128", "FORWARD", "INVERSE",
            "SCALE_STATE", "SCALE_UNITARY", "SCALE_UNNORM", "SCALE_INV_N", "ORDER_NATURAL", "ORDER_BITREV"]

@@ -1,0 +1,379 @@
+// qft_server.cpp -- a continuous-batching request loop for transforms of mixed
+// sizes, cutoffs, directions and dtypes.
+//
+// A worker thread owns a set of CUDA streams, a plan cache keyed by
+// (n, k, direction, dtype, order), and a pool of device buffers.  Requests are
+// admitted in arrival order as soon as (a) the bytes they need on the device
+// (state + workspace) fit in the HBM budget together with everything in
+// flight and (b) an in-flight slot is free; each admitted request is enqueued
+// on the least-loaded stream as copy-in, qft_execute, copy-out and an event,
+// so requests that arrive while others run overlap with them on the device.
+// Completion is detected by polling the events; the buffers go back to the
+// pool and the request's latency (submit to completion) is recorded.  Every
+// request runs the same plan and kernels it would run alone, so its result is
+// the one qft_execute gives for it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/qftfft.h"
+#include "plan_host.hpp"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    qft_request r{};
+    Clock::time_point t_submit;
+};
+
+struct InFlight {
+    Request req;
+    qft_plan_t plan = nullptr;
+    void* state = nullptr;
+    void* ws = nullptr;
+    size_t bytes = 0;
+    int stream = 0;
+    cudaEvent_t done = nullptr;
+    double* h_slot = nullptr;  // pinned 16-byte slot: scale_in (double) then the status word (int)
+    int slot = 0;
+};
+
+struct Result {
+    int status = 1;  // 1 = pending, 0 = ok, < 0 = error
+    double latency_ms = 0.0;
+    double scale_in = 0.0;
+};
+
+}  // namespace
+
+struct qft_server_s {
+    size_t budget = 0, in_use = 0;
+    int nstreams = 8, max_inflight = 64, device = 0;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> stream_load;
+    std::map<std::tuple<int, int, int, int, int>, qft_plan_t> plans;
+    std::multimap<size_t, void*> pool;  // free device buffers by size
+    size_t pooled = 0;
+    std::deque<Request> pending;
+    std::vector<InFlight> inflight;
+    std::unordered_map<uint64_t, Result> results;
+    std::vector<double> latencies;
+    Clock::time_point t_first{}, t_last{};
+    uint64_t next_ticket = 1, completed = 0, failed = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::atomic<bool> stop{false};
+    std::thread worker;
+    double* slots = nullptr;  // pinned host memory, two doubles per in-flight slot
+    std::vector<int> free_slots;
+};
+
+namespace {
+
+size_t request_bytes(qft_plan_t p) {
+    return ((size_t(1) << p->n) * p->esize + 255) / 256 * 256 + (qft_workspace_size(p) + 255) / 256 * 256;
+}
+
+// Device buffer of at least `bytes` from the pool (an idle buffer of up to
+// twice the size is reused), or a new allocation; idle pooled buffers are
+// freed first if a new allocation would exceed the budget.  *got = its size.
+void* pool_get(qft_server_s* s, size_t bytes, size_t* got) {
+    auto it = s->pool.lower_bound(bytes);
+    if (it != s->pool.end() && it->first <= bytes * 2) {
+        void* p = it->second;
+        *got = it->first;
+        s->pooled -= it->first;
+        s->pool.erase(it);
+        return p;
+    }
+    while (!s->pool.empty() && s->in_use + s->pooled + bytes > s->budget) {
+        auto v = s->pool.begin();
+        cudaFree(v->second);
+        s->pooled -= v->first;
+        s->pool.erase(v);
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *got = bytes;
+    return p;
+}
+
+void pool_put(qft_server_s* s, void* p, size_t bytes) {
+    s->pool.emplace(bytes, p);
+    s->pooled += bytes;
+}
+
+qft_plan_t get_plan(qft_server_s* s, const qft_request& r) {
+    const int kk = (r.k < 0 || r.k > r.n - 1) ? -1 : r.k;
+    auto key = std::make_tuple(r.n, kk, r.direction, r.dtype, r.order);
+    auto it = s->plans.find(key);
+    if (it != s->plans.end()) return it->second;
+    qft_opts o{};
+    o.order = r.order;
+    qft_plan_t p = nullptr;
+    if (qft_plan_create(&p, r.n, kk, r.direction, r.dtype, &o) != QFT_OK) return nullptr;
+    s->plans[key] = p;
+    return p;
+}
+
+void finish(qft_server_s* s, const Request& rq, int status, double scale_in) {
+    const auto now = Clock::now();
+    Result& res = s->results[rq.ticket];
+    res.status = status;
+    res.scale_in = scale_in;
+    res.latency_ms = std::chrono::duration<double, std::milli>(now - rq.t_submit).count();
+    if (status == QFT_OK) {
+        s->latencies.push_back(res.latency_ms);
+        if (s->completed == 0) s->t_first = rq.t_submit;
+        s->t_last = now;
+        ++s->completed;
+    } else {
+        ++s->failed;
+    }
+}
+
+// Issue one admitted request; returns false if it could not be issued.
+int issue(qft_server_s* s, InFlight& f) {
+    const qft_request& r = f.req.r;
+    const size_t N = size_t(1) << r.n;
+    const size_t sbytes = N * f.plan->esize;
+    cudaStream_t st = s->streams[f.stream];
+    cudaError_t e = cudaMemcpyAsync(f.state, r.input, sbytes,
+                                    r.input_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return qft::set_cuda_error(e);
+    int rc = qft_execute(f.plan, f.state, f.ws, nullptr, r.scale_mode, reinterpret_cast<qft_stream_t>(st));
+    if (rc != QFT_OK) return rc;
+    e = cudaMemcpyAsync(r.output, f.state, sbytes, r.output_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        st);
+    // scale_in (offset 0) and the status word (offset 8) of the workspace in one copy
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f.h_slot, f.ws, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(f.done, st);
+    return e == cudaSuccess ? QFT_OK : qft::set_cuda_error(e);
+}
+
+void worker_loop(qft_server_s* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lock(s->mu);
+    while (true) {
+        // 1. retire finished requests
+        for (size_t i = 0; i < s->inflight.size();) {
+            InFlight& f = s->inflight[i];
+            const cudaError_t q = cudaEventQuery(f.done);
+            if (q == cudaErrorNotReady) { ++i; continue; }
+            int rc = QFT_OK;
+            if (q != cudaSuccess) rc = qft::set_cuda_error(q);
+            else {
+                int32_t dev_status;
+                std::memcpy(&dev_status, f.h_slot + 1, sizeof(dev_status));
+                if (dev_status != 0) rc = dev_status;
+            }
+            const double scale_in = f.h_slot[0];
+            finish(s, f.req, rc, scale_in);
+            if (rc == QFT_OK && f.req.r.scale_in_out) *f.req.r.scale_in_out = scale_in;
+            pool_put(s, f.state, f.bytes);
+            s->in_use -= f.bytes;
+            s->stream_load[f.stream]--;
+            s->free_slots.push_back(f.slot);
+            cudaEventDestroy(f.done);
+            s->inflight[i] = s->inflight.back();
+            s->inflight.pop_back();
+            s->cv_done.notify_all();
+        }
+        // 2. admit in arrival order while budget and slots allow
+        while (!s->pending.empty() && static_cast<int>(s->inflight.size()) < s->max_inflight) {
+            Request& rq = s->pending.front();
+            qft_plan_t p = get_plan(s, rq.r);
+            if (!p) { finish(s, rq, QFT_ERR_BAD_ARG, 0.0); s->pending.pop_front(); s->cv_done.notify_all(); continue; }
+            const size_t bytes = request_bytes(p);
+            if (bytes > s->budget) { finish(s, rq, QFT_ERR_BUDGET, 0.0); s->pending.pop_front(); s->cv_done.notify_all(); continue; }
+            if (s->in_use + bytes > s->budget) break;  // wait for memory to free up (keeps arrival order)
+            InFlight f;
+            f.req = rq;
+            f.plan = p;
+            f.state = pool_get(s, bytes, &f.bytes);
+            if (!f.state) break;
+            f.ws = static_cast<char*>(f.state) + ((size_t(1) << p->n) * p->esize + 255) / 256 * 256;
+            f.stream = static_cast<int>(std::min_element(s->stream_load.begin(), s->stream_load.end()) - s->stream_load.begin());
+            f.slot = s->free_slots.back();
+            s->free_slots.pop_back();
+            f.h_slot = s->slots + 2 * f.slot;
+            cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
+            const int rc = issue(s, f);
+            s->pending.pop_front();
+            if (rc != QFT_OK) {
+                finish(s, f.req, rc, 0.0);
+                pool_put(s, f.state, f.bytes);
+                s->free_slots.push_back(f.slot);
+                cudaEventDestroy(f.done);
+                s->cv_done.notify_all();
+                continue;
+            }
+            s->in_use += f.bytes;
+            s->stream_load[f.stream]++;
+            s->inflight.push_back(f);
+        }
+        if (s->stop && s->pending.empty() && s->inflight.empty()) break;
+        if (s->inflight.empty()) {
+            s->cv_work.wait_for(lock, std::chrono::milliseconds(2));
+        } else {
+            lock.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lock.lock();
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int qft_server_create(qft_server_t* out, size_t hbm_budget_bytes, int streams, int max_inflight) {
+    if (!out) return QFT_ERR_BAD_ARG;
+    *out = nullptr;
+    if (hbm_budget_bytes == 0 || streams < 0 || streams > 64 || max_inflight < 0 || max_inflight > 4096)
+        return QFT_ERR_BAD_ARG;
+    qft_server_s* s = new (std::nothrow) qft_server_s();
+    if (!s) return QFT_ERR_NOMEM;
+    s->budget = hbm_budget_bytes;
+    if (streams) s->nstreams = streams;
+    if (max_inflight) s->max_inflight = max_inflight;
+    if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return QFT_ERR_CUDA; }
+    for (int i = 0; i < s->nstreams; ++i) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (auto x : s->streams) cudaStreamDestroy(x);
+            delete s;
+            return QFT_ERR_CUDA;
+        }
+        s->streams.push_back(st);
+    }
+    s->stream_load.assign(s->nstreams, 0);
+    if (cudaMallocHost(&s->slots, 2 * sizeof(double) * s->max_inflight) != cudaSuccess) {
+        for (auto x : s->streams) cudaStreamDestroy(x);
+        delete s;
+        return QFT_ERR_NOMEM;
+    }
+    for (int i = s->max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->worker = std::thread(worker_loop, s);
+    *out = s;
+    return QFT_OK;
+}
+
+int qft_server_submit(qft_server_t s, const qft_request* req, uint64_t* ticket) {
+    if (!s || !req || !ticket || !req->input || !req->output) return QFT_ERR_BAD_ARG;
+    if (req->dtype != QFT_C64 && req->dtype != QFT_C128) return QFT_ERR_BAD_ARG;
+    if (req->direction != QFT_FORWARD && req->direction != QFT_INVERSE) return QFT_ERR_BAD_ARG;
+    if (req->n < 1 || req->n > (req->dtype == QFT_C64 ? 34 : 33)) return QFT_ERR_BAD_ARG;
+    if (req->scale_mode < QFT_SCALE_STATE || req->scale_mode > QFT_SCALE_INV_N) return QFT_ERR_BAD_ARG;
+    Request r;
+    r.r = *req;
+    r.t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->stop) return QFT_ERR_STATE;
+        r.ticket = s->next_ticket++;
+        s->results[r.ticket] = Result{};
+        s->pending.push_back(r);
+    }
+    s->cv_work.notify_one();
+    *ticket = r.ticket;
+    return QFT_OK;
+}
+
+int qft_server_poll(qft_server_t s, uint64_t ticket, int* done) {
+    if (!s || !done) return QFT_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) return QFT_ERR_STATE;
+    *done = it->second.status != 1;
+    return it->second.status == 1 ? QFT_OK : it->second.status;
+}
+
+int qft_server_wait(qft_server_t s, uint64_t ticket, int timeout_ms, double* latency_ms) {
+    if (!s) return QFT_ERR_BAD_ARG;
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) return QFT_ERR_STATE;
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (s->results[ticket].status == 1) {
+        if (timeout_ms >= 0 && s->cv_done.wait_until(lock, deadline) == std::cv_status::timeout &&
+            s->results[ticket].status == 1)
+            return QFT_ERR_TIMEOUT;
+        if (timeout_ms < 0) s->cv_done.wait_for(lock, std::chrono::milliseconds(10));
+    }
+    const Result res = s->results[ticket];
+    if (latency_ms) *latency_ms = res.latency_ms;
+    s->results.erase(ticket);
+    return res.status;
+}
+
+int qft_server_get_stats(qft_server_t s, qft_server_stats* out) {
+    if (!s || !out) return QFT_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->completed = static_cast<long long>(s->completed);
+    out->failed = static_cast<long long>(s->failed);
+    out->pending = static_cast<long long>(s->pending.size());
+    out->in_flight = static_cast<long long>(s->inflight.size());
+    out->bytes_in_use = s->in_use;
+    out->bytes_pooled = s->pooled;
+    if (!s->latencies.empty()) {
+        std::vector<double> v = s->latencies;
+        auto pct = [&](double p) {
+            const size_t i = std::min(v.size() - 1, static_cast<size_t>(p * (v.size() - 1) + 0.5));
+            std::nth_element(v.begin(), v.begin() + i, v.end());
+            return v[i];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        out->max_ms = *std::max_element(s->latencies.begin(), s->latencies.end());
+        const double span = std::chrono::duration<double>(s->t_last - s->t_first).count();
+        out->requests_per_s = span > 0 ? static_cast<double>(s->completed) / span : 0.0;
+    }
+    return QFT_OK;
+}
+
+int qft_server_reset_stats(qft_server_t s) {
+    if (!s) return QFT_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->latencies.clear();
+    s->completed = 0;
+    s->failed = 0;
+    return QFT_OK;
+}
+
+int qft_server_destroy(qft_server_t s) {
+    if (!s) return QFT_ERR_BAD_ARG;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (auto& kv : s->pool) cudaFree(kv.second);
+    for (auto& kv : s->plans) qft_plan_destroy(kv.second);
+    for (auto st : s->streams) cudaStreamDestroy(st);
+    cudaFreeHost(s->slots);
+    delete s;
+    return QFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+"""The serving loop on the GPU: mixed requests, each result equal to the same
+request run alone (qft_execute with the same plan), budget refusal, stats."""
+import numpy as np
+import pytest
+
+import qft_inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+q = pytest.importorskip("paper_2606_18981_gb300")
+
+TOL = {"c64": lambda n: 2e-6, "c128": lambda n: 1e-13 * n}
+
+
+def rel(a, b):
+    a = a.to(torch.complex128)
+    b = b.to(torch.complex128)
+    return float(torch.linalg.vector_norm(a - b) / max(torch.linalg.vector_norm(b), 1e-300))
+
+
+def alone(x, n, k, direction, dt, order, mode):
+    p = q.Plan(n, k, direction, dt, order)
+    st = x.clone().cuda()
+    ws = p.alloc_workspace()
+    p.execute(st, ws, mode)
+    torch.cuda.synchronize()
+    return st, p.scale_in(ws)
+
+
+def test_results_alone_equal_results_in_the_mix():
+    rng = np.random.default_rng(5)
+    srv = q.Server(8 << 30, streams=6, max_inflight=24)
+    reqs = []
+    for i in range(60):
+        n = int(rng.integers(6, 23))
+        k = int(rng.choice([-1, 4, 8, 16]))
+        direction = int(rng.choice([-1, 1]))
+        dt = "c64" if i % 3 else "c128"
+        order = int(i % 5 == 0)
+        mode = int(rng.integers(0, 4))
+        td = torch.complex64 if dt == "c64" else torch.complex128
+        x = torch.from_numpy(qft_inputs.make(qft_inputs.KINDS[i % 3], n, 77 + i)).to(td)
+        on_dev = i % 2 == 0
+        xin = x.cuda() if on_dev else x.pin_memory()
+        out = torch.empty(1 << n, dtype=td, device="cuda") if on_dev else torch.empty(1 << n, dtype=td).pin_memory()
+        t = srv.submit(xin, out, n, k, direction, dt, order, mode)
+        reqs.append((t, x, out, n, k, direction, dt, order, mode))
+    for t, x, out, n, k, direction, dt, order, mode in reqs:
+        rc, lat, scale = srv.wait(t, 60000)
+        assert rc == 0 and lat > 0
+        ref, s_ref = alone(x, n, k, direction, dt, order, mode)
+        assert rel(out.cuda(), ref) <= TOL[dt](n)
+        assert abs(scale - s_ref) <= 1e-9 * max(s_ref, 1e-300)
+    st = srv.stats()
+    assert st.completed == 60 and st.failed == 0 and st.p99_ms >= st.p50_ms > 0
+    assert st.bytes_in_use == 0
+    srv.close()
+
+
+def test_budget_refusal_and_small_budget_progress():
+    srv = q.Server(1 << 20, streams=2)  # 1 MiB: n = 16 (512 KiB state + workspace) fits, n = 18 does not
+    x = torch.zeros(1 << 18, dtype=torch.complex64, device="cuda")
+    out = torch.empty_like(x)
+    t = srv.submit(x, out, 18)
+    rc, _, _ = srv.wait(t, 10000)
+    assert rc == q.ERR_BUDGET
+    xs = [torch.randn(1 << 15, dtype=torch.complex64, device="cuda") for _ in range(8)]
+    outs = [torch.empty_like(v) for v in xs]
+    ts = [srv.submit(v, o, 15) for v, o in zip(xs, outs)]  # only one fits at a time
+    for t, v, o in zip(ts, xs, outs):
+        rc, _, _ = srv.wait(t, 20000)
+        assert rc == 0
+        ref, _ = alone(v, 15, -1, -1, "c64", 0, 0)
+        assert rel(o, ref) <= 2e-6
+    srv.close()
