@@ -320,6 +320,60 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
     return out
 
 
+def serving_workload(q, torch, dev, rates=(1000, 5000, 10000, 20000, 50000), per_rate=300, seed=5):
+    """The serving configuration: Poisson arrivals at each rate, n with
+    P(n) proportional to 1/n over 10..28, dtype uniform in {complex64,
+    complex128}, k uniform in {exact, 4, 8, 16}, direction uniform; inputs
+    and outputs resident on the device; HBM admission budget 120 GB."""
+    import numpy as np
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = np.arange(10, 29)
+    pn = (1.0 / ns) / np.sum(1.0 / ns)
+    inputs, outputs = {}, {}
+    for n in ns:
+        for dt in ("c64", "c128"):
+            td = torch.complex64 if dt == "c64" else torch.complex128
+            inputs[(int(n), dt)] = torch.randn(1 << int(n), dtype=td, device=dev)
+            outputs[(int(n), dt)] = torch.empty(1 << int(n), dtype=td, device=dev)
+    srv = q.Server(120 * 10**9, streams=8, max_inflight=64)
+    # warm the plan cache and buffer pool
+    for n in ns:
+        for dt in ("c64", "c128"):
+            t = srv.submit(inputs[(int(n), dt)], outputs[(int(n), dt)], int(n), -1, q.FORWARD, dt)
+            srv.wait(t)
+    res = {}
+    for rate in rates:
+        srv.reset_stats()
+        gaps = rng.exponential(1.0 / rate, per_rate)
+        t0 = time.perf_counter()
+        due = t0
+        tickets = []
+        for i in range(per_rate):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                pass
+            n = int(rng.choice(ns, p=pn))
+            dt = ("c64", "c128")[int(rng.integers(0, 2))]
+            k = int(rng.choice([-1, 4, 8, 16]))
+            direction = (q.FORWARD, q.INVERSE)[int(rng.integers(0, 2))]
+            tickets.append(srv.submit(inputs[(n, dt)], outputs[(n, dt)], n, k, direction, dt))
+        bad = 0
+        for t in tickets:
+            rc, _, _ = srv.wait(t)
+            bad += rc != 0
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        res[f"{rate}_req_per_s"] = {"offered_req_per_s": rate, "requests": per_rate, "failed": bad,
+                                    "served_req_per_s": per_rate / wall, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+                                    "max_ms": st.max_ms}
+    srv.close()
+    del inputs, outputs
+    torch.cuda.empty_cache()
+    res["n_distribution"] = "P(n) proportional to 1/n for n = 10..28"
+    return res
+
+
 def timed_transform(q, torch, plan, state, ws, stream, steps, warmup):
     """Device-timed steps on resident data; returns (ms/step, [mean ms per pass])."""
     P = plan.info().passes
@@ -447,6 +501,10 @@ def run_ours(args, world, rank, local):
             extra["batched_4096_n8to18_c64"] = batched_workload(q, torch, dev, stream)
         except Exception as ex:
             extra["batched_4096_n8to18_c64"] = {"error": str(ex)[:300]}
+        try:
+            extra["serving_poisson"] = serving_workload(q, torch, dev)
+        except Exception as ex:
+            extra["serving_poisson"] = {"error": str(ex)[:300]}
         for name, (nn, ddt, kk) in {"aqft_k4_c64_n30": (30, "c64", 4), "plain_c128_n30": (30, "c128", -1),
                                      "c64_n26": (26, "c64", -1), "c64_n33": (33, "c64", -1)}.items():
             try:
