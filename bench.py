@@ -285,14 +285,15 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         batch.execute(stream=stream)
-    g.replay()
-    torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     bb = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
+    with torch.cuda.stream(stream):  # replay() launches on the current stream
         g.replay()
-    bb.record(stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            g.replay()
+        bb.record(stream)
     torch.cuda.synchronize()
     status = batch.status(stream)
     ms = a.elapsed_time(bb) / reps
