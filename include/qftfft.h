@@ -94,8 +94,16 @@ typedef struct {
                                  kernel's bounded wait expires and reports QFT_ERR_TIMEOUT  */
     int threads;        /* CTA size of the pass kernel: 256 (stages <= 5 wires) or 512
                            (stages <= 4 wires); 0 = default                                 */
-    int reserved[1];
+    int precision;      /* QFT_PREC_*: 0 = CUDA cores in the dtype's own precision; otherwise
+                           complex64 only, each pass's fused block of <= 6 wires as a dense
+                           complex GEMM on the tensor cores (see enum qft_precision)        */
 } qft_opts;
+
+/* Precision tier (complex64 plans): the block matrix and the data are rounded to
+ * the operand format, products accumulate in FP32.  The x3 tiers split each
+ * operand into hi + lo and add hi*hi + lo*hi + hi*lo. */
+enum qft_precision { QFT_PREC_NATIVE = 0, QFT_PREC_TF32 = 1, QFT_PREC_BF16 = 2, QFT_PREC_BF16X3 = 3,
+                     QFT_PREC_FP16 = 4, QFT_PREC_FP16X3 = 5 };
 
 /* What the planner built (Sec. 3.1: the plan is defined by the qubit count,
  * the fused blocks and the pre-fusion gate counters). */

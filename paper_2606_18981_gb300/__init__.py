@@ -24,6 +24,7 @@ C64, C128 = 0, 1
 FORWARD, INVERSE = -1, +1
 SCALE_STATE, SCALE_UNITARY, SCALE_UNNORM, SCALE_INV_N = 0, 1, 2, 3
 ORDER_NATURAL, ORDER_BITREV = 0, 1
+PREC_NATIVE, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_FP16, PREC_FP16X3 = 0, 1, 2, 3, 4, 5
 OK, ERR_BAD_ARG, ERR_SIZE, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED, ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 
@@ -57,7 +58,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("tile_bits", ctypes.c_int), ("coalesce_bits", ctypes.c_int),
                 ("max_stage_bits", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
                 ("test_skip_first_load", ctypes.c_int), ("threads", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("precision", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -150,12 +151,13 @@ class Plan:
 
     def __init__(self, n: int, k: int = -1, direction: int = FORWARD, dtype="c64", order: int = ORDER_NATURAL,
                  tile_bits: int = 0, coalesce_bits: int = 0, max_stage_bits: int = 0,
-                 wait_limit_ms: int = 0, test_skip_first_load: int = 0, threads: int = 0):
+                 wait_limit_ms: int = 0, test_skip_first_load: int = 0, threads: int = 0, precision: int = 0):
         self._h = _vp()
         self.n, self.k, self.direction = int(n), int(k), int(direction)
         self.dtype = _dtype_code(dtype)
         self.order = int(order)
-        opts = Opts(order, tile_bits, coalesce_bits, max_stage_bits, wait_limit_ms, test_skip_first_load, threads)
+        opts = Opts(order, tile_bits, coalesce_bits, max_stage_bits, wait_limit_ms, test_skip_first_load, threads,
+                    precision)
         _check(_lib.qft_plan_create(ctypes.byref(self._h), self.n, self.k, self.direction, self.dtype,
                                     ctypes.byref(opts)), "qft_plan_create")
 

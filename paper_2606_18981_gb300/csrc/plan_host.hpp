@@ -15,6 +15,10 @@ namespace qft {
 cudaError_t launch_pass(int dtype, int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid,
                         size_t smem, cudaStream_t stream);
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes);
+cudaError_t launch_tc_pass(int dir, int prec, const CUtensorMap& map, const PassParams& P, const void* a_hi,
+                           const void* a_lo, int kpad, int ncols, int grid, size_t smem, cudaStream_t st);
+size_t tc_smem_bytes(const PassParams& P, int prec, int kpad, int ncols);
+cudaError_t tc_prepare_a(int prec, const double* d_src, void* d_hi, void* d_lo, int kpad, cudaStream_t st);
 
 // Workspace layout of one transform: [0, 4096) metadata (scale_in at 0,
 // status word at 8, norm partial sums from 64); the ping-pong state buffer
@@ -36,6 +40,10 @@ struct PassHost {
     cuuint32_t box[5];
     int wires = 0;
     int run_bits = 0;  // low input address bits inside the tile (log2 amplitudes per HBM run)
+    // tensor-core tier: the pass's block matrix in operand format (plan-owned device memory)
+    void* tc_a_hi = nullptr;
+    void* tc_a_lo = nullptr;
+    int tc_kpad = 0, tc_ncols = 0;
 };
 
 int set_cuda_error(cudaError_t e);           // records e for qft_last_cuda_error, returns QFT_ERR_CUDA
@@ -45,6 +53,13 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn();
 }  // namespace qft
 
 struct qft_plan_s {
+    ~qft_plan_s() {
+        for (auto& ph : passes) {
+            if (ph.tc_a_hi) cudaFree(ph.tc_a_hi);
+            if (ph.tc_a_lo) cudaFree(ph.tc_a_lo);
+        }
+    }
+    int precision = 0;  // QFT_PREC_*
     int n = 0, k = -1, kk = 0, dir = -1, dtype = 0, order = 0;
     size_t esize = 8;
     int TB = 13, cmin = 2, rmax = 4;

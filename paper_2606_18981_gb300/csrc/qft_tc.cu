@@ -1,0 +1,402 @@
+// qft_tc.cu -- the precision tier: a pass whose fused block of r <= 6 wires is
+// applied as a dense complex GEMM on the 5th-generation tensor cores.
+//
+// Within one block the circuit is a fixed 2^r x 2^r unitary F (the block's
+// Hadamards and controlled phases, Sec. 2 / Fig. 1) applied to every column of
+// 2^r amplitudes after that column's cross twiddle (the controlled phases from
+// wires above the block, Eq. 5).  The planner builds F in FP64 on the host,
+// embeds it as the real matrix [[Re F, -Im F], [Im F, Re F]] (2^{r+1} square,
+// padded to M = 128 rows) and rounds it to the tier's operand format, split
+// into hi + lo parts for the x3 tiers.  Per tile the kernel
+//   1. loads the tile by TMA (as the CUDA-core pass kernel does),
+//   2. applies the cross twiddles in FP32 on the CUDA cores, scales each column
+//      by a power of two (its largest component near 2^14, so FP16 neither
+//      overflows nor loses the low part to subnormals), and writes the column as
+//      [Re; Im] into the B operand in shared memory (hi and lo parts),
+//   3. issues tcgen05.mma (one elected thread; D = 128 x N FP32 in tensor
+//      memory; hi*hi + lo*hi + hi*lo for the split tiers),
+//   4. reads D back with tcgen05.ld, undoes the column scale, applies the output
+//      scale and stores through the pass's output address map.
+// Operand layout: K-major, no swizzle, 8-row x 16-byte core matrices, the K
+// neighbour of a core matrix 128 bytes further (leading byte offset) and the
+// next group of 8 rows K/kc * 128 bytes further (stride byte offset).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plan.hpp"
+#include "qft_device.cuh"
+
+namespace qft {
+
+// precision tiers (qft_opts.precision)
+enum TcPrec { TC_TF32 = 1, TC_BF16 = 2, TC_BF16X3 = 3, TC_FP16 = 4, TC_FP16X3 = 5 };
+
+template <int PREC> struct TcOp;
+template <> struct TcOp<TC_TF32> { static constexpr int bytes = 4, kind = 2, fmt = 2, split = 0; };
+template <> struct TcOp<TC_BF16> { static constexpr int bytes = 2, kind = 1, fmt = 1, split = 0; };
+template <> struct TcOp<TC_BF16X3> { static constexpr int bytes = 2, kind = 1, fmt = 1, split = 1; };
+template <> struct TcOp<TC_FP16> { static constexpr int bytes = 2, kind = 1, fmt = 0, split = 0; };
+template <> struct TcOp<TC_FP16X3> { static constexpr int bytes = 2, kind = 1, fmt = 0, split = 1; };
+
+// Round x to the operand format; hi = rounded value (stored), returns it as float.
+template <int PREC>
+__device__ __forceinline__ float store_op(void* dst, float x) {
+    if constexpr (PREC == TC_TF32) {
+        uint32_t t;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+        *static_cast<uint32_t*>(dst) = t;
+        return __uint_as_float(t);
+    } else if constexpr (PREC == TC_BF16 || PREC == TC_BF16X3) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        *static_cast<__nv_bfloat16*>(dst) = h;
+        return __bfloat162float(h);
+    } else {
+        const __half h = __float2half_rn(x);
+        *static_cast<__half*>(dst) = h;
+        return __half2float(h);
+    }
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32;
+    d |= static_cast<uint64_t>(1) << 46;  // descriptor version; base offset 0; no swizzle
+    return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    if constexpr (KIND == 2)
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+                     "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    else
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+                     "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Byte offset of element (row, k) in a K-major no-swizzle operand with kpad columns.
+template <int EB>
+__device__ __forceinline__ uint32_t op_offset(int row, int k, int kpad) {
+    constexpr int kc = 16 / EB;
+    return static_cast<uint32_t>((row >> 3) * (kpad / kc) * 128 + (k / kc) * 128 + (row & 7) * 16 + (k % kc) * EB);
+}
+
+struct TcParams {
+    const void* a_hi;  // 128 x kpad operand (already in the shared-memory layout), hi part
+    const void* a_lo;  // lo part (x3 tiers)
+    int32_t kpad;      // K of the GEMM (2^{r+1} rounded up to the MMA K step)
+    int32_t ncols;     // N of the GEMM: columns per tile rounded up to a multiple of 16
+};
+
+constexpr int kTcThreads = 128;
+
+template <int DIR, int PREC>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    qft_tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassParams P,
+                       const __grid_constant__ TcParams Q) {
+    using V = float2;
+    using Op = TcOp<PREC>;
+    constexpr int EB = Op::bytes;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar_load, mbar_mma;
+    __shared__ uint32_t s_taddr;
+    __shared__ double red[kTcThreads / 32];
+    __shared__ __align__(16) V Ubuf[kMaxR * kMaxStages];
+
+    const int tid = threadIdx.x;
+    const StageDesc& S = P.st[0];
+    const int r = S.r;
+    const int J = 1 << r;
+    const int ng = 1 << S.ngbits;  // columns (groups) of the tile
+    const int kpad = Q.kpad, ncols = Q.ncols;
+    const uint32_t tile_elems = 1u << P.tb;
+    const uint32_t tile_bytes = tile_elems * 8u;
+    const size_t a_bytes = static_cast<size_t>(128) * kpad * EB;
+    const size_t b_bytes = static_cast<size_t>(ncols) * kpad * EB;
+    const uint32_t d_bytes = static_cast<uint32_t>(2 * J) * static_cast<uint32_t>(ncols) * 4u;
+    unsigned char* Tb = smem_raw;  // tile, later the D staging area (rows < 2^{r+1})
+    unsigned char* A_hi = Tb + (tile_bytes > d_bytes ? tile_bytes : d_bytes);
+    unsigned char* A_lo = A_hi + a_bytes;
+    unsigned char* B_hi = A_lo + (Op::split ? a_bytes : 0);
+    unsigned char* B_lo = B_hi + b_bytes;
+    unsigned char* tab_raw = B_lo + (Op::split ? b_bytes : 0);
+    int* col_exp = reinterpret_cast<int*>(tab_raw);
+    tab_raw += 4 * 256;
+    GroupTab<V> tab;
+    tab.ntab = P.ntab;
+    tab.tw = reinterpret_cast<V*>(tab_raw);
+    tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * sizeof(V) * static_cast<size_t>(P.ntab));
+    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * sizeof(V) + 8) * static_cast<size_t>(P.ntab));
+    V* T = reinterpret_cast<V*>(Tb);
+    float* D = reinterpret_cast<float*>(Tb);
+
+    build_group_tables<float, DIR, kTcThreads>(P, tab);
+    // the fixed block matrix (hi, lo) into shared memory
+    {
+        const uint4* src = static_cast<const uint4*>(Q.a_hi);
+        uint4* dst = reinterpret_cast<uint4*>(A_hi);
+        for (size_t i = tid; i < a_bytes / 16; i += kTcThreads) dst[i] = src[i];
+        if (Op::split) {
+            src = static_cast<const uint4*>(Q.a_lo);
+            dst = reinterpret_cast<uint4*>(A_lo);
+            for (size_t i = tid; i < a_bytes / 16; i += kTcThreads) dst[i] = src[i];
+        }
+        // zero B once: padding columns (>= ng) stay zero, the others are rewritten per tile
+        for (size_t i = tid; i < b_bytes / 16; i += kTcThreads) {
+            reinterpret_cast<uint4*>(B_hi)[i] = make_uint4(0, 0, 0, 0);
+            if (Op::split) reinterpret_cast<uint4*>(B_lo)[i] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    uint32_t tcols = 32;
+    while (tcols < static_cast<uint32_t>(ncols)) tcols <<= 1;
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                     "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar_load, 1);
+        mbar_init(&mbar_mma, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+
+    float scale = 1.f;
+    if (P.last && !P.first) {
+        double s = 0.0;
+        for (int i = tid; i < P.npartials; i += kTcThreads) s += P.partials[i];
+        const double scale_in = sqrt(block_sum<kTcThreads>(s, red));
+        scale = static_cast<float>(output_factor(P, scale_in));
+        if (blockIdx.x == 0 && tid == 0) {
+            P.meta[0] = scale_in;
+            if (P.user_scale) *P.user_scale = scale_in;
+        }
+    }
+    const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(Op::fmt) << 7) | (static_cast<uint32_t>(Op::fmt) << 10) |
+                           (static_cast<uint32_t>(ncols >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+    const uint32_t lbo = 128u, sbo = static_cast<uint32_t>(kpad / (16 / EB)) * 128u;
+    const int kstep = 32 / EB;
+    const uint32_t koff_step = static_cast<uint32_t>(kstep / (16 / EB)) * 128u;
+
+    double norm_acc = 0.0;
+    uint32_t ph_load = 0, ph_mma = 0;
+    bool aborted = false;
+    for (int64_t tile = blockIdx.x; tile < P.num_tiles; tile += gridDim.x) {
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            issue_tile_load(P, &tmap, tile, Tb, &mbar_load, tile_bytes);
+        }
+        compute_tile_twiddles<float, DIR>(P, tile, Ubuf);
+        uint64_t I_tile;
+        int64_t out_tile;
+        tile_coords(P, tile, I_tile, out_tile);
+        const bool ok = mbar_wait_bounded(&mbar_load, ph_load, P.wait_limit_ns);
+        ph_load ^= 1u;
+        if (__syncthreads_or(!ok)) { aborted = true; break; }
+        if (P.first && P.last) {
+            double s = 0.0;
+            for (uint32_t i = tid; i < tile_elems; i += kTcThreads) {
+                const V a = T[i];
+                s += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
+            }
+            const double scale_in = sqrt(block_sum<kTcThreads>(s, red));
+            scale = static_cast<float>(output_factor(P, scale_in));
+            if (tid == 0) {
+                P.meta[0] = scale_in;
+                if (P.user_scale) *P.user_scale = scale_in;
+            }
+        }
+        // 2. columns: cross twiddle, column scale, [Re; Im] into B (hi / lo)
+        for (int g = tid; g < ng; g += kTcThreads) {
+            const int lo5 = P.tab_off[0] + (g & 31), hi5 = P.tab_off[0] + 32 + (g >> 5);
+            const uint32_t pb = tab.pb[lo5] | tab.pb[hi5];
+            V tau[6];
+            for (int e = 0; e < r; ++e) {
+                if (S.cross) {
+                    V t = cmul(tab.tw[e * tab.ntab + lo5], tab.tw[e * tab.ntab + hi5]);
+                    if (S.tile_above) t = cmul(t, Ubuf[S.uoff + e]);
+                    tau[e] = t;
+                } else {
+                    tau[e] = make_float2(1.f, 0.f);
+                }
+            }
+            float amax = 0.f;
+            for (int j = 0; j < J; ++j) {
+                V x = T[pb + (static_cast<uint32_t>(j) << S.q)];
+                if (P.first && !P.last) norm_acc += static_cast<double>(x.x) * x.x + static_cast<double>(x.y) * x.y;
+                for (int e = 0; e < r; ++e)
+                    if (j & (1 << e)) x = cmul(x, tau[e]);
+                T[pb + (static_cast<uint32_t>(j) << S.q)] = x;
+                amax = fmaxf(amax, fmaxf(fabsf(x.x), fabsf(x.y)));
+            }
+            const int ex = amax > 0.f ? 14 - ilogbf(amax) : 0;
+            col_exp[g] = ex;
+            for (int j = 0; j < J; ++j) {
+                const V x = T[pb + (static_cast<uint32_t>(j) << S.q)];
+                const float re = ldexpf(x.x, ex), im = ldexpf(x.y, ex);
+                const float hre = store_op<PREC>(B_hi + op_offset<EB>(g, j, kpad), re);
+                const float him = store_op<PREC>(B_hi + op_offset<EB>(g, J + j, kpad), im);
+                if (Op::split) {
+                    store_op<PREC>(B_lo + op_offset<EB>(g, j, kpad), re - hre);
+                    store_op<PREC>(B_lo + op_offset<EB>(g, J + j, kpad), im - him);
+                }
+            }
+            for (int k = 2 * J; k < kpad; ++k) {  // K padding
+                store_op<PREC>(B_hi + op_offset<EB>(g, k, kpad), 0.f);
+                if (Op::split) store_op<PREC>(B_lo + op_offset<EB>(g, k, kpad), 0.f);
+            }
+        }
+        fence_proxy_async_smem();  // B written by threads, read by the tensor cores
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // 3. the GEMM
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(A_hi), a1 = smem_u32(A_lo), b0 = smem_u32(B_hi), b1 = smem_u32(B_lo);
+            uint32_t acc = 0;
+            for (int kb = 0; kb < kpad / kstep; ++kb) {
+                const uint32_t ko = static_cast<uint32_t>(kb) * koff_step;
+                umma<Op::kind>(taddr, umma_desc(a0 + ko, lbo, sbo), umma_desc(b0 + ko, lbo, sbo), idesc, acc);
+                acc = 1;
+                if (Op::split) {
+                    umma<Op::kind>(taddr, umma_desc(a1 + ko, lbo, sbo), umma_desc(b0 + ko, lbo, sbo), idesc, 1);
+                    umma<Op::kind>(taddr, umma_desc(a0 + ko, lbo, sbo), umma_desc(b1 + ko, lbo, sbo), idesc, 1);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar_mma)));
+        }
+        const bool okm = mbar_wait_bounded(&mbar_mma, ph_mma, P.wait_limit_ns);
+        ph_mma ^= 1u;
+        if (__syncthreads_or(!okm)) { aborted = true; break; }
+        tc_fence_after();
+        // 4. D (128 rows x ncols) from tensor memory to shared memory, row m = lane
+        {
+            const int w = tid >> 5, l = tid & 31;
+            const int m = w * 32 + l;
+            for (int c = 0; c < ncols; c += 16) {
+                uint32_t v[16];
+                const uint32_t a = taddr + (static_cast<uint32_t>(w * 32) << 16) + static_cast<uint32_t>(c);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(a));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (m < 2 * J)
+                    for (int j = 0; j < 16; ++j) D[m * ncols + c + j] = __uint_as_float(v[j]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        // 5. store: output j of column g is (D[j][g], D[J + j][g]) / 2^ex * scale
+        {
+            V* __restrict__ out = static_cast<V*>(P.out);
+            for (int idx = tid; idx < ng * J; idx += kTcThreads) {
+                const int g = idx % ng, j = idx / ng;
+                const int lo5 = P.tab_off[0] + (g & 31), hi5 = P.tab_off[0] + 32 + (g >> 5);
+                int64_t o = out_tile + tab.ob[lo5] + tab.ob[hi5];
+                for (int e = 0; e < r; ++e)
+                    if (j & (1 << e)) o += int64_t(1) << P.p_out[S.q + e];
+                const float f = ldexpf(scale, -col_exp[g]);
+                out[o] = make_float2(D[j * ncols + g] * f, D[(J + j) * ncols + g] * f);
+            }
+        }
+        __syncthreads();
+    }
+    if (aborted && tid == 0) atomicExch(P.status, -5);
+    if (!aborted && P.first && !P.last) {
+        const double tot = block_sum<kTcThreads>(norm_acc, red);
+        if (tid == 0) P.partials[blockIdx.x] = tot;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(tcols));
+}
+
+size_t tc_smem_bytes(const PassParams& P, int prec, int kpad, int ncols) {
+    const int eb = prec == TC_TF32 ? 4 : 2;
+    const bool split = prec == TC_BF16X3 || prec == TC_FP16X3;
+    const size_t tile = (size_t(1) << P.tb) * 8;
+    const size_t dst = size_t(2) * (size_t(1) << P.st[0].r) * ncols * 4;
+    const size_t stage = tile > dst ? tile : dst;
+    const size_t a = size_t(128) * kpad * eb * (split ? 2 : 1);
+    const size_t b = size_t(ncols) * kpad * eb * (split ? 2 : 1);
+    return stage + a + b + 4 * 256 + size_t(P.ntab) * (kMaxR * 8 + 8 + 4);
+}
+
+template <int DIR, int PREC>
+static cudaError_t launch_tc_t(const CUtensorMap& map, const PassParams& P, const TcParams& Q, int grid, size_t smem,
+                               cudaStream_t st) {
+    auto kern = qft_tc_pass_kernel<DIR, PREC>;
+    static thread_local size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    kern<<<grid, kTcThreads, smem, st>>>(map, P, Q);
+    return cudaGetLastError();
+}
+
+template <int DIR>
+static cudaError_t launch_tc_dir(int prec, const CUtensorMap& map, const PassParams& P, const TcParams& Q, int grid,
+                                 size_t smem, cudaStream_t st) {
+    switch (prec) {
+        case TC_TF32: return launch_tc_t<DIR, TC_TF32>(map, P, Q, grid, smem, st);
+        case TC_BF16: return launch_tc_t<DIR, TC_BF16>(map, P, Q, grid, smem, st);
+        case TC_BF16X3: return launch_tc_t<DIR, TC_BF16X3>(map, P, Q, grid, smem, st);
+        case TC_FP16: return launch_tc_t<DIR, TC_FP16>(map, P, Q, grid, smem, st);
+        default: return launch_tc_t<DIR, TC_FP16X3>(map, P, Q, grid, smem, st);
+    }
+}
+
+cudaError_t launch_tc_pass(int dir, int prec, const CUtensorMap& map, const PassParams& P, const void* a_hi,
+                           const void* a_lo, int kpad, int ncols, int grid, size_t smem, cudaStream_t st) {
+    TcParams Q;
+    Q.a_hi = a_hi;
+    Q.a_lo = a_lo;
+    Q.kpad = kpad;
+    Q.ncols = ncols;
+    return dir < 0 ? launch_tc_dir<-1>(prec, map, P, Q, grid, smem, st) : launch_tc_dir<+1>(prec, map, P, Q, grid, smem, st);
+}
+
+// Round the FP64 real block matrix (128 x kpad, row-major) into the operand
+// format, split into hi and lo, in the shared-memory operand layout.
+template <int PREC>
+__global__ void tc_prepare_a_kernel(const double* src, unsigned char* hi, unsigned char* lo, int kpad) {
+    constexpr int EB = TcOp<PREC>::bytes;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 128 * kpad; i += gridDim.x * blockDim.x) {
+        const int row = i / kpad, k = i % kpad;
+        const double x = src[i];
+        const float h = store_op<PREC>(hi + op_offset<EB>(row, k, kpad), static_cast<float>(x));
+        store_op<PREC>(lo + op_offset<EB>(row, k, kpad), static_cast<float>(x - static_cast<double>(h)));
+    }
+}
+
+cudaError_t tc_prepare_a(int prec, const double* d_src, void* d_hi, void* d_lo, int kpad, cudaStream_t st) {
+    unsigned char* hi = static_cast<unsigned char*>(d_hi);
+    unsigned char* lo = static_cast<unsigned char*>(d_lo);
+    switch (prec) {
+        case TC_TF32: tc_prepare_a_kernel<TC_TF32><<<64, 256, 0, st>>>(d_src, hi, lo, kpad); break;
+        case TC_BF16: tc_prepare_a_kernel<TC_BF16><<<64, 256, 0, st>>>(d_src, hi, lo, kpad); break;
+        case TC_BF16X3: tc_prepare_a_kernel<TC_BF16X3><<<64, 256, 0, st>>>(d_src, hi, lo, kpad); break;
+        case TC_FP16: tc_prepare_a_kernel<TC_FP16><<<64, 256, 0, st>>>(d_src, hi, lo, kpad); break;
+        default: tc_prepare_a_kernel<TC_FP16X3><<<64, 256, 0, st>>>(d_src, hi, lo, kpad); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace qft

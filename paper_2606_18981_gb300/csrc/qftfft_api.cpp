@@ -283,7 +283,7 @@ int plan_passes(qft_plan_s* pl) {
     for (int w = 0; w < n; ++w) brev[w] = n - 1 - w;
     const bool natural = pl->order == QFT_ORDER_NATURAL;
 
-    if (n <= pl->TB) {
+    if (n <= (pl->precision ? pl->rmax : pl->TB)) {
         PassHost ph;
         if (!build_pass(pl, ph, 0, n, {}, ident, natural ? brev : ident, true, true)) return QFT_ERR_UNSUPPORTED;
         ph.prm.load_mode = 1;
@@ -366,6 +366,82 @@ int plan_passes(qft_plan_s* pl) {
     return QFT_OK;
 }
 
+// Tensor-core tier: for each pass (one block of r wires) build the block's
+// 2^r x 2^r unitary in FP64 by running its gates (unnormalised H on each wire
+// from the top, then the controlled phases of distance <= kk, Sec. 2 / Fig. 1)
+// on the basis vectors, embed it as the real matrix [[Re, -Im], [Im, Re]],
+// pad it to 128 x kpad, and round it on the device to the operand format (hi
+// and lo parts).  The matrices are plan-owned device memory.
+int prepare_tensor_passes(qft_plan_s* pl) {
+    const double two_pi = 6.283185307179586476925286766559;
+    for (auto& ph : pl->passes) {
+        const PassParams& P = ph.prm;
+        if (P.nstages != 1) return QFT_ERR_UNSUPPORTED;
+        const int r = P.st[0].r;
+        const int J = 1 << r;
+        const int kstep = pl->precision == QFT_PREC_TF32 ? 8 : 16;
+        const int kpad = std::max(kstep, (2 * J + kstep - 1) / kstep * kstep);
+        const int ng = 1 << P.st[0].ngbits;
+        const int ncols = std::max(16, (ng + 15) / 16 * 16);
+        if (ncols > 256 || 2 * J > 128) return QFT_ERR_UNSUPPORTED;
+        std::vector<double> Fre(size_t(J) * J), Fim(size_t(J) * J);
+        std::vector<double> vr(J), vi(J);
+        for (int ji = 0; ji < J; ++ji) {
+            std::fill(vr.begin(), vr.end(), 0.0);
+            std::fill(vi.begin(), vi.end(), 0.0);
+            vr[ji] = 1.0;
+            for (int t = r - 1; t >= 0; --t) {
+                const int bit = 1 << t;
+                for (int j = 0; j < J; ++j)
+                    if (!(j & bit)) {
+                        const double ar = vr[j], ai = vi[j], br = vr[j | bit], bi = vi[j | bit];
+                        vr[j] = ar + br; vi[j] = ai + bi;
+                        vr[j | bit] = ar - br; vi[j | bit] = ai - bi;
+                    }
+                const int lo = std::max(0, t - pl->kk);
+                const int mask = (bit - 1) & ~((1 << lo) - 1);
+                for (int j = 0; j < J; ++j)
+                    if (j & bit) {
+                        const double th = pl->dir * two_pi * static_cast<double>(j & mask) / static_cast<double>(2 * bit);
+                        const double c = std::cos(th), s = std::sin(th);
+                        const double xr = vr[j] * c - vi[j] * s;
+                        vi[j] = vr[j] * s + vi[j] * c;
+                        vr[j] = xr;
+                    }
+            }
+            for (int jo = 0; jo < J; ++jo) {
+                Fre[size_t(jo) * J + ji] = vr[jo];
+                Fim[size_t(jo) * J + ji] = vi[jo];
+            }
+        }
+        std::vector<double> A(size_t(128) * kpad, 0.0);
+        for (int jo = 0; jo < J; ++jo)
+            for (int ji = 0; ji < J; ++ji) {
+                const double fr = Fre[size_t(jo) * J + ji], fi = Fim[size_t(jo) * J + ji];
+                A[size_t(jo) * kpad + ji] = fr;
+                A[size_t(jo) * kpad + J + ji] = -fi;
+                A[size_t(J + jo) * kpad + ji] = fi;
+                A[size_t(J + jo) * kpad + J + ji] = fr;
+            }
+        const size_t eb = pl->precision == QFT_PREC_TF32 ? 4 : 2;
+        const size_t abytes = size_t(128) * kpad * eb;
+        double* d_src = nullptr;
+        cudaError_t e = cudaMalloc(&d_src, A.size() * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&ph.tc_a_hi, abytes);
+        if (e == cudaSuccess) e = cudaMalloc(&ph.tc_a_lo, abytes);
+        if (e == cudaSuccess) e = cudaMemcpy(d_src, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = tc_prepare_a(pl->precision, d_src, ph.tc_a_hi, ph.tc_a_lo, kpad, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(d_src);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        ph.tc_kpad = kpad;
+        ph.tc_ncols = ncols;
+        ph.smem = tc_smem_bytes(P, pl->precision, kpad, ncols);
+        if (ph.smem > 227 * 1024 - 4096) return QFT_ERR_UNSUPPORTED;
+    }
+    return QFT_OK;
+}
+
 int encode_maps(qft_plan_s* pl, const void* state, const void* work) {
     if (pl->map_state == state && pl->map_work == work && !pl->maps.empty()) return QFT_OK;
     auto fn = get_encode_fn();
@@ -431,7 +507,7 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
     pl->esize = dtype == QFT_C64 ? 8 : 16;
     pl->TB = dtype == QFT_C64 ? 13 : 12;
     pl->cmin = dtype == QFT_C64 ? 4 : 3;  // HBM runs of >= 128 bytes
-    pl->rmax = kMaxR;
+    pl->rmax = kMaxStageR;
     pl->threads = 256;
     if (opts) {
         if (opts->order != QFT_ORDER_NATURAL && opts->order != QFT_ORDER_BITREV) { delete pl; return QFT_ERR_BAD_ARG; }
@@ -446,6 +522,14 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
             if (opts->coalesce_bits < 1 || opts->coalesce_bits > 6) { delete pl; return QFT_ERR_BAD_ARG; }
             pl->cmin = opts->coalesce_bits;
         }
+        if (opts->precision < QFT_PREC_NATIVE || opts->precision > QFT_PREC_FP16X3) { delete pl; return QFT_ERR_BAD_ARG; }
+        if (opts->precision != QFT_PREC_NATIVE) {
+            if (dtype != QFT_C64) { delete pl; return QFT_ERR_UNSUPPORTED; }
+            pl->precision = opts->precision;
+            pl->TB = 12;   // 2^12-amplitude tiles: 64 columns of one 6-wire block
+            pl->cmin = 6;
+            pl->rmax = 6;  // one block per pass
+        }
         if (opts->wait_limit_ms < 0) { delete pl; return QFT_ERR_BAD_ARG; }
         if (opts->wait_limit_ms) pl->wait_limit_ns = uint64_t(opts->wait_limit_ms) * 1000000ull;
         pl->test_skip_first_load = opts->test_skip_first_load ? 1 : 0;
@@ -455,7 +539,7 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
             if (pl->threads == 512) pl->rmax = 4;
         }
         if (opts->max_stage_bits) {
-            if (opts->max_stage_bits < 1 || opts->max_stage_bits > (pl->threads == 512 ? 4 : kMaxR)) {
+            if (opts->max_stage_bits < 1 || opts->max_stage_bits > (pl->threads == 512 ? 4 : kMaxStageR)) {
                 delete pl;
                 return QFT_ERR_BAD_ARG;
             }
@@ -476,6 +560,7 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
     for (int t = n - 1; t >= 0; --t) pl->n_cp += std::min(pl->kk, t);
     pl->n_swap = n / 2;
     int rc = plan_passes(pl);
+    if (rc == QFT_OK && pl->precision) rc = prepare_tensor_passes(pl);
     if (rc != QFT_OK) {
         delete pl;
         return rc;
@@ -567,7 +652,11 @@ int execute_range(qft_plan_t pl, void* d_state, void* d_workspace, double* d_sca
         P.status = reinterpret_cast<int32_t*>(ws + kStatusOff);
         P.wait_limit_ns = pl->wait_limit_ns;
         P.test_skip_first_load = pl->test_skip_first_load;
-        e = launch_pass(pl->dtype, pl->dir, pl->threads, pl->maps[i], P, ph.grid, ph.smem, st);
+        if (pl->precision)
+            e = launch_tc_pass(pl->dir, pl->precision, pl->maps[i], P, ph.tc_a_hi, ph.tc_a_lo, ph.tc_kpad,
+                               ph.tc_ncols, ph.grid, ph.smem, st);
+        else
+            e = launch_pass(pl->dtype, pl->dir, pl->threads, pl->maps[i], P, ph.grid, ph.smem, st);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return QFT_OK;

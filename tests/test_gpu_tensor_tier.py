@@ -1,0 +1,64 @@
+"""Precision tier on the GPU: fused blocks as tcgen05 GEMMs, error vs the FP64 oracle.
+
+Bounds per tier (relative L2 against the oracle, n <= 24): the x3 split tiers
+keep ~22 (FP16) / ~16 (BF16) significant bits per operand, single tiers 11 /
+8 bits; each pass adds one rounding of the data and of the block matrix.
+"""
+import numpy as np
+import pytest
+
+import qft_inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+q = pytest.importorskip("paper_2606_18981_gb300")
+
+BOUND = {q.PREC_FP16X3: 2e-6, q.PREC_BF16X3: 1e-4, q.PREC_TF32: 5e-3, q.PREC_FP16: 5e-3, q.PREC_BF16: 4e-2}
+
+
+def run(x, n, k, prec, order=0, direction=-1, mode=0):
+    p = q.Plan(n, k, direction, "c64", order, precision=prec)
+    st = torch.from_numpy(x).to(torch.complex64).cuda()
+    ws = p.alloc_workspace()
+    p.execute(st, ws, mode)
+    out = st.cpu().numpy().astype(np.complex128)
+    assert p.status(ws) == 0
+    return out
+
+
+@pytest.mark.parametrize("prec", [q.PREC_FP16X3, q.PREC_BF16X3, q.PREC_TF32, q.PREC_FP16, q.PREC_BF16])
+@pytest.mark.parametrize("n,k", [(6, -1), (11, -1), (14, 4), (20, -1), (24, 8)])
+def test_tier_error_vs_oracle(oracle_mod, prec, n, k):
+    x = qft_inputs.gaussian(n, seed=n).astype(np.complex64).astype(np.complex128)
+    got = run(x, n, k, prec)
+    ref, _ = oracle_mod.qft(x, k, -1, 0, True)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"tier {prec} n={n} k={k}: rel L2 {err:.3e}")
+    assert err <= BOUND[prec]
+
+
+@pytest.mark.parametrize("order,direction,mode", [(1, -1, 0), (0, 1, 2), (0, -1, 1)])
+def test_tier_orders_directions_scales(oracle_mod, order, direction, mode):
+    n = 16
+    x = qft_inputs.tones(n, seed=4).astype(np.complex64).astype(np.complex128)
+    got = run(x, n, -1, q.PREC_FP16X3, order, direction, mode)
+    ref, _ = oracle_mod.qft(x, -1, direction, mode, order == 0)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= BOUND[q.PREC_FP16X3]
+
+
+def test_tier_index_maps_bit_exact():
+    """k = 0, small integers: every product and sum is exact in FP16 / FP32, so the
+    tier reproduces the integer Walsh-Hadamard transform with the qubit reversal."""
+    n = 14
+    rng = np.random.default_rng(1)
+    xi = (rng.integers(-3, 4, size=1 << n) + 1j * rng.integers(-3, 4, size=1 << n)).astype(np.complex128)
+    w = xi.copy()
+    h = 1
+    while h < w.size:
+        w = w.reshape(-1, 2, h)
+        w = np.stack([w[:, 0] + w[:, 1], w[:, 0] - w[:, 1]], axis=1).reshape(-1)
+        h *= 2
+    rev = np.array([int(format(i, f"0{n}b")[::-1], 2) for i in range(1 << n)])
+    got = run(xi, n, 0, q.PREC_FP16X3, 0, -1, q.SCALE_UNNORM)
+    assert np.array_equal(got, w[rev])

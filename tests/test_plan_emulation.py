@@ -59,6 +59,27 @@ def test_structure_all_sizes(dt, order):
                     assert P["run_bits"] >= (2 if dt == "c64" else 1), "HBM runs must be >= 32 bytes"
 
 
+@pytest.mark.parametrize("n", [3, 6, 7, 10, 13, 16])
+@pytest.mark.parametrize("prec", [1, 5])
+def test_emulated_tensor_tier_plans(oracle_mod, n, prec):
+    """Tensor-core tier plans: one block of <= 6 wires per pass, 12-bit tiles."""
+    x = qft_inputs.gaussian(n, seed=300 + n, normalise=False)
+    for order in (q.ORDER_NATURAL, q.ORDER_BITREV):
+        p = q.Plan(n, -1 if n % 2 else 3, q.FORWARD, "c64", order, precision=prec)
+        for i in range(p.info().passes):
+            P = parse(p.describe_pass(i))
+            assert P["nstages"] == 1 and P["st"][0]["r"] <= 6 and P["tb"] - P["st"][0]["r"] <= 8
+        got = emulate(p, x, q.SCALE_STATE)
+        ref, _ = oracle_mod.qft(x, k=p.k, sign=-1, mode=0, natural_order=(order == q.ORDER_NATURAL))
+        assert rel_l2(got, ref) < 1e-12
+
+
+def test_tensor_tier_rejects_complex128():
+    with pytest.raises(q.QftError) as e:
+        q.Plan(20, dtype="c128", precision=q.PREC_FP16X3)
+    assert e.value.code == q.ERR_UNSUPPORTED
+
+
 def test_plan_counters_table2():
     """Pre-fusion counters of the plan reproduce Table 2 for n = 22."""
     for k, cnt in ((21, 231), (16, 216), (12, 186), (10, 165), (8, 140), (6, 111), (4, 78)):
