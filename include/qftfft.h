@@ -96,7 +96,9 @@ typedef struct {
                            (stages <= 4 wires); 0 = default                                 */
     int precision;      /* QFT_PREC_*: 0 = CUDA cores in the dtype's own precision; otherwise
                            complex64 only, each pass's fused block of <= 6 wires as a dense
-                           complex GEMM on the tensor cores (see enum qft_precision)        */
+                           complex GEMM on the tensor cores (see enum qft_precision).  The
+                           block matrices are built and uploaded (plan-owned device memory)
+                           by the plan's first execute, which should precede any capture. */
 } qft_opts;
 
 /* Precision tier (complex64 plans): the block matrix and the data are rounded to

@@ -372,18 +372,32 @@ int plan_passes(qft_plan_s* pl) {
 // on the basis vectors, embed it as the real matrix [[Re, -Im], [Im, Re]],
 // pad it to 128 x kpad, and round it on the device to the operand format (hi
 // and lo parts).  The matrices are plan-owned device memory.
-int prepare_tensor_passes(qft_plan_s* pl) {
-    const double two_pi = 6.283185307179586476925286766559;
+// Host-only check at plan creation: every pass is one block whose GEMM fits.
+int check_tensor_passes(qft_plan_s* pl) {
     for (auto& ph : pl->passes) {
         const PassParams& P = ph.prm;
         if (P.nstages != 1) return QFT_ERR_UNSUPPORTED;
+        const int J = 1 << P.st[0].r;
+        const int kstep = pl->precision == QFT_PREC_TF32 ? 8 : 16;
+        ph.tc_kpad = std::max(kstep, (2 * J + kstep - 1) / kstep * kstep);
+        const int ng = 1 << P.st[0].ngbits;
+        ph.tc_ncols = std::max(16, (ng + 15) / 16 * 16);
+        if (ph.tc_ncols > 256 || 2 * J > 128) return QFT_ERR_UNSUPPORTED;
+        ph.smem = tc_smem_bytes(P, pl->precision, ph.tc_kpad, ph.tc_ncols);
+        if (ph.smem > 227 * 1024 - 4096) return QFT_ERR_UNSUPPORTED;
+    }
+    return QFT_OK;
+}
+
+// Device side, once per plan (at its first execute): build and upload the matrices.
+int prepare_tensor_passes(qft_plan_s* pl) {
+    const double two_pi = 6.283185307179586476925286766559;
+    for (auto& ph : pl->passes) {
+        if (ph.tc_a_hi) continue;
+        const PassParams& P = ph.prm;
         const int r = P.st[0].r;
         const int J = 1 << r;
-        const int kstep = pl->precision == QFT_PREC_TF32 ? 8 : 16;
-        const int kpad = std::max(kstep, (2 * J + kstep - 1) / kstep * kstep);
-        const int ng = 1 << P.st[0].ngbits;
-        const int ncols = std::max(16, (ng + 15) / 16 * 16);
-        if (ncols > 256 || 2 * J > 128) return QFT_ERR_UNSUPPORTED;
+        const int kpad = ph.tc_kpad;
         std::vector<double> Fre(size_t(J) * J), Fim(size_t(J) * J);
         std::vector<double> vr(J), vi(J);
         for (int ji = 0; ji < J; ++ji) {
@@ -433,11 +447,12 @@ int prepare_tensor_passes(qft_plan_s* pl) {
         if (e == cudaSuccess) e = tc_prepare_a(pl->precision, d_src, ph.tc_a_hi, ph.tc_a_lo, kpad, nullptr);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(d_src);
-        if (e != cudaSuccess) return set_cuda_error(e);
-        ph.tc_kpad = kpad;
-        ph.tc_ncols = ncols;
-        ph.smem = tc_smem_bytes(P, pl->precision, kpad, ncols);
-        if (ph.smem > 227 * 1024 - 4096) return QFT_ERR_UNSUPPORTED;
+        if (e != cudaSuccess) {
+            cudaFree(ph.tc_a_hi);
+            cudaFree(ph.tc_a_lo);
+            ph.tc_a_hi = ph.tc_a_lo = nullptr;
+            return set_cuda_error(e);
+        }
     }
     return QFT_OK;
 }
@@ -560,7 +575,7 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
     for (int t = n - 1; t >= 0; --t) pl->n_cp += std::min(pl->kk, t);
     pl->n_swap = n / 2;
     int rc = plan_passes(pl);
-    if (rc == QFT_OK && pl->precision) rc = prepare_tensor_passes(pl);
+    if (rc == QFT_OK && pl->precision) rc = check_tensor_passes(pl);
     if (rc != QFT_OK) {
         delete pl;
         return rc;
@@ -633,6 +648,10 @@ int execute_range(qft_plan_t pl, void* d_state, void* d_workspace, double* d_sca
     char* ws = static_cast<char*>(d_workspace);
     void* work = ws + kMetaBytes;
     std::lock_guard<std::mutex> lock(pl->mu);
+    if (pl->precision && !pl->passes[0].tc_a_hi) {
+        const int prc = prepare_tensor_passes(pl);
+        if (prc != QFT_OK) return prc;
+    }
     int rc = encode_maps(pl, d_state, work);
     if (rc != QFT_OK) return rc;
     cudaError_t e = cudaSuccess;

@@ -127,9 +127,6 @@ def _gather_tma(P, src_u64, tiles):
     return addr
 
 
-W32 = np.exp(2j * np.pi * np.arange(32) / 32)
-
-
 def _block_circuit(v, R, kk, sign):
     """v: (..., 2^R) complex; the block's H (unnormalised) + controlled phases."""
     for t in range(R - 1, -1, -1):
@@ -143,8 +140,7 @@ def _block_circuit(v, R, kk, sign):
         mask = (bit - 1) & ~((1 << lo) - 1)
         for j in range(1 << R):
             if j & bit:
-                m = ((j & mask) << (4 - t)) & 31
-                v[..., j] *= W32[m] if sign > 0 else np.conj(W32[m])
+                v[..., j] *= np.exp(sign * 2j * np.pi * (j & mask) / (2 * bit))
     return v
 
 
