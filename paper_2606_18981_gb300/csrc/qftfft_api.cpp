@@ -299,6 +299,12 @@ int plan_passes(qft_plan_s* pl) {
         P = (n + cap - 1) / cap;
         a.assign(P, n / P);
         for (int j = 0; j < n % P; ++j) a[j] += 1;
+    } else if (pl->precision) {
+        // tensor tier: every pass is one block of <= cap wires
+        P = (n + cap - 1) / cap;
+        if (P < 2) P = 2;
+        a.assign(P, n / P);
+        for (int j = 0; j < n % P; ++j) a[j] += 1;
     } else {
         P = 1 + (n - TB + cap - 1) / cap;
         if (P < 2) P = 2;
