@@ -375,6 +375,59 @@ def serving_workload(q, torch, dev, rates=(1000, 5000, 10000, 20000, 50000), per
     return res
 
 
+def tensor_tier_workload(q, torch, dev, stream):
+    """Precision tier: fused 6-wire blocks as tcgen05 GEMMs (TF32, BF16, FP16,
+    split x3).  Per tier: time of one exact forward transform at n = 24 and of
+    256 transforms at n = 20, and the relative L2 error of the n = 24 result
+    against the FP64 oracle (the same seeded Gaussian input for every tier)."""
+    import numpy as np
+
+    import oracle
+    import qft_inputs
+
+    oracle.build()
+    n = 24
+    x = qft_inputs.gaussian(n, seed=24).astype(np.complex64)
+    ref, _ = oracle.qft(x.astype(np.complex128), -1, -1, oracle.SCALE_STATE, True)
+    xd = torch.from_numpy(x).to(dev)
+    tiers = {"native_fp32": q.PREC_NATIVE, "fp16x3": q.PREC_FP16X3, "bf16x3": q.PREC_BF16X3, "tf32": q.PREC_TF32,
+             "fp16": q.PREC_FP16, "bf16": q.PREC_BF16}
+    out = {}
+    a = torch.cuda.Event(enable_timing=True)
+    bb = torch.cuda.Event(enable_timing=True)
+    for name, prec in tiers.items():
+        p = q.Plan(n, -1, q.FORWARD, "c64", q.ORDER_NATURAL, precision=prec)
+        st = xd.clone()
+        ws = p.alloc_workspace(dev)
+        p.execute(st, ws, q.SCALE_STATE, stream=stream)
+        torch.cuda.synchronize()
+        got = st.cpu().numpy().astype(np.complex128)
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        a.record(stream)
+        for _ in range(10):
+            p.execute(st, ws, q.SCALE_STATE, stream=stream)
+        bb.record(stream)
+        torch.cuda.synchronize()
+        ms24 = a.elapsed_time(bb) / 10
+        p20 = q.Plan(20, -1, q.FORWARD, "c64", q.ORDER_NATURAL, precision=prec)
+        bufs = torch.empty(256, 1 << 20, dtype=torch.complex64, device=dev)
+        ws20 = p20.alloc_workspace(dev)
+        p20.execute(bufs[0], ws20, q.SCALE_STATE, stream=stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for i in range(256):
+            p20.execute(bufs[i], ws20, q.SCALE_STATE, stream=stream)
+        bb.record(stream)
+        torch.cuda.synchronize()
+        ms256 = a.elapsed_time(bb)
+        out[name] = {"rel_l2_vs_fp64_oracle_n24": err, "passes_n24": p.info().passes, "ms_n24": ms24,
+                     "amplitudes_per_s_n24": (1 << n) / (ms24 / 1e3), "ms_256x_n20": ms256,
+                     "transforms_per_s_256x_n20": 256 / (ms256 / 1e3)}
+        del st, ws, bufs, ws20
+    torch.cuda.empty_cache()
+    return out
+
+
 def timed_transform(q, torch, plan, state, ws, stream, steps, warmup):
     """Device-timed steps on resident data; returns (ms/step, [mean ms per pass])."""
     P = plan.info().passes
@@ -502,6 +555,10 @@ def run_ours(args, world, rank, local):
             extra["batched_4096_n8to18_c64"] = batched_workload(q, torch, dev, stream)
         except Exception as ex:
             extra["batched_4096_n8to18_c64"] = {"error": str(ex)[:300]}
+        try:
+            extra["tensor_tier"] = tensor_tier_workload(q, torch, dev, stream)
+        except Exception as ex:
+            extra["tensor_tier"] = {"error": str(ex)[:300]}
         try:
             extra["serving_poisson"] = serving_workload(q, torch, dev)
         except Exception as ex:

@@ -156,8 +156,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (Op::split) reinterpret_cast<uint4*>(B_lo)[i] = make_uint4(0, 0, 0, 0);
         }
     }
+    // One accumulator per K step where tensor memory allows (<= 512 columns):
+    // each accumulator then sums only 16 (8 for TF32) products before the
+    // accumulators are added pairwise in FP32 on the CUDA cores, which keeps
+    // the FP32 accumulation error of the long dot products down.
+    uint32_t cols_pow2 = 16;
+    while (cols_pow2 < static_cast<uint32_t>(ncols)) cols_pow2 <<= 1;
+    const int kstep_n = kpad / (32 / EB);
+    int nacc = 1;
+    while (nacc * 2 <= kstep_n && cols_pow2 * static_cast<uint32_t>(nacc * 2) <= 512u) nacc *= 2;
     uint32_t tcols = 32;
-    while (tcols < static_cast<uint32_t>(ncols)) tcols <<= 1;
+    while (tcols < cols_pow2 * static_cast<uint32_t>(nacc)) tcols <<= 1;
     if (tid < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
                      "r"(tcols));
@@ -264,14 +273,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // 3. the GEMM
         if (tid == 0) {
             const uint32_t a0 = smem_u32(A_hi), a1 = smem_u32(A_lo), b0 = smem_u32(B_hi), b1 = smem_u32(B_lo);
-            uint32_t acc = 0;
             for (int kb = 0; kb < kpad / kstep; ++kb) {
                 const uint32_t ko = static_cast<uint32_t>(kb) * koff_step;
-                umma<Op::kind>(taddr, umma_desc(a0 + ko, lbo, sbo), umma_desc(b0 + ko, lbo, sbo), idesc, acc);
-                acc = 1;
+                const uint32_t dst = taddr + static_cast<uint32_t>(kb % nacc) * cols_pow2;
+                const uint32_t acc = kb >= nacc ? 1u : 0u;
+                umma<Op::kind>(dst, umma_desc(a0 + ko, lbo, sbo), umma_desc(b0 + ko, lbo, sbo), idesc, acc);
                 if (Op::split) {
-                    umma<Op::kind>(taddr, umma_desc(a1 + ko, lbo, sbo), umma_desc(b0 + ko, lbo, sbo), idesc, 1);
-                    umma<Op::kind>(taddr, umma_desc(a0 + ko, lbo, sbo), umma_desc(b1 + ko, lbo, sbo), idesc, 1);
+                    umma<Op::kind>(dst, umma_desc(a1 + ko, lbo, sbo), umma_desc(b0 + ko, lbo, sbo), idesc, 1);
+                    umma<Op::kind>(dst, umma_desc(a0 + ko, lbo, sbo), umma_desc(b1 + ko, lbo, sbo), idesc, 1);
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -286,16 +295,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int w = tid >> 5, l = tid & 31;
             const int m = w * 32 + l;
             for (int c = 0; c < ncols; c += 16) {
-                uint32_t v[16];
-                const uint32_t a = taddr + (static_cast<uint32_t>(w * 32) << 16) + static_cast<uint32_t>(c);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                    : "r"(a));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float sum[16];
+                // pairwise sum over the accumulators: level by level, 16 columns at a time
+                float part[8][16];
+                const int np = nacc < 8 ? nacc : 8;
+                for (int a0 = 0; a0 < nacc; a0 += np) {
+                    for (int i = 0; i < np; ++i) {
+                        uint32_t v[16];
+                        const uint32_t a = taddr + (static_cast<uint32_t>(w * 32) << 16) +
+                                           static_cast<uint32_t>(a0 + i) * cols_pow2 + static_cast<uint32_t>(c);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                              "=r"(v[14]), "=r"(v[15])
+                            : "r"(a));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) part[i][j] = __uint_as_float(v[j]);
+                    }
+                    for (int width = 1; width < np; width *= 2)
+                        for (int i = 0; i + width < np; i += 2 * width)
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) part[i][j] += part[i + width][j];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) sum[j] = a0 == 0 ? part[0][j] : sum[j] + part[0][j];
+                }
                 if (m < 2 * J)
-                    for (int j = 0; j < 16; ++j) D[m * ncols + c + j] = __uint_as_float(v[j]);
+                    for (int j = 0; j < 16; ++j) D[m * ncols + c + j] = sum[j];
             }
         }
         tc_fence_before();
