@@ -269,7 +269,7 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
     plans = {}
     for n, k, _ in specs:
         if (n, k) not in plans:
-            plans[(n, k)] = q.Plan(n, k, q.FORWARD, "c64", q.ORDER_NATURAL)
+            plans[(n, k)] = q.Plan(n, k, q.FORWARD, "c64", q.ORDER_NATURAL, tuned=True)
     pool = torch.empty(amps + 64 * count, dtype=torch.complex64, device=dev)
     states, off = [], 0
     for i, (n, k, kind) in enumerate(specs):
@@ -303,7 +303,7 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
     del batch, states, pool, g
     torch.cuda.empty_cache()
     # the plain single-transform complex128 path on the same transforms
-    p128 = {key: q.Plan(key[0], key[1], q.FORWARD, "c128", q.ORDER_NATURAL) for key in plans}
+    p128 = {key: q.Plan(key[0], key[1], q.FORWARD, "c128", q.ORDER_NATURAL, tuned=True) for key in plans}
     ws = {key: p.alloc_workspace(dev) for key, p in p128.items()}
     buf = torch.empty(1 << 18, dtype=torch.complex128, device=dev)
     sub = specs[:1024]
@@ -465,7 +465,7 @@ def run_ours(args, world, rank, local):
     n, dt, k = args.n, args.dtype, args.k
     N = 1 << n
     eb = 8 if dt == "c64" else 16
-    plan = q.Plan(n, k, q.FORWARD, dt, q.ORDER_NATURAL, threads=args.threads)
+    plan = q.Plan(n, k, q.FORWARD, dt, q.ORDER_NATURAL, threads=args.threads, tuned=True)
     info = plan.info()
     P = info.passes
     stream = torch.cuda.Stream(device=dev)
@@ -566,7 +566,7 @@ def run_ours(args, world, rank, local):
         for name, (nn, ddt, kk) in {"aqft_k4_c64_n30": (30, "c64", 4), "plain_c128_n30": (30, "c128", -1),
                                      "c64_n26": (26, "c64", -1), "c64_n33": (33, "c64", -1)}.items():
             try:
-                p2 = q.Plan(nn, kk, q.FORWARD, ddt, q.ORDER_NATURAL)
+                p2 = q.Plan(nn, kk, q.FORWARD, ddt, q.ORDER_NATURAL, tuned=True)
                 free, _ = torch.cuda.mem_get_info()
                 need = (1 << nn) * (8 if ddt == "c64" else 16) * 2 + (1 << 30)
                 if free < need:

@@ -151,11 +151,20 @@ class Plan:
 
     def __init__(self, n: int, k: int = -1, direction: int = FORWARD, dtype="c64", order: int = ORDER_NATURAL,
                  tile_bits: int = 0, coalesce_bits: int = 0, max_stage_bits: int = 0,
-                 wait_limit_ms: int = 0, test_skip_first_load: int = 0, threads: int = 0, precision: int = 0):
+                 wait_limit_ms: int = 0, test_skip_first_load: int = 0, threads: int = 0, precision: int = 0,
+                 tuned: bool = False):
         self._h = _vp()
         self.n, self.k, self.direction = int(n), int(k), int(direction)
         self.dtype = _dtype_code(dtype)
         self.order = int(order)
+        if tuned and precision == 0:  # plan shape from the autotuner's cache, where it has one
+            from .autotune import best_opts
+
+            t = best_opts(self.n, "c64" if self.dtype == C64 else "c128")
+            tile_bits = tile_bits or t.get("tile_bits", 0)
+            coalesce_bits = coalesce_bits or t.get("coalesce_bits", 0)
+            max_stage_bits = max_stage_bits or t.get("max_stage_bits", 0)
+            threads = threads or t.get("threads", 0)
         opts = Opts(order, tile_bits, coalesce_bits, max_stage_bits, wait_limit_ms, test_skip_first_load, threads,
                     precision)
         _check(_lib.qft_plan_create(ctypes.byref(self._h), self.n, self.k, self.direction, self.dtype,

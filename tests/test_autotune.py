@@ -1,0 +1,34 @@
+"""Autotuner cache handling (CPU) and a small tuning run (GPU)."""
+import json
+
+import pytest
+
+q = pytest.importorskip("paper_2606_18981_gb300")
+from paper_2606_18981_gb300 import autotune  # noqa: E402
+
+
+def test_best_opts_reads_cache(tmp_path, monkeypatch):
+    path = tmp_path / "cache.json"
+    path.write_text(json.dumps({"c64": {"20": {"opts": {"tile_bits": 12, "coalesce_bits": 4, "max_stage_bits": 4,
+                                                       "threads": 512}}}}))
+    monkeypatch.setattr(autotune, "CACHE", str(path))
+    monkeypatch.setattr(autotune, "_cache", None)
+    assert autotune.best_opts(20, "c64") == {"tile_bits": 12, "coalesce_bits": 4, "max_stage_bits": 4, "threads": 512}
+    assert autotune.best_opts(21, "c64") == {}
+    p = q.Plan(20, tuned=True)
+    assert list(p.info().tile_bits)[0] == 12
+
+
+def test_every_candidate_is_a_valid_plan():
+    for dt, cands in autotune.CANDIDATES.items():
+        for tb, cb, sb, th in cands:
+            for n in (8, 14, 20, 26, 30):
+                q.Plan(n, -1, q.FORWARD, dt, tile_bits=tb, coalesce_bits=cb, max_stage_bits=sb, threads=th)
+
+
+@pytest.mark.gpu
+def test_tune_small_range(tmp_path):
+    cache = autotune.tune([14, 18], "c64", reps=2, path=str(tmp_path / "c.json"), verbose=False)
+    assert set(cache["c64"]) == {"14", "18"}
+    for e in cache["c64"].values():
+        assert e["ms"] > 0 and e["passes"] >= 1
