@@ -99,6 +99,11 @@ typedef struct {
                            complex GEMM on the tensor cores (see enum qft_precision).  The
                            block matrices are built and uploaded (plan-owned device memory)
                            by the plan's first execute, which should precede any capture. */
+    int paired;         /* complex64: 1 = where a pass's lowest tile bit is a batch wire, each
+                           thread runs the two groups that differ in it with packed FP32x2
+                           arithmetic (blocks of <= 4 wires); 0 = default: one group per
+                           thread.  (Passes whose tile is <= 2^12 amplitudes and whose blocks
+                           have <= 4 wires, or <= 3 when paired, run two CTAs per SM.)     */
 } qft_opts;
 
 /* Precision tier (complex64 plans): the block matrix and the data are rounded to

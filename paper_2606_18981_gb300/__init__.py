@@ -58,7 +58,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("tile_bits", ctypes.c_int), ("coalesce_bits", ctypes.c_int),
                 ("max_stage_bits", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
                 ("test_skip_first_load", ctypes.c_int), ("threads", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("paired", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -152,7 +152,7 @@ class Plan:
     def __init__(self, n: int, k: int = -1, direction: int = FORWARD, dtype="c64", order: int = ORDER_NATURAL,
                  tile_bits: int = 0, coalesce_bits: int = 0, max_stage_bits: int = 0,
                  wait_limit_ms: int = 0, test_skip_first_load: int = 0, threads: int = 0, precision: int = 0,
-                 tuned: bool = False):
+                 paired: int = 0, tuned: bool = False):
         self._h = _vp()
         self.n, self.k, self.direction = int(n), int(k), int(direction)
         self.dtype = _dtype_code(dtype)
@@ -165,8 +165,9 @@ class Plan:
             coalesce_bits = coalesce_bits or t.get("coalesce_bits", 0)
             max_stage_bits = max_stage_bits or t.get("max_stage_bits", 0)
             threads = threads or t.get("threads", 0)
+            paired = paired or t.get("paired", 0)
         opts = Opts(order, tile_bits, coalesce_bits, max_stage_bits, wait_limit_ms, test_skip_first_load, threads,
-                    precision)
+                    precision, paired)
         _check(_lib.qft_plan_create(ctypes.byref(self._h), self.n, self.k, self.direction, self.dtype,
                                     ctypes.byref(opts)), "qft_plan_create")
 

@@ -19,11 +19,18 @@ import statistics
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 
-# candidate plan shapes: (tile_bits, coalesce_bits, max_stage_bits, threads); 0 = planner default
+# candidate plan shapes (qft_opts fields; 0 = planner default).  Complex64
+# tiles of 2^12 amplitudes run two CTAs per SM; "paired" selects the packed
+# FP32x2 stages.
+_KEYS = ("tile_bits", "coalesce_bits", "max_stage_bits", "threads", "paired")
 CANDIDATES = {
-    "c64": [(0, 0, 0, 0), (13, 4, 5, 256), (13, 4, 4, 256), (13, 4, 4, 512), (13, 5, 5, 256), (12, 4, 4, 256),
-            (13, 3, 5, 256), (12, 3, 4, 512)],
-    "c128": [(0, 0, 0, 0), (12, 3, 5, 256), (12, 3, 4, 256), (12, 3, 4, 512), (11, 3, 4, 256), (12, 2, 4, 256)],
+    "c64": [dict(zip(_KEYS, c)) for c in (
+        (0, 0, 0, 0, 0), (13, 4, 5, 256, 0), (13, 3, 5, 256, 0), (13, 5, 5, 256, 0), (13, 4, 4, 512, 0),
+        (12, 4, 4, 256, 0), (12, 3, 4, 256, 0), (12, 5, 4, 256, 0), (12, 4, 3, 256, 0), (11, 4, 4, 256, 0),
+        (13, 4, 4, 256, 1), (12, 4, 3, 256, 1))],
+    "c128": [dict(zip(_KEYS, c)) for c in (
+        (0, 0, 0, 0, 0), (12, 3, 5, 256, 0), (12, 3, 4, 256, 0), (12, 3, 4, 512, 0), (11, 3, 4, 256, 0),
+        (12, 2, 4, 256, 0))],
 }
 
 _cache: dict | None = None
@@ -48,7 +55,8 @@ def _read(path: str) -> dict:
 
 
 def best_opts(n: int, dtype: str = "c64") -> dict:
-    """Plan keyword arguments the cache holds for (dtype, n) ({} if none)."""
+    """Plan keyword arguments the cache holds for (dtype, n) ({} if none); zero
+    fields (planner defaults) are left out."""
     entry = load_cache().get(dtype, {}).get(str(int(n)))
     if not entry:
         return {}
@@ -56,6 +64,7 @@ def best_opts(n: int, dtype: str = "c64") -> dict:
 
 
 def _time_plan(q, torch, plan, state, ws, reps):
+    torch.cuda.synchronize()  # state was written on the current stream
     s = torch.cuda.Stream()
     plan.execute(state, ws, q.SCALE_STATE, stream=s)
     torch.cuda.synchronize()
@@ -90,10 +99,8 @@ def tune(ns, dtype: str = "c64", reps: int = 5, path: str | None = None, verbose
         ref = None
         results = []
         for cand in CANDIDATES[dtype]:
-            tb, cb, sb, th = cand
             try:
-                p = q.Plan(n, -1, q.FORWARD, dtype, q.ORDER_NATURAL, tile_bits=tb, coalesce_bits=cb,
-                           max_stage_bits=sb, threads=th)
+                p = q.Plan(n, -1, q.FORWARD, dtype, q.ORDER_NATURAL, **cand)
             except q.QftError:
                 continue
             ws = p.alloc_workspace()
@@ -110,12 +117,13 @@ def tune(ns, dtype: str = "c64", reps: int = 5, path: str | None = None, verbose
             ms = _time_plan(q, torch, p, x.clone(), ws, reps)
             results.append((ms, cand, p.info().passes))
             del ws, st
-        ms, cand, passes = min(results)
-        cache[dtype][str(n)] = {"opts": {"tile_bits": cand[0], "coalesce_bits": cand[1], "max_stage_bits": cand[2],
-                                         "threads": cand[3]}, "ms": ms, "passes": passes,
-                                "candidates": {str(c): m for m, c, _ in results}}
+        ms, i_best, passes = min((m, i, ps) for i, (m, _, ps) in enumerate(results))
+        cand = results[i_best][1]
+        cache[dtype][str(n)] = {"opts": dict(cand), "ms": ms, "passes": passes,
+                                "candidates": {",".join(str(cand_v) for cand_v in c.values()): m
+                                               for m, c, _ in results}}
         if verbose:
-            print(f"{dtype} n={n}: best {cand} {ms:.4f} ms ({passes} passes)", flush=True)
+            print(f"{dtype} n={n}: best {tuple(cand.values())} {ms:.4f} ms ({passes} passes)", flush=True)
         del x, ref
         torch.cuda.empty_cache()
     with open(path, "w") as f:

@@ -90,6 +90,8 @@ struct PassParams {
     int32_t* status;               // workspace status word (bounded waits report here)
     uint64_t wait_limit_ns;        // bound of each tile wait
     int32_t test_skip_first_load;  // test hook: never issue the first load (the wait must expire)
+    int32_t paired;                // complex64: tile bit 0 is a SIMD lane of packed f32x2 stages (qft_pair.cuh)
+    int32_t ntw;                   // twiddle planes in the group tables (the widest block of the pass)
 };
 
 // One tile of one pass of one transform in a batched launch.

@@ -12,9 +12,11 @@
 
 namespace qft {
 
-cudaError_t launch_pass(int dtype, int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid,
-                        size_t smem, cudaStream_t stream);
+cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P,
+                        int grid, size_t smem, cudaStream_t stream);
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes);
+cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+                          cudaStream_t stream);
 cudaError_t launch_tc_pass(int dir, int prec, const CUtensorMap& map, const PassParams& P, const void* a_hi,
                            const void* a_lo, int kpad, int ncols, int grid, size_t smem, cudaStream_t st);
 size_t tc_smem_bytes(const PassParams& P, int prec, int kpad, int ncols);
@@ -32,6 +34,7 @@ struct PassHost {
     PassParams prm;
     int in_buf = 0, out_buf = 0;  // 0 = caller's state, 1 = workspace ping-pong buffer
     int grid = 1;
+    int minb = 1;  // CTAs per SM the pass kernel is built for (2: tiles <= 2^12, stages <= 4 wires)
     size_t smem = 0;
     // TMA description
     int rank = 5;
@@ -64,6 +67,7 @@ struct qft_plan_s {
     size_t esize = 8;
     int TB = 13, cmin = 2, rmax = 4;
     int threads = 256;  // CTA size of the pass kernel (256: stages of <= 5 wires; 512: <= 4)
+    bool pairing = false;  // complex64 passes may use the paired (packed f32x2) kernel
     uint64_t wait_limit_ns = 2000000000ull;
     int test_skip_first_load = 0;
     int num_sms = 148;

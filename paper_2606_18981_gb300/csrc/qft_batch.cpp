@@ -22,7 +22,7 @@
 #include "plan_host.hpp"
 
 namespace qft {
-cudaError_t launch_batch(int dtype, int dir, const BatchItem* items, int nitems, const PassParams* descs,
+cudaError_t launch_batch(int dtype, int dir, int minb, const BatchItem* items, int nitems, const PassParams* descs,
                          const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
                          int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream);
 size_t batch_smem_bytes(int max_tb, int max_ntab, size_t elem_bytes);
@@ -31,7 +31,7 @@ size_t batch_smem_bytes(int max_tb, int max_ntab, size_t elem_bytes);
 using namespace qft;
 
 struct qft_batch_s {
-    int count = 0, dtype = 0, dir = -1, nitems = 0, max_tb = 1, max_ntab = 1, grid = 1;
+    int count = 0, dtype = 0, dir = -1, nitems = 0, max_tb = 1, max_ntab = 1, grid = 1, minb = 1;
     size_t smem = 0;
     uint64_t wait_ns = 2000000000ull;
     // device tables owned by the batch
@@ -177,8 +177,17 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
     b->nitems = static_cast<int>(items.size());
     b->ncounters = ncounters;
     b->smem = batch_smem_bytes(b->max_tb, b->max_ntab, plans[0]->esize);
-    b->grid = std::max(1, std::min(plans[0]->num_sms, b->nitems));
     if (b->smem > 227 * 1024 - 4096) { free_batch(b); return QFT_ERR_UNSUPPORTED; }
+    // two CTAs per SM when both fit in shared memory and every block has <= 4 wires
+    // (the 128-register kernel), for unpaired complex64 passes
+    bool small = b->dtype == QFT_C64 && b->max_tb <= 12 && 2 * (b->smem + 3 * 1024) <= 228 * 1024;
+    for (const auto& d : descs) {
+        if (d.paired) small = false;
+        for (int s = 0; s < d.nstages; ++s)
+            if (d.st[s].r > 4) small = false;
+    }
+    b->minb = small ? 2 : 1;
+    b->grid = std::max(1, std::min(plans[0]->num_sms * b->minb, b->nitems));
 
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_counters), sizeof(int) * ncounters);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_descs), sizeof(PassParams) * descs.size());
@@ -202,7 +211,7 @@ int qft_batch_execute(qft_batch_t b, qft_stream_t stream) {
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->ncounters, st);
     if (e != cudaSuccess) return set_cuda_error(e);
     // counter indices in the items start at 2: [0] queue head, [1] status word
-    e = launch_batch(b->dtype, b->dir, b->d_items, b->nitems, b->d_descs, b->d_maps, b->d_counters,
+    e = launch_batch(b->dtype, b->dir, b->minb, b->d_items, b->nitems, b->d_descs, b->d_maps, b->d_counters,
                      b->d_counters, b->d_counters + 1, b->wait_ns, b->max_tb, b->max_ntab, b->grid, b->smem, st);
     return e == cudaSuccess ? QFT_OK : set_cuda_error(e);
 }

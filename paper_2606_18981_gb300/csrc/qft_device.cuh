@@ -81,6 +81,14 @@ __device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_
         : "memory");
 }
 
+// Index of the lowest set bit of j (j > 0).  Written as plain arithmetic so
+// that, with j a constant of an unrolled loop, it folds to a constant and the
+// register arrays it indexes stay in registers (an opaque intrinsic there
+// would force those arrays into local memory).
+__host__ __device__ constexpr int low_bit(int j) {
+    return (j & 1) ? 0 : (j & 2) ? 1 : (j & 4) ? 2 : (j & 8) ? 3 : (j & 16) ? 4 : (j & 32) ? 5 : 6;
+}
+
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
@@ -215,7 +223,7 @@ template <typename V>
 struct GroupTab {
     uint32_t* pb;
     int64_t* ob;
-    V* tw;  // [e][entry], e < kMaxR: plane e holds factor e of every entry (lane reads are consecutive)
+    V* tw;  // [e][entry], e < ntw: plane e holds factor e of every entry (lane reads are consecutive)
     int ntab;
 };
 
@@ -330,7 +338,7 @@ __device__ __forceinline__ void build_group_tables(const PassParams& P, GroupTab
             const int idx = P.tab_off[s] + i;
             tab.pb[idx] = pb;
             tab.ob[idx] = ob;
-            for (int e = 0; e < kMaxR; ++e) {
+            for (int e = 0; e < P.ntw; ++e) {
                 V w;
                 w.x = T(1);
                 w.y = T(0);

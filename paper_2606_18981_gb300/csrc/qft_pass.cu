@@ -30,6 +30,7 @@
 
 #include "plan.hpp"
 #include "qft_device.cuh"
+#include "qft_pair.cuh"
 
 namespace qft {
 
@@ -58,7 +59,7 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
     uint32_t soff[NJ];
     soff[0] = 0;
 #pragma unroll
-    for (int j = 1; j < NJ; ++j) soff[j] = soff[j & (j - 1)] ^ static_cast<uint32_t>(S.img[__ffs(j) - 1]);
+    for (int j = 1; j < NJ; ++j) soff[j] = soff[j & (j - 1)] ^ static_cast<uint32_t>(S.img[low_bit(j)]);
     const bool cross = S.cross != 0;
     const bool use_u = cross && S.tile_above;
     V u[R];
@@ -111,10 +112,10 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
             V tl[1 << LB], th[1 << HB];
 #pragma unroll
             for (int a = 1; a < (1 << LB); ++a)
-                tl[a] = (a & (a - 1)) ? cmul(tl[a & (a - 1)], tau[__ffs(a) - 1]) : tau[__ffs(a) - 1];
+                tl[a] = (a & (a - 1)) ? cmul(tl[a & (a - 1)], tau[low_bit(a)]) : tau[low_bit(a)];
 #pragma unroll
             for (int b = 1; b < (1 << HB); ++b)
-                th[b] = (b & (b - 1)) ? cmul(th[b & (b - 1)], tau[LB + __ffs(b) - 1]) : tau[LB + __ffs(b) - 1];
+                th[b] = (b & (b - 1)) ? cmul(th[b & (b - 1)], tau[LB + low_bit(b)]) : tau[LB + low_bit(b)];
 #pragma unroll
             for (int j = 1; j < NJ; ++j) {
                 const int a = j & ((1 << LB) - 1), b = j >> LB;
@@ -144,7 +145,7 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
     }
 }
 
-template <typename T, int DIR, int KIND, int NT>
+template <typename T, int DIR, int KIND, int NT, int MAXR>
 __device__ __forceinline__ void dispatch_r(const PassParams& P, int s, const GroupTab<typename Vec2<T>::type>& tab,
                                            const typename Vec2<T>::type* A, typename Vec2<T>::type* Bb,
                                            int64_t out_tile, T scale, const typename Vec2<T>::type* U,
@@ -157,26 +158,29 @@ __device__ __forceinline__ void dispatch_r(const PassParams& P, int s, const Gro
         case 3: run_stage<T, DIR, 3, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
         case 4: run_stage<T, DIR, 4, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
         default:
-            if constexpr (NT <= 256)
+            if constexpr (MAXR >= 5)
                 run_stage<T, DIR, 5, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
             break;
     }
 }
 
-template <typename T, int DIR, int NT>
+template <typename T, int DIR, int NT, int MAXR>
 __device__ __forceinline__ void dispatch_stage(const PassParams& P, int s, const GroupTab<typename Vec2<T>::type>& tab,
                                                const typename Vec2<T>::type* A, typename Vec2<T>::type* Bb,
                                                int64_t out_tile, T scale, const typename Vec2<T>::type* U,
                                                bool acc_norm, double& norm_acc) {
     const bool first = (s == 0), last = (s == P.nstages - 1);
-    if (first && last) dispatch_r<T, DIR, K_ONLY, NT>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
-    else if (first) dispatch_r<T, DIR, K_FIRST, NT>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
-    else if (last) dispatch_r<T, DIR, K_LAST, NT>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
-    else dispatch_r<T, DIR, K_MID, NT>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
+    if (first && last) dispatch_r<T, DIR, K_ONLY, NT, MAXR>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
+    else if (first) dispatch_r<T, DIR, K_FIRST, NT, MAXR>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
+    else if (last) dispatch_r<T, DIR, K_LAST, NT, MAXR>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
+    else dispatch_r<T, DIR, K_MID, NT, MAXR>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
 }
 
-template <typename T, int DIR, int NT>
-__global__ void __launch_bounds__(NT, 1)
+// MINB = CTAs per SM the launch is built for: 2 caps registers at 65536 / (2 NT)
+// and is used only for passes whose stages hold <= 4 wires and whose buffers
+// fit twice in shared memory (tiles of <= 2^12 complex64 amplitudes).
+template <typename T, int DIR, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     qft_pass_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassParams P) {
     using V = typename Vec2<T>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -195,8 +199,8 @@ __global__ void __launch_bounds__(NT, 1)
     GroupTab<V> tab;
     tab.ntab = ntab;
     tab.tw = reinterpret_cast<V*>(tab_raw);
-    tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * sizeof(V) * static_cast<size_t>(ntab));
-    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * sizeof(V) + 8) * static_cast<size_t>(ntab));
+    tab.ob = reinterpret_cast<int64_t*>(tab_raw + P.ntw * sizeof(V) * static_cast<size_t>(ntab));
+    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (P.ntw * sizeof(V) + 8) * static_cast<size_t>(ntab));
 
     build_group_tables<T, DIR, NT>(P, tab);
     if (tid == 0) {
@@ -261,8 +265,9 @@ __global__ void __launch_bounds__(NT, 1)
         for (int s = 0; s < P.nstages; ++s) {
             const bool last_stage = (s == P.nstages - 1);
             const bool from_A = (s == 0);
-            dispatch_stage<T, DIR, NT>(P, s, tab, Ab, B, out_tile, scale, Ucur + P.st[s].uoff,
-                                       P.first && !P.last, norm_acc);
+            dispatch_stage<T, DIR, NT, (NT <= 256 && MINB == 1) ? 5 : 4>(P, s, tab, Ab, B, out_tile, scale,
+                                                                        Ucur + P.st[s].uoff, P.first && !P.last,
+                                                                        norm_acc);
             if (last_stage) compute_tile_twiddles<T, DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1]);
             __syncthreads();
             if (from_A) {
@@ -311,8 +316,8 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-template <typename T, int DIR, int NT>
-__global__ void __launch_bounds__(NT, 1)
+template <typename T, int DIR, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     qft_batch_kernel(const BatchItem* __restrict__ items, int nitems, const PassParams* __restrict__ descs,
                      const CUtensorMap* __restrict__ maps, int* counters, int* next, int* status,
                      uint64_t wait_ns, int max_tb, int max_ntab) {
@@ -320,19 +325,26 @@ __global__ void __launch_bounds__(NT, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ double red[NT / 32];
-    __shared__ __align__(16) V Ubuf[kMaxR * kMaxStages];
+    __shared__ __align__(16) P2 Ubuf_raw[kMaxR * kMaxStages];
     __shared__ int s_item;
 
     const int tid = threadIdx.x;
     const uint32_t max_elems = 1u << max_tb;
     V* B = reinterpret_cast<V*>(smem_raw);
     V* A = B + max_elems;
+    V* Ubuf = reinterpret_cast<V*>(Ubuf_raw);
+    // group tables; twiddle planes sized for 16-byte entries (complex128, or pairs of complex64)
     unsigned char* tab_raw = smem_raw + 2 * static_cast<size_t>(max_elems) * sizeof(V);
     GroupTab<V> tab;
     tab.ntab = max_ntab;
     tab.tw = reinterpret_cast<V*>(tab_raw);
-    tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * sizeof(V) * static_cast<size_t>(max_ntab));
-    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * sizeof(V) + 8) * static_cast<size_t>(max_ntab));
+    tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * 16 * static_cast<size_t>(max_ntab));
+    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * 16 + 8) * static_cast<size_t>(max_ntab));
+    GroupTabP tabp;
+    tabp.ntab = max_ntab;
+    tabp.tw = reinterpret_cast<P2*>(tab_raw);
+    tabp.ob = tab.ob;
+    tabp.pb = tab.pb;
     if (tid == 0) mbar_init(&mbar, 1);
     __syncthreads();
     uint32_t parity = 0;
@@ -344,8 +356,15 @@ __global__ void __launch_bounds__(NT, 1)
         if (item >= nitems) break;
         const BatchItem it = items[item];
         const PassParams& P = descs[it.desc];
+        constexpr bool kCanPair = sizeof(T) == 4 && MINB == 1;  // paired items only in the one-CTA kernel
+        const bool paired = kCanPair && P.paired;
         if (it.shape != cached_shape) {
-            build_group_tables<T, DIR, NT>(P, tab);
+            if constexpr (kCanPair) {
+                if (paired) build_group_tables_p<DIR, NT>(P, tabp);
+                else build_group_tables<T, DIR, NT>(P, tab);
+            } else {
+                build_group_tables<T, DIR, NT>(P, tab);
+            }
             cached_shape = it.shape;
         }
         bool ok = true;
@@ -362,7 +381,12 @@ __global__ void __launch_bounds__(NT, 1)
                 issue_tile_load(P, maps + (it.map >= 0 ? it.map : 0), it.tile, A, &mbar, bytes);
             }
         }
-        compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
+        if constexpr (kCanPair) {
+            if (paired) compute_tile_twiddles_p<DIR>(P, it.tile, Ubuf_raw);
+            else compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
+        } else {
+            compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
+        }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(status, -5);  // QFT_ERR_TIMEOUT
             return;
@@ -404,8 +428,17 @@ __global__ void __launch_bounds__(NT, 1)
         }
         double norm_acc = 0.0;
         for (int s = 0; s < P.nstages; ++s) {
-            dispatch_stage<T, DIR, NT>(P, s, tab, A, B, out_tile, scale, Ubuf + P.st[s].uoff,
-                                       P.first && !P.last, norm_acc);
+            if constexpr (kCanPair) {
+                if (paired) {
+                    dispatch_stage_p<DIR, NT, 4>(P, s, tabp, reinterpret_cast<const float2*>(A), reinterpret_cast<P2*>(B),
+                                              out_tile, static_cast<float>(scale), Ubuf_raw + P.st[s].uoff,
+                                              P.first && !P.last, norm_acc);
+                    __syncthreads();
+                    continue;
+                }
+            }
+            dispatch_stage<T, DIR, NT, MINB == 1 ? 5 : 4>(P, s, tab, A, B, out_tile, scale, Ubuf + P.st[s].uoff,
+                                                          P.first && !P.last, norm_acc);
             __syncthreads();
         }
         if (P.first && !P.last) {
@@ -421,11 +454,11 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
-template <typename T, int DIR, int NT>
+template <typename T, int DIR, int NT, int MINB>
 static cudaError_t launch_batch_t(const BatchItem* items, int nitems, const PassParams* descs,
                                   const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
                                   int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
-    auto kern = qft_batch_kernel<T, DIR, NT>;
+    auto kern = qft_batch_kernel<T, DIR, NT, MINB>;
     static thread_local size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -436,30 +469,34 @@ static cudaError_t launch_batch_t(const BatchItem* items, int nitems, const Pass
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(int dtype, int dir, const BatchItem* items, int nitems, const PassParams* descs,
+// minb = 2: complex64 batches whose tiles are <= 2^12 amplitudes and whose
+// blocks have <= 4 wires run two CTAs per SM (one CTA's load overlaps the
+// other's stages).
+cudaError_t launch_batch(int dtype, int dir, int minb, const BatchItem* items, int nitems, const PassParams* descs,
                          const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
                          int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
+#define QFT_BATCH_ARGS items, nitems, descs, maps, counters, next, status, wait_ns, max_tb, max_ntab, grid, smem, stream
+    if (dtype == 0 && minb == 2)
+        return dir < 0 ? launch_batch_t<float, -1, 256, 2>(QFT_BATCH_ARGS) : launch_batch_t<float, +1, 256, 2>(QFT_BATCH_ARGS);
     if (dtype == 0)
-        return dir < 0 ? launch_batch_t<float, -1, 256>(items, nitems, descs, maps, counters, next, status, wait_ns,
-                                                         max_tb, max_ntab, grid, smem, stream)
-                       : launch_batch_t<float, +1, 256>(items, nitems, descs, maps, counters, next, status, wait_ns,
-                                                         max_tb, max_ntab, grid, smem, stream);
-    return dir < 0 ? launch_batch_t<double, -1, 256>(items, nitems, descs, maps, counters, next, status, wait_ns,
-                                                      max_tb, max_ntab, grid, smem, stream)
-                   : launch_batch_t<double, +1, 256>(items, nitems, descs, maps, counters, next, status, wait_ns,
-                                                      max_tb, max_ntab, grid, smem, stream);
+        return dir < 0 ? launch_batch_t<float, -1, 256, 1>(QFT_BATCH_ARGS) : launch_batch_t<float, +1, 256, 1>(QFT_BATCH_ARGS);
+    return dir < 0 ? launch_batch_t<double, -1, 256, 1>(QFT_BATCH_ARGS) : launch_batch_t<double, +1, 256, 1>(QFT_BATCH_ARGS);
+#undef QFT_BATCH_ARGS
 }
 
 size_t batch_smem_bytes(int max_tb, int max_ntab, size_t elem_bytes) {
-    return 2 * (size_t(1) << max_tb) * elem_bytes + size_t(max_ntab) * (kMaxR * elem_bytes + 8 + 4);
+    return 2 * (size_t(1) << max_tb) * elem_bytes + size_t(max_ntab) * (kMaxR * 16 + 8 + 4);
 }
 
 // ------------------------------------------------------------- launchers
 
-template <typename T, int DIR, int NT>
+cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+                          cudaStream_t stream);  // qft_pair.cu
+
+template <typename T, int DIR, int NT, int MINB>
 static cudaError_t launch_pass_t(const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                                  cudaStream_t stream) {
-    auto kern = qft_pass_kernel<T, DIR, NT>;
+    auto kern = qft_pass_kernel<T, DIR, NT, MINB>;
     static thread_local size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -474,22 +511,27 @@ template <int NT>
 static cudaError_t launch_nt(int dtype, int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                              cudaStream_t stream) {
     if (dtype == 0)
-        return dir < 0 ? launch_pass_t<float, -1, NT>(map, P, grid, smem, stream)
-                       : launch_pass_t<float, +1, NT>(map, P, grid, smem, stream);
-    return dir < 0 ? launch_pass_t<double, -1, NT>(map, P, grid, smem, stream)
-                   : launch_pass_t<double, +1, NT>(map, P, grid, smem, stream);
+        return dir < 0 ? launch_pass_t<float, -1, NT, 1>(map, P, grid, smem, stream)
+                       : launch_pass_t<float, +1, NT, 1>(map, P, grid, smem, stream);
+    return dir < 0 ? launch_pass_t<double, -1, NT, 1>(map, P, grid, smem, stream)
+                   : launch_pass_t<double, +1, NT, 1>(map, P, grid, smem, stream);
 }
 
-cudaError_t launch_pass(int dtype, int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid,
-                        size_t smem, cudaStream_t stream) {
+cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P,
+                        int grid, size_t smem, cudaStream_t stream) {
+    if (P.paired) return launch_pass_p(dir, minb, map, P, grid, smem, stream);
+    if (minb == 2 && dtype == 0 && threads == 256)
+        return dir < 0 ? launch_pass_t<float, -1, 256, 2>(map, P, grid, smem, stream)
+                       : launch_pass_t<float, +1, 256, 2>(map, P, grid, smem, stream);
     if (threads == 512) return launch_nt<512>(dtype, dir, map, P, grid, smem, stream);
     return launch_nt<256>(dtype, dir, map, P, grid, smem, stream);
 }
 
 // Dynamic shared memory of one CTA: buffer B, the two TMA load buffers and
-// the group tables (kMaxR twiddle factors + output offset + tile bits per entry).
+// the group tables (ntw twiddle factors + output offset + tile bits per entry).
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes) {
-    return 3 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (kMaxR * elem_bytes + 8 + 4);
+    const size_t tw_bytes = P.paired ? 16 : elem_bytes;  // paired passes keep twiddle planes as pairs
+    return 3 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (P.ntw * tw_bytes + 8 + 4);
 }
 
 }  // namespace qft

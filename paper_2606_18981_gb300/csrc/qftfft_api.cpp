@@ -122,6 +122,12 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
         P.p_out[i] = Lout[tw[i]];
         pos[tw[i]] = i;
     }
+    // Paired complex64 stages need tile bit 0 to be a batch wire (a SIMD lane
+    // that no block of this pass touches); they take blocks of <= 4 wires.
+    const bool paired = pl->pairing && !(first && last) && (tw[0] < glo || tw[0] >= glo + a);
+    P.paired = paired ? 1 : 0;
+    const int pb0 = paired ? 1 : 0;  // group indices skip tile bit 0
+    const int rmax = paired ? std::min(pl->rmax, 4) : pl->rmax;
     // tile coordinate segments (bit m of the tile coordinate <-> wire nt[m])
     P.nseg = 0;
     for (int m = 0; m < static_cast<int>(nt.size());) {
@@ -206,7 +212,7 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
     for (auto& rr : runs) {
         // as few stages as rmax allows, sizes as equal as possible (larger first)
         const int len = rr.second;
-        const int nst = (len + pl->rmax - 1) / pl->rmax;
+        const int nst = (len + rmax - 1) / rmax;
         int top = rr.first;
         for (int i = 0; i < nst; ++i) {
             const int r = len / nst + (i < len % nst ? 1 : 0);
@@ -216,21 +222,25 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
             S.wlo = top - r + 1;
             S.q = pos[S.wlo];
             S.cross = (top < n - 1) ? 1 : 0;
-            S.ngbits = tb - r;
+            S.ngbits = tb - r - pb0;
             S.tile_above = 0;
             for (int w : nt)
                 if (w > top) S.tile_above = 1;
-            for (int e = 0; e < kMaxR; ++e) S.img[e] = e < r ? static_cast<int32_t>(swizzle(1u << (S.q + e), pl->esize)) : 0;
+            for (int e = 0; e < kMaxR; ++e)
+                S.img[e] = e >= r ? 0
+                           : paired ? static_cast<int32_t>(swizzle(1u << (S.q + e - 1), 16))  // 16-byte pair units
+                                    : static_cast<int32_t>(swizzle(1u << (S.q + e), pl->esize));
             top -= r;
         }
     }
     // Lane order of each stage's group index.
-    const int SW = pl->esize == 8 ? 4 : 3;     // swizzle slot bits
-    const int wave_lanes = pl->esize == 8 ? 4 : 3;  // log2 lanes per SMEM wavefront
+    const bool unit16 = paired || pl->esize == 16;  // buffer-B access width: 16 bytes (pairs, complex128)
+    const int SW = unit16 ? 3 : 4;                    // swizzle slot bits
+    const int wave_lanes = unit16 ? 3 : 4;            // log2 lanes per SMEM wavefront
     for (int s = 0; s < P.nstages; ++s) {
         StageDesc& S = P.st[s];
         std::vector<int> others;
-        for (int p = 0; p < tb; ++p)
+        for (int p = pb0; p < tb; ++p)
             if (p < S.q || p >= S.q + S.r) others.push_back(p);
         std::vector<int> order;
         if (s == P.nstages - 1) {
@@ -242,8 +252,9 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
             std::vector<char> used_res(SW, 0), taken(tb, 0);
             for (int p : others) {
                 if (static_cast<int>(order.size()) >= wave_lanes) break;
-                if (!used_res[p % SW]) {
-                    used_res[p % SW] = 1;
+                const int res = (p - pb0) % SW;  // residue of the buffer-B unit bit
+                if (!used_res[res]) {
+                    used_res[res] = 1;
                     taken[p] = 1;
                     order.push_back(p);
                 }
@@ -256,6 +267,7 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
         S.lo_tw = S.hi_tw = 0;
         for (int i = 0; i < S.ngbits; ++i)
             if (P.p_wire[S.gpos[i]] > hi_w) (i < 5 ? S.lo_tw : S.hi_tw) = 1;
+        if (paired && P.p_wire[0] > hi_w) S.lo_tw = 1;  // the lane entries carry the pair wire's phase
         if (!S.lo_tw && !S.hi_tw) S.hi_tw = 1;  // keep one (all-ones) factor so tau is defined
     }
     int ntab = 0, nU = 0;
@@ -268,10 +280,21 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
     }
     P.ntab = ntab;
     P.nU = nU;
+    int maxr = 0;
+    for (int s = 0; s < P.nstages; ++s) maxr = std::max(maxr, static_cast<int>(P.st[s].r));
+    P.ntw = maxr;
     ph.smem = pass_smem_bytes(P, pl->esize);
     if (ph.smem > 227 * 1024 - 4096) return false;
+    // Two CTAs per SM (16 warps) when the pass's buffers fit twice into the
+    // SM's 228 KB of shared memory (with the static part and the 1 KB the
+    // system reserves per CTA) and its stages are small enough for 128
+    // registers per thread.
+    ph.minb = 1;
+    if (pl->dtype == QFT_C64 && pl->threads == 256 && maxr <= (paired ? 3 : 4) &&
+        2 * (ph.smem + 3 * 1024) <= 228 * 1024)
+        ph.minb = 2;
     const int64_t tiles = P.num_tiles;
-    ph.grid = static_cast<int>(std::min<int64_t>(tiles, pl->num_sms));
+    ph.grid = static_cast<int>(std::min<int64_t>(tiles, int64_t(pl->num_sms) * ph.minb));
     return true;
 }
 
@@ -530,6 +553,8 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
     pl->cmin = dtype == QFT_C64 ? 4 : 3;  // HBM runs of >= 128 bytes
     pl->rmax = kMaxStageR;
     pl->threads = 256;
+    pl->pairing = false;
+    bool rmax_given = false;
     if (opts) {
         if (opts->order != QFT_ORDER_NATURAL && opts->order != QFT_ORDER_BITREV) { delete pl; return QFT_ERR_BAD_ARG; }
         pl->order = opts->order;
@@ -559,7 +584,9 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
             pl->threads = opts->threads;
             if (pl->threads == 512) pl->rmax = 4;
         }
+        pl->pairing = opts->paired && dtype == QFT_C64 && pl->threads == 256 && !pl->precision;
         if (opts->max_stage_bits) {
+            rmax_given = true;
             if (opts->max_stage_bits < 1 || opts->max_stage_bits > (pl->threads == 512 ? 4 : kMaxStageR)) {
                 delete pl;
                 return QFT_ERR_BAD_ARG;
@@ -567,6 +594,10 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
             pl->rmax = opts->max_stage_bits;
         }
     }
+    // complex64 tiles of <= 2^12 amplitudes fit two CTAs per SM; blocks of <= 4
+    // wires keep the kernel within the 128 registers that needs.
+    if (dtype == QFT_C64 && !pl->precision && pl->threads == 256 && pl->TB <= 12 && !rmax_given)
+        pl->rmax = std::min(pl->rmax, 4);
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) {
         int sms = 0;
@@ -681,7 +712,7 @@ int execute_range(qft_plan_t pl, void* d_state, void* d_workspace, double* d_sca
             e = launch_tc_pass(pl->dir, pl->precision, pl->maps[i], P, ph.tc_a_hi, ph.tc_a_lo, ph.tc_kpad,
                                ph.tc_ncols, ph.grid, ph.smem, st);
         else
-            e = launch_pass(pl->dtype, pl->dir, pl->threads, pl->maps[i], P, ph.grid, ph.smem, st);
+            e = launch_pass(pl->dtype, pl->dir, pl->threads, ph.minb, pl->maps[i], P, ph.grid, ph.smem, st);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return QFT_OK;
@@ -724,7 +755,7 @@ int qft_plan_describe_pass(qft_plan_t pl, int i, long long* out, int cap) {
     for (int d = 0; d < kMaxDims; ++d) v.push_back((long long)ph.gdim[d]);
     for (int d = 0; d < 4; ++d) v.push_back((long long)ph.gstride[d]);
     for (int d = 0; d < kMaxDims; ++d) v.push_back((long long)ph.box[d]);
-    v.insert(v.end(), {ph.grid, (long long)ph.smem, ph.in_buf, ph.out_buf, P.npartials, ph.run_bits});
+    v.insert(v.end(), {ph.grid, (long long)ph.smem, ph.in_buf, ph.out_buf, P.npartials, ph.run_bits, P.paired, ph.minb});
     for (size_t j = 0; j < v.size() && static_cast<int>(j) < cap; ++j) out[j] = v[j];
     return static_cast<int>(v.size());
 }

@@ -41,9 +41,16 @@ def parse(rec):
     P["gdim"] = [nx() for _ in range(K_MAX_DIMS)]
     P["gstride"] = [nx() for _ in range(4)]
     P["box"] = [nx() for _ in range(K_MAX_DIMS)]
-    for k in ("grid", "smem", "in_buf", "out_buf", "npartials", "run_bits"):
+    for k in ("grid", "smem", "in_buf", "out_buf", "npartials", "run_bits", "paired", "minb"):
         P[k] = nx()
     return P
+
+
+def _groups(P, S):
+    """Group bits of a stage as the emulation enumerates them: a paired stage's
+    thread also covers tile bit 0 (its SIMD lane), so it is one more group bit."""
+    gpos = list(S["gpos"][:S["ngbits"]])
+    return gpos + [0] if P["paired"] else gpos
 
 
 def _brev(v, length):
@@ -67,13 +74,17 @@ def check_structure(P, esize):
     assert sorted(outs) == list(range(n)), "output address bits must be a permutation"
     assert sum(s["len"] for s in P["seg"]) == n - tb
     assert P["num_tiles"] == 1 << (n - tb)
+    pb0 = 1 if P["paired"] else 0
+    if P["paired"]:
+        assert esize == 8 and not (P["first"] and P["last"])
+        assert all(s["q"] >= 1 and s["r"] <= 4 for s in P["st"]), "tile bit 0 is the pair lane, blocks <= 4 wires"
     for s in P["st"]:
-        assert 1 <= s["r"] <= K_MAX_R and s["ngbits"] == tb - s["r"]
+        assert 1 <= s["r"] <= K_MAX_R and s["ngbits"] == tb - s["r"] - pb0
         assert 0 <= s["q"] and s["q"] + s["r"] <= tb
         for e in range(s["r"]):
             assert P["p_wire"][s["q"] + e] == s["wlo"] + e, "stage block must be consecutive wires on consecutive tile bits"
         others = sorted(s["gpos"][:s["ngbits"]])
-        assert others == [p for p in range(tb) if not (s["q"] <= p < s["q"] + s["r"])]
+        assert others == [p for p in range(pb0, tb) if not (s["q"] <= p < s["q"] + s["r"])]
     seg_wires = [s["wire"] + i for s in P["seg"] for i in range(s["len"])]
     uoff = 0
     for s in P["st"]:
@@ -81,6 +92,7 @@ def check_structure(P, esize):
         assert s["tile_above"] == int(any(w > hi for w in seg_wires)), "per-tile twiddle flag"
         assert s["uoff"] == uoff
         lanes_above = any(P["p_wire"][s["gpos"][i]] > hi for i in range(min(5, s["ngbits"])))
+        lanes_above = lanes_above or (P["paired"] and P["p_wire"][0] > hi)
         high_above = any(P["p_wire"][s["gpos"][i]] > hi for i in range(5, s["ngbits"]))
         assert s["lo_tw"] == int(lanes_above) and s["hi_tw"] == int(high_above or not lanes_above)
         uoff += s["r"]
@@ -102,6 +114,9 @@ def check_structure(P, esize):
         for d in range(1, K_MAX_DIMS):
             assert P["gstride"][d - 1] % 16 == 0 and P["gstride"][d - 1] < (1 << 40)
     assert P["smem"] <= 227 * 1024
+    if P["minb"] == 2:  # two CTAs per SM: both fit in shared memory, stages within the 128-register kernel
+        assert 2 * (P["smem"] + 3 * 1024) <= 228 * 1024
+        assert max(s["r"] for s in P["st"]) <= (3 if P["paired"] else 4)
 
 
 def _gather_tma(P, src_u64, tiles):
@@ -178,14 +193,15 @@ def run_pass(P, src, dst, esize, sign, scale_mode, norm_sq):
     Bbuf = A.copy()
     written = None
     for si, S in enumerate(P["st"]):
-        R, q, ng = S["r"], S["q"], 1 << S["ngbits"]
+        gpos = _groups(P, S)
+        R, q, ng = S["r"], S["q"], 1 << len(gpos)
         g = np.arange(ng, dtype=np.int64)
         pb = np.zeros(ng, dtype=np.int64)
         iw = np.zeros(ng, dtype=np.uint64)
         ob = np.zeros(ng, dtype=np.int64)
-        for i in range(S["ngbits"]):
+        for i in range(len(gpos)):
             bit = (g >> i) & 1
-            p = S["gpos"][i]
+            p = gpos[i]
             pb |= bit << p
             iw |= bit.astype(np.uint64) << np.uint64(P["p_wire"][p])
             ob += bit << P["p_out"][p]

@@ -21,9 +21,9 @@ def test_best_opts_reads_cache(tmp_path, monkeypatch):
 
 def test_every_candidate_is_a_valid_plan():
     for dt, cands in autotune.CANDIDATES.items():
-        for tb, cb, sb, th in cands:
+        for cand in cands:
             for n in (8, 14, 20, 26, 30):
-                q.Plan(n, -1, q.FORWARD, dt, tile_bits=tb, coalesce_bits=cb, max_stage_bits=sb, threads=th)
+                q.Plan(n, -1, q.FORWARD, dt, **cand)
 
 
 @pytest.mark.gpu

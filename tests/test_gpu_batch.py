@@ -24,7 +24,7 @@ def rel(a, b):
     return float(torch.linalg.vector_norm(a - b) / max(torch.linalg.vector_norm(b), 1e-300))
 
 
-def make_batch(count, nmin, nmax, dt, order, seed, direction=q.FORWARD):
+def make_batch(count, nmin, nmax, dt, order, seed, direction=q.FORWARD, opts=None):
     rng = np.random.default_rng(seed)
     td = torch.complex64 if dt == "c64" else torch.complex128
     plans, xs, ks = {}, [], []
@@ -37,14 +37,18 @@ def make_batch(count, nmin, nmax, dt, order, seed, direction=q.FORWARD):
     for i, (n, k, kind) in enumerate(specs):
         key = (n, k)
         if key not in plans:
-            plans[key] = q.Plan(n, k, direction, dt, order)
+            plans[key] = q.Plan(n, k, direction, dt, order, **(opts or {}))
         xs.append(torch.from_numpy(qft_inputs.make(kind, n, seed * 1000 + i)).to(td).cuda())
     return specs, plans, xs
 
 
-@pytest.mark.parametrize("dt,order", [("c64", 0), ("c64", 1), ("c128", 0)])
-def test_batch_matches_single_transforms(oracle_mod, dt, order):
-    specs, plans, xs = make_batch(96, 3, 17, dt, order, seed=7)
+# plan shapes: defaults; 2^12-amplitude tiles (the batch runs two CTAs per SM);
+# paired complex64 stages
+@pytest.mark.parametrize("dt,order,opts", [("c64", 0, None), ("c64", 1, None), ("c128", 0, None),
+                                           ("c64", 0, {"tile_bits": 12}), ("c64", 1, {"tile_bits": 12}),
+                                           ("c64", 0, {"paired": 1})])
+def test_batch_matches_single_transforms(oracle_mod, dt, order, opts):
+    specs, plans, xs = make_batch(96, 3, 17, dt, order, seed=7, opts=opts)
     states = [x.clone() for x in xs]
     scales = torch.zeros(len(xs), dtype=torch.float64, device="cuda")
     b = q.Batch([plans[(n, k)] for n, k, _ in specs], states, q.SCALE_STATE, scale_out=scales)

@@ -273,3 +273,29 @@ def test_max_size_round_trip(n, dt):
     assert _chunked_norm(state, x, 1.0 / x_norm) <= 2 * TOL[dt](n)
     del state, x, ws
     torch.cuda.empty_cache()
+
+
+# Kernel variants the planner selects from its options: two CTAs per SM
+# (complex64 tiles of <= 2^12 amplitudes), the paired packed-FP32x2 stages,
+# both together, and small tiles.  Every variant must match the oracle.
+VARIANTS = {
+    "two_ctas": dict(tile_bits=12),
+    "two_ctas_c3": dict(tile_bits=12, coalesce_bits=3),
+    "paired": dict(paired=1),
+    "paired_two_ctas": dict(tile_bits=12, paired=1, max_stage_bits=3),
+    "tile11": dict(tile_bits=11),
+}
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("direction", [-1, 1])
+@pytest.mark.parametrize("n,k", [(14, -1), (17, 5), (20, -1), (23, 9)])
+def test_kernel_variants(oracle_mod, variant, order, direction, n, k):
+    x = qft_inputs.make(qft_inputs.KINDS[(n + direction) % 3], n, seed=n * 7 + order)
+    p = q.Plan(n, k, direction, "c64", order, **VARIANTS[variant])
+    got, s_in = run(x, n, k, direction, "c64", order, plan=p)
+    ref, s_ref = oracle_mod.qft(as_dt(x, "c64"), k, direction, 0, order == 0)
+    assert_close(got, ref, "c64", n)
+    assert abs(s_in - s_ref) <= 1e-6 * s_ref
+

@@ -98,3 +98,15 @@ def test_plan_argument_errors():
         q.Plan(10, direction=2)
     with pytest.raises(ValueError):
         q.Plan(10, dtype="c32")
+
+
+def test_variant_plans_use_the_intended_kernels():
+    """The planner actually selects two CTAs per SM / paired stages for these options."""
+    import plan_emulator as pe
+    descs = lambda p: [pe.parse(p.describe_pass(i)) for i in range(p.info().passes)]  # noqa: E731
+    d = descs(q.Plan(26, -1, q.FORWARD, "c64", 0, tile_bits=12))
+    assert all(P["minb"] == 2 and not P["paired"] for P in d)
+    d = descs(q.Plan(26, -1, q.FORWARD, "c64", 0, paired=1))
+    assert all(P["paired"] for P in d)
+    d = descs(q.Plan(26, -1, q.FORWARD, "c64", 0, tile_bits=12, paired=1, max_stage_bits=3))
+    assert all(P["paired"] and P["minb"] == 2 for P in d)
