@@ -51,6 +51,10 @@ def parse_args():
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--k", type=int, default=-1)
     ap.add_argument("--threads", type=int, default=0, help="pass-kernel CTA size (256 or 512; 0 = default)")
+    ap.add_argument("--tile-bits", type=int, default=0,
+                    help="plan shape override (with --coalesce-bits, --max-stage-bits); 0 = the tuned shape")
+    ap.add_argument("--coalesce-bits", type=int, default=0)
+    ap.add_argument("--max-stage-bits", type=int, default=0)
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -137,7 +141,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("qft_pass.cu", "plan.hpp"):
+    for f in ("qft_pass.cu", "qft_device.cuh", "qft_pair.cuh", "plan.hpp"):
         h.update(open(os.path.join(ROOT, "paper_2606_18981_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -479,7 +483,9 @@ def run_ours(args, world, rank, local):
     n, dt, k = args.n, args.dtype, args.k
     N = 1 << n
     eb = 8 if dt == "c64" else 16
-    plan = q.Plan(n, k, q.FORWARD, dt, q.ORDER_NATURAL, threads=args.threads, tuned=True)
+    shape = dict(tile_bits=args.tile_bits, coalesce_bits=args.coalesce_bits, max_stage_bits=args.max_stage_bits)
+    override = any(shape.values())
+    plan = q.Plan(n, k, q.FORWARD, dt, q.ORDER_NATURAL, threads=args.threads, tuned=not override, **shape)
     info = plan.info()
     P = info.passes
     stream = torch.cuda.Stream(device=dev)
