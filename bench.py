@@ -162,6 +162,21 @@ def ncu_traffic(n, dt):
         return None
 
 
+def whole_job_rate(ms_local, units_per_rank, world, device="cpu"):
+    """Replicas: every rank processes units_per_rank in ms_local.  The job's time
+    is the slowest rank's (all-reduce MAX over the ranks) and its rate is the
+    units of all ranks over that time.  Returns (ms_max, units per second)."""
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * units_per_rank / (ms_max / 1000.0)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -516,13 +531,7 @@ def run_ours(args, world, rank, local):
     status = plan.status(ws, stream)
     if status != 0:
         raise RuntimeError(f"device status {status}")
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * N / (ms_max / 1000.0)
+    ms_max, value = whole_job_rate(ms, N, world, dev)
 
     # end to end through host buffers
     e2e = None
@@ -548,13 +557,8 @@ def run_ours(args, world, rank, local):
         b.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e_ms = a.elapsed_time(b) / e_steps
-        e_t = torch.tensor([e_ms], device=dev)
-        if world > 1:
-            import torch.distributed as dist
-
-            dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * N / (float(e_t.item()) / 1000.0), "unit": UNIT, "ms_per_step": float(e_t.item()),
+        e_ms_max, e_value = whole_job_rate(a.elapsed_time(b) / e_steps, N, world, dev)
+        e2e = {"value": e_value, "unit": UNIT, "ms_per_step": e_ms_max,
                "h2d_bytes_per_step": N * eb, "d2h_bytes_per_step": N * eb, "steps": e_steps}
         del host_in, host_out
 

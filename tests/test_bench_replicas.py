@@ -1,0 +1,52 @@
+"""The N > 1 bench path (independent replicas, one per GPU): whole-job time is
+the slowest rank's and the rate counts every rank's work.  Runs as two gloo
+ranks on CPU."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    import bench
+
+    ms, rate = bench.whole_job_rate(10.0 + 5.0 * rank, 1000, world)
+    dist.barrier()
+    out[rank] = (ms, rate)
+    dist.destroy_process_group()
+
+
+def test_whole_job_rate_two_gloo_ranks():
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    for r in (0, 1):
+        ms, rate = res[r]
+        assert ms == pytest.approx(15.0)  # the slower rank's time, on every rank
+        assert rate == pytest.approx(2 * 1000 / 0.015)  # both ranks' units
+
+
+def test_whole_job_rate_single_rank():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    ms, rate = bench.whole_job_rate(4.0, 1 << 20, 1)
+    assert ms == 4.0 and rate == pytest.approx((1 << 20) / 0.004)
