@@ -353,7 +353,394 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(tcols));
 }
 
+// ---------------------------------------------------------------- fast path
+//
+// Tiles of 2^12 amplitudes with one block of R = 4..6 wires (every pass of a
+// transform of n >= 13 wires).  256 threads; thread t owns column c = t % NG
+// of the tile (NG = 2^{12-R} columns = the GEMM's N) and the 16 consecutive
+// block indices j of chunk t / NG, so lanes run along consecutive columns.
+// Per tile: TMA load (double-buffered, the tile after next streams in during
+// the GEMM), cross twiddles and column scaling in registers, operands written
+// as 16-byte core-matrix rows, the MMAs from one thread, all TMEM loads of a
+// 16-column chunk in flight before one wait, and the outputs stored from the
+// result staging area with lanes along columns.
+
+constexpr int kTcFastThreads = 256;
+
+// Round 16 consecutive K entries of one operand row (k0 a multiple of 16) to
+// the operand format and write them as 16-byte core-matrix rows at p0, p0 +
+// 128, ...; the rounded values come back in r.
+template <int PREC>
+__device__ __forceinline__ void write_op16(unsigned char* p0, const float (&v)[16], float (&r)[16]) {
+    if constexpr (TcOp<PREC>::bytes == 2) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float a = v[m * 8 + 2 * h], b = v[m * 8 + 2 * h + 1];
+                if constexpr (PREC == TC_BF16 || PREC == TC_BF16X3) {
+                    const __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
+                    const float2 f = __bfloat1622float2(t);
+                    r[m * 8 + 2 * h] = f.x;
+                    r[m * 8 + 2 * h + 1] = f.y;
+                    w[h] = *reinterpret_cast<const uint32_t*>(&t);
+                } else {
+                    const __half2 t = __floats2half2_rn(a, b);
+                    const float2 f = __half22float2(t);
+                    r[m * 8 + 2 * h] = f.x;
+                    r[m * 8 + 2 * h + 1] = f.y;
+                    w[h] = *reinterpret_cast<const uint32_t*>(&t);
+                }
+            }
+            *reinterpret_cast<uint4*>(p0 + m * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[h]) : "f"(v[m * 4 + h]));
+                r[m * 4 + h] = __uint_as_float(w[h]);
+            }
+            *reinterpret_cast<uint4*>(p0 + m * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+template <int PREC, int R>
+struct TcFast {
+    static constexpr int EB = TcOp<PREC>::bytes;
+    static constexpr int J = 1 << R;
+    static constexpr int NG = 1 << (12 - R);
+    static constexpr int KPAD = 2 * J;
+    static constexpr int KSTEP = 32 / EB;  // K per MMA
+    static constexpr int KSTEPS = KPAD / KSTEP;
+    static constexpr int NACC = (KSTEPS < 512 / NG) ? KSTEPS : 512 / NG;  // accumulators (TMEM: NACC x NG <= 512)
+    static constexpr uint32_t TILE_BYTES = 4096u * 8u;
+    static constexpr size_t D_BYTES = size_t(2 * J) * NG * 4;
+    static constexpr size_t A_BYTES = size_t(128) * KPAD * EB;
+    static constexpr size_t B_BYTES = size_t(NG) * KPAD * EB;
+    static constexpr int SPLIT = TcOp<PREC>::split;
+    static size_t smem(int ntab, int ntw) {
+        return 2 * size_t(TILE_BYTES) + D_BYTES + A_BYTES * (SPLIT ? 2 : 1) + B_BYTES * (SPLIT ? 2 : 1) +
+               size_t(ntab) * (size_t(ntw) * 8 + 8 + 4);
+    }
+};
+
+template <int DIR, int PREC, int R>
+__global__ void __launch_bounds__(kTcFastThreads, 1)
+    qft_tc_fast_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassParams P,
+                       const __grid_constant__ TcParams Q) {
+    using V = float2;
+    using F = TcFast<PREC, R>;
+    using Op = TcOp<PREC>;
+    constexpr int NT = kTcFastThreads;
+    constexpr int J = F::J, NG = F::NG, KPAD = F::KPAD, EB = F::EB;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar_load[2];
+    __shared__ __align__(8) uint64_t mbar_mma;
+    __shared__ uint32_t s_taddr;
+    __shared__ double red[NT / 32];
+    __shared__ float s_amax[NT];
+    __shared__ int s_exp[NG];
+    __shared__ __align__(16) V Ubuf[kMaxR * kMaxStages];
+
+    const int tid = threadIdx.x;
+    const StageDesc& S = P.st[0];
+    unsigned char* const T0 = smem_raw;  // two tile buffers
+    float* const D = reinterpret_cast<float*>(smem_raw + 2 * F::TILE_BYTES);  // 2J x NG results
+    unsigned char* const A_hi = smem_raw + 2 * F::TILE_BYTES + F::D_BYTES;
+    unsigned char* const A_lo = A_hi + F::A_BYTES;
+    unsigned char* const B_hi = A_lo + (F::SPLIT ? F::A_BYTES : 0);
+    unsigned char* const B_lo = B_hi + F::B_BYTES;
+    unsigned char* const tab_raw = B_lo + (F::SPLIT ? F::B_BYTES : 0);
+    GroupTab<V> tab;
+    tab.ntab = P.ntab;
+    tab.tw = reinterpret_cast<V*>(tab_raw);
+    tab.ob = reinterpret_cast<int64_t*>(tab_raw + size_t(P.ntw) * sizeof(V) * P.ntab);
+    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (size_t(P.ntw) * sizeof(V) + 8) * P.ntab);
+
+    build_group_tables<float, DIR, NT>(P, tab);
+    {
+        const uint4* src = static_cast<const uint4*>(Q.a_hi);
+        for (size_t i = tid; i < F::A_BYTES / 16; i += NT) reinterpret_cast<uint4*>(A_hi)[i] = src[i];
+        if (F::SPLIT) {
+            src = static_cast<const uint4*>(Q.a_lo);
+            for (size_t i = tid; i < F::A_BYTES / 16; i += NT) reinterpret_cast<uint4*>(A_lo)[i] = src[i];
+        }
+    }
+    constexpr uint32_t kTcols = static_cast<uint32_t>(NG * F::NACC) < 32u ? 32u : static_cast<uint32_t>(NG * F::NACC);
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                     "r"(kTcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar_load[0], 1);
+        mbar_init(&mbar_load[1], 1);
+        mbar_init(&mbar_mma, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+
+    float scale = 1.f;
+    if (P.last) {  // never also the first pass here: scale_in from the first pass's partials
+        double s = 0.0;
+        for (int i = tid; i < P.npartials; i += NT) s += P.partials[i];
+        const double scale_in = sqrt(block_sum<NT>(s, red));
+        scale = static_cast<float>(output_factor(P, scale_in));
+        if (blockIdx.x == 0 && tid == 0) {
+            P.meta[0] = scale_in;
+            if (P.user_scale) *P.user_scale = scale_in;
+        }
+    }
+    constexpr uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(Op::fmt) << 7) |
+                               (static_cast<uint32_t>(Op::fmt) << 10) | (static_cast<uint32_t>(NG >> 3) << 17) |
+                               (static_cast<uint32_t>(128 >> 4) << 24);
+    constexpr int KC = 16 / EB;
+    constexpr uint32_t lbo = 128u, sbo = static_cast<uint32_t>(KPAD / KC) * 128u;
+    constexpr uint32_t koff_step = static_cast<uint32_t>(F::KSTEP / KC) * 128u;
+
+    const int c = tid % NG, jq = tid / NG;  // column, chunk of 16 block indices
+    const int lo5 = P.tab_off[0] + (c & 31), hi5 = P.tab_off[0] + 32 + (c >> 5);
+    const uint32_t q = static_cast<uint32_t>(S.q);
+
+    double norm_acc = 0.0;
+    uint32_t ph_load = 0u, ph_mma = 0u;
+    bool aborted = false;
+    int64_t tile = blockIdx.x;
+    if (tid == 0 && !P.test_skip_first_load) {
+        if (tile < P.num_tiles) issue_tile_load(P, &tmap, tile, T0, &mbar_load[0], F::TILE_BYTES);
+        if (tile + gridDim.x < P.num_tiles)
+            issue_tile_load(P, &tmap, tile + gridDim.x, T0 + F::TILE_BYTES, &mbar_load[1], F::TILE_BYTES);
+    }
+    for (int k = 0; tile < P.num_tiles; tile += gridDim.x, ++k) {
+        const int buf = k & 1;
+        const V* const T = reinterpret_cast<const V*>(T0 + buf * F::TILE_BYTES);
+        compute_tile_twiddles<float, DIR>(P, tile, Ubuf);
+        uint64_t I_tile;
+        int64_t out_tile;
+        tile_coords(P, tile, I_tile, out_tile);
+        const bool ok = mbar_wait_bounded(&mbar_load[buf], (ph_load >> buf) & 1u, P.wait_limit_ns);
+        ph_load ^= 1u << buf;
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        // 1. this thread's 16 amplitudes: cross twiddle, column scale, operands
+        V x[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = T[tab.pb[lo5] | tab.pb[hi5] | (static_cast<uint32_t>(jq * 16 + i) << q)];
+        if (P.first) {
+            float a = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a += x[i].x * x[i].x + x[i].y * x[i].y;
+            norm_acc += static_cast<double>(a);
+        }
+        if (S.cross) {
+            V tau[R];
+#pragma unroll
+            for (int e = 0; e < R; ++e) {
+                if (S.lo_tw && S.hi_tw) tau[e] = cmul(tab.tw[e * tab.ntab + lo5], tab.tw[e * tab.ntab + hi5]);
+                else if (S.lo_tw) tau[e] = tab.tw[e * tab.ntab + lo5];
+                else tau[e] = tab.tw[e * tab.ntab + hi5];
+                if (S.tile_above) tau[e] = cmul(tau[e], Ubuf[S.uoff + e]);
+            }
+            // block index j = jq * 16 + i: the chunk bits (>= 4) give one factor
+            V bq = make_float2(1.f, 0.f);
+#pragma unroll
+            for (int e = 4; e < R; ++e)
+                if ((jq >> (e - 4)) & 1) bq = cmul(bq, tau[e]);
+            V tl[4], th[4];
+            tl[1] = tau[0];
+            tl[2] = tau[1];
+            tl[3] = cmul(tau[0], tau[1]);
+            th[0] = bq;
+            th[1] = cmul(bq, tau[2]);
+            th[2] = cmul(bq, tau[3]);
+            th[3] = cmul(th[1], tau[3]);
+#pragma unroll
+            for (int i = 1; i < 16; ++i)
+                if (i & 3) x[i] = cmul(x[i], tl[i & 3]);
+            if (jq) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) x[i] = cmul(x[i], th[i >> 2]);
+            } else {
+#pragma unroll
+                for (int i = 4; i < 16; ++i) x[i] = cmul(x[i], th[i >> 2]);
+            }
+        }
+        float amax = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) amax = fmaxf(amax, fmaxf(fabsf(x[i].x), fabsf(x[i].y)));
+        s_amax[tid] = amax;
+        __syncthreads();
+        float cm = 0.f;
+#pragma unroll
+        for (int h = 0; h < J / 16; ++h) cm = fmaxf(cm, s_amax[h * NG + c]);
+        // exponent so that the column's largest component is near 2^14
+        int ex = 0;
+        if (cm > 0.f) {
+            const int e8 = static_cast<int>((__float_as_uint(cm) >> 23) & 255u);
+            ex = 14 - (e8 - 127);
+            ex = ex < -100 ? -100 : (ex > 100 ? 100 : ex);
+        }
+        if (jq == 0) s_exp[c] = ex;
+        {
+            const float sc = __uint_as_float(static_cast<uint32_t>(ex + 127) << 23);
+            float re[16], im[16], rr[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                re[i] = x[i].x * sc;
+                im[i] = x[i].y * sc;
+            }
+            const uint32_t ore = op_offset<EB>(c, jq * 16, KPAD), oim = op_offset<EB>(c, J + jq * 16, KPAD);
+            write_op16<PREC>(B_hi + ore, re, rr);
+            if (F::SPLIT) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) re[i] -= rr[i];
+                write_op16<PREC>(B_lo + ore, re, rr);
+            }
+            write_op16<PREC>(B_hi + oim, im, rr);
+            if (F::SPLIT) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) im[i] -= rr[i];
+                write_op16<PREC>(B_lo + oim, im, rr);
+            }
+        }
+        fence_proxy_async_smem();  // B written by threads, read by the tensor cores
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // 2. prefetch the tile after next into the consumed buffer; the GEMM
+        if (tid == 0) {
+            const int64_t nt = tile + 2 * static_cast<int64_t>(gridDim.x);
+            if (nt < P.num_tiles) issue_tile_load(P, &tmap, nt, T0 + buf * F::TILE_BYTES, &mbar_load[buf], F::TILE_BYTES);
+            const uint32_t a0 = smem_u32(A_hi), a1 = smem_u32(A_lo), b0 = smem_u32(B_hi), b1 = smem_u32(B_lo);
+#pragma unroll
+            for (int kb = 0; kb < F::KSTEPS; ++kb) {
+                const uint32_t ko = static_cast<uint32_t>(kb) * koff_step;
+                const uint32_t dst = taddr + static_cast<uint32_t>(kb % F::NACC) * NG;
+                const uint32_t acc = kb >= F::NACC ? 1u : 0u;
+                umma<Op::kind>(dst, umma_desc(a0 + ko, lbo, sbo), umma_desc(b0 + ko, lbo, sbo), idesc, acc);
+                if (F::SPLIT) {
+                    umma<Op::kind>(dst, umma_desc(a1 + ko, lbo, sbo), umma_desc(b0 + ko, lbo, sbo), idesc, 1);
+                    umma<Op::kind>(dst, umma_desc(a0 + ko, lbo, sbo), umma_desc(b1 + ko, lbo, sbo), idesc, 1);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar_mma)));
+        }
+        const bool okm = mbar_wait_bounded(&mbar_mma, ph_mma, P.wait_limit_ns);
+        ph_mma ^= 1u;
+        if (__syncthreads_or(!okm)) {
+            aborted = true;
+            break;
+        }
+        tc_fence_after();
+        // 3. accumulators -> D: warp w reads TMEM lanes 32 (w & 3).. (rows m) for
+        //    half (w >> 2) of the columns, 16 columns per step, the accumulators
+        //    summed pairwise
+        {
+            const int w = tid >> 5, l = tid & 31, qd = w & 3, chalf = w >> 2;
+            const int m = qd * 32 + l;
+            if (qd * 32 < 2 * J) {
+#pragma unroll 1
+                for (int cc = chalf * (NG / 2); cc < (chalf + 1) * (NG / 2); cc += 16) {
+                    uint32_t v[F::NACC][16];
+#pragma unroll
+                    for (int a = 0; a < F::NACC; ++a) {
+                        const uint32_t addr = taddr + (static_cast<uint32_t>(qd * 32) << 16) +
+                                              static_cast<uint32_t>(a * NG + cc);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                            : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                              "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]),
+                              "=r"(v[a][11]), "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
+                            : "r"(addr));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float s[F::NACC];
+#pragma unroll
+                        for (int a = 0; a < F::NACC; ++a) s[a] = __uint_as_float(v[a][j]);
+#pragma unroll
+                        for (int width = 1; width < F::NACC; width *= 2)
+#pragma unroll
+                            for (int a = 0; a + width < F::NACC; a += 2 * width) s[a] += s[a + width];
+                        D[m * NG + cc + j] = s[0];
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        // 4. outputs: amplitude j of column c is (D[j][c], D[J + j][c]) * 2^-ex * scale
+        {
+            const float f = scale * __uint_as_float(static_cast<uint32_t>(127 - s_exp[c]) << 23);
+            int64_t base = out_tile + tab.ob[lo5] + tab.ob[hi5];
+#pragma unroll
+            for (int e = 4; e < R; ++e)
+                if ((jq >> (e - 4)) & 1) base += int64_t(1) << P.p_out[S.q + e];
+            int64_t oo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) oo[e] = int64_t(1) << P.p_out[S.q + e];
+            V* __restrict__ out = static_cast<V*>(P.out) + base;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                int64_t o = 0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (i & (1 << e)) o += oo[e];
+                const int j = jq * 16 + i;
+                out[o] = make_float2(D[j * NG + c] * f, D[(J + j) * NG + c] * f);
+            }
+        }
+    }
+    if (aborted && tid == 0) {
+        atomicExch(P.status, -5);  // QFT_ERR_TIMEOUT
+        for (int b = 0; b < 2; ++b) mbar_wait_bounded(&mbar_load[b], (ph_load >> b) & 1u, P.wait_limit_ns);
+    }
+    if (!aborted && P.first) {
+        const double tot = block_sum<NT>(norm_acc, red);
+        if (tid == 0) P.partials[blockIdx.x] = tot;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcols));
+}
+
+// The fast path serves passes with 2^12-amplitude tiles, one block of 4..6
+// wires and more than one pass.
+static bool tc_fast_ok(const PassParams& P) {
+    return P.tb == 12 && P.nstages == 1 && P.st[0].r >= 4 && P.st[0].r <= 6 && !(P.first && P.last);
+}
+
+template <int PREC>
+static size_t tc_fast_smem(const PassParams& P) {
+    switch (P.st[0].r) {
+        case 4: return TcFast<PREC, 4>::smem(P.ntab, P.ntw);
+        case 5: return TcFast<PREC, 5>::smem(P.ntab, P.ntw);
+        default: return TcFast<PREC, 6>::smem(P.ntab, P.ntw);
+    }
+}
+
 size_t tc_smem_bytes(const PassParams& P, int prec, int kpad, int ncols) {
+    if (tc_fast_ok(P)) {
+        switch (prec) {
+            case TC_TF32: return tc_fast_smem<TC_TF32>(P);
+            case TC_BF16: return tc_fast_smem<TC_BF16>(P);
+            case TC_BF16X3: return tc_fast_smem<TC_BF16X3>(P);
+            case TC_FP16: return tc_fast_smem<TC_FP16>(P);
+            default: return tc_fast_smem<TC_FP16X3>(P);
+        }
+    }
     const int eb = prec == TC_TF32 ? 4 : 2;
     const bool split = prec == TC_BF16X3 || prec == TC_FP16X3;
     const size_t tile = (size_t(1) << P.tb) * 8;
@@ -364,9 +751,30 @@ size_t tc_smem_bytes(const PassParams& P, int prec, int kpad, int ncols) {
     return stage + a + b + 4 * 256 + size_t(P.ntab) * (kMaxR * 8 + 8 + 4);
 }
 
+template <int DIR, int PREC, int R>
+static cudaError_t launch_tc_fast_t(const CUtensorMap& map, const PassParams& P, const TcParams& Q, int grid,
+                                    size_t smem, cudaStream_t st) {
+    auto kern = qft_tc_fast_kernel<DIR, PREC, R>;
+    static thread_local size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    kern<<<grid, kTcFastThreads, smem, st>>>(map, P, Q);
+    return cudaGetLastError();
+}
+
 template <int DIR, int PREC>
 static cudaError_t launch_tc_t(const CUtensorMap& map, const PassParams& P, const TcParams& Q, int grid, size_t smem,
                                cudaStream_t st) {
+    if (tc_fast_ok(P)) {
+        switch (P.st[0].r) {
+            case 4: return launch_tc_fast_t<DIR, PREC, 4>(map, P, Q, grid, smem, st);
+            case 5: return launch_tc_fast_t<DIR, PREC, 5>(map, P, Q, grid, smem, st);
+            default: return launch_tc_fast_t<DIR, PREC, 6>(map, P, Q, grid, smem, st);
+        }
+    }
     auto kern = qft_tc_pass_kernel<DIR, PREC>;
     static thread_local size_t configured = 0;
     if (smem > configured) {

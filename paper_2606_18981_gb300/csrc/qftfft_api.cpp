@@ -414,7 +414,12 @@ int check_tensor_passes(qft_plan_s* pl) {
         if (ph.tc_ncols > 256 || 2 * J > 128) return QFT_ERR_UNSUPPORTED;
         ph.smem = tc_smem_bytes(P, pl->precision, ph.tc_kpad, ph.tc_ncols);
         if (ph.smem > 227 * 1024 - 4096) return QFT_ERR_UNSUPPORTED;
+        // the tensor-core kernels run one CTA per SM (each holds all 512 TMEM columns)
+        ph.minb = 1;
+        ph.grid = static_cast<int>(std::min<int64_t>(P.num_tiles, pl->num_sms));
     }
+    // the last pass sums one norm partial per CTA of the first pass
+    pl->passes.back().prm.npartials = pl->passes[0].grid;
     return QFT_OK;
 }
 
