@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--tile-bits", type=int, default=0,
                     help="plan shape override (with --coalesce-bits, --max-stage-bits); 0 = the tuned shape")
     ap.add_argument("--coalesce-bits", type=int, default=0)
+    ap.add_argument("--precision", default="native", choices=["native", "tf32", "bf16", "bf16x3", "fp16", "fp16x3"],
+                    help="complex64 only: run the transform on the tensor-core precision tier")
     ap.add_argument("--max-stage-bits", type=int, default=0)
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -499,6 +501,10 @@ def run_ours(args, world, rank, local):
     N = 1 << n
     eb = 8 if dt == "c64" else 16
     shape = dict(tile_bits=args.tile_bits, coalesce_bits=args.coalesce_bits, max_stage_bits=args.max_stage_bits)
+    prec = {"native": 0, "tf32": q.PREC_TF32, "bf16": q.PREC_BF16, "bf16x3": q.PREC_BF16X3, "fp16": q.PREC_FP16,
+            "fp16x3": q.PREC_FP16X3}[args.precision]
+    if prec:
+        shape = {"precision": prec}
     override = any(shape.values())
     plan = q.Plan(n, k, q.FORWARD, dt, q.ORDER_NATURAL, threads=args.threads, tuned=not override, **shape)
     info = plan.info()
@@ -567,8 +573,8 @@ def run_ours(args, world, rank, local):
     mean_launch_ms = statistics.mean(per_pass)
     achieved = bytes_per_launch / (mean_launch_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(n, dt), "peak_source": peak_src,
-                "kernel": "qft_pass_kernel", "bytes_per_launch": bytes_per_launch,
+                "traffic": None if prec else ncu_traffic(n, dt), "peak_source": peak_src,
+                "kernel": "qft_tc_fast_kernel" if prec else "qft_pass_kernel", "bytes_per_launch": bytes_per_launch,
                 "launch_ms": per_pass}
 
     extra = {}
@@ -624,7 +630,9 @@ def run_ours(args, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if dt == "c64" else "f64", "data": "synthetic",
-                "config": {"workload": workload_name(n, dt, k), "n": n, "amplitudes": N,
+                "config": {"workload": workload_name(n, dt, k) + ("" if not prec else
+                                                                 f", tensor-core tier {args.precision}"),
+                           "n": n, "amplitudes": N,
                            "dtype": "complex64" if dt == "c64" else "complex128", "passes": P,
                            "wires_per_pass": list(info.wires_per_pass)[:P],
                            "state_bytes": N * eb,

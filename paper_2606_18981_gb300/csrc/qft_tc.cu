@@ -445,12 +445,16 @@ __global__ void __launch_bounds__(kTcFastThreads, 1)
     __shared__ double red[NT / 32];
     __shared__ float s_amax[NT];
     __shared__ int s_exp[NG];
+    __shared__ int64_t s_obc[NG];
     __shared__ __align__(16) V Ubuf[kMaxR * kMaxStages];
 
     const int tid = threadIdx.x;
     const StageDesc& S = P.st[0];
     unsigned char* const T0 = smem_raw;  // two tile buffers
-    float* const D = reinterpret_cast<float*>(smem_raw + 2 * F::TILE_BYTES);  // 2J x NG results
+    // results, column-major: column c holds its 2J rows (Re then Im), 16-byte
+    // chunks XOR-swizzled by (c & 7) so that both the row-wise writes from
+    // tensor memory and the column-wise reads are conflict-free
+    float* const D = reinterpret_cast<float*>(smem_raw + 2 * F::TILE_BYTES);
     unsigned char* const A_hi = smem_raw + 2 * F::TILE_BYTES + F::D_BYTES;
     unsigned char* const A_lo = A_hi + F::A_BYTES;
     unsigned char* const B_hi = A_lo + (F::SPLIT ? F::A_BYTES : 0);
@@ -508,6 +512,10 @@ __global__ void __launch_bounds__(kTcFastThreads, 1)
     const int c = tid % NG, jq = tid / NG;  // column, chunk of 16 block indices
     const int lo5 = P.tab_off[0] + (c & 31), hi5 = P.tab_off[0] + 32 + (c >> 5);
     const uint32_t q = static_cast<uint32_t>(S.q);
+    bool jmajor = false;  // a block wire holds output address bit 0
+#pragma unroll
+    for (int e = 0; e < R; ++e) jmajor = jmajor || P.p_out[S.q + e] == 0;
+    if (jq == 0) s_obc[c] = tab.ob[lo5] + tab.ob[hi5];  // output offset of each column (tile-invariant)
 
     double norm_acc = 0.0;
     uint32_t ph_load = 0u, ph_mma = 0u;
@@ -673,15 +681,38 @@ __global__ void __launch_bounds__(kTcFastThreads, 1)
                         for (int width = 1; width < F::NACC; width *= 2)
 #pragma unroll
                             for (int a = 0; a + width < F::NACC; a += 2 * width) s[a] += s[a + width];
-                        D[m * NG + cc + j] = s[0];
+                        const int col = cc + j;
+                        D[col * (2 * J) + ((((m >> 2) ^ (col & 7)) << 2) | (m & 3))] = s[0];
                     }
                 }
             }
         }
         tc_fence_before();
         __syncthreads();
-        // 4. outputs: amplitude j of column c is (D[j][c], D[J + j][c]) * 2^-ex * scale
-        {
+        // 4. outputs: amplitude j of column c is (D[j][c], D[J + j][c]) * 2^-ex * scale.
+        //    Lanes run along the columns, unless a block wire holds output address
+        //    bit 0 (the first pass of a natural-order plan): then along j, so that
+        //    every warp store covers a contiguous output run.
+        if (jmajor) {
+            const int j = tid % J;
+            const int64_t jofs = out_tile + [&] {
+                int64_t o = 0;
+#pragma unroll
+                for (int e = 0; e < R; ++e)
+                    if ((j >> e) & 1) o += int64_t(1) << P.p_out[S.q + e];
+                return o;
+            }();
+            const int sre = ((j >> 2) << 2) | (j & 3), sim = (((J + j) >> 2) << 2) | (j & 3);
+            V* __restrict__ out = static_cast<V*>(P.out) + jofs;
+#pragma unroll 4
+            for (int kk = 0; kk < 16; ++kk) {
+                const int cc = tid / J + kk * (NT / J);
+                const int sw = (cc & 7) << 2;
+                const float f = scale * __uint_as_float(static_cast<uint32_t>(127 - s_exp[cc]) << 23);
+                const float* Dc = D + cc * (2 * J);
+                out[s_obc[cc]] = make_float2(Dc[sre ^ sw] * f, Dc[sim ^ sw] * f);
+            }
+        } else {
             const float f = scale * __uint_as_float(static_cast<uint32_t>(127 - s_exp[c]) << 23);
             int64_t base = out_tile + tab.ob[lo5] + tab.ob[hi5];
 #pragma unroll
@@ -691,16 +722,25 @@ __global__ void __launch_bounds__(kTcFastThreads, 1)
 #pragma unroll
             for (int e = 0; e < 4; ++e) oo[e] = int64_t(1) << P.p_out[S.q + e];
             V* __restrict__ out = static_cast<V*>(P.out) + base;
+            const float4* Dc = reinterpret_cast<const float4*>(D + c * (2 * J));
+            float re[16], im[16];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {  // rows jq*16 + 4h .. +3 (Re) and J + the same (Im)
+                const float4 a = Dc[((jq * 16) / 4 + h) ^ (c & 7)];
+                const float4 bb = Dc[((J + jq * 16) / 4 + h) ^ (c & 7)];
+                re[4 * h] = a.x; re[4 * h + 1] = a.y; re[4 * h + 2] = a.z; re[4 * h + 3] = a.w;
+                im[4 * h] = bb.x; im[4 * h + 1] = bb.y; im[4 * h + 2] = bb.z; im[4 * h + 3] = bb.w;
+            }
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 int64_t o = 0;
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                     if (i & (1 << e)) o += oo[e];
-                const int j = jq * 16 + i;
-                out[o] = make_float2(D[j * NG + c] * f, D[(J + j) * NG + c] * f);
+                out[o] = make_float2(re[i] * f, im[i] * f);
             }
         }
+
     }
     if (aborted && tid == 0) {
         atomicExch(P.status, -5);  // QFT_ERR_TIMEOUT
