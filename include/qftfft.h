@@ -171,7 +171,8 @@ int qft_execute_pass(qft_plan_t plan, int pass, void* d_state, void* d_workspace
  * (Batching is not in the paper, which times one transform at a time; it is
  * the same circuit per transform.)  All plans of a batch must share dtype and
  * direction.  Each transform's result, scale handling and accuracy are those
- * of qft_execute with the same plan. */
+ * of qft_execute with the same plan.  Plans of the tensor-core precision tier
+ * (qft_opts.precision != 0) are not batched: QFT_ERR_UNSUPPORTED. */
 typedef struct qft_batch_s* qft_batch_t;
 
 /* Bytes of caller-owned device workspace a batch of these plans needs

@@ -91,6 +91,7 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
     for (int i = 0; i < count; ++i) {
         if (!plans[i] || !d_states[i] || (reinterpret_cast<uintptr_t>(d_states[i]) & 255)) return QFT_ERR_BAD_ARG;
         if (plans[i]->dtype != plans[0]->dtype || plans[i]->dir != plans[0]->dir) return QFT_ERR_UNSUPPORTED;
+        if (plans[i]->precision) return QFT_ERR_UNSUPPORTED;  // tensor-core tier plans run only through qft_execute
     }
     if (workspace_bytes < qft_batch_workspace_size(plans, count)) return QFT_ERR_SIZE;
     auto fn = get_encode_fn();

@@ -100,3 +100,10 @@ def test_batch_inverse_round_trip():
     torch.cuda.synchronize()
     for st, x, (n, _, _) in zip(states, xs, specs):
         assert rel(st, x) <= 4e-6
+
+
+def test_batch_rejects_tensor_tier_plans():
+    p = q.Plan(14, -1, q.FORWARD, "c64", 0, precision=q.PREC_FP16X3)
+    x = torch.zeros(1 << 14, dtype=torch.complex64, device="cuda")
+    with pytest.raises(q.QftError):
+        q.Batch([p], [x], q.SCALE_STATE)
