@@ -143,7 +143,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("qft_pass.cu", "qft_device.cuh", "qft_pair.cuh", "plan.hpp"):
+    for f in ("qft_pass_kernels.cuh", "qft_device.cuh", "qft_pair.cuh", "plan.hpp"):
         h.update(open(os.path.join(ROOT, "paper_2606_18981_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -337,22 +337,28 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
            "amplitudes_per_s": amps / (ms / 1e3), "status": status, "launches_per_batch": 1,
            "graph": True, "plans": best,
            "ms_per_batch_by_plans": {name: t[0] for name, t in timed.items()}}
-    # the plain single-transform complex128 path on the same transforms
-    p128 = {key: q.Plan(key[0], key[1], q.FORWARD, "c128", q.ORDER_NATURAL, tuned=True) for key in plans}
-    ws = {key: p.alloc_workspace(dev) for key, p in p128.items()}
+    # the plain single-transform complex128 paths on the same transforms: the
+    # default double-float kernel and IEEE FP64
     buf = torch.empty(1 << 18, dtype=torch.complex128, device=dev)
     sub = specs[:1024]
-    for n, k, _ in sub[:16]:
-        p128[(n, k)].execute(buf[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
-    torch.cuda.synchronize()
-    a.record(stream)
-    for n, k, _ in sub:
-        p128[(n, k)].execute(buf[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
-    bb.record(stream)
-    torch.cuda.synchronize()
-    ms128 = a.elapsed_time(bb)
-    out["plain_c128_single"] = {"transforms": len(sub), "ms": ms128, "transforms_per_s": len(sub) / (ms128 / 1e3)}
+    for label, prec in (("plain_c128_single", 0), ("plain_c128_fp64_single", q.PREC_FP64)):
+        p128 = {key: q.Plan(key[0], key[1], q.FORWARD, "c128", q.ORDER_NATURAL, tuned=not prec, precision=prec)
+                for key in plans}
+        ws = {key: p.alloc_workspace(dev) for key, p in p128.items()}
+        for n, k, _ in sub[:16]:
+            p128[(n, k)].execute(buf[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for n, k, _ in sub:
+            p128[(n, k)].execute(buf[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
+        bb.record(stream)
+        torch.cuda.synchronize()
+        ms128 = a.elapsed_time(bb)
+        out[label] = {"transforms": len(sub), "ms": ms128, "transforms_per_s": len(sub) / (ms128 / 1e3)}
+        del p128, ws
     out["speedup_vs_plain_c128_single"] = out["transforms_per_s"] / out["plain_c128_single"]["transforms_per_s"]
+    out["speedup_vs_plain_c128_fp64_single"] = (out["transforms_per_s"] /
+                                                out["plain_c128_fp64_single"]["transforms_per_s"])
     return out
 
 
@@ -425,14 +431,17 @@ def tensor_tier_workload(q, torch, dev, stream):
     x = qft_inputs.gaussian(n, seed=24).astype(np.complex64)
     ref, _ = oracle.qft(x.astype(np.complex128), -1, -1, oracle.SCALE_STATE, True)
     xd = torch.from_numpy(x).to(dev)
-    tiers = {"native_fp32": q.PREC_NATIVE, "fp16x3": q.PREC_FP16X3, "bf16x3": q.PREC_BF16X3, "tf32": q.PREC_TF32,
-             "fp16": q.PREC_FP16, "bf16": q.PREC_BF16}
+    tiers = {"native_fp32": ("c64", q.PREC_NATIVE), "fp16x3": ("c64", q.PREC_FP16X3),
+             "bf16x3": ("c64", q.PREC_BF16X3), "tf32": ("c64", q.PREC_TF32), "fp16": ("c64", q.PREC_FP16),
+             "bf16": ("c64", q.PREC_BF16), "c128_double_float": ("c128", q.PREC_NATIVE),
+             "c128_fp64": ("c128", q.PREC_FP64)}
     out = {}
     a = torch.cuda.Event(enable_timing=True)
     bb = torch.cuda.Event(enable_timing=True)
-    for name, prec in tiers.items():
-        p = q.Plan(n, -1, q.FORWARD, "c64", q.ORDER_NATURAL, precision=prec)
-        st = xd.clone()
+    for name, (dt, prec) in tiers.items():
+        tdt = torch.complex64 if dt == "c64" else torch.complex128
+        p = q.Plan(n, -1, q.FORWARD, dt, q.ORDER_NATURAL, precision=prec)
+        st = xd.to(tdt, copy=True)
         ws = p.alloc_workspace(dev)
         p.execute(st, ws, q.SCALE_STATE, stream=stream)
         torch.cuda.synchronize()
@@ -444,8 +453,8 @@ def tensor_tier_workload(q, torch, dev, stream):
         bb.record(stream)
         torch.cuda.synchronize()
         ms24 = a.elapsed_time(bb) / 10
-        p20 = q.Plan(20, -1, q.FORWARD, "c64", q.ORDER_NATURAL, precision=prec)
-        bufs = torch.empty(256, 1 << 20, dtype=torch.complex64, device=dev)
+        p20 = q.Plan(20, -1, q.FORWARD, dt, q.ORDER_NATURAL, precision=prec)
+        bufs = torch.empty(256, 1 << 20, dtype=tdt, device=dev)
         ws20 = p20.alloc_workspace(dev)
         p20.execute(bufs[0], ws20, q.SCALE_STATE, stream=stream)
         torch.cuda.synchronize()
@@ -610,10 +619,11 @@ def run_ours(args, world, rank, local):
             extra["serving_poisson"] = serving_workload(q, torch, dev)
         except Exception as ex:
             extra["serving_poisson"] = {"error": str(ex)[:300]}
-        for name, (nn, ddt, kk) in {"aqft_k4_c64_n30": (30, "c64", 4), "plain_c128_n30": (30, "c128", -1),
-                                     "c64_n26": (26, "c64", -1), "c64_n33": (33, "c64", -1)}.items():
+        for name, (nn, ddt, kk, prc) in {"aqft_k4_c64_n30": (30, "c64", 4, 0), "c128_n30": (30, "c128", -1, 0),
+                                          "c128_fp64_n30": (30, "c128", -1, q.PREC_FP64),
+                                          "c64_n26": (26, "c64", -1, 0), "c64_n33": (33, "c64", -1, 0)}.items():
             try:
-                p2 = q.Plan(nn, kk, q.FORWARD, ddt, q.ORDER_NATURAL, tuned=True)
+                p2 = q.Plan(nn, kk, q.FORWARD, ddt, q.ORDER_NATURAL, tuned=not prc, precision=prc)
                 free, _ = torch.cuda.mem_get_info()
                 need = (1 << nn) * (8 if ddt == "c64" else 16) * 2 + (1 << 30)
                 if free < need:
@@ -646,7 +656,8 @@ def run_ours(args, world, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if dt == "c64" else "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32" if dt == "c64" else "f32x2 (double-float)",
+                "data": "synthetic",
                 "config": {"workload": workload_name(n, dt, k) + ("" if not prec else
                                                                  f", tensor-core tier {args.precision}"),
                            "n": n, "amplitudes": N,

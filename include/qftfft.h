@@ -94,11 +94,13 @@ typedef struct {
                                  kernel's bounded wait expires and reports QFT_ERR_TIMEOUT  */
     int threads;        /* CTA size of the pass kernel: 256 (stages <= 5 wires) or 512
                            (stages <= 4 wires); 0 = default                                 */
-    int precision;      /* QFT_PREC_*: 0 = CUDA cores in the dtype's own precision; otherwise
-                           complex64 only, each pass's fused block of <= 6 wires as a dense
-                           complex GEMM on the tensor cores (see enum qft_precision).  The
-                           block matrices are built and uploaded (plan-owned device memory)
-                           by the plan's first execute, which should precede any capture. */
+    int precision;      /* QFT_PREC_*: 0 = the default CUDA-core path (complex64 in FP32;
+                           complex128 in double-float, see QFT_PREC_FP64); 6 = complex128 in
+                           IEEE FP64 arithmetic; 1..5 = complex64 only, each pass's fused
+                           block of <= 6 wires as a dense complex GEMM on the tensor cores
+                           (see enum qft_precision).  The block matrices are built and
+                           uploaded (plan-owned device memory) by the plan's first execute,
+                           which should precede any capture. */
     int paired;         /* complex64: 1 = where a pass's lowest tile bit is a batch wire, each
                            thread runs the two groups that differ in it with packed FP32x2
                            arithmetic (blocks of <= 4 wires); 0 = default: one group per
@@ -108,9 +110,21 @@ typedef struct {
 
 /* Precision tier (complex64 plans): the block matrix and the data are rounded to
  * the operand format, products accumulate in FP32.  The x3 tiers split each
- * operand into hi + lo and add hi*hi + lo*hi + hi*lo. */
+ * operand into hi + lo and add hi*hi + lo*hi + hi*lo.
+ *
+ * complex128 plans compute by default in double-float arithmetic: every
+ * amplitude is an unevaluated sum of two FP32 numbers (about 48 significant
+ * bits) and all arithmetic runs on the FP32 pipe with error-free
+ * transformations, because GB300 executes FP64 at 1/64 of its FP32 rate.  The
+ * input and output stay IEEE complex128 in memory; the relative L2 error
+ * against the exact transform stays far inside 1e-13 n.  Before the first pass
+ * a pre-pass reads the state once for its largest binary exponent, and the
+ * input is scaled by that power of two (exactly) so every FP64 magnitude is
+ * handled; zero and subnormal FP64 components are read as zero.
+ * QFT_PREC_FP64 runs the same passes in IEEE FP64 arithmetic instead.
+ * Batches (qft_batch_*) run complex128 transforms in FP64. */
 enum qft_precision { QFT_PREC_NATIVE = 0, QFT_PREC_TF32 = 1, QFT_PREC_BF16 = 2, QFT_PREC_BF16X3 = 3,
-                     QFT_PREC_FP16 = 4, QFT_PREC_FP16X3 = 5 };
+                     QFT_PREC_FP16 = 4, QFT_PREC_FP16X3 = 5, QFT_PREC_FP64 = 6 };
 
 /* What the planner built (Sec. 3.1: the plan is defined by the qubit count,
  * the fused blocks and the pre-fusion gate counters). */
@@ -158,6 +172,15 @@ int qft_load(qft_plan_t plan, void* d_state, const void* src, size_t len, int sr
  * scale_in = 0.  Concurrent executes must use distinct workspaces. */
 int qft_execute(qft_plan_t plan, void* d_state, void* d_workspace, double* d_scale_in, int scale_mode,
                 qft_stream_t stream);
+
+/* qft_execute out of place: reads d_in (N amplitudes, 256-byte aligned,
+ * not modified) and writes the result to d_out (N amplitudes, 256-byte
+ * aligned).  Same steps, workspace, scale_in and errors as qft_execute; the
+ * state is never copied: the first pass reads d_in and the last pass writes
+ * d_out.  d_in == d_out is the in-place transform; buffers that overlap
+ * otherwise give undefined results. */
+int qft_execute_oop(qft_plan_t plan, const void* d_in, void* d_out, void* d_workspace, double* d_scale_in,
+                    int scale_mode, qft_stream_t stream);
 
 /* One pass of qft_execute: launches only pass `pass` (0 .. passes-1, see
  * qft_plan_get_info).  Calling it for pass = 0, 1, ..., passes-1 in order on

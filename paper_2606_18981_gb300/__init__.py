@@ -24,7 +24,7 @@ C64, C128 = 0, 1
 FORWARD, INVERSE = -1, +1
 SCALE_STATE, SCALE_UNITARY, SCALE_UNNORM, SCALE_INV_N = 0, 1, 2, 3
 ORDER_NATURAL, ORDER_BITREV = 0, 1
-PREC_NATIVE, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_FP16, PREC_FP16X3 = 0, 1, 2, 3, 4, 5
+PREC_NATIVE, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_FP16, PREC_FP16X3, PREC_FP64 = 0, 1, 2, 3, 4, 5, 6
 OK, ERR_BAD_ARG, ERR_SIZE, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED, ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 

@@ -17,6 +17,9 @@ cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtenso
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes);
 cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                           cudaStream_t stream);
+cudaError_t launch_pass_df(int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+                           cudaStream_t stream);
+cudaError_t launch_df_maxexp(const void* state, size_t n_amps, int* out, int num_sms, cudaStream_t stream);
 cudaError_t launch_tc_pass(int dir, int prec, const CUtensorMap& map, const PassParams& P, const void* a_hi,
                            const void* a_lo, int kpad, int ncols, int grid, size_t smem, cudaStream_t st);
 size_t tc_smem_bytes(const PassParams& P, int prec, int kpad, int ncols);
@@ -27,6 +30,7 @@ cudaError_t tc_prepare_a(int prec, const double* d_src, void* d_hi, void* d_lo, 
 // from 4096.
 constexpr size_t kMetaBytes = 4096;
 constexpr size_t kStatusOff = 8;
+constexpr size_t kMaxExpOff = 16;  // double-float plans: largest biased FP64 exponent of the input (int)
 constexpr size_t kPartialOff = 64;
 constexpr int kMaxPartials = (kMetaBytes - kPartialOff) / 8;
 
@@ -62,7 +66,8 @@ struct qft_plan_s {
             if (ph.tc_a_lo) cudaFree(ph.tc_a_lo);
         }
     }
-    int precision = 0;  // QFT_PREC_*
+    int precision = 0;  // QFT_PREC_* (tensor-core tiers; QFT_PREC_FP64 is kept in fp64 below)
+    bool df = false;    // complex128 in double-float arithmetic (the default for complex128)
     int n = 0, k = -1, kk = 0, dir = -1, dtype = 0, order = 0;
     size_t esize = 8;
     int TB = 13, cmin = 2, rmax = 4;
@@ -76,6 +81,7 @@ struct qft_plan_s {
     size_t ws_bytes = 0;
     // tensor maps for the last (state, workspace) pointer pair
     std::mutex mu;
+    const void* map_in = nullptr;
     const void* map_state = nullptr;
     const void* map_work = nullptr;
     std::vector<CUtensorMap> maps;

@@ -6,8 +6,10 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "plan.hpp"
+#include "qft_df.cuh"
 
 namespace qft {
 
@@ -16,6 +18,7 @@ namespace qft {
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<dfloat> { using type = dcomplex; };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -97,20 +100,53 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
     r.y = a.x * b.y + a.y * b.x;
     return r;
 }
+// complex64: the real and imaginary parts of an amplitude sit in one 64-bit
+// register pair, so a complex add or subtract is one packed FP32x2
+// instruction (add/sub.rn.f32x2, sm_100 and later; per-lane IEEE
+// round-to-nearest, the same results as two scalar adds) -- half the
+// instructions of the butterfly network.
+__device__ __forceinline__ uint64_t f2pack(float x, float y) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 f2unpack(uint64_t r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pack(a.x, a.y)), "l"(f2pack(b.x, b.y)));
+    return f2unpack(d);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pack(a.x, a.y)), "l"(f2pack(b.x, b.y)));
+    return f2unpack(d);
+}
+// double-float complex128 amplitudes (qft_df.cuh)
+__device__ __forceinline__ dcomplex cadd(dcomplex a, dcomplex b) { return dc_add(a, b); }
+__device__ __forceinline__ dcomplex csub(dcomplex a, dcomplex b) { return dc_sub(a, b); }
+__device__ __forceinline__ dcomplex cmul(dcomplex a, dcomplex b) { return dc_mul(a, b); }
 
 // exp(2 pi i m / 32) for m = 0..15 (cos, sin): the rotations of controlled
 // phases between wires at distance <= 4 inside one register block
 // (R_2 .. R_5 and their products).
-__device__ constexpr double kW32c[16] = {
-    1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
-    0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173, 0.19509032201612826785,
-    0.0, -0.19509032201612826785, -0.38268343236508977173, -0.55557023301960222474,
-    -0.70710678118654752440, -0.83146961230254523708, -0.92387953251128675613, -0.98078528040323044913};
-__device__ constexpr double kW32s[16] = {
-    0.0, 0.19509032201612826785, 0.38268343236508977173, 0.55557023301960222474,
-    0.70710678118654752440, 0.83146961230254523708, 0.92387953251128675613, 0.98078528040323044913,
-    1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
-    0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173, 0.19509032201612826785};
+#define QFT_W32_COS 1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708, 0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173, 0.19509032201612826785, 0.0, -0.19509032201612826785, -0.38268343236508977173, -0.55557023301960222474, -0.70710678118654752440, -0.83146961230254523708, -0.92387953251128675613, -0.98078528040323044913
+#define QFT_W32_SIN 0.0, 0.19509032201612826785, 0.38268343236508977173, 0.55557023301960222474, 0.70710678118654752440, 0.83146961230254523708, 0.92387953251128675613, 0.98078528040323044913, 1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708, 0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173, 0.19509032201612826785
+__device__ constexpr double kW32c[16] = {QFT_W32_COS};
+__device__ constexpr double kW32s[16] = {QFT_W32_SIN};
+// Compile-time copies for constant initialisers evaluated by the host compiler
+// (a local array here must never reach device code at run time).
+constexpr double w32c_ct(int i) {
+    const double t[16] = {QFT_W32_COS};
+    return t[i];
+}
+constexpr double w32s_ct(int i) {
+    const double t[16] = {QFT_W32_SIN};
+    return t[i];
+}
 
 // z *= exp(DIR * 2 pi i m / 32).  With m a compile-time constant after loop
 // unrolling the trivial rotations (1, +-i, -1) reduce to moves and negations.
@@ -134,6 +170,41 @@ __device__ __forceinline__ void rot32(V& z, int m) {
     if (neg) { z.x = -z.x; z.y = -z.y; }
 }
 
+// The same rotations for double-float amplitudes: the constants are split
+// into FP32 pairs at compile time, the products formed by df_dot2.
+struct W32Pair {
+    float ch[16], cl[16], sh[16], sl[16];
+    constexpr W32Pair() : ch(), cl(), sh(), sl() {
+        for (int i = 0; i < 16; ++i) {
+            ch[i] = static_cast<float>(w32c_ct(i));
+            cl[i] = static_cast<float>(w32c_ct(i) - static_cast<double>(ch[i]));
+            sh[i] = static_cast<float>(w32s_ct(i));
+            sl[i] = static_cast<float>(w32s_ct(i) - static_cast<double>(sh[i]));
+        }
+    }
+};
+__device__ constexpr W32Pair kW32df{};
+
+template <int DIR>
+__device__ __forceinline__ void rot32(dcomplex& z, int m) {
+    m &= 31;
+    if (m == 0) return;
+    const bool neg = m >= 16;
+    const int mm = m & 15;
+    if (mm == 8) {
+        const dfloat t = z.x;
+        if (DIR > 0) { z.x = df_neg(z.y); z.y = t; } else { z.x = z.y; z.y = df_neg(t); }
+    } else if (mm != 0) {
+        const dfloat c(kW32df.ch[mm], kW32df.cl[mm]);
+        const dfloat s = DIR > 0 ? dfloat(kW32df.sh[mm], kW32df.sl[mm]) : dfloat(-kW32df.sh[mm], -kW32df.sl[mm]);
+        // (x + i y)(c + i s) = (x c - y s) + i (x s + y c)
+        const dfloat re = df_dot2(z.x, c, z.y, s);
+        z.y = df_dot2(z.x, s, df_neg(z.y), c);
+        z.x = re;
+    }
+    if (neg) { z.x = df_neg(z.x); z.y = df_neg(z.y); }
+}
+
 __device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
 
@@ -143,21 +214,27 @@ __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sin
 // floating-point sine/cosine only sees |x| <= 1/4 (in units of pi).
 template <typename T, int DIR>
 __device__ __forceinline__ typename Vec2<T>::type phase_turns(uint64_t beta, int n) {
-    const uint64_t b = (beta << (64 - n)) >> 24;            // beta mod 2^n, scaled to 2^40 per turn
-    const uint64_t q4 = (b + (1ull << 37)) >> 38;            // nearest quarter turn, 0..4
-    const int64_t rem = static_cast<int64_t>(b) - static_cast<int64_t>(q4 << 38);  // |rem| <= 2^37
-    const T x = static_cast<T>(rem) * static_cast<T>(1.0 / 549755813888.0);      // rem / 2^39
-    T s, c;
-    sincospi_t(x, &s, &c);
-    typename Vec2<T>::type r;
-    switch (q4 & 3) {
-        case 0: r.x = c; r.y = s; break;
-        case 1: r.x = -s; r.y = c; break;
-        case 2: r.x = -c; r.y = -s; break;
-        default: r.x = s; r.y = -c; break;
+    if constexpr (std::is_same<T, dfloat>::value) {
+        // double-float twiddles: the FP64 value split into a pair
+        const double2 w = phase_turns<double, DIR>(beta, n);
+        return dcomplex{dfloat(w.x), dfloat(w.y)};
+    } else {
+        const uint64_t b = (beta << (64 - n)) >> 24;            // beta mod 2^n, scaled to 2^40 per turn
+        const uint64_t q4 = (b + (1ull << 37)) >> 38;            // nearest quarter turn, 0..4
+        const int64_t rem = static_cast<int64_t>(b) - static_cast<int64_t>(q4 << 38);  // |rem| <= 2^37
+        const T x = static_cast<T>(rem) * static_cast<T>(1.0 / 549755813888.0);      // rem / 2^39
+        T s, c;
+        sincospi_t(x, &s, &c);
+        typename Vec2<T>::type r;
+        switch (q4 & 3) {
+            case 0: r.x = c; r.y = s; break;
+            case 1: r.x = -s; r.y = c; break;
+            case 2: r.x = -c; r.y = -s; break;
+            default: r.x = s; r.y = -c; break;
+        }
+        if (DIR < 0) r.y = -r.y;
+        return r;
     }
-    if (DIR < 0) r.y = -r.y;
-    return r;
 }
 
 // XOR swizzle of buffer B: the low SW bits of a tile index are XORed with the
@@ -213,7 +290,8 @@ __device__ __forceinline__ void block_circuit(V (&v)[1 << R], int kk) {
 // part whose tile bits are disjoint, so every per-group quantity that is
 // additive over disjoint bits is the combination of one lane entry (index
 // g & 31) and one high entry (index 32 + (g >> 5)):
-//   pb  tile index bits (OR),  ob  output address offset (sum),
+//   pb  tile index bits (OR),  sb  their swizzled buffer-B offset (XOR),
+//   ob  output address offset (sum),
 //   V   the cross-twiddle factors exp(s 2 pi i beta_e / 2^n) of the group's
 //       tile wires above the block, one per block wire e (product).
 // The tile coordinate's share of the cross twiddle, U_e, is computed once per
@@ -222,6 +300,7 @@ __device__ __forceinline__ void block_circuit(V (&v)[1 << R], int kk) {
 template <typename V>
 struct GroupTab {
     uint32_t* pb;
+    uint32_t* sb;  // swz(pb): the swizzle is XOR-linear, so a group's buffer-B base is sb[lane] ^ sb[high]
     int64_t* ob;
     V* tw;  // [e][entry], e < ntw: plane e holds factor e of every entry (lane reads are consecutive)
     int ntab;
@@ -260,6 +339,111 @@ __device__ __forceinline__ double output_factor(const PassParams& P, double scal
         case 2: return 1.0;                                              // unnormalised
         default: return P.inv_root_n * P.inv_root_n;                     // 1/N
     }
+}
+
+// Amplitude input/output of the pass kernels.  float2 / double2 states are
+// read and written as they are.  The double-float complex128 kernel keeps
+// amplitudes as dcomplex pairs between passes (the workspace holds 16-byte df
+// pairs, like double2) and converts only where the caller's FP64 data enters
+// (the first pass) and leaves (the last pass), with the exponent shift of its
+// range normalisation (qft_df.cuh).
+struct AmpIO {
+    int raw_in;     // the tile holds the caller's FP64 input (first pass of a df transform)
+    int raw_out;    // the output is the caller's FP64 state (last pass of a df transform)
+    int shift_in;   // input scaled by 2^-shift_in
+    int shift_out;  // output scaled by 2^shift_out
+};
+
+template <typename T>
+struct AmpTraits {
+    using V = typename Vec2<T>::type;
+    static constexpr bool kDF = false;
+    __device__ static __forceinline__ V load(const V* A, uint32_t i, const AmpIO&) { return A[i]; }
+    // |v|^2 summed over a group: norm_add per amplitude, norm_done once
+    using NormAcc = T;
+    __device__ static __forceinline__ void norm_add(NormAcc& a, const V& v) { a += v.x * v.x + v.y * v.y; }
+    __device__ static __forceinline__ double norm_done(NormAcc a) { return static_cast<double>(a); }
+    __device__ static __forceinline__ double norm2_at(const V* A, uint32_t i, const AmpIO&) {
+        const V a = A[i];
+        return static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
+    }
+    __device__ static __forceinline__ void settle(V&) {}
+    __device__ static __forceinline__ void store(V* out, int64_t o, V w, T scale, const AmpIO&) {
+        w.x *= scale;
+        w.y *= scale;
+        out[o] = w;
+    }
+    // output factor f (decode scale) as the kernel's scale; the shift is unused
+    __device__ static __forceinline__ void out_scale(double f, T& scale, int& shift_out, int) {
+        scale = static_cast<T>(f);
+        shift_out = 0;
+    }
+};
+
+template <>
+struct AmpTraits<dfloat> {
+    using V = dcomplex;
+    static constexpr bool kDF = true;
+    __device__ static __forceinline__ V load(const V* A, uint32_t i, const AmpIO& io) {
+        if (io.raw_in) {
+            const double2 d = reinterpret_cast<const double2*>(A)[i];
+            return dcomplex{df_from_double_shift(d.x, io.shift_in), df_from_double_shift(d.y, io.shift_in)};
+        }
+        return A[i];
+    }
+    // sum of |v|^2: exact squares of the high parts (two_prod) plus 2 hi lo,
+    // accumulated with two_sum, returned as FP64
+    using NormAcc = dfloat;
+    __device__ static __forceinline__ void norm_add1(NormAcc& a, dfloat z) {
+        const float p = z.hi * z.hi;
+        float e = __fmaf_rn(z.hi, z.hi, -p);
+        e = __fmaf_rn(2.f * z.hi, z.lo, e);
+        const dfloat s = two_sum(a.hi, p);
+        a.hi = s.hi;
+        a.lo += s.lo + e;
+    }
+    __device__ static __forceinline__ void norm_add(NormAcc& a, const V& v) {
+        norm_add1(a, v.x);
+        norm_add1(a, v.y);
+    }
+    __device__ static __forceinline__ double norm_done(NormAcc a) {
+        return static_cast<double>(a.hi) + static_cast<double>(a.lo);
+    }
+    __device__ static __forceinline__ double norm2_at(const V* A, uint32_t i, const AmpIO& io) {
+        NormAcc a(0.f, 0.f);
+        norm_add(a, load(A, i, io));
+        return norm_done(a);
+    }
+    __device__ static __forceinline__ void settle(V& v) { v = dc_norm(v); }
+    // Only the last pass has an output scale (the others run with scale 1).
+    __device__ static __forceinline__ void store(V* out, int64_t o, V w, dfloat scale, const AmpIO& io) {
+        if (io.raw_out) {
+            w = dcomplex{df_mul(w.x, scale), df_mul(w.y, scale)};
+            double2 d;
+            d.x = df_to_double_shift(w.x, io.shift_out);
+            d.y = df_to_double_shift(w.y, io.shift_out);
+            reinterpret_cast<double2*>(out)[o] = d;
+        } else {
+            out[o] = dc_norm(w);
+        }
+    }
+    // f * 2^k = m * 2^(e + k) with m in [1/2, 1): the pair carries m, the FP64
+    // conversion of the output adds e + k to the exponent
+    __device__ static __forceinline__ void out_scale(double f, dfloat& scale, int& shift_out, int k) {
+        int e = 0;
+        const double m = frexp(f, &e);
+        scale = dfloat(m);
+        shift_out = (m == 0.0) ? 0 : e + k;
+    }
+};
+
+// Exponent shift of the double-float range normalisation: the largest biased
+// FP64 exponent of the input (written by the maximum-exponent pre-pass into
+// the workspace's metadata) less the bias, so that the largest scaled
+// component lies in [1, 2).  0 for an all-zero input.
+__device__ __forceinline__ int df_shift_from_meta(const double* meta) {
+    const int mx = reinterpret_cast<const int*>(meta)[4];
+    return mx > 0 ? mx - 1023 : 0;
 }
 
 __device__ __forceinline__ void issue_tile_load(const PassParams& P, const CUtensorMap* map, int64_t tile,
@@ -337,6 +521,7 @@ __device__ __forceinline__ void build_group_tables(const PassParams& P, GroupTab
             }
             const int idx = P.tab_off[s] + i;
             tab.pb[idx] = pb;
+            tab.sb[idx] = swz<sizeof(V) == 8 ? 4 : 3>(pb);
             tab.ob[idx] = ob;
             for (int e = 0; e < P.ntw; ++e) {
                 V w;

@@ -1,0 +1,229 @@
+// qft_df.cuh -- double-float ("df") arithmetic for the complex128 pass kernel.
+//
+// GB300 executes FP64 at 1/64 of its FP32 rate, so a complex128 transform
+// whose butterflies and twiddles run on the FP64 pipe is bound by that pipe
+// at a few percent of the HBM roofline.  The df path keeps every amplitude as
+// an unevaluated sum hi + lo of two FP32 numbers (about 48 significant bits)
+// and runs all arithmetic on the FP32 pipe with error-free transformations:
+//
+//   two_sum(a, b)   s + e = a + b exactly            (Knuth; 6 FP32 adds)
+//   two_prod(a, b)  p + e = a * b exactly            (p = a*b, e = fma(a, b, -p))
+//   fast_two_sum    renormalisation when |s| >= |e|  (Dekker; 3 adds)
+//
+// Sums inside the butterfly network are left unnormalised (hi, lo) pairs;
+// products and every value written to shared or global memory are
+// renormalised.  The relative error of one operation is a few units of 2^-48,
+// so an n-wire transform stays far inside the complex128 tolerance 1e-13 n.
+//
+// Range: FP32 exponents.  The transform is linear, so before the first pass a
+// reduction finds the largest binary exponent of the input and the first pass
+// scales the input by 2^-k (an integer exponent shift, exact) so that its
+// largest component lies in [1, 2); the last pass multiplies by 2^k while it
+// converts back to FP64.  Intermediates then stay below 2^(n/2 + 1) and every
+// component that matters at the 2^-48 level of the largest one is a normal
+// FP32 pair.
+//
+// Conversions between FP64 and df use integer bit manipulation only (no FP64
+// instruction): the FP64 -> df split truncates the 53-bit significand into
+// 24 + 29 bits (the low part rounded to 24 bits), and df -> FP64 adds the two
+// significands in a 64-bit integer.  Both are __host__ __device__ so the host
+// test harness can check them bit for bit against long double arithmetic.
+#pragma once
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+#include <cuda_runtime.h>
+
+namespace qft {
+
+struct dfloat {
+    float hi, lo;
+    __host__ __device__ constexpr dfloat() : hi(0.f), lo(0.f) {}
+    __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr dfloat(int v) : hi(static_cast<float>(v)), lo(0.f) {}
+    // Nearest pair to d (host: table set-up, device: once per CTA or tile).
+    __host__ __device__ explicit dfloat(double d)
+        : hi(static_cast<float>(d)), lo(static_cast<float>(d - static_cast<double>(static_cast<float>(d)))) {}
+};
+
+struct __align__(16) dcomplex {
+    dfloat x, y;
+};
+
+// ------------------------------------------------------------ bit helpers
+
+__host__ __device__ __forceinline__ uint32_t f2u(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float u2f(uint32_t u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+__host__ __device__ __forceinline__ uint64_t d2u(double d) {
+#ifdef __CUDA_ARCH__
+    return static_cast<uint64_t>(__double_as_longlong(d));
+#else
+    uint64_t u;
+    std::memcpy(&u, &d, 8);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ double u2d(uint64_t u) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(static_cast<long long>(u));
+#else
+    double d;
+    std::memcpy(&d, &u, 8);
+    return d;
+#endif
+}
+__host__ __device__ __forceinline__ float fma_f(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return std::fma(a, b, c);
+#endif
+}
+
+// ------------------------------------------------- error-free transforms
+
+__host__ __device__ __forceinline__ dfloat two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return dfloat(s, e);
+}
+
+__host__ __device__ __forceinline__ dfloat fast_two_sum(float s, float e) {
+    const float h = s + e;
+    return dfloat(h, e - (h - s));
+}
+
+__host__ __device__ __forceinline__ dfloat df_norm(dfloat a) { return fast_two_sum(a.hi, a.lo); }
+
+// a + b and a - b, left unnormalised: the exact sum of the high parts plus the
+// rounded sum of the low parts and its error term.
+__host__ __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+    dfloat s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return s;
+}
+__host__ __device__ __forceinline__ dfloat df_sub(dfloat a, dfloat b) {
+    dfloat s = two_sum(a.hi, -b.hi);
+    s.lo += a.lo - b.lo;
+    return s;
+}
+__host__ __device__ __forceinline__ dfloat df_neg(dfloat a) { return dfloat(-a.hi, -a.lo); }
+
+// a * b (renormalised): the exact product of the high parts plus the cross terms.
+__host__ __device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+    const float p = a.hi * b.hi;
+    float e = fma_f(a.hi, b.hi, -p);
+    e = fma_f(a.hi, b.lo, e);
+    e = fma_f(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+// a.hi*b.hi - c.hi*d.hi as an exact two_sum of the exact products, plus every
+// cross term: one component of a complex product (renormalised).
+__host__ __device__ __forceinline__ dfloat df_dot2(dfloat a, dfloat b, dfloat c, dfloat d) {
+    const float p1 = a.hi * b.hi;
+    const float e1 = fma_f(a.hi, b.hi, -p1);
+    const float p2 = c.hi * d.hi;
+    const float e2 = fma_f(c.hi, d.hi, -p2);
+    dfloat s = two_sum(p1, -p2);
+    float t = s.lo + (e1 - e2);
+    t = fma_f(a.hi, b.lo, t);
+    t = fma_f(a.lo, b.hi, t);
+    t = fma_f(-c.hi, d.lo, t);
+    t = fma_f(-c.lo, d.hi, t);
+    return fast_two_sum(s.hi, t);
+}
+
+__host__ __device__ __forceinline__ dcomplex dc_add(dcomplex a, dcomplex b) {
+    return dcomplex{df_add(a.x, b.x), df_add(a.y, b.y)};
+}
+__host__ __device__ __forceinline__ dcomplex dc_sub(dcomplex a, dcomplex b) {
+    return dcomplex{df_sub(a.x, b.x), df_sub(a.y, b.y)};
+}
+// (a.x + i a.y)(b.x + i b.y) = (a.x b.x - a.y b.y) + i (a.x b.y + a.y b.x)
+__host__ __device__ __forceinline__ dcomplex dc_mul(dcomplex a, dcomplex b) {
+    return dcomplex{df_dot2(a.x, b.x, a.y, b.y), df_dot2(a.x, b.y, df_neg(a.y), b.x)};
+}
+__host__ __device__ __forceinline__ dcomplex dc_norm(dcomplex a) { return dcomplex{df_norm(a.x), df_norm(a.y)}; }
+
+// ------------------------------------------------ FP64 <-> df conversions
+
+// FP64 value d times 2^-k as a df pair, by integer operations only.  The
+// significand is split into its top 24 bits (hi, exact) and the remaining 29
+// bits (lo, rounded to 24 bits).  Zero and subnormal FP64 inputs, and values
+// whose scaled magnitude is below 2^-126, become 0, and the low part of
+// values below 2^-74 is dropped; with k
+// chosen so that the largest component lies in [1, 2), both only touch
+// components 2^-74 below the largest, far under the df precision.  k must
+// keep the scaled largest component below 2^128 (it does: it is at most 2).
+__host__ __device__ __forceinline__ dfloat df_from_double_shift(double d, int k) {
+    const uint64_t b = d2u(d);
+    const uint32_t hw = static_cast<uint32_t>(b >> 32), lw = static_cast<uint32_t>(b);
+    const int Eraw = static_cast<int>((hw >> 20) & 0x7FFu);
+    const int E = Eraw - k;  // biased FP64 exponent of d * 2^-k
+    const uint32_t sign = hw & 0x80000000u;
+    dfloat r;
+    if (Eraw != 0 && E >= 897) {  // d normal, and d * 2^-k normal as FP32 (biased exponent E - 896 >= 1)
+        r.hi = u2f(sign | (static_cast<uint32_t>(E - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+        const uint32_t m = lw & 0x1FFFFFFFu;                  // low 29 significand bits
+        const float scale = E >= 949 ? u2f(static_cast<uint32_t>(E - 948) << 23) : 0.f;  // 2^(E - 1075)
+        r.lo = u2f(f2u(static_cast<float>(m) * scale) | sign);
+    } else {
+        r.hi = 0.f;
+        r.lo = 0.f;
+    }
+    return r;
+}
+
+// (a.hi + a.lo) * 2^k as FP64, for a pair normalised by fast_two_sum
+// (|lo| <= ulp(hi) / 2).  The two significands are added in a 64-bit integer
+// (lo's bits below the 53-bit significand are truncated); a result whose
+// exponent leaves the FP64 normal range becomes 0 (underflow) or infinity.
+__host__ __device__ __forceinline__ double df_to_double_shift(dfloat a, int k) {
+    const uint32_t hb = f2u(a.hi);
+    const int Eh = static_cast<int>((hb >> 23) & 0xFFu);
+    if (Eh == 0) return 0.0;  // hi is zero (or subnormal, below any value that matters)
+    const uint64_t sh = static_cast<uint64_t>(hb >> 31);
+    uint64_t M = static_cast<uint64_t>((hb & 0x7FFFFFu) | 0x800000u) << 29;  // 53-bit significand, ulp 2^(Eh-179)
+    const uint32_t lb = f2u(a.lo);
+    const int El = static_cast<int>((lb >> 23) & 0xFFu);
+    if (El != 0) {
+        const uint64_t Ml = (lb & 0x7FFFFFu) | 0x800000u;
+        const int sa = El - Eh + 29;  // lo = Ml * 2^(El-150) = Ml * 2^sa ulps
+        uint64_t add = 0;
+        if (sa >= 0) add = sa < 40 ? (Ml << sa) : 0;
+        else if (sa > -25) add = Ml >> (-sa);
+        if ((lb >> 31) == sh) M += add;
+        else M -= add;
+    }
+    int Ed = Eh + 896 + k;  // biased FP64 exponent
+    if (M >= (uint64_t(1) << 53)) {
+        M >>= 1;
+        ++Ed;
+    } else if (M < (uint64_t(1) << 52)) {
+        M <<= 1;
+        --Ed;
+    }
+    if (Ed <= 0) return sh ? -0.0 : 0.0;
+    if (Ed >= 2047) return u2d((sh << 63) | (uint64_t(0x7FF) << 52));
+    return u2d((sh << 63) | (static_cast<uint64_t>(Ed) << 52) | (M & ((uint64_t(1) << 52) - 1)));
+}
+
+}  // namespace qft

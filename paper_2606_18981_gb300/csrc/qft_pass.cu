@@ -1,537 +1,50 @@
-// qft_pass.cu -- the SMEM-staged pass kernel of the QFT->FFT hot path (sm_103a).
-//
-// One launch = one HBM sweep over the state.  A persistent CTA loops over
-// tiles: a tile (2^tb amplitudes, the pass's wire group plus batch wires) is
-// fetched by TMA into buffer A (cp.async.bulk.tensor, or a 1D cp.async.bulk
-// for contiguous tiles), completion tracked by an mbarrier; then the pass's
-// register stages run:
-//
-//   stage s: every thread takes the 2^r amplitudes that differ only in the
-//   stage's r wires (one fused block of the circuit), multiplies them by the
-//   cross twiddle of the controlled phases whose target wire lies above the
-//   block (Eq. 5 / Sec. 2: diagonal two-level updates, folded into one phase
-//   per amplitude computed from exact integer phases), then applies the
-//   block's own Hadamards and controlled phases in registers (Sec. 2,
-//   Fig. 1 order), and writes the amplitudes back to buffer B (XOR-swizzled
-//   so that every stage reads and writes without bank conflicts).
-//
-// The last stage of a pass stores straight from registers to HBM with the
-// output wire->address map of the pass (this is where the qubit-reversal
-// swaps and the decode scale of Sec. 3 step 4 are folded in).  While stages
-// 1.. run on buffer B, the TMA engine already fetches the next tile into A.
-//
-// The first pass also accumulates ||x||^2 (Sec. 3 step 1) from the raw
-// amplitudes it reads; the last pass turns the per-CTA partial sums into
-// scale_in and applies 1/scale_in together with the folded 2^{-n/2} of the
-// n unnormalised butterflies.
+// qft_pass.cu -- host-side dispatch of the pass and batch kernels to their
+// per-dtype instantiations, and the shared-memory sizes of both kernels.
+// The kernels themselves are templates in qft_pass_kernels.cuh.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
 #include "plan.hpp"
-#include "qft_device.cuh"
-#include "qft_pair.cuh"
 
 namespace qft {
 
-// Stage kinds: where a stage reads its amplitudes and where it writes them.
-enum StageKind { K_FIRST = 0, K_MID = 1, K_LAST = 2, K_ONLY = 3 };
-//   K_FIRST  TMA buffer A (dense tile order) -> swizzled buffer B
-//   K_MID    B -> B
-//   K_LAST   B -> HBM through the pass's output address map (with the output scale)
-//   K_ONLY   A -> HBM (a pass of a single stage)
-
-template <typename T, int DIR, int R, int KIND, int NT>
-__device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& S,
-                                          const GroupTab<typename Vec2<T>::type>& tab, int toff,
-                                          const typename Vec2<T>::type* __restrict__ A,
-                                          typename Vec2<T>::type* __restrict__ Bb, int64_t out_tile, T scale,
-                                          const typename Vec2<T>::type* __restrict__ U, bool acc_norm,
-                                          double& norm_acc) {
-    using V = typename Vec2<T>::type;
-    constexpr int NJ = 1 << R;
-    constexpr int SW = sizeof(V) == 8 ? 4 : 3;
-    constexpr bool kFromA = (KIND == K_FIRST || KIND == K_ONLY);
-    constexpr bool kToGlobal = (KIND == K_LAST || KIND == K_ONLY);
-    const int ng = 1 << S.ngbits;
-    const uint32_t q = static_cast<uint32_t>(S.q);
-    // swizzled offsets of the register bits (the swizzle is XOR-linear), by Gray steps
-    uint32_t soff[NJ];
-    soff[0] = 0;
-#pragma unroll
-    for (int j = 1; j < NJ; ++j) soff[j] = soff[j & (j - 1)] ^ static_cast<uint32_t>(S.img[low_bit(j)]);
-    const bool cross = S.cross != 0;
-    const bool use_u = cross && S.tile_above;
-    V u[R];
-#pragma unroll
-    for (int e = 0; e < R; ++e) {
-        u[e].x = T(1);
-        u[e].y = T(0);
-    }
-    if (use_u) {
-#pragma unroll
-        for (int e = 0; e < R; ++e) u[e] = U[e];
-    }
-    int64_t oo[R];
-    if (kToGlobal) {
-#pragma unroll
-        for (int e = 0; e < R; ++e) oo[e] = int64_t(1) << P.p_out[q + e];
-    }
-    for (int g = threadIdx.x; g < ng; g += NT) {
-        const int lo5 = toff + (g & 31), hi5 = toff + 32 + (g >> 5);
-        const uint32_t pb = tab.pb[lo5] | tab.pb[hi5];
-        V v[NJ];
-        if (kFromA) {
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) v[j] = A[pb + (uint32_t(j) << q)];
-        } else {
-            const uint32_t base = swz<SW>(pb);
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) v[j] = Bb[base ^ soff[j]];
-        }
-        if (kFromA && acc_norm) {
-            T a = T(0);
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) a += v[j].x * v[j].x + v[j].y * v[j].y;
-            norm_acc += static_cast<double>(a);
-        }
-        if (cross) {
-            // tau_e for each block wire, then the diagonal prod_e tau_e^{j_e}
-            // applied as (low 2 bits) x (high bits) products.
-            V tau[R];
-#pragma unroll
-            for (int e = 0; e < R; ++e) {
-                // lane / high table factors that are identically 1 are skipped
-                if (S.lo_tw && S.hi_tw) tau[e] = cmul(tab.tw[e * tab.ntab + lo5], tab.tw[e * tab.ntab + hi5]);
-                else if (S.lo_tw) tau[e] = tab.tw[e * tab.ntab + lo5];
-                else tau[e] = tab.tw[e * tab.ntab + hi5];
-                if (use_u) tau[e] = cmul(tau[e], u[e]);
-            }
-            constexpr int LB = R < 2 ? R : 2;
-            constexpr int HB = R - LB;
-            V tl[1 << LB], th[1 << HB];
-#pragma unroll
-            for (int a = 1; a < (1 << LB); ++a)
-                tl[a] = (a & (a - 1)) ? cmul(tl[a & (a - 1)], tau[low_bit(a)]) : tau[low_bit(a)];
-#pragma unroll
-            for (int b = 1; b < (1 << HB); ++b)
-                th[b] = (b & (b - 1)) ? cmul(th[b & (b - 1)], tau[LB + low_bit(b)]) : tau[LB + low_bit(b)];
-#pragma unroll
-            for (int j = 1; j < NJ; ++j) {
-                const int a = j & ((1 << LB) - 1), b = j >> LB;
-                if (a) v[j] = cmul(v[j], tl[a]);
-                if (b) v[j] = cmul(v[j], th[b]);
-            }
-        }
-        block_circuit<DIR, R>(v, P.kk);
-        if (kToGlobal) {
-            V* __restrict__ out = static_cast<V*>(P.out) + (out_tile + tab.ob[lo5] + tab.ob[hi5]);
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                int64_t o = 0;
-#pragma unroll
-                for (int e = 0; e < R; ++e)
-                    if (j & (1 << e)) o += oo[e];
-                V w = v[j];
-                w.x *= scale;
-                w.y *= scale;
-                out[o] = w;
-            }
-        } else {
-            const uint32_t base = swz<SW>(pb);
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) Bb[base ^ soff[j]] = v[j];
-        }
-    }
-}
-
-template <typename T, int DIR, int KIND, int NT, int MAXR>
-__device__ __forceinline__ void dispatch_r(const PassParams& P, int s, const GroupTab<typename Vec2<T>::type>& tab,
-                                           const typename Vec2<T>::type* A, typename Vec2<T>::type* Bb,
-                                           int64_t out_tile, T scale, const typename Vec2<T>::type* U,
-                                           bool acc_norm, double& norm_acc) {
-    const StageDesc& S = P.st[s];
-    const int toff = P.tab_off[s];
-    switch (S.r) {
-        case 1: run_stage<T, DIR, 1, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
-        case 2: run_stage<T, DIR, 2, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
-        case 3: run_stage<T, DIR, 3, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
-        case 4: run_stage<T, DIR, 4, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc); break;
-        default:
-            if constexpr (MAXR >= 5)
-                run_stage<T, DIR, 5, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
-            break;
-    }
-}
-
-template <typename T, int DIR, int NT, int MAXR>
-__device__ __forceinline__ void dispatch_stage(const PassParams& P, int s, const GroupTab<typename Vec2<T>::type>& tab,
-                                               const typename Vec2<T>::type* A, typename Vec2<T>::type* Bb,
-                                               int64_t out_tile, T scale, const typename Vec2<T>::type* U,
-                                               bool acc_norm, double& norm_acc) {
-    const bool first = (s == 0), last = (s == P.nstages - 1);
-    if (first && last) dispatch_r<T, DIR, K_ONLY, NT, MAXR>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
-    else if (first) dispatch_r<T, DIR, K_FIRST, NT, MAXR>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
-    else if (last) dispatch_r<T, DIR, K_LAST, NT, MAXR>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
-    else dispatch_r<T, DIR, K_MID, NT, MAXR>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc);
-}
-
-// MINB = CTAs per SM the launch is built for: 2 caps registers at 65536 / (2 NT)
-// and is used only for passes whose stages hold <= 4 wires and whose buffers
-// fit twice in shared memory (tiles of <= 2^12 complex64 amplitudes).
-template <typename T, int DIR, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB)
-    qft_pass_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassParams P) {
-    using V = typename Vec2<T>::type;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ double red[NT / 32];
-    __shared__ __align__(16) V Ubuf[2][kMaxR * kMaxStages];
-
-    const int tid = threadIdx.x;
-    const uint32_t tile_elems = 1u << P.tb;
-    const uint32_t tile_bytes = tile_elems * static_cast<uint32_t>(sizeof(V));
-    // buffer B first, then the two TMA load buffers, then the group tables
-    V* B = reinterpret_cast<V*>(smem_raw);
-    V* const A0 = B + tile_elems;  // load buffer k & 1 is A0 + (k & 1) * tile_elems
-    unsigned char* tab_raw = smem_raw + 3 * static_cast<size_t>(tile_bytes);
-    const int ntab = P.ntab;
-    GroupTab<V> tab;
-    tab.ntab = ntab;
-    tab.tw = reinterpret_cast<V*>(tab_raw);
-    tab.ob = reinterpret_cast<int64_t*>(tab_raw + P.ntw * sizeof(V) * static_cast<size_t>(ntab));
-    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (P.ntw * sizeof(V) + 8) * static_cast<size_t>(ntab));
-
-    build_group_tables<T, DIR, NT>(P, tab);
-    if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-    }
-    int64_t tile = blockIdx.x;
-    compute_tile_twiddles<T, DIR>(P, tile, Ubuf[0]);
-    __syncthreads();
-
-    // Last pass of a multi-pass plan: scale_in from the first pass's partials.
-    T scale = T(1);
-    if (P.last && !P.first) {
-        double s = 0.0;
-        for (int i = tid; i < P.npartials; i += NT) s += P.partials[i];
-        const double tot = block_sum<NT>(s, red);
-        const double scale_in = sqrt(tot);
-        scale = static_cast<T>(output_factor(P, scale_in));
-        if (blockIdx.x == 0 && tid == 0) {
-            P.meta[0] = scale_in;
-            if (P.user_scale) *P.user_scale = scale_in;
-        }
-    }
-
-    double norm_acc = 0.0;
-    uint32_t parity = 0u;  // bit b: phase parity of mbar[b]
-    bool aborted = false;
-    if (tid == 0 && !P.test_skip_first_load) {
-        if (tile < P.num_tiles) issue_tile_load(P, &tmap, tile, A0, &mbar[0], tile_bytes);
-        if (tile + gridDim.x < P.num_tiles)
-            issue_tile_load(P, &tmap, tile + gridDim.x, A0 + tile_elems, &mbar[1], tile_bytes);
-    }
-
-    for (int k = 0; tile < P.num_tiles; tile += gridDim.x, ++k) {
-        const int buf = k & 1;
-        V* const Ab = A0 + (buf ? tile_elems : 0u);
-        uint64_t I_tile;
-        int64_t out_tile;
-        tile_coords(P, tile, I_tile, out_tile);
-        const bool ok = mbar_wait_bounded(&mbar[buf], (parity >> buf) & 1u, P.wait_limit_ns);
-        parity ^= 1u << buf;
-        if (__syncthreads_or(!ok)) {
-            aborted = true;
-            break;
-        }
-        if (P.first && P.last) {
-            // Single-pass transform (the whole state is this tile): norm first.
-            double s = 0.0;
-            for (uint32_t i = tid; i < tile_elems; i += NT) {
-                const V a = Ab[i];
-                s += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
-            }
-            const double tot = block_sum<NT>(s, red);
-            const double scale_in = sqrt(tot);
-            scale = static_cast<T>(output_factor(P, scale_in));
-            if (tid == 0) {
-                P.meta[0] = scale_in;
-                if (P.user_scale) *P.user_scale = scale_in;
-            }
-        }
-        const V* Ucur = Ubuf[buf];
-        for (int s = 0; s < P.nstages; ++s) {
-            const bool last_stage = (s == P.nstages - 1);
-            const bool from_A = (s == 0);
-            dispatch_stage<T, DIR, NT, (NT <= 256 && MINB == 1) ? 5 : 4>(P, s, tab, Ab, B, out_tile, scale,
-                                                                        Ucur + P.st[s].uoff, P.first && !P.last,
-                                                                        norm_acc);
-            if (last_stage) compute_tile_twiddles<T, DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1]);
-            __syncthreads();
-            if (from_A) {
-                // A[buf] is consumed: fetch the tile after next into it.
-                const int64_t nt = tile + 2 * static_cast<int64_t>(gridDim.x);
-                if (tid == 0 && nt < P.num_tiles) {
-                    fence_proxy_async_smem();
-                    issue_tile_load(P, &tmap, nt, Ab, &mbar[buf], tile_bytes);
-                }
-            }
-        }
-    }
-
-    if (aborted) {
-        if (tid == 0) {
-            atomicExch(P.status, -5);  // QFT_ERR_TIMEOUT
-            // let in-flight copies land before the CTA's shared memory is released
-            for (int b = 0; b < 2; ++b) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, P.wait_limit_ns);
-        }
-        return;
-    }
-    if (P.first && !P.last) {
-        const double tot = block_sum<NT>(norm_acc, red);
-        if (tid == 0) P.partials[blockIdx.x] = tot;
-    }
-}
-
-// ------------------------------------------------------------ batched launch
-//
-// One persistent launch over a list of tile work items drawn from many
-// transforms of different sizes and plans.  Each CTA claims items in order
-// from an atomic counter; an item is one tile of one pass of one transform.
-// Items are ordered transform by transform, so the second pass of a
-// transform runs right after its first (its intermediate is still in L2).
-// A second-pass item waits (bounded) until every first-pass tile of its
-// transform has signalled completion; the producers were claimed earlier by
-// running CTAs and never wait themselves, so the waits always end.
-
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-template <typename T, int DIR, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB)
-    qft_batch_kernel(const BatchItem* __restrict__ items, int nitems, const PassParams* __restrict__ descs,
-                     const CUtensorMap* __restrict__ maps, int* counters, int* next, int* status,
-                     uint64_t wait_ns, int max_tb, int max_ntab) {
-    using V = typename Vec2<T>::type;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ double red[NT / 32];
-    __shared__ __align__(16) P2 Ubuf_raw[kMaxR * kMaxStages];
-    __shared__ int s_item;
-
-    const int tid = threadIdx.x;
-    const uint32_t max_elems = 1u << max_tb;
-    V* B = reinterpret_cast<V*>(smem_raw);
-    V* A = B + max_elems;
-    V* Ubuf = reinterpret_cast<V*>(Ubuf_raw);
-    // group tables; twiddle planes sized for 16-byte entries (complex128, or pairs of complex64)
-    unsigned char* tab_raw = smem_raw + 2 * static_cast<size_t>(max_elems) * sizeof(V);
-    GroupTab<V> tab;
-    tab.ntab = max_ntab;
-    tab.tw = reinterpret_cast<V*>(tab_raw);
-    tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * 16 * static_cast<size_t>(max_ntab));
-    tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * 16 + 8) * static_cast<size_t>(max_ntab));
-    GroupTabP tabp;
-    tabp.ntab = max_ntab;
-    tabp.tw = reinterpret_cast<P2*>(tab_raw);
-    tabp.ob = tab.ob;
-    tabp.pb = tab.pb;
-    if (tid == 0) mbar_init(&mbar, 1);
-    __syncthreads();
-    uint32_t parity = 0;
-    int cached_shape = -1;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(next, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= nitems) break;
-        const BatchItem it = items[item];
-        const PassParams& P = descs[it.desc];
-        constexpr bool kCanPair = sizeof(T) == 4 && MINB == 1;  // paired items only in the one-CTA kernel
-        const bool paired = kCanPair && P.paired;
-        if (it.shape != cached_shape) {
-            if constexpr (kCanPair) {
-                if (paired) build_group_tables_p<DIR, NT>(P, tabp);
-                else build_group_tables<T, DIR, NT>(P, tab);
-            } else {
-                build_group_tables<T, DIR, NT>(P, tab);
-            }
-            cached_shape = it.shape;
-        }
-        bool ok = true;
-        if (tid == 0) {
-            if (it.wait_ctr >= 0) {
-                const uint64_t t0 = global_timer_ns();
-                while (ld_acquire_gpu(counters + it.wait_ctr) < it.wait_target) {
-                    if (global_timer_ns() - t0 > wait_ns) { ok = false; break; }
-                }
-                fence_proxy_async_global();  // the first pass's stores before this pass's TMA reads
-            }
-            if (ok) {
-                const uint32_t bytes = (1u << P.tb) * static_cast<uint32_t>(sizeof(V));
-                issue_tile_load(P, maps + (it.map >= 0 ? it.map : 0), it.tile, A, &mbar, bytes);
-            }
-        }
-        if constexpr (kCanPair) {
-            if (paired) compute_tile_twiddles_p<DIR>(P, it.tile, Ubuf_raw);
-            else compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
-        } else {
-            compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
-        }
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(status, -5);  // QFT_ERR_TIMEOUT
-            return;
-        }
-        const bool okw = mbar_wait_bounded(&mbar, parity, wait_ns);
-        parity ^= 1u;
-        if (__syncthreads_or(!okw)) {
-            if (tid == 0) {
-                atomicExch(status, -5);
-                mbar_wait_bounded(&mbar, parity ^ 1u, wait_ns);
-            }
-            return;
-        }
-        uint64_t I_tile;
-        int64_t out_tile;
-        tile_coords(P, it.tile, I_tile, out_tile);
-        T scale = T(1);
-        if (P.first && P.last) {
-            double s = 0.0;
-            for (uint32_t i = tid; i < (1u << P.tb); i += NT) {
-                const V a = A[i];
-                s += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
-            }
-            const double scale_in = sqrt(block_sum<NT>(s, red));
-            scale = static_cast<T>(output_factor(P, scale_in));
-            if (tid == 0) {
-                P.meta[0] = scale_in;
-                if (P.user_scale) *P.user_scale = scale_in;
-            }
-        } else if (P.last) {
-            double s = 0.0;
-            for (int i = tid; i < P.npartials; i += NT) s += P.partials[i];
-            const double scale_in = sqrt(block_sum<NT>(s, red));
-            scale = static_cast<T>(output_factor(P, scale_in));
-            if (tid == 0 && it.tile == 0) {
-                P.meta[0] = scale_in;
-                if (P.user_scale) *P.user_scale = scale_in;
-            }
-        }
-        double norm_acc = 0.0;
-        for (int s = 0; s < P.nstages; ++s) {
-            if constexpr (kCanPair) {
-                if (paired) {
-                    dispatch_stage_p<DIR, NT, 4>(P, s, tabp, reinterpret_cast<const float2*>(A), reinterpret_cast<P2*>(B),
-                                              out_tile, static_cast<float>(scale), Ubuf_raw + P.st[s].uoff,
-                                              P.first && !P.last, norm_acc);
-                    __syncthreads();
-                    continue;
-                }
-            }
-            dispatch_stage<T, DIR, NT, MINB == 1 ? 5 : 4>(P, s, tab, A, B, out_tile, scale, Ubuf + P.st[s].uoff,
-                                                          P.first && !P.last, norm_acc);
-            __syncthreads();
-        }
-        if (P.first && !P.last) {
-            const double tot = block_sum<NT>(norm_acc, red);
-            if (tid == 0) P.partials[it.tile] = tot;  // one partial per first-pass tile
-        }
-        if (it.signal_ctr >= 0) {
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) atomicAdd(counters + it.signal_ctr, 1);
-        }
-        fence_proxy_async_smem();  // this item's shared-memory reads before the next item's TMA write
-    }
-}
-
-template <typename T, int DIR, int NT, int MINB>
-static cudaError_t launch_batch_t(const BatchItem* items, int nitems, const PassParams* descs,
-                                  const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
-                                  int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
-    auto kern = qft_batch_kernel<T, DIR, NT, MINB>;
-    static thread_local size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
-    kern<<<grid, NT, smem, stream>>>(items, nitems, descs, maps, counters, next, status, wait_ns, max_tb, max_ntab);
-    return cudaGetLastError();
-}
+cudaError_t launch_pass_f32(int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream);
+cudaError_t launch_pass_f64(int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream);
+cudaError_t launch_batch_f32(int dir, int minb, const BatchItem* items, int nitems, const PassParams* descs, const CUtensorMap* maps, int* counters,
+                             int* next, int* status, uint64_t wait_ns, int max_tb, int max_ntab, int grid, size_t smem,
+                             cudaStream_t stream);
+cudaError_t launch_batch_f64(int dir, const BatchItem* items, int nitems, const PassParams* descs, const CUtensorMap* maps, int* counters,
+                             int* next, int* status, uint64_t wait_ns, int max_tb, int max_ntab, int grid, size_t smem,
+                             cudaStream_t stream);
+cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream);  // qft_pair.cu
 
 // minb = 2: complex64 batches whose tiles are <= 2^12 amplitudes and whose
 // blocks have <= 4 wires run two CTAs per SM (one CTA's load overlaps the
 // other's stages).
-cudaError_t launch_batch(int dtype, int dir, int minb, const BatchItem* items, int nitems, const PassParams* descs,
-                         const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
-                         int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
-#define QFT_BATCH_ARGS items, nitems, descs, maps, counters, next, status, wait_ns, max_tb, max_ntab, grid, smem, stream
-    if (dtype == 0 && minb == 2)
-        return dir < 0 ? launch_batch_t<float, -1, 256, 2>(QFT_BATCH_ARGS) : launch_batch_t<float, +1, 256, 2>(QFT_BATCH_ARGS);
-    if (dtype == 0)
-        return dir < 0 ? launch_batch_t<float, -1, 256, 1>(QFT_BATCH_ARGS) : launch_batch_t<float, +1, 256, 1>(QFT_BATCH_ARGS);
-    return dir < 0 ? launch_batch_t<double, -1, 256, 1>(QFT_BATCH_ARGS) : launch_batch_t<double, +1, 256, 1>(QFT_BATCH_ARGS);
-#undef QFT_BATCH_ARGS
+cudaError_t launch_batch(int dtype, int dir, int minb, const BatchItem* items, int nitems, const PassParams* descs, const CUtensorMap* maps, int* counters,
+                             int* next, int* status, uint64_t wait_ns, int max_tb, int max_ntab, int grid, size_t smem,
+                             cudaStream_t stream) {
+    if (dtype == 0) return launch_batch_f32(dir, minb, items, nitems, descs, maps, counters, next, status, wait_ns, max_tb, max_ntab, grid, smem, stream);
+    return launch_batch_f64(dir, items, nitems, descs, maps, counters, next, status, wait_ns, max_tb, max_ntab, grid, smem, stream);
 }
 
 size_t batch_smem_bytes(int max_tb, int max_ntab, size_t elem_bytes) {
-    return 2 * (size_t(1) << max_tb) * elem_bytes + size_t(max_ntab) * (kMaxR * 16 + 8 + 4);
+    return 2 * (size_t(1) << max_tb) * elem_bytes + size_t(max_ntab) * (kMaxR * 16 + 8 + 4 + 4);
 }
 
-// ------------------------------------------------------------- launchers
-
-cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
-                          cudaStream_t stream);  // qft_pair.cu
-
-template <typename T, int DIR, int NT, int MINB>
-static cudaError_t launch_pass_t(const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
-                                 cudaStream_t stream) {
-    auto kern = qft_pass_kernel<T, DIR, NT, MINB>;
-    static thread_local size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
-    kern<<<grid, NT, smem, stream>>>(map, P);
-    return cudaGetLastError();
-}
-
-template <int NT>
-static cudaError_t launch_nt(int dtype, int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
-                             cudaStream_t stream) {
-    if (dtype == 0)
-        return dir < 0 ? launch_pass_t<float, -1, NT, 1>(map, P, grid, smem, stream)
-                       : launch_pass_t<float, +1, NT, 1>(map, P, grid, smem, stream);
-    return dir < 0 ? launch_pass_t<double, -1, NT, 1>(map, P, grid, smem, stream)
-                   : launch_pass_t<double, +1, NT, 1>(map, P, grid, smem, stream);
-}
-
-cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P,
-                        int grid, size_t smem, cudaStream_t stream) {
+cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream) {
     if (P.paired) return launch_pass_p(dir, minb, map, P, grid, smem, stream);
-    if (minb == 2 && dtype == 0 && threads == 256)
-        return dir < 0 ? launch_pass_t<float, -1, 256, 2>(map, P, grid, smem, stream)
-                       : launch_pass_t<float, +1, 256, 2>(map, P, grid, smem, stream);
-    if (threads == 512) return launch_nt<512>(dtype, dir, map, P, grid, smem, stream);
-    return launch_nt<256>(dtype, dir, map, P, grid, smem, stream);
+    if (dtype == 0) return launch_pass_f32(dir, threads, minb, map, P, grid, smem, stream);
+    return launch_pass_f64(dir, threads, map, P, grid, smem, stream);
 }
 
 // Dynamic shared memory of one CTA: buffer B, the two TMA load buffers and
-// the group tables (ntw twiddle factors + output offset + tile bits per entry).
+// the group tables (ntw twiddle factors + output offset + tile bits + their
+// swizzled buffer-B offset per entry).
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes) {
     const size_t tw_bytes = P.paired ? 16 : elem_bytes;  // paired passes keep twiddle planes as pairs
-    return 3 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (P.ntw * tw_bytes + 8 + 4);
+    return 3 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (P.ntw * tw_bytes + 8 + 4 + (P.paired ? 0 : 4));
 }
 
 }  // namespace qft

@@ -1,0 +1,43 @@
+// qft_pass_df.cu -- the double-float complex128 pass kernel (qft_pass_kernels.cuh
+// instantiated with T = dfloat, arithmetic in qft_df.cuh) and the
+// maximum-exponent pre-pass of its range normalisation.
+//
+// A complex128 transform on this path reads the caller's FP64 state in its
+// first pass, converts each component to an FP32 pair scaled by 2^-k, keeps
+// 16-byte pairs in the workspace between passes (the same footprint as
+// double2), and converts back to FP64 times 2^k in its last pass.  k is the
+// largest binary exponent of the input, found by qft_df_maxexp_kernel before
+// the first pass and left in the workspace metadata (int at byte 16).
+#include "qft_pass_kernels.cuh"
+
+namespace qft {
+
+// Largest biased FP64 exponent over the real and imaginary parts of n2
+// doubles, atomically max-combined into *out (which the caller zeroes).
+__global__ void __launch_bounds__(256) qft_df_maxexp_kernel(const uint4* __restrict__ x, size_t n16, int* out) {
+    uint32_t m = 0;
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n16; i += size_t(gridDim.x) * blockDim.x) {
+        const uint4 v = x[i];  // two doubles: high words in .y and .w
+        m = max(m, max((v.y >> 20) & 0x7FFu, (v.w >> 20) & 0x7FFu));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, static_cast<int>(m));
+}
+
+cudaError_t launch_df_maxexp(const void* state, size_t n_amps, int* out, int num_sms, cudaStream_t stream) {
+    const size_t n16 = n_amps * 2 / 2;  // one 16-byte load per complex128 amplitude
+    size_t blocks = (n16 + 255) / 256;
+    const size_t cap = size_t(num_sms) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    qft_df_maxexp_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(static_cast<const uint4*>(state), n16, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass_df(int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+                           cudaStream_t stream) {
+    return dir < 0 ? launch_pass_t<dfloat, -1, 256, 1>(map, P, grid, smem, stream)
+                   : launch_pass_t<dfloat, +1, 256, 1>(map, P, grid, smem, stream);
+}
+
+}  // namespace qft

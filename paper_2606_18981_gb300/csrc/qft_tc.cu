@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tab.tw = reinterpret_cast<V*>(tab_raw);
     tab.ob = reinterpret_cast<int64_t*>(tab_raw + kMaxR * sizeof(V) * static_cast<size_t>(P.ntab));
     tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (kMaxR * sizeof(V) + 8) * static_cast<size_t>(P.ntab));
+    tab.sb = tab.pb + P.ntab;
     V* T = reinterpret_cast<V*>(Tb);
     float* D = reinterpret_cast<float*>(Tb);
 
@@ -425,7 +426,7 @@ struct TcFast {
     static constexpr int SPLIT = TcOp<PREC>::split;
     static size_t smem(int ntab, int ntw) {
         return 2 * size_t(TILE_BYTES) + D_BYTES + A_BYTES * (SPLIT ? 2 : 1) + B_BYTES * (SPLIT ? 2 : 1) +
-               size_t(ntab) * (size_t(ntw) * 8 + 8 + 4);
+               size_t(ntab) * (size_t(ntw) * 8 + 8 + 4 + 4);
     }
 };
 
@@ -465,6 +466,7 @@ __global__ void __launch_bounds__(kTcFastThreads, 1)
     tab.tw = reinterpret_cast<V*>(tab_raw);
     tab.ob = reinterpret_cast<int64_t*>(tab_raw + size_t(P.ntw) * sizeof(V) * P.ntab);
     tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (size_t(P.ntw) * sizeof(V) + 8) * P.ntab);
+    tab.sb = tab.pb + P.ntab;
 
     build_group_tables<float, DIR, NT>(P, tab);
     {
@@ -788,7 +790,7 @@ size_t tc_smem_bytes(const PassParams& P, int prec, int kpad, int ncols) {
     const size_t stage = tile > dst ? tile : dst;
     const size_t a = size_t(128) * kpad * eb * (split ? 2 : 1);
     const size_t b = size_t(ncols) * kpad * eb * (split ? 2 : 1);
-    return stage + a + b + 4 * 256 + size_t(P.ntab) * (kMaxR * 8 + 8 + 4);
+    return stage + a + b + 4 * 256 + size_t(P.ntab) * (kMaxR * 8 + 8 + 4 + 4);
 }
 
 template <int DIR, int PREC, int R>

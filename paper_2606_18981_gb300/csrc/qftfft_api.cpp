@@ -491,15 +491,18 @@ int prepare_tensor_passes(qft_plan_s* pl) {
     return QFT_OK;
 }
 
-int encode_maps(qft_plan_s* pl, const void* state, const void* work) {
-    if (pl->map_state == state && pl->map_work == work && !pl->maps.empty()) return QFT_OK;
+// Tensor maps of every pass for the buffers of one execute: the first pass
+// reads `in` (the caller's input; the state itself for in-place execution),
+// later passes read the state or the workspace buffer.
+int encode_maps(qft_plan_s* pl, const void* in, const void* state, const void* work) {
+    if (pl->map_in == in && pl->map_state == state && pl->map_work == work && !pl->maps.empty()) return QFT_OK;
     auto fn = get_encode_fn();
     pl->maps.assign(pl->passes.size(), CUtensorMap{});
     for (size_t i = 0; i < pl->passes.size(); ++i) {
         PassHost& ph = pl->passes[i];
         if (ph.prm.load_mode == 1) continue;
         if (!fn) return cuda_fail(cudaErrorNotSupported);
-        const void* base = ph.in_buf == 0 ? state : work;
+        const void* base = ph.in_buf == 0 ? (i == 0 ? in : state) : work;
         const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
         CUresult r = fn(&pl->maps[i], CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(base), ph.gdim,
                         ph.gstride, ph.box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -511,6 +514,7 @@ int encode_maps(qft_plan_s* pl, const void* state, const void* work) {
             return QFT_ERR_CUDA;
         }
     }
+    pl->map_in = in;
     pl->map_state = state;
     pl->map_work = work;
     return QFT_OK;
@@ -560,6 +564,7 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
     pl->threads = 256;
     pl->pairing = false;
     bool rmax_given = false;
+    bool fp64 = false;
     if (opts) {
         if (opts->order != QFT_ORDER_NATURAL && opts->order != QFT_ORDER_BITREV) { delete pl; return QFT_ERR_BAD_ARG; }
         pl->order = opts->order;
@@ -573,8 +578,11 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
             if (opts->coalesce_bits < 1 || opts->coalesce_bits > 6) { delete pl; return QFT_ERR_BAD_ARG; }
             pl->cmin = opts->coalesce_bits;
         }
-        if (opts->precision < QFT_PREC_NATIVE || opts->precision > QFT_PREC_FP16X3) { delete pl; return QFT_ERR_BAD_ARG; }
-        if (opts->precision != QFT_PREC_NATIVE) {
+        if (opts->precision < QFT_PREC_NATIVE || opts->precision > QFT_PREC_FP64) { delete pl; return QFT_ERR_BAD_ARG; }
+        if (opts->precision == QFT_PREC_FP64) {
+            if (dtype != QFT_C128) { delete pl; return QFT_ERR_UNSUPPORTED; }
+            fp64 = true;
+        } else if (opts->precision != QFT_PREC_NATIVE) {
             if (dtype != QFT_C64) { delete pl; return QFT_ERR_UNSUPPORTED; }
             pl->precision = opts->precision;
             pl->TB = 12;   // 2^12-amplitude tiles: 64 columns of one 6-wire block
@@ -603,6 +611,13 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
     // wires keep the kernel within the 128 registers that needs.
     if (dtype == QFT_C64 && !pl->precision && pl->threads == 256 && pl->TB <= 12 && !rmax_given)
         pl->rmax = std::min(pl->rmax, 4);
+    // complex128 runs in double-float unless FP64 was asked for: 256 threads,
+    // blocks of <= 4 wires (16 pairs of pairs per thread in registers).
+    if (dtype == QFT_C128 && !fp64) {
+        pl->df = true;
+        pl->threads = 256;
+        pl->rmax = std::min(pl->rmax, 4);
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) {
         int sms = 0;
@@ -680,11 +695,14 @@ int qft_read(qft_plan_t pl, const void* d_state, void* dst, int dst_on_device, q
 }
 
 namespace {
-int execute_range(qft_plan_t pl, void* d_state, void* d_workspace, double* d_scale_in, int scale_mode,
-                  qft_stream_t stream, size_t i0, size_t i1) {
-    if (!pl || !d_state || !d_workspace) return QFT_ERR_BAD_ARG;
+// Passes [i0, i1) of one execute.  The first pass reads d_in (d_state for an
+// in-place transform); the result lands in d_state.
+int execute_range(qft_plan_t pl, const void* d_in, void* d_state, void* d_workspace, double* d_scale_in,
+                  int scale_mode, qft_stream_t stream, size_t i0, size_t i1) {
+    if (!pl || !d_in || !d_state || !d_workspace) return QFT_ERR_BAD_ARG;
     if (scale_mode < QFT_SCALE_STATE || scale_mode > QFT_SCALE_INV_N) return QFT_ERR_BAD_ARG;
-    if ((reinterpret_cast<uintptr_t>(d_state) & 255) || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+    if ((reinterpret_cast<uintptr_t>(d_state) & 255) || (reinterpret_cast<uintptr_t>(d_workspace) & 255) ||
+        (reinterpret_cast<uintptr_t>(d_in) & 255))
         return QFT_ERR_BAD_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(d_workspace);
@@ -694,18 +712,23 @@ int execute_range(qft_plan_t pl, void* d_state, void* d_workspace, double* d_sca
         const int prc = prepare_tensor_passes(pl);
         if (prc != QFT_OK) return prc;
     }
-    int rc = encode_maps(pl, d_state, work);
+    int rc = encode_maps(pl, d_in, d_state, work);
     if (rc != QFT_OK) return rc;
     cudaError_t e = cudaSuccess;
     if (i0 == 0) {
-        e = cudaMemsetAsync(ws + kStatusOff, 0, sizeof(int32_t), st);
+        // status word and (double-float plans) the maximum exponent of the input
+        e = cudaMemsetAsync(ws + kStatusOff, 0, kMaxExpOff + sizeof(int32_t) - kStatusOff, st);
         if (e != cudaSuccess) return cuda_fail(e);
+        if (pl->df) {
+            e = launch_df_maxexp(d_in, size_t(1) << pl->n, reinterpret_cast<int*>(ws + kMaxExpOff), pl->num_sms, st);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
     }
     for (size_t i = i0; i < i1; ++i) {
         PassHost& ph = pl->passes[i];
         PassParams P = ph.prm;
         P.scale_mode = scale_mode;
-        P.in = ph.in_buf == 0 ? d_state : work;
+        P.in = ph.in_buf == 0 ? (i == 0 ? d_in : static_cast<const void*>(d_state)) : work;
         P.out = ph.out_buf == 0 ? d_state : work;
         P.partials = reinterpret_cast<double*>(ws + kPartialOff);
         P.meta = reinterpret_cast<double*>(ws);
@@ -716,6 +739,8 @@ int execute_range(qft_plan_t pl, void* d_state, void* d_workspace, double* d_sca
         if (pl->precision)
             e = launch_tc_pass(pl->dir, pl->precision, pl->maps[i], P, ph.tc_a_hi, ph.tc_a_lo, ph.tc_kpad,
                                ph.tc_ncols, ph.grid, ph.smem, st);
+        else if (pl->df)
+            e = launch_pass_df(pl->dir, pl->maps[i], P, ph.grid, ph.smem, st);
         else
             e = launch_pass(pl->dtype, pl->dir, pl->threads, ph.minb, pl->maps[i], P, ph.grid, ph.smem, st);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -727,13 +752,20 @@ int execute_range(qft_plan_t pl, void* d_state, void* d_workspace, double* d_sca
 int qft_execute(qft_plan_t pl, void* d_state, void* d_workspace, double* d_scale_in, int scale_mode,
                 qft_stream_t stream) {
     if (!pl) return QFT_ERR_BAD_ARG;
-    return execute_range(pl, d_state, d_workspace, d_scale_in, scale_mode, stream, 0, pl->passes.size());
+    return execute_range(pl, d_state, d_state, d_workspace, d_scale_in, scale_mode, stream, 0, pl->passes.size());
+}
+
+int qft_execute_oop(qft_plan_t pl, const void* d_in, void* d_out, void* d_workspace, double* d_scale_in,
+                    int scale_mode, qft_stream_t stream) {
+    if (!pl) return QFT_ERR_BAD_ARG;
+    return execute_range(pl, d_in, d_out, d_workspace, d_scale_in, scale_mode, stream, 0, pl->passes.size());
 }
 
 int qft_execute_pass(qft_plan_t pl, int pass, void* d_state, void* d_workspace, double* d_scale_in,
                      int scale_mode, qft_stream_t stream) {
     if (!pl || pass < 0 || pass >= static_cast<int>(pl->passes.size())) return QFT_ERR_BAD_ARG;
-    return execute_range(pl, d_state, d_workspace, d_scale_in, scale_mode, stream, size_t(pass), size_t(pass) + 1);
+    return execute_range(pl, d_state, d_state, d_workspace, d_scale_in, scale_mode, stream, size_t(pass),
+                         size_t(pass) + 1);
 }
 
 int qft_plan_describe_pass(qft_plan_t pl, int i, long long* out, int cap) {
