@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--precision", default="native", choices=["native", "tf32", "bf16", "bf16x3", "fp16", "fp16x3"],
                     help="complex64 only: run the transform on the tensor-core precision tier")
     ap.add_argument("--max-stage-bits", type=int, default=0)
+    ap.add_argument("--pass-split", type=int, default=0, help="planner pass_split option (1: extra wires mid)")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -509,7 +510,8 @@ def run_ours(args, world, rank, local):
     n, dt, k = args.n, args.dtype, args.k
     N = 1 << n
     eb = 8 if dt == "c64" else 16
-    shape = dict(tile_bits=args.tile_bits, coalesce_bits=args.coalesce_bits, max_stage_bits=args.max_stage_bits)
+    shape = dict(tile_bits=args.tile_bits, coalesce_bits=args.coalesce_bits, max_stage_bits=args.max_stage_bits,
+                 pass_split=args.pass_split)
     prec = {"native": 0, "tf32": q.PREC_TF32, "bf16": q.PREC_BF16, "bf16x3": q.PREC_BF16X3, "fp16": q.PREC_FP16,
             "fp16x3": q.PREC_FP16X3}[args.precision]
     if prec:

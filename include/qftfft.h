@@ -106,6 +106,11 @@ typedef struct {
                            arithmetic (blocks of <= 4 wires); 0 = default: one group per
                            thread.  (Passes whose tile is <= 2^12 amplitudes and whose blocks
                            have <= 4 wires, or <= 3 when paired, run two CTAs per SM.)     */
+    int pass_split;     /* NATURAL order, 3 or more passes: how wires left over by an even
+                           split are placed.  0 = default: on the first passes; 1 = on the
+                           middle passes, so the first and last passes (whose HBM runs
+                           the bit reversal spreads over the whole state) keep more batch
+                           wires and so longer runs.                                       */
 } qft_opts;
 
 /* Precision tier (complex64 plans): the block matrix and the data are rounded to
@@ -162,6 +167,15 @@ size_t qft_workspace_size(qft_plan_t plan);
  * while it reads the state and folds 1/scale_in into its last store. */
 int qft_load(qft_plan_t plan, void* d_state, const void* src, size_t len, int src_on_device,
              qft_stream_t stream);
+
+/* Step 1 for a length that is not a power of two: the register has
+ * n = ceil(log2 len) qubits (Sec. 3 step 1), so the caller's len <= 2^n
+ * values are copied to the start of d_state and the other 2^n - len
+ * amplitudes are set to zero.  The transform is then the 2^n-point DFT of the
+ * zero-padded sequence -- the paper's encoding, which is not the len-point
+ * DFT of the data.  len > 2^n gives QFT_ERR_SIZE; len = 2^n is qft_load. */
+int qft_load_padded(qft_plan_t plan, void* d_state, const void* src, size_t len, int src_on_device,
+                    qft_stream_t stream);
 
 /* Steps 1 and 3-4 on the GPU, in place on d_state: scale_in = ||x||_2,
  * psi' = U (x / scale_in), then the output scaling scale_mode (QFT_SCALE_*).
@@ -290,6 +304,37 @@ int qft_get_scale_in(qft_plan_t plan, const void* d_workspace, double* out, qft_
 /* Synchronise stream and read the device status word of the workspace
  * (0 = ok, QFT_ERR_TIMEOUT if a kernel's bounded wait expired). */
 int qft_check_status(qft_plan_t plan, const void* d_workspace, qft_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Real-input transforms of N = 2^n real samples (2 <= n <= 34 for float32
+ * data, QFT_C64; 2 <= n <= 33 for float64 data, QFT_C128).  They pack the
+ * real samples into the N/2 amplitudes of an (n-1)-qubit state (sample 2m as
+ * the real and 2m+1 as the imaginary part, the same bytes) and run the exact
+ * (n-1)-qubit QFT (Sec. 3 steps 2-3) plus one sweep that separates or joins
+ * the spectra of the even and odd samples.  This extends the paper's encode
+ * step (Sec. 3 step 1), which takes complex input only.
+ *
+ *   FORWARD (R2C, numpy.fft.rfft):  d_in = N reals, d_out = N/2 + 1 complex
+ *       X_k = f sum_j x_j e^{-2 pi i j k / N},  k = 0 .. N/2
+ *   INVERSE (C2R, numpy.fft.irfft): d_in = N/2 + 1 complex (a Hermitian half
+ *       spectrum; the imaginary parts of X_0 and X_{N/2} are ignored),
+ *       d_out = N reals
+ *       x_j = f sum_{k=0}^{N-1} X_k e^{+2 pi i j k / N},  X_{N-k} = conj X_k
+ *
+ * f is the scale mode's factor: QFT_SCALE_UNNORM 1, QFT_SCALE_UNITARY
+ * 1/sqrt(N), QFT_SCALE_INV_N 1/N (numpy's rfft is FORWARD + UNNORM, its irfft
+ * INVERSE + INV_N).  QFT_SCALE_STATE has no meaning here: QFT_ERR_BAD_ARG.
+ * d_in and d_out are distinct, 256-byte aligned device buffers; d_in is not
+ * modified.  The workspace is qft_rplan_workspace_size() bytes.  opts as for
+ * qft_plan_create (order must be NATURAL; tensor-core tiers are not offered:
+ * QFT_ERR_UNSUPPORTED).  qft_rplan_create allocates small plan-owned twiddle
+ * tables (complex128 only). */
+typedef struct qft_rplan_s* qft_rplan_t;
+int qft_rplan_create(qft_rplan_t* out, int n, int direction, int dtype, const qft_opts* opts);
+int qft_rplan_destroy(qft_rplan_t plan);
+size_t qft_rplan_workspace_size(qft_rplan_t plan);
+int qft_rplan_execute(qft_rplan_t plan, const void* d_in, void* d_out, void* d_workspace, int scale_mode,
+                      qft_stream_t stream);
 
 /* Diagnostics: write pass i of the plan as a flat integer record (tile bits,
  * register stages with their wires and lane maps, tile-index -> wire and

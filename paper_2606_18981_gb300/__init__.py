@@ -58,7 +58,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("tile_bits", ctypes.c_int), ("coalesce_bits", ctypes.c_int),
                 ("max_stage_bits", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
                 ("test_skip_first_load", ctypes.c_int), ("threads", ctypes.c_int),
-                ("precision", ctypes.c_int), ("paired", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("paired", ctypes.c_int), ("pass_split", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -73,10 +73,17 @@ _lib.qft_plan_get_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
 _lib.qft_workspace_size.argtypes = [_vp]
 _lib.qft_workspace_size.restype = ctypes.c_size_t
 _lib.qft_load.argtypes = [_vp, _vp, _vp, ctypes.c_size_t, ctypes.c_int, _vp]
+_lib.qft_load_padded.argtypes = [_vp, _vp, _vp, ctypes.c_size_t, ctypes.c_int, _vp]
 _lib.qft_execute.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_execute_pass.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_read.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_execute_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.qft_execute_oop.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.qft_rplan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts)]
+_lib.qft_rplan_destroy.argtypes = [_vp]
+_lib.qft_rplan_workspace_size.argtypes = [_vp]
+_lib.qft_rplan_workspace_size.restype = ctypes.c_size_t
+_lib.qft_rplan_execute.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_get_scale_in.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]
 _lib.qft_check_status.argtypes = [_vp, _vp, _vp]
 _lib.qft_plan_describe_pass.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
@@ -152,7 +159,7 @@ class Plan:
     def __init__(self, n: int, k: int = -1, direction: int = FORWARD, dtype="c64", order: int = ORDER_NATURAL,
                  tile_bits: int = 0, coalesce_bits: int = 0, max_stage_bits: int = 0,
                  wait_limit_ms: int = 0, test_skip_first_load: int = 0, threads: int = 0, precision: int = 0,
-                 paired: int = 0, tuned: bool = False):
+                 paired: int = 0, pass_split: int = 0, tuned: bool = False):
         self._h = _vp()
         self.n, self.k, self.direction = int(n), int(k), int(direction)
         self.dtype = _dtype_code(dtype)
@@ -166,8 +173,9 @@ class Plan:
             max_stage_bits = max_stage_bits or t.get("max_stage_bits", 0)
             threads = threads or t.get("threads", 0)
             paired = paired or t.get("paired", 0)
+            pass_split = pass_split or t.get("pass_split", 0)
         opts = Opts(order, tile_bits, coalesce_bits, max_stage_bits, wait_limit_ms, test_skip_first_load, threads,
-                    precision, paired)
+                    precision, paired, pass_split)
         _check(_lib.qft_plan_create(ctypes.byref(self._h), self.n, self.k, self.direction, self.dtype,
                                     ctypes.byref(opts)), "qft_plan_create")
 
@@ -201,21 +209,29 @@ class Plan:
 
         return torch.empty(self.workspace_size(), dtype=torch.uint8, device=device)
 
-    def load(self, state, src, stream=None) -> None:
-        """Copy src (host or device tensor / numpy array) into the device state buffer."""
+    def load(self, state, src, stream=None, pad: bool = False) -> None:
+        """Copy src (host or device tensor / numpy array) into the device state buffer.
+        pad=True: src may be shorter than 2^n; the rest of the state is zeroed."""
         on_dev = 1
         if hasattr(src, "is_cuda"):
             on_dev = 1 if src.is_cuda else 0
             ptr, ln = src.data_ptr(), src.numel()
         else:  # numpy
             on_dev, ptr, ln = 0, src.ctypes.data, src.size
-        _check(_lib.qft_load(self._h, _ptr(state), ptr, ln, on_dev, _stream_handle(stream)), "qft_load")
+        fn = _lib.qft_load_padded if pad else _lib.qft_load
+        _check(fn(self._h, _ptr(state), ptr, ln, on_dev, _stream_handle(stream)), "qft_load")
 
     def execute(self, state, workspace, scale_mode: int = SCALE_STATE, scale_out=None, stream=None) -> None:
         """Run the transform in place on the device state tensor (async on stream)."""
         _check(_lib.qft_execute(self._h, _ptr(state), _ptr(workspace),
                                 _ptr(scale_out) if scale_out is not None else None,
                                 int(scale_mode), _stream_handle(stream)), "qft_execute")
+
+    def execute_oop(self, inp, out, workspace, scale_mode: int = SCALE_STATE, scale_out=None, stream=None) -> None:
+        """Run the transform out of place: reads inp (unchanged), writes out."""
+        _check(_lib.qft_execute_oop(self._h, _ptr(inp), _ptr(out), _ptr(workspace),
+                                    _ptr(scale_out) if scale_out is not None else None,
+                                    int(scale_mode), _stream_handle(stream)), "qft_execute_oop")
 
     def execute_pass(self, i: int, state, workspace, scale_mode: int = SCALE_STATE, scale_out=None,
                      stream=None) -> None:
@@ -247,6 +263,40 @@ class Plan:
         h = getattr(self, "_h", None)
         if h is not None and h.value:
             _lib.qft_plan_destroy(h)
+            self._h = _vp()
+
+
+class RealPlan:
+    """Real-input transform of N = 2^n real samples: FORWARD = R2C (numpy.fft.rfft
+    with SCALE_UNNORM), INVERSE = C2R (numpy.fft.irfft with SCALE_INV_N).
+    dtype "c64" works on float32 data, "c128" on float64 data."""
+
+    def __init__(self, n: int, direction: int = FORWARD, dtype="c64", **opts):
+        self._h = _vp()
+        self.n, self.direction = int(n), int(direction)
+        self.dtype = _dtype_code(dtype)
+        o = Opts(0, opts.get("tile_bits", 0), opts.get("coalesce_bits", 0), opts.get("max_stage_bits", 0),
+                 opts.get("wait_limit_ms", 0), 0, opts.get("threads", 0), opts.get("precision", 0), 0,
+                 opts.get("pass_split", 0))
+        _check(_lib.qft_rplan_create(ctypes.byref(self._h), self.n, self.direction, self.dtype, ctypes.byref(o)),
+               "qft_rplan_create")
+
+    def workspace_size(self) -> int:
+        return int(_lib.qft_rplan_workspace_size(self._h))
+
+    def alloc_workspace(self, device="cuda"):
+        import torch
+
+        return torch.empty(self.workspace_size(), dtype=torch.uint8, device=device)
+
+    def execute(self, inp, out, workspace, scale_mode: int = SCALE_UNNORM, stream=None) -> None:
+        _check(_lib.qft_rplan_execute(self._h, _ptr(inp), _ptr(out), _ptr(workspace), int(scale_mode),
+                                      _stream_handle(stream)), "qft_rplan_execute")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.qft_rplan_destroy(h)
             self._h = _vp()
 
 
@@ -363,11 +413,52 @@ def fft(x, k: int | None = None, inverse: bool = False, norm: str = "backward", 
     p = _plan_cache.get(key)
     if p is None:
         p = _plan_cache[key] = Plan(n, key[1], direction, key[3], ordc)
-    out = x.contiguous().clone()
+    out = torch.empty_like(x)
     ws = p.alloc_workspace(x.device)
-    p.execute(out, ws, mode)
+    p.execute_oop(x.contiguous(), out, ws, mode)
     return out
 
 
-__all__ = ["Plan", "Batch", "Server", "PlanInfo", "QftError", "fft", "lib", "C64", "C128", "FORWARD", "INVERSE",
+_rplan_cache: dict = {}
+
+
+def rfft(x, norm: str = "backward"):
+    """numpy.fft.rfft on a CUDA float32 / float64 tensor of length 2^n (n >= 2)."""
+    import torch
+
+    if not x.is_cuda or x.dtype not in (torch.float32, torch.float64):
+        raise ValueError("rfft expects a CUDA float32 or float64 tensor")
+    N = x.numel()
+    n = N.bit_length() - 1
+    if N < 4 or (1 << n) != N:
+        raise QftError(ERR_SIZE, "rfft")
+    dt = C64 if x.dtype == torch.float32 else C128
+    mode = {"backward": SCALE_UNNORM, "ortho": SCALE_UNITARY, "forward": SCALE_INV_N}[norm]
+    key = (n, FORWARD, dt)
+    p = _rplan_cache.get(key) or _rplan_cache.setdefault(key, RealPlan(n, FORWARD, dt))
+    out = torch.empty(N // 2 + 1, dtype=torch.complex64 if dt == C64 else torch.complex128, device=x.device)
+    p.execute(x.contiguous(), out, p.alloc_workspace(x.device), mode)
+    return out
+
+
+def irfft(X, n: int | None = None, norm: str = "backward"):
+    """numpy.fft.irfft of a CUDA half spectrum X (N/2 + 1 complex values, N = 2^n)."""
+    import torch
+
+    if not X.is_cuda or X.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError("irfft expects a CUDA complex64 or complex128 tensor")
+    N = 2 * (X.numel() - 1) if n is None else int(n)
+    nb = N.bit_length() - 1
+    if N < 4 or (1 << nb) != N or X.numel() != N // 2 + 1:
+        raise QftError(ERR_SIZE, "irfft")
+    dt = C64 if X.dtype == torch.complex64 else C128
+    mode = {"backward": SCALE_INV_N, "ortho": SCALE_UNITARY, "forward": SCALE_UNNORM}[norm]
+    key = (nb, INVERSE, dt)
+    p = _rplan_cache.get(key) or _rplan_cache.setdefault(key, RealPlan(nb, INVERSE, dt))
+    out = torch.empty(N, dtype=torch.float32 if dt == C64 else torch.float64, device=X.device)
+    p.execute(X.contiguous(), out, p.alloc_workspace(X.device), mode)
+    return out
+
+
+__all__ = ["Plan", "RealPlan", "Batch", "Server", "PlanInfo", "QftError", "fft", "rfft", "irfft", "lib", "C64", "C128", "FORWARD", "INVERSE",
            "SCALE_STATE", "SCALE_UNITARY", "SCALE_UNNORM", "SCALE_INV_N", "ORDER_NATURAL", "ORDER_BITREV"]

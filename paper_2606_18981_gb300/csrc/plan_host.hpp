@@ -73,6 +73,7 @@ struct qft_plan_s {
     int TB = 13, cmin = 2, rmax = 4;
     int threads = 256;  // CTA size of the pass kernel (256: stages of <= 5 wires; 512: <= 4)
     bool pairing = false;  // complex64 passes may use the paired (packed f32x2) kernel
+    int pass_split = 0;    // qft_opts.pass_split
     uint64_t wait_limit_ns = 2000000000ull;
     int test_skip_first_load = 0;
     int num_sms = 148;

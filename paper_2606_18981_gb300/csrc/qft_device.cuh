@@ -125,6 +125,17 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pack(a.x, a.y)), "l"(f2pack(b.x, b.y)));
     return f2unpack(d);
 }
+// lane-wise a * b and a * b + c on FP32 pairs (packed FP32x2)
+__device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2pack(a.x, a.y)), "l"(f2pack(b.x, b.y)));
+    return f2unpack(d);
+}
+__device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2pack(a.x, a.y)), "l"(f2pack(b.x, b.y)), "l"(f2pack(c.x, c.y)));
+    return f2unpack(d);
+}
 // double-float complex128 amplitudes (qft_df.cuh)
 __device__ __forceinline__ dcomplex cadd(dcomplex a, dcomplex b) { return dc_add(a, b); }
 __device__ __forceinline__ dcomplex csub(dcomplex a, dcomplex b) { return dc_sub(a, b); }
@@ -360,18 +371,29 @@ struct AmpTraits {
     static constexpr bool kDF = false;
     __device__ static __forceinline__ V load(const V* A, uint32_t i, const AmpIO&) { return A[i]; }
     // |v|^2 summed over a group: norm_add per amplitude, norm_done once
-    using NormAcc = T;
-    __device__ static __forceinline__ void norm_add(NormAcc& a, const V& v) { a += v.x * v.x + v.y * v.y; }
-    __device__ static __forceinline__ double norm_done(NormAcc a) { return static_cast<double>(a); }
+    using NormAcc = V;  // per-component sums (x: real parts, y: imaginary parts)
+    __device__ static __forceinline__ void norm_add(NormAcc& a, const V& v) {
+        if constexpr (sizeof(T) == 4) {
+            a = cfma2(v, v, a);  // one packed FP32x2 fma per amplitude
+        } else {
+            a.x += v.x * v.x;
+            a.y += v.y * v.y;
+        }
+    }
+    __device__ static __forceinline__ double norm_done(NormAcc a) { return static_cast<double>(a.x + a.y); }
     __device__ static __forceinline__ double norm2_at(const V* A, uint32_t i, const AmpIO&) {
         const V a = A[i];
         return static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
     }
     __device__ static __forceinline__ void settle(V&) {}
     __device__ static __forceinline__ void store(V* out, int64_t o, V w, T scale, const AmpIO&) {
-        w.x *= scale;
-        w.y *= scale;
-        out[o] = w;
+        if constexpr (sizeof(T) == 4) {
+            out[o] = cmul2(w, make_float2(scale, scale));  // one packed FP32x2 multiply
+        } else {
+            w.x *= scale;
+            w.y *= scale;
+            out[o] = w;
+        }
     }
     // output factor f (decode scale) as the kernel's scale; the shift is unused
     __device__ static __forceinline__ void out_scale(double f, T& scale, int& shift_out, int) {

@@ -95,7 +95,7 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
             for (int j = 0; j < NJ; ++j) v[j] = Bb[base ^ soff[j]];
         }
         if (kFromA && acc_norm) {
-            typename Tr::NormAcc a(0);
+            typename Tr::NormAcc a{};
 #pragma unroll
             for (int j = 0; j < NJ; ++j) Tr::norm_add(a, v[j]);
             norm_acc += Tr::norm_done(a);

@@ -321,7 +321,16 @@ int plan_passes(qft_plan_s* pl) {
     if (natural) {
         P = (n + cap - 1) / cap;
         a.assign(P, n / P);
-        for (int j = 0; j < n % P; ++j) a[j] += 1;
+        if (pl->pass_split == 1 && P >= 3) {
+            // extra wires to the middle passes first: the first and last
+            // passes then keep more batch wires (longer HBM runs, fewer pages
+            // touched per tile on the strided side of the bit reversal)
+            int extra = n % P;
+            for (int j = 1; j < P - 1 && extra > 0; ++j, --extra) a[j] += 1;
+            for (int j = 0; j < P && extra > 0; j += P - 1, --extra) a[j] += 1;
+        } else {
+            for (int j = 0; j < n % P; ++j) a[j] += 1;
+        }
     } else if (pl->precision) {
         // tensor tier: every pass is one block of <= cap wires
         P = (n + cap - 1) / cap;
@@ -598,6 +607,8 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
             if (pl->threads == 512) pl->rmax = 4;
         }
         pl->pairing = opts->paired && dtype == QFT_C64 && pl->threads == 256 && !pl->precision;
+        if (opts->pass_split < 0 || opts->pass_split > 1) { delete pl; return QFT_ERR_BAD_ARG; }
+        pl->pass_split = opts->pass_split;
         if (opts->max_stage_bits) {
             rmax_given = true;
             if (opts->max_stage_bits < 1 || opts->max_stage_bits > (pl->threads == 512 ? 4 : kMaxStageR)) {
@@ -682,6 +693,21 @@ int qft_load(qft_plan_t pl, void* d_state, const void* src, size_t len, int src_
     cudaError_t e = cudaMemcpyAsync(d_state, src, len * pl->esize,
                                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? QFT_OK : cuda_fail(e);
+}
+
+int qft_load_padded(qft_plan_t pl, void* d_state, const void* src, size_t len, int src_on_device,
+                    qft_stream_t stream) {
+    if (!pl || !d_state || (!src && len)) return QFT_ERR_BAD_ARG;
+    const size_t N = size_t(1) << pl->n;
+    if (len > N) return QFT_ERR_SIZE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* dst = static_cast<char*>(d_state);
+    cudaError_t e = cudaSuccess;
+    if (len && src != d_state)
+        e = cudaMemcpyAsync(dst, src, len * pl->esize, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            st);
+    if (e == cudaSuccess && len < N) e = cudaMemsetAsync(dst + len * pl->esize, 0, (N - len) * pl->esize, st);
     return e == cudaSuccess ? QFT_OK : cuda_fail(e);
 }
 

@@ -110,3 +110,23 @@ def test_variant_plans_use_the_intended_kernels():
     assert all(P["paired"] for P in d)
     d = descs(q.Plan(26, -1, q.FORWARD, "c64", 0, tile_bits=12, paired=1, max_stage_bits=3))
     assert all(P["paired"] and P["minb"] == 2 for P in d)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n,tbits", [(14, 6), (17, 7), (16, 6), (19, 8), (13, 5)])
+def test_pass_split_plans(oracle_mod, dt, n, tbits):
+    """pass_split = 1 (left-over wires on the middle passes): same transform,
+    first and last passes with at least as many batch wires as the default."""
+    x = qft_inputs.gaussian(n, seed=3000 + n, normalise=False)
+    p0 = q.Plan(n, -1, q.FORWARD, dt, q.ORDER_NATURAL, tile_bits=tbits)
+    p1 = q.Plan(n, -1, q.FORWARD, dt, q.ORDER_NATURAL, tile_bits=tbits, pass_split=1)
+    i0, i1 = p0.info(), p1.info()
+    assert i0.passes == i1.passes
+    assert sum(list(i1.wires_per_pass)[:i1.passes]) == n
+    if i1.passes >= 3:
+        assert i1.wires_per_pass[0] <= i0.wires_per_pass[0]
+    for i in range(i1.passes):
+        check_structure(parse(p1.describe_pass(i)), 8 if dt == "c64" else 16)
+    got = emulate(p1, x, q.SCALE_STATE)
+    ref, _ = oracle_mod.qft(x, k=-1, sign=q.FORWARD, mode=q.SCALE_STATE, natural_order=True)
+    assert rel_l2(got, ref) < 1e-12
