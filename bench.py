@@ -144,7 +144,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("qft_pass_kernels.cuh", "qft_device.cuh", "qft_pair.cuh", "plan.hpp"):
+    for f in ("qft_pass_kernels.cuh", "qft_device.cuh", "qft_df.cuh", "qft_pair.cuh", "plan.hpp"):
         h.update(open(os.path.join(ROOT, "paper_2606_18981_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
