@@ -17,7 +17,7 @@ cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtenso
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes);
 cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                           cudaStream_t stream);
-cudaError_t launch_pass_df(int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+cudaError_t launch_pass_df(int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                            cudaStream_t stream);
 cudaError_t launch_df_maxexp(const void* state, size_t n_amps, int* out, int num_sms, cudaStream_t stream);
 cudaError_t launch_tc_pass(int dir, int prec, const CUtensorMap& map, const PassParams& P, const void* a_hi,

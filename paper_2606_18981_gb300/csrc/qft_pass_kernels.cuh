@@ -161,7 +161,10 @@ __device__ __forceinline__ void dispatch_r(const PassParams& P, int s, const Gro
         case 1: run_stage<T, DIR, 1, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc, io); break;
         case 2: run_stage<T, DIR, 2, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc, io); break;
         case 3: run_stage<T, DIR, 3, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc, io); break;
-        case 4: run_stage<T, DIR, 4, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc, io); break;
+        case 4:
+            if constexpr (MAXR >= 4)
+                run_stage<T, DIR, 4, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc, io);
+            break;
         default:
             if constexpr (MAXR >= 5)
                 run_stage<T, DIR, 5, KIND, NT>(P, S, tab, toff, A, Bb, out_tile, scale, U, acc_norm, norm_acc, io);
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(NT, MINB)
             const bool last_stage = (s == P.nstages - 1);
             const bool from_A = (s == 0);
             if (ok)
-                dispatch_stage<T, DIR, NT, (NT <= 256 && MINB == 1 && !Tr::kDF) ? 5 : 4>(
+                dispatch_stage<T, DIR, NT, (NT <= 256 && MINB == 1 && !Tr::kDF) ? 5 : (Tr::kDF && NT > 256) ? 3 : 4>(
                     P, s, tab, Ab, B, out_tile, scale, Ucur + P.st[s].uoff, P.first && !P.last, norm_acc, io);
             if (last_stage) compute_tile_twiddles<T, DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1]);
             if (from_A) {

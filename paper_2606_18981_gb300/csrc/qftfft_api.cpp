@@ -362,6 +362,10 @@ int plan_passes(qft_plan_s* pl) {
     std::vector<int> L1 = ident;
     if (natural) {
         ctop = std::min({c1, a[0], TB - a[P - 1], a[P - 1]});
+        // pass_split: the first pass keeps its extra batch wires on the input
+        // side, and the top wires moved low stay at the coalescing minimum so
+        // the last pass's wires keep forming as few blocks as possible
+        if (pl->pass_split == 1) ctop = std::min(ctop, pl->cmin);
         if (ctop < 1) return QFT_ERR_UNSUPPORTED;
         for (int e = 0; e < ctop; ++e) {
             L1[n - 1 - e] = e;           // top wires to the lowest addresses (their final place)
@@ -622,12 +626,12 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
     // wires keep the kernel within the 128 registers that needs.
     if (dtype == QFT_C64 && !pl->precision && pl->threads == 256 && pl->TB <= 12 && !rmax_given)
         pl->rmax = std::min(pl->rmax, 4);
-    // complex128 runs in double-float unless FP64 was asked for: 256 threads,
-    // blocks of <= 4 wires (16 pairs of pairs per thread in registers).
+    // complex128 runs in double-float unless FP64 was asked for: 256 threads
+    // with blocks of <= 4 wires (16 pair-of-pairs amplitudes per thread in
+    // registers), or 512 threads with blocks of <= 3 wires (twice the warps).
     if (dtype == QFT_C128 && !fp64) {
         pl->df = true;
-        pl->threads = 256;
-        pl->rmax = std::min(pl->rmax, 4);
+        pl->rmax = std::min(pl->rmax, pl->threads == 512 ? 3 : 4);
     }
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) {
@@ -766,7 +770,7 @@ int execute_range(qft_plan_t pl, const void* d_in, void* d_state, void* d_worksp
             e = launch_tc_pass(pl->dir, pl->precision, pl->maps[i], P, ph.tc_a_hi, ph.tc_a_lo, ph.tc_kpad,
                                ph.tc_ncols, ph.grid, ph.smem, st);
         else if (pl->df)
-            e = launch_pass_df(pl->dir, pl->maps[i], P, ph.grid, ph.smem, st);
+            e = launch_pass_df(pl->dir, pl->threads, pl->maps[i], P, ph.grid, ph.smem, st);
         else
             e = launch_pass(pl->dtype, pl->dir, pl->threads, ph.minb, pl->maps[i], P, ph.grid, ph.smem, st);
         if (e != cudaSuccess) return cuda_fail(e);

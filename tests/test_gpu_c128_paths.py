@@ -28,8 +28,8 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def run(x, n, k=-1, direction=-1, order=0, mode=0, precision=0):
-    p = q.Plan(n, k, direction, "c128", order, precision=precision)
+def run(x, n, k=-1, direction=-1, order=0, mode=0, precision=0, threads=0):
+    p = q.Plan(n, k, direction, "c128", order, precision=precision, threads=threads)
     state = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
     p.load(state, torch.from_numpy(np.ascontiguousarray(x)).pin_memory())
     ws = p.alloc_workspace()
@@ -97,3 +97,14 @@ def test_df_matches_fp64_path():
     b, sb = run(x, n, precision=6)
     assert rel_l2(a, b) <= tol(n)
     assert abs(sa - sb) <= 1e-14 * sb
+
+
+@pytest.mark.parametrize("n", [10, 15, 20, 23])
+@pytest.mark.parametrize("order", [0, 1])
+def test_df_512_threads(oracle_mod, n, order):
+    """The 512-thread double-float kernel (blocks of <= 3 wires) against the oracle."""
+    x = qft_inputs.tones(n, seed=400 + n)
+    for direction, k in ((-1, -1), (+1, 5)):
+        got, _ = run(x, n, k, direction, order, 0, 0, threads=512)
+        ref, _ = oracle_mod.qft(x, k, direction, 0, order == 0)
+        assert rel_l2(got, ref) <= tol(n)
