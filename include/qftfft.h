@@ -143,6 +143,9 @@ typedef struct {
     int coalesce_bits[8];            /* log2(contiguous amplitudes per run) per pass   */
     size_t workspace_bytes;          /* qft_workspace_size()                            */
     long long bytes_per_execute;     /* algorithmic HBM bytes: passes * 2 * N * elem   */
+    int n_addr, w0;                  /* array of 2^n_addr amplitudes; the transform acts
+                                        on index bits [w0, w0 + n) (qft_plan_create:
+                                        n_addr = n, w0 = 0)                            */
 } qft_plan_info;
 
 /* Step 2 (Sec. 3, Fig. 1): build the circuit for n qubits, cutoff k
@@ -152,6 +155,24 @@ typedef struct {
  * (c64) or 33 (c128).  *out is set to NULL on failure. */
 int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, const qft_opts* opts);
 int qft_plan_destroy(qft_plan_t plan);
+
+/* A QFT on a subset of the index bits (multi-dimensional and strided batched
+ * transforms as QFTs on qubit subsets): the array has 2^n_addr amplitudes,
+ * and the n-wire (A)QFT of Sec. 3 acts on the qubits q_w0 .. q_{w0+n-1}
+ * (index bits [w0, w0 + n)), independently for every value of the other
+ * index bits.  A row-major 2^a x 2^b array transforms along its rows with
+ * (n_addr = a + b, w0 = 0, n = b) and along its columns with (w0 = b, n = a);
+ * both in turn give the 2-D DFT.  NATURAL order reverses only the n
+ * transform bits.  Supported shapes: w0 = 0 (any n, the planner of
+ * qft_plan_create with the upper bits as a batch index); the n wires plus
+ * min(w0, 4) low batch bits fit one tile (one HBM pass); or w0 >= 4 (3 for
+ * complex128) for any n (several passes).  Other shapes return
+ * QFT_ERR_UNSUPPORTED, as do the tensor-core tiers.  Execution as for qft_plan_create plans (load, execute,
+ * execute_oop, read with 2^n_addr amplitudes), except that QFT_SCALE_STATE is
+ * rejected (QFT_ERR_BAD_ARG): there is no single state to normalise.  Subset
+ * plans are not batched (qft_batch_create: QFT_ERR_UNSUPPORTED). */
+int qft_plan_create_subset(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction, int dtype,
+                           const qft_opts* opts);
 int qft_plan_get_info(qft_plan_t plan, qft_plan_info* info);
 
 /* Bytes of caller-allocated device workspace qft_execute needs (always > 0:

@@ -51,7 +51,7 @@ class PlanInfo(ctypes.Structure):
                 ("passes", ctypes.c_int), ("wires_per_pass", ctypes.c_int * 8),
                 ("stages_per_pass", ctypes.c_int * 8), ("tile_bits", ctypes.c_int * 8),
                 ("coalesce_bits", ctypes.c_int * 8), ("workspace_bytes", ctypes.c_size_t),
-                ("bytes_per_execute", ctypes.c_longlong)]
+                ("bytes_per_execute", ctypes.c_longlong), ("n_addr", ctypes.c_int), ("w0", ctypes.c_int)]
 
 
 class Opts(ctypes.Structure):
@@ -69,6 +69,8 @@ _lib.qft_last_cuda_error.restype = ctypes.c_int
 _lib.qft_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(Opts)]
 _lib.qft_plan_destroy.argtypes = [_vp]
+_lib.qft_plan_create_subset.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts)]
 _lib.qft_plan_get_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
 _lib.qft_workspace_size.argtypes = [_vp]
 _lib.qft_workspace_size.restype = ctypes.c_size_t
@@ -159,12 +161,17 @@ class Plan:
     def __init__(self, n: int, k: int = -1, direction: int = FORWARD, dtype="c64", order: int = ORDER_NATURAL,
                  tile_bits: int = 0, coalesce_bits: int = 0, max_stage_bits: int = 0,
                  wait_limit_ms: int = 0, test_skip_first_load: int = 0, threads: int = 0, precision: int = 0,
-                 paired: int = 0, pass_split: int = 0, tuned: bool = False):
+                 paired: int = 0, pass_split: int = 0, tuned: bool = False, n_addr: int | None = None,
+                 w0: int = 0):
+        """n_addr / w0: a QFT on index bits [w0, w0 + n) of 2^n_addr amplitudes (qft_plan_create_subset)."""
         self._h = _vp()
         self.n, self.k, self.direction = int(n), int(k), int(direction)
+        self.n_addr = int(n) if n_addr is None else int(n_addr)
+        self.w0 = int(w0)
+        subset = self.n_addr != self.n or self.w0 != 0
         self.dtype = _dtype_code(dtype)
         self.order = int(order)
-        if tuned and precision == 0:  # plan shape from the autotuner's cache, where it has one
+        if tuned and precision == 0 and not subset:  # plan shape from the autotuner's cache, where it has one
             from .autotune import best_opts
 
             t = best_opts(self.n, "c64" if self.dtype == C64 else "c128")
@@ -176,8 +183,13 @@ class Plan:
             pass_split = pass_split or t.get("pass_split", 0)
         opts = Opts(order, tile_bits, coalesce_bits, max_stage_bits, wait_limit_ms, test_skip_first_load, threads,
                     precision, paired, pass_split)
-        _check(_lib.qft_plan_create(ctypes.byref(self._h), self.n, self.k, self.direction, self.dtype,
-                                    ctypes.byref(opts)), "qft_plan_create")
+        if subset:
+            _check(_lib.qft_plan_create_subset(ctypes.byref(self._h), self.n_addr, self.w0, self.n, self.k,
+                                               self.direction, self.dtype, ctypes.byref(opts)),
+                   "qft_plan_create_subset")
+        else:
+            _check(_lib.qft_plan_create(ctypes.byref(self._h), self.n, self.k, self.direction, self.dtype,
+                                        ctypes.byref(opts)), "qft_plan_create")
 
     @property
     def handle(self) -> int:
@@ -185,7 +197,8 @@ class Plan:
 
     @property
     def N(self) -> int:
-        return 1 << self.n
+        """Amplitudes of the state buffer (2^n_addr)."""
+        return 1 << self.n_addr
 
     @property
     def elem_bytes(self) -> int:
@@ -419,6 +432,32 @@ def fft(x, k: int | None = None, inverse: bool = False, norm: str = "backward", 
     return out
 
 
+def fft2(x, inverse: bool = False, norm: str = "backward"):
+    """numpy.fft.fft2 / ifft2 of a CUDA complex (2^a, 2^b) tensor: the QFT on the
+    column-index qubits (each row) and then on the row-index qubits (each
+    column), as two subset plans of the a + b qubit register."""
+    import torch
+
+    if not x.is_cuda or x.dim() != 2:
+        raise ValueError("fft2 expects a 2-D CUDA tensor")
+    R, C = x.shape
+    a, b = R.bit_length() - 1, C.bit_length() - 1
+    if R < 2 or C < 2 or (1 << a) != R or (1 << b) != C:
+        raise QftError(ERR_SIZE, "fft2")
+    direction = INVERSE if inverse else FORWARD
+    mode = {("backward", False): SCALE_UNNORM, ("backward", True): SCALE_INV_N,
+            ("ortho", False): SCALE_UNITARY, ("ortho", True): SCALE_UNITARY,
+            ("forward", False): SCALE_INV_N, ("forward", True): SCALE_UNNORM}[(norm, bool(inverse))]
+    dt = _dtype_code(x.dtype)
+    rows = Plan(b, -1, direction, dt, n_addr=a + b, w0=0)
+    cols = Plan(a, -1, direction, dt, n_addr=a + b, w0=b)
+    out = torch.empty_like(x)
+    ws = torch.empty(max(rows.workspace_size(), cols.workspace_size()), dtype=torch.uint8, device=x.device)
+    rows.execute_oop(x.contiguous(), out, ws, mode)
+    cols.execute(out, ws, mode)
+    return out
+
+
 _rplan_cache: dict = {}
 
 
@@ -460,5 +499,5 @@ def irfft(X, n: int | None = None, norm: str = "backward"):
     return out
 
 
-__all__ = ["Plan", "RealPlan", "Batch", "Server", "PlanInfo", "QftError", "fft", "rfft", "irfft", "lib", "C64", "C128", "FORWARD", "INVERSE",
+__all__ = ["Plan", "RealPlan", "Batch", "Server", "PlanInfo", "QftError", "fft", "fft2", "rfft", "irfft", "lib", "C64", "C128", "FORWARD", "INVERSE",
            "SCALE_STATE", "SCALE_UNITARY", "SCALE_UNNORM", "SCALE_INV_N", "ORDER_NATURAL", "ORDER_BITREV"]

@@ -69,6 +69,10 @@ struct qft_plan_s {
     int precision = 0;  // QFT_PREC_* (tensor-core tiers; QFT_PREC_FP64 is kept in fp64 below)
     bool df = false;    // complex128 in double-float arithmetic (the default for complex128)
     int n = 0, k = -1, kk = 0, dir = -1, dtype = 0, order = 0;
+    // Subset plans: the QFT acts on index bits [w0, w0 + n) of an array of
+    // 2^n_addr amplitudes, once for every value of the other bits.  Ordinary
+    // plans have n_addr = n and w0 = 0.
+    int n_addr = 0, w0 = 0;
     size_t esize = 8;
     int TB = 13, cmin = 2, rmax = 4;
     int threads = 256;  // CTA size of the pass kernel (256: stages of <= 5 wires; 512: <= 4)

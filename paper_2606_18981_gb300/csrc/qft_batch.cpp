@@ -55,7 +55,7 @@ size_t meta_bytes(const qft_plan_s* pl) {
 }
 size_t work_bytes(const qft_plan_s* pl) {
     const bool need = pl->order == QFT_ORDER_NATURAL && pl->passes.size() > 1;
-    return need ? align_up((size_t(1) << pl->n) * pl->esize) : 0;
+    return need ? align_up((size_t(1) << pl->n_addr) * pl->esize) : 0;
 }
 
 void free_batch(qft_batch_s* b) {
@@ -92,6 +92,7 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
         if (!plans[i] || !d_states[i] || (reinterpret_cast<uintptr_t>(d_states[i]) & 255)) return QFT_ERR_BAD_ARG;
         if (plans[i]->dtype != plans[0]->dtype || plans[i]->dir != plans[0]->dir) return QFT_ERR_UNSUPPORTED;
         if (plans[i]->precision) return QFT_ERR_UNSUPPORTED;  // tensor-core tier plans run only through qft_execute
+        if (plans[i]->n_addr != plans[i]->n) return QFT_ERR_UNSUPPORTED;  // subset plans run only through qft_execute
     }
     if (workspace_bytes < qft_batch_workspace_size(plans, count)) return QFT_ERR_SIZE;
     auto fn = get_encode_fn();

@@ -78,16 +78,22 @@ int effective_k(int n, int k) { return (k < 0 || k > n - 1) ? std::max(n - 1, 0)
 
 // Build one pass from its wire group [glo, glo + a), batch wires, and the
 // input/output wire -> address maps.
+//
+// Logical wires 0 .. m-1 are the transform's wires (m = pl->n); a subset plan
+// has further logical wires m .. n-1 (n = pl->n_addr address bits) that carry
+// no gate: the kernel's phases only see bits below m (P.n = m), so these
+// wires act as a batch index.
 bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<int>& batch_in,
                 const std::vector<int>& Lin, const std::vector<int>& Lout, bool first, bool last) {
-    const int n = pl->n;
+    const int n = pl->n_addr;
+    const int m = pl->n;
     PassParams& P = ph.prm;
     std::memset(&P, 0, sizeof(P));
-    P.n = n;
+    P.n = m;
     P.kk = pl->kk;
     P.first = first;
     P.last = last;
-    P.inv_root_n = std::ldexp(1.0, -n / 2) * ((n & 1) ? std::sqrt(0.5) : 1.0);
+    P.inv_root_n = std::ldexp(1.0, -m / 2) * ((m & 1) ? std::sqrt(0.5) : 1.0);
     ph.wires = a;
 
     std::vector<char> in_tile(n, 0);
@@ -221,11 +227,11 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
             S.r = r;
             S.wlo = top - r + 1;
             S.q = pos[S.wlo];
-            S.cross = (top < n - 1) ? 1 : 0;
+            S.cross = (top < m - 1) ? 1 : 0;
             S.ngbits = tb - r - pb0;
             S.tile_above = 0;
             for (int w : nt)
-                if (w > top) S.tile_above = 1;
+                if (w > top && w < m) S.tile_above = 1;
             for (int e = 0; e < kMaxR; ++e)
                 S.img[e] = e >= r ? 0
                            : paired ? static_cast<int32_t>(swizzle(1u << (S.q + e - 1), 16))  // 16-byte pair units
@@ -266,8 +272,8 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
         const int hi_w = S.wlo + S.r - 1;
         S.lo_tw = S.hi_tw = 0;
         for (int i = 0; i < S.ngbits; ++i)
-            if (P.p_wire[S.gpos[i]] > hi_w) (i < 5 ? S.lo_tw : S.hi_tw) = 1;
-        if (paired && P.p_wire[0] > hi_w) S.lo_tw = 1;  // the lane entries carry the pair wire's phase
+            if (P.p_wire[S.gpos[i]] > hi_w && P.p_wire[S.gpos[i]] < m) (i < 5 ? S.lo_tw : S.hi_tw) = 1;
+        if (paired && P.p_wire[0] > hi_w && P.p_wire[0] < m) S.lo_tw = 1;  // the lane entries carry the pair wire's phase
         if (!S.lo_tw && !S.hi_tw) S.hi_tw = 1;  // keep one (all-ones) factor so tau is defined
     }
     int ntab = 0, nU = 0;
@@ -298,11 +304,17 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
     return true;
 }
 
+int plan_passes_subset(qft_plan_s* pl);
+
+// The whole register, or (subset plans with w0 = 0) its low n bits with the
+// bits above as a batch index: logical wires n .. n_addr-1 stay at their own
+// addresses in every map.
 int plan_passes(qft_plan_s* pl) {
-    const int n = pl->n;
-    std::vector<int> ident(n);
-    for (int w = 0; w < n; ++w) ident[w] = w;
-    std::vector<int> brev(n);
+    if (pl->w0 != 0) return plan_passes_subset(pl);
+    const int n = pl->n, na = pl->n_addr;
+    std::vector<int> ident(na);
+    for (int w = 0; w < na; ++w) ident[w] = w;
+    std::vector<int> brev = ident;
     for (int w = 0; w < n; ++w) brev[w] = n - 1 - w;
     const bool natural = pl->order == QFT_ORDER_NATURAL;
 
@@ -383,8 +395,8 @@ int plan_passes(qft_plan_s* pl) {
             Lout = natural ? L1 : ident;
         } else if (!last) {
             const int cj = std::min(TB - a[j], glo[j]);
-            std::vector<int> wat(n);
-            for (int w = 0; w < n; ++w) wat[Lin[w]] = w;
+            std::vector<int> wat(na);
+            for (int w = 0; w < na; ++w) wat[Lin[w]] = w;
             for (int adr = 0; adr < cj; ++adr) batch.push_back(wat[adr]);
             Lout = Lin;
         } else {
@@ -393,6 +405,71 @@ int plan_passes(qft_plan_s* pl) {
             Lout = natural ? brev : ident;
         }
         if (!build_pass(pl, ph, glo[j], a[j], batch, Lin, Lout, first, last)) return QFT_ERR_UNSUPPORTED;
+        ph.prm.load_mode = 0;
+        if (natural) {
+            ph.in_buf = first ? 0 : 1;
+            ph.out_buf = last ? 0 : 1;
+        } else {
+            ph.in_buf = ph.out_buf = 0;
+        }
+        pl->passes.push_back(ph);
+    }
+    const int g1 = pl->passes[0].grid;
+    if (g1 > kMaxPartials) return QFT_ERR_UNSUPPORTED;
+    pl->passes.back().prm.npartials = g1;
+    return QFT_OK;
+}
+
+// Subset plans (a QFT on index bits [w0, w0 + m) of 2^n_addr amplitudes, for
+// every value of the other bits).  Logical wire w < m sits at address
+// w0 + w; the other logical wires m, m+1, ... take the remaining addresses in
+// increasing order.  NATURAL order reverses the transform's bits only:
+// logical w < m leaves through address w0 + m - 1 - w.
+//   * One pass when the m wires plus the low batch bits that make the HBM
+//     runs fit a tile: each tile holds whole transforms and is rewritten in
+//     place.
+//   * Several passes when the lowest cmin address bits are batch bits
+//     (w0 >= cmin): every pass's tile takes them for its runs, the passes
+//     cover the transform's wires top-down, and the layout stays the
+//     identity until the last pass (NATURAL: through the workspace buffer,
+//     whose last pass writes the reversed addresses; BITREV: in place).
+int plan_passes_subset(qft_plan_s* pl) {
+    const int n = pl->n_addr, m = pl->n, w0 = pl->w0;
+    const bool natural = pl->order == QFT_ORDER_NATURAL;
+    std::vector<int> Lin(n), Lout(n);
+    {
+        int b = m;
+        for (int adr = 0; adr < n; ++adr)
+            if (adr < w0 || adr >= w0 + m) Lin[b++] = adr;
+        for (int w = 0; w < m; ++w) Lin[w] = w0 + w;
+        Lout = Lin;
+        if (natural)
+            for (int w = 0; w < m; ++w) Lout[w] = w0 + m - 1 - w;
+    }
+    const int TB = pl->TB, cmin = pl->cmin;
+    const int low = std::min(w0, cmin);  // low batch bits a single-pass tile needs for its runs
+    if (m + low <= TB) {
+        PassHost ph;
+        if (!build_pass(pl, ph, 0, m, {}, Lin, Lout, true, true)) return QFT_ERR_UNSUPPORTED;
+        ph.prm.load_mode = ph.run_bits >= ph.prm.tb ? 1 : 0;  // tiles that are address bits 0 .. tb-1: 1D copies
+        ph.in_buf = ph.out_buf = 0;
+        pl->passes.push_back(ph);
+        return QFT_OK;
+    }
+    if (w0 < cmin) return QFT_ERR_UNSUPPORTED;
+    const int cap = TB - cmin;
+    const int P = (m + cap - 1) / cap;
+    if (P > kMaxPasses) return QFT_ERR_UNSUPPORTED;
+    std::vector<int> a(P, m / P);
+    for (int j = 0; j < m % P; ++j) a[j] += 1;
+    std::vector<int> batch;
+    for (int adr = 0; adr < cmin; ++adr) batch.push_back(m + adr);  // logical wires at addresses 0 .. cmin-1
+    int top = m;
+    for (int j = 0; j < P; ++j) {
+        top -= a[j];
+        PassHost ph;
+        const bool first = j == 0, last = j == P - 1;
+        if (!build_pass(pl, ph, top, a[j], batch, Lin, last ? Lout : Lin, first, last)) return QFT_ERR_UNSUPPORTED;
         ph.prm.load_mode = 0;
         if (natural) {
             ph.in_buf = first ? 0 : 1;
@@ -556,16 +633,26 @@ const char* qft_strerror(int code) {
     }
 }
 
-int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, const qft_opts* opts) {
+}  // extern "C"
+
+namespace {
+
+// Plan of an n-wire QFT on index bits [w0, w0 + n) of 2^n_addr amplitudes.
+int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction, int dtype, const qft_opts* opts) {
     if (!out) return QFT_ERR_BAD_ARG;
     *out = nullptr;
     if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
     if (direction != QFT_FORWARD && direction != QFT_INVERSE) return QFT_ERR_BAD_ARG;
     const int nmax = dtype == QFT_C64 ? 34 : 33;
-    if (n < 1 || n > nmax) return QFT_ERR_BAD_ARG;
+    if (n < 1 || w0 < 0 || n_addr > nmax || w0 + n > n_addr) return QFT_ERR_BAD_ARG;
+    const bool subset = n_addr != n;
+    if (subset && opts && opts->precision != QFT_PREC_NATIVE && opts->precision != QFT_PREC_FP64)
+        return QFT_ERR_UNSUPPORTED;
     qft_plan_s* pl = new (std::nothrow) qft_plan_s();
     if (!pl) return QFT_ERR_NOMEM;
     pl->n = n;
+    pl->n_addr = n_addr;
+    pl->w0 = w0;
     pl->k = k;
     pl->kk = effective_k(n, k);
     pl->dir = direction;
@@ -610,7 +697,7 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
             pl->threads = opts->threads;
             if (pl->threads == 512) pl->rmax = 4;
         }
-        pl->pairing = opts->paired && dtype == QFT_C64 && pl->threads == 256 && !pl->precision;
+        pl->pairing = opts->paired && dtype == QFT_C64 && pl->threads == 256 && !pl->precision && !subset;
         if (opts->pass_split < 0 || opts->pass_split > 1) { delete pl; return QFT_ERR_BAD_ARG; }
         pl->pass_split = opts->pass_split;
         if (opts->max_stage_bits) {
@@ -652,11 +739,24 @@ int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, con
         delete pl;
         return rc;
     }
-    const size_t N = size_t(1) << n;
+    const size_t N = size_t(1) << n_addr;
     const bool need_work = pl->order == QFT_ORDER_NATURAL && pl->passes.size() > 1;
     pl->ws_bytes = kMetaBytes + (need_work ? N * pl->esize : 0);
     *out = pl;
     return QFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qft_plan_create(qft_plan_t* out, int n, int k, int direction, int dtype, const qft_opts* opts) {
+    return create_plan(out, n, 0, n, k, direction, dtype, opts);
+}
+
+int qft_plan_create_subset(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction, int dtype,
+                           const qft_opts* opts) {
+    return create_plan(out, n_addr, w0, n, k, direction, dtype, opts);
 }
 
 int qft_plan_destroy(qft_plan_t plan) {
@@ -684,7 +784,9 @@ int qft_plan_get_info(qft_plan_t pl, qft_plan_info* info) {
         info->coalesce_bits[i] = ph.run_bits;
     }
     info->workspace_bytes = pl->ws_bytes;
-    info->bytes_per_execute = static_cast<long long>(pl->passes.size()) * 2LL * (1LL << pl->n) * static_cast<long long>(pl->esize);
+    info->bytes_per_execute = static_cast<long long>(pl->passes.size()) * 2LL * (1LL << pl->n_addr) * static_cast<long long>(pl->esize);
+    info->n_addr = pl->n_addr;
+    info->w0 = pl->w0;
     return QFT_OK;
 }
 
@@ -692,7 +794,7 @@ size_t qft_workspace_size(qft_plan_t pl) { return pl ? pl->ws_bytes : 0; }
 
 int qft_load(qft_plan_t pl, void* d_state, const void* src, size_t len, int src_on_device, qft_stream_t stream) {
     if (!pl || !d_state || !src) return QFT_ERR_BAD_ARG;
-    if (len != (size_t(1) << pl->n)) return QFT_ERR_SIZE;
+    if (len != (size_t(1) << pl->n_addr)) return QFT_ERR_SIZE;
     if (src == d_state) return QFT_OK;
     cudaError_t e = cudaMemcpyAsync(d_state, src, len * pl->esize,
                                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -703,7 +805,7 @@ int qft_load(qft_plan_t pl, void* d_state, const void* src, size_t len, int src_
 int qft_load_padded(qft_plan_t pl, void* d_state, const void* src, size_t len, int src_on_device,
                     qft_stream_t stream) {
     if (!pl || !d_state || (!src && len)) return QFT_ERR_BAD_ARG;
-    const size_t N = size_t(1) << pl->n;
+    const size_t N = size_t(1) << pl->n_addr;
     if (len > N) return QFT_ERR_SIZE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* dst = static_cast<char*>(d_state);
@@ -718,7 +820,7 @@ int qft_load_padded(qft_plan_t pl, void* d_state, const void* src, size_t len, i
 int qft_read(qft_plan_t pl, const void* d_state, void* dst, int dst_on_device, qft_stream_t stream) {
     if (!pl || !d_state || !dst) return QFT_ERR_BAD_ARG;
     if (dst == d_state) return QFT_OK;
-    cudaError_t e = cudaMemcpyAsync(dst, d_state, (size_t(1) << pl->n) * pl->esize,
+    cudaError_t e = cudaMemcpyAsync(dst, d_state, (size_t(1) << pl->n_addr) * pl->esize,
                                     dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                     reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? QFT_OK : cuda_fail(e);
@@ -731,6 +833,8 @@ int execute_range(qft_plan_t pl, const void* d_in, void* d_state, void* d_worksp
                   int scale_mode, qft_stream_t stream, size_t i0, size_t i1) {
     if (!pl || !d_in || !d_state || !d_workspace) return QFT_ERR_BAD_ARG;
     if (scale_mode < QFT_SCALE_STATE || scale_mode > QFT_SCALE_INV_N) return QFT_ERR_BAD_ARG;
+    // a subset plan runs many transforms at once: there is no one state to normalise
+    if (pl->n_addr != pl->n && scale_mode == QFT_SCALE_STATE) return QFT_ERR_BAD_ARG;
     if ((reinterpret_cast<uintptr_t>(d_state) & 255) || (reinterpret_cast<uintptr_t>(d_workspace) & 255) ||
         (reinterpret_cast<uintptr_t>(d_in) & 255))
         return QFT_ERR_BAD_ARG;
@@ -750,7 +854,8 @@ int execute_range(qft_plan_t pl, const void* d_in, void* d_state, void* d_worksp
         e = cudaMemsetAsync(ws + kStatusOff, 0, kMaxExpOff + sizeof(int32_t) - kStatusOff, st);
         if (e != cudaSuccess) return cuda_fail(e);
         if (pl->df) {
-            e = launch_df_maxexp(d_in, size_t(1) << pl->n, reinterpret_cast<int*>(ws + kMaxExpOff), pl->num_sms, st);
+            e = launch_df_maxexp(d_in, size_t(1) << pl->n_addr, reinterpret_cast<int*>(ws + kMaxExpOff), pl->num_sms,
+                                 st);
             if (e != cudaSuccess) return cuda_fail(e);
         }
     }
@@ -822,7 +927,8 @@ int qft_plan_describe_pass(qft_plan_t pl, int i, long long* out, int cap) {
     for (int d = 0; d < kMaxDims; ++d) v.push_back((long long)ph.gdim[d]);
     for (int d = 0; d < 4; ++d) v.push_back((long long)ph.gstride[d]);
     for (int d = 0; d < kMaxDims; ++d) v.push_back((long long)ph.box[d]);
-    v.insert(v.end(), {ph.grid, (long long)ph.smem, ph.in_buf, ph.out_buf, P.npartials, ph.run_bits, P.paired, ph.minb});
+    v.insert(v.end(), {ph.grid, (long long)ph.smem, ph.in_buf, ph.out_buf, P.npartials, ph.run_bits, P.paired, ph.minb,
+                       pl->n_addr});
     for (size_t j = 0; j < v.size() && static_cast<int>(j) < cap; ++j) out[j] = v[j];
     return static_cast<int>(v.size());
 }

@@ -41,7 +41,7 @@ def parse(rec):
     P["gdim"] = [nx() for _ in range(K_MAX_DIMS)]
     P["gstride"] = [nx() for _ in range(4)]
     P["box"] = [nx() for _ in range(K_MAX_DIMS)]
-    for k in ("grid", "smem", "in_buf", "out_buf", "npartials", "run_bits", "paired", "minb"):
+    for k in ("grid", "smem", "in_buf", "out_buf", "npartials", "run_bits", "paired", "minb", "n_addr"):
         P[k] = nx()
     return P
 
@@ -65,15 +65,15 @@ def check_structure(P, esize):
     """Bijection checks that need no data: tile bits + tile-coordinate bits cover
     the input and the output address bits exactly once, TMA boxes fit, stage
     blocks are contiguous runs of wires and tile bits, lane maps are permutations."""
-    n, tb = P["n"], P["tb"]
+    n, tb, na = P["n"], P["tb"], P["n_addr"]  # transform wires; address bits (> n for subset plans)
     wires = sorted(P["p_wire"][:tb] + [s["wire"] + i for s in P["seg"] for i in range(s["len"])])
-    assert wires == list(range(n)), "tile + segment wires must be a permutation of the wires"
+    assert wires == list(range(na)), "tile + segment wires must be a permutation of the wires"
     outs = list(P["p_out"][:tb])
     for s in P["seg"]:
         outs += [s["out"] - i if s["out_rev"] else s["out"] + i for i in range(s["len"])]
-    assert sorted(outs) == list(range(n)), "output address bits must be a permutation"
-    assert sum(s["len"] for s in P["seg"]) == n - tb
-    assert P["num_tiles"] == 1 << (n - tb)
+    assert sorted(outs) == list(range(na)), "output address bits must be a permutation"
+    assert sum(s["len"] for s in P["seg"]) == na - tb
+    assert P["num_tiles"] == 1 << (na - tb)
     pb0 = 1 if P["paired"] else 0
     if P["paired"]:
         assert esize == 8 and not (P["first"] and P["last"])
@@ -89,11 +89,12 @@ def check_structure(P, esize):
     uoff = 0
     for s in P["st"]:
         hi = s["wlo"] + s["r"] - 1
-        assert s["tile_above"] == int(any(w > hi for w in seg_wires)), "per-tile twiddle flag"
+        above = lambda w: hi < w < n  # noqa: E731  (batch wires of subset plans carry no phase)
+        assert s["tile_above"] == int(any(above(w) for w in seg_wires)), "per-tile twiddle flag"
         assert s["uoff"] == uoff
-        lanes_above = any(P["p_wire"][s["gpos"][i]] > hi for i in range(min(5, s["ngbits"])))
-        lanes_above = lanes_above or (P["paired"] and P["p_wire"][0] > hi)
-        high_above = any(P["p_wire"][s["gpos"][i]] > hi for i in range(5, s["ngbits"]))
+        lanes_above = any(above(P["p_wire"][s["gpos"][i]]) for i in range(min(5, s["ngbits"])))
+        lanes_above = lanes_above or (P["paired"] and above(P["p_wire"][0]))
+        high_above = any(above(P["p_wire"][s["gpos"][i]]) for i in range(5, s["ngbits"]))
         assert s["lo_tw"] == int(lanes_above) and s["hi_tw"] == int(high_above or not lanes_above)
         uoff += s["r"]
     # blocks processed top-down and covering each wire once
@@ -241,7 +242,7 @@ def emulate(plan, x, scale_mode=0):
     """Replay every pass of a Plan on input x (numpy complex); returns the output."""
     esize = 8 if plan.dtype == 0 else 16
     info = plan.info()
-    N = 1 << plan.n
+    N = 1 << info.n_addr
     state = np.asarray(x, dtype=np.complex128).copy()
     work = np.zeros(N, dtype=np.complex128)
     bufs = [state, work]

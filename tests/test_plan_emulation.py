@@ -130,3 +130,49 @@ def test_pass_split_plans(oracle_mod, dt, n, tbits):
     got = emulate(p1, x, q.SCALE_STATE)
     ref, _ = oracle_mod.qft(x, k=-1, sign=q.FORWARD, mode=q.SCALE_STATE, natural_order=True)
     assert rel_l2(got, ref) < 1e-12
+
+
+def subset_reference(oracle_mod, x, n_addr, w0, m, k, sign, mode, natural):
+    """The oracle's m-wire transform applied to every sub-vector along index
+    bits [w0, w0 + m) (the other bits fixed)."""
+    a = np.asarray(x, dtype=np.complex128).reshape(1 << (n_addr - w0 - m), 1 << m, 1 << w0)
+    out = np.empty_like(a)
+    for hi in range(a.shape[0]):
+        for lo in range(a.shape[2]):
+            out[hi, :, lo], _ = oracle_mod.qft(a[hi, :, lo].copy(), k=k, sign=sign, mode=mode, natural_order=natural)
+    return out.ravel()
+
+
+SUBSET_CASES = []
+for dt in ("c64", "c128"):
+    for order in (q.ORDER_NATURAL, q.ORDER_BITREV):
+        for n_addr, w0, m, tbits in ((10, 0, 6, 0), (12, 0, 8, 0), (11, 3, 5, 0), (12, 4, 8, 0), (14, 5, 9, 6),
+                                     (15, 4, 11, 7), (13, 6, 7, 0), (12, 2, 6, 0), (15, 0, 11, 6),
+                                     (16, 0, 13, 7)):
+            SUBSET_CASES.append((n_addr, w0, m, dt, order, tbits))
+
+
+@pytest.mark.parametrize("n_addr,w0,m,dt,order,tbits", SUBSET_CASES)
+def test_subset_plans_match_oracle(oracle_mod, n_addr, w0, m, dt, order, tbits):
+    """QFTs on qubit subsets: every sub-vector along bits [w0, w0 + m) transformed
+    independently (single-pass and multi-pass plans, both orders)."""
+    x = qft_inputs.gaussian(n_addr, seed=5000 + n_addr + w0, normalise=False)
+    for direction, k in ((q.FORWARD, -1), (q.INVERSE, 3)):
+        p = q.Plan(m, k, direction, dt, order, tile_bits=tbits, n_addr=n_addr, w0=w0)
+        inf = p.info()
+        assert inf.n_addr == n_addr and inf.w0 == w0 and inf.n == m
+        for i in range(inf.passes):
+            check_structure(parse(p.describe_pass(i)), 8 if dt == "c64" else 16)
+        got = emulate(p, x, q.SCALE_UNNORM)
+        ref = subset_reference(oracle_mod, x, n_addr, w0, m, k, direction, q.SCALE_UNNORM,
+                               order == q.ORDER_NATURAL)
+        assert rel_l2(got, ref) < 1e-12, (n_addr, w0, m, dt, order, direction)
+
+
+def test_subset_plan_rejections():
+    with pytest.raises(q.QftError):
+        q.Plan(20, -1, q.FORWARD, "c64", n_addr=22, w0=1)  # multi-pass with fewer than 4 low batch bits
+    with pytest.raises(q.QftError):
+        q.Plan(8, -1, q.FORWARD, "c64", n_addr=10, w0=4)   # does not fit the array
+    with pytest.raises(q.QftError):
+        q.Plan(8, -1, q.FORWARD, "c64", n_addr=12, w0=2, precision=q.PREC_FP16X3)
