@@ -357,6 +357,36 @@ size_t qft_rplan_workspace_size(qft_rplan_t plan);
 int qft_rplan_execute(qft_rplan_t plan, const void* d_in, void* d_out, void* d_workspace, int scale_mode,
                       qft_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Quantum phase estimation on the QFT engine (eigenvalue estimation, named in
+ * the paper's conclusion, Sec. 6, as the next use of a QFT state-vector
+ * simulator).  The operator U is given in its eigenbasis: d = 2^d_bits
+ * eigenvectors u_j with eigenphases theta_j in turns (U u_j = e^{2 pi i
+ * theta_j} u_j; theta_j is taken mod 1) and the input state's overlaps c_j
+ * (complex, sum |c_j|^2 = 1 for a normalised input).  The joint register
+ * holds m counting qubits in the low index bits and the system state in the
+ * high bits: 2^(m + d_bits) amplitudes of the given dtype.
+ *
+ * qft_qpe_prepare writes the state after H on every counting qubit and the
+ * controlled evolutions C-U^{2^k} (k = 0 .. m-1):
+ *     psi[j 2^m + y] = c_j exp(2 pi i sum_k y_k frac(theta_j 2^k)) / sqrt(2^m)
+ * (the phase accumulated per controlled evolution in FP64).  d_theta: d
+ * doubles, d_coef: d complex128 values, both device memory; d_workspace:
+ * qft_qpe_workspace_size(m, d_bits) bytes of device memory.  The Fourier
+ * readout is then the transform of the counting qubits with omega =
+ * e^{-2 pi i / 2^m} -- this library's QFT_FORWARD, the paper's convention,
+ * which is the textbook inverse QFT of phase estimation: a subset plan
+ * (qft_plan_create_subset(n_addr = m + d_bits, w0 = 0, n = m, k, QFT_FORWARD))
+ * executed with QFT_SCALE_UNITARY.  qft_qpe_probabilities writes
+ *     P(x) = sum_j |psi[j 2^m + x]|^2,   x = 0 .. 2^m - 1
+ * (2^m doubles, device memory): the counting register's distribution, which
+ * concentrates at x ~ theta_j 2^m.  Requires 1 <= m, 0 <= d_bits <= 20,
+ * m + d_bits <= 34 (complex64) or 33 (complex128). */
+size_t qft_qpe_workspace_size(int m, int d_bits);
+int qft_qpe_prepare(void* d_state, int m, int d_bits, const double* d_theta, const void* d_coef, int dtype,
+                    void* d_workspace, qft_stream_t stream);
+int qft_qpe_probabilities(const void* d_state, int m, int d_bits, int dtype, double* d_prob, qft_stream_t stream);
+
 /* Diagnostics: write pass i of the plan as a flat integer record (tile bits,
  * register stages with their wires and lane maps, tile-index -> wire and
  * output-address maps, tile-coordinate segments, TMA box geometry, grid,

@@ -81,6 +81,10 @@ _lib.qft_execute_pass.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int
 _lib.qft_read.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_execute_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_execute_oop.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.qft_qpe_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int]
+_lib.qft_qpe_workspace_size.restype = ctypes.c_size_t
+_lib.qft_qpe_prepare.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]
+_lib.qft_qpe_probabilities.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
 _lib.qft_rplan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts)]
 _lib.qft_rplan_destroy.argtypes = [_vp]
 _lib.qft_rplan_workspace_size.argtypes = [_vp]
@@ -458,6 +462,34 @@ def fft2(x, inverse: bool = False, norm: str = "backward"):
     return out
 
 
+def qpe(thetas, coefs, m: int, k: int = -1, dtype="c128", device="cuda"):
+    """Quantum phase estimation of an operator given by its eigenphases (turns)
+    and the input's overlaps with its eigenvectors: prepare the state after the
+    controlled evolutions, run the Fourier readout of the m counting qubits
+    (omega = e^{-2 pi i / 2^m}: FORWARD here, the textbook inverse QFT; AQFT
+    cutoff k), and return the counting register's distribution P(x), x < 2^m,
+    as a CUDA float64 tensor (it peaks at x ~ theta_j 2^m)."""
+    import torch
+
+    th = torch.as_tensor(thetas, dtype=torch.float64).reshape(-1).to(device)
+    c = torch.as_tensor(coefs, dtype=torch.complex128).reshape(-1).to(device)
+    d = th.numel()
+    db = d.bit_length() - 1
+    if d < 1 or (1 << db) != d or c.numel() != d:
+        raise QftError(ERR_SIZE, "qpe")
+    dt = _dtype_code(dtype)
+    state = torch.empty(d << m, dtype=torch.complex64 if dt == C64 else torch.complex128, device=device)
+    scratch = torch.empty(max(8, int(_lib.qft_qpe_workspace_size(m, db))), dtype=torch.uint8, device=device)
+    _check(_lib.qft_qpe_prepare(state.data_ptr(), m, db, th.data_ptr(), c.data_ptr(), dt, scratch.data_ptr(),
+                                _stream_handle(None)), "qft_qpe_prepare")
+    p = Plan(m, k, FORWARD, dt, n_addr=m + db, w0=0)
+    p.execute(state, p.alloc_workspace(device), SCALE_UNITARY)
+    prob = torch.empty(1 << m, dtype=torch.float64, device=device)
+    _check(_lib.qft_qpe_probabilities(state.data_ptr(), m, db, dt, prob.data_ptr(), _stream_handle(None)),
+           "qft_qpe_probabilities")
+    return prob
+
+
 _rplan_cache: dict = {}
 
 
@@ -499,5 +531,5 @@ def irfft(X, n: int | None = None, norm: str = "backward"):
     return out
 
 
-__all__ = ["Plan", "RealPlan", "Batch", "Server", "PlanInfo", "QftError", "fft", "fft2", "rfft", "irfft", "lib", "C64", "C128", "FORWARD", "INVERSE",
+__all__ = ["Plan", "RealPlan", "Batch", "Server", "PlanInfo", "QftError", "fft", "fft2", "rfft", "irfft", "qpe", "lib", "C64", "C128", "FORWARD", "INVERSE",
            "SCALE_STATE", "SCALE_UNITARY", "SCALE_UNNORM", "SCALE_INV_N", "ORDER_NATURAL", "ORDER_BITREV"]

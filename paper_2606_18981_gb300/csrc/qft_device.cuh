@@ -5,7 +5,9 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "plan.hpp"
@@ -14,6 +16,28 @@
 namespace qft {
 
 // ------------------------------------------------------------------ helpers
+
+// Raise a kernel's dynamic shared-memory limit to at least `smem` on the
+// current device.  The attribute belongs to the function in the device's
+// context, so it is shared by every host thread: the limit only ever grows
+// (a thread that needs less never lowers it under another thread's launch),
+// tracked per kernel (one copy of the statics per instantiation) and device.
+template <typename K>
+inline cudaError_t ensure_dynamic_smem(K kern, size_t smem) {
+    constexpr int kDevs = 64;
+    static std::atomic<size_t> done[kDevs];
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
+    if (smem <= done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem <= done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e == cudaSuccess) done[dev].store(smem, std::memory_order_release);
+    return e;
+}
 
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };

@@ -115,11 +115,9 @@ template <int DIR, int MINB>
 static cudaError_t launch_pass_p_t(const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                                    cudaStream_t stream) {
     auto kern = qft_pass_p_kernel<DIR, 256, MINB>;
-    static thread_local size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    {
+        const cudaError_t e = ensure_dynamic_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
     }
     kern<<<grid, 256, smem, stream>>>(map, P);
     return cudaGetLastError();

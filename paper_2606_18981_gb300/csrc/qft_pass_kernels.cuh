@@ -484,11 +484,9 @@ inline cudaError_t launch_batch_t(const BatchItem* items, int nitems, const Pass
                                   const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
                                   int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
     auto kern = qft_batch_kernel<T, DIR, NT, MINB>;
-    static thread_local size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    {
+        const cudaError_t e = ensure_dynamic_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
     }
     kern<<<grid, NT, smem, stream>>>(items, nitems, descs, maps, counters, next, status, wait_ns, max_tb, max_ntab);
     return cudaGetLastError();
@@ -498,11 +496,9 @@ template <typename T, int DIR, int NT, int MINB>
 inline cudaError_t launch_pass_t(const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                                  cudaStream_t stream) {
     auto kern = qft_pass_kernel<T, DIR, NT, MINB>;
-    static thread_local size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    {
+        const cudaError_t e = ensure_dynamic_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
     }
     kern<<<grid, NT, smem, stream>>>(map, P);
     return cudaGetLastError();

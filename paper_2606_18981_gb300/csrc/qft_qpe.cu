@@ -1,0 +1,137 @@
+// qft_qpe.cu -- quantum phase estimation on the QFT engine (the eigenvalue
+// estimation the paper names as the next use of a QFT state-vector
+// simulator: a state with overlap on the eigenvectors of an operator, a
+// sequence of controlled evolutions, and a Fourier readout, Sec. 6).
+//
+// The operator is given in its eigenbasis: d = 2^d_bits eigenvectors with
+// eigenphases theta_j (in turns, U u_j = e^{2 pi i theta_j} u_j) and the input
+// state's overlaps c_j.  The joint register is m counting qubits (the low index
+// bits) times the d system states (the high bits).  Starting from
+// H^{(x)m}|0> (x) sum_j c_j |u_j>, the controlled evolutions C-U^{2^k} (control
+// counting qubit k) multiply the amplitude of |y>|u_j> by e^{2 pi i theta_j 2^k}
+// for every set bit k of y, so after all m of them
+//
+//     psi[j 2^m + y] = c_j e^{2 pi i phi_j(y)} / sqrt(2^m),
+//     phi_j(y) = sum_k y_k frac(theta_j 2^k)  (mod 1),
+//
+// which qft_qpe_prepare writes in one sweep (the phase is accumulated per
+// controlled evolution, in FP64, so it is exact to rounding for any m).  The
+// Fourier readout is the transform of the counting qubits with
+// omega = e^{-2 pi i / 2^m} (the paper's QFT convention, which is the
+// textbook inverse QFT of phase estimation): a subset plan
+// (qft_plan_create_subset with w0 = 0, n = m, n_addr = m + d_bits, FORWARD,
+// scale QFT_SCALE_UNITARY).  qft_qpe_probabilities then sums |psi|^2 over the
+// system states: P(x) = sum_j |psi[j 2^m + x]|^2, the distribution of the
+// counting register, which peaks at x ~ theta_j 2^m.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/qftfft.h"
+#include "plan_host.hpp"
+
+namespace qft {
+namespace {
+
+// frac(theta_j 2^k) for k < m, j < d: one row of m per eigenphase.
+__global__ void qpe_frac_kernel(const double* __restrict__ theta, int d, int m, double* __restrict__ f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d * m) return;
+    const int j = i / m, k = i % m;
+    const double t = ldexp(theta[j], k);  // exact: a power-of-two scaling
+    f[i] = t - floor(t);
+}
+
+template <typename V, typename T>
+__global__ void __launch_bounds__(256) qpe_prepare_kernel(V* __restrict__ psi, int m, int d, const double* __restrict__ f,
+                                                          const double2* __restrict__ coef, double inv_sqrt_M) {
+    const uint64_t M = uint64_t(1) << m, total = M * uint64_t(d);
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < total; i += uint64_t(gridDim.x) * blockDim.x) {
+        const uint64_t y = i & (M - 1);
+        const int j = static_cast<int>(i >> m);
+        const double* fj = f + size_t(j) * m;
+        double ph = 0.0;
+        for (int k = 0; k < m; ++k)
+            if ((y >> k) & 1) {
+                ph += fj[k];
+                ph -= (ph >= 1.0) ? 1.0 : 0.0;
+            }
+        double s, c;
+        sincospi(2.0 * ph, &s, &c);  // |2 ph| < 2: one reduction-free evaluation
+        const double2 cj = coef[j];
+        V r;
+        r.x = static_cast<T>((cj.x * c - cj.y * s) * inv_sqrt_M);
+        r.y = static_cast<T>((cj.x * s + cj.y * c) * inv_sqrt_M);
+        psi[i] = r;
+    }
+}
+
+template <typename V, typename T>
+__global__ void __launch_bounds__(256) qpe_prob_kernel(const V* __restrict__ psi, int m, int d, double* __restrict__ prob) {
+    const uint64_t M = uint64_t(1) << m;
+    for (uint64_t x = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; x < M; x += uint64_t(gridDim.x) * blockDim.x) {
+        double p = 0.0;
+        for (int j = 0; j < d; ++j) {
+            const V a = psi[uint64_t(j) * M + x];
+            p += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
+        }
+        prob[x] = p;
+    }
+}
+
+int grid_for(uint64_t work) {
+    uint64_t b = (work + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    return static_cast<int>(b < 1 ? 1 : b);
+}
+
+}  // namespace
+}  // namespace qft
+
+extern "C" {
+
+size_t qft_qpe_workspace_size(int m, int d_bits) {
+    if (m < 1 || d_bits < 0 || m > 40 || d_bits > 20) return 0;
+    return (size_t(m) << d_bits) * sizeof(double);
+}
+
+int qft_qpe_prepare(void* d_state, int m, int d_bits, const double* d_theta, const void* d_coef, int dtype,
+                    void* d_workspace, qft_stream_t stream) {
+    if (!d_state || !d_theta || !d_coef || !d_workspace) return QFT_ERR_BAD_ARG;
+    if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
+    const int nmax = dtype == QFT_C64 ? 34 : 33;
+    if (m < 1 || d_bits < 0 || d_bits > 20 || m + d_bits > nmax) return QFT_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int d = 1 << d_bits;
+    double* f = static_cast<double*>(d_workspace);
+    qft::qpe_frac_kernel<<<(d * m + 255) / 256, 256, 0, st>>>(d_theta, d, m, f);
+    const double inv = 1.0 / std::sqrt(static_cast<double>(uint64_t(1) << m));
+    const int grid = qft::grid_for((uint64_t(1) << m) * d);
+    if (dtype == QFT_C64)
+        qft::qpe_prepare_kernel<float2, float><<<grid, 256, 0, st>>>(static_cast<float2*>(d_state), m, d, f,
+                                                                     static_cast<const double2*>(d_coef), inv);
+    else
+        qft::qpe_prepare_kernel<double2, double><<<grid, 256, 0, st>>>(static_cast<double2*>(d_state), m, d, f,
+                                                                       static_cast<const double2*>(d_coef), inv);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QFT_OK : qft::set_cuda_error(e);
+}
+
+int qft_qpe_probabilities(const void* d_state, int m, int d_bits, int dtype, double* d_prob, qft_stream_t stream) {
+    if (!d_state || !d_prob) return QFT_ERR_BAD_ARG;
+    if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
+    if (m < 1 || d_bits < 0 || d_bits > 20 || m + d_bits > 34) return QFT_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = qft::grid_for(uint64_t(1) << m);
+    if (dtype == QFT_C64)
+        qft::qpe_prob_kernel<float2, float><<<grid, 256, 0, st>>>(static_cast<const float2*>(d_state), m, 1 << d_bits,
+                                                                  d_prob);
+    else
+        qft::qpe_prob_kernel<double2, double><<<grid, 256, 0, st>>>(static_cast<const double2*>(d_state), m,
+                                                                    1 << d_bits, d_prob);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QFT_OK : qft::set_cuda_error(e);
+}
+
+}  // extern "C"

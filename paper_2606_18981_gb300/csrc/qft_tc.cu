@@ -797,11 +797,9 @@ template <int DIR, int PREC, int R>
 static cudaError_t launch_tc_fast_t(const CUtensorMap& map, const PassParams& P, const TcParams& Q, int grid,
                                     size_t smem, cudaStream_t st) {
     auto kern = qft_tc_fast_kernel<DIR, PREC, R>;
-    static thread_local size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    {
+        const cudaError_t e = ensure_dynamic_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
     }
     kern<<<grid, kTcFastThreads, smem, st>>>(map, P, Q);
     return cudaGetLastError();
@@ -818,11 +816,9 @@ static cudaError_t launch_tc_t(const CUtensorMap& map, const PassParams& P, cons
         }
     }
     auto kern = qft_tc_pass_kernel<DIR, PREC>;
-    static thread_local size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    {
+        const cudaError_t e = ensure_dynamic_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
     }
     kern<<<grid, kTcThreads, smem, st>>>(map, P, Q);
     return cudaGetLastError();
