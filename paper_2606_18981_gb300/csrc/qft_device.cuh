@@ -5,7 +5,6 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
-#include <atomic>
 #include <cstdint>
 #include <mutex>
 #include <type_traits>
@@ -21,22 +20,37 @@ namespace qft {
 // current device.  The attribute belongs to the function in the device's
 // context, so it is shared by every host thread: the limit only ever grows
 // (a thread that needs less never lowers it under another thread's launch),
-// tracked per kernel (one copy of the statics per instantiation) and device.
-template <typename K>
-inline cudaError_t ensure_dynamic_smem(K kern, size_t smem) {
-    constexpr int kDevs = 64;
-    static std::atomic<size_t> done[kDevs];
+// tracked per kernel (keyed by its address) and device in one process-wide
+// table.
+inline cudaError_t ensure_dynamic_smem_raw(const void* kern, size_t smem) {
+    struct Entry {
+        const void* kern;
+        int dev;
+        size_t smem;
+    };
     static std::mutex mu;
+    static Entry table[256];
+    static int used = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
-    if (smem <= done[dev].load(std::memory_order_acquire)) return cudaSuccess;
     std::lock_guard<std::mutex> lock(mu);
-    if (smem <= done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    int i = 0;
+    while (i < used && !(table[i].kern == kern && table[i].dev == dev)) ++i;
+    if (i < used && smem <= table[i].smem) return cudaSuccess;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e == cudaSuccess) done[dev].store(smem, std::memory_order_release);
-    return e;
+    if (e != cudaSuccess) return e;
+    if (i < used) {
+        table[i].smem = smem;
+    } else if (used < 256) {
+        table[used++] = Entry{kern, dev, smem};
+    }
+    return cudaSuccess;
+}
+
+template <typename K>
+inline cudaError_t ensure_dynamic_smem(K kern, size_t smem) {
+    return ensure_dynamic_smem_raw(reinterpret_cast<const void*>(kern), smem);
 }
 
 template <typename T> struct Vec2;
