@@ -288,10 +288,18 @@ class RealPlan:
     with SCALE_UNNORM), INVERSE = C2R (numpy.fft.irfft with SCALE_INV_N).
     dtype "c64" works on float32 data, "c128" on float64 data."""
 
-    def __init__(self, n: int, direction: int = FORWARD, dtype="c64", **opts):
+    def __init__(self, n: int, direction: int = FORWARD, dtype="c64", tuned: bool = True, **opts):
+        """tuned: the inner (n-1)-qubit plan takes the autotuner's shape for its size
+        (explicit opts win)."""
         self._h = _vp()
         self.n, self.direction = int(n), int(direction)
         self.dtype = _dtype_code(dtype)
+        if tuned and not opts.get("precision", 0):
+            from .autotune import best_opts
+
+            for key, v in best_opts(self.n - 1, "c64" if self.dtype == C64 else "c128").items():
+                if key != "paired":
+                    opts.setdefault(key, v)
         o = Opts(0, opts.get("tile_bits", 0), opts.get("coalesce_bits", 0), opts.get("max_stage_bits", 0),
                  opts.get("wait_limit_ms", 0), 0, opts.get("threads", 0), opts.get("precision", 0), 0,
                  opts.get("pass_split", 0))
@@ -429,7 +437,7 @@ def fft(x, k: int | None = None, inverse: bool = False, norm: str = "backward", 
     key = (n, -1 if k is None else int(k), direction, _dtype_code(x.dtype), ordc)
     p = _plan_cache.get(key)
     if p is None:
-        p = _plan_cache[key] = Plan(n, key[1], direction, key[3], ordc)
+        p = _plan_cache[key] = Plan(n, key[1], direction, key[3], ordc, tuned=True)
     out = torch.empty_like(x)
     ws = p.alloc_workspace(x.device)
     p.execute_oop(x.contiguous(), out, ws, mode)

@@ -240,19 +240,25 @@ __device__ __forceinline__ void rot32(dcomplex& z, int m) {
     if (m == 0) return;
     const bool neg = m >= 16;
     const int mm = m & 15;
+    dfloat x = z.re(), y = z.im();
     if (mm == 8) {
-        const dfloat t = z.x;
-        if (DIR > 0) { z.x = df_neg(z.y); z.y = t; } else { z.x = z.y; z.y = df_neg(t); }
+        const dfloat t = x;
+        if (DIR > 0) { x = df_neg(y); y = t; } else { x = y; y = df_neg(t); }
     } else if (mm != 0) {
         const dfloat c(kW32df.ch[mm], kW32df.cl[mm]);
         const dfloat s = DIR > 0 ? dfloat(kW32df.sh[mm], kW32df.sl[mm]) : dfloat(-kW32df.sh[mm], -kW32df.sl[mm]);
         // (x + i y)(c + i s) = (x c - y s) + i (x s + y c)
-        const dfloat re = df_dot2(z.x, c, z.y, s);
-        z.y = df_dot2(z.x, s, df_neg(z.y), c);
-        z.x = re;
+        const dfloat re = df_dot2(x, c, y, s);
+        y = df_dot2(x, s, df_neg(y), c);
+        x = re;
     }
-    if (neg) { z.x = df_neg(z.x); z.y = df_neg(z.y); }
+    if (neg) { x = df_neg(x); y = df_neg(y); }
+    z = dc_make(x, y);
 }
+
+// The complex number 1 of each amplitude type.
+template <typename V> __device__ __forceinline__ V cunit() { V r; r.x = 1; r.y = 0; return r; }
+template <> __device__ __forceinline__ dcomplex cunit<dcomplex>() { return dc_make(dfloat(1), dfloat(0)); }
 
 __device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
@@ -266,7 +272,7 @@ __device__ __forceinline__ typename Vec2<T>::type phase_turns(uint64_t beta, int
     if constexpr (std::is_same<T, dfloat>::value) {
         // double-float twiddles: the FP64 value split into a pair
         const double2 w = phase_turns<double, DIR>(beta, n);
-        return dcomplex{dfloat(w.x), dfloat(w.y)};
+        return dc_make(dfloat(w.x), dfloat(w.y));
     } else {
         const uint64_t b = (beta << (64 - n)) >> 24;            // beta mod 2^n, scaled to 2^40 per turn
         const uint64_t q4 = (b + (1ull << 37)) >> 38;            // nearest quarter turn, 0..4
@@ -447,7 +453,7 @@ struct AmpTraits<dfloat> {
     __device__ static __forceinline__ V load(const V* A, uint32_t i, const AmpIO& io) {
         if (io.raw_in) {
             const double2 d = reinterpret_cast<const double2*>(A)[i];
-            return dcomplex{df_from_double_shift(d.x, io.shift_in), df_from_double_shift(d.y, io.shift_in)};
+            return dc_make(df_from_double_shift(d.x, io.shift_in), df_from_double_shift(d.y, io.shift_in));
         }
         return A[i];
     }
@@ -463,8 +469,8 @@ struct AmpTraits<dfloat> {
         a.lo += s.lo + e;
     }
     __device__ static __forceinline__ void norm_add(NormAcc& a, const V& v) {
-        norm_add1(a, v.x);
-        norm_add1(a, v.y);
+        norm_add1(a, v.re());
+        norm_add1(a, v.im());
     }
     __device__ static __forceinline__ double norm_done(NormAcc a) {
         return static_cast<double>(a.hi) + static_cast<double>(a.lo);
@@ -478,10 +484,10 @@ struct AmpTraits<dfloat> {
     // Only the last pass has an output scale (the others run with scale 1).
     __device__ static __forceinline__ void store(V* out, int64_t o, V w, dfloat scale, const AmpIO& io) {
         if (io.raw_out) {
-            w = dcomplex{df_mul(w.x, scale), df_mul(w.y, scale)};
+            const dfloat re = df_mul(w.re(), scale), im = df_mul(w.im(), scale);
             double2 d;
-            d.x = df_to_double_shift(w.x, io.shift_out);
-            d.y = df_to_double_shift(w.y, io.shift_out);
+            d.x = df_to_double_shift(re, io.shift_out);
+            d.y = df_to_double_shift(im, io.shift_out);
             reinterpret_cast<double2*>(out)[o] = d;
         } else {
             out[o] = dc_norm(w);
@@ -584,9 +590,7 @@ __device__ __forceinline__ void build_group_tables(const PassParams& P, GroupTab
             tab.sb[idx] = swz<sizeof(V) == 8 ? 4 : 3>(pb);
             tab.ob[idx] = ob;
             for (int e = 0; e < P.ntw; ++e) {
-                V w;
-                w.x = T(1);
-                w.y = T(0);
+                V w = cunit<V>();
                 if (S.cross && e < S.r) w = phase_turns<T, DIR>(cross_phase(iw, P.n, S.wlo + S.r - 1, S.wlo + e, P.kk), P.n);
                 tab.tw[e * ntab + idx] = w;
             }

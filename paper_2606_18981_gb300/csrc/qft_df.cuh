@@ -46,9 +46,24 @@ struct dfloat {
         : hi(static_cast<float>(d)), lo(static_cast<float>(d - static_cast<double>(static_cast<float>(d)))) {}
 };
 
+// A complex amplitude: the high parts of the real and imaginary components in
+// one FP32 pair and the low parts in another, so that a complex add or
+// subtract is a packed FP32x2 two-sum (one instruction for both components).
+// In memory (shared and the workspace between passes): re.hi, im.hi, re.lo,
+// im.lo -- 16 bytes, the size of a complex128 amplitude.
 struct __align__(16) dcomplex {
-    dfloat x, y;
+    float2 hi;  // (re.hi, im.hi)
+    float2 lo;  // (re.lo, im.lo)
+    __host__ __device__ dfloat re() const { return dfloat(hi.x, lo.x); }
+    __host__ __device__ dfloat im() const { return dfloat(hi.y, lo.y); }
 };
+
+__host__ __device__ __forceinline__ dcomplex dc_make(dfloat re, dfloat im) {
+    dcomplex r;
+    r.hi = make_float2(re.hi, im.hi);
+    r.lo = make_float2(re.lo, im.lo);
+    return r;
+}
 
 // ------------------------------------------------------------ bit helpers
 
@@ -151,17 +166,74 @@ __host__ __device__ __forceinline__ dfloat df_dot2(dfloat a, dfloat b, dfloat c,
     return fast_two_sum(s.hi, t);
 }
 
+#ifdef __CUDA_ARCH__
+// Lane-wise FP32 pair arithmetic (add/sub.rn.f32x2, sm_100 and later): the
+// same IEEE results as two scalar operations.
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) {
+    uint64_t pa, pb, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(pa) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(pb) : "f"(b.x), "f"(b.y));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pa), "l"(pb));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
+__device__ __forceinline__ float2 pk_sub(float2 a, float2 b) {
+    uint64_t pa, pb, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(pa) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(pb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pa), "l"(pb));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
+#endif
+
+// a + b: df_add on both components -- on the device as one packed two-sum
+// (8 FP32x2 instructions for the complex add, the same values lane by lane).
 __host__ __device__ __forceinline__ dcomplex dc_add(dcomplex a, dcomplex b) {
-    return dcomplex{df_add(a.x, b.x), df_add(a.y, b.y)};
+#ifdef __CUDA_ARCH__
+    dcomplex r;
+    const float2 s = pk_add(a.hi, b.hi);
+    const float2 bb = pk_sub(s, a.hi);
+    const float2 e = pk_add(pk_sub(a.hi, pk_sub(s, bb)), pk_sub(b.hi, bb));
+    r.hi = s;
+    r.lo = pk_add(pk_add(a.lo, b.lo), e);
+    return r;
+#else
+    return dc_make(df_add(a.re(), b.re()), df_add(a.im(), b.im()));
+#endif
 }
+// a - b: df_sub on both components, packed on the device
 __host__ __device__ __forceinline__ dcomplex dc_sub(dcomplex a, dcomplex b) {
-    return dcomplex{df_sub(a.x, b.x), df_sub(a.y, b.y)};
+#ifdef __CUDA_ARCH__
+    dcomplex r;
+    const float2 s = pk_sub(a.hi, b.hi);
+    const float2 bb = pk_sub(s, a.hi);
+    const float2 e = pk_sub(pk_sub(a.hi, pk_sub(s, bb)), pk_add(b.hi, bb));
+    r.hi = s;
+    r.lo = pk_add(pk_sub(a.lo, b.lo), e);
+    return r;
+#else
+    return dc_make(df_sub(a.re(), b.re()), df_sub(a.im(), b.im()));
+#endif
 }
-// (a.x + i a.y)(b.x + i b.y) = (a.x b.x - a.y b.y) + i (a.x b.y + a.y b.x)
+// (ar + i ai)(br + i bi) = (ar br - ai bi) + i (ar bi + ai br)
 __host__ __device__ __forceinline__ dcomplex dc_mul(dcomplex a, dcomplex b) {
-    return dcomplex{df_dot2(a.x, b.x, a.y, b.y), df_dot2(a.x, b.y, df_neg(a.y), b.x)};
+    const dfloat ar = a.re(), ai = a.im(), br = b.re(), bi = b.im();
+    return dc_make(df_dot2(ar, br, ai, bi), df_dot2(ar, bi, df_neg(ai), br));
 }
-__host__ __device__ __forceinline__ dcomplex dc_norm(dcomplex a) { return dcomplex{df_norm(a.x), df_norm(a.y)}; }
+// renormalise both components (fast two-sum), packed on the device
+__host__ __device__ __forceinline__ dcomplex dc_norm(dcomplex a) {
+#ifdef __CUDA_ARCH__
+    dcomplex r;
+    r.hi = pk_add(a.hi, a.lo);
+    r.lo = pk_sub(a.lo, pk_sub(r.hi, a.hi));
+    return r;
+#else
+    return dc_make(df_norm(a.re()), df_norm(a.im()));
+#endif
+}
 
 // ------------------------------------------------ FP64 <-> df conversions
 

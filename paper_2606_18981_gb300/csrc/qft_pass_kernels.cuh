@@ -70,8 +70,7 @@ __device__ __forceinline__ void run_stage(const PassParams& P, const StageDesc& 
     V u[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) {
-        u[e].x = T(1);
-        u[e].y = T(0);
+        u[e] = cunit<V>();
     }
     if (use_u) {
 #pragma unroll
