@@ -473,6 +473,42 @@ def tensor_tier_workload(q, torch, dev, stream):
     return out
 
 
+def aqft_accuracy(q, torch, dev, n=22, cutoffs=(4, 6, 8, 10, 12, 16, 21)):
+    """The paper's AQFT accuracy experiment (Sec. 4): the single tone at bin 2,
+    n = 22, complex128; per cutoff k the infidelity 1 - F against the exact
+    transform, the top-bin leakage, the kept controlled phases (Table 2) and the
+    time of one transform."""
+    import numpy as np
+
+    import qft_inputs
+
+    x = torch.from_numpy(qft_inputs.single_tone(n, 2)).to(dev)
+
+    def run(k):
+        p = q.Plan(n, k, q.FORWARD, "c128", q.ORDER_NATURAL, tuned=True)
+        ws = p.alloc_workspace(dev)
+        st = x.clone()
+        p.execute(st, ws, q.SCALE_STATE)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        st2 = x.clone()
+        a.record()
+        p.execute(st2, ws, q.SCALE_STATE)
+        b.record()
+        torch.cuda.synchronize()
+        return st.cpu().numpy(), a.elapsed_time(b), p.info().n_cp
+
+    exact, ms_exact, cp_exact = run(-1)
+    y = int(np.argmax(np.abs(exact)))
+    out = {"exact": {"ms": ms_exact, "controlled_phases": cp_exact, "peak_bin": y}}
+    for k in cutoffs:
+        a, ms, cp = run(k)
+        f = abs(np.vdot(a, exact)) ** 2 / (np.vdot(a, a).real * np.vdot(exact, exact).real)
+        out[f"k{k}"] = {"one_minus_F": float(1.0 - f), "leakage": float(1.0 - abs(a[y]) ** 2 / np.vdot(a, a).real),
+                        "controlled_phases": cp, "ms": ms}
+    return out
+
+
 def timed_transform(q, torch, plan, state, ws, stream, steps, warmup):
     """Device-timed steps on resident data; returns (ms/step, [mean ms per pass])."""
     P = plan.info().passes
@@ -621,6 +657,10 @@ def run_ours(args, world, rank, local):
             extra["serving_poisson"] = serving_workload(q, torch, dev)
         except Exception as ex:
             extra["serving_poisson"] = {"error": str(ex)[:300]}
+        try:
+            extra["aqft_accuracy_n22_tone"] = aqft_accuracy(q, torch, dev)
+        except Exception as ex:
+            extra["aqft_accuracy_n22_tone"] = {"error": str(ex)[:300]}
         for name, (nn, ddt, kk, prc) in {"aqft_k4_c64_n30": (30, "c64", 4, 0), "c128_n30": (30, "c128", -1, 0),
                                           "c128_fp64_n30": (30, "c128", -1, q.PREC_FP64),
                                           "c64_n26": (26, "c64", -1, 0), "c64_n33": (33, "c64", -1, 0)}.items():
