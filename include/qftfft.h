@@ -80,7 +80,8 @@ enum qft_status {
     QFT_ERR_TIMEOUT = -5,     /* a bounded wait (host or device) ran out             */
     QFT_ERR_NOMEM = -6,       /* host or plan-owned device allocation failed         */
     QFT_ERR_UNSUPPORTED = -7, /* valid request this build does not implement         */
-    QFT_ERR_STATE = -8        /* call out of order (e.g. unknown ticket)             */
+    QFT_ERR_STATE = -8,       /* call out of order (e.g. unknown ticket)             */
+    QFT_ERR_CANCELED = -9     /* the request was withdrawn before it ran             */
 };
 
 /* Planner options; pass NULL for defaults.  Zero fields mean "choose". */
@@ -294,6 +295,15 @@ int qft_server_poll(qft_server_t server, uint64_t ticket, int* done);
 int qft_server_wait(qft_server_t server, uint64_t ticket, int timeout_ms, double* latency_ms);
 int qft_server_get_stats(qft_server_t server, qft_server_stats* out);
 int qft_server_reset_stats(qft_server_t server);
+/* Withdraw a request that has not been admitted yet: QFT_OK, and the ticket
+ * then reports QFT_ERR_CANCELED (poll / wait).  A request already running or
+ * finished cannot be withdrawn: QFT_ERR_STATE. */
+int qft_server_cancel(qft_server_t server, uint64_t ticket);
+/* Test hook: the server's next `count` device allocations fail as if
+ * cudaMalloc had failed.  A request that cannot get memory while others are
+ * running waits for them; with nothing running it fails with QFT_ERR_NOMEM.
+ * Used to check that an allocation failure is reported and leaks nothing. */
+int qft_server_inject_alloc_failures(qft_server_t server, int count);
 /* Finish every queued request, then stop the worker and free the server's memory. */
 int qft_server_destroy(qft_server_t server);
 

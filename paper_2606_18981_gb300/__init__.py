@@ -25,8 +25,8 @@ FORWARD, INVERSE = -1, +1
 SCALE_STATE, SCALE_UNITARY, SCALE_UNNORM, SCALE_INV_N = 0, 1, 2, 3
 ORDER_NATURAL, ORDER_BITREV = 0, 1
 PREC_NATIVE, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_FP16, PREC_FP16X3, PREC_FP64 = 0, 1, 2, 3, 4, 5, 6
-OK, ERR_BAD_ARG, ERR_SIZE, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED, ERR_STATE = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8
+OK, ERR_BAD_ARG, ERR_SIZE, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED, ERR_STATE, ERR_CANCELED = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
@@ -122,6 +122,8 @@ _lib.qft_server_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POIN
 _lib.qft_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
 _lib.qft_server_reset_stats.argtypes = [_vp]
 _lib.qft_server_destroy.argtypes = [_vp]
+_lib.qft_server_cancel.argtypes = [_vp, ctypes.c_uint64]
+_lib.qft_server_inject_alloc_failures.argtypes = [_vp, ctypes.c_int]
 
 lib = _lib  # the raw ctypes handle (tests call the C ABI through it)
 
@@ -390,6 +392,14 @@ class Server:
         rc = _lib.qft_server_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(lat))
         keep = self._keep.pop(ticket, None)
         return rc, lat.value, keep[2].value if keep else None
+
+    def cancel(self, ticket: int) -> int:
+        """Withdraw a request not yet admitted (0); QFT_ERR_STATE if it already runs or ran."""
+        return _lib.qft_server_cancel(self._h, ctypes.c_uint64(ticket))
+
+    def inject_alloc_failures(self, count: int) -> None:
+        """Test hook: the next `count` device allocations of the server fail."""
+        _check(_lib.qft_server_inject_alloc_failures(self._h, int(count)), "qft_server_inject_alloc_failures")
 
     def stats(self) -> ServerStats:
         st = ServerStats()

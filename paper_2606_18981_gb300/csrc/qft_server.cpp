@@ -81,6 +81,7 @@ struct qft_server_s {
     std::thread worker;
     double* slots = nullptr;  // pinned host memory, two doubles per in-flight slot
     std::vector<int> free_slots;
+    int fail_allocs = 0;      // test hook: allocations still to fail
 };
 
 namespace {
@@ -108,6 +109,10 @@ void* pool_get(qft_server_s* s, size_t bytes, size_t* got) {
         s->pool.erase(v);
     }
     void* p = nullptr;
+    if (s->fail_allocs > 0) {  // injected failure (test hook)
+        --s->fail_allocs;
+        return nullptr;
+    }
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
@@ -209,7 +214,15 @@ void worker_loop(qft_server_s* s) {
             f.req = rq;
             f.plan = p;
             f.state = pool_get(s, bytes, &f.bytes);
-            if (!f.state) break;
+            if (!f.state) {
+                // no memory: wait for running requests to free some; with
+                // nothing running no progress is possible, so report it
+                if (!s->inflight.empty()) break;
+                finish(s, rq, QFT_ERR_NOMEM, 0.0);
+                s->pending.pop_front();
+                s->cv_done.notify_all();
+                continue;
+            }
             f.ws = static_cast<char*>(f.state) + ((size_t(1) << p->n) * p->esize + 255) / 256 * 256;
             f.stream = static_cast<int>(std::min_element(s->stream_load.begin(), s->stream_load.end()) - s->stream_load.begin());
             f.slot = s->free_slots.back();
@@ -323,6 +336,28 @@ int qft_server_wait(qft_server_t s, uint64_t ticket, int timeout_ms, double* lat
     if (latency_ms) *latency_ms = res.latency_ms;
     s->results.erase(ticket);
     return res.status;
+}
+
+int qft_server_cancel(qft_server_t s, uint64_t ticket) {
+    if (!s) return QFT_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+        if (it->ticket != ticket) continue;
+        Result& res = s->results[ticket];
+        res.status = QFT_ERR_CANCELED;
+        res.latency_ms = 0.0;
+        s->pending.erase(it);
+        s->cv_done.notify_all();
+        return QFT_OK;
+    }
+    return QFT_ERR_STATE;
+}
+
+int qft_server_inject_alloc_failures(qft_server_t s, int count) {
+    if (!s || count < 0) return QFT_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->fail_allocs = count;
+    return QFT_OK;
 }
 
 int qft_server_get_stats(qft_server_t s, qft_server_stats* out) {

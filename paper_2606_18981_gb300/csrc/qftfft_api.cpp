@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "../../include/qftfft.h"
+#include <nvtx3/nvToolsExt.h>
 #include "plan_host.hpp"
 
 
@@ -629,6 +630,7 @@ const char* qft_strerror(int code) {
         case QFT_ERR_NOMEM: return "out of memory";
         case QFT_ERR_UNSUPPORTED: return "unsupported configuration";
         case QFT_ERR_STATE: return "call out of order";
+        case QFT_ERR_CANCELED: return "request canceled";
         default: return "unknown error";
     }
 }
@@ -859,9 +861,19 @@ int execute_range(qft_plan_t pl, const void* d_in, void* d_state, void* d_worksp
             if (e != cudaSuccess) return cuda_fail(e);
         }
     }
+    // One NVTX range per execute and one per pass (host-side markers a profiler
+    // lines up with the pass kernels; no cost without a tool attached).
+    static const char* const kPassNames[kMaxPasses] = {"qft pass 1", "qft pass 2", "qft pass 3", "qft pass 4",
+                                                       "qft pass 5", "qft pass 6", "qft pass 7", "qft pass 8"};
+    nvtxRangePushA(pl->df ? "qft execute (complex128, double-float)" : "qft execute");
+    struct RangePop {
+        ~RangePop() { nvtxRangePop(); }
+    } pop_execute;
     for (size_t i = i0; i < i1; ++i) {
         PassHost& ph = pl->passes[i];
         PassParams P = ph.prm;
+        nvtxRangePushA(kPassNames[i < kMaxPasses ? i : kMaxPasses - 1]);
+        RangePop pop_pass;
         P.scale_mode = scale_mode;
         P.in = ph.in_buf == 0 ? (i == 0 ? d_in : static_cast<const void*>(d_state)) : work;
         P.out = ph.out_buf == 0 ? d_state : work;

@@ -74,3 +74,41 @@ def test_budget_refusal_and_small_budget_progress():
         ref, _ = alone(v, 15, -1, -1, "c64", 0, 0)
         assert rel(o, ref) <= 2e-6
     srv.close()
+
+
+def test_cancel_pending_request():
+    """Requests queued behind a full budget can be withdrawn; the others still complete."""
+    srv = q.Server(1 << 20, streams=1, max_inflight=1)  # one n = 15 request at a time
+    xs = [torch.randn(1 << 15, dtype=torch.complex64, device="cuda") for _ in range(6)]
+    outs = [torch.empty_like(v) for v in xs]
+    ts = [srv.submit(v, o, 15) for v, o in zip(xs, outs)]
+    rc_cancel = srv.cancel(ts[-1])
+    for t in ts[:-1]:
+        rc, _, _ = srv.wait(t, 20000)
+        assert rc == 0
+    rc, _, _ = srv.wait(ts[-1], 20000)
+    if rc_cancel == 0:
+        assert rc == q.ERR_CANCELED
+    else:  # already admitted by the time cancel ran: it ran normally
+        assert rc_cancel == q.ERR_STATE and rc == 0
+    assert srv.cancel(ts[0]) == q.ERR_STATE  # finished requests cannot be withdrawn
+    srv.close()
+
+
+def test_injected_allocation_failure_is_reported_and_leaks_nothing():
+    srv = q.Server(1 << 30, streams=2)
+    x = torch.randn(1 << 16, dtype=torch.complex64, device="cuda")
+    out = torch.empty_like(x)
+    srv.inject_alloc_failures(1)
+    t = srv.submit(x, out, 16)
+    rc, _, _ = srv.wait(t, 20000)
+    assert rc == q.ERR_NOMEM
+    st = srv.stats()
+    assert st.in_flight == 0 and st.bytes_in_use == 0 and st.failed >= 1
+    t = srv.submit(x, out, 16)  # the next allocation succeeds
+    rc, _, _ = srv.wait(t, 20000)
+    assert rc == 0
+    ref, _ = alone(x, 16, -1, -1, "c64", 0, 0)
+    assert rel(out, ref) <= 2e-6
+    assert srv.stats().bytes_in_use == 0
+    srv.close()
