@@ -79,7 +79,7 @@ enum qft_status {
     QFT_ERR_CUDA = -4,        /* a CUDA runtime/driver call failed                    */
     QFT_ERR_TIMEOUT = -5,     /* a bounded wait (host or device) ran out             */
     QFT_ERR_NOMEM = -6,       /* host or plan-owned device allocation failed         */
-    QFT_ERR_UNSUPPORTED = -7, /* valid request this build does not implement         */
+    QFT_ERR_UNSUPPORTED = -7, /* valid request the library does not implement       */
     QFT_ERR_STATE = -8,       /* call out of order (e.g. unknown ticket)             */
     QFT_ERR_CANCELED = -9     /* the request was withdrawn before it ran             */
 };

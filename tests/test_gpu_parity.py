@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
 
 Tolerances (relative L2 error against the FP64 oracle): complex64 <= 2e-6,
-complex128 <= 1e-13 * n (the stated spec bounds).  Element by element,
+complex128 <= 1e-13 * n (the stated accuracy bounds).  Element by element,
 every amplitude must also satisfy |got_i - ref_i| <= tol * ||ref||_2, the
 max-norm bound the L2 tolerance implies.  (A bound relative to each bin's own
 magnitude or the RMS is not met even by exact-rounding FP32 arithmetic on
