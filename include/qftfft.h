@@ -108,10 +108,14 @@ typedef struct {
                            thread.  (Passes whose tile is <= 2^12 amplitudes and whose blocks
                            have <= 4 wires, or <= 3 when paired, run two CTAs per SM.)     */
     int pass_split;     /* NATURAL order, 3 or more passes: how wires left over by an even
-                           split are placed.  0 = default: on the first passes; 1 = on the
-                           middle passes, so the first and last passes (whose HBM runs
-                           the bit reversal spreads over the whole state) keep more batch
-                           wires and so longer runs.                                       */
+                           split are placed.  1 = on the middle passes, so the first pass
+                           (whose HBM runs the natural-order input spreads over the whole
+                           state) keeps more batch wires and so longer runs; 2 = on the
+                           first passes; 0 = the planner's choice (1 for complex64 with
+                           n >= 27 and default tiles, where it measured faster; else 2).
+                           With all shape fields 0 the planner also picks 2^12-amplitude
+                           tiles for complex64 n >= 27 and 512 threads for double-float
+                           complex128 n >= 21 (the tuned shapes on GB300).                */
 } qft_opts;
 
 /* Precision tier (complex64 plans): the block matrix and the data are rounded to

@@ -700,8 +700,8 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
             if (pl->threads == 512) pl->rmax = 4;
         }
         pl->pairing = opts->paired && dtype == QFT_C64 && pl->threads == 256 && !pl->precision && !subset;
-        if (opts->pass_split < 0 || opts->pass_split > 1) { delete pl; return QFT_ERR_BAD_ARG; }
-        pl->pass_split = opts->pass_split;
+        if (opts->pass_split < 0 || opts->pass_split > 2) { delete pl; return QFT_ERR_BAD_ARG; }
+        pl->pass_split = opts->pass_split == 1 ? 1 : 0;
         if (opts->max_stage_bits) {
             rmax_given = true;
             if (opts->max_stage_bits < 1 || opts->max_stage_bits > (pl->threads == 512 ? 4 : kMaxStageR)) {
@@ -711,6 +711,17 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
             pl->rmax = opts->max_stage_bits;
         }
     }
+    // Shapes measured fastest on GB300 (the autotuner's choices), used when the
+    // caller leaves the knobs at 0: complex64 with n >= 27 takes 2^12-amplitude
+    // tiles (two CTAs per SM) with the left-over wires on the middle passes;
+    // double-float complex128 with n >= 21 takes 512 threads.
+    const bool shape_given = opts && (opts->tile_bits || opts->coalesce_bits || opts->threads || rmax_given);
+    if (!subset && !shape_given && dtype == QFT_C64 && !pl->precision && n >= 27) {
+        pl->TB = 12;
+        pl->cmin = 4;
+        if (!(opts && opts->pass_split)) pl->pass_split = 1;
+    }
+    if (!shape_given && dtype == QFT_C128 && !fp64 && n >= 21) pl->threads = 512;
     // complex64 tiles of <= 2^12 amplitudes fit two CTAs per SM; blocks of <= 4
     // wires keep the kernel within the 128 registers that needs.
     if (dtype == QFT_C64 && !pl->precision && pl->threads == 256 && pl->TB <= 12 && !rmax_given)
