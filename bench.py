@@ -692,6 +692,16 @@ def run_ours(args, world, rank, local):
             r, w, cores, desc = oracle_sample(n, k, reps=2)
             cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                    "cpu_seconds": w}
+            # the same sample on one host thread (the paper's 1-thread CPU point)
+            try:
+                oracle.set_num_threads(1)
+                r1, w1, _, _ = oracle_sample(min(n, 26), k, reps=1)
+                cpu["value_1_thread"] = r1
+                cpu["sample_1_thread"] = f"the same sweeps at n={min(n, 26)} on one thread"
+                w += w1
+                cpu["cpu_seconds"] = w
+            finally:
+                oracle.set_num_threads(cores)
         except Exception as ex:
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
 
