@@ -132,7 +132,8 @@ typedef struct {
  * input is scaled by that power of two (exactly) so every FP64 magnitude is
  * handled; zero and subnormal FP64 components are read as zero.
  * QFT_PREC_FP64 runs the same passes in IEEE FP64 arithmetic instead.
- * Batches (qft_batch_*) run complex128 transforms in FP64. */
+ * Batches (qft_batch_*) run complex128 transforms in the plans' arithmetic
+ * (all plans of one batch must agree). */
 enum qft_precision { QFT_PREC_NATIVE = 0, QFT_PREC_TF32 = 1, QFT_PREC_BF16 = 2, QFT_PREC_BF16X3 = 3,
                      QFT_PREC_FP16 = 4, QFT_PREC_FP16X3 = 5, QFT_PREC_FP64 = 6 };
 

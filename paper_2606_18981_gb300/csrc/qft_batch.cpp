@@ -26,6 +26,11 @@ cudaError_t launch_batch(int dtype, int dir, int minb, const BatchItem* items, i
                          const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
                          int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream);
 size_t batch_smem_bytes(int max_tb, int max_ntab, size_t elem_bytes);
+cudaError_t launch_batch_df(int dir, const BatchItem* items, int nitems, const PassParams* descs,
+                            const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
+                            int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream);
+cudaError_t launch_df_maxexp_list(const void* const* d_states, const uint64_t* d_n16, int* const* d_outs, int count,
+                                  uint64_t max_n16, int num_sms, cudaStream_t stream);
 }  // namespace qft
 
 using namespace qft;
@@ -40,6 +45,14 @@ struct qft_batch_s {
     CUtensorMap* d_maps = nullptr;
     int* d_counters = nullptr;  // [0] = work-queue head, [1] = status word, then pass-completion counters
     int ncounters = 0;
+    // double-float complex128 batches: per transform its state, amplitude count
+    // and maximum-exponent word (read by the pre-pass before the batch kernel)
+    bool df = false;
+    int num_sms = 148;
+    const void** d_df_states = nullptr;
+    uint64_t* d_df_n16 = nullptr;
+    int** d_df_outs = nullptr;
+    uint64_t df_max_n16 = 0;
 };
 
 namespace {
@@ -60,6 +73,9 @@ size_t work_bytes(const qft_plan_s* pl) {
 
 void free_batch(qft_batch_s* b) {
     if (!b) return;
+    cudaFree(b->d_df_states);
+    cudaFree(b->d_df_n16);
+    cudaFree(b->d_df_outs);
     cudaFree(b->d_descs);
     cudaFree(b->d_items);
     cudaFree(b->d_maps);
@@ -93,6 +109,7 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
         if (plans[i]->dtype != plans[0]->dtype || plans[i]->dir != plans[0]->dir) return QFT_ERR_UNSUPPORTED;
         if (plans[i]->precision) return QFT_ERR_UNSUPPORTED;  // tensor-core tier plans run only through qft_execute
         if (plans[i]->n_addr != plans[i]->n) return QFT_ERR_UNSUPPORTED;  // subset plans run only through qft_execute
+        if (plans[i]->df != plans[0]->df) return QFT_ERR_UNSUPPORTED;       // one arithmetic per batch
     }
     if (workspace_bytes < qft_batch_workspace_size(plans, count)) return QFT_ERR_SIZE;
     auto fn = get_encode_fn();
@@ -103,6 +120,11 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
     b->dtype = plans[0]->dtype;
     b->dir = plans[0]->dir;
     b->wait_ns = plans[0]->wait_limit_ns;
+    b->df = plans[0]->df;
+    b->num_sms = plans[0]->num_sms;
+    std::vector<const void*> df_states;
+    std::vector<uint64_t> df_n16;
+    std::vector<int*> df_outs;
 
     // Transforms with the same plan run next to each other (fewer table rebuilds);
     // each transform's items stay contiguous (its second pass follows its first).
@@ -125,6 +147,12 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
         if (shape == static_cast<int>(shapes.size())) shapes.push_back(pl);
         char* meta = ws + off;
         off += meta_bytes(pl);
+        if (b->df) {
+            df_states.push_back(d_states[i]);
+            df_n16.push_back(uint64_t(1) << pl->n);  // one 16-byte load per complex128 amplitude
+            df_outs.push_back(reinterpret_cast<int*>(meta + kMaxExpOff));
+            b->df_max_n16 = std::max<uint64_t>(b->df_max_n16, uint64_t(1) << pl->n);
+        }
         char* work = ws + off;
         off += work_bytes(pl);
         const int P = static_cast<int>(pl->passes.size());
@@ -195,6 +223,17 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_descs), sizeof(PassParams) * descs.size());
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_items), sizeof(BatchItem) * items.size());
     if (e == cudaSuccess && !maps.empty()) e = cudaMalloc(reinterpret_cast<void**>(&b->d_maps), sizeof(CUtensorMap) * maps.size());
+    if (e == cudaSuccess && b->df) {
+        e = cudaMalloc(reinterpret_cast<void**>(&b->d_df_states), sizeof(void*) * df_states.size());
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_df_n16), sizeof(uint64_t) * df_n16.size());
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_df_outs), sizeof(int*) * df_outs.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_df_states, df_states.data(), sizeof(void*) * df_states.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_df_n16, df_n16.data(), sizeof(uint64_t) * df_n16.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_df_outs, df_outs.data(), sizeof(int*) * df_outs.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) { free_batch(b); cudaGetLastError(); return QFT_ERR_NOMEM; }
     for (auto& d : descs) d.status = b->d_counters + 1;
     e = cudaMemcpy(b->d_descs, descs.data(), sizeof(PassParams) * descs.size(), cudaMemcpyHostToDevice);
@@ -213,8 +252,15 @@ int qft_batch_execute(qft_batch_t b, qft_stream_t stream) {
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->ncounters, st);
     if (e != cudaSuccess) return set_cuda_error(e);
     // counter indices in the items start at 2: [0] queue head, [1] status word
-    e = launch_batch(b->dtype, b->dir, b->minb, b->d_items, b->nitems, b->d_descs, b->d_maps, b->d_counters,
-                     b->d_counters, b->d_counters + 1, b->wait_ns, b->max_tb, b->max_ntab, b->grid, b->smem, st);
+    if (b->df) {
+        e = launch_df_maxexp_list(b->d_df_states, b->d_df_n16, b->d_df_outs, b->count, b->df_max_n16, b->num_sms, st);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        e = launch_batch_df(b->dir, b->d_items, b->nitems, b->d_descs, b->d_maps, b->d_counters, b->d_counters,
+                            b->d_counters + 1, b->wait_ns, b->max_tb, b->max_ntab, b->grid, b->smem, st);
+    } else {
+        e = launch_batch(b->dtype, b->dir, b->minb, b->d_items, b->nitems, b->d_descs, b->d_maps, b->d_counters,
+                         b->d_counters, b->d_counters + 1, b->wait_ns, b->max_tb, b->max_ntab, b->grid, b->smem, st);
+    }
     return e == cudaSuccess ? QFT_OK : set_cuda_error(e);
 }
 

@@ -45,4 +45,49 @@ cudaError_t launch_pass_df(int dir, int threads, const CUtensorMap& map, const P
                    : launch_pass_t<dfloat, +1, 256, 1>(map, P, grid, smem, stream);
 }
 
+// Batches of double-float transforms: zero each transform's maximum-exponent
+// word, then take every transform's maximum in one launch (grid.y = transform).
+__global__ void qft_df_zero_list_kernel(int* const* __restrict__ outs, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) *outs[i] = 0;
+}
+
+__global__ void __launch_bounds__(256) qft_df_maxexp_list_kernel(const uint4* const* __restrict__ states,
+                                                               const uint64_t* __restrict__ n16,
+                                                               int* const* __restrict__ outs) {
+    const int t = blockIdx.y;
+    const uint4* x = states[t];
+    const uint64_t n = n16[t];
+    uint32_t m = 0;
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+        const uint4 v = x[i];
+        m = max(m, max((v.y >> 20) & 0x7FFu, (v.w >> 20) & 0x7FFu));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(outs[t], static_cast<int>(m));
+}
+
+cudaError_t launch_df_maxexp_list(const void* const* d_states, const uint64_t* d_n16, int* const* d_outs, int count,
+                                  uint64_t max_n16, int num_sms, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    qft_df_zero_list_kernel<<<(count + 255) / 256, 256, 0, stream>>>(d_outs, count);
+    uint64_t bx = (max_n16 + 255) / 256;
+    const uint64_t cap = (uint64_t(num_sms) * 8 + count - 1) / count;  // about 8 blocks per SM in all
+    if (bx > cap) bx = cap;
+    if (bx < 1) bx = 1;
+    dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(count));
+    qft_df_maxexp_list_kernel<<<grid, 256, 0, stream>>>(reinterpret_cast<const uint4* const*>(d_states), d_n16,
+                                                         d_outs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_df(int dir, const BatchItem* items, int nitems, const PassParams* descs,
+                            const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
+                            int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
+    return dir < 0 ? launch_batch_t<dfloat, -1, 256, 1>(items, nitems, descs, maps, counters, next, status, wait_ns,
+                                                        max_tb, max_ntab, grid, smem, stream)
+                   : launch_batch_t<dfloat, +1, 256, 1>(items, nitems, descs, maps, counters, next, status, wait_ns,
+                                                        max_tb, max_ntab, grid, smem, stream);
+}
+
 }  // namespace qft

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(NT, MINB)
     __shared__ int s_item;
 
     const int tid = threadIdx.x;
-    const AmpIO kPlainIO{0, 0, 0, 0};  // batches run float2 / double2 states as they are
+    using Tr = AmpTraits<T>;
     const uint32_t max_elems = 1u << max_tb;
     V* B = reinterpret_cast<V*>(smem_raw);
     V* A = B + max_elems;
@@ -427,15 +427,20 @@ __global__ void __launch_bounds__(NT, MINB)
         uint64_t I_tile;
         int64_t out_tile;
         tile_coords(P, it.tile, I_tile, out_tile);
+        // amplitude I/O of this item's transform (double-float: its own exponent shift)
+        AmpIO io{0, 0, 0, 0};
+        if constexpr (Tr::kDF) {
+            io.raw_in = P.first;
+            io.raw_out = P.last;
+            io.shift_in = df_shift_from_meta(P.meta);
+        }
         T scale = T(1);
         if (P.first && P.last) {
             double s = 0.0;
-            for (uint32_t i = tid; i < (1u << P.tb); i += NT) {
-                const V a = A[i];
-                s += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
-            }
-            const double scale_in = sqrt(block_sum<NT>(s, red));
-            scale = static_cast<T>(output_factor(P, scale_in));
+            for (uint32_t i = tid; i < (1u << P.tb); i += NT) s += Tr::norm2_at(A, i, io);
+            const double tot = block_sum<NT>(s, red);
+            const double scale_in = Tr::kDF ? ldexp(sqrt(tot), io.shift_in) : sqrt(tot);
+            Tr::out_scale(output_factor(P, scale_in), scale, io.shift_out, io.shift_in);
             if (tid == 0) {
                 P.meta[0] = scale_in;
                 if (P.user_scale) *P.user_scale = scale_in;
@@ -443,8 +448,9 @@ __global__ void __launch_bounds__(NT, MINB)
         } else if (P.last) {
             double s = 0.0;
             for (int i = tid; i < P.npartials; i += NT) s += P.partials[i];
-            const double scale_in = sqrt(block_sum<NT>(s, red));
-            scale = static_cast<T>(output_factor(P, scale_in));
+            const double tot = block_sum<NT>(s, red);
+            const double scale_in = Tr::kDF ? ldexp(sqrt(tot), io.shift_in) : sqrt(tot);
+            Tr::out_scale(output_factor(P, scale_in), scale, io.shift_out, io.shift_in);
             if (tid == 0 && it.tile == 0) {
                 P.meta[0] = scale_in;
                 if (P.user_scale) *P.user_scale = scale_in;
@@ -461,8 +467,9 @@ __global__ void __launch_bounds__(NT, MINB)
                     continue;
                 }
             }
-            dispatch_stage<T, DIR, NT, MINB == 1 ? 5 : 4>(P, s, tab, A, B, out_tile, scale, Ubuf + P.st[s].uoff,
-                                                          P.first && !P.last, norm_acc, kPlainIO);
+            dispatch_stage<T, DIR, NT, (MINB == 1 && !Tr::kDF) ? 5 : 4>(P, s, tab, A, B, out_tile, scale,
+                                                                        Ubuf + P.st[s].uoff, P.first && !P.last,
+                                                                        norm_acc, io);
             __syncthreads();
         }
         if (P.first && !P.last) {

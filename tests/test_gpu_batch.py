@@ -45,6 +45,8 @@ def make_batch(count, nmin, nmax, dt, order, seed, direction=q.FORWARD, opts=Non
 # plan shapes: defaults; 2^12-amplitude tiles (the batch runs two CTAs per SM);
 # paired complex64 stages
 @pytest.mark.parametrize("dt,order,opts", [("c64", 0, None), ("c64", 1, None), ("c128", 0, None),
+                                           ("c128", 1, None), ("c128", 0, {"threads": 512}),
+                                           ("c128", 0, {"precision": q.PREC_FP64}),
                                            ("c64", 0, {"tile_bits": 12}), ("c64", 1, {"tile_bits": 12}),
                                            ("c64", 0, {"paired": 1})])
 def test_batch_matches_single_transforms(oracle_mod, dt, order, opts):
@@ -107,3 +109,30 @@ def test_batch_rejects_tensor_tier_plans():
     x = torch.zeros(1 << 14, dtype=torch.complex64, device="cuda")
     with pytest.raises(q.QftError):
         q.Batch([p], [x], q.SCALE_STATE)
+
+
+def test_batch_double_float_per_transform_range():
+    """A complex128 (double-float) batch whose transforms differ by up to 2^1000
+    in magnitude: each transform gets its own exponent shift, so every result
+    equals the transform run alone."""
+    specs, plans, xs = make_batch(40, 3, 16, "c128", 0, seed=19)
+    rng = np.random.default_rng(19)
+    xs = [x * (2.0 ** int(rng.integers(-500, 501))) for x in xs]
+    states = [x.clone() for x in xs]
+    b = q.Batch([plans[(n, k)] for n, k, _ in specs], states, q.SCALE_STATE)
+    b.execute()
+    assert b.status() == 0
+    for i, (n, k, _) in enumerate(specs):
+        p = plans[(n, k)]
+        ref = xs[i].clone()
+        p.execute(ref, p.alloc_workspace(), q.SCALE_STATE)
+        torch.cuda.synchronize()
+        assert rel(states[i], ref) <= 1e-13 * n, (i, n, k)
+
+
+def test_batch_rejects_mixed_complex128_arithmetic():
+    a = q.Plan(10, -1, q.FORWARD, "c128")
+    f = q.Plan(10, -1, q.FORWARD, "c128", precision=q.PREC_FP64)
+    xs = [torch.zeros(1 << 10, dtype=torch.complex128, device="cuda") for _ in range(2)]
+    with pytest.raises(q.QftError):
+        q.Batch([a, f], xs, q.SCALE_STATE)
