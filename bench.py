@@ -417,6 +417,70 @@ def serving_workload(q, torch, dev, rates=(100, 300, 1000, 5000, 20000), per_rat
     return res
 
 
+def next_rows_workload(q, torch, dev, peak, reps=5):
+    """The transforms built beyond the single QFT: a real-input forward transform
+    of 2^31 float32 samples (the 30-qubit complex QFT plus one separation
+    sweep), the 2-D transform of a 2^14 x 2^14 complex64 array (row and column
+    subset plans), and phase estimation with 24 counting qubits and 16 system
+    states (prepare sweep, readout subset plan, probability sweep).  Each with
+    its HBM bytes (every pass and sweep reads and writes its data once) as a
+    fraction of the measured peak."""
+    out = {}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # real input: 2^31 samples -> 2^30 + 1 bins
+    n = 31
+    rp = q.RealPlan(n, q.FORWARD, "c64")
+    x = torch.randn(1 << n, dtype=torch.float32, device=dev)
+    X = torch.empty((1 << (n - 1)) + 1, dtype=torch.complex64, device=dev)
+    ws = rp.alloc_workspace(dev)
+    ms = timed(lambda: rp.execute(x, X, ws, q.SCALE_UNNORM))
+    sub = q.Plan(n - 1, -1, q.FORWARD, "c64", tuned=True).info().passes
+    byts = (sub + 1) * 2 * (1 << (n - 1)) * 8
+    out["rfft_n31_f32"] = {"ms": ms, "samples_per_s": (1 << n) / (ms / 1e3), "passes": sub + 1,
+                           "hbm_frac": byts / (ms / 1e3) / 1e9 / peak}
+    del x, X, ws, rp
+    torch.cuda.empty_cache()
+    # 2-D: 2^14 x 2^14 complex64
+    a = b = 14
+    x = torch.randn(1 << a, 1 << b, dtype=torch.complex64, device=dev)
+    rows = q.Plan(b, -1, q.FORWARD, "c64", n_addr=a + b, w0=0)
+    cols = q.Plan(a, -1, q.FORWARD, "c64", n_addr=a + b, w0=b)
+    y = torch.empty_like(x)
+    ws = torch.empty(max(rows.workspace_size(), cols.workspace_size()), dtype=torch.uint8, device=dev)
+
+    def fft2():
+        rows.execute_oop(x, y, ws, q.SCALE_UNNORM)
+        cols.execute(y, ws, q.SCALE_UNNORM)
+
+    ms = timed(fft2)
+    P = rows.info().passes + cols.info().passes
+    byts = P * 2 * (1 << (a + b)) * 8
+    out["fft2_16k_x_16k_c64"] = {"ms": ms, "amplitudes_per_s": (1 << (a + b)) / (ms / 1e3), "passes": P,
+                                 "hbm_frac": byts / (ms / 1e3) / 1e9 / peak}
+    del x, y, ws
+    torch.cuda.empty_cache()
+    # phase estimation: m = 24 counting qubits, 16 eigenphases
+    m, d = 24, 16
+    th = torch.rand(d, dtype=torch.float64, device=dev)
+    c = torch.full((d,), 0.25, dtype=torch.complex128, device=dev)
+    ms = timed(lambda: q.qpe(th, c, m, dtype="c64"))
+    out["qpe_m24_d16_c64"] = {"ms": ms, "amplitudes": d << m,
+                              "note": "includes plan creation and buffer allocation of the convenience call"}
+    return out
+
+
 def tensor_tier_workload(q, torch, dev, stream):
     """Precision tier: fused 6-wire blocks as tcgen05 GEMMs (TF32, BF16, FP16,
     split x3).  Per tier: time of one exact forward transform at n = 24 and of
@@ -657,6 +721,10 @@ def run_ours(args, world, rank, local):
             extra["serving_poisson"] = serving_workload(q, torch, dev)
         except Exception as ex:
             extra["serving_poisson"] = {"error": str(ex)[:300]}
+        try:
+            extra["next_rows"] = next_rows_workload(q, torch, dev, peak)
+        except Exception as ex:
+            extra["next_rows"] = {"error": str(ex)[:300]}
         try:
             extra["aqft_accuracy_n22_tone"] = aqft_accuracy(q, torch, dev)
         except Exception as ex:
