@@ -1,0 +1,18 @@
+// qft_batch_df.cu -- double-float complex128 instantiations of the batched
+// persistent kernel (qft_pass_kernels.cuh): one CTA per SM, both directions.
+// The maximum-exponent pre-pass over the batch's transforms is in
+// qft_pass_df.cu.
+#include "qft_pass_kernels.cuh"
+
+namespace qft {
+
+cudaError_t launch_batch_df(int dir, const BatchItem* items, int nitems, const PassParams* descs,
+                            const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
+                            int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
+    return dir < 0 ? launch_batch_t<dfloat, -1, 256, 1>(items, nitems, descs, maps, counters, next, status, wait_ns,
+                                                        max_tb, max_ntab, grid, smem, stream)
+                   : launch_batch_t<dfloat, +1, 256, 1>(items, nitems, descs, maps, counters, next, status, wait_ns,
+                                                        max_tb, max_ntab, grid, smem, stream);
+}
+
+}  // namespace qft

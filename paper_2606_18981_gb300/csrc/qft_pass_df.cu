@@ -1,6 +1,7 @@
 // qft_pass_df.cu -- the double-float complex128 pass kernel (qft_pass_kernels.cuh
 // instantiated with T = dfloat, arithmetic in qft_df.cuh) and the
-// maximum-exponent pre-pass of its range normalisation.
+// maximum-exponent pre-pass of its range normalisation (single transforms and
+// batches; the batch kernel itself is instantiated in qft_batch_df.cu).
 //
 // A complex128 transform on this path reads the caller's FP64 state in its
 // first pass, converts each component to an FP32 pair scaled by 2^-k, keeps
@@ -79,15 +80,6 @@ cudaError_t launch_df_maxexp_list(const void* const* d_states, const uint64_t* d
     qft_df_maxexp_list_kernel<<<grid, 256, 0, stream>>>(reinterpret_cast<const uint4* const*>(d_states), d_n16,
                                                          d_outs);
     return cudaGetLastError();
-}
-
-cudaError_t launch_batch_df(int dir, const BatchItem* items, int nitems, const PassParams* descs,
-                            const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
-                            int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
-    return dir < 0 ? launch_batch_t<dfloat, -1, 256, 1>(items, nitems, descs, maps, counters, next, status, wait_ns,
-                                                        max_tb, max_ntab, grid, smem, stream)
-                   : launch_batch_t<dfloat, +1, 256, 1>(items, nitems, descs, maps, counters, next, status, wait_ns,
-                                                        max_tb, max_ntab, grid, smem, stream);
 }
 
 }  // namespace qft
