@@ -385,7 +385,9 @@ int qft_rplan_execute(qft_rplan_t plan, const void* d_in, void* d_out, void* d_w
  * qft_qpe_prepare writes the state after H on every counting qubit and the
  * controlled evolutions C-U^{2^k} (k = 0 .. m-1):
  *     psi[j 2^m + y] = c_j exp(2 pi i sum_k y_k frac(theta_j 2^k)) / sqrt(2^m)
- * (the phase accumulated per controlled evolution in FP64).  d_theta: d
+ * (the phases of all controlled evolutions summed exactly as the 64-bit
+ * fixed-point product frac(theta_j) 2^64 * y mod 2^64; only the final
+ * sine/cosine rounds, in the dtype's precision).  d_theta: d
  * doubles, d_coef: d complex128 values, both device memory; d_workspace:
  * qft_qpe_workspace_size(m, d_bits) bytes of device memory.  The Fourier
  * readout is then the transform of the counting qubits with omega =

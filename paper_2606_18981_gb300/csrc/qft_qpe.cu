@@ -12,10 +12,12 @@
 // for every set bit k of y, so after all m of them
 //
 //     psi[j 2^m + y] = c_j e^{2 pi i phi_j(y)} / sqrt(2^m),
-//     phi_j(y) = sum_k y_k frac(theta_j 2^k)  (mod 1),
+//     phi_j(y) = sum_k y_k frac(theta_j 2^k) = frac(theta_j y)  (mod 1),
 //
-// which qft_qpe_prepare writes in one sweep (the phase is accumulated per
-// controlled evolution, in FP64, so it is exact to rounding for any m).  The
+// which qft_qpe_prepare writes in one sweep.  The phase is kept in 64-bit
+// fixed point (2^64 = one turn): Theta_j = frac(theta_j) 2^64, and the sum of
+// the controlled evolutions' phases is the integer product Theta_j y mod 2^64,
+// exact for every y; only the final sine/cosine rounds.  The
 // Fourier readout is the transform of the counting qubits with
 // omega = e^{-2 pi i / 2^m} (the paper's QFT convention, which is the
 // textbook inverse QFT of phase estimation): a subset plan
@@ -34,35 +36,48 @@
 namespace qft {
 namespace {
 
-// frac(theta_j 2^k) for k < m, j < d: one row of m per eigenphase.
-__global__ void qpe_frac_kernel(const double* __restrict__ theta, int d, int m, double* __restrict__ f) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d * m) return;
-    const int j = i / m, k = i % m;
-    const double t = ldexp(theta[j], k);  // exact: a power-of-two scaling
-    f[i] = t - floor(t);
+// Theta_j = frac(theta_j) 2^64 (64-bit fixed point, one turn = 2^64).
+__global__ void qpe_theta_kernel(const double* __restrict__ theta, int d, uint64_t* __restrict__ th64) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d) return;
+    const double f = theta[j] - floor(theta[j]);  // exact
+    const double t = ldexp(f, 64);                // exact scaling; < 2^64
+    th64[j] = t >= 18446744073709551615.0 ? 0ull : __double2ull_rn(t);
+}
+
+// exp(2 pi i phase / 2^64): reduced exactly in integers to the nearest quarter
+// turn, the rest (|x| <= 1/8 turn) through sincospi in the element type.
+template <typename T>
+__device__ __forceinline__ void phase64(uint64_t phase, T& c, T& s) {
+    const uint64_t q4 = (phase + (1ull << 61)) >> 62;               // nearest quarter turn, 0..4
+    const int64_t rem = static_cast<int64_t>(phase - (q4 << 62));  // |rem| <= 2^61
+    const T x = static_cast<T>(rem) * static_cast<T>(1.0 / 9223372036854775808.0);  // rem / 2^63 (units of pi)
+    T sn, cs;
+    if constexpr (sizeof(T) == 4) sincospif(x, &sn, &cs);
+    else sincospi(x, &sn, &cs);
+    switch (q4 & 3) {
+        case 0: c = cs; s = sn; break;
+        case 1: c = -sn; s = cs; break;
+        case 2: c = -cs; s = -sn; break;
+        default: c = sn; s = -cs; break;
+    }
 }
 
 template <typename V, typename T>
-__global__ void __launch_bounds__(256) qpe_prepare_kernel(V* __restrict__ psi, int m, int d, const double* __restrict__ f,
+__global__ void __launch_bounds__(256) qpe_prepare_kernel(V* __restrict__ psi, int m, int d,
+                                                          const uint64_t* __restrict__ th64,
                                                           const double2* __restrict__ coef, double inv_sqrt_M) {
     const uint64_t M = uint64_t(1) << m, total = M * uint64_t(d);
     for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < total; i += uint64_t(gridDim.x) * blockDim.x) {
         const uint64_t y = i & (M - 1);
         const int j = static_cast<int>(i >> m);
-        const double* fj = f + size_t(j) * m;
-        double ph = 0.0;
-        for (int k = 0; k < m; ++k)
-            if ((y >> k) & 1) {
-                ph += fj[k];
-                ph -= (ph >= 1.0) ? 1.0 : 0.0;
-            }
-        double s, c;
-        sincospi(2.0 * ph, &s, &c);  // |2 ph| < 2: one reduction-free evaluation
+        T c, s;
+        phase64<T>(th64[j] * y, c, s);  // frac(theta_j y), exact mod 2^64
         const double2 cj = coef[j];
+        const T ax = static_cast<T>(cj.x * inv_sqrt_M), ay = static_cast<T>(cj.y * inv_sqrt_M);
         V r;
-        r.x = static_cast<T>((cj.x * c - cj.y * s) * inv_sqrt_M);
-        r.y = static_cast<T>((cj.x * s + cj.y * c) * inv_sqrt_M);
+        r.x = ax * c - ay * s;
+        r.y = ax * s + ay * c;
         psi[i] = r;
     }
 }
@@ -93,7 +108,7 @@ extern "C" {
 
 size_t qft_qpe_workspace_size(int m, int d_bits) {
     if (m < 1 || d_bits < 0 || m > 40 || d_bits > 20) return 0;
-    return (size_t(m) << d_bits) * sizeof(double);
+    return (size_t(1) << d_bits) * sizeof(uint64_t);
 }
 
 int qft_qpe_prepare(void* d_state, int m, int d_bits, const double* d_theta, const void* d_coef, int dtype,
@@ -104,15 +119,15 @@ int qft_qpe_prepare(void* d_state, int m, int d_bits, const double* d_theta, con
     if (m < 1 || d_bits < 0 || d_bits > 20 || m + d_bits > nmax) return QFT_ERR_BAD_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int d = 1 << d_bits;
-    double* f = static_cast<double*>(d_workspace);
-    qft::qpe_frac_kernel<<<(d * m + 255) / 256, 256, 0, st>>>(d_theta, d, m, f);
+    uint64_t* th64 = static_cast<uint64_t*>(d_workspace);
+    qft::qpe_theta_kernel<<<(d + 255) / 256, 256, 0, st>>>(d_theta, d, th64);
     const double inv = 1.0 / std::sqrt(static_cast<double>(uint64_t(1) << m));
     const int grid = qft::grid_for((uint64_t(1) << m) * d);
     if (dtype == QFT_C64)
-        qft::qpe_prepare_kernel<float2, float><<<grid, 256, 0, st>>>(static_cast<float2*>(d_state), m, d, f,
+        qft::qpe_prepare_kernel<float2, float><<<grid, 256, 0, st>>>(static_cast<float2*>(d_state), m, d, th64,
                                                                      static_cast<const double2*>(d_coef), inv);
     else
-        qft::qpe_prepare_kernel<double2, double><<<grid, 256, 0, st>>>(static_cast<double2*>(d_state), m, d, f,
+        qft::qpe_prepare_kernel<double2, double><<<grid, 256, 0, st>>>(static_cast<double2*>(d_state), m, d, th64,
                                                                        static_cast<const double2*>(d_coef), inv);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QFT_OK : qft::set_cuda_error(e);
