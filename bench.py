@@ -489,7 +489,7 @@ def next_rows_workload(q, torch, dev, peak, reps=5):
         q.lib.qft_qpe_probabilities(st.data_ptr(), m, db, q.C64, prob.data_ptr(), sh)
 
     ms = timed(qpe_once)
-    byts = (1 + rd.info().passes) * 2 * (d << m) * 8 + (d << m) * 8
+    byts = (1 + rd.info().passes) * 2 * (d << m) * 8  # passes + (prepare write + probability read)
     out["qpe_m24_d16_c64"] = {"ms": ms, "amplitudes": d << m, "readout_passes": rd.info().passes,
                               "hbm_frac": byts / (ms / 1e3) / 1e9 / peak,
                               "steps": "prepare sweep (writes), readout passes, probability sweep (reads)"}
