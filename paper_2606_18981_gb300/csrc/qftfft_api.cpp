@@ -715,13 +715,14 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
     // caller leaves the knobs at 0: complex64 with n >= 27 takes 2^12-amplitude
     // tiles (two CTAs per SM) with the left-over wires on the middle passes;
     // double-float complex128 with n >= 21 takes 512 threads.
+    // (For subset plans the array size decides: their passes sweep all of it.)
     const bool shape_given = opts && (opts->tile_bits || opts->coalesce_bits || opts->threads || rmax_given);
-    if (!subset && !shape_given && dtype == QFT_C64 && !pl->precision && n >= 27) {
+    if (!shape_given && dtype == QFT_C64 && !pl->precision && n_addr >= 27) {
         pl->TB = 12;
         pl->cmin = 4;
         if (!(opts && opts->pass_split)) pl->pass_split = 1;
     }
-    if (!shape_given && dtype == QFT_C128 && !fp64 && n >= 21) pl->threads = 512;
+    if (!shape_given && dtype == QFT_C128 && !fp64 && n_addr >= 21) pl->threads = 512;
     // complex64 tiles of <= 2^12 amplitudes fit two CTAs per SM; blocks of <= 4
     // wires keep the kernel within the 128 registers that needs.
     if (dtype == QFT_C64 && !pl->precision && pl->threads == 256 && pl->TB <= 12 && !rmax_given)
