@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(NT, MINB)
             const bool last_stage = (s == P.nstages - 1);
             const bool from_A = (s == 0);
             if (ok)
-                dispatch_stage<T, DIR, NT, (NT <= 256 && MINB == 1 && !Tr::kDF) ? 5 : (Tr::kDF && NT > 256) ? 3 : 4>(
+                dispatch_stage<T, DIR, NT,
+                               (NT <= 256 && MINB == 1 && !Tr::kDF) ? 5 : ((Tr::kDF || MINB == 2) && NT > 256) ? 3 : 4>(
                     P, s, tab, Ab, B, out_tile, scale, Ucur + P.st[s].uoff, P.first && !P.last, norm_acc, io);
             if (last_stage) compute_tile_twiddles<T, DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1]);
             if (from_A) {

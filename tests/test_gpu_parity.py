@@ -284,6 +284,8 @@ VARIANTS = {
     "paired": dict(paired=1),
     "paired_two_ctas": dict(tile_bits=12, paired=1, max_stage_bits=3),
     "tile11": dict(tile_bits=11),
+    "t512_two_ctas": dict(tile_bits=12, coalesce_bits=4, threads=512, max_stage_bits=3),
+    "split_middle": dict(tile_bits=12, coalesce_bits=4, pass_split=1),
 }
 
 
