@@ -618,7 +618,7 @@ int encode_maps(qft_plan_s* pl, const void* in, const void* state, const void* w
 
 extern "C" {
 
-int qft_version(void) { return 100; }
+int qft_version(void) { return 200; }  // 0.2.0: double-float complex128, real, subset and phase-estimation calls, qft_opts.pass_split
 
 int qft_last_cuda_error(void) { return qft::g_last_cuda; }
 
