@@ -389,7 +389,10 @@ int qft_rplan_execute(qft_rplan_t plan, const void* d_in, void* d_out, void* d_w
  * fixed-point product frac(theta_j) 2^64 * y mod 2^64; only the final
  * sine/cosine rounds, in the dtype's precision).  d_theta: d
  * doubles, d_coef: d complex128 values, both device memory; d_workspace:
- * qft_qpe_workspace_size(m, d_bits) bytes of device memory.  The Fourier
+ * qft_qpe_workspace_size(m, d_bits) bytes of device memory, 16-byte aligned
+ * (QFT_ERR_BAD_ARG otherwise), which the call fills with per-eigenvector
+ * constants and must stay allocated until the prepare has run on the stream.
+ * The Fourier
  * readout is then the transform of the counting qubits with omega =
  * e^{-2 pi i / 2^m} -- this library's QFT_FORWARD, the paper's convention,
  * which is the textbook inverse QFT of phase estimation: a subset plan

@@ -36,25 +36,59 @@
 namespace qft {
 namespace {
 
-// Theta_j = frac(theta_j) 2^64 (64-bit fixed point, one turn = 2^64).
-__global__ void qpe_theta_kernel(const double* __restrict__ theta, int d, uint64_t* __restrict__ th64) {
+// Per eigenvector j, once: Theta_j = frac(theta_j) 2^64 (64-bit fixed point,
+// one turn = 2^64) and the amplitude c_j / sqrt(2^m) rounded to the element
+// type, so that the per-amplitude sweep does no FP64 arithmetic (GB300's FP64
+// pipe runs at a small fraction of its FP32 rate).
+template <typename V, typename T>
+__global__ void qpe_setup_kernel(const double* __restrict__ theta, const double2* __restrict__ coef, int d,
+                                 double inv_sqrt_M, uint64_t* __restrict__ th64, V* __restrict__ cs) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= d) return;
     const double f = theta[j] - floor(theta[j]);  // exact
     const double t = ldexp(f, 64);                // exact scaling; < 2^64
     th64[j] = t >= 18446744073709551615.0 ? 0ull : __double2ull_rn(t);
+    const double2 c = coef[j];
+    V v;
+    v.x = static_cast<T>(c.x * inv_sqrt_M);
+    v.y = static_cast<T>(c.y * inv_sqrt_M);
+    cs[j] = v;
 }
 
 // exp(2 pi i phase / 2^64): reduced exactly in integers to the nearest quarter
 // turn, the rest (|x| <= 1/8 turn) through sincospi in the element type.
+// sin(pi x) and cos(pi x) for |x| <= 1/4 in FP32 from their Taylor series at
+// 0 (t = pi x, |t| <= pi/4; the first omitted terms, t^11/11! and t^12/12!,
+// are below 2e-9 and 2e-10), by Horner's rule: within 1.5 units of 2^-24 of
+// the exact values over the whole interval, with no range reduction (the
+// caller has reduced the phase exactly in integers).
+__device__ __forceinline__ void sincospi_quarter(float x, float& s, float& c) {
+    const float t = x * 3.14159265358979f;
+    const float t2 = t * t;
+    float ps = fmaf(t2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    ps = fmaf(ps, t2, 1.0f / 120.0f);
+    ps = fmaf(ps, t2, -1.0f / 6.0f);
+    s = fmaf(ps * t2, t, t);
+    float pc = fmaf(t2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+    pc = fmaf(pc, t2, -1.0f / 720.0f);
+    pc = fmaf(pc, t2, 1.0f / 24.0f);
+    pc = fmaf(pc, t2, -0.5f);
+    c = fmaf(pc, t2, 1.0f);
+}
+
 template <typename T>
 __device__ __forceinline__ void phase64(uint64_t phase, T& c, T& s) {
     const uint64_t q4 = (phase + (1ull << 61)) >> 62;               // nearest quarter turn, 0..4
     const int64_t rem = static_cast<int64_t>(phase - (q4 << 62));  // |rem| <= 2^61
-    const T x = static_cast<T>(rem) * static_cast<T>(1.0 / 9223372036854775808.0);  // rem / 2^63 (units of pi)
     T sn, cs;
-    if constexpr (sizeof(T) == 4) sincospif(x, &sn, &cs);
-    else sincospi(x, &sn, &cs);
+    if constexpr (sizeof(T) == 4) {
+        // rem / 2^63 (units of pi) from the top 32 bits, rounded: the dropped
+        // part is below 2^-32 of pi, far under FP32's resolution here
+        const int32_t hi = static_cast<int32_t>((rem + (int64_t(1) << 31)) >> 32);
+        sincospi_quarter(static_cast<float>(hi) * (1.0f / 2147483648.0f), sn, cs);
+    } else {
+        sincospi(static_cast<double>(rem) * (1.0 / 9223372036854775808.0), &sn, &cs);
+    }
     switch (q4 & 3) {
         case 0: c = cs; s = sn; break;
         case 1: c = -sn; s = cs; break;
@@ -66,32 +100,74 @@ __device__ __forceinline__ void phase64(uint64_t phase, T& c, T& s) {
 template <typename V, typename T>
 __global__ void __launch_bounds__(256) qpe_prepare_kernel(V* __restrict__ psi, int m, int d,
                                                           const uint64_t* __restrict__ th64,
-                                                          const double2* __restrict__ coef, double inv_sqrt_M) {
+                                                          const V* __restrict__ cs) {
     const uint64_t M = uint64_t(1) << m, total = M * uint64_t(d);
     for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < total; i += uint64_t(gridDim.x) * blockDim.x) {
         const uint64_t y = i & (M - 1);
         const int j = static_cast<int>(i >> m);
         T c, s;
         phase64<T>(th64[j] * y, c, s);  // frac(theta_j y), exact mod 2^64
-        const double2 cj = coef[j];
-        const T ax = static_cast<T>(cj.x * inv_sqrt_M), ay = static_cast<T>(cj.y * inv_sqrt_M);
+        const V a = cs[j];
         V r;
-        r.x = ax * c - ay * s;
-        r.y = ax * s + ay * c;
+        r.x = a.x * c - a.y * s;
+        r.y = a.x * s + a.y * c;
         psi[i] = r;
     }
 }
 
+// P(x) = sum_j |psi[j 2^m + x]|^2.  Each thread takes kXU counting values
+// (one grid stride apart) and kJU system states per step, so kXU * kJU reads
+// are in flight per thread.  complex64 sums each step's kJU squares in FP32
+// (a relative error of at most ~2 kJU 2^-24, below the state's own rounding)
+// and carries the total in FP64; complex128 sums in FP64 throughout.
+constexpr int kXU = 4, kJU = 4;
+
 template <typename V, typename T>
 __global__ void __launch_bounds__(256) qpe_prob_kernel(const V* __restrict__ psi, int m, int d, double* __restrict__ prob) {
     const uint64_t M = uint64_t(1) << m;
-    for (uint64_t x = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; x < M; x += uint64_t(gridDim.x) * blockDim.x) {
-        double p = 0.0;
-        for (int j = 0; j < d; ++j) {
-            const V a = psi[uint64_t(j) * M + x];
-            p += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
+    const uint64_t S = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t x0 = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; x0 < M; x0 += kXU * S) {
+        double p[kXU];
+#pragma unroll
+        for (int u = 0; u < kXU; ++u) p[u] = 0.0;
+        int j = 0;
+        for (; j + kJU <= d; j += kJU) {
+            V a[kXU][kJU];
+#pragma unroll
+            for (int u = 0; u < kXU; ++u) {
+                const uint64_t x = x0 + u * S;
+#pragma unroll
+                for (int v = 0; v < kJU; ++v) {
+                    if (x < M) a[u][v] = psi[uint64_t(j + v) * M + x];
+                    else a[u][v].x = a[u][v].y = T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kXU; ++u) {
+                T t = T(0);
+#pragma unroll
+                for (int v = 0; v < kJU; ++v) {
+                    t = fma(a[u][v].x, a[u][v].x, t);
+                    t = fma(a[u][v].y, a[u][v].y, t);
+                }
+                p[u] += static_cast<double>(t);
+            }
         }
-        prob[x] = p;
+        for (; j < d; ++j) {  // d < kJU
+#pragma unroll
+            for (int u = 0; u < kXU; ++u) {
+                const uint64_t x = x0 + u * S;
+                if (x < M) {
+                    const V a = psi[uint64_t(j) * M + x];
+                    p[u] += static_cast<double>(fma(a.x, a.x, a.y * a.y));
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kXU; ++u) {
+            const uint64_t x = x0 + u * S;
+            if (x < M) prob[x] = p[u];
+        }
     }
 }
 
@@ -108,27 +184,36 @@ extern "C" {
 
 size_t qft_qpe_workspace_size(int m, int d_bits) {
     if (m < 1 || d_bits < 0 || m > 40 || d_bits > 20) return 0;
-    return (size_t(1) << d_bits) * sizeof(uint64_t);
+    return (size_t(1) << d_bits) * (sizeof(uint64_t) + sizeof(double2));
 }
 
 int qft_qpe_prepare(void* d_state, int m, int d_bits, const double* d_theta, const void* d_coef, int dtype,
                     void* d_workspace, qft_stream_t stream) {
     if (!d_state || !d_theta || !d_coef || !d_workspace) return QFT_ERR_BAD_ARG;
+    if (reinterpret_cast<uintptr_t>(d_workspace) % 16 != 0) return QFT_ERR_BAD_ARG;
     if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
     const int nmax = dtype == QFT_C64 ? 34 : 33;
     if (m < 1 || d_bits < 0 || d_bits > 20 || m + d_bits > nmax) return QFT_ERR_BAD_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int d = 1 << d_bits;
-    uint64_t* th64 = static_cast<uint64_t*>(d_workspace);
-    qft::qpe_theta_kernel<<<(d + 255) / 256, 256, 0, st>>>(d_theta, d, th64);
+    // workspace: d scaled coefficients (16 bytes each, complex128-sized for
+    // both dtypes) followed by the d fixed-point phases
+    void* cs = d_workspace;
+    uint64_t* th64 = reinterpret_cast<uint64_t*>(static_cast<char*>(d_workspace) + size_t(d) * sizeof(double2));
     const double inv = 1.0 / std::sqrt(static_cast<double>(uint64_t(1) << m));
+    const int sblocks = (d + 255) / 256;
+    const auto* coef = static_cast<const double2*>(d_coef);
     const int grid = qft::grid_for((uint64_t(1) << m) * d);
-    if (dtype == QFT_C64)
+    if (dtype == QFT_C64) {
+        qft::qpe_setup_kernel<float2, float><<<sblocks, 256, 0, st>>>(d_theta, coef, d, inv, th64, static_cast<float2*>(cs));
         qft::qpe_prepare_kernel<float2, float><<<grid, 256, 0, st>>>(static_cast<float2*>(d_state), m, d, th64,
-                                                                     static_cast<const double2*>(d_coef), inv);
-    else
+                                                                     static_cast<const float2*>(cs));
+    } else {
+        qft::qpe_setup_kernel<double2, double><<<sblocks, 256, 0, st>>>(d_theta, coef, d, inv, th64,
+                                                                        static_cast<double2*>(cs));
         qft::qpe_prepare_kernel<double2, double><<<grid, 256, 0, st>>>(static_cast<double2*>(d_state), m, d, th64,
-                                                                       static_cast<const double2*>(d_coef), inv);
+                                                                       static_cast<const double2*>(cs));
+    }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QFT_OK : qft::set_cuda_error(e);
 }
@@ -138,7 +223,7 @@ int qft_qpe_probabilities(const void* d_state, int m, int d_bits, int dtype, dou
     if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
     if (m < 1 || d_bits < 0 || d_bits > 20 || m + d_bits > 34) return QFT_ERR_BAD_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int grid = qft::grid_for(uint64_t(1) << m);
+    const int grid = qft::grid_for(((uint64_t(1) << m) + qft::kXU - 1) / qft::kXU);
     if (dtype == QFT_C64)
         qft::qpe_prob_kernel<float2, float><<<grid, 256, 0, st>>>(static_cast<const float2*>(d_state), m, 1 << d_bits,
                                                                   d_prob);
