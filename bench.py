@@ -327,8 +327,10 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
         return ms, status, plans
 
     # plan shapes: the default tiles (one CTA per SM) and 2^12-amplitude tiles
-    # (two CTAs per SM, so one CTA's tile load overlaps the other's stages)
-    variants = {"tile13_default": {}, "tile12_two_ctas": {"tile_bits": 12}}
+    # (two CTAs per SM, so one CTA's tile load overlaps the other's stages) and
+    # 2^13 tiles in 512-thread CTAs (blocks of <= 4 wires, 16 warps per SM)
+    variants = {"tile13_default": {}, "tile12_two_ctas": {"tile_bits": 12},
+                "tile13_512_threads": {"tile_bits": 13, "threads": 512}}
     timed = {name: time_batch(opts) for name, opts in variants.items()}
     best = min(timed, key=lambda k: timed[k][0])
     ms, status, plans = timed[best]

@@ -95,6 +95,21 @@ struct PassParams {
 };
 
 // One tile of one pass of one transform in a batched launch.
+// Shared-memory layout of a batched launch: the largest tile (2^max_tb
+// amplitudes) sizes buffer B and the nbuf (1 or 2) load buffers; the group
+// tables hold max_ntab entries of tw_stride twiddle bytes (the widest block's
+// planes) plus offsets.
+struct BatchLayout {
+    int32_t max_tb;
+    int32_t max_ntab;
+    int32_t nbuf;
+    int32_t tw_stride;
+    int32_t threads;  // CTA size of the batch kernel (256 or 512)
+};
+
+// Partial-norm slots per first-pass tile in a batch (one per warp, up to 16 warps).
+constexpr int kBatchNormSlots = 16;
+
 struct BatchItem {
     int32_t desc;         // index of the transform's PassParams for this pass
     int32_t shape;        // passes with equal shape ids share group tables

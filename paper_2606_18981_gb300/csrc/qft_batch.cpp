@@ -24,11 +24,11 @@
 namespace qft {
 cudaError_t launch_batch(int dtype, int dir, int minb, const BatchItem* items, int nitems, const PassParams* descs,
                          const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
-                         int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream);
-size_t batch_smem_bytes(int max_tb, int max_ntab, size_t elem_bytes);
+                         BatchLayout lay, int grid, size_t smem, cudaStream_t stream);
+size_t batch_smem_bytes(BatchLayout lay, size_t elem_bytes);
 cudaError_t launch_batch_df(int dir, const BatchItem* items, int nitems, const PassParams* descs,
                             const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
-                            int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream);
+                            BatchLayout lay, int grid, size_t smem, cudaStream_t stream);
 cudaError_t launch_df_maxexp_list(const void* const* d_states, const uint64_t* d_n16, int* const* d_outs, int count,
                                   uint64_t max_n16, int num_sms, cudaStream_t stream);
 }  // namespace qft
@@ -36,7 +36,8 @@ cudaError_t launch_df_maxexp_list(const void* const* d_states, const uint64_t* d
 using namespace qft;
 
 struct qft_batch_s {
-    int count = 0, dtype = 0, dir = -1, nitems = 0, max_tb = 1, max_ntab = 1, grid = 1, minb = 1;
+    int count = 0, dtype = 0, dir = -1, nitems = 0, grid = 1, minb = 1;
+    BatchLayout lay{1, 1, 1, 8, 256};
     size_t smem = 0;
     uint64_t wait_ns = 2000000000ull;
     // device tables owned by the batch
@@ -61,10 +62,10 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Per-transform workspace inside the batch workspace: meta (scale_in) +
-// one partial sum per first-pass tile, then (natural order, > 1 pass) the
-// ping-pong state buffer.
+// one partial sum per warp of each first-pass tile, then (natural order,
+// > 1 pass) the ping-pong state buffer.
 size_t meta_bytes(const qft_plan_s* pl) {
-    return align_up(64 + 8 * static_cast<size_t>(pl->passes[0].prm.num_tiles));
+    return align_up(64 + 8 * static_cast<size_t>(kBatchNormSlots) * static_cast<size_t>(pl->passes[0].prm.num_tiles));
 }
 size_t work_bytes(const qft_plan_s* pl) {
     const bool need = pl->order == QFT_ORDER_NATURAL && pl->passes.size() > 1;
@@ -133,7 +134,7 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return plans[x] < plans[y]; });
 
     std::vector<PassParams> descs;
-    std::vector<BatchItem> items;
+    std::vector<std::vector<std::vector<BatchItem>>> groups(count);  // [transform][pass] -> its tile items
     std::vector<CUtensorMap> maps;
     std::vector<const qft_plan_s*> shapes;
     char* ws = static_cast<char*>(d_workspace);
@@ -186,6 +187,8 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
             const int desc_idx = static_cast<int>(descs.size());
             descs.push_back(prm);
             const int sig = (j + 1 < P) ? ncounters++ : -1;
+            groups[oi].emplace_back();
+            std::vector<BatchItem>& items = groups[oi].back();
             for (int64_t t = 0; t < prm.num_tiles; ++t) {
                 BatchItem it;
                 it.desc = desc_idx;
@@ -197,26 +200,83 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
                 it.map = map_idx;
                 items.push_back(it);
             }
-            b->max_tb = std::max(b->max_tb, static_cast<int>(prm.tb));
-            b->max_ntab = std::max(b->max_ntab, static_cast<int>(prm.ntab));
+            b->lay.max_tb = std::max(b->lay.max_tb, static_cast<int32_t>(prm.tb));
+            b->lay.max_ntab = std::max(b->lay.max_ntab, static_cast<int32_t>(prm.ntab));
+            // twiddle planes: complex entries of the element type, or 16-byte pairs for paired passes
+            b->lay.tw_stride = std::max(b->lay.tw_stride,
+                                        static_cast<int32_t>(prm.ntw * (prm.paired ? 16 : static_cast<int>(pl->esize))));
             prev_ctr = sig;
             prev_tiles = prm.num_tiles;
         }
     }
     if (rc != QFT_OK) { free_batch(b); return rc; }
-    b->nitems = static_cast<int>(items.size());
     b->ncounters = ncounters;
-    b->smem = batch_smem_bytes(b->max_tb, b->max_ntab, plans[0]->esize);
-    if (b->smem > 227 * 1024 - 4096) { free_batch(b); return QFT_ERR_UNSUPPORTED; }
+    // two load buffers (the next item's tile loads while this one computes)
+    // when they fit, else one
+    constexpr size_t kSmemLimit = 227 * 1024 - 4096;
+    b->lay.nbuf = 2;
+    b->smem = batch_smem_bytes(b->lay, plans[0]->esize);
+    if (b->smem > kSmemLimit) {
+        b->lay.nbuf = 1;
+        b->smem = batch_smem_bytes(b->lay, plans[0]->esize);
+    }
+    if (b->smem > kSmemLimit) { free_batch(b); return QFT_ERR_UNSUPPORTED; }
     // two CTAs per SM when both fit in shared memory and every block has <= 4 wires
     // (the 128-register kernel), for unpaired complex64 passes
-    bool small = b->dtype == QFT_C64 && b->max_tb <= 12 && 2 * (b->smem + 3 * 1024) <= 228 * 1024;
+    bool small = b->dtype == QFT_C64 && b->lay.max_tb <= 12 && 2 * (b->smem + 3 * 1024) <= 228 * 1024;
     for (const auto& d : descs) {
         if (d.paired) small = false;
         for (int s = 0; s < d.nstages; ++s)
             if (d.st[s].r > 4) small = false;
     }
     b->minb = small ? 2 : 1;
+    // 512-thread CTAs (twice the warps per SM) when every plan asked for them
+    // and the batch runs one CTA per SM in complex64 or double-float
+    bool t512 = b->minb == 1 && (b->dtype == QFT_C64 || b->df);
+    for (int i = 0; i < count; ++i)
+        if (plans[i]->threads != 512) t512 = false;
+    for (const auto& d : descs) {
+        if (d.paired) t512 = false;
+        for (int s = 0; s < d.nstages; ++s)
+            if (d.st[s].r > (b->df ? 3 : 4)) t512 = false;
+    }
+    b->lay.threads = t512 ? 512 : 256;
+
+    // Queue order.  A later pass's tiles wait for all tiles of the transform's
+    // previous pass; placed right behind them, they would be claimed while
+    // those are still being computed and their CTAs would idle.  So each later
+    // pass enters the queue only after about one grid's worth of other items
+    // (the first passes of the following transforms) has been queued behind
+    // its predecessor; at the end the remaining passes follow in order.  Every
+    // item still depends only on items earlier in the queue, which the
+    // persistent grid's in-order claiming needs for progress.
+    std::vector<BatchItem> items;
+    {
+        const size_t lag = static_cast<size_t>(plans[0]->num_sms) * b->minb;
+        struct Pending { size_t release; int t, j; };
+        std::vector<Pending> pending;  // release positions are increasing
+        size_t head = 0;
+        auto emit = [&](int t, int j) {
+            const auto& g = groups[t][j];
+            items.insert(items.end(), g.begin(), g.end());
+            if (j + 1 < static_cast<int>(groups[t].size())) pending.push_back({items.size() + lag, t, j + 1});
+        };
+        for (int t = 0; t < count; ++t) {
+            emit(t, 0);
+            while (head < pending.size() && pending[head].release <= items.size()) {
+                const Pending p = pending[head++];
+                emit(p.t, p.j);
+            }
+        }
+        while (head < pending.size()) {
+            const Pending p = pending[head++];
+            emit(p.t, p.j);
+        }
+    }
+    // after a first pass: all its tiles, then the completing CTA's scale_in
+    for (auto& it : items)
+        if (it.wait_ctr >= 0 && it.shape % kMaxPasses == 1) it.wait_target += 1;
+    b->nitems = static_cast<int>(items.size());
     b->grid = std::max(1, std::min(plans[0]->num_sms * b->minb, b->nitems));
 
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_counters), sizeof(int) * ncounters);
@@ -256,10 +316,10 @@ int qft_batch_execute(qft_batch_t b, qft_stream_t stream) {
         e = launch_df_maxexp_list(b->d_df_states, b->d_df_n16, b->d_df_outs, b->count, b->df_max_n16, b->num_sms, st);
         if (e != cudaSuccess) return set_cuda_error(e);
         e = launch_batch_df(b->dir, b->d_items, b->nitems, b->d_descs, b->d_maps, b->d_counters, b->d_counters,
-                            b->d_counters + 1, b->wait_ns, b->max_tb, b->max_ntab, b->grid, b->smem, st);
+                            b->d_counters + 1, b->wait_ns, b->lay, b->grid, b->smem, st);
     } else {
         e = launch_batch(b->dtype, b->dir, b->minb, b->d_items, b->nitems, b->d_descs, b->d_maps, b->d_counters,
-                         b->d_counters, b->d_counters + 1, b->wait_ns, b->max_tb, b->max_ntab, b->grid, b->smem, st);
+                         b->d_counters, b->d_counters + 1, b->wait_ns, b->lay, b->grid, b->smem, st);
     }
     return e == cudaSuccess ? QFT_OK : set_cuda_error(e);
 }

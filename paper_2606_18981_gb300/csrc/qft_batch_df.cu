@@ -1,5 +1,6 @@
 // qft_batch_df.cu -- double-float complex128 instantiations of the batched
-// persistent kernel (qft_pass_kernels.cuh): one CTA per SM, both directions.
+// persistent kernel (qft_pass_kernels.cuh): one CTA per SM of 256 or 512
+// threads, both directions.
 // The maximum-exponent pre-pass over the batch's transforms is in
 // qft_pass_df.cu.
 #include "qft_pass_kernels.cuh"
@@ -8,11 +9,16 @@ namespace qft {
 
 cudaError_t launch_batch_df(int dir, const BatchItem* items, int nitems, const PassParams* descs,
                             const CUtensorMap* maps, int* counters, int* next, int* status, uint64_t wait_ns,
-                            int max_tb, int max_ntab, int grid, size_t smem, cudaStream_t stream) {
+                            BatchLayout lay, int grid, size_t smem, cudaStream_t stream) {
+    if (lay.threads == 512)
+        return dir < 0 ? launch_batch_t<dfloat, -1, 512, 1>(items, nitems, descs, maps, counters, next, status,
+                                                            wait_ns, lay, grid, smem, stream)
+                       : launch_batch_t<dfloat, +1, 512, 1>(items, nitems, descs, maps, counters, next, status,
+                                                            wait_ns, lay, grid, smem, stream);
     return dir < 0 ? launch_batch_t<dfloat, -1, 256, 1>(items, nitems, descs, maps, counters, next, status, wait_ns,
-                                                        max_tb, max_ntab, grid, smem, stream)
+                                                        lay, grid, smem, stream)
                    : launch_batch_t<dfloat, +1, 256, 1>(items, nitems, descs, maps, counters, next, status, wait_ns,
-                                                        max_tb, max_ntab, grid, smem, stream);
+                                                        lay, grid, smem, stream);
 }
 
 }  // namespace qft

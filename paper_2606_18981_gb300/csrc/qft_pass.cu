@@ -12,10 +12,10 @@ namespace qft {
 cudaError_t launch_pass_f32(int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream);
 cudaError_t launch_pass_f64(int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream);
 cudaError_t launch_batch_f32(int dir, int minb, const BatchItem* items, int nitems, const PassParams* descs, const CUtensorMap* maps, int* counters,
-                             int* next, int* status, uint64_t wait_ns, int max_tb, int max_ntab, int grid, size_t smem,
+                             int* next, int* status, uint64_t wait_ns, BatchLayout lay, int grid, size_t smem,
                              cudaStream_t stream);
 cudaError_t launch_batch_f64(int dir, const BatchItem* items, int nitems, const PassParams* descs, const CUtensorMap* maps, int* counters,
-                             int* next, int* status, uint64_t wait_ns, int max_tb, int max_ntab, int grid, size_t smem,
+                             int* next, int* status, uint64_t wait_ns, BatchLayout lay, int grid, size_t smem,
                              cudaStream_t stream);
 cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream);  // qft_pair.cu
 
@@ -23,14 +23,18 @@ cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassP
 // blocks have <= 4 wires run two CTAs per SM (one CTA's load overlaps the
 // other's stages).
 cudaError_t launch_batch(int dtype, int dir, int minb, const BatchItem* items, int nitems, const PassParams* descs, const CUtensorMap* maps, int* counters,
-                             int* next, int* status, uint64_t wait_ns, int max_tb, int max_ntab, int grid, size_t smem,
+                             int* next, int* status, uint64_t wait_ns, BatchLayout lay, int grid, size_t smem,
                              cudaStream_t stream) {
-    if (dtype == 0) return launch_batch_f32(dir, minb, items, nitems, descs, maps, counters, next, status, wait_ns, max_tb, max_ntab, grid, smem, stream);
-    return launch_batch_f64(dir, items, nitems, descs, maps, counters, next, status, wait_ns, max_tb, max_ntab, grid, smem, stream);
+    if (dtype == 0) return launch_batch_f32(dir, minb, items, nitems, descs, maps, counters, next, status, wait_ns, lay, grid, smem, stream);
+    return launch_batch_f64(dir, items, nitems, descs, maps, counters, next, status, wait_ns, lay, grid, smem, stream);
 }
 
-size_t batch_smem_bytes(int max_tb, int max_ntab, size_t elem_bytes) {
-    return 2 * (size_t(1) << max_tb) * elem_bytes + size_t(max_ntab) * (kMaxR * 16 + 8 + 4 + 4);
+// Dynamic shared memory of one batch CTA: buffer B, the load buffers of the
+// largest tile, and the group tables (twiddle planes, output offset, tile bits
+// and their swizzled buffer-B offset per entry).
+size_t batch_smem_bytes(BatchLayout lay, size_t elem_bytes) {
+    return (1 + size_t(lay.nbuf)) * (size_t(1) << lay.max_tb) * elem_bytes +
+           size_t(lay.max_ntab) * (size_t(lay.tw_stride) + 8 + 4 + 4);
 }
 
 cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream) {
