@@ -562,39 +562,51 @@ __device__ __forceinline__ void compute_tile_twiddles(const PassParams& P, int64
 }
 
 // Build the group tables (pb, ob, cross-twiddle factors of the group's tile
-// wires) of every stage of pass P into shared memory.
+// wires) of every stage of pass P into shared memory.  One thread per (stage,
+// entry, twiddle plane): the work of all stages is spread over the CTA, so the
+// build costs about one bit loop and one phase evaluation per thread.
 template <typename T, int DIR, int NT>
 __device__ __forceinline__ void build_group_tables(const PassParams& P, GroupTab<typename Vec2<T>::type>& tab) {
     using V = typename Vec2<T>::type;
-    const int tid = threadIdx.x;
     const int ntab = tab.ntab;
+    const int ntw = P.ntw;
+    int total = 0;
     for (int s = 0; s < P.nstages; ++s) {
+        const int ng = 1 << P.st[s].ngbits;
+        total += (32 + (ng > 32 ? ng >> 5 : 1)) * ntw;
+    }
+    for (int w = threadIdx.x; w < total; w += NT) {
+        int s = 0, rem = w, nent = 0;
+        for (; s < P.nstages; ++s) {
+            const int ng = 1 << P.st[s].ngbits;
+            nent = 32 + (ng > 32 ? ng >> 5 : 1);
+            if (rem < nent * ntw) break;
+            rem -= nent * ntw;
+        }
         const StageDesc& S = P.st[s];
+        const int e = rem / nent, i = rem - e * nent;  // consecutive threads: consecutive entries of one plane
         const int ng = 1 << S.ngbits;
-        const int nhi = ng > 32 ? ng >> 5 : 1;
-        for (int i = tid; i < 32 + nhi; i += NT) {
-            const int g = i < 32 ? (i < ng ? i : 0) : ((i - 32) << 5);
-            uint32_t pb = 0;
-            uint64_t iw = 0;
-            int64_t ob = 0;
-            for (int b = 0; b < S.ngbits; ++b) {
-                if ((g >> b) & 1) {
-                    const int p = S.gpos[b];
-                    pb |= 1u << p;
-                    iw |= 1ull << P.p_wire[p];
-                    ob += int64_t(1) << P.p_out[p];
-                }
+        const int g = i < 32 ? (i < ng ? i : 0) : ((i - 32) << 5);
+        uint32_t pb = 0;
+        uint64_t iw = 0;
+        int64_t ob = 0;
+        for (int b = 0; b < S.ngbits; ++b) {
+            if ((g >> b) & 1) {
+                const int p = S.gpos[b];
+                pb |= 1u << p;
+                iw |= 1ull << P.p_wire[p];
+                ob += int64_t(1) << P.p_out[p];
             }
-            const int idx = P.tab_off[s] + i;
+        }
+        const int idx = P.tab_off[s] + i;
+        if (e == 0) {
             tab.pb[idx] = pb;
             tab.sb[idx] = swz<sizeof(V) == 8 ? 4 : 3>(pb);
             tab.ob[idx] = ob;
-            for (int e = 0; e < P.ntw; ++e) {
-                V w = cunit<V>();
-                if (S.cross && e < S.r) w = phase_turns<T, DIR>(cross_phase(iw, P.n, S.wlo + S.r - 1, S.wlo + e, P.kk), P.n);
-                tab.tw[e * ntab + idx] = w;
-            }
         }
+        V tw = cunit<V>();
+        if (S.cross && e < S.r) tw = phase_turns<T, DIR>(cross_phase(iw, P.n, S.wlo + S.r - 1, S.wlo + e, P.kk), P.n);
+        tab.tw[e * ntab + idx] = tw;
     }
 }
 
