@@ -336,9 +336,13 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
     ms, status, plans = timed[best]
     a = torch.cuda.Event(enable_timing=True)
     bb = torch.cuda.Event(enable_timing=True)
+    # algorithmic HBM bytes: every pass of every transform reads and writes its state once
+    byts = sum(plans[(n, k)].info().passes * 2 * (1 << n) * 8 for n, k, _ in specs)
+    peak, _ = load_peaks()
     out = {"transforms": count, "amplitudes": amps, "ms_per_batch": ms, "transforms_per_s": count / (ms / 1e3),
            "amplitudes_per_s": amps / (ms / 1e3), "status": status, "launches_per_batch": 1,
-           "graph": True, "plans": best,
+           "graph": True, "plans": best, "pass_bytes": byts,
+           "hbm_frac": byts / (ms / 1e3) / 1e9 / peak,
            "ms_per_batch_by_plans": {name: t[0] for name, t in timed.items()}}
     # the plain single-transform complex128 paths on the same transforms: the
     # default double-float kernel and IEEE FP64
