@@ -562,11 +562,48 @@ __device__ __forceinline__ void compute_tile_twiddles(const PassParams& P, int64
 }
 
 // Build the group tables (pb, ob, cross-twiddle factors of the group's tile
-// wires) of every stage of pass P into shared memory.  One thread per (stage,
-// entry, twiddle plane): the work of all stages is spread over the CTA, so the
-// build costs about one bit loop and one phase evaluation per thread.
+// wires) of every stage of pass P into shared memory.
 template <typename T, int DIR, int NT>
 __device__ __forceinline__ void build_group_tables(const PassParams& P, GroupTab<typename Vec2<T>::type>& tab) {
+    using V = typename Vec2<T>::type;
+    const int tid = threadIdx.x;
+    const int ntab = tab.ntab;
+    for (int s = 0; s < P.nstages; ++s) {
+        const StageDesc& S = P.st[s];
+        const int ng = 1 << S.ngbits;
+        const int nhi = ng > 32 ? ng >> 5 : 1;
+        for (int i = tid; i < 32 + nhi; i += NT) {
+            const int g = i < 32 ? (i < ng ? i : 0) : ((i - 32) << 5);
+            uint32_t pb = 0;
+            uint64_t iw = 0;
+            int64_t ob = 0;
+            for (int b = 0; b < S.ngbits; ++b) {
+                if ((g >> b) & 1) {
+                    const int p = S.gpos[b];
+                    pb |= 1u << p;
+                    iw |= 1ull << P.p_wire[p];
+                    ob += int64_t(1) << P.p_out[p];
+                }
+            }
+            const int idx = P.tab_off[s] + i;
+            tab.pb[idx] = pb;
+            tab.sb[idx] = swz<sizeof(V) == 8 ? 4 : 3>(pb);
+            tab.ob[idx] = ob;
+            for (int e = 0; e < P.ntw; ++e) {
+                V w = cunit<V>();
+                if (S.cross && e < S.r) w = phase_turns<T, DIR>(cross_phase(iw, P.n, S.wlo + S.r - 1, S.wlo + e, P.kk), P.n);
+                tab.tw[e * ntab + idx] = w;
+            }
+        }
+    }
+}
+
+// The same tables with one thread per (stage, entry, twiddle plane): the work
+// of all stages is spread over the CTA, so a build costs about one bit loop
+// and one phase evaluation per thread (the batched launch rebuilds them
+// whenever a CTA's next item has another pass shape).
+template <typename T, int DIR, int NT>
+__device__ __forceinline__ void build_group_tables_wide(const PassParams& P, GroupTab<typename Vec2<T>::type>& tab) {
     using V = typename Vec2<T>::type;
     const int ntab = tab.ntab;
     const int ntw = P.ntw;

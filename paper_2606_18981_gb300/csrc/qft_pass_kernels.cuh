@@ -487,9 +487,9 @@ __global__ void __launch_bounds__(NT, MINB)
         if (it.shape != cached_shape) {
             if constexpr (kCanPair) {
                 if (paired) build_group_tables_p<DIR, NT>(P, tabp);
-                else build_group_tables<T, DIR, NT>(P, tab);
+                else build_group_tables_wide<T, DIR, NT>(P, tab);
             } else {
-                build_group_tables<T, DIR, NT>(P, tab);
+                build_group_tables_wide<T, DIR, NT>(P, tab);
             }
             cached_shape = it.shape;
         }
