@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched workload with its default plans (a profiling target); prints its JSON")
     return ap.parse_args()
 
 
@@ -275,7 +277,7 @@ def device_input(torch, kind, n, seed, dt, device):
     return qft_inputs.device_gaussian(n, seed, dt, device=str(device))
 
 
-def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
+def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5, variants=None, baselines=True):
     """The batched configuration: count transforms, n ~ U{8..18}, complex64,
     input kinds ~ U{Gaussian, tones, basis}, AQFT k ~ U{4, 8, n}, forward,
     natural order; one persistent launch captured in a CUDA graph.  Also times
@@ -329,8 +331,9 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
     # plan shapes: the default tiles (one CTA per SM) and 2^12-amplitude tiles
     # (two CTAs per SM, so one CTA's tile load overlaps the other's stages) and
     # 2^13 tiles in 512-thread CTAs (blocks of <= 4 wires, 16 warps per SM)
-    variants = {"tile13_default": {}, "tile12_two_ctas": {"tile_bits": 12},
-                "tile13_512_threads": {"tile_bits": 13, "threads": 512}}
+    if variants is None:
+        variants = {"tile13_default": {}, "tile12_two_ctas": {"tile_bits": 12},
+                    "tile13_512_threads": {"tile_bits": 13, "threads": 512}}
     timed = {name: time_batch(opts) for name, opts in variants.items()}
     best = min(timed, key=lambda k: timed[k][0])
     ms, status, plans = timed[best]
@@ -344,6 +347,8 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5):
            "graph": True, "plans": best, "pass_bytes": byts,
            "hbm_frac": byts / (ms / 1e3) / 1e9 / peak,
            "ms_per_batch_by_plans": {name: t[0] for name, t in timed.items()}}
+    if not baselines:
+        return out
     # the plain single-transform complex128 paths on the same transforms: the
     # default double-float kernel and IEEE FP64
     buf = torch.empty(1 << 18, dtype=torch.complex128, device=dev)
@@ -833,6 +838,17 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.batched_only:
+        import torch
+
+        import paper_2606_18981_gb300 as q
+
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        out = batched_workload(q, torch, dev, torch.cuda.Stream(device=dev), reps=args.steps,
+                               variants={"tile13_default": {}}, baselines=False)
+        print(json.dumps(out))
         return
     run_ours(args, world, rank, local)
 
