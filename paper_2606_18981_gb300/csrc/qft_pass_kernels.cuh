@@ -415,6 +415,8 @@ __global__ void __launch_bounds__(NT, MINB)
     __shared__ double red[NT / 32];
     __shared__ __align__(16) P2 Ubuf_raw[kMaxR * kMaxStages];
     __shared__ int s_first, s_next, s_pref, s_ok;
+    __shared__ __align__(16) PassParams s_prm;
+    static_assert(sizeof(PassParams) % 8 == 0, "descriptor copied in 8-byte words");
 
     const int tid = threadIdx.x;
     using Tr = AmpTraits<T>;
@@ -481,25 +483,31 @@ __global__ void __launch_bounds__(NT, MINB)
             s_pref = pref;
         }
         const BatchItem it = items[item];
-        const PassParams& P = descs[it.desc];
+        const PassParams& Pg = descs[it.desc];
         constexpr bool kCanPair = sizeof(T) == 4 && MINB == 1 && NT == 256;  // paired items: one 256-thread CTA per SM
-        const bool paired = kCanPair && P.paired;
+        const bool paired = kCanPair && Pg.paired;
         if (it.shape != cached_shape) {
             if constexpr (kCanPair) {
-                if (paired) build_group_tables_p<DIR, NT>(P, tabp);
-                else build_group_tables_wide<T, DIR, NT>(P, tab);
+                if (paired) build_group_tables_p<DIR, NT>(Pg, tabp);
+                else build_group_tables_wide<T, DIR, NT>(Pg, tab);
             } else {
-                build_group_tables_wide<T, DIR, NT>(P, tab);
+                build_group_tables_wide<T, DIR, NT>(Pg, tab);
             }
             cached_shape = it.shape;
         }
         if constexpr (kCanPair) {
-            if (paired) compute_tile_twiddles_p<DIR>(P, it.tile, Ubuf_raw);
-            else compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
+            if (paired) compute_tile_twiddles_p<DIR>(Pg, it.tile, Ubuf_raw);
+            else compute_tile_twiddles<T, DIR>(Pg, it.tile, Ubuf);
         } else {
-            compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
+            compute_tile_twiddles<T, DIR>(Pg, it.tile, Ubuf);
         }
-        __syncthreads();  // tables, twiddles, s_next and s_pref
+        {  // the item's pass descriptor into shared memory for the stages (read there many times)
+            const uint64_t* src = reinterpret_cast<const uint64_t*>(&Pg);
+            uint64_t* dst = reinterpret_cast<uint64_t*>(&s_prm);
+            for (int i = tid; i < static_cast<int>(sizeof(PassParams) / 8); i += NT) dst[i] = src[i];
+        }
+        __syncthreads();  // tables, twiddles, descriptor, s_next and s_pref
+        const PassParams& P = s_prm;
         const int nx = s_next;
         const int pref = s_pref;
         const bool okw = mbar_wait_bounded(&mbar[buf], (parity >> buf) & 1u, wait_ns);
