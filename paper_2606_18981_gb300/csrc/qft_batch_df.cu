@@ -1,9 +1,9 @@
 // qft_batch_df.cu -- double-float complex128 instantiations of the batched
-// persistent kernel (qft_pass_kernels.cuh): one CTA per SM of 256 or 512
+// persistent kernel (qft_batch_kernel.cuh): one CTA per SM of 256 or 512
 // threads, both directions.
 // The maximum-exponent pre-pass over the batch's transforms is in
 // qft_pass_df.cu.
-#include "qft_pass_kernels.cuh"
+#include "qft_batch_kernel.cuh"
 
 namespace qft {
 

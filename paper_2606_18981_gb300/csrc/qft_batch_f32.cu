@@ -1,7 +1,7 @@
 // qft_batch_f32.cu -- complex64 instantiations of the batched persistent
-// kernel (qft_pass_kernels.cuh): 256 threads with one or two CTAs per SM, or
+// kernel (qft_batch_kernel.cuh): 256 threads with one or two CTAs per SM, or
 // 512 threads with one, both directions.
-#include "qft_pass_kernels.cuh"
+#include "qft_batch_kernel.cuh"
 
 namespace qft {
 

@@ -1,6 +1,6 @@
 // qft_batch_f64.cu -- complex128 instantiations of the batched persistent
-// kernel (qft_pass_kernels.cuh): one CTA per SM, both directions.
-#include "qft_pass_kernels.cuh"
+// kernel (qft_batch_kernel.cuh): one CTA per SM, both directions.
+#include "qft_batch_kernel.cuh"
 
 namespace qft {
 
