@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(NT, MINB)
     __shared__ double red[NT / 32];
     __shared__ __align__(16) P2 Ubuf_raw[kMaxR * kMaxStages];
     __shared__ int s_first, s_next, s_pref, s_ok;
-    __shared__ __align__(16) PassParams s_prm;
+    __shared__ __align__(16) PassParams s_prm[2];  // this item's pass descriptor and the next one's
+    __shared__ int s_nxdesc;
     static_assert(sizeof(PassParams) % 8 == 0, "descriptor copied in 8-byte words");
 
     const int tid = threadIdx.x;
@@ -153,7 +154,13 @@ __global__ void __launch_bounds__(NT, MINB)
     __syncthreads();
     int item = s_first;
     bool cur_ok = s_ok != 0;
+    constexpr int kWords = static_cast<int>(sizeof(PassParams) / 8);
+    static_assert(kWords <= NT, "one descriptor word per thread");
+    if (item < nitems && tid < kWords)
+        reinterpret_cast<uint64_t*>(&s_prm[0])[tid] = reinterpret_cast<const uint64_t*>(&descs[items[item].desc])[tid];
+    __syncthreads();
     int buf = 0;
+    int pb = 0;  // which s_prm holds this item's descriptor
     bool aborted = false;
     while (item < nitems) {
         if (!cur_ok) {  // the wait for this item's producers gave up (same value in every thread)
@@ -172,43 +179,40 @@ __global__ void __launch_bounds__(NT, MINB)
             }
             s_next = nx;
             s_pref = pref;
+            s_nxdesc = nx < nitems ? items[nx].desc : 0;
         }
         const BatchItem it = items[item];
-        const PassParams& Pg = descs[it.desc];
+        // the pass descriptor, copied into shared memory during the previous item
+        const PassParams& P = s_prm[pb];
         constexpr bool kCanPair = sizeof(T) == 4 && MINB == 1 && NT == 256;  // paired items: one 256-thread CTA per SM
-        const bool paired = kCanPair && Pg.paired;
+        const bool paired = kCanPair && P.paired;
         if (it.shape != cached_shape) {
             if constexpr (kCanPair) {
-                if (paired) build_group_tables_p<DIR, NT>(Pg, tabp);
-                else build_group_tables_wide<T, DIR, NT>(Pg, tab);
+                if (paired) build_group_tables_p<DIR, NT>(P, tabp);
+                else build_group_tables_wide<T, DIR, NT>(P, tab);
             } else {
-                build_group_tables_wide<T, DIR, NT>(Pg, tab);
+                build_group_tables_wide<T, DIR, NT>(P, tab);
             }
             cached_shape = it.shape;
         }
         if constexpr (kCanPair) {
-            if (paired) compute_tile_twiddles_p<DIR>(Pg, it.tile, Ubuf_raw);
-            else compute_tile_twiddles<T, DIR>(Pg, it.tile, Ubuf);
+            if (paired) compute_tile_twiddles_p<DIR>(P, it.tile, Ubuf_raw);
+            else compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
         } else {
-            compute_tile_twiddles<T, DIR>(Pg, it.tile, Ubuf);
+            compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
         }
-        {  // the item's pass descriptor into shared memory for the stages (read there many times)
-            const uint64_t* src = reinterpret_cast<const uint64_t*>(&Pg);
-            uint64_t* dst = reinterpret_cast<uint64_t*>(&s_prm);
-            for (int i = tid; i < static_cast<int>(sizeof(PassParams) / 8); i += NT) dst[i] = src[i];
-        }
-        __syncthreads();  // tables, twiddles, descriptor, s_next and s_pref
-        const PassParams& P = s_prm;
+        __syncthreads();  // tables, twiddles, s_next, s_pref and s_nxdesc
         const int nx = s_next;
         const int pref = s_pref;
+        // Each thread waits for the tile on its own; whether any wait gave up
+        // is decided CTA-wide at the first barrier that follows.  A thread
+        // whose wait gave up skips its stage work, and keeps the phase bit
+        // (and thread 0 the in-flight mark) for the wait on exit.
         const bool okw = mbar_wait_bounded(&mbar[buf], (parity >> buf) & 1u, wait_ns);
-        parity ^= 1u << buf;
-        if (__syncthreads_or(!okw)) {
-            parity ^= 1u << buf;  // this load may still be in flight: wait on it again below
-            aborted = true;
-            break;
+        if (okw) {
+            parity ^= 1u << buf;
+            if (tid == 0) inflight &= ~(1u << buf);
         }
-        if (tid == 0) inflight &= ~(1u << buf);
         uint64_t I_tile;
         int64_t out_tile;
         tile_coords(P, it.tile, I_tile, out_tile);
@@ -220,7 +224,13 @@ __global__ void __launch_bounds__(NT, MINB)
             io.shift_in = df_shift_from_meta(P.meta);
         }
         T scale = T(1);
+        bool checked = false;  // the tile wait's CTA-wide check is done
         if (P.first && P.last) {
+            if (__syncthreads_or(!okw)) {
+                aborted = true;
+                break;
+            }
+            checked = true;
             double s = 0.0;
             for (uint32_t i = tid; i < (1u << P.tb); i += NT) s += Tr::norm2_at(A, i, io);
             const double tot = block_sum<NT>(s, red);
@@ -238,20 +248,36 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         double norm_acc = 0.0;
         for (int s = 0; s < P.nstages; ++s) {
-            if constexpr (kCanPair) {
-                if (paired) {
-                    dispatch_stage_p<DIR, NT, 4>(P, s, tabp, reinterpret_cast<const float2*>(A), reinterpret_cast<P2*>(B),
-                                              out_tile, static_cast<float>(scale), Ubuf_raw + P.st[s].uoff,
-                                              P.first && !P.last, norm_acc);
-                    __syncthreads();
-                    continue;
+            if (okw) {
+                bool done = false;
+                if constexpr (kCanPair) {
+                    if (paired) {
+                        dispatch_stage_p<DIR, NT, 4>(P, s, tabp, reinterpret_cast<const float2*>(A),
+                                                  reinterpret_cast<P2*>(B), out_tile, static_cast<float>(scale),
+                                                  Ubuf_raw + P.st[s].uoff, P.first && !P.last, norm_acc);
+                        done = true;
+                    }
                 }
+                if (!done)
+                    dispatch_stage<T, DIR, NT, kBatchMaxR>(P, s, tab, A, B, out_tile, scale, Ubuf + P.st[s].uoff,
+                                                           P.first && !P.last, norm_acc, io);
             }
-            dispatch_stage<T, DIR, NT, kBatchMaxR>(P, s, tab, A, B, out_tile, scale,
-                                                                        Ubuf + P.st[s].uoff, P.first && !P.last,
-                                                                        norm_acc, io);
-            __syncthreads();
+            if (!checked) {
+                checked = true;
+                if (__syncthreads_or(!okw)) {
+                    aborted = true;
+                    break;
+                }
+            } else {
+                __syncthreads();
+            }
         }
+        if (aborted) break;
+        // the next item's descriptor: loaded now, stored into the other
+        // s_prm after this item's completion signal (its latency overlaps it)
+        uint64_t nd = 0;
+        const bool has_nd = nx < nitems && tid < kWords;
+        if (has_nd) nd = reinterpret_cast<const uint64_t*>(&descs[s_nxdesc])[tid];
         if (P.first && !P.last) {
             // one partial norm per warp of each first-pass tile (no CTA-wide reduction)
 #pragma unroll
@@ -259,6 +285,7 @@ __global__ void __launch_bounds__(NT, MINB)
             if ((tid & 31) == 0) P.partials[it.tile * kBatchNormSlots + (tid >> 5)] = norm_acc;
         }
         if (it.signal_ctr >= 0) batch_signal<T, NT>(it, P, counters);
+        if (has_nd) reinterpret_cast<uint64_t*>(&s_prm[pb ^ 1])[tid] = nd;
         fence_proxy_async_smem();  // this item's shared-memory reads before later TMA writes
         // the next item's load, if its producers were still running above
         if (tid == 0) {
@@ -273,6 +300,7 @@ __global__ void __launch_bounds__(NT, MINB)
         cur_ok = s_ok != 0;
         item = nx;
         buf = bnext;
+        pb ^= 1;
     }
     if (aborted) {
         if (tid == 0) {
