@@ -171,7 +171,7 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
             prm.user_scale = d_scale_in ? d_scale_in + i : nullptr;
             prm.status = nullptr;  // set below once the counter block exists
             prm.wait_limit_ns = pl->wait_limit_ns;
-            prm.test_skip_first_load = 0;
+            prm.test_skip_first_load = pl->test_skip_first_load;
             int map_idx = -1;
             if (prm.load_mode == 0) {
                 if (!fn) { rc = set_cuda_error(cudaErrorNotSupported); break; }

@@ -137,3 +137,22 @@ def test_batch_rejects_mixed_complex128_arithmetic():
     xs = [torch.zeros(1 << 10, dtype=torch.complex128, device="cuda") for _ in range(2)]
     with pytest.raises(q.QftError):
         q.Batch([a, f], xs, q.SCALE_STATE)
+
+
+def test_batch_bounded_wait_reports_timeout():
+    """Tile loads that never arrive (a planner test hook leaves each CTA's first
+    load unissued) make the batch kernel's bounded waits expire: it reports
+    QFT_ERR_TIMEOUT in its status word, and the context stays usable."""
+    plans = [q.Plan(n, -1, q.FORWARD, "c64", 0, test_skip_first_load=1, wait_limit_ms=20) for n in (14, 16, 17)]
+    states = [torch.zeros(1 << p.info().n, dtype=torch.complex64, device="cuda") for p in plans]
+    b = q.Batch(plans, states, q.SCALE_STATE)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.status() == q.ERR_TIMEOUT
+    specs, good, xs = make_batch(8, 8, 14, "c64", 0, seed=5)
+    st = [x.clone() for x in xs]
+    q.Batch([good[(n, k)] for n, k, _ in specs], st, q.SCALE_STATE).execute()
+    torch.cuda.synchronize()
+    for s_, x in zip(st, xs):
+        assert torch.isfinite(torch.view_as_real(s_)).all()
+        assert abs(float(torch.linalg.vector_norm(s_)) - 1.0) < 1e-5
