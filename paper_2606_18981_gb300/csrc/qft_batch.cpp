@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/qftfft.h"
+#include "batch_order.hpp"
 #include "plan_host.hpp"
 
 namespace qft {
@@ -242,39 +243,19 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
     }
     b->lay.threads = t512 ? 512 : 256;
 
-    // Queue order.  A later pass's tiles wait for all tiles of the
-    // transform's previous pass; placed right behind them, they would be
-    // claimed while those are still being computed and their CTAs would idle.
-    // So the transforms (in plan order) form blocks whose first passes hold at
-    // least kBlockGrids grids' worth of items, and the queue runs as a
-    // wavefront: step s holds pass 0 of block s, then pass 1 of block s - 1,
-    // pass 2 of block s - 2, ...  A later pass then follows its predecessor by
-    // about a block of other items (its input still in L2), and each CTA sees
-    // runs of items of one pass shape (fewer table rebuilds).  Every item
-    // depends only on items earlier in the queue, which the persistent grid's
-    // in-order claiming needs for progress.
+    // Queue order: a wavefront over blocks of about kBlockGrids grids' worth
+    // of first-pass items (batch_order.hpp).
     std::vector<BatchItem> items;
     {
         constexpr size_t kBlockGrids = 4;
         const size_t block_items = kBlockGrids * static_cast<size_t>(plans[0]->num_sms) * b->minb;
-        std::vector<std::vector<int>> blocks(1);
-        size_t in_block = 0, max_passes = 1;
-        for (int t = 0; t < count; ++t) {
-            if (in_block >= block_items) {
-                blocks.emplace_back();
-                in_block = 0;
-            }
-            blocks.back().push_back(t);
-            in_block += groups[t][0].size();
-            max_passes = std::max(max_passes, groups[t].size());
+        std::vector<std::vector<size_t>> sizes(count);
+        for (int t = 0; t < count; ++t)
+            for (const auto& g : groups[t]) sizes[t].push_back(g.size());
+        for (const auto& tj : wavefront_order(sizes, block_items)) {
+            const auto& g = groups[tj.first][tj.second];
+            items.insert(items.end(), g.begin(), g.end());
         }
-        const size_t nblocks = blocks.size();
-        for (size_t step = 0; step + 1 < nblocks + max_passes; ++step)
-            for (size_t j = 0; j < max_passes && j <= step; ++j) {
-                if (step - j >= nblocks) continue;
-                for (int t : blocks[step - j])
-                    if (j < groups[t].size()) items.insert(items.end(), groups[t][j].begin(), groups[t][j].end());
-            }
     }
     // after a first pass: all its tiles, then the completing CTA's scale_in
     for (auto& it : items)
