@@ -15,16 +15,18 @@ namespace qft {
 // transforms of different sizes and plans.  Each CTA claims items in order
 // from an atomic counter; an item is one tile of one pass of one transform.
 // A later-pass item waits (bounded) until every tile of its transform's
-// previous pass has signalled completion.  The host queues each later pass
-// about one grid's worth of items behind its predecessor, so the producers
-// have usually finished (and their output is still in L2) when it is claimed.
-// Loads are double-buffered (when two load buffers fit in shared memory):
-// while a CTA computes its current item it has already claimed the next one
-// and, if that item's producers are done, its tile is on the way into the
-// other buffer; otherwise (or with one buffer) the load is issued after the
-// current item, once the producers are done.  Every item depends only on items earlier in the
-// queue, claimed by running CTAs, and the earliest unfinished item is always
-// some CTA's current item with its producers done, so the waits always end.
+// previous pass has signalled completion.  The host queues the items as a
+// wavefront over blocks of transforms (batch_order.hpp), so a later pass sits
+// about a block of other items behind its predecessor: its producers have
+// usually finished when it is claimed.  Loads are double-buffered (when two
+// load buffers fit in shared memory): while a CTA computes its current item
+// it has already claimed the next one and, if that item's producers are
+// done, its tile is on the way into the other buffer; otherwise (or with one
+// buffer) the load is issued after the current item, once the producers are
+// done.  The pass descriptors are staged in shared memory one item ahead.
+// Every item depends only on items earlier in the queue, claimed by running
+// CTAs, and the earliest unfinished item is always some CTA's current item
+// with its producers done, so the waits always end.
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
     int v;
