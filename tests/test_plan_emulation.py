@@ -176,3 +176,42 @@ def test_subset_plan_rejections():
         q.Plan(8, -1, q.FORWARD, "c64", n_addr=10, w0=4)   # does not fit the array
     with pytest.raises(q.QftError):
         q.Plan(8, -1, q.FORWARD, "c64", n_addr=12, w0=2, precision=q.PREC_FP16X3)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("n", [13, 14, 15, 16])
+def test_headline_plan_shape_scaled_down(oracle_mod, dt, order, n):
+    """The plan shape the planner uses for large complex64 states (tiles of
+    TB bits with cmin coalescing bits, left-over wires on the middle passes,
+    blocks of <= 4 wires), scaled down to TB = 6, cmin = 2, blocks <= 2 so
+    that natural order takes the same 4 passes at emulation sizes; both
+    directions, against the oracle."""
+    x = qft_inputs.gaussian(n, seed=4000 + n, normalise=False)
+    for direction in (q.FORWARD, q.INVERSE):
+        p = q.Plan(n, -1, direction, dt, order, tile_bits=6, coalesce_bits=2, max_stage_bits=2, pass_split=1)
+        inf = p.info()
+        # natural order: 4 passes of <= TB - cmin wires; bit-reversed order: the
+        # last pass (contiguous, no batch wires) may take a whole tile
+        assert inf.passes == 4 if order == q.ORDER_NATURAL else inf.passes == 1 + -(-(n - 6) // 4)
+        assert sum(list(inf.wires_per_pass)[:inf.passes]) == n
+        for i in range(inf.passes):
+            check_structure(parse(p.describe_pass(i)), 8 if dt == "c64" else 16)
+        got = emulate(p, x, q.SCALE_STATE)
+        ref, _ = oracle_mod.qft(x, k=-1, sign=direction, mode=q.SCALE_STATE, natural_order=(order == q.ORDER_NATURAL))
+        assert rel_l2(got, ref) < 1e-12, (n, dt, order, direction)
+
+
+def test_default_large_complex64_plans_are_the_tuned_shape():
+    """For complex64 states of 2^27 amplitudes and more, the default plan is the
+    shape measured fastest on GB300: 2^12-amplitude tiles with 4 coalescing bits,
+    blocks of <= 4 wires, two CTAs per SM, left-over wires on the middle passes."""
+    for n in (27, 28, 30, 32):
+        p = q.Plan(n, -1, q.FORWARD, "c64", q.ORDER_NATURAL)
+        inf = p.info()
+        ds = [parse(p.describe_pass(i)) for i in range(inf.passes)]
+        assert all(P["tb"] == 12 and P["minb"] == 2 for P in ds)
+        assert all(s["r"] <= 4 for P in ds for s in P["st"])
+        assert all(P["run_bits"] >= 4 for P in ds)  # >= 128-byte HBM runs
+    w = list(q.Plan(30, -1, q.FORWARD, "c64", q.ORDER_NATURAL).info().wires_per_pass)[:4]
+    assert w == [7, 8, 8, 7]
