@@ -32,6 +32,7 @@
 
 #include "../../include/qftfft.h"
 #include "plan_host.hpp"
+#include "qft_phase64.cuh"
 
 namespace qft {
 namespace {
@@ -56,44 +57,17 @@ __global__ void qpe_setup_kernel(const double* __restrict__ theta, const double2
 }
 
 // exp(2 pi i phase / 2^64): reduced exactly in integers to the nearest quarter
-// turn, the rest (|x| <= 1/8 turn) through sincospi in the element type.
-// sin(pi x) and cos(pi x) for |x| <= 1/4 in FP32 from their Taylor series at
-// 0 (t = pi x, |t| <= pi/4; the first omitted terms, t^11/11! and t^12/12!,
-// are below 2e-9 and 2e-10), by Horner's rule: within 1.5 units of 2^-24 of
-// the exact values over the whole interval, with no range reduction (the
-// caller has reduced the phase exactly in integers).
-__device__ __forceinline__ void sincospi_quarter(float x, float& s, float& c) {
-    const float t = x * 3.14159265358979f;
-    const float t2 = t * t;
-    float ps = fmaf(t2, 1.0f / 362880.0f, -1.0f / 5040.0f);
-    ps = fmaf(ps, t2, 1.0f / 120.0f);
-    ps = fmaf(ps, t2, -1.0f / 6.0f);
-    s = fmaf(ps * t2, t, t);
-    float pc = fmaf(t2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
-    pc = fmaf(pc, t2, -1.0f / 720.0f);
-    pc = fmaf(pc, t2, 1.0f / 24.0f);
-    pc = fmaf(pc, t2, -0.5f);
-    c = fmaf(pc, t2, 1.0f);
-}
-
+// turn, the rest (|x| <= 1/8 turn) in the element type (qft_phase64.cuh).
 template <typename T>
 __device__ __forceinline__ void phase64(uint64_t phase, T& c, T& s) {
-    const uint64_t q4 = (phase + (1ull << 61)) >> 62;               // nearest quarter turn, 0..4
-    const int64_t rem = static_cast<int64_t>(phase - (q4 << 62));  // |rem| <= 2^61
-    T sn, cs;
     if constexpr (sizeof(T) == 4) {
-        // rem / 2^63 (units of pi) from the top 32 bits, rounded: the dropped
-        // part is below 2^-32 of pi, far under FP32's resolution here
-        const int32_t hi = static_cast<int32_t>((rem + (int64_t(1) << 31)) >> 32);
-        sincospi_quarter(static_cast<float>(hi) * (1.0f / 2147483648.0f), sn, cs);
+        phase64_f32(phase, c, s);
     } else {
+        int64_t rem;
+        const uint64_t q4 = phase64_quarter(phase, rem);
+        T sn, cs;
         sincospi(static_cast<double>(rem) * (1.0 / 9223372036854775808.0), &sn, &cs);
-    }
-    switch (q4 & 3) {
-        case 0: c = cs; s = sn; break;
-        case 1: c = -sn; s = cs; break;
-        case 2: c = -cs; s = -sn; break;
-        default: c = sn; s = -cs; break;
+        rotate_quarters(q4, cs, sn, c, s);
     }
 }
 
