@@ -7,7 +7,9 @@ length), the widest register stage, and the CTA size of the pass kernel.  A
 candidate can win only if its output agrees with the default plan's to the
 parity tolerance of its dtype (relative L2).  Results go to a JSON cache
 (``autotune_cache.json`` next to this file by default) that ``best_opts`` reads;
-``Plan(..., tuned=True)`` and the batched / serving helpers use it.
+``Plan(..., tuned=True)`` and the batched / serving helpers use it.  The
+environment variable ``QFTFFT_TUNING_CACHE`` overrides the cache file (a path),
+or turns tuned shapes off (``off``: the planner's defaults everywhere).
 
     python -m paper_2606_18981_gb300.autotune --dtype c64 --nmin 8 --nmax 33
 """
@@ -36,12 +38,29 @@ CANDIDATES = {
 }
 
 _cache: dict | None = None
+ENV = "QFTFFT_TUNING_CACHE"
+
+
+def cache_path() -> str | None:
+    """The cache file in effect: ``$QFTFFT_TUNING_CACHE`` if set (None when it
+    says ``off``, ``none``, ``0`` or is empty), else the package's file."""
+    v = os.environ.get(ENV)
+    if v is None:
+        return CACHE
+    if v.strip().lower() in ("", "off", "none", "0"):
+        return None
+    return v
 
 
 def load_cache(path: str | None = None) -> dict:
-    """The tuning cache at ``path`` (default: the package's cache file, read once)."""
+    """The tuning cache at ``path`` (default: the file in effect; the package's
+    file is read once)."""
     global _cache
-    if path is not None and path != CACHE:
+    if path is None:
+        path = cache_path()
+        if path is None:
+            return {}
+    if path != CACHE:
         return _read(path)
     if _cache is None:
         _cache = _read(CACHE)
@@ -91,7 +110,7 @@ def tune(ns, dtype: str = "c64", reps: int = 5, path: str | None = None, verbose
 
     td = torch.complex64 if dtype == "c64" else torch.complex128
     tol = 2e-6 if dtype == "c64" else 4e-12
-    path = path or CACHE
+    path = path or cache_path() or CACHE
     cache = dict(load_cache(path))
     cache.setdefault(dtype, {})
     for n in ns:

@@ -19,6 +19,19 @@ def test_best_opts_reads_cache(tmp_path, monkeypatch):
     assert list(p.info().tile_bits)[0] == 12
 
 
+def test_cache_override_from_the_environment(tmp_path, monkeypatch):
+    path = tmp_path / "mine.json"
+    path.write_text(json.dumps({"c64": {"18": {"opts": {"tile_bits": 11, "coalesce_bits": 3}}}}))
+    monkeypatch.setenv(autotune.ENV, str(path))
+    assert autotune.cache_path() == str(path)
+    assert autotune.best_opts(18, "c64") == {"tile_bits": 11, "coalesce_bits": 3}
+    assert list(q.Plan(18, tuned=True).info().tile_bits)[0] == 11
+    monkeypatch.setenv(autotune.ENV, "off")
+    assert autotune.cache_path() is None and autotune.best_opts(30, "c64") == {}
+    monkeypatch.delenv(autotune.ENV)
+    assert autotune.cache_path() == autotune.CACHE
+
+
 def test_every_candidate_is_a_valid_plan():
     for dt, cands in autotune.CANDIDATES.items():
         for cand in cands:
