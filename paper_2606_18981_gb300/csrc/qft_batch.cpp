@@ -168,7 +168,6 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
             prm.out = ph.out_buf == 0 ? d_states[i] : work;
             prm.meta = reinterpret_cast<double*>(meta);
             prm.partials = reinterpret_cast<double*>(meta + 64);
-            prm.npartials = static_cast<int32_t>(pl->passes[0].prm.num_tiles);
             prm.user_scale = d_scale_in ? d_scale_in + i : nullptr;
             prm.status = nullptr;  // set below once the counter block exists
             prm.wait_limit_ns = pl->wait_limit_ns;
@@ -222,9 +221,11 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
         b->smem = batch_smem_bytes(b->lay, plans[0]->esize);
     }
     if (b->smem > kSmemLimit) { free_batch(b); return QFT_ERR_UNSUPPORTED; }
-    // two CTAs per SM when both fit in shared memory and every block has <= 4 wires
+    // two CTAs per SM when both fit in shared memory (dynamic + the kernel's
+    // 4 KB of static shared memory + 1 KB the SM reserves per CTA; the grid is
+    // persistent, so both must be resident) and every block has <= 4 wires
     // (the 128-register kernel), for unpaired complex64 passes
-    bool small = b->dtype == QFT_C64 && b->lay.max_tb <= 12 && 2 * (b->smem + 3 * 1024) <= 228 * 1024;
+    bool small = b->dtype == QFT_C64 && b->lay.max_tb <= 12 && 2 * (b->smem + 5 * 1024) <= 228 * 1024;
     for (const auto& d : descs) {
         if (d.paired) small = false;
         for (int s = 0; s < d.nstages; ++s)
