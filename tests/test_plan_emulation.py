@@ -215,3 +215,21 @@ def test_default_large_complex64_plans_are_the_tuned_shape():
         assert all(P["run_bits"] >= 4 for P in ds)  # >= 128-byte HBM runs
     w = list(q.Plan(30, -1, q.FORWARD, "c64", q.ORDER_NATURAL).info().wires_per_pass)[:4]
     assert w == [7, 8, 8, 7]
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("n", [9, 13, 16])
+def test_512_thread_plans_match_oracle(oracle_mod, dt, order, n):
+    """Plans for 512-thread CTAs: blocks of <= 4 wires (complex64) or <= 3
+    (double-float complex128), replayed against the oracle."""
+    x = qft_inputs.gaussian(n, seed=5000 + n, normalise=False)
+    p = q.Plan(n, -1, q.FORWARD, dt, order, threads=512)
+    rmax = 4 if dt == "c64" else 3
+    for i in range(p.info().passes):
+        P = parse(p.describe_pass(i))
+        check_structure(P, 8 if dt == "c64" else 16)
+        assert all(s["r"] <= rmax for s in P["st"])
+    got = emulate(p, x, q.SCALE_UNITARY)
+    ref, _ = oracle_mod.qft(x, k=-1, sign=q.FORWARD, mode=q.SCALE_UNITARY, natural_order=(order == q.ORDER_NATURAL))
+    assert rel_l2(got, ref) < 1e-12
