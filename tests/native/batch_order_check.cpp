@@ -4,6 +4,8 @@
 // the first passes of the next block (or, in the tail, by the other
 // transforms' groups of the same step); groups of one block and pass are
 // contiguous.  Random batches of 1..3-pass transforms, several block sizes.
+// Then the kernel's claim protocol is simulated on such orders with random
+// item times and grid sizes: every run finishes.
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -92,6 +94,69 @@ int main() {
             CHECK(kv.second.second - kv.second.first + 1 == members, "trial %d: block %d pass %d not contiguous",
                   trial, kv.first.first, kv.first.second);
         }
+    }
+    // Progress of the kernel's claim protocol on these orders: G persistent
+    // CTAs claim items in queue order; while computing its current item a CTA
+    // claims the next one and starts its load if the producers are done,
+    // else waits for them after the current item.  Items take random times.
+    // Every run must finish (the earliest unfinished item is always some
+    // CTA's current item with its producers done).
+    for (int trial = 0; trial < 300; ++trial) {
+        const int count = 1 + static_cast<int>(rng() % 120);
+        const int G = 1 + static_cast<int>(rng() % 40);
+        const size_t block = 1 + rng() % (4 * static_cast<size_t>(G));
+        std::vector<std::vector<size_t>> passes(count);
+        for (auto& p : passes) {
+            const int np = 1 + static_cast<int>(rng() % 3);
+            for (int j = 0; j < np; ++j) p.push_back(1 + rng() % 16);
+        }
+        const auto order = qft::wavefront_order(passes, block);
+        struct Item { int t, j; };
+        std::vector<Item> items;
+        for (const auto& tj : order)
+            for (size_t k = 0; k < passes[tj.first][tj.second]; ++k) items.push_back({tj.first, tj.second});
+        const int nitems = static_cast<int>(items.size());
+        std::map<std::pair<int, int>, size_t> done;  // completed tiles per (transform, pass)
+        auto ready = [&](int i) {
+            const Item& it = items[i];
+            return it.j == 0 || done[{it.t, it.j - 1}] == passes[it.t][it.j - 1];
+        };
+        struct Cta { int cur = -1, nx = -1, left = 0; bool waiting = false; };
+        std::vector<Cta> ctas(G);
+        int next = 0, finished = 0;
+        for (auto& c : ctas) {  // first claims; the first load waits for its producers
+            c.cur = next < nitems ? next++ : nitems;
+            c.waiting = c.cur < nitems && !ready(c.cur);
+        }
+        long long tick = 0;
+        bool stuck = false;
+        while (finished < nitems) {
+            bool progress = false;
+            for (auto& c : ctas) {
+                if (c.cur >= nitems) continue;
+                if (c.waiting) {
+                    if (ready(c.cur)) { c.waiting = false; progress = true; }
+                    continue;
+                }
+                if (c.left == 0) {  // start the item: claim the next one
+                    c.nx = next < nitems ? next++ : nitems;
+                    c.left = 1 + static_cast<int>(rng() % 4);
+                    progress = true;
+                }
+                if (--c.left == 0) {  // item stored: signal, move on
+                    const Item& it = items[c.cur];
+                    ++done[{it.t, it.j}];
+                    ++finished;
+                    c.cur = c.nx;
+                    c.waiting = c.cur < nitems && !ready(c.cur);
+                }
+                progress = true;
+            }
+            if (!progress) { stuck = true; break; }
+            if (++tick > 100000000LL) { stuck = true; break; }
+        }
+        CHECK(!stuck, "protocol trial %d (G=%d, %d items): no progress with %d items finished", trial, G, nitems,
+              finished);
     }
     if (fails) {
         std::printf("%d failures\n", fails);

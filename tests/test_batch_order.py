@@ -1,7 +1,10 @@
 """Host check of the batched launch's queue order (csrc/batch_order.hpp),
 compiled and run on the CPU (tests/native/batch_order_check.cpp): every group
 queued once, dependencies only on earlier items, later passes at least a
-block behind their predecessors, runs of one pass shape per block."""
+block behind their predecessors, runs of one pass shape per block; and a
+simulation of the kernel's claim protocol (claim the next item while
+computing, wait for its producers after) on such orders, which must always
+finish (a queue with later passes first does not: the simulation reports it)."""
 import os
 import shutil
 import subprocess
