@@ -77,6 +77,18 @@ def workload_name(n, dt, k):
 REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
 
+def clocks_rejected(clk: dict) -> bool:
+    """A timed region whose clock record disqualifies its numbers: a hardware or
+    thermal slowdown was active, or the SM clock sat well below its maximum
+    with no reason given (a clock lock left by someone else).  sw_power_cap is
+    kept (normal under load)."""
+    reasons = set(clk.get("reasons") or [])
+    if reasons & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}:
+        return True
+    sm, smax = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    return bool(sm and smax and sm < 0.8 * smax and not reasons)
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons while running."""
 
@@ -673,8 +685,16 @@ def run_ours(args, world, rank, local):
             plan.execute(state, ws, q.SCALE_STATE, stream=stream)
     torch.cuda.synchronize()
     barrier()
-    with ClockSampler(gpu_id) as clk:
-        ms, per_pass = timed_transform(q, torch, plan, state, ws, stream, args.steps, 1)
+    # one re-measure if the clock record of the timed region disqualifies it
+    rejected = None
+    for attempt in range(2):
+        with ClockSampler(gpu_id) as clk:
+            ms, per_pass = timed_transform(q, torch, plan, state, ws, stream, args.steps, 1)
+        clocks = clk.summary()
+        if attempt == 0 and clocks_rejected(clocks):
+            rejected = {"ms_per_step": ms, "clocks": clocks}
+            continue
+        break
     barrier()
     status = plan.status(ws, stream)
     if status != 0:
@@ -825,7 +845,9 @@ def run_ours(args, world, rank, local):
                            "l2": "state (and workspace) larger than L2; no flush needed",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": P * args.steps,
-                "clocks": clk.summary(), "extra": extra}
+                "clocks": clocks, "extra": extra}
+        if rejected is not None:  # the first timed region's numbers, not used
+            line["remeasured"] = rejected
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

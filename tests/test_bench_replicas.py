@@ -50,3 +50,19 @@ def test_whole_job_rate_single_rank():
 
     ms, rate = bench.whole_job_rate(4.0, 1 << 20, 1)
     assert ms == 4.0 and rate == pytest.approx((1 << 20) / 0.004)
+
+
+def test_clock_record_rejection_rules():
+    """The bench re-measures once when its timed region saw a hardware or
+    thermal slowdown, or SM clocks far below maximum with no reason given;
+    the power cap alone is kept."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected({**ok, "sm_mhz": 1440.0, "reasons": ["sw_power_cap"]})
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected({**ok, "reasons": [r]})
+    assert bench.clocks_rejected({**ok, "sm_mhz": 990.0})
+    assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]})
