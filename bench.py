@@ -844,7 +844,7 @@ def run_ours(args, world, rank, local):
                            "state_bytes": N * eb,
                            "l2": "state (and workspace) larger than L2; no flush needed",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": P * args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (P + (1 if dt == "c128" and not prec else 0)) * args.steps,
                 "clocks": clocks, "extra": extra}
         if rejected is not None:  # the first timed region's numbers, not used
             line["remeasured"] = rejected
