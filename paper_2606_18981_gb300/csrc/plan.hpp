@@ -120,4 +120,30 @@ struct BatchItem {
     int32_t map;          // index of the tensor map (-1: 1D bulk load)
 };
 
+// Launch parameters of one pass of the wide kernel (qft_wide.cuh: complex64,
+// 2^14-amplitude tiles, two register stages); built by the planner, buffers
+// filled per execute.
+struct WideParams {
+    int32_t n, kk;
+    int32_t first, last, scale_mode;
+    int32_t wlo0, wlo1;   // lowest wire of the stage-0 (top) and stage-1 blocks
+    int32_t l2_prefetch;  // 1: also prefetch the tile after next into L2
+    int32_t test_skip_first_load;
+    int64_t num_tiles;
+    int32_t p_wire[14];  // tile bit x -> logical wire
+    int32_t p_out[14];   // tile bit x -> output address bit
+    int32_t nseg;
+    TileSeg seg[kMaxSegs];          // tile coordinate -> wires / output address bits
+    int32_t dim_src[kMaxDims], dim_len[kMaxDims];  // TMA coordinate of dim d from the tile index
+    int64_t oj[32];                 // output offset of stage-1 register j (x bits 4..8)
+    double inv_root_n;
+    void* out;
+    double* partials;
+    int32_t npartials;
+    double* meta;
+    double* user_scale;
+    int32_t* status;
+    uint64_t wait_limit_ns;
+};
+
 }  // namespace qft

@@ -17,6 +17,9 @@ cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtenso
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes);
 cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                           cudaStream_t stream);
+cudaError_t launch_pass_wide(int dir, int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
+                             cudaStream_t stream);
+constexpr size_t kWideSmem = 215032;  // dynamic shared memory of the wide kernel (checked in qft_wide_fwd.cu)
 cudaError_t launch_pass_df(int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                            cudaStream_t stream);
 cudaError_t launch_df_maxexp(const void* state, size_t n_amps, int* out, int num_sms, cudaStream_t stream);
@@ -47,6 +50,10 @@ struct PassHost {
     cuuint32_t box[5];
     int wires = 0;
     int run_bits = 0;  // low input address bits inside the tile (log2 amplitudes per HBM run)
+    // wide pass (complex64, 2^14-amplitude tiles, qft_wide.cuh): block split and
+    // launch parameters; its tensor map uses the 128-byte swizzle
+    int wide = 0, wide_r0 = 0, wide_r1 = 0, wide_top = 0;
+    WideParams wp{};
     // tensor-core tier: the pass's block matrix in operand format (plan-owned device memory)
     void* tc_a_hi = nullptr;
     void* tc_a_lo = nullptr;
@@ -78,6 +85,8 @@ struct qft_plan_s {
     int threads = 256;  // CTA size of the pass kernel (256: stages of <= 5 wires; 512: <= 4)
     bool pairing = false;  // complex64 passes may use the paired (packed f32x2) kernel
     int pass_split = 0;    // qft_opts.pass_split
+    int wide_tiles = 0;    // complex64 natural order on the wide pass kernel (2^14-amplitude tiles)
+    int l2_prefetch = 0;   // wide passes: also prefetch the tile after next into L2
     uint64_t wait_limit_ns = 2000000000ull;
     int test_skip_first_load = 0;
     int num_sms = 148;

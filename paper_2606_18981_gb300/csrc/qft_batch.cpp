@@ -112,6 +112,8 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
         if (plans[i]->precision) return QFT_ERR_UNSUPPORTED;  // tensor-core tier plans run only through qft_execute
         if (plans[i]->n_addr != plans[i]->n) return QFT_ERR_UNSUPPORTED;  // subset plans run only through qft_execute
         if (plans[i]->df != plans[0]->df) return QFT_ERR_UNSUPPORTED;       // one arithmetic per batch
+        for (const auto& ph : plans[i]->passes)
+            if (ph.wide) return QFT_ERR_UNSUPPORTED;  // wide-tile passes run only through qft_execute
     }
     if (workspace_bytes < qft_batch_workspace_size(plans, count)) return QFT_ERR_SIZE;
     auto fn = get_encode_fn();

@@ -52,3 +52,19 @@ size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes) {
 }
 
 }  // namespace qft
+
+namespace qft {
+
+cudaError_t launch_wide_fwd(int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
+                            cudaStream_t st);
+cudaError_t launch_wide_inv(int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
+                            cudaStream_t st);
+
+// The wide pass kernel (qft_wide.cuh) for one direction and block split.
+cudaError_t launch_pass_wide(int dir, int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
+                             cudaStream_t stream) {
+    return dir < 0 ? launch_wide_fwd(r0, r1, top, map, P, grid, stream)
+                   : launch_wide_inv(r0, r1, top, map, P, grid, stream);
+}
+
+}  // namespace qft

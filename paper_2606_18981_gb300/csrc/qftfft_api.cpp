@@ -308,6 +308,257 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
     return true;
 }
 
+// Wide pass (complex64, qft_wide.cuh): a tile of 2^14 amplitudes in the bit
+// order x0..x3 = the 4 lowest input addresses (batch), x4..x8 = E1 extra batch
+// wires then the r1 wires of the pass's low block, x9..x13 = E0 extra batch
+// wires then the r0 wires of its top block (E = 5 - r).  The TMA box
+// dimensions follow that order (tile bits of consecutive input addresses share
+// one dimension), so the tile lands in shared memory in x order; the
+// tile-coordinate dimensions (box extent 1) follow.  extra_mode picks the extra
+// batch wires: 0 = the lowest free input addresses (stage 1's first), 1 = the
+// same with stage 0's first, 2 = the free addresses just below the low block
+// (so they extend its TMA dimension).  Returns false when the shape does not
+// fit (more than 5 TMA dimensions, or store maps that would not coalesce).
+bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const std::vector<int>& Lin,
+                     const std::vector<int>& Lout, bool first, bool last, bool top, int extra_mode) {
+    const int n = pl->n;
+    const int r1 = a - r0;
+    if (r0 < 4 || r0 > 5 || r1 < 3 || r1 > 5) return false;
+    const int E0 = 5 - r0, E1 = 5 - r1;
+    std::vector<int> wire_at(n);
+    for (int w = 0; w < n; ++w) wire_at[Lin[w]] = w;
+    std::vector<char> used(n, 0);
+    for (int w = glo; w < glo + a; ++w) used[w] = 1;
+    int xw[14];
+    for (int b = 0; b < 4; ++b) {
+        const int w = wire_at[b];
+        if (used[w]) return false;
+        xw[b] = w;
+        used[w] = 1;
+    }
+    std::vector<int> ex0, ex1;
+    if (extra_mode == 2) {
+        std::vector<int> below;  // free wires at decreasing addresses under the low block
+        for (int adr = Lin[glo] - 1; adr >= 0 && static_cast<int>(below.size()) < E0 + E1; --adr)
+            if (!used[wire_at[adr]]) below.push_back(wire_at[adr]);
+        if (static_cast<int>(below.size()) < E0 + E1) return false;
+        for (int i = E1 - 1; i >= 0; --i) ex1.push_back(below[i]);
+        for (int i = E0 + E1 - 1; i >= E1; --i) ex0.push_back(below[i]);
+    } else {
+        std::vector<int> cand;
+        for (int adr = 0; adr < n; ++adr)
+            if (!used[wire_at[adr]]) cand.push_back(wire_at[adr]);
+        if (static_cast<int>(cand.size()) < E0 + E1) return false;
+        const int nfirst = extra_mode == 0 ? E1 : E0;
+        for (int i = 0; i < E0 + E1; ++i) ((i < nfirst) == (extra_mode == 0) ? ex1 : ex0).push_back(cand[i]);
+    }
+    int x = 4;
+    for (int w : ex1) xw[x++] = w;
+    for (int w = glo; w < glo + r1; ++w) xw[x++] = w;
+    for (int w : ex0) xw[x++] = w;
+    for (int w = glo + r1; w < glo + a; ++w) xw[x++] = w;
+    std::vector<char> in_tile(n, 0);
+    for (int b = 0; b < 14; ++b) in_tile[xw[b]] = 1;
+
+    PassParams& P = ph.prm;
+    std::memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.kk = pl->kk;
+    P.first = first;
+    P.last = last;
+    P.tb = 14;
+    P.num_tiles = int64_t(1) << (n - 14);
+    P.inv_root_n = std::ldexp(1.0, -n / 2) * ((n & 1) ? std::sqrt(0.5) : 1.0);
+    ph.wires = a;
+    for (int b = 0; b < 14; ++b) {
+        P.p_wire[b] = xw[b];
+        P.p_out[b] = Lout[xw[b]];
+    }
+    // coalesced stores: the first pass stores along x13..x10 (output 0..3), the others along x0..x2
+    if (top) {
+        for (int i = 0; i < 4; ++i)
+            if (P.p_out[13 - i] != i) return false;
+    } else {
+        for (int i = 0; i < 3; ++i)
+            if (P.p_out[i] != i) return false;
+    }
+    // tile-coordinate wires in input address order -> segments
+    std::vector<int> nt;
+    for (int adr = 0; adr < n; ++adr)
+        if (!in_tile[wire_at[adr]]) nt.push_back(wire_at[adr]);
+    P.nseg = 0;
+    for (int m = 0; m < static_cast<int>(nt.size());) {
+        int len = 1, dir = 0;
+        while (m + len < static_cast<int>(nt.size()) && nt[m + len] == nt[m + len - 1] + 1) {
+            const int d = Lout[nt[m + len]] - Lout[nt[m + len - 1]];
+            if (d != 1 && d != -1) break;
+            if (dir == 0) dir = d;
+            else if (d != dir) break;
+            ++len;
+        }
+        if (P.nseg >= kMaxSegs) return false;
+        TileSeg& S = P.seg[P.nseg++];
+        S.src = m;
+        S.len = len;
+        S.wire = nt[m];
+        S.out = Lout[nt[m]];
+        S.out_rev = dir < 0 ? 1 : 0;
+        m += len;
+    }
+    // TMA dimensions: x0..x3, then runs of x bits at consecutive addresses (<= 8 bits), then
+    // the tile-coordinate address runs
+    int nd = 0;
+    auto add_dim = [&](int len, int adr, int src, bool tile_dim) -> bool {
+        if (nd >= kMaxDims) return false;
+        ph.gdim[nd] = cuuint64_t(1) << len;
+        ph.box[nd] = tile_dim ? (cuuint32_t(1) << len) : 1;
+        if (nd > 0) ph.gstride[nd - 1] = (cuuint64_t(1) << adr) * 8;
+        P.dim_src[nd] = tile_dim ? 0 : src;
+        P.dim_len[nd] = tile_dim ? 0 : len;
+        P.dim_scale[nd] = 1;
+        ++nd;
+        return true;
+    };
+    if (!add_dim(4, 0, 0, true)) return false;
+    for (int b = 4; b < 14;) {
+        int len = 1;
+        while (b + len < 14 && len < 8 && Lin[xw[b + len]] == Lin[xw[b + len - 1]] + 1) ++len;
+        if (!add_dim(len, Lin[xw[b]], 0, true)) return false;
+        b += len;
+    }
+    for (int m = 0; m < static_cast<int>(nt.size());) {
+        int len = 1;
+        while (m + len < static_cast<int>(nt.size()) && Lin[nt[m + len]] == Lin[nt[m + len - 1]] + 1) ++len;
+        if (!add_dim(len, Lin[nt[m]], m, false)) return false;
+        m += len;
+    }
+    P.ndims = nd;
+    for (int d = nd; d < kMaxDims; ++d) {
+        ph.gdim[d] = 1;
+        ph.box[d] = 1;
+        ph.gstride[d - 1] = (cuuint64_t(1) << n) * 8;
+        P.dim_src[d] = 0;
+        P.dim_len[d] = 0;
+        P.dim_scale[d] = 1;
+    }
+    P.load_mode = 0;
+    ph.run_bits = 0;
+    while (ph.run_bits < n && in_tile[wire_at[ph.run_bits]]) ++ph.run_bits;
+    // the two register stages (also read by describe_pass and the CPU plan checks)
+    const int rr[2] = {r0, r1}, qq[2] = {9 + E0, 4 + E1}, wl[2] = {glo + r1, glo};
+    P.nstages = 2;
+    int ntab = 0;
+    for (int s = 0; s < 2; ++s) {
+        StageDesc& S = P.st[s];
+        S.r = rr[s];
+        S.wlo = wl[s];
+        S.q = qq[s];
+        const int hi = S.wlo + S.r - 1;
+        S.cross = hi < n - 1 ? 1 : 0;
+        S.ngbits = 14 - S.r;
+        S.tile_above = 0;
+        for (int w : nt)
+            if (w > hi) S.tile_above = 1;
+        S.uoff = s ? r0 : 0;
+        int i = 0;
+        for (int b = 0; b < 14; ++b)
+            if (b < S.q || b >= S.q + S.r) S.gpos[i++] = b;
+        S.lo_tw = S.hi_tw = 0;
+        for (int g = 0; g < S.ngbits; ++g)
+            if (P.p_wire[S.gpos[g]] > hi) (g < 5 ? S.lo_tw : S.hi_tw) = 1;
+        if (!S.lo_tw && !S.hi_tw) S.hi_tw = 1;
+        P.tab_off[s] = ntab;
+        ntab += 32 + (1 << (S.ngbits - 5));
+    }
+    P.ntab = ntab;
+    P.nU = r0 + r1;
+    P.ntw = std::max(r0, r1);
+    ph.smem = kWideSmem;
+    ph.minb = 1;
+    ph.grid = static_cast<int>(std::min<int64_t>(P.num_tiles, pl->num_sms));
+    ph.wide = 1;
+    ph.wide_r0 = r0;
+    ph.wide_r1 = r1;
+    ph.wide_top = top ? 1 : 0;
+    WideParams& W = ph.wp;
+    std::memset(&W, 0, sizeof(W));
+    W.n = n;
+    W.kk = pl->kk;
+    W.first = first;
+    W.last = last;
+    W.wlo0 = glo + r1;
+    W.wlo1 = glo;
+    W.l2_prefetch = pl->l2_prefetch;
+    W.num_tiles = P.num_tiles;
+    for (int b = 0; b < 14; ++b) {
+        W.p_wire[b] = P.p_wire[b];
+        W.p_out[b] = P.p_out[b];
+    }
+    W.nseg = P.nseg;
+    for (int g = 0; g < kMaxSegs; ++g) W.seg[g] = P.seg[g];
+    for (int d = 0; d < kMaxDims; ++d) {
+        W.dim_src[d] = P.dim_src[d];
+        W.dim_len[d] = P.dim_len[d];
+    }
+    for (int j = 0; j < 32; ++j) {
+        int64_t o = 0;
+        for (int e = 0; e < 5; ++e)
+            if ((j >> e) & 1) o += int64_t(1) << P.p_out[4 + e];
+        W.oj[j] = o;
+    }
+    W.inv_root_n = P.inv_root_n;
+    return true;
+}
+
+// Natural-order complex64 plans on wide passes: P = ceil(n / 10) passes of
+// 7..10 wires each (the top pass takes the remainder first), the layout
+// adapters of plan_passes with the 4 top wires moved to the lowest addresses.
+int plan_passes_wide(qft_plan_s* pl) {
+    const int n = pl->n;
+    if (pl->dtype != QFT_C64 || pl->order != QFT_ORDER_NATURAL || pl->n_addr != n || pl->precision) return QFT_ERR_UNSUPPORTED;
+    int P = std::max(2, (n + 9) / 10);
+    if (P > kMaxPasses) return QFT_ERR_UNSUPPORTED;
+    std::vector<int> a(P, n / P);
+    for (int j = 0; j < n % P; ++j) a[j] += 1;
+    for (int j = 0; j < P; ++j)
+        if (a[j] < 7 || a[j] > 10) return QFT_ERR_UNSUPPORTED;
+    if (n - a[0] < 4) return QFT_ERR_UNSUPPORTED;
+    std::vector<int> glo(P);
+    {
+        int t = n;
+        for (int j = 0; j < P; ++j) { t -= a[j]; glo[j] = t; }
+    }
+    std::vector<int> ident(n), brev(n), L1(n);
+    for (int w = 0; w < n; ++w) {
+        ident[w] = w;
+        brev[w] = n - 1 - w;
+        L1[w] = w;
+    }
+    for (int e = 0; e < 4; ++e) {
+        L1[n - 1 - e] = e;
+        L1[e] = n - 4 + e;
+    }
+    for (int j = 0; j < P; ++j) {
+        const bool first = j == 0, last = j == P - 1;
+        const std::vector<int>& Lin = first ? ident : L1;
+        const std::vector<int>& Lout = last ? brev : L1;
+        PassHost ph;
+        bool ok = false;
+        for (int r0 = 5; r0 >= 4 && !ok; --r0)
+            for (int mode = 0; mode < 3 && !ok; ++mode)
+                ok = build_pass_wide(pl, ph, glo[j], a[j], r0, Lin, Lout, first, last, first, mode);
+        if (!ok) return QFT_ERR_UNSUPPORTED;
+        ph.in_buf = first ? 0 : 1;
+        ph.out_buf = last ? 0 : 1;
+        pl->passes.push_back(ph);
+    }
+    const int g1 = pl->passes[0].grid;
+    if (g1 > kMaxPartials) return QFT_ERR_UNSUPPORTED;
+    pl->passes.back().prm.npartials = g1;
+    pl->passes.back().wp.npartials = g1;
+    return QFT_OK;
+}
+
 int plan_passes_subset(qft_plan_s* pl);
 
 // The whole register, or (subset plans with w0 = 0) its low n bits with the
@@ -315,6 +566,7 @@ int plan_passes_subset(qft_plan_s* pl);
 // addresses in every map.
 int plan_passes(qft_plan_s* pl) {
     if (pl->w0 != 0) return plan_passes_subset(pl);
+    if (pl->wide_tiles) return plan_passes_wide(pl);
     const int n = pl->n, na = pl->n_addr;
     std::vector<int> ident(na);
     for (int w = 0; w < na; ++w) ident[w] = w;
@@ -600,7 +852,8 @@ int encode_maps(qft_plan_s* pl, const void* in, const void* state, const void* w
         const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
         CUresult r = fn(&pl->maps[i], CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(base), ph.gdim,
                         ph.gstride, ph.box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        ph.wide ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             qft::set_cuda_error_code(static_cast<int>(r));
@@ -673,12 +926,20 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
     if (opts) {
         if (opts->order != QFT_ORDER_NATURAL && opts->order != QFT_ORDER_BITREV) { delete pl; return QFT_ERR_BAD_ARG; }
         pl->order = opts->order;
-        if (opts->tile_bits) {
+        if (opts->tile_bits == 14 && dtype == QFT_C64) {
+            // the wide pass kernel: natural order, complex64, the CUDA-core path, whole-register plans
+            if (opts->order != QFT_ORDER_NATURAL || subset || (opts->precision != QFT_PREC_NATIVE) || opts->paired ||
+                opts->threads || opts->max_stage_bits || opts->coalesce_bits) {
+                delete pl;
+                return QFT_ERR_UNSUPPORTED;
+            }
+            pl->wide_tiles = n >= 14 ? 1 : 0;
+        } else if (opts->tile_bits) {
             if (opts->tile_bits < 4 || opts->tile_bits > (dtype == QFT_C64 ? 13 : 12)) { delete pl; return QFT_ERR_BAD_ARG; }
             pl->TB = opts->tile_bits;
         }
         // small tiles keep at least 3 transform wires per pass unless told otherwise
-        if (opts->tile_bits && !opts->coalesce_bits) pl->cmin = std::min(pl->cmin, std::max(1, pl->TB - 3));
+        if (opts->tile_bits && opts->tile_bits <= 13 && !opts->coalesce_bits) pl->cmin = std::min(pl->cmin, std::max(1, pl->TB - 3));
         if (opts->coalesce_bits) {
             if (opts->coalesce_bits < 1 || opts->coalesce_bits > 6) { delete pl; return QFT_ERR_BAD_ARG; }
             pl->cmin = opts->coalesce_bits;
@@ -898,7 +1159,19 @@ int execute_range(qft_plan_t pl, const void* d_in, void* d_state, void* d_worksp
         P.status = reinterpret_cast<int32_t*>(ws + kStatusOff);
         P.wait_limit_ns = pl->wait_limit_ns;
         P.test_skip_first_load = pl->test_skip_first_load;
-        if (pl->precision)
+        if (ph.wide) {
+            WideParams W = ph.wp;
+            W.scale_mode = scale_mode;
+            W.out = P.out;
+            W.partials = P.partials;
+            W.npartials = P.npartials;
+            W.meta = P.meta;
+            W.user_scale = P.user_scale;
+            W.status = P.status;
+            W.wait_limit_ns = P.wait_limit_ns;
+            W.test_skip_first_load = P.test_skip_first_load;
+            e = launch_pass_wide(pl->dir, ph.wide_r0, ph.wide_r1, ph.wide_top, pl->maps[i], W, ph.grid, st);
+        } else if (pl->precision)
             e = launch_tc_pass(pl->dir, pl->precision, pl->maps[i], P, ph.tc_a_hi, ph.tc_a_lo, ph.tc_kpad,
                                ph.tc_ncols, ph.grid, ph.smem, st);
         else if (pl->df)
@@ -955,7 +1228,7 @@ int qft_plan_describe_pass(qft_plan_t pl, int i, long long* out, int cap) {
     for (int d = 0; d < 4; ++d) v.push_back((long long)ph.gstride[d]);
     for (int d = 0; d < kMaxDims; ++d) v.push_back((long long)ph.box[d]);
     v.insert(v.end(), {ph.grid, (long long)ph.smem, ph.in_buf, ph.out_buf, P.npartials, ph.run_bits, P.paired, ph.minb,
-                       pl->n_addr});
+                       pl->n_addr, ph.wide});
     for (size_t j = 0; j < v.size() && static_cast<int>(j) < cap; ++j) out[j] = v[j];
     return static_cast<int>(v.size());
 }

@@ -41,7 +41,7 @@ def parse(rec):
     P["gdim"] = [nx() for _ in range(K_MAX_DIMS)]
     P["gstride"] = [nx() for _ in range(4)]
     P["box"] = [nx() for _ in range(K_MAX_DIMS)]
-    for k in ("grid", "smem", "in_buf", "out_buf", "npartials", "run_bits", "paired", "minb", "n_addr"):
+    for k in ("grid", "smem", "in_buf", "out_buf", "npartials", "run_bits", "paired", "minb", "n_addr", "wide"):
         P[k] = nx()
     return P
 
