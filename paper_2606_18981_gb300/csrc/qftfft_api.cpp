@@ -510,16 +510,43 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
     return true;
 }
 
+int plan_passes_wide_split(qft_plan_s* pl, const std::vector<int>& a);
+
 // Natural-order complex64 plans on wide passes: P = ceil(n / 10) passes of
-// 7..10 wires each (the top pass takes the remainder first), the layout
-// adapters of plan_passes with the 4 top wires moved to the lowest addresses.
+// 7..10 wires each, the layout adapters of plan_passes with the 4 top wires
+// moved to the lowest addresses.
 int plan_passes_wide(qft_plan_s* pl) {
     const int n = pl->n;
     if (pl->dtype != QFT_C64 || pl->order != QFT_ORDER_NATURAL || pl->n_addr != n || pl->precision) return QFT_ERR_UNSUPPORTED;
-    int P = std::max(2, (n + 9) / 10);
+    const int P = std::max(2, (n + 9) / 10);
     if (P > kMaxPasses) return QFT_ERR_UNSUPPORTED;
-    std::vector<int> a(P, n / P);
-    for (int j = 0; j < n % P; ++j) a[j] += 1;
+    // Pass widths: as even as possible.  The wider passes go first; if a pass
+    // of that split has no wide shape, the wider passes are tried at the end
+    // instead, then in the middle.
+    std::vector<std::vector<int>> splits;
+    {
+        std::vector<int> a(P, n / P);
+        const int extra = n % P;
+        for (int j = 0; j < extra; ++j) a[j] += 1;
+        splits.push_back(a);
+        std::vector<int> b(P, n / P);
+        for (int j = 0; j < extra; ++j) b[P - 1 - j] += 1;
+        splits.push_back(b);
+        std::vector<int> c(P, n / P);
+        for (int j = 0; j < extra; ++j) c[1 + j % (P > 2 ? P - 2 : 1)] += 1;
+        splits.push_back(c);
+    }
+    for (const auto& a : splits) {
+        const int rc = plan_passes_wide_split(pl, a);
+        if (rc == QFT_OK) return rc;
+        pl->passes.clear();
+    }
+    return QFT_ERR_UNSUPPORTED;
+}
+
+int plan_passes_wide_split(qft_plan_s* pl, const std::vector<int>& a) {
+    const int n = pl->n;
+    const int P = static_cast<int>(a.size());
     for (int j = 0; j < P; ++j)
         if (a[j] < 7 || a[j] > 10) return QFT_ERR_UNSUPPORTED;
     if (n - a[0] < 4) return QFT_ERR_UNSUPPORTED;
@@ -566,7 +593,11 @@ int plan_passes_subset(qft_plan_s* pl);
 // addresses in every map.
 int plan_passes(qft_plan_s* pl) {
     if (pl->w0 != 0) return plan_passes_subset(pl);
-    if (pl->wide_tiles) return plan_passes_wide(pl);
+    if (pl->wide_tiles) {
+        const int rc = plan_passes_wide(pl);
+        if (rc == QFT_OK || pl->wide_tiles == 1) return rc;  // 1: asked for (tile_bits = 14); 2: the default
+        pl->passes.clear();
+    }
     const int n = pl->n, na = pl->n_addr;
     std::vector<int> ident(na);
     for (int w = 0; w < na; ++w) ident[w] = w;
@@ -987,6 +1018,12 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
         if (!(opts && opts->pass_split)) pl->pass_split = 1;
     }
     if (!shape_given && dtype == QFT_C128 && !fp64 && n_addr >= 21) pl->threads = 512;
+    // complex64, natural order, whole-register plans from n = 23: the wide pass
+    // kernel where the planner finds wide shapes (2^14-amplitude tiles, so
+    // ceil(n / 10) passes), else the shapes above.
+    if (!shape_given && dtype == QFT_C64 && !pl->precision && !subset && pl->order == QFT_ORDER_NATURAL &&
+        !(opts && opts->paired) && n >= 23)
+        pl->wide_tiles = 2;
     // complex64 tiles of <= 2^12 amplitudes fit two CTAs per SM; blocks of <= 4
     // wires keep the kernel within the 128 registers that needs.
     if (dtype == QFT_C64 && !pl->precision && pl->threads == 256 && pl->TB <= 12 && !rmax_given)

@@ -203,18 +203,24 @@ def test_headline_plan_shape_scaled_down(oracle_mod, dt, order, n):
 
 
 def test_default_large_complex64_plans_are_the_tuned_shape():
-    """For complex64 states of 2^27 amplitudes and more, the default plan is the
-    shape measured fastest on GB300: 2^12-amplitude tiles with 4 coalescing bits,
-    blocks of <= 4 wires, two CTAs per SM, left-over wires on the middle passes."""
+    """Default complex64 plans of 2^27 amplitudes and more: natural order runs
+    on wide passes (2^14-amplitude tiles, ceil(n / 10) passes); bit-reversed
+    order keeps the shape measured fastest on GB300 for the 2^12 / 2^13-tile
+    kernel: 2^12-amplitude tiles with 4 coalescing bits, blocks of <= 4 wires,
+    two CTAs per SM."""
     for n in (27, 28, 30, 32):
         p = q.Plan(n, -1, q.FORWARD, "c64", q.ORDER_NATURAL)
         inf = p.info()
         ds = [parse(p.describe_pass(i)) for i in range(inf.passes)]
-        assert all(P["tb"] == 12 and P["minb"] == 2 for P in ds)
-        assert all(s["r"] <= 4 for P in ds for s in P["st"])
+        assert inf.passes == (n + 9) // 10
+        assert all(P["wide"] == 1 and P["tb"] == 14 for P in ds)
         assert all(P["run_bits"] >= 4 for P in ds)  # >= 128-byte HBM runs
-    w = list(q.Plan(30, -1, q.FORWARD, "c64", q.ORDER_NATURAL).info().wires_per_pass)[:4]
-    assert w == [7, 8, 8, 7]
+        p = q.Plan(n, -1, q.FORWARD, "c64", q.ORDER_BITREV)
+        ds = [parse(p.describe_pass(i)) for i in range(p.info().passes)]
+        assert all(P["wide"] == 0 and P["tb"] == 12 and P["minb"] == 2 for P in ds)
+        assert all(s["r"] <= 4 for P in ds for s in P["st"])
+    w = list(q.Plan(30, -1, q.FORWARD, "c64", q.ORDER_NATURAL).info().wires_per_pass)[:3]
+    assert w == [10, 10, 10]
 
 
 @pytest.mark.parametrize("dt", ["c64", "c128"])

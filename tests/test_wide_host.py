@@ -1,0 +1,78 @@
+"""CPU checks of the wide pass kernel (csrc/qft_wide.cuh) before it runs on a
+GPU: its index maps exhaustively (tests/native/wide_index_check.cu: thread
+maps, shared-memory layouts, bank conflicts, store runs), the planner's wide
+pass records (structure, pass counts), and a float64 numpy replay of the
+kernel's data flow against the oracle (tests/wide_emulator.py)."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import qft_inputs
+
+q = pytest.importorskip("paper_2606_18981_gb300")
+from plan_emulator import check_structure, parse  # noqa: E402
+from wide_emulator import emulate_wide, thread_maps  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def index_exe(tmp_path_factory):
+    nvcc = next((c for c in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc") if c and os.path.exists(c)), None)
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path_factory.mktemp("wide") / "wide_index_check")
+    src = os.path.join(ROOT, "tests", "native", "wide_index_check.cu")
+    inc = [f"-I{os.path.join(ROOT, 'paper_2606_18981_gb300', 'csrc')}", f"-I{os.path.join(ROOT, 'include')}"]
+    r = subprocess.run([nvcc, "-std=c++17", "-O2", "--expt-relaxed-constexpr", *inc, "-o", exe, src],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return exe
+
+
+def test_index_maps_and_bank_conflicts(index_exe):
+    r = subprocess.run([index_exe], capture_output=True, text=True, timeout=300)
+    print(r.stdout)
+    assert r.returncode == 0 and "ALL OK" in r.stdout, r.stdout + r.stderr
+
+
+def wide_ns():
+    return [n for n in range(14, 35) if n not in (21, 22)]
+
+
+def test_wide_plan_records():
+    """Every wide plan: ceil(n/10) passes (2 at least), records that pass the
+    structural checks, and the default planner picks wide passes from n = 23."""
+    for n in wide_ns():
+        for k in (-1, 0, 5):
+            p = q.Plan(n, k, q.FORWARD, "c64", q.ORDER_NATURAL, tile_bits=14)
+            info = p.info()
+            assert info.passes == max(2, (n + 9) // 10), n
+            for i in range(info.passes):
+                P = parse(p.describe_pass(i))
+                assert P["wide"] == 1 and P["tb"] == 14 and P["nstages"] == 2
+                check_structure(P, 8)
+        d = q.Plan(n, -1, q.FORWARD, "c64")
+        assert all(parse(d.describe_pass(i))["wide"] == int(n >= 23) for i in range(d.info().passes)), n
+    for n in (21, 22):  # no wide shape: the default planner keeps the 2^13 / 2^12 tiles
+        with pytest.raises(q.QftError):
+            q.Plan(n, -1, q.FORWARD, "c64", q.ORDER_NATURAL, tile_bits=14)
+        d = q.Plan(n, -1, q.FORWARD, "c64")
+        assert all(parse(d.describe_pass(i))["wide"] == 0 for i in range(d.info().passes))
+
+
+@pytest.mark.parametrize("n", [14, 15, 16, 17, 18, 19, 20])
+def test_wide_dataflow_matches_oracle(oracle_mod, index_exe, n):
+    maps = thread_maps(index_exe)
+    x = qft_inputs.gaussian(n, seed=50 + n, normalise=False)
+    for k in (-1, 0, 3):
+        for direction in (q.FORWARD, q.INVERSE):
+            p = q.Plan(n, k, direction, "c64", q.ORDER_NATURAL, tile_bits=14)
+            for mode in (q.SCALE_STATE, q.SCALE_UNNORM, q.SCALE_INV_N):
+                got = emulate_wide(p, x, maps, mode)
+                ref, _ = oracle_mod.qft(x, k=k, sign=direction, mode=mode, natural_order=True)
+                err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+                assert err < 1e-12, (n, k, direction, mode, err)
