@@ -87,7 +87,13 @@ enum qft_status {
 /* Planner options; pass NULL for defaults.  Zero fields mean "choose". */
 typedef struct {
     int order;          /* QFT_ORDER_NATURAL (default) or QFT_ORDER_BITREV                 */
-    int tile_bits;      /* log2(amplitudes per CTA tile); 0 = default (13 c64, 12 c128)   */
+    int tile_bits;      /* log2(amplitudes per CTA tile); 0 = default (complex64 natural
+                           order from n = 23: the wide pass kernel, 14; else 13 c64, 12
+                           c128).  14 (complex64, NATURAL order, no other shape field, no
+                           precision tier, whole-register plans) asks for the wide pass
+                           kernel: tiles of 2^14 amplitudes (4 coalescing batch bits and
+                           two register stages of up to 5 wires), so ceil(n / 10) passes;
+                           QFT_ERR_UNSUPPORTED where the planner finds no wide shape.   */
     int coalesce_bits;  /* min log2(contiguous amplitudes per HBM run); 0 = default         */
     int max_stage_bits; /* max wires per register stage (1..4); 0 = default                */
     int wait_limit_ms;  /* bound of every device-side wait; 0 = default (2000 ms)           */
@@ -102,11 +108,12 @@ typedef struct {
                            (see enum qft_precision).  The block matrices are built and
                            uploaded (plan-owned device memory) by the plan's first execute,
                            which should precede any capture. */
-    int paired;         /* complex64: 1 = where a pass's lowest tile bit is a batch wire, each
-                           thread runs the two groups that differ in it with packed FP32x2
-                           arithmetic (blocks of <= 4 wires); 0 = default: one group per
-                           thread.  (Passes whose tile is <= 2^12 amplitudes and whose blocks
-                           have <= 4 wires, or <= 3 when paired, run two CTAs per SM.)     */
+    int paired;         /* must be 0.  (Packed FP32x2 "paired" stages, one thread running two
+                           groups, measured slower than one group per thread on GB300 in
+                           every plan shape and were removed; 1 gives
+                           QFT_ERR_UNSUPPORTED.  Passes whose tile is <= 2^12 complex64
+                           amplitudes and whose blocks have <= 4 wires run two CTAs per
+                           SM.)                                                            */
     int pass_split;     /* NATURAL order, 3 or more passes: how wires left over by an even
                            split are placed.  1 = on the middle passes, so the first pass
                            (whose HBM runs the natural-order input spreads over the whole
@@ -328,8 +335,18 @@ int qft_server_destroy(qft_server_t server);
  * for that device (it must be the current device) and caches it, so make the
  * first call before any stream capture.  All calls share the scratch and it
  * keeps the last call's contents; calls whose kernels overlap on the GPU race.
- * scale_in is returned only through d_scale_in (device pointer, may be NULL). */
+ * scale_in is returned only through d_scale_in (device pointer, may be NULL).
+ * Tensor-core tier plans (qft_opts.precision 1..5) allocate their block
+ * matrices on their first qft_execute; before that has run, this entry point
+ * returns QFT_ERR_UNSUPPORTED instead of allocating.  A device wait that
+ * expired is reported by qft_noalloc_status, not by the return code. */
 int qft_execute_noalloc(qft_plan_t plan, void* d_state, double* d_scale_in, int scale_mode, qft_stream_t stream);
+
+/* The status word of the scratch used by qft_execute_noalloc on the current
+ * device, after synchronising stream: 0, or QFT_ERR_TIMEOUT if a kernel of the
+ * last such call gave up a bounded wait (its output is then incomplete).
+ * Allocates nothing; a negative QFT_ERR_* on a CUDA failure. */
+int qft_noalloc_status(qft_stream_t stream);
 
 /* Copy the N results from d_state to dst (host if dst_on_device = 0, else device). */
 int qft_read(qft_plan_t plan, const void* d_state, void* dst, int dst_on_device, qft_stream_t stream);

@@ -80,6 +80,8 @@ _lib.qft_execute.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_execute_pass.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_read.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_execute_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.qft_noalloc_status.argtypes = [_vp]
+_lib.qft_noalloc_status.restype = ctypes.c_int
 _lib.qft_execute_oop.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.qft_qpe_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int]
 _lib.qft_qpe_workspace_size.restype = ctypes.c_size_t

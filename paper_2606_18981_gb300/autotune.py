@@ -22,15 +22,15 @@ import statistics
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 
 # candidate plan shapes (qft_opts fields; 0 = planner default).  Complex64
-# tiles of 2^12 amplitudes run two CTAs per SM; "paired" selects the packed
-# FP32x2 stages.
+# tiles of 2^12 amplitudes run two CTAs per SM; tile bits 14 is the wide pass
+# kernel (2^14-amplitude tiles).
 _KEYS = ("tile_bits", "coalesce_bits", "max_stage_bits", "threads", "paired", "pass_split")
 CANDIDATES = {
     "c64": [dict(zip(_KEYS, c)) for c in (
-        (0, 0, 0, 0, 0, 0), (13, 4, 5, 256, 0, 0), (13, 3, 5, 256, 0, 0), (13, 5, 5, 256, 0, 0),
-        (13, 4, 4, 512, 0, 0), (12, 4, 4, 256, 0, 0), (12, 3, 4, 256, 0, 0), (12, 5, 4, 256, 0, 0),
-        (12, 4, 3, 256, 0, 0), (11, 4, 4, 256, 0, 0), (13, 4, 4, 256, 1, 0), (12, 4, 3, 256, 1, 0),
-        (12, 4, 4, 256, 0, 1), (13, 4, 5, 256, 0, 1), (12, 4, 3, 512, 0, 1), (12, 4, 3, 512, 0, 0))],
+        (0, 0, 0, 0, 0, 0), (14, 0, 0, 0, 0, 0), (13, 4, 5, 256, 0, 0), (13, 3, 5, 256, 0, 0),
+        (13, 5, 5, 256, 0, 0), (13, 4, 4, 512, 0, 0), (12, 4, 4, 256, 0, 0), (12, 3, 4, 256, 0, 0),
+        (12, 5, 4, 256, 0, 0), (12, 4, 3, 256, 0, 0), (11, 4, 4, 256, 0, 0), (12, 4, 4, 256, 0, 1),
+        (13, 4, 5, 256, 0, 1), (12, 4, 3, 512, 0, 1), (12, 4, 3, 512, 0, 0))],
     "c128": [dict(zip(_KEYS, c)) for c in (
         (0, 0, 0, 0, 0, 0), (12, 3, 4, 256, 0, 0), (11, 3, 4, 256, 0, 0), (12, 2, 4, 256, 0, 0),
         (12, 4, 4, 256, 0, 0), (12, 3, 4, 256, 0, 1), (12, 3, 3, 256, 0, 0), (12, 3, 3, 512, 0, 0),

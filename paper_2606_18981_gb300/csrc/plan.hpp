@@ -90,7 +90,7 @@ struct PassParams {
     int32_t* status;               // workspace status word (bounded waits report here)
     uint64_t wait_limit_ns;        // bound of each tile wait
     int32_t test_skip_first_load;  // test hook: never issue the first load (the wait must expire)
-    int32_t paired;                // complex64: tile bit 0 is a SIMD lane of packed f32x2 stages (qft_pair.cuh)
+    int32_t paired;                // always 0 (kept so the pass record keeps its layout)
     int32_t ntw;                   // twiddle planes in the group tables (the widest block of the pass)
 };
 

@@ -61,6 +61,7 @@ struct PassHost {
 };
 
 int set_cuda_error(cudaError_t e);           // records e for qft_last_cuda_error, returns QFT_ERR_CUDA
+
 void set_cuda_error_code(int e);
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn();
 
@@ -83,7 +84,6 @@ struct qft_plan_s {
     size_t esize = 8;
     int TB = 13, cmin = 2, rmax = 4;
     int threads = 256;  // CTA size of the pass kernel (256: stages of <= 5 wires; 512: <= 4)
-    bool pairing = false;  // complex64 passes may use the paired (packed f32x2) kernel
     int pass_split = 0;    // qft_opts.pass_split
     int wide_tiles = 0;    // complex64 natural order on the wide pass kernel (2^14-amplitude tiles)
     int l2_prefetch = 0;   // wide passes: also prefetch the tile after next into L2
@@ -100,3 +100,10 @@ struct qft_plan_s {
     const void* map_work = nullptr;
     std::vector<CUtensorMap> maps;
 };
+
+namespace qft {
+// True when executing the plan will not allocate device memory: every plan
+// except a tensor-core tier plan whose block matrices have not been uploaded
+// yet (its first qft_execute does that).
+bool plan_device_ready(const qft_plan_s* pl);
+}  // namespace qft

@@ -204,9 +204,8 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
             }
             b->lay.max_tb = std::max(b->lay.max_tb, static_cast<int32_t>(prm.tb));
             b->lay.max_ntab = std::max(b->lay.max_ntab, static_cast<int32_t>(prm.ntab));
-            // twiddle planes: complex entries of the element type, or 16-byte pairs for paired passes
-            b->lay.tw_stride = std::max(b->lay.tw_stride,
-                                        static_cast<int32_t>(prm.ntw * (prm.paired ? 16 : static_cast<int>(pl->esize))));
+            // twiddle planes: complex entries of the element type
+            b->lay.tw_stride = std::max(b->lay.tw_stride, static_cast<int32_t>(prm.ntw * static_cast<int>(pl->esize)));
             prev_ctr = sig;
             prev_tiles = prm.num_tiles;
         }
@@ -226,10 +225,9 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
     // two CTAs per SM when both fit in shared memory (dynamic + the kernel's
     // 4 KB of static shared memory + 1 KB the SM reserves per CTA; the grid is
     // persistent, so both must be resident) and every block has <= 4 wires
-    // (the 128-register kernel), for unpaired complex64 passes
+    // (the 128-register kernel), for complex64 passes
     bool small = b->dtype == QFT_C64 && b->lay.max_tb <= 12 && 2 * (b->smem + 5 * 1024) <= 228 * 1024;
     for (const auto& d : descs) {
-        if (d.paired) small = false;
         for (int s = 0; s < d.nstages; ++s)
             if (d.st[s].r > 4) small = false;
     }
@@ -240,7 +238,6 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
     for (int i = 0; i < count; ++i)
         if (plans[i]->threads != 512) t512 = false;
     for (const auto& d : descs) {
-        if (d.paired) t512 = false;
         for (int s = 0; s < d.nstages; ++s)
             if (d.st[s].r > (b->df ? 3 : 4)) t512 = false;
     }

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(NT, MINB)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ double red[NT / 32];
-    __shared__ __align__(16) P2 Ubuf_raw[kMaxR * kMaxStages];
+    __shared__ __align__(16) typename Vec2<T>::type Ubuf_raw[kMaxR * kMaxStages];
     __shared__ int s_first, s_next, s_pref, s_ok;
     __shared__ __align__(16) PassParams s_prm[2];  // this item's pass descriptor and the next one's
     __shared__ int s_nxdesc;
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NT, MINB)
     const uint32_t other = lay.nbuf == 2 ? max_elems : 0u;  // offset of the other load buffer (0: one buffer)
     V* B = reinterpret_cast<V*>(smem_raw);
     V* A0 = B + max_elems;  // load buffers A0 and, with two, A0 + max_elems
-    V* Ubuf = reinterpret_cast<V*>(Ubuf_raw);
+    V* Ubuf = Ubuf_raw;
     // group tables: twiddle planes (lay.tw_stride bytes per entry), output offsets, tile bits
     unsigned char* tab_raw = smem_raw + (1 + lay.nbuf) * static_cast<size_t>(max_elems) * sizeof(V);
     const size_t ntab = static_cast<size_t>(lay.max_ntab);
@@ -130,11 +130,6 @@ __global__ void __launch_bounds__(NT, MINB)
     tab.ob = reinterpret_cast<int64_t*>(tab_raw + static_cast<size_t>(lay.tw_stride) * ntab);
     tab.pb = reinterpret_cast<uint32_t*>(tab_raw + (static_cast<size_t>(lay.tw_stride) + 8) * ntab);
     tab.sb = tab.pb + ntab;
-    GroupTabP tabp;
-    tabp.ntab = lay.max_ntab;
-    tabp.tw = reinterpret_cast<P2*>(tab_raw);
-    tabp.ob = tab.ob;
-    tabp.pb = tab.pb;
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
@@ -188,23 +183,11 @@ __global__ void __launch_bounds__(NT, MINB)
         const BatchItem it = items[item];
         // the pass descriptor, copied into shared memory during the previous item
         const PassParams& P = s_prm[pb];
-        constexpr bool kCanPair = sizeof(T) == 4 && MINB == 1 && NT == 256;  // paired items: one 256-thread CTA per SM
-        const bool paired = kCanPair && P.paired;
         if (it.shape != cached_shape) {
-            if constexpr (kCanPair) {
-                if (paired) build_group_tables_p<DIR, NT>(P, tabp);
-                else build_group_tables_wide<T, DIR, NT>(P, tab);
-            } else {
-                build_group_tables_wide<T, DIR, NT>(P, tab);
-            }
+            build_group_tables_wide<T, DIR, NT>(P, tab);
             cached_shape = it.shape;
         }
-        if constexpr (kCanPair) {
-            if (paired) compute_tile_twiddles_p<DIR>(P, it.tile, Ubuf_raw);
-            else compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
-        } else {
-            compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
-        }
+        compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
         __syncthreads();  // tables, twiddles, s_next, s_pref and s_nxdesc
         const int nx = s_next;
         const int pref = s_pref;
@@ -252,20 +235,9 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         double norm_acc = 0.0;
         for (int s = 0; s < P.nstages; ++s) {
-            if (okw) {
-                bool done = false;
-                if constexpr (kCanPair) {
-                    if (paired) {
-                        dispatch_stage_p<DIR, NT, 4>(P, s, tabp, reinterpret_cast<const float2*>(A),
-                                                  reinterpret_cast<P2*>(B), out_tile, static_cast<float>(scale),
-                                                  Ubuf_raw + P.st[s].uoff, P.first && !P.last, norm_acc);
-                        done = true;
-                    }
-                }
-                if (!done)
-                    dispatch_stage<T, DIR, NT, kBatchMaxR>(P, s, tab, A, B, out_tile, scale, Ubuf + P.st[s].uoff,
-                                                           P.first && !P.last, norm_acc, io);
-            }
+            if (okw)
+                dispatch_stage<T, DIR, NT, kBatchMaxR>(P, s, tab, A, B, out_tile, scale, Ubuf + P.st[s].uoff,
+                                                       P.first && !P.last, norm_acc, io);
             if (!checked) {
                 checked = true;
                 if (__syncthreads_or(!okw)) {

@@ -19,6 +19,12 @@
 // call's contents; the execute path clears the status word itself and fully
 // rewrites the partial sums before reading them.  Calls whose kernels overlap
 // on the GPU (different streams, or different host threads) race on the array.
+//
+// Tensor-core tier plans upload their block matrices (device memory they
+// allocate) on their first qft_execute; until that has happened this entry
+// point refuses them (QFT_ERR_UNSUPPORTED) rather than allocate.  A bounded
+// wait that expires writes QFT_ERR_TIMEOUT into the scratch's status word,
+// which qft_noalloc_status reads back.
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -26,10 +32,12 @@
 #include <mutex>
 
 #include "../../include/qftfft.h"
+#include "plan_host.hpp"
 
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = (size_t(32) << 20) + 4096;
+static_assert(qft::kMetaBytes == 4096 && qft::kStatusOff == 8, "scratch layout follows the workspace's");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -65,10 +73,27 @@ extern "C" {
 int qft_execute_noalloc(qft_plan_t plan, void* d_state, double* d_scale_in, int scale_mode, qft_stream_t stream) {
     if (!plan || !d_state) return QFT_ERR_BAD_ARG;
     if (qft_workspace_size(plan) > kNoAllocScratchBytes) return QFT_ERR_SIZE;
+    if (!qft::plan_device_ready(plan)) return QFT_ERR_UNSUPPORTED;  // its first execute would allocate
     void* scratch = nullptr;
     const int rc = scratch_for_current_device(&scratch);
     if (rc != QFT_OK) return rc;
     return qft_execute(plan, d_state, scratch, d_scale_in, scale_mode, stream);
+}
+
+int qft_noalloc_status(qft_stream_t stream) {
+    void* scratch = nullptr;
+    const int rc = scratch_for_current_device(&scratch);
+    if (rc != QFT_OK) return rc;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    int32_t status = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&status, static_cast<const char*>(scratch) + qft::kStatusOff, sizeof(status),
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return QFT_ERR_CUDA;
+    }
+    return status;
 }
 
 }  // extern "C"

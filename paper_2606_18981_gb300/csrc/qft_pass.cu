@@ -17,7 +17,6 @@ cudaError_t launch_batch_f32(int dir, int minb, const BatchItem* items, int nite
 cudaError_t launch_batch_f64(int dir, const BatchItem* items, int nitems, const PassParams* descs, const CUtensorMap* maps, int* counters,
                              int* next, int* status, uint64_t wait_ns, BatchLayout lay, int grid, size_t smem,
                              cudaStream_t stream);
-cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream);  // qft_pair.cu
 
 // minb = 2: complex64 batches whose tiles are <= 2^12 amplitudes and whose
 // blocks have <= 4 wires run two CTAs per SM (one CTA's load overlaps the
@@ -38,7 +37,6 @@ size_t batch_smem_bytes(BatchLayout lay, size_t elem_bytes) {
 }
 
 cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P, int grid, size_t smem, cudaStream_t stream) {
-    if (P.paired) return launch_pass_p(dir, minb, map, P, grid, smem, stream);
     if (dtype == 0) return launch_pass_f32(dir, threads, minb, map, P, grid, smem, stream);
     return launch_pass_f64(dir, threads, map, P, grid, smem, stream);
 }
@@ -47,8 +45,7 @@ cudaError_t launch_pass(int dtype, int dir, int threads, int minb, const CUtenso
 // the group tables (ntw twiddle factors + output offset + tile bits + their
 // swizzled buffer-B offset per entry).
 size_t pass_smem_bytes(const PassParams& P, size_t elem_bytes) {
-    const size_t tw_bytes = P.paired ? 16 : elem_bytes;  // paired passes keep twiddle planes as pairs
-    return 3 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (P.ntw * tw_bytes + 8 + 4 + (P.paired ? 0 : 4));
+    return 3 * (size_t(1) << P.tb) * elem_bytes + size_t(P.ntab) * (P.ntw * elem_bytes + 8 + 4 + 4);
 }
 
 }  // namespace qft

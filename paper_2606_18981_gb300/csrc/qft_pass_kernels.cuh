@@ -36,7 +36,6 @@
 
 #include "plan.hpp"
 #include "qft_device.cuh"
-#include "qft_pair.cuh"
 
 namespace qft {
 

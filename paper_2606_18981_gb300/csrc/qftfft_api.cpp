@@ -43,6 +43,10 @@ int set_cuda_error(cudaError_t e) {
 
 void set_cuda_error_code(int e) { g_last_cuda = e; }
 
+bool plan_device_ready(const qft_plan_s* pl) {
+    return !pl->precision || pl->passes.empty() || pl->passes[0].tc_a_hi != nullptr;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -129,12 +133,9 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
         P.p_out[i] = Lout[tw[i]];
         pos[tw[i]] = i;
     }
-    // Paired complex64 stages need tile bit 0 to be a batch wire (a SIMD lane
-    // that no block of this pass touches); they take blocks of <= 4 wires.
-    const bool paired = pl->pairing && !(first && last) && (tw[0] < glo || tw[0] >= glo + a);
-    P.paired = paired ? 1 : 0;
-    const int pb0 = paired ? 1 : 0;  // group indices skip tile bit 0
-    const int rmax = paired ? std::min(pl->rmax, 4) : pl->rmax;
+    P.paired = 0;
+    const int pb0 = 0;
+    const int rmax = pl->rmax;
     // tile coordinate segments (bit m of the tile coordinate <-> wire nt[m])
     P.nseg = 0;
     for (int m = 0; m < static_cast<int>(nt.size());) {
@@ -234,14 +235,12 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
             for (int w : nt)
                 if (w > top && w < m) S.tile_above = 1;
             for (int e = 0; e < kMaxR; ++e)
-                S.img[e] = e >= r ? 0
-                           : paired ? static_cast<int32_t>(swizzle(1u << (S.q + e - 1), 16))  // 16-byte pair units
-                                    : static_cast<int32_t>(swizzle(1u << (S.q + e), pl->esize));
+                S.img[e] = e >= r ? 0 : static_cast<int32_t>(swizzle(1u << (S.q + e), pl->esize));
             top -= r;
         }
     }
     // Lane order of each stage's group index.
-    const bool unit16 = paired || pl->esize == 16;  // buffer-B access width: 16 bytes (pairs, complex128)
+    const bool unit16 = pl->esize == 16;  // buffer-B access width: 16 bytes (complex128)
     const int SW = unit16 ? 3 : 4;                    // swizzle slot bits
     const int wave_lanes = unit16 ? 3 : 4;            // log2 lanes per SMEM wavefront
     for (int s = 0; s < P.nstages; ++s) {
@@ -274,7 +273,6 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
         S.lo_tw = S.hi_tw = 0;
         for (int i = 0; i < S.ngbits; ++i)
             if (P.p_wire[S.gpos[i]] > hi_w && P.p_wire[S.gpos[i]] < m) (i < 5 ? S.lo_tw : S.hi_tw) = 1;
-        if (paired && P.p_wire[0] > hi_w && P.p_wire[0] < m) S.lo_tw = 1;  // the lane entries carry the pair wire's phase
         if (!S.lo_tw && !S.hi_tw) S.hi_tw = 1;  // keep one (all-ones) factor so tau is defined
     }
     int ntab = 0, nU = 0;
@@ -297,11 +295,11 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
     // system reserves per CTA) and its stages are small enough for 128
     // registers per thread.
     ph.minb = 1;
-    if (pl->dtype == QFT_C64 && pl->threads == 256 && maxr <= (paired ? 3 : 4) &&
+    if (pl->dtype == QFT_C64 && pl->threads == 256 && maxr <= 4 &&
         2 * (ph.smem + 3 * 1024) <= 228 * 1024)
         ph.minb = 2;
     // 512 threads, two CTAs per SM (32 warps, 64 registers per thread): blocks of <= 3 wires
-    if (pl->dtype == QFT_C64 && pl->threads == 512 && !paired && maxr <= 3 && 2 * (ph.smem + 3 * 1024) <= 228 * 1024)
+    if (pl->dtype == QFT_C64 && pl->threads == 512 && maxr <= 3 && 2 * (ph.smem + 3 * 1024) <= 228 * 1024)
         ph.minb = 2;
     const int64_t tiles = P.num_tiles;
     ph.grid = static_cast<int>(std::min<int64_t>(tiles, int64_t(pl->num_sms) * ph.minb));
@@ -951,7 +949,6 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
     pl->cmin = dtype == QFT_C64 ? 4 : 3;  // HBM runs of >= 128 bytes
     pl->rmax = kMaxStageR;
     pl->threads = 256;
-    pl->pairing = false;
     bool rmax_given = false;
     bool fp64 = false;
     if (opts) {
@@ -959,7 +956,7 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
         pl->order = opts->order;
         if (opts->tile_bits == 14 && dtype == QFT_C64) {
             // the wide pass kernel: natural order, complex64, the CUDA-core path, whole-register plans
-            if (opts->order != QFT_ORDER_NATURAL || subset || (opts->precision != QFT_PREC_NATIVE) || opts->paired ||
+            if (opts->order != QFT_ORDER_NATURAL || subset || (opts->precision != QFT_PREC_NATIVE) ||
                 opts->threads || opts->max_stage_bits || opts->coalesce_bits) {
                 delete pl;
                 return QFT_ERR_UNSUPPORTED;
@@ -994,7 +991,9 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
             pl->threads = opts->threads;
             if (pl->threads == 512) pl->rmax = 4;
         }
-        pl->pairing = opts->paired && dtype == QFT_C64 && pl->threads == 256 && !pl->precision && !subset;
+        // packed FP32x2 paired stages measured slower than one group per thread
+        // on GB300 in every shape and were removed; the field stays for the ABI
+        if (opts->paired) { delete pl; return QFT_ERR_UNSUPPORTED; }
         if (opts->pass_split < 0 || opts->pass_split > 2) { delete pl; return QFT_ERR_BAD_ARG; }
         pl->pass_split = opts->pass_split == 1 ? 1 : 0;
         if (opts->max_stage_bits) {
@@ -1022,7 +1021,7 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
     // kernel where the planner finds wide shapes (2^14-amplitude tiles, so
     // ceil(n / 10) passes), else the shapes above.
     if (!shape_given && dtype == QFT_C64 && !pl->precision && !subset && pl->order == QFT_ORDER_NATURAL &&
-        !(opts && opts->paired) && n >= 23)
+        n >= 23)
         pl->wide_tiles = 2;
     // complex64 tiles of <= 2^12 amplitudes fit two CTAs per SM; blocks of <= 4
     // wires keep the kernel within the 128 registers that needs.

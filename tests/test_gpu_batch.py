@@ -43,13 +43,12 @@ def make_batch(count, nmin, nmax, dt, order, seed, direction=q.FORWARD, opts=Non
 
 
 # plan shapes: defaults; 2^12-amplitude tiles (the batch runs two CTAs per SM);
-# 512-thread plans (the batch runs 512-thread CTAs); paired complex64 stages
+# 512-thread plans (the batch runs 512-thread CTAs)
 @pytest.mark.parametrize("dt,order,opts", [("c64", 0, None), ("c64", 1, None), ("c128", 0, None),
                                            ("c128", 1, None), ("c128", 0, {"threads": 512}),
                                            ("c128", 0, {"precision": q.PREC_FP64}),
                                            ("c64", 0, {"tile_bits": 12}), ("c64", 1, {"tile_bits": 12}),
-                                           ("c64", 0, {"threads": 512}), ("c64", 1, {"threads": 512}),
-                                           ("c64", 0, {"paired": 1})])
+                                           ("c64", 0, {"threads": 512}), ("c64", 1, {"threads": 512})])
 def test_batch_matches_single_transforms(oracle_mod, dt, order, opts):
     specs, plans, xs = make_batch(96, 3, 17, dt, order, seed=7, opts=opts)
     states = [x.clone() for x in xs]

@@ -1,8 +1,16 @@
 """Precision tier on the GPU: fused blocks as tcgen05 GEMMs, error vs the FP64 oracle.
 
-Bounds per tier (relative L2 against the oracle, n <= 24): the x3 split tiers
-keep ~22 (FP16) / ~16 (BF16) significant bits per operand, single tiers 11 /
-8 bits; each pass adds one rounding of the data and of the block matrix.
+Relative L2 bounds against the oracle (n <= 24):
+  * FP16x3 (hi + lo FP16 operands, three products, FP32 accumulation): the
+    split-tier target, 1e-6;
+  * BF16x3: reported as is, like plain BF16.  A BF16 hi + lo pair carries
+    16 significant bits (8 + 8), so its operand rounding alone is ~2^-17
+    relative per pass and the transform lands near 7e-6; it cannot meet the
+    1e-6 split target, and the bound here is its own level (2e-5);
+  * single-operand tiers: TF32 and FP16 keep 11 bits, BF16 8 bits.
+Element by element each tier also meets the bound of tests/parity.py with
+its operand format's unit roundoff in place of FP32's (2^-22 FP16x3, 2^-16
+BF16x3, 2^-11 TF32 / FP16, 2^-8 BF16).
 """
 import numpy as np
 import pytest
@@ -14,28 +22,34 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 q = pytest.importorskip("paper_2606_18981_gb300")
 
-BOUND = {q.PREC_FP16X3: 2e-6, q.PREC_BF16X3: 1e-4, q.PREC_TF32: 5e-3, q.PREC_FP16: 5e-3, q.PREC_BF16: 4e-2}
+from parity import elementwise_bound, plan_shape  # noqa: E402
+
+BOUND = {q.PREC_FP16X3: 1e-6, q.PREC_BF16X3: 2e-5, q.PREC_TF32: 5e-3, q.PREC_FP16: 5e-3, q.PREC_BF16: 4e-2}
+EPS = {q.PREC_FP16X3: 2.0 ** -22, q.PREC_BF16X3: 2.0 ** -16, q.PREC_TF32: 2.0 ** -11, q.PREC_FP16: 2.0 ** -11,
+       q.PREC_BF16: 2.0 ** -8}
 
 
-def run(x, n, k, prec, order=0, direction=-1, mode=0):
+def run(x, n, k, prec, order=0, direction=-1, mode=0, shape=False):
     p = q.Plan(n, k, direction, "c64", order, precision=prec)
     st = torch.from_numpy(x).to(torch.complex64).cuda()
     ws = p.alloc_workspace()
     p.execute(st, ws, mode)
     out = st.cpu().numpy().astype(np.complex128)
     assert p.status(ws) == 0
-    return out
+    return (out, plan_shape(p)) if shape else out
 
 
 @pytest.mark.parametrize("prec", [q.PREC_FP16X3, q.PREC_BF16X3, q.PREC_TF32, q.PREC_FP16, q.PREC_BF16])
 @pytest.mark.parametrize("n,k", [(6, -1), (11, -1), (14, 4), (20, -1), (24, 8)])
 def test_tier_error_vs_oracle(oracle_mod, prec, n, k):
     x = qft_inputs.gaussian(n, seed=n).astype(np.complex64).astype(np.complex128)
-    got = run(x, n, k, prec)
+    got, (a_last, natural) = run(x, n, k, prec, shape=True)
     ref, _ = oracle_mod.qft(x, k, -1, 0, True)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    print(f"tier {prec} n={n} k={k}: rel L2 {err:.3e}")
+    ratio = np.max(np.abs(got - ref) / elementwise_bound(ref, "c64", n, a_last, natural, eps=EPS[prec]))
+    print(f"tier {prec} n={n} k={k}: rel L2 {err:.3e}, element ratio {ratio:.3f}")
     assert err <= BOUND[prec]
+    assert ratio <= 1.0
 
 
 @pytest.mark.parametrize("order,direction,mode", [(1, -1, 0), (0, 1, 2), (0, -1, 1)])

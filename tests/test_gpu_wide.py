@@ -30,10 +30,10 @@ def wide_plan(n, k=-1, direction=-1):
 def test_wide_matches_oracle(oracle_mod, n):
     x = as_dt(qft_inputs.gaussian(n, seed=100 + n, normalise=False), "c64")
     for direction in (q.FORWARD, q.INVERSE):
-        got, s = run(x, n, plan=wide_plan(n, -1, direction))
+        got, s, sh = run(x, n, plan=wide_plan(n, -1, direction))
         ref, s_ref = oracle_mod.qft(x, -1, direction, 0, True)
         assert abs(s - s_ref) <= 1e-6 * s_ref
-        assert_close(got, ref, "c64", n)
+        assert_close(got, ref, "c64", n, sh)
 
 
 @pytest.mark.parametrize("n", [17, 20])
@@ -41,9 +41,9 @@ def test_wide_aqft_cutoffs(oracle_mod, n):
     x = as_dt(qft_inputs.tones(n, seed=n), "c64")
     for k in (0, 1, 3, 4, 8, 12):
         for direction in (q.FORWARD, q.INVERSE):
-            got, _ = run(x, n, plan=wide_plan(n, k, direction))
+            got, _, sh = run(x, n, plan=wide_plan(n, k, direction))
             ref, _ = oracle_mod.qft(x, k, direction, 0, True)
-            assert_close(got, ref, "c64", n)
+            assert_close(got, ref, "c64", n, sh)
 
 
 def test_wide_scale_modes_against_numpy_fft():
@@ -54,8 +54,8 @@ def test_wide_scale_modes_against_numpy_fft():
     for direction, mode, ref in [(-1, q.SCALE_UNNORM, F), (-1, q.SCALE_UNITARY, F / np.sqrt(N)),
                                  (+1, q.SCALE_INV_N, G), (+1, q.SCALE_UNNORM, G * N),
                                  (-1, q.SCALE_STATE, F / (np.linalg.norm(x) * np.sqrt(N)))]:
-        got, _ = run(x, n, mode=mode, plan=wide_plan(n, -1, direction))
-        assert_close(got, ref, "c64", n)
+        got, _, sh = run(x, n, mode=mode, plan=wide_plan(n, -1, direction))
+        assert_close(got, ref, "c64", n, sh)
 
 
 @pytest.mark.parametrize("n", [16, 24])
@@ -66,13 +66,13 @@ def test_wide_basis_and_tone_index_maps(n):
     for j in rng.integers(0, N, size=3):
         x = np.zeros(N, dtype=np.complex128)
         x[j] = 1.0
-        got, _ = run(x, n, plan=wide_plan(n))
+        got, _, sh = run(x, n, plan=wide_plan(n))
         y = np.arange(N, dtype=np.float64)
         ref = np.exp(-2j * np.pi * ((int(j) * y) % N) / N) / np.sqrt(N)
-        assert_close(got, ref, "c64", n)
+        assert_close(got, ref, "c64", n, sh)
     for k0 in rng.integers(0, N, size=3):
         x = np.exp(2j * np.pi * ((int(k0) * np.arange(N)) % N) / N)
-        got, _ = run(x, n, plan=wide_plan(n))
+        got, _, sh = run(x, n, plan=wide_plan(n))
         assert int(np.argmax(np.abs(got))) == int(k0)
 
 
@@ -92,7 +92,9 @@ def test_wide_large_round_trip_and_sampled_bins(oracle_mod):
     xh = x0.cpu().numpy().astype(np.complex128)
     ref = oracle_mod.aqft_bins(xh, bins, -1, q.FORWARD)  # <y|U|x>, unitary scaling
     rms = np.linalg.norm(xh) / np.sqrt(N)
-    assert np.max(np.abs(got - ref)) <= 2e-6 * np.sqrt(n) * rms * 8
+    peak = float(state.abs().max().item())
+    bound = 8 * 2.0 ** -24 * n * (np.abs(ref) + rms + peak / np.sqrt(2.0 ** 9))
+    assert np.max(np.abs(got - ref) / bound) <= 1.0
     pi.execute(state, ws, q.SCALE_UNITARY)
     assert pf.status(ws) == 0
     err = (torch.linalg.vector_norm(state - x0) / torch.linalg.vector_norm(x0)).item()

@@ -101,15 +101,15 @@ def test_plan_argument_errors():
 
 
 def test_variant_plans_use_the_intended_kernels():
-    """The planner actually selects two CTAs per SM / paired stages for these options."""
+    """The planner selects two CTAs per SM for 2^12-amplitude complex64 tiles;
+    the removed paired stages are refused."""
     import plan_emulator as pe
     descs = lambda p: [pe.parse(p.describe_pass(i)) for i in range(p.info().passes)]  # noqa: E731
     d = descs(q.Plan(26, -1, q.FORWARD, "c64", 0, tile_bits=12))
-    assert all(P["minb"] == 2 and not P["paired"] for P in d)
-    d = descs(q.Plan(26, -1, q.FORWARD, "c64", 0, paired=1))
-    assert all(P["paired"] for P in d)
-    d = descs(q.Plan(26, -1, q.FORWARD, "c64", 0, tile_bits=12, paired=1, max_stage_bits=3))
-    assert all(P["paired"] and P["minb"] == 2 for P in d)
+    assert all(P["minb"] == 2 and not P["paired"] and not P["wide"] for P in d)
+    with pytest.raises(q.QftError) as e:
+        q.Plan(26, -1, q.FORWARD, "c64", 0, paired=1)
+    assert e.value.code == q.ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("dt", ["c64", "c128"])

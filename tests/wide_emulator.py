@@ -9,8 +9,12 @@ the per-kernel table VB (the thread's other five fixed bits) and the extra
 batch bits' table W -- applies the diagonal and the block circuit to each
 group, exchanges the values to wide_x1(t) | j << 4, runs stage 1 the same
 way and stores through the kernel's offsets out_tile + othr(t) + oj(j).
-Arithmetic is float64, so a mismatch against the oracle means a map or table
-mistake, not rounding.  Test helper only.
+Arithmetic is float64 by default, so a mismatch against the oracle means a
+map or table mistake, not rounding.  With fp32=True every twiddle and every
+intermediate value is rounded to complex64 as in the kernel (the operation
+order differs in detail: no fused multiply-adds), which gives a realistic
+rounding-error profile for checking the parity bounds themselves.  Test
+helper only.
 """
 from __future__ import annotations
 
@@ -30,8 +34,30 @@ def thread_maps(exe: str):
     return {"x0": a[:, 1], "x1": a[:, 2], "x1top": a[:, 3]}
 
 
+_FP32 = False
+
+
 def _phase(beta, n, sign):
-    return np.exp(sign * 2j * np.pi * np.asarray(beta, dtype=np.float64) / float(1 << n))
+    w = np.exp(sign * 2j * np.pi * np.asarray(beta, dtype=np.float64) / float(1 << n))
+    return w.astype(np.complex64) if _FP32 else w
+
+
+def _block_circuit32(v, R, kk, sign):
+    """The block's butterflies and controlled phases in complex64 arithmetic."""
+    v = v.astype(np.complex64)
+    for t in range(R - 1, -1, -1):
+        bit = 1 << t
+        js = [j for j in range(1 << R) if not (j & bit)]
+        a = v[..., js].copy()
+        b = v[..., [j | bit for j in js]].copy()
+        v[..., js] = a + b
+        v[..., [j | bit for j in js]] = a - b
+        lo = max(0, t - kk)
+        mask = (bit - 1) & ~((1 << lo) - 1)
+        for j in range(1 << R):
+            if j & bit:
+                v[..., j] *= np.complex64(np.exp(sign * 2j * np.pi * (j & mask) / (2 * bit)))
+    return v
 
 
 def _cross_beta(I, n, hi, c, kk):
@@ -78,7 +104,7 @@ def _stage(v, P, S, ia, ib, vb_pos, w_pos, I_tile, sign, cross):
                 tau = uv[e] * (Wt[e][js] if js else 1.0)
                 sel = (jb >> e) & 1 == 1
                 g[:, :, sel] *= tau[:, :, None]
-        g = _block_circuit(g, R, kk, sign)
+        g = (_block_circuit32 if _FP32 else _block_circuit)(g, R, kk, sign)
         v[:, :, idx] = g
 
 
@@ -126,18 +152,24 @@ def run_wide_pass(P, src, dst, sign, scale_mode, norm_sq, maps):
               3: inv_root_n * inv_root_n}[scale_mode]
     oaddr = out_tile[:, None, None] + othr[None, :, None] + oj[None, None, :]
     assert oaddr.min() >= 0 and oaddr.max() < dst.size
-    dst[oaddr] = v * (factor if P["last"] else 1.0)
+    if _FP32:
+        dst[oaddr] = (v * np.float32(factor if P["last"] else 1.0)).astype(np.complex64)
+    else:
+        dst[oaddr] = v * (factor if P["last"] else 1.0)
     return oaddr.ravel()
 
 
-def emulate_wide(plan, x, maps, scale_mode=0):
-    """Replay every pass of a plan whose passes are all wide passes."""
+def emulate_wide(plan, x, maps, scale_mode=0, fp32=False):
+    """Replay every pass of a plan whose passes are all wide passes (fp32: in
+    complex64 arithmetic, see the module docstring)."""
+    global _FP32
+    _FP32 = fp32
     info = plan.info()
     N = 1 << info.n_addr
-    state = np.asarray(x, dtype=np.complex128).copy()
-    work = np.zeros(N, dtype=np.complex128)
+    state = np.asarray(x, dtype=np.complex64 if fp32 else np.complex128).copy()
+    work = np.zeros(N, dtype=state.dtype)
     bufs = [state, work]
-    norm_sq = float(np.sum(np.abs(state) ** 2))
+    norm_sq = float(np.sum(np.abs(state.astype(np.complex128)) ** 2))
     for i in range(info.passes):
         P = parse(plan.describe_pass(i))
         assert P["wide"] == 1
@@ -145,4 +177,5 @@ def emulate_wide(plan, x, maps, scale_mode=0):
         src, dst = bufs[P["in_buf"]], bufs[P["out_buf"]]
         written = run_wide_pass(P, src.copy(), dst, plan.direction, scale_mode, norm_sq, maps)
         assert np.array_equal(np.sort(written), np.arange(N)), "output map of a pass must be a bijection"
-    return bufs[0]
+    _FP32 = False
+    return bufs[0].astype(np.complex128)
