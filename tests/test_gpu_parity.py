@@ -223,41 +223,70 @@ def _column_stats(state, n, a_last, natural):
     return peak, col
 
 
-@pytest.mark.parametrize("n,dt", [(30, "c64"), (33, "c64"), (28, "c128")])
-def test_large_sampled_bins(oracle_mod, n, dt):
-    """The benchmark's exact plan (same constructor call as bench.py) at full
-    size: 64 output bins against the oracle's direct O(N) sums of the
-    closed-form matrix elements, each within the element-wise bound at 1x,
-    plus the output norm."""
-    free, _ = torch.cuda.mem_get_info()
-    eb = 8 if dt == "c64" else 16
-    if free < 2.5 * (1 << n) * eb + (4 << 30):
-        pytest.skip("not enough device memory")
-    p = q.Plan(n, -1, q.FORWARD, dt, q.ORDER_NATURAL, tuned=True)
-    a_last, natural = plan_shape(p)
-    x = _bench_like(n, dt, 2024)
-    xh = x.cpu().numpy().astype(np.complex128)
-    state = x
-    ws = p.alloc_workspace()
-    p.execute(state, ws, q.SCALE_UNITARY)
-    assert p.status(ws) == 0
-    rng = np.random.default_rng(n)
-    N = 1 << n
-    ys = np.unique(np.concatenate([[0, 1, 2, N - 1, N >> 1], rng.integers(0, N, size=80)]))[:64]
-    got = state[torch.from_numpy(ys).cuda()].cpu().numpy().astype(np.complex128)
-    ref = oracle_mod.aqft_bins(xh, ys, -1, q.FORWARD)
-    norm = float(np.linalg.norm(xh))
-    rms = norm / np.sqrt(N)
+def _bound_at(ys, ref, state, n, dt, shape, rms):
+    """Element-wise bound (tests/parity.py) at sampled bins, with the output's
+    peak and last-pass column norms taken from the device result."""
+    a_last, natural = shape
     peak, col = _column_stats(state, n, a_last, natural)
     cidx = torch.from_numpy((ys % (1 << (n - a_last))) if natural else (ys >> a_last)).cuda()
     colv = col[cidx].cpu().numpy()
-    bound = 8 * (2.0 ** -24 if dt == "c64" else 2.0 ** -46) * n * (
-        np.abs(ref) + rms + np.maximum(colv, peak) / np.sqrt(2.0 ** a_last))
+    eps = 2.0 ** -24 if dt == "c64" else 2.0 ** -46
+    return 8 * eps * n * (np.abs(ref) + rms + np.maximum(colv, peak) / np.sqrt(2.0 ** a_last))
+
+
+@pytest.mark.parametrize("n,dt", [(30, "c64"), (33, "c64"), (28, "c128")])
+def test_large_sampled_bins(oracle_mod, n, dt):
+    """The benchmark's exact plan (the same constructor call as bench.py) at
+    full size.  Input: 2^16 Gaussian amplitudes at random positions, zero
+    elsewhere, so the oracle's DFT definition summed over the nonzeros gives
+    any output bin exactly and quickly; 64 bins, each within the element-wise
+    bound at 1x, and the output norm."""
+    free, _ = torch.cuda.mem_get_info()
+    eb = 8 if dt == "c64" else 16
+    if free < 2.2 * (1 << n) * eb + (4 << 30):
+        pytest.skip("not enough device memory")
+    N = 1 << n
+    p = q.Plan(n, -1, q.FORWARD, dt, q.ORDER_NATURAL, tuned=True)
+    rng = np.random.default_rng(n)
+    idx = np.unique(rng.integers(0, N, size=1 << 16))
+    vals = rng.standard_normal(idx.size) + 1j * rng.standard_normal(idx.size)
+    state = torch.zeros(N, dtype=tdt(dt), device="cuda")
+    state[torch.from_numpy(idx).cuda()] = torch.from_numpy(vals).to(tdt(dt)).cuda()
+    vals = vals.astype(np.complex64 if dt == "c64" else np.complex128).astype(np.complex128)
+    ws = p.alloc_workspace()
+    p.execute(state, ws, q.SCALE_UNITARY)
+    assert p.status(ws) == 0
+    ys = np.unique(np.concatenate([[0, 1, 2, N - 1, N >> 1, int(idx[0])], rng.integers(0, N, size=80)]))[:64]
+    got = state[torch.from_numpy(ys).cuda()].cpu().numpy().astype(np.complex128)
+    ref = oracle_mod.dft_bins_sparse(idx, vals, n, ys, q.FORWARD) / np.sqrt(N)
+    norm = float(np.linalg.norm(vals))
+    bound = _bound_at(ys, ref, state, n, dt, plan_shape(p), norm / np.sqrt(N))
     ratio = np.abs(got - ref) / bound
     assert ratio.max() <= 1.0, (int(ys[np.argmax(ratio)]), float(ratio.max()))
-    nrm = _chunked_norm(state)
-    assert abs(nrm - norm) <= TOL[dt](n) * norm
-    del state, x, ws
+    assert abs(_chunked_norm(state) - norm) <= TOL[dt](n) * norm
+    del state, ws
+    torch.cuda.empty_cache()
+
+
+def test_large_sampled_bins_bench_input(oracle_mod):
+    """n = 30 complex64 on the benchmark's plan and its own input (seeded
+    Gaussian amplitudes drawn on the device): 8 output bins against the
+    oracle's O(N) direct sums of the closed-form matrix elements, each within
+    the element-wise bound at 1x."""
+    n, dt = 30, "c64"
+    N = 1 << n
+    p = q.Plan(n, -1, q.FORWARD, dt, q.ORDER_NATURAL, tuned=True)
+    x = _bench_like(n, dt, 2024)
+    xh = x.cpu().numpy().astype(np.complex128)
+    ws = p.alloc_workspace()
+    p.execute(x, ws, q.SCALE_UNITARY)
+    assert p.status(ws) == 0
+    ys = np.concatenate([[0, 1, N - 1], np.random.default_rng(30).integers(0, N, size=5)])
+    got = x[torch.from_numpy(ys).cuda()].cpu().numpy().astype(np.complex128)
+    ref = oracle_mod.aqft_bins(xh, ys, -1, q.FORWARD)
+    bound = _bound_at(ys, ref, x, n, dt, plan_shape(p), float(np.linalg.norm(xh)) / np.sqrt(N))
+    assert np.max(np.abs(got - ref) / bound) <= 1.0
+    del x, ws
     torch.cuda.empty_cache()
 
 
