@@ -212,15 +212,22 @@ def _bench_like(n, dt, seed):
     return x
 
 
-def _column_stats(state, n, a_last, natural):
-    """Peak magnitude and per-column norms (last-pass columns) of a device output."""
-    mag2 = (state.real.to(torch.float64) ** 2 + state.imag.to(torch.float64) ** 2)
-    peak = float(mag2.max().sqrt().item())
-    if natural:
-        col = mag2.view(1 << a_last, 1 << (n - a_last)).sum(dim=0).sqrt()
-    else:
-        col = mag2.view(1 << (n - a_last), 1 << a_last).sum(dim=1).sqrt()
-    return peak, col
+def _column_stats(state, n, a_last, natural, chunk=1 << 27):
+    """Peak magnitude and per-column norms (last-pass columns) of a device
+    output, accumulated in chunks of rows so no full-size temporary is made."""
+    rows, cols = (1 << a_last, 1 << (n - a_last)) if natural else (1 << (n - a_last), 1 << a_last)
+    view = state.view(rows, cols)
+    step = max(1, chunk // cols)
+    peak = 0.0
+    col = torch.zeros(cols if natural else rows, dtype=torch.float64, device=state.device)
+    for r in range(0, rows, step):
+        m2 = view[r:r + step].abs().to(torch.float64) ** 2
+        peak = max(peak, float(m2.max().sqrt().item()))
+        if natural:
+            col += m2.sum(dim=0)
+        else:
+            col[r:r + step] = m2.sum(dim=1)
+    return peak, col.sqrt()
 
 
 def _bound_at(ys, ref, state, n, dt, shape, rms):
