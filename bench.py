@@ -158,7 +158,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("qft_pass_kernels.cuh", "qft_device.cuh", "qft_df.cuh", "qft_pair.cuh", "plan.hpp"):
+    for f in ("qft_wide.cuh", "qft_pass_kernels.cuh", "qft_device.cuh", "qft_df.cuh", "plan.hpp"):
         h.update(open(os.path.join(ROOT, "paper_2606_18981_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -234,24 +234,59 @@ def oracle_sample(n, k, reps=1):
     return statistics.median(rates), work, oracle.num_threads(), desc
 
 
+def oracle_full_runs(sizes=(22, 24), k=-1):
+    """The whole oracle transform (encode, gate-by-gate circuit, decode) on a
+    seeded Gaussian input, on one host thread and on all of them, at each size.
+    The paper's own CPU numbers for n = 22 (Sec. 4, FP32, 2x AMD EPYC Zen2) are
+    quoted beside: no-AVX OpenMP 3.86 s on 1 thread, 0.064 s on 64; AVX
+    1.60 s / 0.037 s; FFTW 0.47 s / 0.032 s.  The oracle computes in FP64."""
+    import oracle
+    import qft_inputs
+
+    cores = oracle.num_threads()
+    runs = []
+    try:
+        for n in sizes:
+            x = qft_inputs.gaussian(n, seed=n, normalise=False)
+            for th in (1, cores):
+                oracle.set_num_threads(th)
+                t0 = time.perf_counter()
+                oracle.qft(x, k, oracle.FORWARD, oracle.SCALE_STATE, True)
+                sec = time.perf_counter() - t0
+                runs.append({"n": n, "threads": th, "seconds": sec, "amplitudes_per_s": (1 << n) / sec})
+    finally:
+        oracle.set_num_threads(cores)
+    return {"runs": runs, "precision": "FP64",
+            "paper_n22_context": "Sec. 4, FP32 on 2x AMD EPYC Zen2: no-AVX OpenMP 3.86 s (1 thread) / 0.064 s "
+                                 "(64 threads); AVX 1.60 s / 0.037 s; FFTW 0.47 s / 0.032 s"}
+
+
 def run_reference(args, world, rank):
+    """The reference arm: the CPU FP64 oracle as it stands, on the host cores.
+    Each step runs the bounded sample of oracle_sample on the benchmark's
+    workload (one H sweep, one controlled-phase sweep and the swap sweeps on
+    the full state); ms_per_step is the wall time a step actually took, and
+    value is the sample scaled to a whole transform (amplitudes/s)."""
     if rank != 0:
         return
     import oracle
 
     oracle.build()
     n, k = args.n, args.k
-    rates = []
-    t_all = 0.0
+    rates, walls = [], []
     for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         r, w, cores, desc = oracle_sample(n, k, reps=1)
-        t_all += w
+        wall = time.perf_counter() - t0
         if s >= args.warmup:
             rates.append(r)
+            walls.append(wall)
     val = statistics.median(rates)
     N = 1 << n
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * N / val,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(walls),
+            "ms_per_step_meaning": "wall time of one step's bounded sample (not a whole transform)",
+            "ms_per_transform_extrapolated": 1000.0 * N / val,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(n, args.dtype, k), "n": n,
                                             "parallelism": "host cores (OpenMP)"},
@@ -638,6 +673,44 @@ def timed_transform(q, torch, plan, state, ws, stream, steps, warmup):
     return total / steps, per_pass
 
 
+def plan_is_wide(plan):
+    """True when every pass of the plan runs on the wide pass kernel."""
+    return all(plan.describe_pass(i)[-1] == 1 for i in range(plan.info().passes))
+
+
+def summarize_extra(extra):
+    """One small dict per secondary workload (the detailed records stay in
+    "extra", printed last)."""
+    out = {}
+
+    def pick(d, *keys):
+        return {k: d[k] for k in keys if isinstance(d, dict) and k in d}
+
+    if "c64_n33" in extra:
+        out["largest_c64_n33"] = pick(extra["c64_n33"], "ms_per_step", "amplitudes_per_s", "passes",
+                                      "passes_algorithmic", "hbm_frac_per_launch", "hbm_frac_transform", "error")
+    for key in ("c128_n30", "c128_fp64_n30"):
+        if key in extra:
+            out[key] = pick(extra[key], "ms_per_step", "amplitudes_per_s", "passes", "hbm_frac_per_launch", "error")
+    b = extra.get("batched_4096_n8to18_c64", {})
+    if b:
+        out["batched"] = pick(b, "ms_per_batch", "transforms_per_s", "hbm_frac", "plans",
+                              "speedup_vs_plain_c128_single", "error")
+    t = extra.get("tensor_tier", {})
+    if t:
+        out["tensor_tier"] = {k: pick(v, "rel_l2_vs_fp64_oracle_n24", "ms_n24", "transforms_per_s_256x_n20")
+                              for k, v in t.items() if isinstance(v, dict)}
+        if "error" in t:
+            out["tensor_tier"]["error"] = t["error"]
+    sv = extra.get("serving_poisson", {})
+    if sv:
+        out["serving"] = {k: pick(v, "served_req_per_s", "p50_ms", "p99_ms") for k, v in sv.items()
+                          if isinstance(v, dict)}
+        if "error" in sv:
+            out["serving"]["error"] = sv["error"]
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -758,38 +831,26 @@ def run_ours(args, world, rank, local):
     bytes_per_launch = 2 * N * eb
     mean_launch_ms = statistics.mean(per_pass)
     achieved = bytes_per_launch / (mean_launch_ms / 1000.0) / 1e9
+    wide = plan_is_wide(plan)
+    # the pass count of the scope's cost model: ceil((n + 4 coalescing bits) / 14)
+    # wires per pass for tiles of 2^14 amplitudes (at least 2 for n > 14)
+    p_alg = max(1 if n <= 14 else 2, -(-(n + 4) // 14))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None if prec else ncu_traffic(n, dt), "peak_source": peak_src,
-                "kernel": "qft_tc_fast_kernel" if prec else "qft_pass_kernel", "bytes_per_launch": bytes_per_launch,
-                "launch_ms": per_pass}
+                "kernel": "qft_tc_fast_kernel" if prec else ("qft_wide_kernel" if wide else "qft_pass_kernel"),
+                "bytes_per_launch": bytes_per_launch, "launch_ms": per_pass, "passes": P,
+                "passes_algorithmic": p_alg,
+                "transform_frac": p_alg * bytes_per_launch / (ms / 1000.0) / 1e9 / peak}
 
     extra = {}
+    summary = {}
     if rank == 0 and world == 1 and not args.no_extra:
         del state, ws
         torch.cuda.empty_cache()
-        try:
-            extra["batched_4096_n8to18_c64"] = batched_workload(q, torch, dev, stream)
-        except Exception as ex:
-            extra["batched_4096_n8to18_c64"] = {"error": str(ex)[:300]}
-        try:
-            extra["tensor_tier"] = tensor_tier_workload(q, torch, dev, stream)
-        except Exception as ex:
-            extra["tensor_tier"] = {"error": str(ex)[:300]}
-        try:
-            extra["serving_poisson"] = serving_workload(q, torch, dev)
-        except Exception as ex:
-            extra["serving_poisson"] = {"error": str(ex)[:300]}
-        try:
-            extra["next_rows"] = next_rows_workload(q, torch, dev, peak)
-        except Exception as ex:
-            extra["next_rows"] = {"error": str(ex)[:300]}
-        try:
-            extra["aqft_accuracy_n22_tone"] = aqft_accuracy(q, torch, dev)
-        except Exception as ex:
-            extra["aqft_accuracy_n22_tone"] = {"error": str(ex)[:300]}
-        for name, (nn, ddt, kk, prc) in {"aqft_k4_c64_n30": (30, "c64", 4, 0), "c128_n30": (30, "c128", -1, 0),
+        for name, (nn, ddt, kk, prc) in {"c64_n33": (33, "c64", -1, 0), "c128_n30": (30, "c128", -1, 0),
                                           "c128_fp64_n30": (30, "c128", -1, q.PREC_FP64),
-                                          "c64_n26": (26, "c64", -1, 0), "c64_n33": (33, "c64", -1, 0)}.items():
+                                          "aqft_k4_c64_n30": (30, "c64", 4, 0), "c64_n26": (26, "c64", -1, 0),
+                                          "c64_n28": (28, "c64", -1, 0)}.items():
             try:
                 p2 = q.Plan(nn, kk, q.FORWARD, ddt, q.ORDER_NATURAL, tuned=not prc, precision=prc)
                 free, _ = torch.cuda.mem_get_info()
@@ -801,13 +862,26 @@ def run_ours(args, world, rank, local):
                 ws2 = p2.alloc_workspace(dev)
                 ms2, pp2 = timed_transform(q, torch, p2, st2, ws2, stream, 5, 2)
                 eb2 = 8 if ddt == "c64" else 16
-                extra[name] = {"amplitudes_per_s": (1 << nn) / (ms2 / 1000.0), "ms_per_step": ms2,
-                               "passes": p2.info().passes,
-                               "hbm_frac": (2 * (1 << nn) * eb2 / (statistics.mean(pp2) / 1000.0) / 1e9) / peak}
+                pa2 = max(2, -(-(nn + 4) // 14))
+                extra[name] = {"ms_per_step": ms2, "amplitudes_per_s": (1 << nn) / (ms2 / 1000.0),
+                               "passes": p2.info().passes, "passes_algorithmic": pa2,
+                               "launch_ms": pp2,
+                               "hbm_frac_per_launch": (2 * (1 << nn) * eb2 / (statistics.mean(pp2) / 1000.0) / 1e9) / peak,
+                               "hbm_frac_transform": (pa2 * 2 * (1 << nn) * eb2 / (ms2 / 1000.0) / 1e9) / peak}
                 del st2, ws2
                 torch.cuda.empty_cache()
             except Exception as ex:  # secondary numbers must not sink the headline
                 extra[name] = {"error": str(ex)[:200]}
+        for key, fn in (("batched_4096_n8to18_c64", lambda: batched_workload(q, torch, dev, stream)),
+                        ("tensor_tier", lambda: tensor_tier_workload(q, torch, dev, stream)),
+                        ("serving_poisson", lambda: serving_workload(q, torch, dev)),
+                        ("next_rows", lambda: next_rows_workload(q, torch, dev, peak)),
+                        ("aqft_accuracy_n22_tone", lambda: aqft_accuracy(q, torch, dev))):
+            try:
+                extra[key] = fn()
+            except Exception as ex:
+                extra[key] = {"error": str(ex)[:300]}
+        summary = summarize_extra(extra)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -818,16 +892,9 @@ def run_ours(args, world, rank, local):
             r, w, cores, desc = oracle_sample(n, k, reps=2)
             cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                    "cpu_seconds": w}
-            # the same sample on one host thread (the paper's 1-thread CPU point)
-            try:
-                oracle.set_num_threads(1)
-                r1, w1, _, _ = oracle_sample(min(n, 26), k, reps=1)
-                cpu["value_1_thread"] = r1
-                cpu["sample_1_thread"] = f"the same sweeps at n={min(n, 26)} on one thread"
-                w += w1
-                cpu["cpu_seconds"] = w
-            finally:
-                oracle.set_num_threads(cores)
+            t0 = time.perf_counter()
+            cpu["full_transform"] = oracle_full_runs()
+            cpu["cpu_seconds"] = w + (time.perf_counter() - t0)
         except Exception as ex:
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
 
@@ -845,7 +912,9 @@ def run_ours(args, world, rank, local):
                            "l2": "state (and workspace) larger than L2; no flush needed",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (P + (1 if dt == "c128" and not prec else 0)) * args.steps,
-                "clocks": clocks, "extra": extra}
+                "clocks": clocks}
+        line.update(summary)  # compact secondary results, ahead of the detailed extras
+        line["extra"] = extra
         if rejected is not None:  # the first timed region's numbers, not used
             line["remeasured"] = rejected
         print(json.dumps(line), flush=True)
