@@ -25,11 +25,15 @@
 //   2. stage 0: read T, cross twiddle of the controlled phases from wires
 //      above the block (Eq. 5, exact integer phases), the block's Hadamards
 //      and controlled phases in registers (Sec. 2, Fig. 1 order);
-//   3. barrier: T is consumed, thread 0 issues the next tile's load into T,
-//      so it streams in during everything that follows;
+//   3. as soon as every thread has read its values (a split barrier: warp 0
+//      waits, the others only arrive), thread 0 issues the next tile's load
+//      into T, so it streams in during all the compute that follows;
 //   4. exchange through buffer Z in two rounds (x bit 3, which is warp bit 0
-//      in both thread maps, so a round is whole warps): the round's warps
-//      write their stage-0 results, barrier, read their stage-1 inputs;
+//      in both thread maps, so a round is whole warps): the even warps write
+//      their stage-0 results, sync among themselves, read their stage-1
+//      inputs and go straight on to stage 1, while the odd warps, released by
+//      a named barrier once Z is free, do the same -- one half's exchange
+//      overlaps the other half's arithmetic;
 //   5. stage 1 (cross twiddle + block circuit) and the store straight from
 //      registers through the pass's output address map (the qubit-reversal
 //      layout adapter and, in the last pass, the decode scale).
@@ -101,6 +105,28 @@ __device__ __forceinline__ void tma_prefetch_l2_5d(const CUtensorMap* map, const
                      reinterpret_cast<uint64_t>(map)),
                  "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4])
                  : "memory");
+}
+
+// Named CTA barriers (barrier 0 is __syncthreads): bar.arrive signals without
+// waiting (with release semantics for the thread's earlier shared-memory
+// accesses), bar.sync waits for `count` arrivals.
+__device__ __forceinline__ void bar_sync_n(uint32_t id, uint32_t count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_n(uint32_t id, uint32_t count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+constexpr uint32_t kBarTileRead = 1;  // all threads have read the tile buffer (warp 0 waits)
+constexpr uint32_t kBarEvenWrote = 2; // the even warps' exchange writes are done
+constexpr uint32_t kBarZFree = 3;     // the even warps have read the exchange buffer
+constexpr uint32_t kBarOddWrote = 4;  // the odd warps' exchange writes are done
+
+// Tile visited at schedule position s: s itself, or s bit-reversed over
+// log_tiles bits (so that the tiles in flight at one time differ in the high
+// tile bits, for passes whose output addresses run the other way).
+__device__ __forceinline__ int64_t wide_tile_at(const WideParams& P, int64_t s) {
+    if (!P.tile_rev || P.log_tiles == 0) return s;
+    return static_cast<int64_t>(__brevll(static_cast<uint64_t>(s)) >> (64 - P.log_tiles));
 }
 
 __device__ __forceinline__ void wide_coords(const WideParams& P, int64_t tile, int32_t c[5]) {
@@ -260,8 +286,9 @@ __global__ void __launch_bounds__(kWideThreads, 1)
         W1[w] = phase_turns<float, DIR>(cross_phase(I, P.n, hi1, P.wlo1 + e, P.kk), P.n);
     }
     if (tid == 0) mbar_init(&mbar, 1);
-    int64_t tile = blockIdx.x;
-    wide_tile_twiddles<DIR, R0, R1>(P, tile, UA[0]);
+    const uint32_t warp = tid >> 5;
+    int64_t seq = blockIdx.x;  // schedule position; the tile is wide_tile_at(P, seq)
+    wide_tile_twiddles<DIR, R0, R1>(P, wide_tile_at(P, seq), UA[0]);
     __syncthreads();
 
     // Last pass: scale_in from the first pass's per-CTA partial sums.
@@ -284,28 +311,44 @@ __global__ void __launch_bounds__(kWideThreads, 1)
         }
     }
 
-    if (tid == 0 && !P.test_skip_first_load && tile < P.num_tiles) {
+    auto issue = [&](int64_t s) {  // thread 0: load the tile at schedule position s into T
         int32_t c[5];
-        wide_coords(P, tile, c);
+        wide_coords(P, wide_tile_at(P, s), c);
         mbar_arrive_expect_tx(&mbar, static_cast<uint32_t>(kWideTileBytes));
         tma_load_5d(T, &tmap, c, &mbar);
-        if (P.l2_prefetch && tile + gridDim.x < P.num_tiles) {
-            wide_coords(P, tile + gridDim.x, c);
+        if (P.l2_prefetch && s + gridDim.x < P.num_tiles) {
+            wide_coords(P, wide_tile_at(P, s + gridDim.x), c);
             tma_prefetch_l2_5d(&tmap, c);
         }
-    }
+    };
+    if (tid == 0 && !P.test_skip_first_load && seq < P.num_tiles) issue(seq);
 
     double norm_acc = 0.0;
     uint32_t parity = 0u;
-    bool aborted = false;
-    for (int k = 0; tile < P.num_tiles; tile += gridDim.x, ++k) {
-        const bool ok = mbar_wait_bounded(&mbar, parity, P.wait_limit_ns);
+    bool aborted = false, next_issued = false, ok = true;
+    for (int k = 0; seq < P.num_tiles; seq += gridDim.x, ++k) {
+        const int64_t tile = wide_tile_at(P, seq);
+        ok = mbar_wait_bounded(&mbar, parity, P.wait_limit_ns);
         parity ^= 1u;
         const float2* Ucur = UA[k & 1];
         float2 v[32];
         if (ok) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = T[pT + (uint32_t(j) << 9)];
+        }
+        // T has been read: the next tile streams into it during the rest of this one.
+        next_issued = false;
+        if (warp == 0) {
+            bar_sync_n(kBarTileRead, kWideThreads);
+            if (tid == 0 && ok && seq + gridDim.x < P.num_tiles) {
+                fence_proxy_async_smem();
+                issue(seq + gridDim.x);
+                next_issued = true;
+            }
+        } else {
+            bar_arrive_n(kBarTileRead, kWideThreads);
+        }
+        if (ok) {
             if (P.first) {
                 float2 s0 = make_float2(0.f, 0.f), s1 = s0;
 #pragma unroll
@@ -320,44 +363,24 @@ __global__ void __launch_bounds__(kWideThreads, 1)
             for (int e = 0; e < R0; ++e) uv[e] = cmul(Ucur[e * 16 + ia0], VB[e * 32 + ib0]);
             wide_stage<DIR, R0>(v, uv, W0, cross0, P.kk);
         }
-        // T is consumed: the next tile streams into it during the rest of this one.
+        // every thread is past the previous tile's exchange: Z may be written
         if (__syncthreads_or(!ok)) {
             aborted = true;
-            parity ^= 1u;  // this tile's phase may not have completed: wait on it again below
             break;
         }
-        if (tid == 0) {
-            const int64_t nt = tile + gridDim.x;
-            if (nt < P.num_tiles) {
-                int32_t c[5];
-                wide_coords(P, nt, c);
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&mbar, static_cast<uint32_t>(kWideTileBytes));
-                tma_load_5d(T, &tmap, c, &mbar);
-                if (P.l2_prefetch && nt + gridDim.x < P.num_tiles) {
-                    wide_coords(P, nt + gridDim.x, c);
-                    tma_prefetch_l2_5d(&tmap, c);
-                }
-            }
-        }
-        wide_tile_twiddles<DIR, R0, R1>(P, tile + gridDim.x, UA[(k + 1) & 1]);
-        // exchange, round 0 (warps with x bit 3 = 0) then round 1
-        if (!round1) {
+        wide_tile_twiddles<DIR, R0, R1>(P, wide_tile_at(P, seq + gridDim.x), UA[(k + 1) & 1]);
+        if (!round1) {  // even warps: x bit 3 = 0
 #pragma unroll
             for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
-        }
-        __syncthreads();
-        if (!round1) {
+            bar_sync_n(kBarEvenWrote, kWideThreads / 2);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
-        }
-        __syncthreads();
-        if (round1) {
+            bar_arrive_n(kBarZFree, kWideThreads);
+        } else {  // odd warps: x bit 3 = 1, once the even warps have read Z
+            bar_sync_n(kBarZFree, kWideThreads);
 #pragma unroll
             for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
-        }
-        __syncthreads();
-        if (round1) {
+            bar_sync_n(kBarOddWrote, kWideThreads / 2);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
         }
@@ -384,8 +407,10 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     if (aborted) {
         if (tid == 0) {
             atomicExch(P.status, -5);  // QFT_ERR_TIMEOUT
-            // let an in-flight copy land before the CTA's shared memory is released
-            mbar_wait_bounded(&mbar, parity, P.wait_limit_ns);
+            // let the copy in flight land before the CTA's shared memory is released:
+            // the next tile's if thread 0 issued it, else this tile's
+            if (next_issued) mbar_wait_bounded(&mbar, parity, P.wait_limit_ns);
+            else if (!ok) mbar_wait_bounded(&mbar, parity ^ 1u, P.wait_limit_ns);
         }
         return;
     }
