@@ -232,6 +232,9 @@ template <int DIR, int R0, int R1, bool TOP>
 __global__ void __launch_bounds__(kWideThreads, 1)
     qft_wide_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ WideParams P) {
     constexpr int E0 = 5 - R0, E1 = 5 - R1;
+    // The even and odd warps' exchange rounds overlap each other's arithmetic
+    // in the first pass.
+    constexpr bool kOverlapExchange = TOP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* const T = reinterpret_cast<float2*>(smem_raw);
     float2* const Z = reinterpret_cast<float2*>(smem_raw + kWideTileBytes);
@@ -241,6 +244,7 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     __shared__ __align__(16) float2 W0[(1 << E0) * R0];
     __shared__ __align__(16) float2 W1[(1 << E1) * R1];
     __shared__ double red[kWideThreads / 32];
+    __shared__ int64_t s_othr[kWideThreads];  // each thread's output offset (kept out of registers)
 
     const uint32_t tid = threadIdx.x;
     const uint32_t x0 = wide_x0(tid), x1 = wide_x1(tid, TOP);
@@ -253,9 +257,12 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     // The thread's output offset, and the indices of its fixed bits in the
     // cross-twiddle tables: x0..x3 (UA) and the other five (VB: stage 0
     // x4..x8, stage 1 x9..x13).
-    int64_t othr = 0;
-    for (int b = 0; b < kWideTileBits; ++b)
-        if ((x1 >> b) & 1u) othr += int64_t(1) << P.p_out[b];
+    {
+        int64_t othr = 0;
+        for (int b = 0; b < kWideTileBits; ++b)
+            if ((x1 >> b) & 1u) othr += int64_t(1) << P.p_out[b];
+        s_othr[tid] = othr;
+    }
     const uint32_t ia0 = x0 & 15u, ib0 = (x0 >> 4) & 31u;
     const uint32_t ia1 = x1 & 15u, ib1 = x1 >> 9;
     // VB: entry (i * 32 + b), i as in UA; bits x4 + k (stage 0) or x9 + k (stage 1) = bit k of b
@@ -369,20 +376,47 @@ __global__ void __launch_bounds__(kWideThreads, 1)
             break;
         }
         wide_tile_twiddles<DIR, R0, R1>(P, wide_tile_at(P, seq + gridDim.x), UA[(k + 1) & 1]);
-        if (!round1) {  // even warps: x bit 3 = 0
+        if constexpr (kOverlapExchange) {
+            if (!round1) {  // even warps: x bit 3 = 0
 #pragma unroll
-            for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
-            bar_sync_n(kBarEvenWrote, kWideThreads / 2);
+                for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
+                bar_sync_n(kBarEvenWrote, kWideThreads / 2);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
-            bar_arrive_n(kBarZFree, kWideThreads);
-        } else {  // odd warps: x bit 3 = 1, once the even warps have read Z
-            bar_sync_n(kBarZFree, kWideThreads);
+                for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
+                bar_arrive_n(kBarZFree, kWideThreads);
+            } else {  // odd warps: x bit 3 = 1, once the even warps have read Z
+                bar_sync_n(kBarZFree, kWideThreads);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
-            bar_sync_n(kBarOddWrote, kWideThreads / 2);
+                for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
+                bar_sync_n(kBarOddWrote, kWideThreads / 2);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
+                for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
+            }
+        } else {  // both halves in lock step
+            if (!round1) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
+            }
+            __syncthreads();
+            if (!round1) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
+            }
+            __syncthreads();
+            if (round1) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
+            }
+            __syncthreads();
+            if (round1) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
+            }
+        }
+        if (P.last) {  // the decode scale (stage 1 is linear, so it may come first)
+            const float2 sc = make_float2(scale, scale);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = cmul2(v[j], sc);
         }
         {
             float2 uv[R1];
@@ -393,15 +427,9 @@ __global__ void __launch_bounds__(kWideThreads, 1)
         uint64_t I_tile;
         int64_t out_tile;
         wide_tile_coords(P, tile, I_tile, out_tile);
-        float2* __restrict__ outp = static_cast<float2*>(P.out) + (out_tile + othr);
-        if (P.last) {
-            const float2 sc = make_float2(scale, scale);
+        float2* __restrict__ outp = static_cast<float2*>(P.out) + (out_tile + s_othr[tid]);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) outp[P.oj[j]] = cmul2(v[j], sc);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) outp[P.oj[j]] = v[j];
-        }
+        for (int j = 0; j < 32; ++j) outp[P.oj[j]] = v[j];
     }
 
     if (aborted) {

@@ -495,7 +495,7 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
     // wires outside the tile to the highest addresses), the CTAs visit the
     // tiles in bit-reversed order, so that concurrent tiles write to
     // addresses that differ in low bits and spread over the memory channels.
-    W.tile_rev = (nt.size() >= 2 && Lout[nt.back()] < Lout[nt.front()]) ? 1 : 0;
+    W.tile_rev = 0;
     for (int b = 0; b < 14; ++b) {
         W.p_wire[b] = P.p_wire[b];
         W.p_out[b] = P.p_out[b];

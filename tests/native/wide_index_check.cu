@@ -109,7 +109,7 @@ int main(int argc, char** argv) {
                 cover = cover && wr.size() == 8192 && wr == rd;
             }
         check(cover, "each round: 8192 distinct slots written, exactly those read");
-        check(kWideSmemBytes + 6 * 1024 <= 227 * 1024, "shared memory (dynamic + static) within 227 KiB");
+        check(kWideSmemBytes + 10 * 1024 <= 227 * 1024, "shared memory (dynamic + static) within 227 KiB");
     }
     // 4. bank conflicts, per warp instruction (fixed j)
     {
