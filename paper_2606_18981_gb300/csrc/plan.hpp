@@ -129,8 +129,6 @@ struct WideParams {
     int32_t wlo0, wlo1;   // lowest wire of the stage-0 (top) and stage-1 blocks
     int32_t l2_prefetch;  // 1: also prefetch the tile after next into L2
     int32_t test_skip_first_load;
-    int32_t tile_rev;     // 1: the CTAs visit tiles in bit-reversed order (see the planner)
-    int32_t log_tiles;    // log2(num_tiles)
     int64_t num_tiles;
     int32_t p_wire[14];  // tile bit x -> logical wire
     int32_t p_out[14];   // tile bit x -> output address bit

@@ -25,9 +25,8 @@
 //   2. stage 0: read T, cross twiddle of the controlled phases from wires
 //      above the block (Eq. 5, exact integer phases), the block's Hadamards
 //      and controlled phases in registers (Sec. 2, Fig. 1 order);
-//   3. as soon as every thread has read its values (a split barrier: warp 0
-//      waits, the others only arrive), thread 0 issues the next tile's load
-//      into T, so it streams in during all the compute that follows;
+//   3. barrier: T is consumed, thread 0 issues the next tile's load into T,
+//      so it streams in during the exchange, stage 1 and the stores;
 //   4. exchange through buffer Z in two rounds (x bit 3, which is warp bit 0
 //      in both thread maps, so a round is whole warps): the even warps write
 //      their stage-0 results, sync among themselves, read their stage-1
@@ -116,18 +115,9 @@ __device__ __forceinline__ void bar_sync_n(uint32_t id, uint32_t count) {
 __device__ __forceinline__ void bar_arrive_n(uint32_t id, uint32_t count) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
-constexpr uint32_t kBarTileRead = 1;  // all threads have read the tile buffer (warp 0 waits)
 constexpr uint32_t kBarEvenWrote = 2; // the even warps' exchange writes are done
 constexpr uint32_t kBarZFree = 3;     // the even warps have read the exchange buffer
 constexpr uint32_t kBarOddWrote = 4;  // the odd warps' exchange writes are done
-
-// Tile visited at schedule position s: s itself, or s bit-reversed over
-// log_tiles bits (so that the tiles in flight at one time differ in the high
-// tile bits, for passes whose output addresses run the other way).
-__device__ __forceinline__ int64_t wide_tile_at(const WideParams& P, int64_t s) {
-    if (!P.tile_rev || P.log_tiles == 0) return s;
-    return static_cast<int64_t>(__brevll(static_cast<uint64_t>(s)) >> (64 - P.log_tiles));
-}
 
 __device__ __forceinline__ void wide_coords(const WideParams& P, int64_t tile, int32_t c[5]) {
 #pragma unroll
@@ -232,9 +222,7 @@ template <int DIR, int R0, int R1, bool TOP>
 __global__ void __launch_bounds__(kWideThreads, 1)
     qft_wide_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ WideParams P) {
     constexpr int E0 = 5 - R0, E1 = 5 - R1;
-    // The even and odd warps' exchange rounds overlap each other's arithmetic
-    // in the first pass.
-    constexpr bool kOverlapExchange = TOP;
+
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* const T = reinterpret_cast<float2*>(smem_raw);
     float2* const Z = reinterpret_cast<float2*>(smem_raw + kWideTileBytes);
@@ -293,9 +281,8 @@ __global__ void __launch_bounds__(kWideThreads, 1)
         W1[w] = phase_turns<float, DIR>(cross_phase(I, P.n, hi1, P.wlo1 + e, P.kk), P.n);
     }
     if (tid == 0) mbar_init(&mbar, 1);
-    const uint32_t warp = tid >> 5;
-    int64_t seq = blockIdx.x;  // schedule position; the tile is wide_tile_at(P, seq)
-    wide_tile_twiddles<DIR, R0, R1>(P, wide_tile_at(P, seq), UA[0]);
+    int64_t tile = blockIdx.x;
+    wide_tile_twiddles<DIR, R0, R1>(P, seq, UA[0]);
     __syncthreads();
 
     // Last pass: scale_in from the first pass's per-CTA partial sums.
@@ -318,23 +305,22 @@ __global__ void __launch_bounds__(kWideThreads, 1)
         }
     }
 
-    auto issue = [&](int64_t s) {  // thread 0: load the tile at schedule position s into T
+    auto issue = [&](int64_t s) {  // thread 0: load tile s into T
         int32_t c[5];
-        wide_coords(P, wide_tile_at(P, s), c);
+        wide_coords(P, s, c);
         mbar_arrive_expect_tx(&mbar, static_cast<uint32_t>(kWideTileBytes));
         tma_load_5d(T, &tmap, c, &mbar);
         if (P.l2_prefetch && s + gridDim.x < P.num_tiles) {
-            wide_coords(P, wide_tile_at(P, s + gridDim.x), c);
+            wide_coords(P, s + gridDim.x, c);
             tma_prefetch_l2_5d(&tmap, c);
         }
     };
-    if (tid == 0 && !P.test_skip_first_load && seq < P.num_tiles) issue(seq);
+    if (tid == 0 && !P.test_skip_first_load && tile < P.num_tiles) issue(tile);
 
     double norm_acc = 0.0;
     uint32_t parity = 0u;
-    bool aborted = false, next_issued = false, ok = true;
-    for (int k = 0; seq < P.num_tiles; seq += gridDim.x, ++k) {
-        const int64_t tile = wide_tile_at(P, seq);
+    bool aborted = false, ok = true;
+    for (int k = 0; tile < P.num_tiles; tile += gridDim.x, ++k) {
         ok = mbar_wait_bounded(&mbar, parity, P.wait_limit_ns);
         parity ^= 1u;
         const float2* Ucur = UA[k & 1];
@@ -342,20 +328,6 @@ __global__ void __launch_bounds__(kWideThreads, 1)
         if (ok) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = T[pT + (uint32_t(j) << 9)];
-        }
-        // T has been read: the next tile streams into it during the rest of this one.
-        next_issued = false;
-        if (warp == 0) {
-            bar_sync_n(kBarTileRead, kWideThreads);
-            if (tid == 0 && ok && seq + gridDim.x < P.num_tiles) {
-                fence_proxy_async_smem();
-                issue(seq + gridDim.x);
-                next_issued = true;
-            }
-        } else {
-            bar_arrive_n(kBarTileRead, kWideThreads);
-        }
-        if (ok) {
             if (P.first) {
                 float2 s0 = make_float2(0.f, 0.f), s1 = s0;
 #pragma unroll
@@ -375,43 +347,26 @@ __global__ void __launch_bounds__(kWideThreads, 1)
             aborted = true;
             break;
         }
-        wide_tile_twiddles<DIR, R0, R1>(P, wide_tile_at(P, seq + gridDim.x), UA[(k + 1) & 1]);
-        if constexpr (kOverlapExchange) {
-            if (!round1) {  // even warps: x bit 3 = 0
+        // T has been read: the next tile streams into it during the rest of this one.
+        if (tid == 0 && tile + gridDim.x < P.num_tiles) {
+            fence_proxy_async_smem();
+            issue(tile + gridDim.x);
+        }
+        wide_tile_twiddles<DIR, R0, R1>(P, tile + gridDim.x, UA[(k + 1) & 1]);
+        if (!round1) {  // even warps: x bit 3 = 0
 #pragma unroll
-                for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
-                bar_sync_n(kBarEvenWrote, kWideThreads / 2);
+            for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
+            bar_sync_n(kBarEvenWrote, kWideThreads / 2);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
-                bar_arrive_n(kBarZFree, kWideThreads);
-            } else {  // odd warps: x bit 3 = 1, once the even warps have read Z
-                bar_sync_n(kBarZFree, kWideThreads);
+            for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
+            bar_arrive_n(kBarZFree, kWideThreads);
+        } else {  // odd warps: x bit 3 = 1, once the even warps have read Z
+            bar_sync_n(kBarZFree, kWideThreads);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
-                bar_sync_n(kBarOddWrote, kWideThreads / 2);
+            for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
+            bar_sync_n(kBarOddWrote, kWideThreads / 2);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
-            }
-        } else {  // both halves in lock step
-            if (!round1) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
-            }
-            __syncthreads();
-            if (!round1) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
-            }
-            __syncthreads();
-            if (round1) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
-            }
-            __syncthreads();
-            if (round1) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
-            }
+            for (int j = 0; j < 32; ++j) v[j] = Z[a1 + wide_k1(j)];
         }
         if (P.last) {  // the decode scale (stage 1 is linear, so it may come first)
             const float2 sc = make_float2(scale, scale);
@@ -435,10 +390,9 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     if (aborted) {
         if (tid == 0) {
             atomicExch(P.status, -5);  // QFT_ERR_TIMEOUT
-            // let the copy in flight land before the CTA's shared memory is released:
-            // the next tile's if thread 0 issued it, else this tile's
-            if (next_issued) mbar_wait_bounded(&mbar, parity, P.wait_limit_ns);
-            else if (!ok) mbar_wait_bounded(&mbar, parity ^ 1u, P.wait_limit_ns);
+            // let this tile's copy land before the CTA's shared memory is released
+            // (the next tile's is issued only after the check)
+            if (!ok) mbar_wait_bounded(&mbar, parity ^ 1u, P.wait_limit_ns);
         }
         return;
     }

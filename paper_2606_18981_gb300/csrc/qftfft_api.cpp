@@ -488,14 +488,6 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
     W.wlo1 = glo;
     W.l2_prefetch = pl->l2_prefetch;
     W.num_tiles = P.num_tiles;
-    W.log_tiles = n - 14;
-    // Tiles run in flight together (one per CTA) along the low tile-coordinate
-    // bits.  Where those bits carry high output address bits (the last pass
-    // of a natural-order plan: the bit reversal sends the lowest input
-    // wires outside the tile to the highest addresses), the CTAs visit the
-    // tiles in bit-reversed order, so that concurrent tiles write to
-    // addresses that differ in low bits and spread over the memory channels.
-    W.tile_rev = 0;
     for (int b = 0; b < 14; ++b) {
         W.p_wire[b] = P.p_wire[b];
         W.p_out[b] = P.p_out[b];
