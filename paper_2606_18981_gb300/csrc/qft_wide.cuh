@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     }
     if (tid == 0) mbar_init(&mbar, 1);
     int64_t tile = blockIdx.x;
-    wide_tile_twiddles<DIR, R0, R1>(P, seq, UA[0]);
+    wide_tile_twiddles<DIR, R0, R1>(P, tile, UA[0]);
     __syncthreads();
 
     // Last pass: scale_in from the first pass's per-CTA partial sums.
