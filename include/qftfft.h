@@ -97,8 +97,10 @@ typedef struct {
     int coalesce_bits;  /* min log2(contiguous amplitudes per HBM run); 0 = default         */
     int max_stage_bits; /* max wires per register stage (1..4); 0 = default                */
     int wait_limit_ms;  /* bound of every device-side wait; 0 = default (2000 ms)           */
-    int test_skip_first_load; /* test hook: 1 = never issue the first tile load, so the
-                                 kernel's bounded wait expires and reports QFT_ERR_TIMEOUT  */
+    int test_skip_first_load; /* TEST HOOK, 0 in normal use: 1 = never issue the first
+                                 tile load, so the kernel's bounded wait expires and
+                                 reports QFT_ERR_TIMEOUT (exercises failure reporting
+                                 without a fault; see also the test-hook section)       */
     int threads;        /* CTA size of the pass kernel: 256 (stages <= 5 wires) or 512
                            (stages <= 4 wires); 0 = default                                 */
     int precision;      /* QFT_PREC_*: 0 = the default CUDA-core path (complex64 in FP32;
@@ -159,6 +161,12 @@ typedef struct {
     int n_addr, w0;                  /* array of 2^n_addr amplitudes; the transform acts
                                         on index bits [w0, w0 + n) (qft_plan_create:
                                         n_addr = n, w0 = 0)                            */
+    int fused_blocks;                /* Sec. 3.1's plan (num_qubits, fused_blocks,
+                                        max_fused_size): the fused gate blocks the
+                                        circuit is cut into -- here the register stages
+                                        of all passes, each one block of consecutive
+                                        wires with its Hadamards and controlled phases */
+    int max_fused_size;              /* qubits of the widest fused block               */
 } qft_plan_info;
 
 /* Step 2 (Sec. 3, Fig. 1): build the circuit for n qubits, cutoff k
@@ -311,11 +319,6 @@ int qft_server_reset_stats(qft_server_t server);
  * then reports QFT_ERR_CANCELED (poll / wait).  A request already running or
  * finished cannot be withdrawn: QFT_ERR_STATE. */
 int qft_server_cancel(qft_server_t server, uint64_t ticket);
-/* Test hook: the server's next `count` device allocations fail as if
- * cudaMalloc had failed.  A request that cannot get memory while others are
- * running waits for them; with nothing running it fails with QFT_ERR_NOMEM.
- * Used to check that an allocation failure is reported and leaks nothing. */
-int qft_server_inject_alloc_failures(qft_server_t server, int count);
 /* Finish every queued request, then stop the worker and free the server's memory. */
 int qft_server_destroy(qft_server_t server);
 
@@ -348,7 +351,11 @@ int qft_execute_noalloc(qft_plan_t plan, void* d_state, double* d_scale_in, int 
  * Allocates nothing; a negative QFT_ERR_* on a CUDA failure. */
 int qft_noalloc_status(qft_stream_t stream);
 
-/* Copy the N results from d_state to dst (host if dst_on_device = 0, else device). */
+/* Read-back after Sec. 3 step 4 (the decode scaling, applied by qft_execute's
+ * last pass): copy the N results from d_state to dst (host if dst_on_device =
+ * 0, else device).  Asynchronous on stream; pinned host memory gives an
+ * asynchronous copy.  QFT_ERR_BAD_ARG on null pointers; dst == d_state is a
+ * no-op. */
 int qft_read(qft_plan_t plan, const void* d_state, void* dst, int dst_on_device, qft_stream_t stream);
 
 /* Synchronise stream, then return scale_in recorded in the workspace by the last execute. */
@@ -431,6 +438,16 @@ int qft_qpe_probabilities(const void* d_state, int m, int d_bits, int dtype, dou
  * negative error.  The record order is fixed by this library version and is
  * read by the test-suite's index checks; it is not a stable interface. */
 int qft_plan_describe_pass(qft_plan_t plan, int i, long long* out, int cap);
+
+/* ---------------------------------------------------------------- test hooks
+ * For the test-suite's failure-reporting checks; not for normal use.  (The
+ * other hook is qft_opts.test_skip_first_load.)
+ *
+ * The server's next `count` device allocations fail as if cudaMalloc had
+ * failed.  A request that cannot get memory while others are running waits
+ * for them; with nothing running it fails with QFT_ERR_NOMEM.  Used to check
+ * that an allocation failure is reported and leaks nothing. */
+int qft_server_inject_alloc_failures(qft_server_t server, int count);
 
 /* Error description (static string). */
 const char* qft_strerror(int code);

@@ -51,7 +51,8 @@ class PlanInfo(ctypes.Structure):
                 ("passes", ctypes.c_int), ("wires_per_pass", ctypes.c_int * 8),
                 ("stages_per_pass", ctypes.c_int * 8), ("tile_bits", ctypes.c_int * 8),
                 ("coalesce_bits", ctypes.c_int * 8), ("workspace_bytes", ctypes.c_size_t),
-                ("bytes_per_execute", ctypes.c_longlong), ("n_addr", ctypes.c_int), ("w0", ctypes.c_int)]
+                ("bytes_per_execute", ctypes.c_longlong), ("n_addr", ctypes.c_int), ("w0", ctypes.c_int),
+                ("fused_blocks", ctypes.c_int), ("max_fused_size", ctypes.c_int)]
 
 
 class Opts(ctypes.Structure):

@@ -1101,6 +1101,11 @@ int qft_plan_get_info(qft_plan_t pl, qft_plan_info* info) {
     info->bytes_per_execute = static_cast<long long>(pl->passes.size()) * 2LL * (1LL << pl->n_addr) * static_cast<long long>(pl->esize);
     info->n_addr = pl->n_addr;
     info->w0 = pl->w0;
+    for (const PassHost& ph : pl->passes)
+        for (int s = 0; s < ph.prm.nstages; ++s) {
+            info->fused_blocks += 1;
+            info->max_fused_size = std::max(info->max_fused_size, static_cast<int>(ph.prm.st[s].r));
+        }
     return QFT_OK;
 }
 

@@ -239,3 +239,15 @@ def test_512_thread_plans_match_oracle(oracle_mod, dt, order, n):
     got = emulate(p, x, q.SCALE_UNITARY)
     ref, _ = oracle_mod.qft(x, k=-1, sign=q.FORWARD, mode=q.SCALE_UNITARY, natural_order=(order == q.ORDER_NATURAL))
     assert rel_l2(got, ref) < 1e-12
+
+
+def test_plan_info_fused_blocks():
+    """Sec. 3.1's plan record: the fused blocks (register stages of all passes)
+    cover every wire once, and max_fused_size is the widest block."""
+    for n, dt in ((10, "c64"), (20, "c64"), (30, "c64"), (33, "c64"), (22, "c128"), (30, "c128")):
+        p = q.Plan(n, -1, q.FORWARD, dt)
+        info = p.info()
+        recs = [parse(p.describe_pass(i)) for i in range(info.passes)]
+        rs = [s["r"] for P in recs for s in P["st"]]
+        assert info.fused_blocks == len(rs) == sum(info.stages_per_pass[:info.passes])
+        assert info.max_fused_size == max(rs) and sum(rs) == n
