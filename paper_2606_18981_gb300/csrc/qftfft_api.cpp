@@ -511,8 +511,9 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
 int plan_passes_wide_split(qft_plan_s* pl, const std::vector<int>& a);
 
 // Natural-order complex64 plans on wide passes: P = ceil(n / 10) passes of
-// 7..10 wires each, the layout adapters of plan_passes with the 4 top wires
-// moved to the lowest addresses.
+// 7..10 wires each; the first pass moves the 4 top wires to the lowest
+// addresses (layout L1 below), the middle passes run in place on L1, the
+// last pass writes the bit-reversed order.
 int plan_passes_wide(qft_plan_s* pl) {
     const int n = pl->n;
     if (pl->dtype != QFT_C64 || pl->order != QFT_ORDER_NATURAL || pl->n_addr != n || pl->precision) return QFT_ERR_UNSUPPORTED;
@@ -559,10 +560,14 @@ int plan_passes_wide_split(qft_plan_s* pl, const std::vector<int>& a) {
         brev[w] = n - 1 - w;
         L1[w] = w;
     }
-    for (int e = 0; e < 4; ++e) {
-        L1[n - 1 - e] = e;
-        L1[e] = n - 4 + e;
-    }
+    // Layout between the passes: the 4 top wires reversed at addresses 0..3
+    // (the batch bits of the later passes, already where the bit reversal
+    // puts them), every other wire shifted up by 4.  The first pass then
+    // writes 256-byte runs (its batch wires 0..3 and top wires land on
+    // addresses 0..7), and each later pass's wires sit on consecutive
+    // addresses -- the last pass's tile is one contiguous 128 KiB block.
+    for (int w = 0; w < n - 4; ++w) L1[w] = w + 4;
+    for (int e = 0; e < 4; ++e) L1[n - 1 - e] = e;
     for (int j = 0; j < P; ++j) {
         const bool first = j == 0, last = j == P - 1;
         const std::vector<int>& Lin = first ? ident : L1;
