@@ -421,11 +421,14 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5, variants
     return out
 
 
-def serving_workload(q, torch, dev, rates=(100, 300, 1000, 5000, 20000), per_rate=300, seed=5):
+def serving_workload(q, torch, dev, rates=(100, 1000, 5000, 10000, 20000, 50000), per_rate=400, seed=5,
+                     compare_unbatched_at=5000):
     """The serving configuration: Poisson arrivals at each rate, n with
     P(n) proportional to 1/n over 10..28, dtype uniform in {complex64,
     complex128}, k uniform in {exact, 4, 8, 16}, direction uniform; inputs
-    and outputs resident on the device; HBM admission budget 120 GB."""
+    and outputs resident on the device; HBM admission budget 120 GB.  Small
+    requests (n <= 18) are continuously batched; at one rate the same stream
+    is also served with batching off."""
     import numpy as np
 
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -444,8 +447,13 @@ def serving_workload(q, torch, dev, rates=(100, 300, 1000, 5000, 20000), per_rat
             t = srv.submit(inputs[(int(n), dt)], outputs[(int(n), dt)], int(n), -1, q.FORWARD, dt)
             srv.wait(t)
     res = {}
-    for rate in rates:
+    runs = [(rate, True) for rate in rates]
+    if compare_unbatched_at:
+        runs.append((compare_unbatched_at, False))
+    for rate, batching in runs:
+        srv.set_batching(18 if batching else 0)
         srv.reset_stats()
+        rng = np.random.Generator(np.random.PCG64(seed * 100003 + rate))  # the same requests with and without batching
         gaps = rng.exponential(1.0 / rate, per_rate)
         t0 = time.perf_counter()
         due = t0
@@ -465,9 +473,10 @@ def serving_workload(q, torch, dev, rates=(100, 300, 1000, 5000, 20000), per_rat
             bad += rc != 0
         wall = time.perf_counter() - t0
         st = srv.stats()
-        res[f"{rate}_req_per_s"] = {"offered_req_per_s": rate, "requests": per_rate, "failed": bad,
-                                    "served_req_per_s": per_rate / wall, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-                                    "max_ms": st.max_ms}
+        key = f"{rate}_req_per_s" + ("" if batching else "_unbatched")
+        res[key] = {"offered_req_per_s": rate, "requests": per_rate, "failed": bad,
+                    "served_req_per_s": per_rate / wall, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+                    "max_ms": st.max_ms, "batches": st.batches, "batched_requests": st.batched_requests}
     srv.close()
     del inputs, outputs
     torch.cuda.empty_cache()

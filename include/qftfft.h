@@ -277,15 +277,23 @@ int qft_batch_status(qft_batch_t batch, qft_stream_t stream);
 int qft_batch_destroy(qft_batch_t batch);
 
 /* ---------------------------------------------------------------- serving
- * A request loop for transforms of mixed n, cutoff, direction and dtype
- * (not in the paper; each request runs the circuit of Sec. 3 exactly as
- * qft_execute does).  A worker thread admits requests in arrival order as
- * soon as their device bytes (state + workspace) fit in the HBM budget next
- * to everything in flight and an in-flight slot is free, runs each on the
- * least-loaded of its streams (copy in, execute, copy out), so new requests
- * overlap with running ones, and records each request's latency from submit
- * to completion.  The server allocates and pools its own device buffers and
- * caches one plan per (n, k, direction, dtype, order). */
+ * A continuous-batching request loop for transforms of mixed n, cutoff,
+ * direction and dtype (not in the paper; each request runs the circuit of
+ * Sec. 3).  A worker thread admits requests in arrival order as soon as their
+ * device bytes fit in the HBM budget next to everything in flight and an
+ * in-flight slot is free.  Small requests (n <= the batching limit, 18 by
+ * default, see qft_server_set_batching) join the batch forming for their
+ * (dtype, direction, scale mode), and every pass of the worker launches each
+ * forming batch whose slot is free as one batched persistent launch (the
+ * qft_batch kernel) on a high-priority stream, so requests that arrive while
+ * others run join the next batch as slots and memory free up.  Larger
+ * requests run their own passes (copy in, qft_execute, copy out) on the
+ * least-loaded of the normal-priority streams; the batches are scheduled
+ * between those passes.  Server batches use one fixed kernel shape, so a
+ * request's result is bit for bit the same alone and in any mix.  Each
+ * request's latency is recorded from submit to completion.  The server
+ * allocates and pools its own device buffers and caches one plan per (n, k,
+ * direction, dtype, order). */
 typedef struct {
     int n, k, direction, dtype, order, scale_mode; /* as qft_plan_create / qft_execute        */
     const void* input;                             /* 2^n complex values, host or device     */
@@ -300,6 +308,8 @@ typedef struct {
     size_t bytes_in_use, bytes_pooled;
     double p50_ms, p99_ms, max_ms;                 /* submit-to-completion latency           */
     double requests_per_s;                         /* completed / (last completion - first submit) */
+    long long batches;                             /* batched launches since the last reset       */
+    long long batched_requests;                    /* requests those launches carried              */
 } qft_server_stats;
 
 /* Start a server on the current device.  hbm_budget_bytes bounds the device
@@ -319,6 +329,9 @@ int qft_server_reset_stats(qft_server_t server);
  * then reports QFT_ERR_CANCELED (poll / wait).  A request already running or
  * finished cannot be withdrawn: QFT_ERR_STATE. */
 int qft_server_cancel(qft_server_t server, uint64_t ticket);
+/* Requests with n <= max_n (0 <= max_n <= 34; 0 = none) are batched; the
+ * default is 18.  Requests already admitted keep their path. */
+int qft_server_set_batching(qft_server_t server, int max_n);
 /* Finish every queued request, then stop the worker and free the server's memory. */
 int qft_server_destroy(qft_server_t server);
 

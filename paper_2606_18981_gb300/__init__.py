@@ -115,7 +115,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("pending", ctypes.c_longlong),
                 ("in_flight", ctypes.c_longlong), ("bytes_in_use", ctypes.c_size_t), ("bytes_pooled", ctypes.c_size_t),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("requests_per_s", ctypes.c_double)]
+                ("requests_per_s", ctypes.c_double), ("batches", ctypes.c_longlong),
+                ("batched_requests", ctypes.c_longlong)]
 
 
 _lib.qft_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int]
@@ -127,6 +128,7 @@ _lib.qft_server_reset_stats.argtypes = [_vp]
 _lib.qft_server_destroy.argtypes = [_vp]
 _lib.qft_server_cancel.argtypes = [_vp, ctypes.c_uint64]
 _lib.qft_server_inject_alloc_failures.argtypes = [_vp, ctypes.c_int]
+_lib.qft_server_set_batching.argtypes = [_vp, ctypes.c_int]
 
 lib = _lib  # the raw ctypes handle (tests call the C ABI through it)
 
@@ -399,6 +401,10 @@ class Server:
     def cancel(self, ticket: int) -> int:
         """Withdraw a request not yet admitted (0); QFT_ERR_STATE if it already runs or ran."""
         return _lib.qft_server_cancel(self._h, ctypes.c_uint64(ticket))
+
+    def set_batching(self, max_n: int) -> None:
+        """Batch requests with n <= max_n (0: none; default 18)."""
+        _check(_lib.qft_server_set_batching(self._h, int(max_n)), "qft_server_set_batching")
 
     def inject_alloc_failures(self, count: int) -> None:
         """Test hook: the next `count` device allocations of the server fail."""

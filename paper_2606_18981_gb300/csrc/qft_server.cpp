@@ -1,17 +1,26 @@
 // qft_server.cpp -- a continuous-batching request loop for transforms of mixed
 // sizes, cutoffs, directions and dtypes.
 //
-// A worker thread owns a set of CUDA streams, a plan cache keyed by
-// (n, k, direction, dtype, order), and a pool of device buffers.  Requests are
-// admitted in arrival order as soon as (a) the bytes they need on the device
-// (state + workspace) fit in the HBM budget together with everything in
-// flight and (b) an in-flight slot is free; each admitted request is enqueued
-// on the least-loaded stream as copy-in, qft_execute, copy-out and an event,
-// so requests that arrive while others run overlap with them on the device.
-// Completion is detected by polling the events; the buffers go back to the
-// pool and the request's latency (submit to completion) is recorded.  Every
-// request runs the same plan and kernels it would run alone, so its result is
-// the one qft_execute gives for it.
+// A worker thread owns CUDA streams, a plan cache keyed by (n, k, direction,
+// dtype, order), a pool of device buffers and a few batch slots (device
+// tables of a batched launch, allocated once).  Requests are admitted in
+// arrival order as soon as the device bytes they need fit in the HBM budget
+// together with everything in flight and an in-flight slot is free.
+//   * Small requests (n <= the batching limit, 18 by default) join the batch
+//     that is forming for their (dtype, direction, scale mode); on every pass
+//     of the worker loop each forming batch whose slot is free is launched as
+//     one persistent batched launch (the a9 kernel) on a high-priority stream:
+//     copy-ins, the batch, copy-outs, one read-back of the scale_in values and
+//     the status word, an event.  Requests that arrive while batches run are
+//     admitted into the next ones as slots and memory free up.
+//   * Larger requests run their own passes (copy-in, qft_execute, copy-out) on
+//     the least-loaded of the normal-priority streams; the high-priority
+//     batches are scheduled between those passes.
+// Completion is detected by polling events; buffers go back to the pool and
+// each request's latency (submit to completion) is recorded.  Server batches
+// use one fixed kernel shape (one 256-thread CTA per SM), and a transform's
+// arithmetic in a batch does not depend on the other transforms in it, so a
+// request's result is bit for bit the same alone and in any mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +38,7 @@
 #include <vector>
 
 #include "../../include/qftfft.h"
+#include "batch_host.hpp"
 #include "plan_host.hpp"
 
 namespace {
@@ -51,6 +61,7 @@ struct InFlight {
     cudaEvent_t done = nullptr;
     double* h_slot = nullptr;  // pinned 16-byte slot: scale_in (double) then the status word (int)
     int slot = 0;
+    size_t reserve = 0;  // batched requests: their share of the batch workspace, held in the budget
 };
 
 struct Result {
@@ -58,6 +69,20 @@ struct Result {
     double latency_ms = 0.0;
     double scale_in = 0.0;
 };
+
+// A batched launch of admitted small requests.
+struct Slot {
+    qft::BatchSlot S;
+    bool busy = false;
+    cudaEvent_t done = nullptr;
+    std::vector<InFlight> reqs;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    double* h_scale = nullptr;  // pinned: scale_in per transform, then the status word
+};
+
+constexpr int kSlotTransforms = 512;      // requests per batched launch, at most
+constexpr size_t kSlotItems = size_t(1) << 16;  // tile items per batched launch, at most
 
 }  // namespace
 
@@ -82,6 +107,13 @@ struct qft_server_s {
     double* slots = nullptr;  // pinned host memory, two doubles per in-flight slot
     std::vector<int> free_slots;
     int fail_allocs = 0;      // test hook: allocations still to fail
+    // continuous batching
+    int batch_max_n = 18;     // requests with n <= this run in batched launches (0: never)
+    cudaStream_t batch_stream = nullptr;
+    std::vector<Slot> bslots;
+    std::map<std::tuple<int, int, int>, std::vector<InFlight>> forming;  // (dtype, direction, scale mode)
+    long long forming_count = 0, batched_count = 0;  // admitted-not-launched, launched-not-finished
+    long long batches_launched = 0, batched_requests = 0;
 };
 
 namespace {
@@ -155,6 +187,75 @@ void finish(qft_server_s* s, const Request& rq, int status, double scale_in) {
     }
 }
 
+bool batchable(const qft_server_s* s, qft_plan_t p) {
+    return s->batch_max_n > 0 && p->n <= s->batch_max_n && !p->precision && p->threads != 512 && p->n_addr == p->n &&
+           !s->bslots.empty();
+}
+
+size_t state_bytes(qft_plan_t p) { return ((size_t(1) << p->n) * p->esize + 255) / 256 * 256; }
+
+// Launch the oldest requests of one forming batch into a free slot; returns
+// QFT_OK (launched), QFT_ERR_NOMEM (no workspace memory now: retry later) or
+// an error for the requests taken.
+int launch_batch_slot(qft_server_s* s, Slot& slot, std::vector<InFlight>& group, int scale_mode) {
+    const size_t take = std::min(group.size(), static_cast<size_t>(kSlotTransforms));
+    std::vector<qft_plan_t> plans(take);
+    std::vector<void*> states(take);
+    size_t items = 0;
+    size_t cnt = 0;
+    for (; cnt < take; ++cnt) {
+        qft_plan_t p = group[cnt].plan;
+        size_t it = 0;
+        for (const auto& ph : p->passes) it += static_cast<size_t>(ph.prm.num_tiles);
+        if (items + it > kSlotItems) break;
+        items += it;
+        plans[cnt] = p;
+        states[cnt] = group[cnt].state;
+    }
+    plans.resize(cnt);
+    states.resize(cnt);
+    const int count = static_cast<int>(cnt);
+    const size_t wsb = qft::batch_workspace_bytes(plans.data(), count);  // held in the budget since admission
+    size_t got = 0;
+    void* ws = pool_get(s, wsb, &got);
+    if (!ws) return QFT_ERR_NOMEM;
+    qft::BatchTables T;
+    int rc = qft::batch_build(plans.data(), states.data(), count, ws, got, slot.S.d_scale, scale_mode, true, T);
+    cudaStream_t st = s->batch_stream;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < count && rc == QFT_OK && e == cudaSuccess; ++i) {
+        const qft_request& r = group[i].req.r;
+        e = cudaMemcpyAsync(states[i], r.input, (size_t(1) << r.n) * plans[i]->esize,
+                            r.input_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    }
+    if (rc == QFT_OK && e == cudaSuccess) rc = qft::slot_run(slot.S, T, st);
+    for (int i = 0; i < count && rc == QFT_OK && e == cudaSuccess; ++i) {
+        const qft_request& r = group[i].req.r;
+        e = cudaMemcpyAsync(r.output, states[i], (size_t(1) << r.n) * plans[i]->esize,
+                            r.output_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    }
+    if (rc == QFT_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(slot.h_scale, slot.S.d_scale, sizeof(double) * count, cudaMemcpyDeviceToHost, st);
+    if (rc == QFT_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(slot.h_scale + kSlotTransforms, slot.S.D.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (rc == QFT_OK && e == cudaSuccess) e = cudaEventRecord(slot.done, st);
+    if (rc == QFT_OK && e != cudaSuccess) rc = qft::set_cuda_error(e);
+    if (rc != QFT_OK) {
+        pool_put(s, ws, got);
+        return rc == QFT_ERR_NOMEM ? QFT_ERR_CUDA : rc;
+    }
+    slot.busy = true;
+    slot.ws = ws;
+    slot.ws_bytes = got;
+    slot.reqs.assign(group.begin(), group.begin() + count);
+    group.erase(group.begin(), group.begin() + count);
+    s->forming_count -= count;
+    s->batched_count += count;
+    s->batches_launched += 1;
+    s->batched_requests += count;
+    return QFT_OK;
+}
+
 // Issue one admitted request; returns false if it could not be issued.
 int issue(qft_server_s* s, InFlight& f) {
     const qft_request& r = f.req.r;
@@ -172,6 +273,13 @@ int issue(qft_server_s* s, InFlight& f) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(f.h_slot, f.ws, 16, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaEventRecord(f.done, st);
     return e == cudaSuccess ? QFT_OK : qft::set_cuda_error(e);
+}
+
+void fail_request(qft_server_s* s, InFlight& f, int rc) {
+    finish(s, f.req, rc, 0.0);
+    pool_put(s, f.state, f.bytes);
+    s->in_use -= f.bytes + f.reserve;
+    s->cv_done.notify_all();
 }
 
 void worker_loop(qft_server_s* s) {
@@ -202,14 +310,46 @@ void worker_loop(qft_server_s* s) {
             s->inflight.pop_back();
             s->cv_done.notify_all();
         }
+        // ... and finished batches
+        for (Slot& slot : s->bslots) {
+            if (!slot.busy) continue;
+            const cudaError_t q = cudaEventQuery(slot.done);
+            if (q == cudaErrorNotReady) continue;
+            int rc = QFT_OK;
+            if (q != cudaSuccess) rc = qft::set_cuda_error(q);
+            else {
+                int32_t dev_status;
+                std::memcpy(&dev_status, slot.h_scale + kSlotTransforms, sizeof(dev_status));
+                if (dev_status != 0) rc = dev_status;
+            }
+            for (size_t i = 0; i < slot.reqs.size(); ++i) {
+                InFlight& f = slot.reqs[i];
+                const double scale_in = slot.h_scale[i];
+                finish(s, f.req, rc, scale_in);
+                if (rc == QFT_OK && f.req.r.scale_in_out) *f.req.r.scale_in_out = scale_in;
+                pool_put(s, f.state, f.bytes);
+                s->in_use -= f.bytes + f.reserve;
+            }
+            s->batched_count -= static_cast<long long>(slot.reqs.size());
+            slot.reqs.clear();
+            pool_put(s, slot.ws, slot.ws_bytes);
+            slot.ws = nullptr;
+            slot.busy = false;
+            s->cv_done.notify_all();
+        }
         // 2. admit in arrival order while budget and slots allow
-        while (!s->pending.empty() && static_cast<int>(s->inflight.size()) < s->max_inflight) {
+        auto active = [&]() {
+            return static_cast<long long>(s->inflight.size()) + s->forming_count + s->batched_count;
+        };
+        while (!s->pending.empty() && active() < s->max_inflight) {
             Request& rq = s->pending.front();
             qft_plan_t p = get_plan(s, rq.r);
             if (!p) { finish(s, rq, QFT_ERR_BAD_ARG, 0.0); s->pending.pop_front(); s->cv_done.notify_all(); continue; }
-            const size_t bytes = request_bytes(p);
-            if (bytes > s->budget) { finish(s, rq, QFT_ERR_BUDGET, 0.0); s->pending.pop_front(); s->cv_done.notify_all(); continue; }
-            if (s->in_use + bytes > s->budget) break;  // wait for memory to free up (keeps arrival order)
+            const bool small = batchable(s, p);
+            const size_t bytes = small ? state_bytes(p) : request_bytes(p);
+            const size_t reserve = small ? qft::batch_transform_workspace_bytes(p) + 256 : 0;
+            if (bytes + reserve > s->budget) { finish(s, rq, QFT_ERR_BUDGET, 0.0); s->pending.pop_front(); s->cv_done.notify_all(); continue; }
+            if (s->in_use + bytes + reserve > s->budget) break;  // wait for memory to free up (keeps arrival order)
             InFlight f;
             f.req = rq;
             f.plan = p;
@@ -217,34 +357,71 @@ void worker_loop(qft_server_s* s) {
             if (!f.state) {
                 // no memory: wait for running requests to free some; with
                 // nothing running no progress is possible, so report it
-                if (!s->inflight.empty()) break;
+                if (active() > 0) break;
                 finish(s, rq, QFT_ERR_NOMEM, 0.0);
                 s->pending.pop_front();
                 s->cv_done.notify_all();
                 continue;
             }
-            f.ws = static_cast<char*>(f.state) + ((size_t(1) << p->n) * p->esize + 255) / 256 * 256;
+            s->pending.pop_front();
+            f.reserve = reserve;
+            s->in_use += f.bytes + reserve;
+            if (small) {
+                s->forming[std::make_tuple(p->dtype, p->dir, f.req.r.scale_mode)].push_back(f);
+                s->forming_count += 1;
+                continue;
+            }
+            f.ws = static_cast<char*>(f.state) + state_bytes(p);
             f.stream = static_cast<int>(std::min_element(s->stream_load.begin(), s->stream_load.end()) - s->stream_load.begin());
             f.slot = s->free_slots.back();
             s->free_slots.pop_back();
             f.h_slot = s->slots + 2 * f.slot;
             cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
             const int rc = issue(s, f);
-            s->pending.pop_front();
             if (rc != QFT_OK) {
-                finish(s, f.req, rc, 0.0);
-                pool_put(s, f.state, f.bytes);
                 s->free_slots.push_back(f.slot);
                 cudaEventDestroy(f.done);
-                s->cv_done.notify_all();
+                fail_request(s, f, rc);
                 continue;
             }
-            s->in_use += f.bytes;
             s->stream_load[f.stream]++;
             s->inflight.push_back(f);
         }
-        if (s->stop && s->pending.empty() && s->inflight.empty()) break;
-        if (s->inflight.empty()) {
+        // 3. launch forming batches into free slots, oldest group first
+        while (s->forming_count > 0) {
+            Slot* slot = nullptr;
+            for (Slot& sl : s->bslots)
+                if (!sl.busy) { slot = &sl; break; }
+            if (!slot) break;
+            auto oldest = s->forming.end();
+            for (auto it = s->forming.begin(); it != s->forming.end(); ++it)
+                if (!it->second.empty() &&
+                    (oldest == s->forming.end() || it->second.front().req.t_submit < oldest->second.front().req.t_submit))
+                    oldest = it;
+            if (oldest == s->forming.end()) break;
+            const int rc = launch_batch_slot(s, *slot, oldest->second, std::get<2>(oldest->first));
+            if (rc == QFT_ERR_NOMEM) {
+                // no workspace memory now: retry on the next pass while others run; with
+                // nothing running no progress is possible, so the group fails
+                bool running = !s->inflight.empty();
+                for (const Slot& sl : s->bslots) running = running || sl.busy;
+                if (running) break;
+                for (InFlight& f : oldest->second) fail_request(s, f, QFT_ERR_NOMEM);
+                s->forming_count -= static_cast<long long>(oldest->second.size());
+                oldest->second.clear();
+                continue;
+            }
+            if (rc != QFT_OK) {              // the oldest request of the group fails; the rest retry
+                InFlight f = oldest->second.front();
+                oldest->second.erase(oldest->second.begin());
+                s->forming_count -= 1;
+                fail_request(s, f, rc);
+            }
+        }
+        bool busy_slots = false;
+        for (const Slot& sl : s->bslots) busy_slots = busy_slots || sl.busy;
+        if (s->stop && s->pending.empty() && s->inflight.empty() && s->forming_count == 0 && !busy_slots) break;
+        if (s->inflight.empty() && !busy_slots && s->forming_count == 0) {
             s->cv_work.wait_for(lock, std::chrono::milliseconds(2));
         } else {
             lock.unlock();
@@ -285,6 +462,24 @@ int qft_server_create(qft_server_t* out, size_t hbm_budget_bytes, int streams, i
         return QFT_ERR_NOMEM;
     }
     for (int i = s->max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
+    // continuous batching: a high-priority stream and three batch slots
+    {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        bool ok = cudaStreamCreateWithPriority(&s->batch_stream, cudaStreamNonBlocking, greatest) == cudaSuccess;
+        for (int i = 0; i < 3 && ok; ++i) {
+            Slot sl;
+            ok = qft::slot_create(sl.S, kSlotTransforms, kSlotItems) == QFT_OK &&
+                 cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaMallocHost(&sl.h_scale, sizeof(double) * (kSlotTransforms + 1)) == cudaSuccess;
+            if (ok) s->bslots.push_back(sl);
+            else {
+                qft::slot_destroy(sl.S);
+                if (sl.done) cudaEventDestroy(sl.done);
+            }
+        }
+        if (!ok) cudaGetLastError();  // batching unavailable: every request runs on its own
+    }
     s->worker = std::thread(worker_loop, s);
     *out = s;
     return QFT_OK;
@@ -353,6 +548,13 @@ int qft_server_cancel(qft_server_t s, uint64_t ticket) {
     return QFT_ERR_STATE;
 }
 
+int qft_server_set_batching(qft_server_t s, int max_n) {
+    if (!s || max_n < 0 || max_n > 34) return QFT_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->batch_max_n = max_n;
+    return QFT_OK;
+}
+
 int qft_server_inject_alloc_failures(qft_server_t s, int count) {
     if (!s || count < 0) return QFT_ERR_BAD_ARG;
     std::lock_guard<std::mutex> lock(s->mu);
@@ -370,6 +572,8 @@ int qft_server_get_stats(qft_server_t s, qft_server_stats* out) {
     out->in_flight = static_cast<long long>(s->inflight.size());
     out->bytes_in_use = s->in_use;
     out->bytes_pooled = s->pooled;
+    out->batches = s->batches_launched;
+    out->batched_requests = s->batched_requests;
     if (!s->latencies.empty()) {
         std::vector<double> v = s->latencies;
         auto pct = [&](double p) {
@@ -392,6 +596,8 @@ int qft_server_reset_stats(qft_server_t s) {
     s->latencies.clear();
     s->completed = 0;
     s->failed = 0;
+    s->batches_launched = 0;
+    s->batched_requests = 0;
     return QFT_OK;
 }
 
@@ -406,6 +612,12 @@ int qft_server_destroy(qft_server_t s) {
     for (auto& kv : s->pool) cudaFree(kv.second);
     for (auto& kv : s->plans) qft_plan_destroy(kv.second);
     for (auto st : s->streams) cudaStreamDestroy(st);
+    for (Slot& sl : s->bslots) {
+        qft::slot_destroy(sl.S);
+        cudaEventDestroy(sl.done);
+        cudaFreeHost(sl.h_scale);
+    }
+    if (s->batch_stream) cudaStreamDestroy(s->batch_stream);
     cudaFreeHost(s->slots);
     delete s;
     return QFT_OK;

@@ -28,11 +28,10 @@ def alone(x, n, k, direction, dt, order, mode):
     return st, p.scale_in(ws)
 
 
-def test_results_alone_equal_results_in_the_mix():
-    rng = np.random.default_rng(5)
-    srv = q.Server(8 << 30, streams=6, max_inflight=24)
-    reqs = []
-    for i in range(60):
+def _mixed_requests(count=60, seed=5):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
         n = int(rng.integers(6, 23))
         k = int(rng.choice([-1, 4, 8, 16]))
         direction = int(rng.choice([-1, 1]))
@@ -41,20 +40,69 @@ def test_results_alone_equal_results_in_the_mix():
         mode = int(rng.integers(0, 4))
         td = torch.complex64 if dt == "c64" else torch.complex128
         x = torch.from_numpy(qft_inputs.make(qft_inputs.KINDS[i % 3], n, 77 + i)).to(td)
-        on_dev = i % 2 == 0
+        out.append((x, n, k, direction, dt, order, mode, i % 2 == 0))
+    return out
+
+
+def _serve(srv, reqs, one_at_a_time):
+    results = []
+    pending = []
+    for x, n, k, direction, dt, order, mode, on_dev in reqs:
+        td = x.dtype
         xin = x.cuda() if on_dev else x.pin_memory()
         out = torch.empty(1 << n, dtype=td, device="cuda") if on_dev else torch.empty(1 << n, dtype=td).pin_memory()
         t = srv.submit(xin, out, n, k, direction, dt, order, mode)
-        reqs.append((t, x, out, n, k, direction, dt, order, mode))
-    for t, x, out, n, k, direction, dt, order, mode in reqs:
+        pending.append((t, out))
+        if one_at_a_time:
+            rc, lat, scale = srv.wait(t, 60000)
+            assert rc == 0 and lat > 0
+            results.append((out.cpu(), scale))
+            pending.clear()
+    for t, out in pending:
         rc, lat, scale = srv.wait(t, 60000)
         assert rc == 0 and lat > 0
-        ref, s_ref = alone(x, n, k, direction, dt, order, mode)
-        assert rel(out.cuda(), ref) <= TOL[dt](n)
-        assert abs(scale - s_ref) <= 1e-9 * max(s_ref, 1e-300)
+        results.append((out.cpu(), scale))
+    return results
+
+
+def test_results_alone_equal_results_in_the_mix():
+    """Every request's result is bit for bit the same when it is served alone
+    (one request at a time) and in a mix of 60 requests of different sizes,
+    cutoffs, directions, dtypes, orders and scale modes (served concurrently:
+    the small ones in batched launches, the large ones on their own), and it
+    equals qft_execute on the same plan within the parity tolerance."""
+    reqs = _mixed_requests()
+    srv = q.Server(8 << 30, streams=6, max_inflight=24)
+    alone_res = _serve(srv, reqs, one_at_a_time=True)
+    srv.reset_stats()
+    mix_res = _serve(srv, reqs, one_at_a_time=False)
     st = srv.stats()
     assert st.completed == 60 and st.failed == 0 and st.p99_ms >= st.p50_ms > 0
     assert st.bytes_in_use == 0
+    for (a, sa), (b, sb), (x, n, k, direction, dt, order, mode, _) in zip(alone_res, mix_res, reqs):
+        assert torch.equal(a, b), (n, k, direction, dt, order, mode)
+        assert sa == sb
+        ref, s_ref = alone(x, n, k, direction, dt, order, mode)
+        assert rel(b.cuda(), ref) <= TOL[dt](n)
+        assert abs(sb - s_ref) <= 1e-9 * max(s_ref, 1e-300)
+    srv.close()
+
+
+def test_small_requests_share_batched_launches():
+    """Requests of n <= 18 submitted together run in batched launches that
+    carry several requests each; with batching off none are batched; the
+    results are the same either way."""
+    reqs = [r for r in _mixed_requests(80, seed=9) if r[1] <= 18]
+    srv = q.Server(8 << 30, streams=4, max_inflight=64)
+    res = _serve(srv, reqs, one_at_a_time=False)
+    st = srv.stats()
+    assert st.batched_requests == len(reqs) and 0 < st.batches < len(reqs)
+    srv.set_batching(0)
+    srv.reset_stats()
+    res_single = _serve(srv, reqs, one_at_a_time=False)
+    assert srv.stats().batches == 0
+    for (a, _), (b, _), (x, n, k, direction, dt, order, mode, _) in zip(res, res_single, reqs):
+        assert rel(a.cuda(), b.cuda()) <= TOL[dt](n)
     srv.close()
 
 
