@@ -371,50 +371,61 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5, variants
         torch.cuda.synchronize()
         status = batch.status(stream)
         ms = a.elapsed_time(bb) / reps
+        info = batch.info()
+        shape = {"kernel_launches": info.kernel_launches, "wide_groups": info.wide_groups,
+                 "wide_transforms": info.wide_transforms, "persistent_items": info.persistent_items,
+                 "side_streams": info.side_streams}
         del batch, states, pool, g
         torch.cuda.empty_cache()
-        return ms, status, plans
+        return ms, status, plans, shape
 
-    # plan shapes: the default tiles (one CTA per SM) and 2^12-amplitude tiles
-    # (two CTAs per SM, so one CTA's tile load overlaps the other's stages) and
-    # 2^13 tiles in 512-thread CTAs (blocks of <= 4 wires, 16 warps per SM)
+    # plan shapes: the default (n = 14..18 on the 2^14-tile pass kernel in
+    # groups, the rest in the persistent launch on 2^13 tiles), and, all in the
+    # persistent launch, 2^12-amplitude tiles (two CTAs per SM, so one CTA's
+    # tile load overlaps the other's stages) and 2^13 tiles in 512-thread CTAs
+    # (blocks of <= 4 wires, 16 warps per SM)
     if variants is None:
-        variants = {"tile13_default": {}, "tile12_two_ctas": {"tile_bits": 12},
+        variants = {"default_wide_groups": {}, "tile12_two_ctas": {"tile_bits": 12},
                     "tile13_512_threads": {"tile_bits": 13, "threads": 512}}
     timed = {name: time_batch(opts) for name, opts in variants.items()}
     best = min(timed, key=lambda k: timed[k][0])
-    ms, status, plans = timed[best]
+    ms, status, plans, shape = timed[best]
     a = torch.cuda.Event(enable_timing=True)
     bb = torch.cuda.Event(enable_timing=True)
     # algorithmic HBM bytes: every pass of every transform reads and writes its state once
     byts = sum(plans[(n, k)].info().passes * 2 * (1 << n) * 8 for n, k, _ in specs)
     peak, _ = load_peaks()
     out = {"transforms": count, "amplitudes": amps, "ms_per_batch": ms, "transforms_per_s": count / (ms / 1e3),
-           "amplitudes_per_s": amps / (ms / 1e3), "status": status, "launches_per_batch": 1,
+           "amplitudes_per_s": amps / (ms / 1e3), "status": status,
+           "launches_per_batch": shape["kernel_launches"], "batch_shape": shape,
            "graph": True, "plans": best, "pass_bytes": byts,
            "hbm_frac": byts / (ms / 1e3) / 1e9 / peak,
            "ms_per_batch_by_plans": {name: t[0] for name, t in timed.items()}}
     if not baselines:
         return out
-    # the plain single-transform complex128 paths on the same transforms: the
-    # default double-float kernel and IEEE FP64
+    # the plain single-transform paths on the same transforms: complex64 (the
+    # batch's own arithmetic and accuracy) and, for reference, complex128 in
+    # the default double-float kernel and in IEEE FP64
     buf = torch.empty(1 << 18, dtype=torch.complex128, device=dev)
     sub = specs[:1024]
-    for label, prec in (("plain_c128_single", 0), ("plain_c128_fp64_single", q.PREC_FP64)):
-        p128 = {key: q.Plan(key[0], key[1], q.FORWARD, "c128", q.ORDER_NATURAL, tuned=not prec, precision=prec)
+    for label, dt, prec in (("plain_c64_single", "c64", 0), ("plain_c128_single", "c128", 0),
+                            ("plain_c128_fp64_single", "c128", q.PREC_FP64)):
+        p128 = {key: q.Plan(key[0], key[1], q.FORWARD, dt, q.ORDER_NATURAL, tuned=not prec, precision=prec)
                 for key in plans}
         ws = {key: p.alloc_workspace(dev) for key, p in p128.items()}
+        bview = buf if dt == "c128" else buf.view(torch.complex64)
         for n, k, _ in sub[:16]:
-            p128[(n, k)].execute(buf[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
+            p128[(n, k)].execute(bview[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
         torch.cuda.synchronize()
         a.record(stream)
         for n, k, _ in sub:
-            p128[(n, k)].execute(buf[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
+            p128[(n, k)].execute(bview[:1 << n], ws[(n, k)], q.SCALE_STATE, stream=stream)
         bb.record(stream)
         torch.cuda.synchronize()
         ms128 = a.elapsed_time(bb)
         out[label] = {"transforms": len(sub), "ms": ms128, "transforms_per_s": len(sub) / (ms128 / 1e3)}
         del p128, ws
+    out["speedup_vs_plain_c64_single"] = out["transforms_per_s"] / out["plain_c64_single"]["transforms_per_s"]
     out["speedup_vs_plain_c128_single"] = out["transforms_per_s"] / out["plain_c128_single"]["transforms_per_s"]
     out["speedup_vs_plain_c128_fp64_single"] = (out["transforms_per_s"] /
                                                 out["plain_c128_fp64_single"]["transforms_per_s"])
@@ -703,8 +714,8 @@ def summarize_extra(extra):
             out[key] = pick(extra[key], "ms_per_step", "amplitudes_per_s", "passes", "hbm_frac_per_launch", "error")
     b = extra.get("batched_4096_n8to18_c64", {})
     if b:
-        out["batched"] = pick(b, "ms_per_batch", "transforms_per_s", "hbm_frac", "plans",
-                              "speedup_vs_plain_c128_single", "error")
+        out["batched"] = pick(b, "ms_per_batch", "transforms_per_s", "hbm_frac", "plans", "launches_per_batch",
+                              "speedup_vs_plain_c64_single", "speedup_vs_plain_c128_single", "error")
     t = extra.get("tensor_tier", {})
     if t:
         out["tensor_tier"] = {k: pick(v, "rel_l2_vs_fp64_oracle_n24", "ms_n24", "transforms_per_s_256x_n20")
@@ -947,7 +958,7 @@ def main():
         dev = torch.device("cuda", local)
         torch.cuda.set_device(dev)
         out = batched_workload(q, torch, dev, torch.cuda.Stream(device=dev), reps=args.steps,
-                               variants={"tile13_default": {}}, baselines=False)
+                               variants={"default_wide_groups": {}}, baselines=False)
         print(json.dumps(out))
         return
     run_ours(args, world, rank, local)

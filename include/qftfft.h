@@ -246,12 +246,16 @@ int qft_execute_pass(qft_plan_t plan, int pass, void* d_state, void* d_workspace
                      int scale_mode, qft_stream_t stream);
 
 /* ---------------------------------------------------------------- batches
- * Many transforms of different sizes and cutoffs in one persistent launch.
- * (Batching is not in the paper, which times one transform at a time; it is
- * the same circuit per transform.)  All plans of a batch must share dtype and
+ * Many transforms of different sizes and cutoffs in one call.  (Batching is
+ * not in the paper, which times one transform at a time; it is the same
+ * circuit per transform.)  All plans of a batch must share dtype and
  * direction.  Each transform's result, scale handling and accuracy are those
- * of qft_execute with the same plan.  Plans of the tensor-core precision tier
- * (qft_opts.precision != 0) are not batched: QFT_ERR_UNSUPPORTED. */
+ * of qft_execute with the same plan, within the parity bounds of its
+ * arithmetic (a transform may run on another pass shape than its plan's, see
+ * qft_batch_execute).  Plans of the tensor-core precision tier
+ * (qft_opts.precision != 0) are not batched: QFT_ERR_UNSUPPORTED; nor are
+ * plans on 2^14-amplitude tiles (qft_opts.tile_bits = 14, and the default
+ * complex64 natural-order plans from n = 23) outside 14 <= n <= 20. */
 typedef struct qft_batch_s* qft_batch_t;
 
 /* Bytes of caller-owned device workspace a batch of these plans needs
@@ -268,9 +272,26 @@ size_t qft_batch_workspace_size(const qft_plan_t* plans, int count);
 int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_states, int count, void* d_workspace,
                      size_t workspace_bytes, double* d_scale_in, int scale_mode);
 
-/* Run every transform of the batch in place: two memsets and one kernel launch
- * on stream (capturable into a CUDA graph).  Asynchronous. */
+/* Run every transform of the batch in place, asynchronously, on stream
+ * (capturable into a CUDA graph).  Complex64 natural-order transforms of
+ * 14 <= n <= 20 qubits whose plans leave the tile shape to the planner (or ask
+ * for tile_bits = 14) run on the 2^14-amplitude-tile pass kernel: one launch
+ * per pass for all transforms of one (n, k, direction), on the batch's side
+ * streams, which wait for stream and which stream then waits for.  The rest
+ * run in one persistent launch over a work list on stream itself.  Before
+ * either, one memset clears the counters and the status word. */
 int qft_batch_execute(qft_batch_t batch, qft_stream_t stream);
+
+/* How a batch runs (qft_batch_execute). */
+typedef struct {
+    int transforms;        /* count given to qft_batch_create                        */
+    int wide_groups;       /* (n, k, direction) groups on the 2^14-tile pass kernel   */
+    int wide_transforms;   /* transforms in those groups                            */
+    int persistent_items;  /* tile items of the persistent launch (0: no launch)      */
+    int kernel_launches;   /* kernels one qft_batch_execute launches                 */
+    int side_streams;      /* streams the groups run on                              */
+} qft_batch_info;
+int qft_batch_get_info(qft_batch_t batch, qft_batch_info* info);
 
 /* Synchronise stream and read the batch's device status word (0 or QFT_ERR_TIMEOUT). */
 int qft_batch_status(qft_batch_t batch, qft_stream_t stream);

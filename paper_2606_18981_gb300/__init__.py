@@ -103,6 +103,14 @@ _lib.qft_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctyp
                                   ctypes.c_size_t, _vp, ctypes.c_int]
 _lib.qft_batch_execute.argtypes = [_vp, _vp]
 _lib.qft_batch_status.argtypes = [_vp, _vp]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("transforms", ctypes.c_int), ("wide_groups", ctypes.c_int), ("wide_transforms", ctypes.c_int),
+                ("persistent_items", ctypes.c_int), ("kernel_launches", ctypes.c_int), ("side_streams", ctypes.c_int)]
+
+
+_lib.qft_batch_get_info.argtypes = [_vp, ctypes.POINTER(BatchInfo)]
 _lib.qft_batch_destroy.argtypes = [_vp]
 
 class Request(ctypes.Structure):
@@ -333,7 +341,7 @@ class RealPlan:
 
 
 class Batch:
-    """Many transforms (plans[i] on device tensors states[i]) run by one persistent launch."""
+    """Many transforms (plans[i] on device tensors states[i]) in one call: wide groups plus one persistent launch."""
 
     def __init__(self, plans, states, scale_mode: int = SCALE_STATE, scale_out=None, device="cuda"):
         import torch
@@ -357,6 +365,11 @@ class Batch:
 
     def status(self, stream=None) -> int:
         return _lib.qft_batch_status(self._h, _stream_handle(stream))
+
+    def info(self) -> BatchInfo:
+        out = BatchInfo()
+        _check(_lib.qft_batch_get_info(self._h, ctypes.byref(out)), "qft_batch_get_info")
+        return out
 
     def __del__(self):
         h = getattr(self, "_h", None)

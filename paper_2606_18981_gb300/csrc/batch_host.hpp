@@ -27,6 +27,7 @@ struct BatchTables {
     std::vector<const void*> df_states;
     std::vector<uint64_t> df_n16;
     std::vector<int*> df_outs;
+    std::vector<size_t> meta_off, work_off;  // per transform: its meta and ping-pong buffer in the workspace
 };
 
 // Device copies of the tables the kernels read.  counters[0] is the work-queue
@@ -50,15 +51,19 @@ size_t batch_transform_workspace_bytes(const qft_plan_s* pl);
 // per-transform workspace inside d_workspace, scale_in into d_scale_in[i]
 // (optional).  fixed_shape: run one 256-thread CTA per SM whatever the plans,
 // so that a transform's result does not depend on which others share the
-// batch (plans that need 512 threads give QFT_ERR_UNSUPPORTED).
+// batch (plans that need 512 threads give QFT_ERR_UNSUPPORTED).  exclude
+// (optional, one flag per transform): transforms that get their workspace
+// share but no work items (they run in wide groups, below).
 int batch_build(const qft_plan_t* plans, void* const* d_states, int count, void* d_workspace, size_t workspace_bytes,
-                double* d_scale_in, int scale_mode, bool fixed_shape, BatchTables& T);
+                double* d_scale_in, int scale_mode, bool fixed_shape, BatchTables& T,
+                const std::vector<char>* exclude = nullptr);
 
 // Point every descriptor's status word at counters + 1 (before the upload).
 void batch_set_status(BatchTables& T, int* d_counters);
 
-// Zero the counters and launch (with the double-float pre-pass first) on st.
-cudaError_t batch_launch(const BatchTables& T, const BatchDevice& D, cudaStream_t st);
+// Zero the counters (unless zero = false: the caller did) and launch (with
+// the double-float pre-pass first) on st.
+cudaError_t batch_launch(const BatchTables& T, const BatchDevice& D, cudaStream_t st, bool zero = true);
 
 // Device tables allocated once for batches up to a capacity, with pinned
 // staging of the same layout: slot_run copies a batch's tables into the

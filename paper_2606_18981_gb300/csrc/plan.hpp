@@ -123,6 +123,12 @@ struct BatchItem {
 // Launch parameters of one pass of the wide kernel (qft_wide.cuh: complex64,
 // 2^14-amplitude tiles, two register stages); built by the planner, buffers
 // filled per execute.
+// Group mode of the wide pass kernel: the last pass keeps the decode scales of
+// at most this many tiles per CTA, so a launch has at most this many tiles per SM.
+constexpr int kWideGroupTilesPerCta = 512;
+// ... and its transforms take at most this many distinct cutoffs k.
+constexpr int kWideGroupMaxK = 4;
+
 struct WideParams {
     int32_t n, kk;
     int32_t first, last, scale_mode;
@@ -144,6 +150,18 @@ struct WideParams {
     double* user_scale;
     int32_t* status;
     uint64_t wait_limit_ns;
+    // Group mode (the kernel's GROUP instantiations): one launch runs this pass
+    // for G transforms of the same plan; tile s is local tile s & (2^lt_bits - 1)
+    // of transform s >> lt_bits (num_tiles = G << lt_bits, lt_bits <= 6).
+    int32_t lt_bits;
+    const void* maps;         // per transform: the pass's input CUtensorMap (device, 64-byte aligned)
+    void* const* outs;        // per transform: the pass's output base (device)
+    double* tpart;            // per tile: the first pass's squared-norm sum, read by the last pass
+    double* const* gscale;    // per transform: where the last pass stores scale_in (entries may be null)
+    // the transforms' cutoffs: transforms [gk_end[i-1], gk_end[i]) have k_eff = gk_val[i] (i < gk_n)
+    int32_t gk_n;
+    int32_t gk_end[kWideGroupMaxK];
+    int32_t gk_val[kWideGroupMaxK];
 };
 
 }  // namespace qft

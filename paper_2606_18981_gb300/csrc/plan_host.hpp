@@ -19,6 +19,8 @@ cudaError_t launch_pass_p(int dir, int minb, const CUtensorMap& map, const PassP
                           cudaStream_t stream);
 cudaError_t launch_pass_wide(int dir, int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
                              cudaStream_t stream);
+cudaError_t launch_pass_wide_group(int dir, int r0, int r1, int top, const WideParams& P, int grid,
+                                   cudaStream_t stream);
 constexpr size_t kWideSmem = 215032;  // dynamic shared memory of the wide kernel (checked in qft_wide_fwd.cu)
 cudaError_t launch_pass_df(int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
                            cudaStream_t stream);
@@ -87,6 +89,7 @@ struct qft_plan_s {
     int pass_split = 0;    // qft_opts.pass_split
     int wide_tiles = 0;    // complex64 natural order on the wide pass kernel (2^14-amplitude tiles)
     int l2_prefetch = 0;   // wide passes: also prefetch the tile after next into L2
+    bool shape_given = false;  // the caller fixed the tile shape (tile_bits, coalesce_bits, threads, max_stage_bits)
     uint64_t wait_limit_ns = 2000000000ull;
     int test_skip_first_load = 0;
     int num_sms = 148;

@@ -11,12 +11,22 @@
 // transform's passes).  These tables live in device memory owned by the
 // batch object.  qft_batch_execute is then two memsets and one kernel launch
 // on the caller's stream, so it can be captured into a CUDA graph.
+//
+// Wide groups: complex64 natural-order transforms of 14 <= n <= 20 qubits
+// (default-shape or wide plans) run instead on the wide pass kernel in group
+// mode (qft_wide.cuh), one launch per pass for all transforms of one (n, k,
+// direction), on side streams forked from the caller's stream and joined back
+// to it, beside the persistent launch over the rest.  Their passes carry
+// 2^14-amplitude tiles in one CTA per SM, where the persistent kernel carries
+// 2^13 in a CTA that also claims, waits and loads.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/qftfft.h"
@@ -38,9 +48,31 @@ cudaError_t launch_df_maxexp_list(const void* const* d_states, const uint64_t* d
 
 using namespace qft;
 
+// One wide group: the transforms of one (n, k, direction) on the wide pass
+// kernel in group mode.
+struct WideGroup {
+    qft_plan_t plan = nullptr;    // its wide plan (owned by the batch)
+    std::vector<int> members;     // transform indices
+    std::vector<WideParams> wp;   // per pass, device pointers filled in
+    std::vector<int> grid;        // per pass
+    int side = 0;                 // side stream index
+};
+
 struct qft_batch_s {
     BatchTables T;
     BatchDevice D;  // device tables owned by the batch object
+    std::vector<WideGroup> wide;
+    void* d_wide = nullptr;  // the groups' tensor maps, output pointers, scale pointers and tile sums
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    ~qft_batch_s() {
+        for (auto& g : wide) qft_plan_destroy(g.plan);
+        cudaFree(d_wide);
+        for (auto st : side) cudaStreamDestroy(st);
+        for (auto ev : join) cudaEventDestroy(ev);
+        if (fork) cudaEventDestroy(fork);
+    }
 };
 
 namespace {
@@ -87,7 +119,7 @@ size_t batch_workspace_bytes(const qft_plan_t* plans, int count) {
 }
 
 int batch_build(const qft_plan_t* plans, void* const* d_states, int count, void* d_workspace, size_t workspace_bytes,
-                double* d_scale_in, int scale_mode, bool fixed_shape, BatchTables& T) {
+                double* d_scale_in, int scale_mode, bool fixed_shape, BatchTables& T, const std::vector<char>* exclude) {
     if (!plans || !d_states || count <= 0 || !d_workspace) return QFT_ERR_BAD_ARG;
     if (scale_mode < QFT_SCALE_STATE || scale_mode > QFT_SCALE_INV_N) return QFT_ERR_BAD_ARG;
     if (reinterpret_cast<uintptr_t>(d_workspace) & (kAlign - 1)) return QFT_ERR_BAD_ARG;
@@ -97,8 +129,9 @@ int batch_build(const qft_plan_t* plans, void* const* d_states, int count, void*
         if (plans[i]->precision) return QFT_ERR_UNSUPPORTED;  // tensor-core tier plans run only through qft_execute
         if (plans[i]->n_addr != plans[i]->n) return QFT_ERR_UNSUPPORTED;  // subset plans run only through qft_execute
         if (plans[i]->df != plans[0]->df) return QFT_ERR_UNSUPPORTED;       // one arithmetic per batch
+        if (exclude && (*exclude)[i]) continue;  // run elsewhere (the wide groups of qft_batch_create)
         for (const auto& ph : plans[i]->passes)
-            if (ph.wide) return QFT_ERR_UNSUPPORTED;  // wide-tile passes run only through qft_execute
+            if (ph.wide) return QFT_ERR_UNSUPPORTED;  // wide-tile passes run here only in wide groups
     }
     if (workspace_bytes < batch_workspace_bytes(plans, count)) return QFT_ERR_SIZE;
     auto fn = get_encode_fn();
@@ -122,23 +155,33 @@ int batch_build(const qft_plan_t* plans, void* const* d_states, int count, void*
     std::vector<CUtensorMap>& maps = T.maps;
     std::vector<const qft_plan_s*> shapes;
     char* ws = static_cast<char*>(d_workspace);
-    size_t off = kAlign;
+    // per-transform workspace (meta, then the ping-pong buffer), in index order
+    T.meta_off.assign(count, 0);
+    T.work_off.assign(count, 0);
+    {
+        size_t off = kAlign;
+        for (int i = 0; i < count; ++i) {
+            T.meta_off[i] = off;
+            off += meta_bytes(plans[i]);
+            T.work_off[i] = off;
+            off += work_bytes(plans[i]);
+        }
+    }
     int ncounters = 2;  // queue head, status
     for (int oi = 0; oi < count; ++oi) {
         const int i = order[oi];
+        if (exclude && (*exclude)[i]) continue;
         qft_plan_s* pl = plans[i];
         int shape = static_cast<int>(std::find(shapes.begin(), shapes.end(), pl) - shapes.begin());
         if (shape == static_cast<int>(shapes.size())) shapes.push_back(pl);
-        char* meta = ws + off;
-        off += meta_bytes(pl);
+        char* meta = ws + T.meta_off[i];
         if (T.df) {
             T.df_states.push_back(d_states[i]);
             T.df_n16.push_back(uint64_t(1) << pl->n);  // one 16-byte load per complex128 amplitude
             T.df_outs.push_back(reinterpret_cast<int*>(meta + kMaxExpOff));
             T.df_max_n16 = std::max<uint64_t>(T.df_max_n16, uint64_t(1) << pl->n);
         }
-        char* work = ws + off;
-        off += work_bytes(pl);
+        char* work = ws + T.work_off[i];
         const int P = static_cast<int>(pl->passes.size());
         int prev_ctr = -1;
         int64_t prev_tiles = 0;
@@ -231,11 +274,16 @@ int batch_build(const qft_plan_t* plans, void* const* d_states, int count, void*
     {
         constexpr size_t kBlockGrids = 4;
         const size_t block_items = kBlockGrids * static_cast<size_t>(plans[0]->num_sms) * T.minb;
-        std::vector<std::vector<size_t>> sizes(count);
-        for (int t = 0; t < count; ++t)
-            for (const auto& g : groups[t]) sizes[t].push_back(g.size());
+        std::vector<std::vector<size_t>> sizes;
+        std::vector<int> which;  // the transforms (in sorted order) with items here
+        for (int t = 0; t < count; ++t) {
+            if (groups[t].empty()) continue;
+            which.push_back(t);
+            sizes.emplace_back();
+            for (const auto& g : groups[t]) sizes.back().push_back(g.size());
+        }
         for (const auto& tj : wavefront_order(sizes, block_items)) {
-            const auto& g = groups[tj.first][tj.second];
+            const auto& g = groups[which[tj.first]][tj.second];
             items.insert(items.end(), g.begin(), g.end());
         }
     }
@@ -251,8 +299,8 @@ void batch_set_status(BatchTables& T, int* d_counters) {
     for (auto& d : T.descs) d.status = d_counters + 1;
 }
 
-cudaError_t batch_launch(const BatchTables& T, const BatchDevice& D, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(D.counters, 0, sizeof(int) * T.ncounters, st);
+cudaError_t batch_launch(const BatchTables& T, const BatchDevice& D, cudaStream_t st, bool zero) {
+    cudaError_t e = zero ? cudaMemsetAsync(D.counters, 0, sizeof(int) * T.ncounters, st) : cudaSuccess;
     if (e != cudaSuccess) return e;
     // counter indices in the items start at 2: [0] queue head, [1] status word
     if (T.df) {
@@ -345,6 +393,210 @@ int slot_run(BatchSlot& S, BatchTables& T, cudaStream_t st) {
 
 }  // namespace qft
 
+// ------------------------------------------------------------ wide groups
+
+namespace {
+
+constexpr int kWideGroupMinN = 14, kWideGroupMaxN = 20;  // the group kernel sums <= 64 tile norms per transform
+constexpr int kMaxSide = 4;                              // side streams of a batch
+
+// Complex64 natural-order whole-register plans of 14..20 qubits that leave
+// the shape to the planner or ask for 2^14-amplitude tiles (the test hook
+// test_skip_first_load stays with the persistent launch unless the plan asked
+// for those tiles).
+bool wide_group_eligible(const qft_plan_s* pl) {
+    return pl->dtype == QFT_C64 && !pl->df && !pl->precision && pl->order == QFT_ORDER_NATURAL &&
+           pl->n_addr == pl->n && pl->w0 == 0 && pl->n >= kWideGroupMinN && pl->n <= kWideGroupMaxN &&
+           (!pl->shape_given || pl->wide_tiles == 1) && (!pl->test_skip_first_load || pl->wide_tiles == 1);
+}
+
+// Form the groups: one wide plan per (n, direction) among the eligible
+// transforms (the cutoff k is per transform in group mode; the pass shapes do
+// not depend on it); members of a group whose wide plan could not be built
+// stay on the persistent launch.  A group holds at most kWideGroupTilesPerCta
+// tiles per SM (the group kernel keeps that many decode scales per CTA) and
+// kWideGroupMaxK distinct cutoffs; more transforms of one key open another
+// group.  exclude[i] = 1 for the grouped transforms.
+int wide_groups_form(const qft_plan_t* plans, int count, std::vector<WideGroup>& groups, std::vector<char>& exclude) {
+    exclude.assign(count, 0);
+    std::vector<std::pair<std::tuple<int, int, int>, int>> keys;  // (n, dir, test hook) -> open group
+    for (int i = 0; i < count; ++i) {
+        const qft_plan_s* pl = plans[i];
+        if (!pl || !wide_group_eligible(pl)) continue;
+        const auto key = std::make_tuple(pl->n, pl->dir, pl->test_skip_first_load);
+        auto it = std::find_if(keys.begin(), keys.end(), [&](const auto& kv) { return kv.first == key; });
+        const size_t cap = (static_cast<size_t>(kWideGroupTilesPerCta) * pl->num_sms) >> (pl->n - 14);
+        if (it != keys.end() && it->second >= 0) {
+            const WideGroup& og = groups[it->second];
+            std::vector<int> ks;
+            for (int m : og.members)
+                if (std::find(ks.begin(), ks.end(), plans[m]->kk) == ks.end()) ks.push_back(plans[m]->kk);
+            const bool new_k = std::find(ks.begin(), ks.end(), pl->kk) == ks.end();
+            if (og.members.size() >= cap || (new_k && static_cast<int>(ks.size()) >= kWideGroupMaxK)) {
+                keys.erase(it);  // full: this member opens a new group
+                it = keys.end();
+            }
+        }
+        int g;
+        if (it == keys.end()) {
+            qft_opts o{};
+            o.order = QFT_ORDER_NATURAL;
+            o.tile_bits = 14;
+            o.wait_limit_ms = static_cast<int>((pl->wait_limit_ns + 999999ull) / 1000000ull);
+            o.test_skip_first_load = pl->test_skip_first_load;
+            qft_plan_t wp = nullptr;
+            int rc = qft_plan_create(&wp, pl->n, pl->k, pl->dir, QFT_C64, &o);
+            if (rc == QFT_ERR_NOMEM) return rc;
+            bool ok = rc == QFT_OK && wp->passes.size() >= 2;
+            if (ok)
+                for (const auto& ph : wp->passes) ok = ok && ph.wide && ph.in_buf == (&ph == &wp->passes[0] ? 0 : 1);
+            if (!ok) {
+                qft_plan_destroy(wp);
+                wp = nullptr;
+            }
+            g = wp ? static_cast<int>(groups.size()) : -1;
+            if (wp) {
+                groups.emplace_back();
+                groups.back().plan = wp;
+            }
+            keys.emplace_back(key, g);
+        } else {
+            g = it->second;
+        }
+        if (g < 0) continue;
+        groups[g].members.push_back(i);
+        exclude[i] = 1;
+    }
+    return QFT_OK;
+}
+
+// Device tables of the groups (one allocation): per group and pass a tensor
+// map and an output pointer per member, per group a scale pointer and the
+// tile sums per member.  Fills each group's WideParams.
+int wide_groups_bind(qft_batch_s* b, const qft_plan_t* plans, void* const* d_states, char* ws, double* d_scale_in,
+                     int scale_mode) {
+    auto& groups = b->wide;
+    if (groups.empty()) return QFT_OK;
+    auto plans_kk = [&](int i) { return plans[i]->kk; };
+    auto fn = get_encode_fn();
+    if (!fn) return set_cuda_error(cudaErrorNotSupported);
+    size_t n_maps = 0, n_ptrs = 0, n_tp = 0;
+    for (const auto& g : groups) {
+        const size_t G = g.members.size(), P = g.plan->passes.size();
+        n_maps += G * P;
+        n_ptrs += G * P + G;
+        n_tp += G << (g.plan->n - 14);
+    }
+    const size_t o_ptrs = n_maps * sizeof(CUtensorMap);
+    const size_t o_tp = (o_ptrs + n_ptrs * sizeof(void*) + 255) / 256 * 256;
+    const size_t bytes = o_tp + n_tp * sizeof(double);
+    cudaError_t e = cudaMalloc(&b->d_wide, bytes);
+    if (e != cudaSuccess) {
+        b->d_wide = nullptr;
+        cudaGetLastError();
+        return QFT_ERR_NOMEM;
+    }
+    std::vector<unsigned char> host(o_tp, 0);
+    void** hptrs = reinterpret_cast<void**>(host.data() + o_ptrs);
+    char* dbase = static_cast<char*>(b->d_wide);
+    size_t im = 0, ip = 0, it = 0;
+    const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
+    for (auto& g : groups) {
+        const qft_plan_s* wp = g.plan;
+        const int G = static_cast<int>(g.members.size()), P = static_cast<int>(wp->passes.size());
+        // members in runs of equal cutoff (the kernel rebuilds its tables once per run)
+        std::stable_sort(g.members.begin(), g.members.end(), [&](int x, int y) { return plans_kk(x) < plans_kk(y); });
+        int gk_n = 0;
+        int32_t gk_end[kWideGroupMaxK] = {}, gk_val[kWideGroupMaxK] = {};
+        for (int m = 0; m < G; ++m) {
+            const int kk = plans_kk(g.members[m]);
+            if (gk_n == 0 || gk_val[gk_n - 1] != kk) {
+                if (gk_n == kWideGroupMaxK) return QFT_ERR_UNSUPPORTED;  // wide_groups_form keeps this from happening
+                gk_val[gk_n++] = kk;
+            }
+            gk_end[gk_n - 1] = m + 1;
+        }
+        double** d_gscale = reinterpret_cast<double**>(dbase + o_ptrs) + ip;
+        for (int m = 0; m < G; ++m) hptrs[ip++] = d_scale_in ? d_scale_in + g.members[m] : nullptr;
+        double* d_tp = reinterpret_cast<double*>(dbase + o_tp) + it;
+        it += static_cast<size_t>(G) << (wp->n - 14);
+        g.wp.clear();
+        g.grid.clear();
+        for (int j = 0; j < P; ++j) {
+            const PassHost& ph = wp->passes[j];
+            const CUtensorMap* d_maps = reinterpret_cast<const CUtensorMap*>(dbase) + im;
+            void* const* d_outs = reinterpret_cast<void* const*>(dbase + o_ptrs) + ip;
+            for (int m = 0; m < G; ++m) {
+                const int i = g.members[m];
+                void* work = ws + b->T.work_off[i];
+                void* in = ph.in_buf == 0 ? d_states[i] : work;
+                CUtensorMap tm;  // encoded in place (64-byte aligned), then copied into the upload buffer
+                CUresult r = fn(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, in, ph.gdim, ph.gstride, ph.box, estride,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) {
+                    set_cuda_error_code(static_cast<int>(r));
+                    return QFT_ERR_CUDA;
+                }
+                std::memcpy(host.data() + sizeof(CUtensorMap) * im++, &tm, sizeof(tm));
+                hptrs[ip++] = ph.out_buf == 0 ? d_states[i] : work;
+            }
+            WideParams W = ph.wp;
+            W.scale_mode = scale_mode;
+            W.lt_bits = wp->n - 14;
+            W.num_tiles = static_cast<int64_t>(G) << W.lt_bits;
+            W.maps = d_maps;
+            W.outs = d_outs;
+            W.tpart = d_tp;
+            W.gscale = d_scale_in ? d_gscale : nullptr;
+            W.out = nullptr;
+            W.partials = nullptr;
+            W.npartials = 0;
+            W.meta = nullptr;
+            W.user_scale = nullptr;
+            W.status = b->D.counters + 1;
+            W.wait_limit_ns = wp->wait_limit_ns;
+            W.test_skip_first_load = wp->test_skip_first_load;
+            W.kk = gk_val[0];
+            W.gk_n = gk_n;
+            for (int r = 0; r < kWideGroupMaxK; ++r) {
+                W.gk_end[r] = gk_end[r];
+                W.gk_val[r] = gk_val[r];
+            }
+            g.wp.push_back(W);
+            g.grid.push_back(static_cast<int>(std::min<int64_t>(W.num_tiles, wp->num_sms)));
+        }
+    }
+    e = cudaMemcpy(b->d_wide, host.data(), o_tp, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    // side streams (groups by decreasing size, each to the least-loaded stream) and the fork / join events
+    const int nside = std::min<int>(kMaxSide, static_cast<int>(groups.size()));
+    std::vector<int> byd(groups.size());
+    std::iota(byd.begin(), byd.end(), 0);
+    auto tiles = [&](int g) { return groups[g].wp[0].num_tiles; };
+    std::stable_sort(byd.begin(), byd.end(), [&](int x, int y) { return tiles(x) > tiles(y); });
+    std::vector<int64_t> load(nside, 0);
+    for (int g : byd) {
+        const int sidx = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+        groups[g].side = sidx;
+        load[sidx] += tiles(g);
+    }
+    std::vector<WideGroup> sorted;
+    for (int g : byd) sorted.push_back(std::move(groups[g]));
+    groups = std::move(sorted);
+    b->side.assign(nside, nullptr);
+    b->join.assign(nside, nullptr);
+    e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int k = 0; k < nside && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return QFT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t qft_batch_workspace_size(const qft_plan_t* plans, int count) { return batch_workspace_bytes(plans, count); }
@@ -353,9 +605,16 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
                      size_t workspace_bytes, double* d_scale_in, int scale_mode) {
     if (!out) return QFT_ERR_BAD_ARG;
     *out = nullptr;
+    if (!plans || !d_states || count <= 0 || !d_workspace) return QFT_ERR_BAD_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!plans[i]) return QFT_ERR_BAD_ARG;
     qft_batch_s* b = new (std::nothrow) qft_batch_s();
     if (!b) return QFT_ERR_NOMEM;
-    int rc = batch_build(plans, d_states, count, d_workspace, workspace_bytes, d_scale_in, scale_mode, false, b->T);
+    std::vector<char> exclude;
+    int rc = wide_groups_form(plans, count, b->wide, exclude);
+    if (rc == QFT_OK)
+        rc = batch_build(plans, d_states, count, d_workspace, workspace_bytes, d_scale_in, scale_mode, false, b->T,
+                         &exclude);
     if (rc != QFT_OK) {
         delete b;
         return rc;
@@ -363,8 +622,10 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
     BatchTables& T = b->T;
     BatchDevice& D = b->D;
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&D.counters), sizeof(int) * T.ncounters);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&D.descs), sizeof(PassParams) * T.descs.size());
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&D.items), sizeof(BatchItem) * T.items.size());
+    if (e == cudaSuccess && !T.descs.empty())
+        e = cudaMalloc(reinterpret_cast<void**>(&D.descs), sizeof(PassParams) * T.descs.size());
+    if (e == cudaSuccess && !T.items.empty())
+        e = cudaMalloc(reinterpret_cast<void**>(&D.items), sizeof(BatchItem) * T.items.size());
     if (e == cudaSuccess && !T.maps.empty())
         e = cudaMalloc(reinterpret_cast<void**>(&D.maps), sizeof(CUtensorMap) * T.maps.size());
     if (e == cudaSuccess && T.df) {
@@ -385,8 +646,10 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
         return QFT_ERR_NOMEM;
     }
     batch_set_status(T, D.counters);
-    e = cudaMemcpy(D.descs, T.descs.data(), sizeof(PassParams) * T.descs.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(D.items, T.items.data(), sizeof(BatchItem) * T.items.size(), cudaMemcpyHostToDevice);
+    if (!T.descs.empty())
+        e = cudaMemcpy(D.descs, T.descs.data(), sizeof(PassParams) * T.descs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !T.items.empty())
+        e = cudaMemcpy(D.items, T.items.data(), sizeof(BatchItem) * T.items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !T.maps.empty())
         e = cudaMemcpy(D.maps, T.maps.data(), sizeof(CUtensorMap) * T.maps.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(D.counters, 0, sizeof(int) * T.ncounters);
@@ -395,13 +658,40 @@ int qft_batch_create(qft_batch_t* out, const qft_plan_t* plans, void* const* d_s
         delete b;
         return set_cuda_error(e);
     }
+    rc = wide_groups_bind(b, plans, d_states, static_cast<char*>(d_workspace), d_scale_in, scale_mode);
+    if (rc != QFT_OK) {
+        free_device(D);
+        delete b;
+        return rc;
+    }
     *out = b;
     return QFT_OK;
 }
 
 int qft_batch_execute(qft_batch_t b, qft_stream_t stream) {
     if (!b) return QFT_ERR_BAD_ARG;
-    const cudaError_t e = batch_launch(b->T, b->D, reinterpret_cast<cudaStream_t>(stream));
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (b->wide.empty()) {
+        const cudaError_t e = batch_launch(b->T, b->D, st);
+        return e == cudaSuccess ? QFT_OK : set_cuda_error(e);
+    }
+    // zero the counters (and status word), fork the side streams, run the
+    // persistent launch and the groups' passes side by side, join
+    cudaError_t e = cudaMemsetAsync(b->D.counters, 0, sizeof(int) * b->T.ncounters, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, st);
+    for (size_t k = 0; k < b->side.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+    if (e == cudaSuccess && b->T.nitems > 0) e = batch_launch(b->T, b->D, st, false);
+    for (const auto& g : b->wide) {
+        for (size_t j = 0; j < g.wp.size() && e == cudaSuccess; ++j) {
+            const PassHost& ph = g.plan->passes[j];
+            e = launch_pass_wide_group(g.plan->dir, ph.wide_r0, ph.wide_r1, ph.wide_top, g.wp[j], g.grid[j],
+                                       b->side[g.side]);
+        }
+    }
+    for (size_t k = 0; k < b->side.size() && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->join[k], b->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join[k], 0);
+    }
     return e == cudaSuccess ? QFT_OK : set_cuda_error(e);
 }
 
@@ -418,6 +708,22 @@ int qft_batch_status(qft_batch_t b, qft_stream_t stream) {
 int qft_batch_destroy(qft_batch_t b) {
     if (b) free_device(b->D);
     delete b;
+    return QFT_OK;
+}
+
+int qft_batch_get_info(qft_batch_t b, qft_batch_info* info) {
+    if (!b || !info) return QFT_ERR_BAD_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->transforms = b->T.count;
+    info->persistent_items = b->T.nitems;
+    info->wide_groups = static_cast<int>(b->wide.size());
+    int launches = b->T.nitems > 0 ? 1 + (b->T.df ? 1 : 0) : 0;
+    for (const auto& g : b->wide) {
+        info->wide_transforms += static_cast<int>(g.members.size());
+        launches += static_cast<int>(g.wp.size());
+    }
+    info->kernel_launches = launches;
+    info->side_streams = static_cast<int>(b->side.size());
     return QFT_OK;
 }
 

@@ -56,12 +56,24 @@ cudaError_t launch_wide_fwd(int r0, int r1, int top, const CUtensorMap& map, con
                             cudaStream_t st);
 cudaError_t launch_wide_inv(int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
                             cudaStream_t st);
+cudaError_t launch_wide_group_fwd(int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
+                                  cudaStream_t st);
+cudaError_t launch_wide_group_inv(int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
+                                  cudaStream_t st);
 
 // The wide pass kernel (qft_wide.cuh) for one direction and block split.
 cudaError_t launch_pass_wide(int dir, int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
                              cudaStream_t stream) {
     return dir < 0 ? launch_wide_fwd(r0, r1, top, map, P, grid, stream)
                    : launch_wide_inv(r0, r1, top, map, P, grid, stream);
+}
+
+// The same in group mode (P.maps, P.outs, P.tpart set; map unused).
+cudaError_t launch_pass_wide_group(int dir, int r0, int r1, int top, const WideParams& P, int grid,
+                                   cudaStream_t stream) {
+    static const CUtensorMap unused{};
+    return dir < 0 ? launch_wide_group_fwd(r0, r1, top, unused, P, grid, stream)
+                   : launch_wide_group_inv(r0, r1, top, unused, P, grid, stream);
 }
 
 }  // namespace qft

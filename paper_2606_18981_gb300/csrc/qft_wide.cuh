@@ -39,6 +39,18 @@
 // Shared memory: T = 128 KiB, Z = 82 KiB (a 64 KiB half tile, padded so that
 // every access pattern is bank-conflict free and every address is a thread
 // base plus a compile-time offset).  One CTA per SM.
+//
+// Group mode (GROUP = true; batches of same-plan transforms): one launch runs
+// the pass for G transforms at their own addresses.  Global tile s is local
+// tile s mod 2^lt_bits of transform s >> lt_bits: the TMA load takes that
+// transform's tensor map from a device array, the stores its output base.
+// The norm is kept per transform: the first pass writes each tile's squared
+// sum (a fixed-order CTA reduction in double-float arithmetic on the FP32
+// pipe), and the last pass, before its first tile, sums each of its tiles'
+// transform's tile sums in a fixed order and keeps the decode scale in shared
+// memory, so every tile of a transform applies the same scale (Sec. 3 step 4).
+// (FP64 runs at a small fraction of the FP32 rate on this GPU, so no FP64
+// arithmetic is done per tile.)
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -46,6 +58,7 @@
 
 #include "plan.hpp"
 #include "qft_device.cuh"
+#include "qft_df.cuh"
 
 namespace qft {
 
@@ -119,6 +132,32 @@ constexpr uint32_t kBarEvenWrote = 2; // the even warps' exchange writes are don
 constexpr uint32_t kBarZFree = 3;     // the even warps have read the exchange buffer
 constexpr uint32_t kBarOddWrote = 4;  // the odd warps' exchange writes are done
 
+// 8-byte asynchronous global -> shared copy (no register holds the value in flight).
+__device__ __forceinline__ void cp_async_8(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Local tile of global tile s (group mode: the tile within its transform).
+template <bool GROUP>
+__device__ __forceinline__ int64_t wide_local(const WideParams& P, int64_t s) {
+    if constexpr (GROUP) return s & ((int64_t(1) << P.lt_bits) - 1);
+    else return s;
+}
+
+// Decode factor of the last pass from scale_in (Sec. 3 step 4; scale modes as qft_execute).
+__device__ __forceinline__ float wide_decode_factor(const WideParams& P, double scale_in) {
+    double f;
+    switch (P.scale_mode) {
+        case 0: f = scale_in > 0.0 ? P.inv_root_n / scale_in : 0.0; break;
+        case 1: f = P.inv_root_n; break;
+        case 2: f = 1.0; break;
+        default: f = P.inv_root_n * P.inv_root_n; break;
+    }
+    return static_cast<float>(f);
+}
+
 __device__ __forceinline__ void wide_coords(const WideParams& P, int64_t tile, int32_t c[5]) {
 #pragma unroll
     for (int d = 0; d < 5; ++d) {
@@ -148,14 +187,14 @@ __device__ __forceinline__ void wide_tile_coords(const WideParams& P, int64_t ti
 // thread's other 5 fixed bits).  UA holds the first part for every value a of
 // x0..x3: entry (i * 16 + a), i < R0 for stage-0 wire wlo0 + i, i = R0 + e for
 // stage-1 wire wlo1 + e.  Threads 0 .. 16 (R0 + R1) - 1 build one entry each.
-template <int DIR, int R0, int R1>
-__device__ __forceinline__ void wide_tile_twiddles(const WideParams& P, int64_t tile, float2* UA) {
+template <int DIR, int R0, int R1, bool GROUP>
+__device__ __forceinline__ void wide_tile_twiddles(const WideParams& P, int64_t tile, float2* UA, int kk) {
     const int t = threadIdx.x;
     if (t >= 16 * (R0 + R1) || tile >= P.num_tiles) return;
     const int i = t >> 4, a = t & 15;
     uint64_t I;
     int64_t dummy;
-    wide_tile_coords(P, tile, I, dummy);
+    wide_tile_coords(P, wide_local<GROUP>(P, tile), I, dummy);
 #pragma unroll
     for (int b = 0; b < 4; ++b)
         if ((a >> b) & 1) I |= 1ull << P.p_wire[b];
@@ -163,7 +202,7 @@ __device__ __forceinline__ void wide_tile_twiddles(const WideParams& P, int64_t 
     const int e = s ? i - R0 : i;
     const int wlo = s ? P.wlo1 : P.wlo0;
     const int hi = wlo + (s ? R1 : R0) - 1;
-    UA[t] = phase_turns<float, DIR>(cross_phase(I, P.n, hi, wlo + e, P.kk), P.n);
+    UA[t] = phase_turns<float, DIR>(cross_phase(I, P.n, hi, wlo + e, kk), P.n);
 }
 
 // Diagonal prod_e tau_e^{j_e} on the 2^R amplitudes of one group: the low two
@@ -218,7 +257,7 @@ __device__ __forceinline__ void wide_stage(float2 (&v)[32], const float2 (&uv)[R
     }
 }
 
-template <int DIR, int R0, int R1, bool TOP>
+template <int DIR, int R0, int R1, bool TOP, bool GROUP>
 __global__ void __launch_bounds__(kWideThreads, 1)
     qft_wide_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ WideParams P) {
     constexpr int E0 = 5 - R0, E1 = 5 - R1;
@@ -232,6 +271,9 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     __shared__ __align__(16) float2 W0[(1 << E0) * R0];
     __shared__ __align__(16) float2 W1[(1 << E1) * R1];
     __shared__ double red[kWideThreads / 32];
+    __shared__ float2 redt[GROUP ? 2 : 1][kWideThreads / 32];  // group mode: per-tile warp sums (hi, lo), double-buffered
+    __shared__ float s_scale[GROUP ? kWideGroupTilesPerCta : 1];  // group mode, last pass: decode scale of the k-th tile
+    __shared__ void* s_outp[2];  // group mode: the output base of the k-th tile's transform, fetched a tile ahead
     __shared__ int64_t s_othr[kWideThreads];  // each thread's output offset (kept out of registers)
 
     const uint32_t tid = threadIdx.x;
@@ -253,66 +295,113 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     }
     const uint32_t ia0 = x0 & 15u, ib0 = (x0 >> 4) & 31u;
     const uint32_t ia1 = x1 & 15u, ib1 = x1 >> 9;
-    // VB: entry (i * 32 + b), i as in UA; bits x4 + k (stage 0) or x9 + k (stage 1) = bit k of b
-    for (int t = tid; t < 32 * (R0 + R1); t += kWideThreads) {
-        const int i = t >> 5, b = t & 31;
-        const int s = i < R0 ? 0 : 1;
-        const int e = s ? i - R0 : i;
-        const int wlo = s ? P.wlo1 : P.wlo0;
-        const int hi = wlo + (s ? R1 : R0) - 1;
-        uint64_t I = 0;
-        for (int k = 0; k < 5; ++k)
-            if ((b >> k) & 1) I |= 1ull << P.p_wire[(s ? 9 : 4) + k];
-        VB[t] = (s || cross0) ? phase_turns<float, DIR>(cross_phase(I, P.n, hi, wlo + e, P.kk), P.n) : cunit<float2>();
-    }
-    // the extra batch bits' factors, per group of the thread's registers
-    if (tid < (1 << E0) * R0) {
-        const int js = tid / R0, e = tid % R0;
-        uint64_t I = 0;
-        for (int i = 0; i < E0; ++i)
-            if ((js >> i) & 1) I |= 1ull << P.p_wire[9 + i];
-        W0[tid] = cross0 ? phase_turns<float, DIR>(cross_phase(I, P.n, hi0, P.wlo0 + e, P.kk), P.n) : cunit<float2>();
-    }
-    if (tid >= 64 && tid < 64 + (1 << E1) * R1) {
-        const int w = tid - 64, js = w / R1, e = w % R1;
-        uint64_t I = 0;
-        for (int i = 0; i < E1; ++i)
-            if ((js >> i) & 1) I |= 1ull << P.p_wire[4 + i];
-        W1[w] = phase_turns<float, DIR>(cross_phase(I, P.n, hi1, P.wlo1 + e, P.kk), P.n);
-    }
-    if (tid == 0) mbar_init(&mbar, 1);
+    // The cutoff k of global tile s's transform (group mode: from the sorted
+    // cutoff runs; else the plan's).
+    auto kk_of = [&](int64_t s) -> int {
+        if constexpr (GROUP) {
+            const int64_t ti = s >> P.lt_bits;
+            int v = P.gk_val[0];
+#pragma unroll
+            for (int i = 1; i < kWideGroupMaxK; ++i)
+                if (i < P.gk_n && ti >= P.gk_end[i - 1]) v = P.gk_val[i];
+            return v;
+        } else {
+            return P.kk;
+        }
+    };
+    // The kernel-wide cross-twiddle tables for cutoff kk.
+    auto build_tables = [&](int kk) {
+        // VB: entry (i * 32 + b), i as in UA; bits x4 + k (stage 0) or x9 + k (stage 1) = bit k of b
+        for (int t = tid; t < 32 * (R0 + R1); t += kWideThreads) {
+            const int i = t >> 5, b = t & 31;
+            const int s = i < R0 ? 0 : 1;
+            const int e = s ? i - R0 : i;
+            const int wlo = s ? P.wlo1 : P.wlo0;
+            const int hi = wlo + (s ? R1 : R0) - 1;
+            uint64_t I = 0;
+            for (int k = 0; k < 5; ++k)
+                if ((b >> k) & 1) I |= 1ull << P.p_wire[(s ? 9 : 4) + k];
+            VB[t] = (s || cross0) ? phase_turns<float, DIR>(cross_phase(I, P.n, hi, wlo + e, kk), P.n) : cunit<float2>();
+        }
+        // the extra batch bits' factors, per group of the thread's registers
+        if (tid < (1 << E0) * R0) {
+            const int js = tid / R0, e = tid % R0;
+            uint64_t I = 0;
+            for (int i = 0; i < E0; ++i)
+                if ((js >> i) & 1) I |= 1ull << P.p_wire[9 + i];
+            W0[tid] = cross0 ? phase_turns<float, DIR>(cross_phase(I, P.n, hi0, P.wlo0 + e, kk), P.n) : cunit<float2>();
+        }
+        if (tid >= 64 && tid < 64 + (1 << E1) * R1) {
+            const int w = tid - 64, js = w / R1, e = w % R1;
+            uint64_t I = 0;
+            for (int i = 0; i < E1; ++i)
+                if ((js >> i) & 1) I |= 1ull << P.p_wire[4 + i];
+            W1[w] = phase_turns<float, DIR>(cross_phase(I, P.n, hi1, P.wlo1 + e, kk), P.n);
+        }
+    };
     int64_t tile = blockIdx.x;
-    wide_tile_twiddles<DIR, R0, R1>(P, tile, UA[0]);
+    int kk_tab = kk_of(tile);  // the cutoff the tables hold
+    build_tables(kk_tab);
+    if (tid == 0) mbar_init(&mbar, 1);
+    if constexpr (GROUP) {
+        if (tid == 0 && tile < P.num_tiles) s_outp[0] = P.outs[tile >> P.lt_bits];
+    }
+    wide_tile_twiddles<DIR, R0, R1, GROUP>(P, tile, UA[0], kk_tab);
+    if constexpr (GROUP) {
+        // Last pass: the decode scale of each of this CTA's tiles (the host keeps
+        // them <= kWideGroupTilesPerCta): warp w takes tiles w, w + 16, ...; its
+        // lanes sum the transform's tile sums in a fixed xor-butterfly order.
+        if (P.last) {
+            const int64_t mine = (P.num_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+            const int lane = tid & 31, tpt = 1 << P.lt_bits;
+            for (int64_t j = tid >> 5; j < mine; j += kWideThreads / 32) {
+                const int64_t s = blockIdx.x + j * gridDim.x;
+                const int64_t ti = s >> P.lt_bits;
+                const double* tp = P.tpart + (ti << P.lt_bits);
+                double a = lane < tpt ? tp[lane] : 0.0;
+                if (lane + 32 < tpt) a += tp[lane + 32];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) {
+                    const double scale_in = sqrt(a);
+                    s_scale[j] = wide_decode_factor(P, scale_in);
+                    if ((s & (tpt - 1)) == 0 && P.gscale) {
+                        double* g = P.gscale[ti];
+                        if (g) *g = scale_in;
+                    }
+                }
+            }
+        }
+    }
     __syncthreads();
 
-    // Last pass: scale_in from the first pass's per-CTA partial sums.
+    // Last pass: scale_in from the first pass's per-CTA partial sums (group
+    // mode: per tile, below).
     float scale = 1.f;
-    if (P.last) {
+    if (!GROUP && P.last) {
         double s = 0.0;
         for (int i = tid; i < P.npartials; i += kWideThreads) s += P.partials[i];
         const double scale_in = sqrt(block_sum<kWideThreads>(s, red));
-        double f;
-        switch (P.scale_mode) {
-            case 0: f = scale_in > 0.0 ? P.inv_root_n / scale_in : 0.0; break;
-            case 1: f = P.inv_root_n; break;
-            case 2: f = 1.0; break;
-            default: f = P.inv_root_n * P.inv_root_n; break;
-        }
-        scale = static_cast<float>(f);
+        scale = wide_decode_factor(P, scale_in);
         if (blockIdx.x == 0 && tid == 0) {
             P.meta[0] = scale_in;
             if (P.user_scale) *P.user_scale = scale_in;
         }
     }
 
+    // the input tensor map of global tile s
+    auto map_of = [&](int64_t s) -> const CUtensorMap* {
+        if constexpr (GROUP) return static_cast<const CUtensorMap*>(P.maps) + (s >> P.lt_bits);
+        else return &tmap;
+    };
     auto issue = [&](int64_t s) {  // thread 0: load tile s into T
         int32_t c[5];
-        wide_coords(P, s, c);
+        wide_coords(P, wide_local<GROUP>(P, s), c);
         mbar_arrive_expect_tx(&mbar, static_cast<uint32_t>(kWideTileBytes));
-        tma_load_5d(T, &tmap, c, &mbar);
+        tma_load_5d(T, map_of(s), c, &mbar);
         if (P.l2_prefetch && s + gridDim.x < P.num_tiles) {
-            wide_coords(P, s + gridDim.x, c);
-            tma_prefetch_l2_5d(&tmap, c);
+            wide_coords(P, wide_local<GROUP>(P, s + gridDim.x), c);
+            tma_prefetch_l2_5d(map_of(s + gridDim.x), c);
         }
     };
     if (tid == 0 && !P.test_skip_first_load && tile < P.num_tiles) issue(tile);
@@ -321,10 +410,21 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     uint32_t parity = 0u;
     bool aborted = false, ok = true;
     for (int k = 0; tile < P.num_tiles; tile += gridDim.x, ++k) {
+        const int kk = kk_of(tile);
+        if constexpr (GROUP) {
+            if (P.last) scale = s_scale[k];
+            if (kk != kk_tab) {  // the next transform run: every thread is done with the tables
+                __syncthreads();
+                build_tables(kk);
+                __syncthreads();
+                kk_tab = kk;
+            }
+        }
         ok = mbar_wait_bounded(&mbar, parity, P.wait_limit_ns);
         parity ^= 1u;
         const float2* Ucur = UA[k & 1];
         float2 v[32];
+        float tile_norm = 0.f;  // group mode: the thread's share of this tile's squared norm
         if (ok) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = T[pT + (uint32_t(j) << 9)];
@@ -335,24 +435,48 @@ __global__ void __launch_bounds__(kWideThreads, 1)
                     s0 = cfma2(v[j], v[j], s0);
                     s1 = cfma2(v[j + 16], v[j + 16], s1);
                 }
-                norm_acc += static_cast<double>((s0.x + s0.y) + (s1.x + s1.y));
+                const float ts = (s0.x + s0.y) + (s1.x + s1.y);
+                if constexpr (GROUP) tile_norm = ts;
+                else norm_acc += static_cast<double>(ts);
             }
             float2 uv[R0];
 #pragma unroll
             for (int e = 0; e < R0; ++e) uv[e] = cmul(Ucur[e * 16 + ia0], VB[e * 32 + ib0]);
-            wide_stage<DIR, R0>(v, uv, W0, cross0, P.kk);
+            wide_stage<DIR, R0>(v, uv, W0, cross0, kk);
+        }
+        if constexpr (GROUP) {
+            if (P.first) {  // the warp's sum in double-float (two-sum is exact, so every lane ends equal)
+                dfloat t(tile_norm, 0.f);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    t = df_add(t, dfloat(__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)));
+                if ((tid & 31) == 0) redt[k & 1][tid >> 5] = make_float2(t.hi, t.lo);
+            }
+        }
+        if constexpr (GROUP) {
+            if (tid == 0) cp_async_wait_all();  // this tile's output base has landed in s_outp
         }
         // every thread is past the previous tile's exchange: Z may be written
         if (__syncthreads_or(!ok)) {
             aborted = true;
             break;
         }
+        if constexpr (GROUP) {
+            if (P.first && tid == 32) {  // the tile's sum, warps in order (the next write to this half is two tiles on)
+                dfloat t(redt[k & 1][0].x, redt[k & 1][0].y);
+#pragma unroll
+                for (int w = 1; w < kWideThreads / 32; ++w) t = df_add(t, dfloat(redt[k & 1][w].x, redt[k & 1][w].y));
+                t = df_norm(t);
+                P.tpart[tile] = static_cast<double>(t.hi) + static_cast<double>(t.lo);
+            }
+        }
         // T has been read: the next tile streams into it during the rest of this one.
         if (tid == 0 && tile + gridDim.x < P.num_tiles) {
             fence_proxy_async_smem();
             issue(tile + gridDim.x);
+            if constexpr (GROUP) cp_async_8(&s_outp[(k + 1) & 1], P.outs + ((tile + gridDim.x) >> P.lt_bits));
         }
-        wide_tile_twiddles<DIR, R0, R1>(P, tile + gridDim.x, UA[(k + 1) & 1]);
+        wide_tile_twiddles<DIR, R0, R1, GROUP>(P, tile + gridDim.x, UA[(k + 1) & 1], kk_of(tile + gridDim.x));
         if (!round1) {  // even warps: x bit 3 = 0
 #pragma unroll
             for (int j = 0; j < 32; ++j) Z[a0 + wide_k0(j)] = v[j];
@@ -377,12 +501,15 @@ __global__ void __launch_bounds__(kWideThreads, 1)
             float2 uv[R1];
 #pragma unroll
             for (int e = 0; e < R1; ++e) uv[e] = cmul(Ucur[(R0 + e) * 16 + ia1], VB[(R0 + e) * 32 + ib1]);
-            wide_stage<DIR, R1>(v, uv, W1, true, P.kk);
+            wide_stage<DIR, R1>(v, uv, W1, true, kk);
         }
         uint64_t I_tile;
         int64_t out_tile;
-        wide_tile_coords(P, tile, I_tile, out_tile);
-        float2* __restrict__ outp = static_cast<float2*>(P.out) + (out_tile + s_othr[tid]);
+        wide_tile_coords(P, wide_local<GROUP>(P, tile), I_tile, out_tile);
+        float2* base;
+        if constexpr (GROUP) base = static_cast<float2*>(s_outp[k & 1]);
+        else base = static_cast<float2*>(P.out);
+        float2* __restrict__ outp = base + (out_tile + s_othr[tid]);
 #pragma unroll
         for (int j = 0; j < 32; ++j) outp[P.oj[j]] = v[j];
     }
@@ -393,22 +520,43 @@ __global__ void __launch_bounds__(kWideThreads, 1)
             // let this tile's copy land before the CTA's shared memory is released
             // (the next tile's is issued only after the check)
             if (!ok) mbar_wait_bounded(&mbar, parity ^ 1u, P.wait_limit_ns);
+            if constexpr (GROUP) cp_async_wait_all();
         }
         return;
     }
-    if (P.first) {
+    if (!GROUP && P.first) {
         const double tot = block_sum<kWideThreads>(norm_acc, red);
         if (tid == 0) P.partials[blockIdx.x] = tot;
     }
 }
 
-template <int DIR, int R0, int R1, bool TOP>
+template <int DIR, int R0, int R1, bool TOP, bool GROUP>
 inline cudaError_t launch_wide_t(const CUtensorMap& map, const WideParams& P, int grid, cudaStream_t stream) {
-    auto kern = qft_wide_kernel<DIR, R0, R1, TOP>;
+    auto kern = qft_wide_kernel<DIR, R0, R1, TOP, GROUP>;
     const cudaError_t e = ensure_dynamic_smem(kern, kWideSmemBytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, kWideThreads, kWideSmemBytes, stream>>>(map, P);
     return cudaGetLastError();
+}
+
+// Dispatch over the block splits (R0, R1) in {4, 5} x {3, 4, 5} and the
+// first-pass store map, for one direction and mode (one translation unit each,
+// so that they compile in parallel).
+template <int DIR, bool GROUP>
+inline cudaError_t launch_wide_dir(int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
+                                   cudaStream_t st) {
+#define QFT_WIDE_CASE(A, B)                                                        \
+    if (r0 == A && r1 == B)                                                        \
+        return top ? launch_wide_t<DIR, A, B, true, GROUP>(map, P, grid, st)       \
+                   : launch_wide_t<DIR, A, B, false, GROUP>(map, P, grid, st);
+    QFT_WIDE_CASE(5, 5)
+    QFT_WIDE_CASE(5, 4)
+    QFT_WIDE_CASE(5, 3)
+    QFT_WIDE_CASE(4, 5)
+    QFT_WIDE_CASE(4, 4)
+    QFT_WIDE_CASE(4, 3)
+#undef QFT_WIDE_CASE
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace qft

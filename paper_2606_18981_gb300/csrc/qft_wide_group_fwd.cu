@@ -1,0 +1,14 @@
+// qft_wide_group_fwd.cu -- forward (DIR = -1) group-mode instantiations of the wide pass kernel
+// (qft_wide.cuh): top block of R0 in {4, 5} wires, low block of R1 in
+// {3, 4, 5} wires, with or without the first-pass store map.  Each direction
+// and mode is its own translation unit so that they compile in parallel.
+#include "qft_wide.cuh"
+
+namespace qft {
+
+cudaError_t launch_wide_group_fwd(int r0, int r1, int top, const CUtensorMap& map, const WideParams& P, int grid,
+                                 cudaStream_t st) {
+    return launch_wide_dir<-1, true>(r0, r1, top, map, P, grid, st);
+}
+
+}  // namespace qft

@@ -1016,6 +1016,7 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
     // double-float complex128 with n >= 21 takes 512 threads.
     // (For subset plans the array size decides: their passes sweep all of it.)
     const bool shape_given = opts && (opts->tile_bits || opts->coalesce_bits || opts->threads || rmax_given);
+    pl->shape_given = shape_given;
     if (!shape_given && dtype == QFT_C64 && !pl->precision && n_addr >= 27) {
         pl->TB = 12;
         pl->cmin = 4;

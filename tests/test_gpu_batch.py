@@ -155,3 +155,113 @@ def test_batch_bounded_wait_reports_timeout():
     for s_, x in zip(st, xs):
         assert torch.isfinite(torch.view_as_real(s_)).all()
         assert abs(float(torch.linalg.vector_norm(s_)) - 1.0) < 1e-5
+
+
+# ---------------------------------------------------------------- wide groups
+# Complex64 natural-order transforms of 14..20 qubits run on the 2^14-tile pass
+# kernel in group mode (one launch per pass per (n, direction), the cutoff k
+# per transform).
+
+@pytest.mark.parametrize("direction,mode", [(q.FORWARD, q.SCALE_STATE), (q.INVERSE, q.SCALE_UNITARY),
+                                            (q.FORWARD, q.SCALE_UNNORM)])
+def test_wide_groups_match_single_transforms_and_oracle(oracle_mod, direction, mode):
+    specs, plans, xs = make_batch(72, 10, 20, "c64", 0, seed=23, direction=direction)
+    states = [x.clone() for x in xs]
+    scales = torch.zeros(len(xs), dtype=torch.float64, device="cuda")
+    b = q.Batch([plans[(n, k)] for n, k, _ in specs], states, mode, scale_out=scales)
+    info = b.info()
+    grouped = sum(1 for n, _, _ in specs if 14 <= n <= 20)
+    assert info.wide_transforms == grouped > 0
+    assert info.wide_groups == len({n for n, _, _ in specs if 14 <= n <= 20})  # one group per n: k is per transform
+    assert info.kernel_launches == 2 * info.wide_groups + (1 if grouped < len(specs) else 0)
+    b.execute()
+    assert b.status() == 0
+    for i, (n, k, _) in enumerate(specs):
+        p = plans[(n, k)]
+        ref = xs[i].clone()
+        ws = p.alloc_workspace()
+        p.execute(ref, ws, mode)
+        torch.cuda.synchronize()
+        assert rel(states[i], ref) <= TOL["c64"](n), (i, n, k)
+        assert abs(scales[i].item() - p.scale_in(ws)) <= 1e-6 * max(p.scale_in(ws), 1e-300), (i, n)
+    for i in [j for j, (n, _, _) in enumerate(specs) if n >= 14][:6]:
+        n, k, _ = specs[i]
+        want, _ = oracle_mod.qft(xs[i].cpu().numpy().astype(np.complex128), k, direction, mode, True)
+        got = states[i].cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= TOL["c64"](n), (i, n, k)
+
+
+def test_wide_groups_elementwise_parity(oracle_mod):
+    """Every amplitude of grouped transforms against the oracle within the
+    element-wise bound of the wide plan's shape (2 passes, natural order)."""
+    from parity import elementwise_bound, plan_shape
+
+    ns = [14, 15, 17, 20, 14, 20]
+    plans = {n: q.Plan(n, -1, q.FORWARD, "c64", 0) for n in set(ns)}
+    xs = [torch.from_numpy(qft_inputs.gaussian(n, seed=40 + i)).to(torch.complex64).cuda() for i, n in enumerate(ns)]
+    states = [x.clone() for x in xs]
+    b = q.Batch([plans[n] for n in ns], states, q.SCALE_STATE)
+    assert b.info().wide_transforms == len(ns)
+    b.execute()
+    assert b.status() == 0
+    wide = {n: q.Plan(n, -1, q.FORWARD, "c64", 0, tile_bits=14) for n in set(ns)}
+    for i, n in enumerate(ns):
+        ref, _ = oracle_mod.qft(xs[i].cpu().numpy().astype(np.complex128), -1, -1, 0, True)
+        a_last, natural = plan_shape(wide[n])
+        bound = elementwise_bound(ref, "c64", n, a_last, natural)
+        got = states[i].cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(got - ref) / bound) <= 1.0, (i, n)
+
+
+def test_wide_groups_are_deterministic():
+    specs, plans, xs = make_batch(48, 12, 19, "c64", 0, seed=29)
+    states = [x.clone() for x in xs]
+    b = q.Batch([plans[(n, k)] for n, k, _ in specs], states, q.SCALE_STATE)
+    assert b.info().wide_transforms > 0
+    b.execute()
+    torch.cuda.synchronize()
+    first = [st.clone() for st in states]
+    for st, x in zip(states, xs):
+        st.copy_(x)
+    b.execute()
+    torch.cuda.synchronize()
+    for st, f in zip(states, first):
+        assert torch.equal(st, f)
+
+
+def test_wide_groups_take_tile14_plans_in_range_only():
+    xs = {n: torch.from_numpy(qft_inputs.gaussian(n, seed=n)).to(torch.complex64).cuda() for n in (16, 24)}
+    p16 = q.Plan(16, 8, q.FORWARD, "c64", 0, tile_bits=14)
+    st = xs[16].clone()
+    b = q.Batch([p16], [st], q.SCALE_STATE)
+    assert b.info().wide_transforms == 1 and b.info().persistent_items == 0
+    b.execute()
+    ref = xs[16].clone()
+    p16.execute(ref, p16.alloc_workspace(), q.SCALE_STATE)
+    torch.cuda.synchronize()
+    assert rel(st, ref) <= 1e-6
+    p24 = q.Plan(24, -1, q.FORWARD, "c64", 0)  # 2^14-amplitude tiles by default from n = 23
+    assert p24.info().tile_bits[0] == 14
+    with pytest.raises(q.QftError):
+        q.Batch([p24], [xs[24].clone()], q.SCALE_STATE)
+
+
+def test_wide_groups_bounded_wait_reports_timeout():
+    """Group-mode passes whose first tile loads are never issued (the planner
+    test hook on 2^14-tile plans) let their bounded waits expire: the batch
+    status reads QFT_ERR_TIMEOUT and the next batch runs normally."""
+    plans = [q.Plan(n, -1, q.FORWARD, "c64", 0, tile_bits=14, test_skip_first_load=1, wait_limit_ms=20)
+             for n in (14, 16)]
+    states = [torch.zeros(1 << p.info().n, dtype=torch.complex64, device="cuda") for p in plans]
+    b = q.Batch(plans, states, q.SCALE_STATE)
+    assert b.info().wide_transforms == 2
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.status() == q.ERR_TIMEOUT
+    specs, good, xs = make_batch(8, 14, 17, "c64", 0, seed=6)
+    st = [x.clone() for x in xs]
+    b2 = q.Batch([good[(n, k)] for n, k, _ in specs], st, q.SCALE_STATE)
+    b2.execute()
+    assert b2.status() == 0
+    for s_ in st:
+        assert abs(float(torch.linalg.vector_norm(s_)) - 1.0) < 1e-5
