@@ -699,12 +699,16 @@ def plan_is_wide(plan):
 
 
 def summarize_extra(extra):
-    """One small dict per secondary workload (the detailed records stay in
-    "extra", printed last)."""
+    """One small dict per secondary workload, numbers to 4 significant digits
+    (the detailed records stay in "extra"; the summaries end the line, so a
+    reader of its last kilobytes sees them)."""
     out = {}
 
+    def short(v):
+        return float(f"{v:.4g}") if isinstance(v, float) else v
+
     def pick(d, *keys):
-        return {k: d[k] for k in keys if isinstance(d, dict) and k in d}
+        return {k: short(d[k]) for k in keys if isinstance(d, dict) and k in d}
 
     if "c64_n33" in extra:
         out["largest_c64_n33"] = pick(extra["c64_n33"], "ms_per_step", "amplitudes_per_s", "passes",
@@ -933,10 +937,10 @@ def run_ours(args, world, rank, local):
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (P + (1 if dt == "c128" and not prec else 0)) * args.steps,
                 "clocks": clocks}
-        line.update(summary)  # compact secondary results, ahead of the detailed extras
         line["extra"] = extra
         if rejected is not None:  # the first timed region's numbers, not used
             line["remeasured"] = rejected
+        line.update(summary)  # compact secondary results last, after the detailed extras
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
