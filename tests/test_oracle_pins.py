@@ -340,3 +340,47 @@ def test_sparse_dft_bins_against_dense_and_numpy(oracle_mod):
     b = rng.integers(0, 1 << n, size=1000, dtype=np.uint64)
     got = oracle_mod._mulmod_pow2(a, b, n)
     assert all(int(g) == (int(x) * int(y)) % (1 << n) for g, x, y in zip(got, a, b))
+
+
+# ------------------------------------------------ Sec. 4 accuracy measures
+
+def test_fidelity_closed_forms(oracle_mod):
+    """F = |<a,b>|^2 / (|a|^2 |b|^2) (Sec. 4): 1 under any complex rescaling,
+    0 for orthogonal states, cos^2(theta) between unit vectors at angle
+    theta, symmetric in its arguments."""
+    rng = np.random.default_rng(7)
+    a = rng.normal(size=64) + 1j * rng.normal(size=64)
+    assert abs(oracle_mod.fidelity(a, (0.3 - 2.1j) * a) - 1.0) < 1e-14
+    e0, e1 = np.eye(8)[0], np.eye(8)[1]
+    assert oracle_mod.fidelity(e0, e1) == 0.0
+    for th in (0.1, 0.7, 1.3):
+        b = np.cos(th) * e0 + np.exp(0.4j) * np.sin(th) * e1
+        assert abs(oracle_mod.fidelity(e0, b) - np.cos(th) ** 2) < 1e-15
+    b = rng.normal(size=64) + 1j * rng.normal(size=64)
+    assert abs(oracle_mod.fidelity(a, b) - oracle_mod.fidelity(b, a)) < 1e-15
+    # the transform of a basis state |0> has no controlled-phase rotation at
+    # any cutoff (every control bit is 0): the range-k result is exact
+    x = np.zeros(1 << 8, complex)
+    x[0] = 1
+    ex, _ = oracle_mod.qft(x, -1, -1, 0, True)
+    for k in (0, 2, 5):
+        ak, _ = oracle_mod.qft(x, k, -1, 0, True)
+        assert abs(oracle_mod.fidelity(ak, ex) - 1.0) < 1e-14
+
+
+def test_leakage_closed_forms(oracle_mod):
+    """Leakage = 1 - |approx[y*]|^2 / |approx|^2 at y* = argmax |exact| (Sec. 4):
+    0 for a state on the peak bin, p for weight p moved off it, 1 - 1/N for a
+    flat state, and scale invariant."""
+    N = 32
+    exact = np.zeros(N, complex)
+    exact[5] = 1
+    assert oracle_mod.leakage(exact, exact) == 0.0
+    for p in (1e-3, 0.25, 0.9):
+        approx = np.zeros(N, complex)
+        approx[5] = np.sqrt(1 - p)
+        approx[9] = 1j * np.sqrt(p)
+        assert abs(oracle_mod.leakage(approx, exact) - p) < 1e-15
+        assert abs(oracle_mod.leakage(3.7 * approx, exact) - p) < 1e-14
+    flat = np.exp(1j * np.arange(N)) / np.sqrt(N)
+    assert abs(oracle_mod.leakage(flat, exact) - (1 - 1 / N)) < 1e-14
