@@ -632,6 +632,37 @@ def tensor_tier_workload(q, torch, dev, stream):
                      "transforms_per_s_256x_n20": 256 / (ms256 / 1e3)}
         del st, ws, bufs, ws20
     torch.cuda.empty_cache()
+    # fused block width f (max_stage_bits) of the FP16x3 tier: error at n = 21
+    # against the oracle, time at n = 21 and n = 28 (f = 7: 3 and 4 passes of 7 wires)
+    n21 = 21
+    x21 = qft_inputs.gaussian(n21, seed=21).astype(np.complex64)
+    ref21, _ = oracle.qft(x21.astype(np.complex128), -1, -1, oracle.SCALE_STATE, True)
+    st28 = torch.empty(1 << 28, dtype=torch.complex64, device=dev)
+    st28.copy_(qft_inputs.device_gaussian(28, 28, "c64", device=str(dev)))
+    widths = {}
+    for f in (4, 5, 6, 7):
+        rec = {}
+        for nn in (n21, 28):
+            p = q.Plan(nn, -1, q.FORWARD, "c64", q.ORDER_NATURAL, precision=q.PREC_FP16X3, max_stage_bits=f)
+            st = torch.from_numpy(x21).to(dev) if nn == n21 else st28
+            ws = p.alloc_workspace(dev)
+            p.execute(st, ws, q.SCALE_STATE, stream=stream)
+            torch.cuda.synchronize()
+            if nn == n21:
+                got = st.cpu().numpy().astype(np.complex128)
+                rec["rel_l2_vs_fp64_oracle_n21"] = float(np.linalg.norm(got - ref21) / np.linalg.norm(ref21))
+            a.record(stream)
+            for _ in range(5):
+                p.execute(st, ws, q.SCALE_STATE, stream=stream)
+            bb.record(stream)
+            torch.cuda.synchronize()
+            rec[f"ms_n{nn}"] = a.elapsed_time(bb) / 5
+            rec[f"wires_per_pass_n{nn}"] = list(p.info().wires_per_pass)[:p.info().passes]
+            del ws
+        widths[f"f{f}"] = rec
+    out["fp16x3_block_widths"] = widths
+    del st28
+    torch.cuda.empty_cache()
     return out
 
 
@@ -723,7 +754,10 @@ def summarize_extra(extra):
     t = extra.get("tensor_tier", {})
     if t:
         out["tensor_tier"] = {k: pick(v, "rel_l2_vs_fp64_oracle_n24", "ms_n24", "transforms_per_s_256x_n20")
-                              for k, v in t.items() if isinstance(v, dict)}
+                              for k, v in t.items() if isinstance(v, dict) and k != "fp16x3_block_widths"}
+        if "fp16x3_block_widths" in t:
+            out["tensor_tier"]["fp16x3_block_widths"] = {
+                k: pick(v, "rel_l2_vs_fp64_oracle_n21", "ms_n21", "ms_n28") for k, v in t["fp16x3_block_widths"].items()}
         if "error" in t:
             out["tensor_tier"]["error"] = t["error"]
     sv = extra.get("serving_poisson", {})
@@ -754,8 +788,8 @@ def run_ours(args, world, rank, local):
                  pass_split=args.pass_split)
     prec = {"native": 0, "tf32": q.PREC_TF32, "bf16": q.PREC_BF16, "bf16x3": q.PREC_BF16X3, "fp16": q.PREC_FP16,
             "fp16x3": q.PREC_FP16X3}[args.precision]
-    if prec:
-        shape = {"precision": prec}
+    if prec:  # with a tensor-core tier, max_stage_bits is the fused block width f
+        shape = {"precision": prec, "max_stage_bits": args.max_stage_bits}
     override = any(shape.values())
     plan = q.Plan(n, k, q.FORWARD, dt, q.ORDER_NATURAL, threads=args.threads, tuned=not override, **shape)
     info = plan.info()

@@ -95,7 +95,11 @@ typedef struct {
                            two register stages of up to 5 wires), so ceil(n / 10) passes;
                            QFT_ERR_UNSUPPORTED where the planner finds no wide shape.   */
     int coalesce_bits;  /* min log2(contiguous amplitudes per HBM run); 0 = default         */
-    int max_stage_bits; /* max wires per register stage (1..4); 0 = default                */
+    int max_stage_bits; /* max wires per register stage (1..5; 1..4 with 512 threads); 0 =
+                           default.  With a tensor-core tier (precision 1..5) it is f, the
+                           widest fused block (4..7; 0 = 6): one block of <= f wires per
+                           pass, 2^12-amplitude tiles for f = 5, 6 and 2^11 for f = 4, 7
+                           (QFT_ERR_BAD_ARG outside 4..7)                                   */
     int wait_limit_ms;  /* bound of every device-side wait; 0 = default (2000 ms)           */
     int test_skip_first_load; /* TEST HOOK, 0 in normal use: 1 = never issue the first
                                  tile load, so the kernel's bounded wait expires and
@@ -106,7 +110,8 @@ typedef struct {
     int precision;      /* QFT_PREC_*: 0 = the default CUDA-core path (complex64 in FP32;
                            complex128 in double-float, see QFT_PREC_FP64); 6 = complex128 in
                            IEEE FP64 arithmetic; 1..5 = complex64 only, each pass's fused
-                           block of <= 6 wires as a dense complex GEMM on the tensor cores
+                           block of <= f wires (max_stage_bits; default 6) as a dense
+                           complex GEMM on the tensor cores
                            (see enum qft_precision).  The block matrices are built and
                            uploaded (plan-owned device memory) by the plan's first execute,
                            which should precede any capture. */

@@ -30,7 +30,7 @@ constexpr int kMaxTileBits = 14;
 constexpr int kMaxSegs = 8;
 constexpr int kMaxPasses = 8;
 constexpr int kMaxDims = 5;
-constexpr int kMaxR = 6;       // wires per block (6 only in the tensor-core tier; table planes)
+constexpr int kMaxR = 7;       // wires per block (6 and 7 only in the tensor-core tier; table planes)
 constexpr int kMaxStageR = 5;  // wires per register stage of the CUDA-core pass kernel
 // The pass kernel runs with 256 threads per CTA (register stages of up to 5
 // wires) or 512 threads (stages of up to 4 wires).

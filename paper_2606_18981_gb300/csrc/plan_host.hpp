@@ -28,6 +28,8 @@ cudaError_t launch_df_maxexp(const void* state, size_t n_amps, int* out, int num
 cudaError_t launch_tc_pass(int dir, int prec, const CUtensorMap& map, const PassParams& P, const void* a_hi,
                            const void* a_lo, int kpad, int ncols, int grid, size_t smem, cudaStream_t st);
 size_t tc_smem_bytes(const PassParams& P, int prec, int kpad, int ncols);
+// true when the pass runs on the fast tensor-core kernel (the only one for 7-wire blocks)
+bool tc_fast_pass(const PassParams& P);
 cudaError_t tc_prepare_a(int prec, const double* d_src, void* d_hi, void* d_lo, int kpad, cudaStream_t st);
 
 // Workspace layout of one transform: [0, 4096) metadata (scale_in at 0,

@@ -608,7 +608,7 @@ int plan_passes(qft_plan_s* pl) {
     for (int w = 0; w < n; ++w) brev[w] = n - 1 - w;
     const bool natural = pl->order == QFT_ORDER_NATURAL;
 
-    if (n <= (pl->precision ? pl->rmax : pl->TB)) {
+    if (n <= (pl->precision ? std::min(pl->rmax, 6) : pl->TB)) {  // a single pass: 2J <= 128 rows
         PassHost ph;
         if (!build_pass(pl, ph, 0, n, {}, ident, natural ? brev : ident, true, true)) return QFT_ERR_UNSUPPORTED;
         ph.prm.load_mode = 1;
@@ -622,6 +622,7 @@ int plan_passes(qft_plan_s* pl) {
     std::vector<int> a;
     if (natural) {
         P = (n + cap - 1) / cap;
+        if (pl->precision && P < 2) P = 2;  // n = 7 with 7-wire blocks: no single 7-wire pass
         a.assign(P, n / P);
         if (pl->pass_split == 1 && P >= 3) {
             // extra wires to the middle passes first: the first and last
@@ -660,7 +661,7 @@ int plan_passes(qft_plan_s* pl) {
         for (int j = 0; j < P; ++j) { top -= a[j]; glo[j] = top; }
     }
     const int c1 = std::min(TB - a[0], glo[0]);
-    int ctop = 0;
+    int ctop = 0, shift = 0;
     std::vector<int> L1 = ident;
     if (natural) {
         ctop = std::min({c1, a[0], TB - a[P - 1], a[P - 1]});
@@ -669,9 +670,19 @@ int plan_passes(qft_plan_s* pl) {
         // the last pass's wires keep forming as few blocks as possible
         if (pl->pass_split == 1) ctop = std::min(ctop, pl->cmin);
         if (ctop < 1) return QFT_ERR_UNSUPPORTED;
-        for (int e = 0; e < ctop; ++e) {
-            L1[n - 1 - e] = e;           // top wires to the lowest addresses (their final place)
-            L1[e] = n - ctop + e;        // lowest wires to the top
+        if (pl->precision && ctop < a[P - 1]) {
+            // the tensor-core tier runs one block per pass, so the last pass's
+            // wires must sit on consecutive addresses: the top wires go
+            // (reversed) to the lowest addresses and every other wire moves
+            // up by ctop
+            shift = ctop;
+            for (int w = 0; w < n - ctop; ++w) L1[w] = w + ctop;
+            for (int e = 0; e < ctop; ++e) L1[n - 1 - e] = e;
+        } else {
+            for (int e = 0; e < ctop; ++e) {
+                L1[n - 1 - e] = e;           // top wires to the lowest addresses (their final place)
+                L1[e] = n - ctop + e;        // lowest wires to the top
+            }
         }
     }
     for (int j = 0; j < P; ++j) {
@@ -684,7 +695,7 @@ int plan_passes(qft_plan_s* pl) {
             for (int w = 0; w < c1; ++w) batch.push_back(w);
             Lout = natural ? L1 : ident;
         } else if (!last) {
-            const int cj = std::min(TB - a[j], glo[j]);
+            const int cj = std::min(TB - a[j], glo[j] + shift);
             std::vector<int> wat(na);
             for (int w = 0; w < na; ++w) wat[Lin[w]] = w;
             for (int adr = 0; adr < cj; ++adr) batch.push_back(wat[adr]);
@@ -791,7 +802,9 @@ int check_tensor_passes(qft_plan_s* pl) {
         ph.tc_kpad = std::max(kstep, (2 * J + kstep - 1) / kstep * kstep);
         const int ng = 1 << P.st[0].ngbits;
         ph.tc_ncols = std::max(16, (ng + 15) / 16 * 16);
-        if (ph.tc_ncols > 256 || 2 * J > 128) return QFT_ERR_UNSUPPORTED;
+        // 7-wire blocks (2J = 256 > 128 rows) only on the fast kernel, whose
+        // B operand carries the real embedding
+        if (ph.tc_ncols > 256 || (2 * J > 128 && !tc_fast_pass(P))) return QFT_ERR_UNSUPPORTED;
         ph.smem = tc_smem_bytes(P, pl->precision, ph.tc_kpad, ph.tc_ncols);
         if (ph.smem > 227 * 1024 - 4096) return QFT_ERR_UNSUPPORTED;
         // the tensor-core kernels run one CTA per SM (each holds all 512 TMEM columns)
@@ -846,6 +859,11 @@ int prepare_tensor_passes(qft_plan_s* pl) {
         for (int jo = 0; jo < J; ++jo)
             for (int ji = 0; ji < J; ++ji) {
                 const double fr = Fre[size_t(jo) * J + ji], fi = Fim[size_t(jo) * J + ji];
+                if (2 * J > 128) {  // [Re F | Im F]; the kernel's B operand holds [Re x; -Im x] and [Im x; Re x]
+                    A[size_t(jo) * kpad + ji] = fr;
+                    A[size_t(jo) * kpad + J + ji] = fi;
+                    continue;
+                }
                 A[size_t(jo) * kpad + ji] = fr;
                 A[size_t(jo) * kpad + J + ji] = -fi;
                 A[size_t(J + jo) * kpad + ji] = fi;
@@ -984,9 +1002,16 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
         } else if (opts->precision != QFT_PREC_NATIVE) {
             if (dtype != QFT_C64) { delete pl; return QFT_ERR_UNSUPPORTED; }
             pl->precision = opts->precision;
-            pl->TB = 12;   // 2^12-amplitude tiles: 64 columns of one 6-wire block
-            pl->cmin = 6;
-            pl->rmax = 6;  // one block per pass
+            // one fused block of <= f wires per pass, f = max_stage_bits (4..7;
+            // 0 = 6): 2^12-amplitude tiles for f = 5, 6 (2^(12-r) GEMM columns
+            // per r-wire block); 2^11 for f = 7, whose operands need the shared
+            // memory of the other half, and for f = 4, whose 3-wire blocks
+            // would otherwise exceed the 256 columns of one MMA
+            const int f = opts->max_stage_bits ? opts->max_stage_bits : 6;
+            if (f < 4 || f > 7) { delete pl; return QFT_ERR_BAD_ARG; }
+            pl->TB = (f == 7 || f == 4) ? 11 : 12;
+            pl->cmin = pl->TB - f;
+            pl->rmax = f;
         }
         if (opts->wait_limit_ms < 0) { delete pl; return QFT_ERR_BAD_ARG; }
         if (opts->wait_limit_ms) pl->wait_limit_ns = uint64_t(opts->wait_limit_ms) * 1000000ull;
@@ -1001,7 +1026,7 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
         if (opts->paired) { delete pl; return QFT_ERR_UNSUPPORTED; }
         if (opts->pass_split < 0 || opts->pass_split > 2) { delete pl; return QFT_ERR_BAD_ARG; }
         pl->pass_split = opts->pass_split == 1 ? 1 : 0;
-        if (opts->max_stage_bits) {
+        if (opts->max_stage_bits && !pl->precision) {
             rmax_given = true;
             if (opts->max_stage_bits < 1 || opts->max_stage_bits > (pl->threads == 512 ? 4 : kMaxStageR)) {
                 delete pl;

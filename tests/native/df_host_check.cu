@@ -117,6 +117,25 @@ int main() {
         check(wd <= std::ldexp(1.0, -45), "df_dot2 error / (|ab|+|cd|)", wd, std::ldexp(1.0, -45));
         check(wm <= std::ldexp(1.0, -45), "df_mul relative error", wm, std::ldexp(1.0, -45));
     }
+    // 8. dc_mul (complex product v w, each component a df_dot2p): error of a
+    //    component <= 2^-45 times the sum of its two products' magnitudes
+    {
+        double wc = 0;
+        for (int i = 0; i < 200000; ++i) {
+            auto rnd = [&]() {
+                const double d = std::ldexp(u(rng), ex(rng) / 4);
+                return qft::df_norm(qft::df_from_double_shift(d, 0));
+            };
+            const qft::dcomplex v = qft::dc_make(rnd(), rnd()), w = qft::dc_make(rnd(), rnd());
+            const long double vr = val(v.re()), vi = val(v.im()), wr = val(w.re()), wi = val(w.im());
+            const qft::dcomplex z = qft::dc_mul(v, w);
+            const long double re = wr * vr - wi * vi, im = wr * vi + wi * vr;
+            const long double sre = std::fabs(wr * vr) + std::fabs(wi * vi), sim = std::fabs(wr * vi) + std::fabs(wi * vr);
+            wc = std::fmax(wc, (double)(std::fabs(val(z.re()) - re) / sre));
+            wc = std::fmax(wc, (double)(std::fabs(val(z.im()) - im) / sim));
+        }
+        check(wc <= std::ldexp(1.0, -45), "dc_mul component error / (sum |products|)", wc, std::ldexp(1.0, -45));
+    }
     std::printf(g_fail ? "FAILED %d\n" : "ALL OK\n", g_fail);
     return g_fail ? 1 : 0;
 }

@@ -14,7 +14,7 @@ from __future__ import annotations
 
 import numpy as np
 
-K_MAX_STAGES, K_MAX_TILE_BITS, K_MAX_SEGS, K_MAX_DIMS, K_MAX_R = 8, 14, 8, 5, 6
+K_MAX_STAGES, K_MAX_TILE_BITS, K_MAX_SEGS, K_MAX_DIMS, K_MAX_R = 8, 14, 8, 5, 7
 
 
 def parse(rec):

@@ -10,7 +10,8 @@ Relative L2 bounds against the oracle (n <= 24):
   * single-operand tiers: TF32 and FP16 keep 11 bits, BF16 8 bits.
 Element by element each tier also meets the bound of tests/parity.py with
 its operand format's unit roundoff in place of FP32's (2^-22 FP16x3, 2^-16
-BF16x3, 2^-11 TF32 / FP16, 2^-8 BF16).
+BF16x3, 2^-11 TF32 / FP16, 2^-8 BF16).  The same bounds hold for every fused
+block width f = 4..7 (7-wire blocks put the real embedding in the B operand).
 """
 import numpy as np
 import pytest
@@ -29,8 +30,8 @@ EPS = {q.PREC_FP16X3: 2.0 ** -22, q.PREC_BF16X3: 2.0 ** -16, q.PREC_TF32: 2.0 **
        q.PREC_BF16: 2.0 ** -8}
 
 
-def run(x, n, k, prec, order=0, direction=-1, mode=0, shape=False):
-    p = q.Plan(n, k, direction, "c64", order, precision=prec)
+def run(x, n, k, prec, order=0, direction=-1, mode=0, shape=False, f=0):
+    p = q.Plan(n, k, direction, "c64", order, precision=prec, max_stage_bits=f)
     st = torch.from_numpy(x).to(torch.complex64).cuda()
     ws = p.alloc_workspace()
     p.execute(st, ws, mode)
@@ -75,4 +76,40 @@ def test_tier_index_maps_bit_exact():
         h *= 2
     rev = np.array([int(format(i, f"0{n}b")[::-1], 2) for i in range(1 << n)])
     got = run(xi, n, 0, q.PREC_FP16X3, 0, -1, q.SCALE_UNNORM)
+    assert np.array_equal(got, w[rev])
+
+
+@pytest.mark.parametrize("prec", [q.PREC_FP16X3, q.PREC_TF32, q.PREC_BF16])
+@pytest.mark.parametrize("f,n,k,order", [(4, 13, -1, 0), (4, 20, 8, 1), (5, 16, -1, 0), (7, 14, -1, 0),
+                                         (7, 20, 4, 0), (7, 21, -1, 0), (7, 21, -1, 1)])
+def test_tier_block_widths_vs_oracle(oracle_mod, prec, f, n, k, order):
+    """Fused blocks of up to f wires (max_stage_bits = f), in both orders."""
+    x = qft_inputs.gaussian(n, seed=50 + n).astype(np.complex64).astype(np.complex128)
+    got, (a_last, natural) = run(x, n, k, prec, order=order, shape=True, f=f)
+    ref, _ = oracle_mod.qft(x, k, -1, 0, order == 0)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    ratio = np.max(np.abs(got - ref) / elementwise_bound(ref, "c64", n, a_last, natural, eps=EPS[prec]))
+    print(f"tier {prec} f={f} n={n} k={k} order={order}: rel L2 {err:.3e}, element ratio {ratio:.3f}")
+    assert err <= BOUND[prec]
+    assert ratio <= 1.0
+
+
+@pytest.mark.parametrize("n", [14, 21])
+def test_tier_seven_wire_blocks_bit_exact(n):
+    """k = 0 with 7-wire blocks: the integer Walsh-Hadamard transform and the
+    qubit reversal, bit for bit, through the B-side embedding [Re; -Im],
+    [Im; Re] of the 7-wire GEMM."""
+    rng = np.random.default_rng(n)
+    xi = (rng.integers(-3, 4, size=1 << n) + 1j * rng.integers(-3, 4, size=1 << n)).astype(np.complex128)
+    w = xi.copy()
+    h = 1
+    while h < w.size:
+        w = w.reshape(-1, 2, h)
+        w = np.stack([w[:, 0] + w[:, 1], w[:, 0] - w[:, 1]], axis=1).reshape(-1)
+        h *= 2
+    idx = np.arange(1 << n)
+    rev = np.zeros_like(idx)
+    for b in range(n):
+        rev |= ((idx >> b) & 1) << (n - 1 - b)
+    got = run(xi, n, 0, q.PREC_FP16X3, 0, -1, q.SCALE_UNNORM, f=7)
     assert np.array_equal(got, w[rev])

@@ -74,6 +74,36 @@ def test_emulated_tensor_tier_plans(oracle_mod, n, prec):
         assert rel_l2(got, ref) < 1e-12
 
 
+@pytest.mark.parametrize("f,n", [(4, 9), (4, 13), (5, 13), (5, 16), (7, 7), (7, 12), (7, 13), (7, 14), (7, 16),
+                                 (7, 20), (7, 21)])
+@pytest.mark.parametrize("prec", [1, 5])
+def test_emulated_tensor_tier_block_widths(oracle_mod, f, n, prec):
+    """Tier plans of fused blocks of <= f wires (max_stage_bits = f): every pass
+    is one block of <= f wires, f = 7 plans do run 7-wire blocks where n
+    allows, and the replayed plan matches the oracle in both orders."""
+    x = qft_inputs.gaussian(n, seed=400 + n, normalise=False)
+    for order in (q.ORDER_NATURAL, q.ORDER_BITREV):
+        p = q.Plan(n, -1 if n % 2 else 5, q.FORWARD, "c64", order, precision=prec, max_stage_bits=f)
+        rs = []
+        for i in range(p.info().passes):
+            P = parse(p.describe_pass(i))
+            assert P["nstages"] == 1 and P["st"][0]["r"] <= f
+            assert P["tb"] == (11 if f in (4, 7) else 12) or P["tb"] == n
+            rs.append(P["st"][0]["r"])
+        if f == 7 and n in (13, 14, 20, 21):
+            assert 7 in rs
+        got = emulate(p, x, q.SCALE_STATE)
+        ref, _ = oracle_mod.qft(x, k=p.k, sign=-1, mode=0, natural_order=(order == q.ORDER_NATURAL))
+        assert rel_l2(got, ref) < 1e-12
+
+
+def test_tensor_tier_block_width_range():
+    for f in (1, 3, 8):
+        with pytest.raises(q.QftError) as e:
+            q.Plan(20, precision=q.PREC_FP16X3, max_stage_bits=f)
+        assert e.value.code == q.ERR_BAD_ARG
+
+
 def test_tensor_tier_rejects_complex128():
     with pytest.raises(q.QftError) as e:
         q.Plan(20, dtype="c128", precision=q.PREC_FP16X3)
