@@ -880,8 +880,20 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         barrier()
         e_ms_max, e_value = whole_job_rate(a.elapsed_time(b) / e_steps, N, world, dev)
+        # the host link alone: one pinned copy of the state each way, and both at once
+        link = {}
+        for label, fn in (("h2d_gbs", lambda: states[1].copy_(host_in, non_blocking=True)),
+                          ("d2h_gbs", lambda: host_out[1].copy_(states[1], non_blocking=True))):
+            with torch.cuda.stream(s_in):
+                fn()
+                a.record(s_in)
+                fn()
+                b.record(s_in)
+            torch.cuda.synchronize()
+            link[label] = N * eb / (a.elapsed_time(b) / 1e3) / 1e9
         e2e = {"value": e_value, "unit": UNIT, "ms_per_step": e_ms_max,
                "h2d_bytes_per_step": N * eb, "d2h_bytes_per_step": N * eb, "steps": e_steps,
+               "link_gbs_per_step": 2 * N * eb / (e_ms_max / 1e3) / 1e9, "host_link_alone": link,
                "pipeline": "two steps in flight on three streams: H2D of step k+1 and D2H of step k-1 overlap the compute of step k"}
         del host_in, host_out, states, wss
 

@@ -30,7 +30,7 @@ CANDIDATES = {
         (0, 0, 0, 0, 0, 0), (14, 0, 0, 0, 0, 0), (13, 4, 5, 256, 0, 0), (13, 3, 5, 256, 0, 0),
         (13, 5, 5, 256, 0, 0), (13, 4, 4, 512, 0, 0), (12, 4, 4, 256, 0, 0), (12, 3, 4, 256, 0, 0),
         (12, 5, 4, 256, 0, 0), (12, 4, 3, 256, 0, 0), (11, 4, 4, 256, 0, 0), (12, 4, 4, 256, 0, 1),
-        (13, 4, 5, 256, 0, 1), (12, 4, 3, 512, 0, 1), (12, 4, 3, 512, 0, 0))],
+        (13, 4, 5, 256, 0, 1))],
     "c128": [dict(zip(_KEYS, c)) for c in (
         (0, 0, 0, 0, 0, 0), (12, 3, 4, 256, 0, 0), (11, 3, 4, 256, 0, 0), (12, 2, 4, 256, 0, 0),
         (12, 4, 4, 256, 0, 0), (12, 3, 4, 256, 0, 1), (12, 3, 3, 256, 0, 0), (12, 3, 3, 512, 0, 0),

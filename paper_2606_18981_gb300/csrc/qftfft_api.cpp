@@ -298,9 +298,6 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
     if (pl->dtype == QFT_C64 && pl->threads == 256 && maxr <= 4 &&
         2 * (ph.smem + 3 * 1024) <= 228 * 1024)
         ph.minb = 2;
-    // 512 threads, two CTAs per SM (32 warps, 64 registers per thread): blocks of <= 3 wires
-    if (pl->dtype == QFT_C64 && pl->threads == 512 && maxr <= 3 && 2 * (ph.smem + 3 * 1024) <= 228 * 1024)
-        ph.minb = 2;
     const int64_t tiles = P.num_tiles;
     ph.grid = static_cast<int>(std::min<int64_t>(tiles, int64_t(pl->num_sms) * ph.minb));
     return true;

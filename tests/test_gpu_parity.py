@@ -364,7 +364,7 @@ VARIANTS = {
     "two_ctas_c3": dict(tile_bits=12, coalesce_bits=3),
     "tile11": dict(tile_bits=11),
     "wide": dict(tile_bits=14),
-    "t512_two_ctas": dict(tile_bits=12, coalesce_bits=4, threads=512, max_stage_bits=3),
+    "t512_blocks3": dict(tile_bits=12, coalesce_bits=4, threads=512, max_stage_bits=3),
     "split_middle": dict(tile_bits=12, coalesce_bits=4, pass_split=1),
 }
 
