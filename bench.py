@@ -433,13 +433,14 @@ def batched_workload(q, torch, dev, stream, count=4096, seed=3, reps=5, variants
 
 
 def serving_workload(q, torch, dev, rates=(100, 1000, 5000, 10000, 20000, 50000), per_rate=400, seed=5,
-                     compare_unbatched_at=5000):
+                     compare_unbatched_at=5000, c64_only_rates=(5000, 10000, 20000, 50000)):
     """The serving configuration: Poisson arrivals at each rate, n with
     P(n) proportional to 1/n over 10..28, dtype uniform in {complex64,
     complex128}, k uniform in {exact, 4, 8, 16}, direction uniform; inputs
     and outputs resident on the device; HBM admission budget 120 GB.  Small
     requests (n <= 18) are continuously batched; at one rate the same stream
-    is also served with batching off."""
+    is also served with batching off, and at the higher rates a complex64-only
+    stream (the same mix otherwise) shows the saturation of that part alone."""
     import numpy as np
 
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -458,10 +459,11 @@ def serving_workload(q, torch, dev, rates=(100, 1000, 5000, 10000, 20000, 50000)
             t = srv.submit(inputs[(int(n), dt)], outputs[(int(n), dt)], int(n), -1, q.FORWARD, dt)
             srv.wait(t)
     res = {}
-    runs = [(rate, True) for rate in rates]
+    runs = [(rate, True, False) for rate in rates]
     if compare_unbatched_at:
-        runs.append((compare_unbatched_at, False))
-    for rate, batching in runs:
+        runs.append((compare_unbatched_at, False, False))
+    runs += [(rate, True, True) for rate in c64_only_rates]
+    for rate, batching, c64_only in runs:
         srv.set_batching(18 if batching else 0)
         srv.reset_stats()
         rng = np.random.Generator(np.random.PCG64(seed * 100003 + rate))  # the same requests with and without batching
@@ -475,6 +477,8 @@ def serving_workload(q, torch, dev, rates=(100, 1000, 5000, 10000, 20000, 50000)
                 pass
             n = int(rng.choice(ns, p=pn))
             dt = ("c64", "c128")[int(rng.integers(0, 2))]
+            if c64_only:
+                dt = "c64"
             k = int(rng.choice([-1, 4, 8, 16]))
             direction = (q.FORWARD, q.INVERSE)[int(rng.integers(0, 2))]
             tickets.append(srv.submit(inputs[(n, dt)], outputs[(n, dt)], n, k, direction, dt))
@@ -484,7 +488,7 @@ def serving_workload(q, torch, dev, rates=(100, 1000, 5000, 10000, 20000, 50000)
             bad += rc != 0
         wall = time.perf_counter() - t0
         st = srv.stats()
-        key = f"{rate}_req_per_s" + ("" if batching else "_unbatched")
+        key = f"{rate}_req_per_s" + ("" if batching else "_unbatched") + ("_c64_only" if c64_only else "")
         res[key] = {"offered_req_per_s": rate, "requests": per_rate, "failed": bad,
                     "served_req_per_s": per_rate / wall, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
                     "max_ms": st.max_ms, "batches": st.batches, "batched_requests": st.batched_requests}

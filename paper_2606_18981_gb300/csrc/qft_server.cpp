@@ -9,7 +9,7 @@
 //   * Small requests (n <= the batching limit, 18 by default) join the batch
 //     that is forming for their (dtype, direction, scale mode); on every pass
 //     of the worker loop each forming batch whose slot is free is launched as
-//     one persistent batched launch (the a9 kernel) on a high-priority stream:
+//     one persistent batched launch (qft_batch_kernel) on a high-priority stream:
 //     copy-ins, the batch, copy-outs, one read-back of the scale_in values and
 //     the status word, an event.  Requests that arrive while batches run are
 //     admitted into the next ones as slots and memory free up.
