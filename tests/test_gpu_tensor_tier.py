@@ -53,11 +53,12 @@ def test_tier_error_vs_oracle(oracle_mod, prec, n, k):
     assert ratio <= 1.0
 
 
-@pytest.mark.parametrize("order,direction,mode", [(1, -1, 0), (0, 1, 2), (0, -1, 1)])
-def test_tier_orders_directions_scales(oracle_mod, order, direction, mode):
-    n = 16
+@pytest.mark.parametrize("f", [6, 7])
+@pytest.mark.parametrize("order,direction,mode", [(1, -1, 0), (0, 1, 2), (0, -1, 1), (1, 1, 3)])
+def test_tier_orders_directions_scales(oracle_mod, order, direction, mode, f):
+    n = 16 if f == 6 else 14
     x = qft_inputs.tones(n, seed=4).astype(np.complex64).astype(np.complex128)
-    got = run(x, n, -1, q.PREC_FP16X3, order, direction, mode)
+    got = run(x, n, -1, q.PREC_FP16X3, order, direction, mode, f=f)
     ref, _ = oracle_mod.qft(x, -1, direction, mode, order == 0)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= BOUND[q.PREC_FP16X3]
 
