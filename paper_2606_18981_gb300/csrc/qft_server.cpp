@@ -13,9 +13,11 @@
 //     copy-ins, the batch, copy-outs, one read-back of the scale_in values and
 //     the status word, an event.  Requests that arrive while batches run are
 //     admitted into the next ones as slots and memory free up.
-//   * Larger requests run their own passes (copy-in, qft_execute, copy-out) on
-//     the least-loaded of the normal-priority streams; the high-priority
-//     batches are scheduled between those passes.
+//   * Larger requests run their own passes on the least-loaded of the
+//     normal-priority streams (the high-priority batches are scheduled between
+//     those passes): out of place from the caller's input into its output when
+//     both are device buffers (then the request holds only a workspace), else
+//     copy-in, qft_execute, copy-out through a pooled state buffer.
 // Completion is detected by polling events; buffers go back to the pool and
 // each request's latency (submit to completion) is recorded.  Server batches
 // use one fixed kernel shape (one 256-thread CTA per SM), and a transform's
@@ -62,6 +64,7 @@ struct InFlight {
     double* h_slot = nullptr;  // pinned 16-byte slot: scale_in (double) then the status word (int)
     int slot = 0;
     size_t reserve = 0;  // batched requests: their share of the batch workspace, held in the budget
+    bool direct = false; // single request run from the caller's input into its output (no copies)
 };
 
 struct Result {
@@ -120,6 +123,15 @@ namespace {
 
 size_t request_bytes(qft_plan_t p) {
     return ((size_t(1) << p->n) * p->esize + 255) / 256 * 256 + (qft_workspace_size(p) + 255) / 256 * 256;
+}
+
+// A single request whose input and output are both device buffers at 256-byte
+// alignment runs out of place straight from the input into the output: its
+// first pass reads the caller's input, its last pass writes the caller's
+// output, and it needs only a workspace (no state buffer and no copies).
+bool direct_path(const qft_request& r) {
+    return r.input_on_device && r.output_on_device && !(reinterpret_cast<uintptr_t>(r.input) & 255) &&
+           !(reinterpret_cast<uintptr_t>(r.output) & 255);
 }
 
 // Device buffer of at least `bytes` from the pool (an idle buffer of up to
@@ -262,6 +274,14 @@ int issue(qft_server_s* s, InFlight& f) {
     const size_t N = size_t(1) << r.n;
     const size_t sbytes = N * f.plan->esize;
     cudaStream_t st = s->streams[f.stream];
+    if (f.direct) {
+        const int rc = qft_execute_oop(f.plan, r.input, r.output, f.ws, nullptr, r.scale_mode,
+                                       reinterpret_cast<qft_stream_t>(st));
+        if (rc != QFT_OK) return rc;
+        cudaError_t e = cudaMemcpyAsync(f.h_slot, f.ws, 16, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaEventRecord(f.done, st);
+        return e == cudaSuccess ? QFT_OK : qft::set_cuda_error(e);
+    }
     cudaError_t e = cudaMemcpyAsync(f.state, r.input, sbytes,
                                     r.input_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return qft::set_cuda_error(e);
@@ -346,7 +366,9 @@ void worker_loop(qft_server_s* s) {
             qft_plan_t p = get_plan(s, rq.r);
             if (!p) { finish(s, rq, QFT_ERR_BAD_ARG, 0.0); s->pending.pop_front(); s->cv_done.notify_all(); continue; }
             const bool small = batchable(s, p);
-            const size_t bytes = small ? state_bytes(p) : request_bytes(p);
+            const bool direct = !small && direct_path(rq.r);
+            const size_t bytes = small ? state_bytes(p)
+                                       : direct ? (qft_workspace_size(p) + 255) / 256 * 256 : request_bytes(p);
             const size_t reserve = small ? qft::batch_transform_workspace_bytes(p) + 256 : 0;
             if (bytes + reserve > s->budget) { finish(s, rq, QFT_ERR_BUDGET, 0.0); s->pending.pop_front(); s->cv_done.notify_all(); continue; }
             if (s->in_use + bytes + reserve > s->budget) break;  // wait for memory to free up (keeps arrival order)
@@ -371,7 +393,8 @@ void worker_loop(qft_server_s* s) {
                 s->forming_count += 1;
                 continue;
             }
-            f.ws = static_cast<char*>(f.state) + state_bytes(p);
+            f.direct = direct;
+            f.ws = direct ? static_cast<char*>(f.state) : static_cast<char*>(f.state) + state_bytes(p);
             f.stream = static_cast<int>(std::min_element(s->stream_load.begin(), s->stream_load.end()) - s->stream_load.begin());
             f.slot = s->free_slots.back();
             s->free_slots.pop_back();

@@ -88,6 +88,40 @@ def test_results_alone_equal_results_in_the_mix():
     srv.close()
 
 
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_device_requests_run_out_of_place_with_the_same_bits(dt):
+    """A large request whose input and output are device buffers at 256-byte
+    alignment runs from the input straight into the output (no state buffer,
+    no copies); its result is bit for bit the one of the same request through
+    pinned host buffers (copy-in, execute, copy-out) and through misaligned
+    device buffers (which take the copy path)."""
+    td = torch.complex64 if dt == "c64" else torch.complex128
+    srv = q.Server(8 << 30, streams=2, max_inflight=8)
+    for n, k, direction, order, mode in [(20, -1, -1, 0, 0), (22, 8, 1, 0, 2), (21, -1, -1, 1, 1)]:
+        x = torch.from_numpy(qft_inputs.make("gaussian", n, 300 + n)).to(td)
+        xd = x.cuda()
+        od = torch.empty(1 << n, dtype=td, device="cuda")
+        xh = x.pin_memory()
+        oh = torch.empty(1 << n, dtype=td).pin_memory()
+        big_in = torch.empty((1 << n) + 1, dtype=td, device="cuda")
+        big_out = torch.empty((1 << n) + 1, dtype=td, device="cuda")
+        xm, om = big_in[1:], big_out[1:]  # one element off: not 256-byte aligned
+        xm.copy_(xd)
+        got = []
+        for a, b in ((xd, od), (xh, oh), (xm, om)):
+            t = srv.submit(a, b, n, k, direction, dt, order, mode)
+            rc, _, scale = srv.wait(t, 60000)
+            assert rc == 0
+            got.append((b.cpu(), scale))
+        assert torch.equal(xd.cpu(), x)  # the input is left as it was
+        for b, sc in got[1:]:
+            assert torch.equal(got[0][0], b) and got[0][1] == sc
+        ref, s_ref = alone(x, n, k, direction, dt, order, mode)
+        assert rel(got[0][0].cuda(), ref) <= TOL[dt](n)
+    assert srv.stats().bytes_in_use == 0
+    srv.close()
+
+
 def test_small_requests_share_batched_launches():
     """Requests of n <= 18 submitted together run in batched launches that
     carry several requests each; with batching off none are batched; the
