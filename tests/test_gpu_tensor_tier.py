@@ -114,3 +114,39 @@ def test_tier_seven_wire_blocks_bit_exact(n):
         rev |= ((idx >> b) & 1) << (n - 1 - b)
     got = run(xi, n, 0, q.PREC_FP16X3, 0, -1, q.SCALE_UNNORM, f=7)
     assert np.array_equal(got, w[rev])
+
+
+@pytest.mark.parametrize("f", [6, 7])
+def test_tier_full_size_sampled_bins(oracle_mod, f):
+    """n = 28 on the FP16x3 tier (f = 7: four passes of 7-wire blocks): an
+    input of 2^16 Gaussian amplitudes at random positions (zero elsewhere), so
+    the oracle's DFT definition over the nonzeros gives 64 output bins exactly;
+    each within the element-wise bound with the tier's unit roundoff (a flat
+    spectrum: no peak term), and the output norm."""
+    n = 28
+    N = 1 << n
+    free, _ = torch.cuda.mem_get_info()
+    if free < 3 * N * 8 + (4 << 30):
+        pytest.skip("not enough device memory")
+    p = q.Plan(n, -1, q.FORWARD, "c64", q.ORDER_NATURAL, precision=q.PREC_FP16X3, max_stage_bits=f)
+    rng = np.random.default_rng(100 + f)
+    idx = np.unique(rng.integers(0, N, size=1 << 16))
+    vals = (rng.standard_normal(idx.size) + 1j * rng.standard_normal(idx.size)).astype(np.complex64)
+    state = torch.zeros(N, dtype=torch.complex64, device="cuda")
+    state[torch.from_numpy(idx).cuda()] = torch.from_numpy(vals).cuda()
+    ws = p.alloc_workspace()
+    p.execute(state, ws, q.SCALE_UNITARY)
+    assert p.status(ws) == 0
+    ys = np.unique(np.concatenate([[0, 1, N - 1, N >> 1], rng.integers(0, N, size=80)]))[:64]
+    got = state[torch.from_numpy(ys).cuda()].cpu().numpy().astype(np.complex128)
+    vals = vals.astype(np.complex128)
+    ref = oracle_mod.dft_bins_sparse(idx, vals, n, ys, q.FORWARD) / np.sqrt(N)
+    norm = float(np.linalg.norm(vals))
+    bound = 8 * EPS[q.PREC_FP16X3] * n * (np.abs(ref) + norm / np.sqrt(N))
+    ratio = np.abs(got - ref) / bound
+    print(f"tier f={f} n={n}: worst bin ratio {ratio.max():.3f}")
+    assert ratio.max() <= 1.0
+    total = float(sum(torch.linalg.vector_norm(c.to(torch.complex128)) ** 2 for c in state.split(1 << 24)) ** 0.5)
+    assert abs(total - norm) <= BOUND[q.PREC_FP16X3] * norm
+    del state, ws
+    torch.cuda.empty_cache()
