@@ -23,6 +23,12 @@ Functions:
   dft_bins_sparse(idx, vals, n, ys, sign)
                                output bins of the Sec. 2 DFT of an input with
                                few nonzeros, summed over the nonzeros only
+  mc_sample(x, u)              Sec. 6 Monte Carlo backend: importance-sampled input
+                               indices and weights for given uniforms
+  mc_bins(idx, w, n, ys, k, sign)
+                               per output bin: the sample mean of the path
+                               amplitudes, the unbiased power estimate, the
+                               standard error
   gate_counts(n, k)            Table 2
   gate_list(n, k)              Fig. 1
   fidelity(a, b), leakage(...) Sec. 4 accuracy measures
@@ -89,6 +95,11 @@ def _load():
         lib.oracle_apply_gate.restype = None
         lib.oracle_bit_reverse.argtypes = [ctypes.c_int64, ctypes.c_int]
         lib.oracle_bit_reverse.restype = ctypes.c_int64
+        lib.oracle_mc_sample.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int64, i64p, dp]
+        lib.oracle_mc_sample.restype = ctypes.c_uint64
+        lib.oracle_mc_bins.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p, dp, ctypes.c_int64, i64p,
+                                       ctypes.c_int, dp]
+        lib.oracle_mc_bins.restype = None
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
@@ -269,3 +280,37 @@ def leakage(approx, exact) -> float:
     ystar = int(np.argmax(np.abs(np.asarray(exact).ravel())))
     tot = np.vdot(approx, approx).real
     return float(1.0 - abs(approx[ystar]) ** 2 / tot) if tot > 0 else 0.0
+
+
+def mc_sample(x, u):
+    """Sec. 6 Monte Carlo backend, sampling step: for each uniform u_m in [0, 1)
+    (a multiple of 2^-53) the input index j_m drawn with probability
+    q_j / T (q_j = ceil(|x_j| 2^(62-n) / max|x|), T = sum q) and its weight
+    w_m = x_j T / q_j.  Returns (idx int64, w complex128, T)."""
+    lib = _load()
+    x = _as_c128(x)
+    n = _log2_exact(x.size)
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    idx = np.empty(u.size, dtype=np.int64)
+    w = np.empty(u.size, dtype=np.complex128)
+    T = lib.oracle_mc_sample(n, _dptr(x), u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(u.size),
+                             idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(w))
+    return idx, w, int(T)
+
+
+def mc_bins(idx, w, n: int, ys, k: int = -1, sign: int = FORWARD):
+    """Sec. 6 Monte Carlo backend, estimation step: per output bin y of the
+    range-k transform (natural order) the mean of z_m = w_m e^{sign 2 pi i
+    phase(j_m, y)/N} / sqrt(N) (an unbiased estimate of <y|U_k|x>), the
+    unbiased power estimate (|sum z|^2 - sum |z|^2) / (M (M-1)) and the
+    standard error of the mean.  Returns (amp complex128, power, stderr)."""
+    lib = _load()
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    w = _as_c128(w)
+    ys = np.ascontiguousarray(np.asarray(ys, dtype=np.int64))
+    out = np.empty(4 * ys.size, dtype=np.float64)
+    lib.oracle_mc_bins(int(n), int(k), int(sign), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(w),
+                       int(idx.size), ys.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(ys.size),
+                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    out = out.reshape(-1, 4)
+    return out[:, 0] + 1j * out[:, 1], out[:, 2], out[:, 3]

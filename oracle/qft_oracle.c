@@ -334,3 +334,100 @@ int oracle_gate_list(int n, int k, int natural_order, int *gates, int cap)
 
 /* Bit reversal of an n-bit index (exposed for the tests' index-map checks). */
 int64_t oracle_bit_reverse(int64_t i, int n) { return bit_reverse(i, n); }
+
+/* ------------------------------------ Monte Carlo sum over histories (Sec. 6)
+ *
+ * Sec. 6 proposes a Monte Carlo backend "in the sum-over-histories style": the
+ * amplitude <y|U_k|x> is a sum over input indices j of x_j times the phase the
+ * kept controlled rotations give the path j -> y, and sampling input indices
+ * with importance weights gives unbiased estimates of single output bins and
+ * of the power spectrum.  Readings (the passage gives no formulas):
+ *   - the proposal is p_j proportional to |x_j| (the magnitude of term j),
+ *     made exact in integers: q_j = ceil(|x_j| 2^S / max_j |x_j|) with
+ *     S = 62 - n (q_j >= 1 whenever x_j != 0, so no nonzero term is left out
+ *     and the estimator stays unbiased), T = sum_j q_j, p_j = q_j / T;
+ *   - a uniform u in [0, 1), a multiple of 2^-53, selects the target
+ *     t = floor(u 2^53 T / 2^53) in [0, T) and the index j with
+ *     C_{j-1} <= t < C_j, C the inclusive prefix sums of q;
+ *   - the sample's weight is w = x_j T / q_j (= x_j / p_j), so that
+ *     z = w exp(s 2 pi i phase(j, y) / N) / sqrt(N) has mean <y|U_k|x>;
+ *   - per bin: the mean of z over the M samples, the unbiased estimate
+ *     (|sum z|^2 - sum |z|^2) / (M (M - 1)) of |<y|U_k|x>|^2, and the
+ *     standard error sqrt((sum |z|^2 / M - |mean|^2) / (M - 1)) of the mean.
+ * |x_j| is sqrt(re^2 + im^2) in FP64 without contraction (this file is built
+ * with -ffp-contract=off). */
+
+/* Importance sampling of M input indices: idx[m] and the complex weight
+ * w[2m], w[2m+1] for the uniform u[m].  Returns T (0 for a zero input: then
+ * every index is 0 and every weight 0). */
+uint64_t oracle_mc_sample(int n, const double *x, const double *u, int64_t m, int64_t *idx, double *w)
+{
+    const int64_t N = (int64_t)1 << n;
+    double mx = 0.0;
+    for (int64_t j = 0; j < N; j++) {
+        const double a = sqrt(x[2 * j] * x[2 * j] + x[2 * j + 1] * x[2 * j + 1]);
+        if (a > mx) mx = a;
+    }
+    if (mx == 0.0) {
+        for (int64_t i = 0; i < m; i++) { idx[i] = 0; w[2 * i] = 0.0; w[2 * i + 1] = 0.0; }
+        return 0;
+    }
+    const double scale = ldexp(1.0, 62 - n) / mx;
+    uint64_t *C = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
+    if (!C) return 0;
+    uint64_t acc = 0;
+    for (int64_t j = 0; j < N; j++) {
+        const double a = sqrt(x[2 * j] * x[2 * j] + x[2 * j + 1] * x[2 * j + 1]);
+        const uint64_t q = a > 0.0 ? (uint64_t)ceil(a * scale) : 0;
+        acc += q;
+        C[j] = acc;
+    }
+    const uint64_t T = acc;
+    for (int64_t i = 0; i < m; i++) {
+        const uint64_t u53 = (uint64_t)(u[i] * 9007199254740992.0); /* u * 2^53, exact */
+        const uint64_t t = (uint64_t)(((unsigned __int128)u53 * T) >> 53);
+        int64_t lo = 0, hi = N - 1; /* smallest j with C[j] > t */
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (C[mid] > t) hi = mid; else lo = mid + 1;
+        }
+        const uint64_t q = C[lo] - (lo ? C[lo - 1] : 0);
+        const double f = (double)T / (double)q;
+        idx[i] = lo;
+        w[2 * i] = x[2 * lo] * f;
+        w[2 * i + 1] = x[2 * lo + 1] * f;
+    }
+    free(C);
+    return T;
+}
+
+/* Per output bin ys[b] of the range-k transform with swaps (natural order):
+ * out[4b..4b+3] = (Re mean, Im mean, power estimate, standard error) of the
+ * M samples (idx, w) drawn by oracle_mc_sample. */
+void oracle_mc_bins(int n, int k, int sign, const int64_t *idx, const double *w, int64_t m, const int64_t *ys,
+                    int nbins, double *out)
+{
+    const int kk = effective_k(n, k);
+    const double inv_root = 1.0 / sqrt(ldexp(1.0, n));
+#pragma omp parallel for schedule(dynamic)
+    for (int b = 0; b < nbins; b++) {
+        double sr = 0.0, si = 0.0, sq = 0.0;
+        for (int64_t i = 0; i < m; i++) {
+            const uint64_t p = aqft_phase(n, kk, (uint64_t)idx[i], (uint64_t)ys[b]);
+            const double th = sign * ORACLE_TWO_PI * ldexp((double)p, -n);
+            const double c = cos(th), s = sin(th);
+            const double zr = (w[2 * i] * c - w[2 * i + 1] * s) * inv_root;
+            const double zi = (w[2 * i] * s + w[2 * i + 1] * c) * inv_root;
+            sr += zr;
+            si += zi;
+            sq += zr * zr + zi * zi;
+        }
+        const double M = (double)m;
+        const double mr = sr / M, mi = si / M;
+        out[4 * b] = mr;
+        out[4 * b + 1] = mi;
+        out[4 * b + 2] = m > 1 ? (sr * sr + si * si - sq) / (M * (M - 1.0)) : 0.0;
+        const double v = m > 1 ? (sq / M - (mr * mr + mi * mi)) / (M - 1.0) : 0.0;
+        out[4 * b + 3] = v > 0.0 ? sqrt(v) : 0.0;
+    }
+}

@@ -1,0 +1,108 @@
+"""Pins for the oracle's Monte Carlo backend (Sec. 6: sum-over-histories
+estimates of single output bins with importance-weighted input indices).
+
+The estimator's defining properties fix it without reference to its own code:
+exact single-path cases (a basis state, a tone on its own bin: every sample
+carries the whole amplitude), unbiasedness of the mean and of the power
+estimate (averaged over many independent runs, within a few standard errors
+of the exact bins from the DFT definition / closed-form AQFT elements), the
+variance of the mean (E|z|^2 - |mean|^2) / M with E|z|^2 known exactly, and
+the sampling law (a fine grid of uniforms lands on index j in proportion to
+its integer weight q_j, i.e. to |x_j|)."""
+import numpy as np
+import pytest
+
+import qft_inputs
+
+
+def _uniforms(rng, m):
+    return rng.integers(0, 2 ** 53, size=m, dtype=np.int64).astype(np.float64) / 2.0 ** 53
+
+
+def _q(x, n):
+    x = np.asarray(x, dtype=np.complex128)
+    a = np.sqrt(x.real * x.real + x.imag * x.imag)  # |x_j| as the definition forms it
+    return np.where(a > 0, np.ceil(a * (2.0 ** (62 - n) / a.max())), 0).astype(np.uint64)
+
+
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_tone_on_its_bin_is_exact(oracle_mod, sign):
+    n, k0 = 10, 37
+    N = 1 << n
+    x = np.exp(-sign * 2j * np.pi * k0 * np.arange(N) / N)
+    idx, w, T = oracle_mod.mc_sample(x, _uniforms(np.random.default_rng(3), 500))
+    amp, power, se = oracle_mod.mc_bins(idx, w, n, [k0], -1, sign)
+    assert abs(amp[0] - np.sqrt(N)) <= 1e-9 * np.sqrt(N)
+    assert abs(power[0] - N) <= 1e-9 * N and se[0] <= 1e-9 * np.sqrt(N)
+
+
+@pytest.mark.parametrize("k", [-1, 2])
+def test_basis_state_is_exact(oracle_mod, k):
+    n, j0 = 9, 301
+    N = 1 << n
+    x = np.zeros(N, complex)
+    x[j0] = 0.6 - 0.8j
+    ys = np.arange(0, N, 7)
+    idx, w, T = oracle_mod.mc_sample(x, _uniforms(np.random.default_rng(4), 64))
+    assert np.all(idx == j0)
+    amp, power, se = oracle_mod.mc_bins(idx, w, n, ys, k, -1)
+    ref = oracle_mod.aqft_bins(x, ys, k, -1)
+    assert np.max(np.abs(amp - ref)) <= 1e-12
+    # the standard error is the square root of a rounding-level difference
+    assert np.max(np.abs(power - np.abs(ref) ** 2)) <= 1e-12 and np.max(se) <= 1e-6 * np.max(np.abs(ref))
+
+
+def test_zero_input(oracle_mod):
+    idx, w, T = oracle_mod.mc_sample(np.zeros(64, complex), [0.5, 0.25])
+    assert T == 0 and np.all(w == 0)
+    amp, power, se = oracle_mod.mc_bins(idx, w, 6, [0, 5])
+    assert np.all(amp == 0) and np.all(power == 0)
+
+
+def test_sampling_law_on_a_fine_grid(oracle_mod):
+    """Uniforms i / K (K = 2^16) land on index j about K q_j / T times (within
+    one, since each index owns a contiguous run of targets)."""
+    n = 5
+    x = qft_inputs.gaussian(n, seed=11, normalise=False)
+    x[3] = 0  # a zero amplitude is never drawn
+    K = 1 << 16
+    idx, w, T = oracle_mod.mc_sample(x, np.arange(K) / K)
+    q = _q(x, n)
+    assert T == int(q.sum())
+    counts = np.bincount(idx, minlength=1 << n)
+    assert counts[3] == 0
+    assert np.all(np.abs(counts - K * q.astype(np.float64) / float(T)) <= 1.0)
+    # weights: x_j T / q_j, i.e. x_j / p_j
+    j = idx[K // 3]
+    assert np.isclose(w[K // 3], x[j] * float(T) / float(q[j]), rtol=1e-15)
+
+
+@pytest.mark.parametrize("k", [-1, 3])
+def test_unbiased_mean_and_power_and_variance(oracle_mod, k):
+    """Gaussian input, n = 8: over R = 400 independent runs of M = 64 samples
+    the average estimate of each bin is within 5 standard errors of the exact
+    bin (closed-form AQFT elements, which the oracle's pins tie to the DFT
+    definition), the average power estimate within 5 standard errors of
+    |bin|^2, and the spread of the estimates matches (E|z|^2 - |bin|^2) / M."""
+    n, R, M = 8, 400, 64
+    N = 1 << n
+    x = qft_inputs.gaussian(n, seed=8, normalise=False)
+    ys = np.array([0, 1, 17, 128, 200, 255])
+    ref = oracle_mod.aqft_bins(x, ys, k, -1)
+    q = _q(x, n).astype(np.float64)
+    T = q.sum()
+    Ez2 = np.sum(np.abs(x) ** 2 * T / q) / N  # E|z|^2 = sum_j p_j |x_j / p_j|^2 / N, the same for every bin
+    var = (Ez2 - np.abs(ref) ** 2) / M
+    rng = np.random.default_rng(2024)
+    amps, pows = [], []
+    for _ in range(R):
+        idx, w, _T = oracle_mod.mc_sample(x, _uniforms(rng, M))
+        a, p, _ = oracle_mod.mc_bins(idx, w, n, ys, k, -1)
+        amps.append(a)
+        pows.append(p)
+    amps, pows = np.array(amps), np.array(pows)
+    assert np.all(np.abs(amps.mean(0) - ref) <= 5 * np.sqrt(var / R))
+    pstd = pows.std(0, ddof=1)
+    assert np.all(np.abs(pows.mean(0) - np.abs(ref) ** 2) <= 5 * pstd / np.sqrt(R))
+    emp = np.mean(np.abs(amps - ref) ** 2, axis=0)
+    assert np.all((emp > 0.75 * var) & (emp < 1.33 * var))

@@ -38,6 +38,12 @@ MUTANTS = {
     "decode_unnorm_scale": ("else if (mode == 2) f = scale_in * rootN;", "else if (mode == 2) f = scale_in * rootN * rootN;"),
     "counts_off_by_one": ("for (int d = 1; d <= kk && d <= t; d++) cp++;",
                           "for (int d = 0; d <= kk && d <= t; d++) cp++;"),
+    "mc_weight_not_divided_by_p": ("const double f = (double)T / (double)q;", "const double f = 1.0;"),
+    "mc_phase_sign": ("const double th = sign * ORACLE_TWO_PI * ldexp((double)p, -n);\n            const double c = cos(th), s = sin(th);\n            const double zr",
+                      "const double th = -sign * ORACLE_TWO_PI * ldexp((double)p, -n);\n            const double c = cos(th), s = sin(th);\n            const double zr"),
+    "mc_power_biased": ("(sr * sr + si * si - sq) / (M * (M - 1.0))", "(sr * sr + si * si) / (M * M)"),
+    "mc_proposal_uniform": ("const uint64_t q = a > 0.0 ? (uint64_t)ceil(a * scale) : 0;",
+                            "const uint64_t q = a > 0.0 ? (uint64_t)ldexp(1.0, 62 - n) : 0;"),
 }
 
 
@@ -91,6 +97,35 @@ def _pin_failures(o):
     _, s = o.encode(x)
     if abs(s - np.linalg.norm(x)) > 1e-12 * np.linalg.norm(x):
         bad.append("encode_norm")
+    # Monte Carlo backend (Sec. 6): a tone on its own bin is exact; over many
+    # runs the mean and the power estimate are unbiased; the draw frequencies
+    # follow |x_j|
+    nt, k0 = 6, 9
+    tone = np.exp(2j * np.pi * k0 * np.arange(1 << nt) / (1 << nt))
+    rng = np.random.default_rng(1)
+    idx, w, _ = o.mc_sample(tone, rng.integers(0, 2 ** 53, 64).astype(np.float64) / 2.0 ** 53)
+    amp, _, _ = o.mc_bins(idx, w, nt, [k0], -1, -1)
+    if abs(amp[0] - np.sqrt(1 << nt)) > 1e-9:
+        bad.append("mc_tone_exact")
+    xg = qft_inputs.gaussian(nt, seed=5, normalise=False)
+    ys = np.array([0, 3, 40])
+    ref = o.aqft_bins(xg, ys, -1, -1)
+    amps, pows = [], []
+    for _ in range(300):
+        idx, w, _ = o.mc_sample(xg, rng.integers(0, 2 ** 53, 32).astype(np.float64) / 2.0 ** 53)
+        a, p, _ = o.mc_bins(idx, w, nt, ys, -1, -1)
+        amps.append(a)
+        pows.append(p)
+    amps, pows = np.array(amps), np.array(pows)
+    if np.any(np.abs(amps.mean(0) - ref) > 5 * amps.std(0) / np.sqrt(300)):
+        bad.append("mc_unbiased_mean")
+    if np.any(np.abs(pows.mean(0) - np.abs(ref) ** 2) > 5 * pows.std(0) / np.sqrt(300)):
+        bad.append("mc_unbiased_power")
+    K = 1 << 14
+    idx, _, _ = o.mc_sample(xg, np.arange(K) / K)
+    freq = np.bincount(idx, minlength=1 << nt) / K
+    if np.max(np.abs(freq - np.abs(xg) / np.abs(xg).sum())) > 1e-3:
+        bad.append("mc_draw_law")
     return bad
 
 
