@@ -285,8 +285,9 @@ def leakage(approx, exact) -> float:
 def mc_sample(x, u):
     """Sec. 6 Monte Carlo backend, sampling step: for each uniform u_m in [0, 1)
     (a multiple of 2^-53) the input index j_m drawn with probability
-    q_j / T (q_j = ceil(|x_j| 2^(62-n) / max|x|), T = sum q) and its weight
-    w_m = x_j T / q_j.  Returns (idx int64, w complex128, T)."""
+    q_j / T (q_j = ceil(m_j 2^(62-n) / max m), m_j = max(|Re x_j|, |Im x_j|),
+    T = sum q) and its weight w_m = x_j T / q_j.  Returns (idx int64,
+    w complex128, T)."""
     lib = _load()
     x = _as_c128(x)
     n = _log2_exact(x.size)

@@ -342,10 +342,12 @@ int64_t oracle_bit_reverse(int64_t i, int n) { return bit_reverse(i, n); }
  * kept controlled rotations give the path j -> y, and sampling input indices
  * with importance weights gives unbiased estimates of single output bins and
  * of the power spectrum.  Readings (the passage gives no formulas):
- *   - the proposal is p_j proportional to |x_j| (the magnitude of term j),
- *     made exact in integers: q_j = ceil(|x_j| 2^S / max_j |x_j|) with
- *     S = 62 - n (q_j >= 1 whenever x_j != 0, so no nonzero term is left out
- *     and the estimator stays unbiased), T = sum_j q_j, p_j = q_j / T;
+ *   - the proposal follows the magnitude of term j: p_j proportional to
+ *     m_j = max(|Re x_j|, |Im x_j|) (within a factor sqrt(2) of |x_j|, and
+ *     formed without rounding), made exact in integers:
+ *     q_j = ceil(m_j 2^S / max_j m_j) with S = 62 - n (q_j >= 1 whenever
+ *     x_j != 0, so no nonzero term is left out and the estimator stays
+ *     unbiased), T = sum_j q_j, p_j = q_j / T;
  *   - a uniform u in [0, 1), a multiple of 2^-53, selects the target
  *     t = floor(u 2^53 T / 2^53) in [0, T) and the index j with
  *     C_{j-1} <= t < C_j, C the inclusive prefix sums of q;
@@ -353,9 +355,7 @@ int64_t oracle_bit_reverse(int64_t i, int n) { return bit_reverse(i, n); }
  *     z = w exp(s 2 pi i phase(j, y) / N) / sqrt(N) has mean <y|U_k|x>;
  *   - per bin: the mean of z over the M samples, the unbiased estimate
  *     (|sum z|^2 - sum |z|^2) / (M (M - 1)) of |<y|U_k|x>|^2, and the
- *     standard error sqrt((sum |z|^2 / M - |mean|^2) / (M - 1)) of the mean.
- * |x_j| is sqrt(re^2 + im^2) in FP64 without contraction (this file is built
- * with -ffp-contract=off). */
+ *     standard error sqrt((sum |z|^2 / M - |mean|^2) / (M - 1)) of the mean. */
 
 /* Importance sampling of M input indices: idx[m] and the complex weight
  * w[2m], w[2m+1] for the uniform u[m].  Returns T (0 for a zero input: then
@@ -365,7 +365,7 @@ uint64_t oracle_mc_sample(int n, const double *x, const double *u, int64_t m, in
     const int64_t N = (int64_t)1 << n;
     double mx = 0.0;
     for (int64_t j = 0; j < N; j++) {
-        const double a = sqrt(x[2 * j] * x[2 * j] + x[2 * j + 1] * x[2 * j + 1]);
+        const double a = fmax(fabs(x[2 * j]), fabs(x[2 * j + 1]));
         if (a > mx) mx = a;
     }
     if (mx == 0.0) {
@@ -377,7 +377,7 @@ uint64_t oracle_mc_sample(int n, const double *x, const double *u, int64_t m, in
     if (!C) return 0;
     uint64_t acc = 0;
     for (int64_t j = 0; j < N; j++) {
-        const double a = sqrt(x[2 * j] * x[2 * j] + x[2 * j + 1] * x[2 * j + 1]);
+        const double a = fmax(fabs(x[2 * j]), fabs(x[2 * j + 1]));
         const uint64_t q = a > 0.0 ? (uint64_t)ceil(a * scale) : 0;
         acc += q;
         C[j] = acc;

@@ -8,7 +8,7 @@ estimate (averaged over many independent runs, within a few standard errors
 of the exact bins from the DFT definition / closed-form AQFT elements), the
 variance of the mean (E|z|^2 - |mean|^2) / M with E|z|^2 known exactly, and
 the sampling law (a fine grid of uniforms lands on index j in proportion to
-its integer weight q_j, i.e. to |x_j|)."""
+its integer weight q_j, i.e. to max(|Re x_j|, |Im x_j|))."""
 import numpy as np
 import pytest
 
@@ -19,16 +19,25 @@ def _uniforms(rng, m):
     return rng.integers(0, 2 ** 53, size=m, dtype=np.int64).astype(np.float64) / 2.0 ** 53
 
 
-def _q(x, n):
+def _mag(x):
+    """The proposal's magnitude of each term: max(|Re x_j|, |Im x_j|)."""
     x = np.asarray(x, dtype=np.complex128)
-    a = np.sqrt(x.real * x.real + x.imag * x.imag)  # |x_j| as the definition forms it
+    return np.maximum(np.abs(x.real), np.abs(x.imag))
+
+
+def _q(x, n):
+    a = _mag(x)
     return np.where(a > 0, np.ceil(a * (2.0 ** (62 - n) / a.max())), 0).astype(np.uint64)
 
 
 @pytest.mark.parametrize("sign", [-1, 1])
 def test_tone_on_its_bin_is_exact(oracle_mod, sign):
-    n, k0 = 10, 37
+    """A tone at bin N/4 (x_j = i^j, every term of the same magnitude and
+    max(|Re|, |Im|)): the proposal is uniform, every path reaches bin N/4 with
+    the same phase, so every sample carries the whole amplitude."""
+    n = 10
     N = 1 << n
+    k0 = N // 4
     x = np.exp(-sign * 2j * np.pi * k0 * np.arange(N) / N)
     idx, w, T = oracle_mod.mc_sample(x, _uniforms(np.random.default_rng(3), 500))
     amp, power, se = oracle_mod.mc_bins(idx, w, n, [k0], -1, sign)

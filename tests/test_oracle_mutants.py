@@ -44,6 +44,8 @@ MUTANTS = {
     "mc_power_biased": ("(sr * sr + si * si - sq) / (M * (M - 1.0))", "(sr * sr + si * si) / (M * M)"),
     "mc_proposal_uniform": ("const uint64_t q = a > 0.0 ? (uint64_t)ceil(a * scale) : 0;",
                             "const uint64_t q = a > 0.0 ? (uint64_t)ldexp(1.0, 62 - n) : 0;"),
+    "mc_proposal_real_part_only": ("const double a = fmax(fabs(x[2 * j]), fabs(x[2 * j + 1]));\n        const uint64_t q",
+                                   "const double a = fabs(x[2 * j]) + 1e-300;\n        const uint64_t q"),
 }
 
 
@@ -100,7 +102,7 @@ def _pin_failures(o):
     # Monte Carlo backend (Sec. 6): a tone on its own bin is exact; over many
     # runs the mean and the power estimate are unbiased; the draw frequencies
     # follow |x_j|
-    nt, k0 = 6, 9
+    nt, k0 = 6, 16  # bin N/4: x_j = i^j, uniform proposal
     tone = np.exp(2j * np.pi * k0 * np.arange(1 << nt) / (1 << nt))
     rng = np.random.default_rng(1)
     idx, w, _ = o.mc_sample(tone, rng.integers(0, 2 ** 53, 64).astype(np.float64) / 2.0 ** 53)
@@ -124,7 +126,8 @@ def _pin_failures(o):
     K = 1 << 14
     idx, _, _ = o.mc_sample(xg, np.arange(K) / K)
     freq = np.bincount(idx, minlength=1 << nt) / K
-    if np.max(np.abs(freq - np.abs(xg) / np.abs(xg).sum())) > 1e-3:
+    mag = np.maximum(np.abs(xg.real), np.abs(xg.imag))
+    if np.max(np.abs(freq - mag / mag.sum())) > 1e-3:
         bad.append("mc_draw_law")
     return bad
 
