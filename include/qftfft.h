@@ -470,6 +470,52 @@ int qft_qpe_prepare(void* d_state, int m, int d_bits, const double* d_theta, con
                     void* d_workspace, qft_stream_t stream);
 int qft_qpe_probabilities(const void* d_state, int m, int d_bits, int dtype, double* d_prob, qft_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Monte Carlo backend (Sec. 6, "Monte Carlo simulation in the sum-over-
+ * histories style"): estimates of single output bins of the range-k transform
+ * (natural order) from importance-sampled input indices, at a cost set by the
+ * number of samples M instead of the 2^n amplitudes.  The amplitude
+ * <y|U_k|x> is the sum over input indices j of x_j exp(s 2 pi i phase(j, y) / N)
+ * / sqrt(N), phase(j, y) = sum of j_a y_b 2^(a+b) over n-1-k <= a+b <= n-1
+ * (j y mod N for the exact transform; s = direction).
+ *
+ * qft_mc_prepare builds the proposal from the input x (2^n amplitudes of the
+ * dtype, device memory, 16-byte aligned): q_j = ceil(m_j 2^(62-n) / max m)
+ * with m_j = max(|Re x_j|, |Im x_j|) -- an integer for every index, at least
+ * 1 for every nonzero amplitude -- and their prefix sums, T = sum q, into
+ * d_workspace (qft_mc_workspace_size(n) bytes of device memory, 256-byte
+ * aligned; the workspace holds the proposal until the next prepare and also
+ * the partial sums of qft_mc_sample and qft_mc_bins).
+ *
+ * qft_mc_sample draws M >= 1 indices: for uniform u_i in [0, 1) (d_uniforms,
+ * M doubles in device memory, drawn by the caller; u_i 2^53 is truncated to
+ * an integer) the target t = floor(u_i 2^53 T / 2^53) selects the index j
+ * with C_{j-1} <= t < C_j (C the prefix sums of q), written to d_index (M
+ * int64), and its weight w = x_j T / q_j to d_weight (M complex128, 2M
+ * doubles, 16-byte aligned).  Every step is integer or correctly rounded FP64
+ * arithmetic.  A zero input gives index 0 and weight 0 everywhere.
+ *
+ * qft_mc_bins evaluates, for each of nbins (<= 65536) output bins d_bins
+ * (int64, device memory), the mean of z_i = w_i exp(s 2 pi i phase(j_i, y) /
+ * N) / sqrt(N) over the M samples (an unbiased estimate of <y|U_k|x>), the
+ * unbiased estimate (|sum z|^2 - sum |z|^2) / (M (M - 1)) of |<y|U_k|x>|^2
+ * and the standard error sqrt((sum |z|^2 / M - |mean|^2) / (M - 1)) of the
+ * mean: d_out[4b .. 4b+3] = (Re mean, Im mean, power, standard error),
+ * doubles in device memory.  The phase is exact (integers mod 2^n); its
+ * sine and cosine and the products are FP32, summed in FP32 over runs of 32
+ * samples and in FP64 beyond.  d_workspace must be the one the samples were
+ * drawn with (it holds their sum of |w|^2).  k < 0 or k >= n - 1: exact.
+ *
+ * All three return QFT_ERR_BAD_ARG for null or misaligned pointers and out of
+ * range sizes (1 <= n <= 34 complex64, 33 complex128), and are asynchronous
+ * on the stream. */
+size_t qft_mc_workspace_size(int n);
+int qft_mc_prepare(int n, int dtype, const void* d_x, void* d_workspace, qft_stream_t stream);
+int qft_mc_sample(int n, int dtype, const void* d_x, const void* d_workspace, const double* d_uniforms, int64_t m,
+                  int64_t* d_index, double* d_weight, qft_stream_t stream);
+int qft_mc_bins(int n, int k, int direction, const int64_t* d_index, const double* d_weight, int64_t m,
+                const int64_t* d_bins, int nbins, const void* d_workspace, double* d_out, qft_stream_t stream);
+
 /* Diagnostics: write pass i of the plan as a flat integer record (tile bits,
  * register stages with their wires and lane maps, tile-index -> wire and
  * output-address maps, tile-coordinate segments, TMA box geometry, grid,

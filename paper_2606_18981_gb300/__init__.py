@@ -88,6 +88,12 @@ _lib.qft_qpe_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int]
 _lib.qft_qpe_workspace_size.restype = ctypes.c_size_t
 _lib.qft_qpe_prepare.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]
 _lib.qft_qpe_probabilities.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
+_lib.qft_mc_workspace_size.argtypes = [ctypes.c_int]
+_lib.qft_mc_workspace_size.restype = ctypes.c_size_t
+_lib.qft_mc_prepare.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+_lib.qft_mc_sample.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
+_lib.qft_mc_bins.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int,
+                             _vp, _vp, _vp]
 _lib.qft_rplan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts)]
 _lib.qft_rplan_destroy.argtypes = [_vp]
 _lib.qft_rplan_workspace_size.argtypes = [_vp]
@@ -528,6 +534,54 @@ def qpe(thetas, coefs, m: int, k: int = -1, dtype="c128", device="cuda"):
     _check(_lib.qft_qpe_probabilities(state.data_ptr(), m, db, dt, prob.data_ptr(), _stream_handle(None)),
            "qft_qpe_probabilities")
     return prob
+
+
+class MonteCarlo:
+    """Monte Carlo estimates of single output bins (Sec. 6, sum over histories)
+    of the range-k transform of one input x (a CUDA complex64 / complex128
+    tensor of length 2^n): prepare once, then draw samples from caller-given
+    uniforms and evaluate any bins (qft_mc_prepare / qft_mc_sample /
+    qft_mc_bins)."""
+
+    def __init__(self, x):
+        import torch
+
+        if not x.is_cuda or x.dtype not in (torch.complex64, torch.complex128):
+            raise ValueError("MonteCarlo expects a CUDA complex64 or complex128 tensor")
+        N = x.numel()
+        n = N.bit_length() - 1
+        if (1 << n) != N:
+            raise QftError(ERR_SIZE, "MonteCarlo")
+        self.n = n
+        self.dtype = C64 if x.dtype == torch.complex64 else C128
+        self.x = x.contiguous()
+        self.ws = torch.empty(int(_lib.qft_mc_workspace_size(n)), dtype=torch.uint8, device=x.device)
+        _check(_lib.qft_mc_prepare(n, self.dtype, self.x.data_ptr(), self.ws.data_ptr(), _stream_handle(None)),
+               "qft_mc_prepare")
+
+    def sample(self, u, stream=None):
+        """Indices (int64) and weights (complex128) for the uniforms u (CUDA float64)."""
+        import torch
+
+        u = u.contiguous()
+        m = u.numel()
+        idx = torch.empty(m, dtype=torch.int64, device=u.device)
+        w = torch.empty(m, dtype=torch.complex128, device=u.device)
+        _check(_lib.qft_mc_sample(self.n, self.dtype, self.x.data_ptr(), self.ws.data_ptr(), u.data_ptr(), m,
+                                  idx.data_ptr(), w.data_ptr(), _stream_handle(stream)), "qft_mc_sample")
+        return idx, w
+
+    def bins(self, idx, w, ys, k: int = -1, direction: int = FORWARD, stream=None):
+        """(mean complex128, power float64, standard error float64) per bin of ys."""
+        import torch
+
+        ys = torch.as_tensor(ys, dtype=torch.int64, device=idx.device).contiguous()
+        out = torch.empty(4 * max(1, ys.numel()), dtype=torch.float64, device=idx.device)
+        _check(_lib.qft_mc_bins(self.n, int(k), int(direction), idx.data_ptr(), w.data_ptr(), idx.numel(),
+                                ys.data_ptr(), ys.numel(), self.ws.data_ptr(), out.data_ptr(), _stream_handle(stream)),
+               "qft_mc_bins")
+        o = out[:4 * ys.numel()].view(-1, 4)
+        return torch.complex(o[:, 0], o[:, 1]), o[:, 2], o[:, 3]
 
 
 _rplan_cache: dict = {}

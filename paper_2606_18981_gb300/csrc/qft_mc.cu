@@ -1,0 +1,467 @@
+// qft_mc.cu -- the Monte Carlo backend of Sec. 6: estimates of single output
+// bins of the (A)QFT "in the sum-over-histories style".
+//
+// The amplitude <y|U_k|x> is a sum over input indices j of x_j times the
+// phase that the kept controlled rotations give the path j -> y (the
+// closed-form matrix element exp(s 2 pi i phase(j, y) / N) / sqrt(N), with
+// phase(j, y) = sum of j_a y_b 2^(a+b) over n-1-k <= a+b <= n-1, mod 2^n;
+// j y mod 2^n for the exact transform).  Drawing input indices with
+// importance weights gives unbiased estimates of single bins and of the power
+// spectrum, at a cost set by the number of samples instead of 2^n.
+//
+//   qft_mc_prepare  the proposal, exact in integers: per index
+//                   q_j = ceil(m_j 2^(62-n) / max m), m_j = max(|Re x_j|, |Im x_j|)
+//                   (q_j >= 1 for every nonzero x_j, so the estimator is
+//                   unbiased); prefix sums of q in blocks of 4096 indices
+//                   and the blocks' exclusive offsets, T = sum q.
+//   qft_mc_sample   for each given uniform u: t = floor(u 2^53 T / 2^53), the
+//                   index j with C_{j-1} <= t < C_j (two binary searches), and
+//                   the weight w = x_j T / q_j.
+//   qft_mc_bins     per bin y: the mean of z = w exp(s 2 pi i phase(j, y)/N)
+//                   / sqrt(N), the unbiased power estimate
+//                   (|sum z|^2 - sum |z|^2) / (M (M - 1)) and the standard
+//                   error of the mean.
+//
+// The proposal, the draws and the weights are integer or correctly rounded
+// FP64 operations, so they are the same bits on any IEEE machine; the bins
+// evaluate the phase exactly in integers and the sine and cosine in FP32,
+// and sum in FP32 over runs of 32 samples and in FP64 beyond.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/qftfft.h"
+#include "plan_host.hpp"
+#include "qft_device.cuh"
+
+namespace qft {
+namespace {
+
+constexpr int kMcChunk = 4096;          // indices per prefix-sum block
+constexpr int kMcScanThreads = 256;     // 16 indices per thread
+constexpr int kMcSampleBlocks = 1024;   // blocks of the sampling kernel (partial sums of |w|^2)
+constexpr int kMcBinsPerBlock = 8;      // bins evaluated together per sample load
+constexpr int kMcMaxSplit = 32;         // sample chunks per bin group
+constexpr int kMcMaxBins = 1 << 16;
+
+struct McLayout {
+    size_t meta, bsum, wpart, part, cdf, total;
+};
+
+__host__ __device__ inline size_t mc_align(size_t b) { return (b + 255) / 256 * 256; }
+
+__host__ __device__ inline McLayout mc_layout(int n) {
+    const int64_t N = int64_t(1) << n;
+    const int64_t nb = (N + kMcChunk - 1) / kMcChunk;
+    McLayout L;
+    L.meta = 0;                                                         // T, max magnitude bits
+    L.bsum = 256;                                                       // nb block offsets
+    L.wpart = L.bsum + mc_align(size_t(nb) * 8);                        // sum |w|^2 per sampling block
+    L.part = L.wpart + mc_align(size_t(kMcSampleBlocks) * 8);           // bin partial sums
+    L.cdf = L.part + mc_align(size_t(kMcMaxSplit) * kMcMaxBins * 16);  // local inclusive prefix sums
+    L.total = L.cdf + mc_align(size_t(N) * 8);
+    return L;
+}
+
+// The magnitude used by the proposal, max(|Re|, |Im|) as FP64 bits: for
+// non-negative doubles the integer order of the bits is the value order.
+__device__ __forceinline__ uint64_t mag_bits(float2 v) {
+    const uint64_t a = static_cast<uint64_t>(__double_as_longlong(static_cast<double>(v.x))) & 0x7FFFFFFFFFFFFFFFull;
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(static_cast<double>(v.y))) & 0x7FFFFFFFFFFFFFFFull;
+    return a > b ? a : b;
+}
+__device__ __forceinline__ uint64_t mag_bits(double2 v) {
+    const uint64_t a = static_cast<uint64_t>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
+    return a > b ? a : b;
+}
+__device__ __forceinline__ double2 as_d2(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 as_d2(double2 v) { return v; }
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int o) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, static_cast<uint32_t>(v), o);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, static_cast<uint32_t>(v >> 32), o);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+__device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, int o) {
+    const uint32_t lo = __shfl_up_sync(0xffffffffu, static_cast<uint32_t>(v), o);
+    const uint32_t hi = __shfl_up_sync(0xffffffffu, static_cast<uint32_t>(v >> 32), o);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
+// max_j m_j (as bits) into *maxbits (zeroed by the caller).
+template <typename V>
+__global__ void mc_max_kernel(const V* __restrict__ x, int64_t N, unsigned long long* maxbits) {
+    uint64_t m = 0;
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < N; j += int64_t(gridDim.x) * blockDim.x) {
+        const uint64_t b = mag_bits(x[j]);
+        m = b > m ? b : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t b = shfl_xor_u64(m, o);
+        m = b > m ? b : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(maxbits, static_cast<unsigned long long>(m));
+}
+
+// Exclusive scan of one value per thread across a block of NT threads
+// (warp shuffles, then the warp totals); returns the thread's exclusive
+// prefix and the block total in *total.
+template <int NT>
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* warp_tot, uint64_t* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = shfl_up_u64(incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t t = lane < NT / 32 ? warp_tot[lane] : 0;
+        uint64_t ti = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = shfl_up_u64(ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < NT / 32) warp_tot[lane] = ti - t;  // exclusive prefix of the warp totals
+        if (lane == NT / 32 - 1) warp_tot[NT / 32] = ti;
+    }
+    __syncthreads();
+    const uint64_t r = warp_tot[w] + incl - v;
+    *total = warp_tot[NT / 32];
+    __syncthreads();
+    return r;
+}
+
+// q_j and its inclusive prefix within each block of kMcChunk indices
+// (cdf[j]); the block's total into bsum[b].
+template <typename V>
+__global__ void __launch_bounds__(kMcScanThreads)
+    mc_quant_scan_kernel(const V* __restrict__ x, int64_t N, int n, const unsigned long long* maxbits,
+                         uint64_t* __restrict__ cdf, uint64_t* __restrict__ bsum) {
+    constexpr int IT = kMcChunk / kMcScanThreads;
+    __shared__ uint64_t warp_tot[kMcScanThreads / 32 + 1];
+    const double mx = __longlong_as_double(static_cast<long long>(*maxbits));
+    const double scale = mx > 0.0 ? __ddiv_rn(ldexp(1.0, 62 - n), mx) : 0.0;
+    const int64_t j0 = blockIdx.x * int64_t(kMcChunk) + int64_t(threadIdx.x) * IT;
+    uint64_t q[IT];
+    uint64_t run = 0;
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        q[i] = 0;
+        if (j0 + i < N) {
+            const double m = __longlong_as_double(static_cast<long long>(mag_bits(x[j0 + i])));
+            if (m > 0.0) q[i] = static_cast<uint64_t>(ceil(__dmul_rn(m, scale)));
+        }
+        run += q[i];
+        q[i] = run;  // thread-local inclusive prefix
+    }
+    uint64_t total;
+    const uint64_t base = block_exclusive_scan<kMcScanThreads>(run, warp_tot, &total);
+#pragma unroll
+    for (int i = 0; i < IT; ++i)
+        if (j0 + i < N) cdf[j0 + i] = base + q[i];
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// In place: bsum[b] <- sum of bsum[0 .. b-1]; the grand total T into meta[0].
+__global__ void __launch_bounds__(1024) mc_scan_offsets_kernel(uint64_t* bsum, int64_t nb, uint64_t* meta) {
+    constexpr int IT = 8;
+    __shared__ uint64_t warp_tot[1024 / 32 + 1];
+    uint64_t carry = 0;
+    for (int64_t c0 = 0; c0 < nb; c0 += 1024 * IT) {
+        const int64_t j0 = c0 + int64_t(threadIdx.x) * IT;
+        uint64_t v[IT];
+        uint64_t run = 0;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            v[i] = j0 + i < nb ? bsum[j0 + i] : 0;
+            const uint64_t t = v[i];
+            v[i] = run;  // exclusive within the thread
+            run += t;
+        }
+        uint64_t total;
+        const uint64_t base = block_exclusive_scan<1024>(run, warp_tot, &total);
+#pragma unroll
+        for (int i = 0; i < IT; ++i)
+            if (j0 + i < nb) bsum[j0 + i] = carry + base + v[i];
+        carry += total;
+    }
+    if (threadIdx.x == 0) meta[0] = carry;
+}
+
+// One draw per uniform: the index and its weight; per block the sum of |w|^2.
+template <typename V>
+__global__ void __launch_bounds__(256)
+    mc_sample_kernel(const V* __restrict__ x, int64_t N, const uint64_t* __restrict__ cdf,
+                     const uint64_t* __restrict__ boff, int64_t nb, const uint64_t* __restrict__ meta,
+                     const double* __restrict__ u, int64_t m, int64_t* __restrict__ idx, double2* __restrict__ w,
+                     double* __restrict__ wpart) {
+    __shared__ double red[8];
+    const uint64_t T = meta[0];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x) {
+        if (T == 0) {
+            idx[i] = 0;
+            w[i] = make_double2(0.0, 0.0);
+            continue;
+        }
+        const uint64_t u53 = __double2ull_rz(__dmul_rn(u[i], 9007199254740992.0));  // u 2^53, exact
+        const uint64_t hi = __umul64hi(u53, T), lo = u53 * T;
+        const uint64_t t = (hi << 11) | (lo >> 53);  // floor(u53 T / 2^53) < T
+        // the block: the last b with boff[b] <= t
+        int64_t a = 0, b = nb - 1;
+        while (a < b) {
+            const int64_t mid = a + (b - a + 1) / 2;
+            if (boff[mid] <= t) a = mid; else b = mid - 1;
+        }
+        const uint64_t r = t - boff[a];
+        const int64_t base = a * kMcChunk;
+        int64_t c = base + kMcChunk - 1 < N - 1 ? base + kMcChunk - 1 : N - 1;
+        int64_t s = base;  // the first index with cdf > r
+        while (s < c) {
+            const int64_t mid = s + (c - s) / 2;
+            if (cdf[mid] > r) c = mid; else s = mid + 1;
+        }
+        const uint64_t q = cdf[s] - (s > base ? cdf[s - 1] : 0);
+        const double f = __ddiv_rn(__ull2double_rn(T), __ull2double_rn(q));
+        const double2 v = as_d2(x[s]);
+        const double2 wv = make_double2(__dmul_rn(v.x, f), __dmul_rn(v.y, f));
+        idx[i] = s;
+        w[i] = wv;
+        acc = __dadd_rn(acc, __dadd_rn(__dmul_rn(wv.x, wv.x), __dmul_rn(wv.y, wv.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 8; ++k) s += red[k];
+        wpart[blockIdx.x] = s;
+    }
+}
+
+// Bins: block (g, c) takes the kMcBinsPerBlock bins of group g and the
+// samples of chunk c; per sample it forms the integer phase of each bin
+// (exact: j y; range k: the windows of the set bits of y), the FP32
+// sine/cosine and the product with the FP32 weight, summed in FP32 over
+// runs of 32 samples and in FP64 beyond; the block's sums go to part[c][bin].
+template <int DIR, bool EXACT>
+__global__ void __launch_bounds__(256)
+    mc_bins_kernel(int n, int kk, const int64_t* __restrict__ idx, const double2* __restrict__ w, int64_t m,
+                   const int64_t* __restrict__ ys, int nbins, double2* __restrict__ part) {
+    constexpr int B = kMcBinsPerBlock;
+    __shared__ uint64_t win[64];
+    __shared__ double2 red[256 / 32][B];
+    if (!EXACT && threadIdx.x < n) {
+        const int b = threadIdx.x;  // output bit b: input bits [max(0, n-1-kk-b), n-1-b]
+        int lo = n - 1 - kk - b;
+        if (lo < 0) lo = 0;
+        const int hi = n - 1 - b;
+        win[b] = ((hi - lo + 1) >= 64 ? ~0ull : ((1ull << (hi - lo + 1)) - 1ull)) << lo;
+    }
+    __syncthreads();
+    const int g0 = blockIdx.x * B;
+    uint64_t y[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) y[b] = g0 + b < nbins ? static_cast<uint64_t>(ys[g0 + b]) : 0ull;
+    const int64_t per = (m + gridDim.y - 1) / gridDim.y;
+    const int64_t s0 = blockIdx.y * per, s1 = s0 + per < m ? s0 + per : m;
+    double2 dacc[B];
+    float2 facc[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        dacc[b] = make_double2(0.0, 0.0);
+        facc[b] = make_float2(0.f, 0.f);
+    }
+    int cnt = 0;
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+        const uint64_t j = static_cast<uint64_t>(idx[i]);
+        const double2 wd = w[i];
+        const float2 wf = make_float2(static_cast<float>(wd.x), static_cast<float>(wd.y));
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            uint64_t p;
+            if constexpr (EXACT) {
+                p = j * y[b];
+            } else {
+                p = 0;
+#pragma unroll 1
+                for (int bit = 0; bit < n; ++bit)
+                    if ((y[b] >> bit) & 1ull) p += (j & win[bit]) << bit;
+            }
+            const float2 e = phase_turns<float, DIR>(p, n);
+            facc[b].x += wf.x * e.x - wf.y * e.y;
+            facc[b].y += wf.x * e.y + wf.y * e.x;
+        }
+        if (++cnt == 32) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                dacc[b].x += facc[b].x;
+                dacc[b].y += facc[b].y;
+                facc[b] = make_float2(0.f, 0.f);
+            }
+            cnt = 0;
+        }
+    }
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        double sx = dacc[b].x + facc[b].x, sy = dacc[b].y + facc[b].y;
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if (lane == 0) red[wq][b] = make_double2(sx, sy);
+    }
+    __syncthreads();
+    if (threadIdx.x < B && g0 + threadIdx.x < nbins) {
+        double sx = 0.0, sy = 0.0;
+        for (int k = 0; k < 256 / 32; ++k) {
+            sx += red[k][threadIdx.x].x;
+            sy += red[k][threadIdx.x].y;
+        }
+        part[size_t(blockIdx.y) * nbins + g0 + threadIdx.x] = make_double2(sx, sy);
+    }
+}
+
+// Per bin: the chunks' sums in order, then mean, power estimate, standard error.
+__global__ void mc_finalize_kernel(int n, int64_t m, int nbins, int split, const double2* __restrict__ part,
+                                   const double* __restrict__ wpart, int nwpart, double* __restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    double sx = 0.0, sy = 0.0;
+    for (int c = 0; c < split; ++c) {
+        sx += part[size_t(c) * nbins + b].x;
+        sy += part[size_t(c) * nbins + b].y;
+    }
+    double q = 0.0;
+    for (int k = 0; k < nwpart; ++k) q += wpart[k];
+    const double inv_n = ldexp(1.0, -n);  // |z|^2 = |w|^2 / N
+    const double inv_root = sqrt(inv_n);
+    sx *= inv_root;
+    sy *= inv_root;
+    q *= inv_n;
+    const double M = static_cast<double>(m);
+    const double mr = sx / M, mi = sy / M;
+    out[4 * b] = mr;
+    out[4 * b + 1] = mi;
+    out[4 * b + 2] = m > 1 ? (sx * sx + sy * sy - q) / (M * (M - 1.0)) : 0.0;
+    const double v = m > 1 ? (q / M - (mr * mr + mi * mi)) / (M - 1.0) : 0.0;
+    out[4 * b + 3] = v > 0.0 ? sqrt(v) : 0.0;
+}
+
+int mc_launch_error() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QFT_OK : set_cuda_error(e);
+}
+
+}  // namespace
+}  // namespace qft
+
+using namespace qft;
+
+extern "C" {
+
+size_t qft_mc_workspace_size(int n) {
+    if (n < 1 || n > 34) return 0;
+    return mc_layout(n).total;
+}
+
+int qft_mc_prepare(int n, int dtype, const void* d_x, void* d_workspace, qft_stream_t stream) {
+    if (!d_x || !d_workspace || n < 1 || n > (dtype == QFT_C64 ? 34 : 33)) return QFT_ERR_BAD_ARG;
+    if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_x) & 15) || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+        return QFT_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const McLayout L = mc_layout(n);
+    char* ws = static_cast<char*>(d_workspace);
+    uint64_t* meta = reinterpret_cast<uint64_t*>(ws + L.meta);
+    uint64_t* bsum = reinterpret_cast<uint64_t*>(ws + L.bsum);
+    uint64_t* cdf = reinterpret_cast<uint64_t*>(ws + L.cdf);
+    const int64_t N = int64_t(1) << n;
+    const int64_t nb = (N + kMcChunk - 1) / kMcChunk;
+    cudaError_t e = cudaMemsetAsync(meta, 0, 256, st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    auto* mx = reinterpret_cast<unsigned long long*>(meta + 1);
+    const int gmax = static_cast<int>(N / 256 < 152 * 16 ? (N + 255) / 256 : 152 * 16);
+    if (dtype == QFT_C64) {
+        mc_max_kernel<<<gmax, 256, 0, st>>>(static_cast<const float2*>(d_x), N, mx);
+        mc_quant_scan_kernel<<<static_cast<unsigned>(nb), kMcScanThreads, 0, st>>>(static_cast<const float2*>(d_x), N, n,
+                                                                                   mx, cdf, bsum);
+    } else {
+        mc_max_kernel<<<gmax, 256, 0, st>>>(static_cast<const double2*>(d_x), N, mx);
+        mc_quant_scan_kernel<<<static_cast<unsigned>(nb), kMcScanThreads, 0, st>>>(static_cast<const double2*>(d_x), N,
+                                                                                   n, mx, cdf, bsum);
+    }
+    mc_scan_offsets_kernel<<<1, 1024, 0, st>>>(bsum, nb, meta);
+    return mc_launch_error();
+}
+
+int qft_mc_sample(int n, int dtype, const void* d_x, const void* d_workspace, const double* d_uniforms, int64_t m,
+                  int64_t* d_index, double* d_weight, qft_stream_t stream) {
+    if (!d_x || !d_workspace || !d_uniforms || !d_index || !d_weight || m < 1) return QFT_ERR_BAD_ARG;
+    if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
+    if (n < 1 || n > (dtype == QFT_C64 ? 34 : 33)) return QFT_ERR_BAD_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_x) & 15) || (reinterpret_cast<uintptr_t>(d_workspace) & 255) ||
+        (reinterpret_cast<uintptr_t>(d_uniforms) & 7) || (reinterpret_cast<uintptr_t>(d_index) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_weight) & 15))
+        return QFT_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const McLayout L = mc_layout(n);
+    const char* ws = static_cast<const char*>(d_workspace);
+    const uint64_t* meta = reinterpret_cast<const uint64_t*>(ws + L.meta);
+    const uint64_t* boff = reinterpret_cast<const uint64_t*>(ws + L.bsum);
+    const uint64_t* cdf = reinterpret_cast<const uint64_t*>(ws + L.cdf);
+    double* wpart = reinterpret_cast<double*>(const_cast<char*>(ws) + L.wpart);
+    const int64_t N = int64_t(1) << n;
+    const int64_t nb = (N + kMcChunk - 1) / kMcChunk;
+    auto* w2 = reinterpret_cast<double2*>(d_weight);
+    if (dtype == QFT_C64)
+        mc_sample_kernel<<<kMcSampleBlocks, 256, 0, st>>>(static_cast<const float2*>(d_x), N, cdf, boff, nb, meta,
+                                                          d_uniforms, m, d_index, w2, wpart);
+    else
+        mc_sample_kernel<<<kMcSampleBlocks, 256, 0, st>>>(static_cast<const double2*>(d_x), N, cdf, boff, nb, meta,
+                                                          d_uniforms, m, d_index, w2, wpart);
+    return mc_launch_error();
+}
+
+int qft_mc_bins(int n, int k, int direction, const int64_t* d_index, const double* d_weight, int64_t m,
+                const int64_t* d_bins, int nbins, const void* d_workspace, double* d_out, qft_stream_t stream) {
+    if (!d_index || !d_weight || !d_workspace || !d_out || m < 1 || nbins < 0 || nbins > kMcMaxBins)
+        return QFT_ERR_BAD_ARG;
+    if (nbins > 0 && !d_bins) return QFT_ERR_BAD_ARG;
+    if (n < 1 || n > 34 || (direction != QFT_FORWARD && direction != QFT_INVERSE)) return QFT_ERR_BAD_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_index) & 7) || (reinterpret_cast<uintptr_t>(d_weight) & 15) ||
+        (reinterpret_cast<uintptr_t>(d_bins) & 7) || (reinterpret_cast<uintptr_t>(d_out) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+        return QFT_ERR_BAD_ARG;
+    if (nbins == 0) return QFT_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const McLayout L = mc_layout(n);
+    char* ws = static_cast<char*>(const_cast<void*>(d_workspace));
+    auto* part = reinterpret_cast<double2*>(ws + L.part);
+    const double* wpart = reinterpret_cast<const double*>(ws + L.wpart);
+    const int kk = (k < 0 || k > n - 1) ? n - 1 : k;
+    const bool exact = kk >= n - 1;
+    const int groups = (nbins + kMcBinsPerBlock - 1) / kMcBinsPerBlock;
+    int split = (2 * 152 + groups - 1) / groups;
+    if (split > kMcMaxSplit) split = kMcMaxSplit;
+    if (int64_t(split) > (m + 255) / 256) split = static_cast<int>((m + 255) / 256);
+    if (split < 1) split = 1;
+    const dim3 grid(groups, split);
+    const auto* w2 = reinterpret_cast<const double2*>(d_weight);
+    if (direction < 0) {
+        if (exact) mc_bins_kernel<-1, true><<<grid, 256, 0, st>>>(n, kk, d_index, w2, m, d_bins, nbins, part);
+        else mc_bins_kernel<-1, false><<<grid, 256, 0, st>>>(n, kk, d_index, w2, m, d_bins, nbins, part);
+    } else {
+        if (exact) mc_bins_kernel<+1, true><<<grid, 256, 0, st>>>(n, kk, d_index, w2, m, d_bins, nbins, part);
+        else mc_bins_kernel<+1, false><<<grid, 256, 0, st>>>(n, kk, d_index, w2, m, d_bins, nbins, part);
+    }
+    mc_finalize_kernel<<<(nbins + 127) / 128, 128, 0, st>>>(n, m, nbins, split, part, wpart, kMcSampleBlocks, d_out);
+    return mc_launch_error();
+}
+
+}  // extern "C"
