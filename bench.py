@@ -670,6 +670,66 @@ def tensor_tier_workload(q, torch, dev, stream):
     return out
 
 
+def monte_carlo_workload(q, torch, dev, stream, peak, n=30, m=1 << 22, nbins=1024, reps=3):
+    """The Monte Carlo backend (Sec. 6, sum over histories) on a tone-mixture
+    input of 2^30 complex64 amplitudes (1-8 tones plus noise, as the single-
+    transform configuration): the proposal (qft_mc_prepare), 2^22 draws and
+    1024 bins (the 8 largest bins of the spectrum and random ones).  Reports
+    each step's time, the sample-bin pairs per second, the prepare step's HBM
+    fraction (it reads the input twice and writes 8 bytes per index), and the
+    estimates' errors against the exact bins, taken from the state-vector
+    transform of the same input (SCALE_UNITARY: <y|U|x>), in standard errors."""
+    N = 1 << n
+    x = device_input(torch, "tones", n, 777, "c64", dev)
+    plan = q.Plan(n, -1, q.FORWARD, "c64", q.ORDER_NATURAL, tuned=True)
+    ws = plan.alloc_workspace(dev)
+    X = x.clone()
+    plan.execute(X, ws, q.SCALE_UNITARY)
+    g = torch.Generator(device=dev)
+    g.manual_seed(2606)
+    ys = torch.cat([torch.topk(X.abs(), 8).indices,
+                    torch.randint(0, N, (nbins - 8,), generator=g, device=dev)]).to(torch.int64)
+    ref = X[ys].to(torch.complex128)
+    del X, ws, plan
+    torch.cuda.empty_cache()
+    u = torch.rand(m, dtype=torch.float64, device=dev, generator=g)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    times = {}
+    with torch.cuda.stream(stream):
+        mc = q.MonteCarlo(x)
+        idx, w = mc.sample(u, stream=stream)
+        mc.bins(idx, w, ys, stream=stream)
+        torch.cuda.synchronize()
+        for name, fn in (("prepare", lambda: q._check(q._lib.qft_mc_prepare(n, q.C64, x.data_ptr(), mc.ws.data_ptr(),
+                                                                             q._stream_handle(stream)), "prepare")),
+                         ("sample", lambda: mc.sample(u, stream=stream)),
+                         ("bins", lambda: mc.bins(idx, w, ys, stream=stream))):
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times[name] = a.elapsed_time(b) / reps
+        idx, w = mc.sample(u, stream=stream)
+        amp, power, se = mc.bins(idx, w, ys, stream=stream)
+        torch.cuda.synchronize()
+    z = (amp - ref).abs() / se
+    strong = ref.abs() >= 0.1 * ref.abs().max()  # the tones' bins
+    top_rel = ((amp - ref).abs() / ref.abs())[strong].max().item()
+    out = {"n": n, "samples": m, "bins": nbins, "ms_prepare": times["prepare"], "ms_sample": times["sample"],
+           "ms_bins": times["bins"], "pairs_per_s": m * nbins / (times["bins"] / 1e3),
+           "samples_per_s": m / (times["sample"] / 1e3),
+           "hbm_frac_prepare": 24 * N / (times["prepare"] / 1e3) / 1e9 / peak,
+           "max_err_in_std_errors": float(z.max().item()),
+           "frac_within_3_std_errors": float((z <= 3).double().mean().item()),
+           "tone_bins": int(strong.sum().item()), "tone_bins_max_rel_err": top_rel,
+           "reference": "the state-vector transform of the same input"}
+    del mc, idx, w, u, x
+    torch.cuda.empty_cache()
+    return out
+
+
 def aqft_accuracy(q, torch, dev, n=22, cutoffs=(4, 6, 8, 10, 12, 16, 21)):
     """The paper's AQFT accuracy experiment (Sec. 4): the single tone at bin 2,
     n = 22, complex128; per cutoff k the infidelity 1 - F against the exact
@@ -764,6 +824,10 @@ def summarize_extra(extra):
                 k: pick(v, "rel_l2_vs_fp64_oracle_n21", "ms_n21", "ms_n28") for k, v in t["fp16x3_block_widths"].items()}
         if "error" in t:
             out["tensor_tier"]["error"] = t["error"]
+    mcw = extra.get("monte_carlo_n30_tones", {})
+    if mcw:
+        out["monte_carlo"] = pick(mcw, "ms_prepare", "ms_sample", "ms_bins", "pairs_per_s", "hbm_frac_prepare",
+                                  "max_err_in_std_errors", "tone_bins_max_rel_err", "error")
     sv = extra.get("serving_poisson", {})
     if sv:
         out["serving"] = {k: pick(v, "served_req_per_s", "p50_ms", "p99_ms") for k, v in sv.items()
@@ -946,7 +1010,8 @@ def run_ours(args, world, rank, local):
                 torch.cuda.empty_cache()
             except Exception as ex:  # secondary numbers must not sink the headline
                 extra[name] = {"error": str(ex)[:200]}
-        for key, fn in (("batched_4096_n8to18_c64", lambda: batched_workload(q, torch, dev, stream)),
+        for key, fn in (("monte_carlo_n30_tones", lambda: monte_carlo_workload(q, torch, dev, stream, peak)),
+                        ("batched_4096_n8to18_c64", lambda: batched_workload(q, torch, dev, stream)),
                         ("tensor_tier", lambda: tensor_tier_workload(q, torch, dev, stream)),
                         ("serving_poisson", lambda: serving_workload(q, torch, dev)),
                         ("next_rows", lambda: next_rows_workload(q, torch, dev, peak)),

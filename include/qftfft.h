@@ -480,9 +480,11 @@ int qft_qpe_probabilities(const void* d_state, int m, int d_bits, int dtype, dou
  * (j y mod N for the exact transform; s = direction).
  *
  * qft_mc_prepare builds the proposal from the input x (2^n amplitudes of the
- * dtype, device memory, 16-byte aligned): q_j = ceil(m_j 2^(62-n) / max m)
- * with m_j = max(|Re x_j|, |Im x_j|) -- an integer for every index, at least
- * 1 for every nonzero amplitude -- and their prefix sums, T = sum q, into
+ * dtype, device memory, 16-byte aligned): an integer weight per index,
+ * q_j = floor(m_j 2^S / 2^(E+1)) + 1 (0 for x_j = 0) with
+ * m_j = max(|Re x_j|, |Im x_j|), 2^E <= max m < 2^(E+1) and S = min(62 - n, 52),
+ * formed by shifting the significand of m_j -- at least 1 for every nonzero
+ * amplitude -- and their prefix sums, T = sum q, into
  * d_workspace (qft_mc_workspace_size(n) bytes of device memory, 256-byte
  * aligned; the workspace holds the proposal until the next prepare and also
  * the partial sums of qft_mc_sample and qft_mc_bins).
@@ -492,8 +494,9 @@ int qft_qpe_probabilities(const void* d_state, int m, int d_bits, int dtype, dou
  * an integer) the target t = floor(u_i 2^53 T / 2^53) selects the index j
  * with C_{j-1} <= t < C_j (C the prefix sums of q), written to d_index (M
  * int64), and its weight w = x_j T / q_j to d_weight (M complex128, 2M
- * doubles, 16-byte aligned).  Every step is integer or correctly rounded FP64
- * arithmetic.  A zero input gives index 0 and weight 0 everywhere.
+ * doubles, 16-byte aligned).  Every step is integer arithmetic or one correctly
+ * rounded FP64 division and product.  A zero input gives index 0 and weight 0
+ * everywhere.
  *
  * qft_mc_bins evaluates, for each of nbins (<= 65536) output bins d_bins
  * (int64, device memory), the mean of z_i = w_i exp(s 2 pi i phase(j_i, y) /

@@ -344,10 +344,15 @@ int64_t oracle_bit_reverse(int64_t i, int n) { return bit_reverse(i, n); }
  * of the power spectrum.  Readings (the passage gives no formulas):
  *   - the proposal follows the magnitude of term j: p_j proportional to
  *     m_j = max(|Re x_j|, |Im x_j|) (within a factor sqrt(2) of |x_j|, and
- *     formed without rounding), made exact in integers:
- *     q_j = ceil(m_j 2^S / max_j m_j) with S = 62 - n (q_j >= 1 whenever
- *     x_j != 0, so no nonzero term is left out and the estimator stays
- *     unbiased), T = sum_j q_j, p_j = q_j / T;
+ *     formed without rounding), made exact in integers from the binary
+ *     representation of m_j: with its significand s_j (53 bits, the implicit
+ *     bit included for normal numbers) and biased exponent e_j (at least 1),
+ *     e_max the largest e_j and S = min(62 - n, 52),
+ *         q_j = (s_j >> (e_max - e_j + 53 - S)) + 1  (0 if x_j = 0),
+ *     i.e. floor(m_j 2^S / 2^(E+1)) + 1 with 2^E <= max m < 2^(E+1): an
+ *     integer within one of m_j's share of 2^S, at least 1 whenever x_j != 0
+ *     (so no nonzero term is left out and the estimator stays unbiased);
+ *     T = sum_j q_j <= 2^n (2^S + 1), p_j = q_j / T;
  *   - a uniform u in [0, 1), a multiple of 2^-53, selects the target
  *     t = floor(u 2^53 T / 2^53) in [0, T) and the index j with
  *     C_{j-1} <= t < C_j, C the inclusive prefix sums of q;
@@ -357,29 +362,50 @@ int64_t oracle_bit_reverse(int64_t i, int n) { return bit_reverse(i, n); }
  *     (|sum z|^2 - sum |z|^2) / (M (M - 1)) of |<y|U_k|x>|^2, and the
  *     standard error sqrt((sum |z|^2 / M - |mean|^2) / (M - 1)) of the mean. */
 
+/* The bits of m_j = max(|Re x_j|, |Im x_j|) (sign cleared). */
+static uint64_t mc_mag_bits(const double *x, int64_t j)
+{
+    uint64_t a, b;
+    memcpy(&a, &x[2 * j], 8);
+    memcpy(&b, &x[2 * j + 1], 8);
+    a &= 0x7FFFFFFFFFFFFFFFull;
+    b &= 0x7FFFFFFFFFFFFFFFull;
+    return a > b ? a : b;
+}
+
+/* q_j of the proposal from the bits of m_j (see above). */
+static uint64_t mc_weight(uint64_t bits, int emax, int S)
+{
+    if (bits == 0) return 0;
+    const int eb = (int)(bits >> 52);
+    const int e = eb > 0 ? eb : 1;
+    const uint64_t sig = (bits & 0xFFFFFFFFFFFFFull) | (eb > 0 ? (uint64_t)1 << 52 : 0);
+    const int sh = emax - e + 53 - S;
+    return (sh < 64 ? sig >> sh : 0) + 1;
+}
+
 /* Importance sampling of M input indices: idx[m] and the complex weight
  * w[2m], w[2m+1] for the uniform u[m].  Returns T (0 for a zero input: then
  * every index is 0 and every weight 0). */
 uint64_t oracle_mc_sample(int n, const double *x, const double *u, int64_t m, int64_t *idx, double *w)
 {
     const int64_t N = (int64_t)1 << n;
-    double mx = 0.0;
+    uint64_t mb = 0;
     for (int64_t j = 0; j < N; j++) {
-        const double a = fmax(fabs(x[2 * j]), fabs(x[2 * j + 1]));
-        if (a > mx) mx = a;
+        const uint64_t b = mc_mag_bits(x, j);
+        if (b > mb) mb = b;
     }
-    if (mx == 0.0) {
+    if (mb == 0) {
         for (int64_t i = 0; i < m; i++) { idx[i] = 0; w[2 * i] = 0.0; w[2 * i + 1] = 0.0; }
         return 0;
     }
-    const double scale = ldexp(1.0, 62 - n) / mx;
+    const int emax = (int)(mb >> 52) > 0 ? (int)(mb >> 52) : 1;
+    const int S = 62 - n < 52 ? 62 - n : 52;
     uint64_t *C = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
     if (!C) return 0;
     uint64_t acc = 0;
     for (int64_t j = 0; j < N; j++) {
-        const double a = fmax(fabs(x[2 * j]), fabs(x[2 * j + 1]));
-        const uint64_t q = a > 0.0 ? (uint64_t)ceil(a * scale) : 0;
-        acc += q;
+        acc += mc_weight(mc_mag_bits(x, j), emax, S);
         C[j] = acc;
     }
     const uint64_t T = acc;

@@ -9,11 +9,13 @@
 // importance weights gives unbiased estimates of single bins and of the power
 // spectrum, at a cost set by the number of samples instead of 2^n.
 //
-//   qft_mc_prepare  the proposal, exact in integers: per index
-//                   q_j = ceil(m_j 2^(62-n) / max m), m_j = max(|Re x_j|, |Im x_j|)
-//                   (q_j >= 1 for every nonzero x_j, so the estimator is
-//                   unbiased); prefix sums of q in blocks of 4096 indices
-//                   and the blocks' exclusive offsets, T = sum q.
+//   qft_mc_prepare  the proposal, exact in integers: per index an integer
+//                   weight q_j = floor(m_j 2^S / 2^(E+1)) + 1 (0 for x_j = 0),
+//                   m_j = max(|Re x_j|, |Im x_j|), 2^E <= max m < 2^(E+1),
+//                   S = min(62 - n, 52), formed by shifting the significand of
+//                   m_j (q_j >= 1 for every nonzero x_j, so the estimator is
+//                   unbiased); prefix sums of q in blocks of 4096 indices and
+//                   the blocks' exclusive offsets, T = sum q.
 //   qft_mc_sample   for each given uniform u: t = floor(u 2^53 T / 2^53), the
 //                   index j with C_{j-1} <= t < C_j (two binary searches), and
 //                   the weight w = x_j T / q_j.
@@ -22,8 +24,9 @@
 //                   (|sum z|^2 - sum |z|^2) / (M (M - 1)) and the standard
 //                   error of the mean.
 //
-// The proposal, the draws and the weights are integer or correctly rounded
-// FP64 operations, so they are the same bits on any IEEE machine; the bins
+// The proposal and the draws are integer operations and the weights one
+// correctly rounded FP64 division and product, so they are the same bits on
+// any IEEE machine; the bins
 // evaluate the phase exactly in integers and the sine and cosine in FP32,
 // and sum in FP32 over runs of 32 samples and in FP64 beyond.
 #include <cuda_runtime.h>
@@ -64,17 +67,39 @@ __host__ __device__ inline McLayout mc_layout(int n) {
     return L;
 }
 
+// The bits of |f| as an FP64 number, by integer operations (the FP32 -> FP64
+// conversion is exact; doing it in integers keeps it off the FP64 pipe).
+__device__ __forceinline__ uint64_t abs_f32_as_f64_bits(float f) {
+    const uint32_t fb = __float_as_uint(f) & 0x7FFFFFFFu;
+    if (fb == 0u) return 0ull;
+    const uint32_t e = fb >> 23, m = fb & 0x7FFFFFu;
+    if (e == 255u) return (0x7FFull << 52) | (static_cast<uint64_t>(m) << 29);
+    if (e == 0u) {  // subnormal: m 2^-149, normalised
+        const int p = 31 - __clz(m);  // highest set bit, 0..22
+        return (static_cast<uint64_t>(p + 874) << 52) | ((static_cast<uint64_t>(m) << (52 - p)) & 0xFFFFFFFFFFFFFull);
+    }
+    return (static_cast<uint64_t>(e + 896u) << 52) | (static_cast<uint64_t>(m) << 29);
+}
+
 // The magnitude used by the proposal, max(|Re|, |Im|) as FP64 bits: for
 // non-negative doubles the integer order of the bits is the value order.
 __device__ __forceinline__ uint64_t mag_bits(float2 v) {
-    const uint64_t a = static_cast<uint64_t>(__double_as_longlong(static_cast<double>(v.x))) & 0x7FFFFFFFFFFFFFFFull;
-    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(static_cast<double>(v.y))) & 0x7FFFFFFFFFFFFFFFull;
+    const uint64_t a = abs_f32_as_f64_bits(v.x), b = abs_f32_as_f64_bits(v.y);
     return a > b ? a : b;
 }
 __device__ __forceinline__ uint64_t mag_bits(double2 v) {
     const uint64_t a = static_cast<uint64_t>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
     const uint64_t b = static_cast<uint64_t>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
     return a > b ? a : b;
+}
+// q_j from the bits of m_j: the significand shifted to the common scale, plus one.
+__device__ __forceinline__ uint64_t mc_weight(uint64_t bits, int emax, int S) {
+    if (bits == 0) return 0;
+    const int eb = static_cast<int>(bits >> 52);
+    const int e = eb > 0 ? eb : 1;
+    const uint64_t sig = (bits & 0xFFFFFFFFFFFFFull) | (eb > 0 ? (1ull << 52) : 0ull);
+    const int sh = emax - e + 53 - S;
+    return (sh < 64 ? sig >> sh : 0ull) + 1ull;
 }
 __device__ __forceinline__ double2 as_d2(float2 v) { return make_double2(v.x, v.y); }
 __device__ __forceinline__ double2 as_d2(double2 v) { return v; }
@@ -136,34 +161,48 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* w
 }
 
 // q_j and its inclusive prefix within each block of kMcChunk indices
-// (cdf[j]); the block's total into bsum[b].
+// (cdf[j]); the block's total into bsum[b].  Loads and stores are coalesced
+// (index i * 256 + t of the block for thread t); the scan runs on 16
+// consecutive indices per thread through shared memory, padded by one word
+// per 16 so that those reads and writes are free of bank conflicts.
 template <typename V>
 __global__ void __launch_bounds__(kMcScanThreads)
     mc_quant_scan_kernel(const V* __restrict__ x, int64_t N, int n, const unsigned long long* maxbits,
                          uint64_t* __restrict__ cdf, uint64_t* __restrict__ bsum) {
     constexpr int IT = kMcChunk / kMcScanThreads;
-    __shared__ uint64_t warp_tot[kMcScanThreads / 32 + 1];
-    const double mx = __longlong_as_double(static_cast<long long>(*maxbits));
-    const double scale = mx > 0.0 ? __ddiv_rn(ldexp(1.0, 62 - n), mx) : 0.0;
-    const int64_t j0 = blockIdx.x * int64_t(kMcChunk) + int64_t(threadIdx.x) * IT;
+    constexpr int NT = kMcScanThreads;
+    __shared__ uint64_t warp_tot[NT / 32 + 1];
+    __shared__ uint64_t qs[kMcChunk + kMcChunk / 16];
+    const uint64_t mb = *maxbits;
+    const int emax = static_cast<int>(mb >> 52) > 0 ? static_cast<int>(mb >> 52) : 1;
+    const int S = 62 - n < 52 ? 62 - n : 52;
+    const int64_t base = blockIdx.x * int64_t(kMcChunk);
+    const int t = threadIdx.x;
+    auto pad = [](int e) { return e + (e >> 4); };
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int e = i * NT + t;
+        qs[pad(e)] = base + e < N ? mc_weight(mag_bits(x[base + e]), emax, S) : 0ull;
+    }
+    __syncthreads();
     uint64_t q[IT];
     uint64_t run = 0;
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
-        q[i] = 0;
-        if (j0 + i < N) {
-            const double m = __longlong_as_double(static_cast<long long>(mag_bits(x[j0 + i])));
-            if (m > 0.0) q[i] = static_cast<uint64_t>(ceil(__dmul_rn(m, scale)));
-        }
-        run += q[i];
+        run += qs[pad(t * IT + i)];
         q[i] = run;  // thread-local inclusive prefix
     }
     uint64_t total;
-    const uint64_t base = block_exclusive_scan<kMcScanThreads>(run, warp_tot, &total);
+    const uint64_t off = block_exclusive_scan<NT>(run, warp_tot, &total);
 #pragma unroll
-    for (int i = 0; i < IT; ++i)
-        if (j0 + i < N) cdf[j0 + i] = base + q[i];
-    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+    for (int i = 0; i < IT; ++i) qs[pad(t * IT + i)] = off + q[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int e = i * NT + t;
+        if (base + e < N) cdf[base + e] = qs[pad(e)];
+    }
+    if (t == 0) bsum[blockIdx.x] = total;
 }
 
 // In place: bsum[b] <- sum of bsum[0 .. b-1]; the grand total T into meta[0].

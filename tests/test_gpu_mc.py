@@ -22,17 +22,23 @@ def _uniforms(seed, m):
 
 
 def _input(kind, n, seed):
-    x = qft_inputs.make(kind, n, seed) if kind != "sparse" else None
+    if kind == "tiny":  # magnitudes down to FP32 subnormals and exact zeros
+        rng = np.random.default_rng(seed)
+        x = (rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)) * 10.0 ** rng.uniform(-44, -30, 1 << n)
+        x[rng.integers(0, 1 << n, size=(1 << n) // 8)] = 0
+        return x
     if kind == "sparse":  # a few nonzeros, many exact zeros (never drawn)
         rng = np.random.default_rng(seed)
         x = np.zeros(1 << n, complex)
         pos = rng.integers(0, 1 << n, size=max(1, (1 << n) // 16))
         x[pos] = rng.standard_normal(pos.size) + 1j * rng.standard_normal(pos.size)
-    return x
+        return x
+    return qft_inputs.make(kind, n, seed)
 
 
 @pytest.mark.parametrize("dt", ["c64", "c128"])
-@pytest.mark.parametrize("n,kind", [(5, "gaussian"), (12, "tones"), (13, "sparse"), (17, "gaussian"), (20, "sparse")])
+@pytest.mark.parametrize("n,kind", [(5, "gaussian"), (12, "tones"), (13, "sparse"), (14, "tiny"), (17, "gaussian"),
+                                    (20, "sparse")])
 def test_draws_and_weights_bitwise(oracle_mod, dt, n, kind):
     td = torch.complex64 if dt == "c64" else torch.complex128
     x = torch.from_numpy(_input(kind, n, 40 + n)).to(td)

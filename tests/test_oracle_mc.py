@@ -26,8 +26,13 @@ def _mag(x):
 
 
 def _q(x, n):
+    """The proposal's integer weights as the reading defines them: floor(m_j
+    2^S / 2^(E+1)) + 1 for m_j > 0, S = min(62 - n, 52), 2^E <= max m < 2^(E+1)
+    (formed here with exact float scaling by powers of two)."""
     a = _mag(x)
-    return np.where(a > 0, np.ceil(a * (2.0 ** (62 - n) / a.max())), 0).astype(np.uint64)
+    S = min(62 - n, 52)
+    E = np.frexp(a.max())[1] - 1
+    return np.where(a > 0, np.floor(np.ldexp(a, S - E - 1)) + 1, 0).astype(np.uint64)
 
 
 @pytest.mark.parametrize("sign", [-1, 1])

@@ -42,10 +42,8 @@ MUTANTS = {
     "mc_phase_sign": ("const double th = sign * ORACLE_TWO_PI * ldexp((double)p, -n);\n            const double c = cos(th), s = sin(th);\n            const double zr",
                       "const double th = -sign * ORACLE_TWO_PI * ldexp((double)p, -n);\n            const double c = cos(th), s = sin(th);\n            const double zr"),
     "mc_power_biased": ("(sr * sr + si * si - sq) / (M * (M - 1.0))", "(sr * sr + si * si) / (M * M)"),
-    "mc_proposal_uniform": ("const uint64_t q = a > 0.0 ? (uint64_t)ceil(a * scale) : 0;",
-                            "const uint64_t q = a > 0.0 ? (uint64_t)ldexp(1.0, 62 - n) : 0;"),
-    "mc_proposal_real_part_only": ("const double a = fmax(fabs(x[2 * j]), fabs(x[2 * j + 1]));\n        const uint64_t q",
-                                   "const double a = fabs(x[2 * j]) + 1e-300;\n        const uint64_t q"),
+    "mc_proposal_uniform": ("return (sh < 64 ? sig >> sh : 0) + 1;", "return (uint64_t)1 << 20;"),
+    "mc_proposal_real_part_only": ("    return a > b ? a : b;\n}\n\n/* q_j", "    return a | 1;\n}\n\n/* q_j"),
 }
 
 
