@@ -1055,7 +1055,11 @@ def run_ours(args, world, rank, local):
         line["extra"] = extra
         if rejected is not None:  # the first timed region's numbers, not used
             line["remeasured"] = rejected
-        line.update(summary)  # compact secondary results last, after the detailed extras
+        # compact secondary results last, after the detailed extras, the most
+        # looked-for at the very end
+        order = ("serving", "tensor_tier", "monte_carlo", "c128_fp64_n30", "c128_n30", "largest_c64_n33", "batched")
+        for key in [k for k in summary if k not in order] + [k for k in order if k in summary]:
+            line[key] = summary[key]
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
