@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mc-only", action="store_true",
+                    help="run only the Monte Carlo backend workload at --n and print its record")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched workload with its default plans (a profiling target); prints its JSON")
     return ap.parse_args()
@@ -1072,6 +1074,17 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.mc_only:
+        import torch
+
+        import paper_2606_18981_gb300 as q
+
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        peak, _ = load_peaks()
+        print(json.dumps(monte_carlo_workload(q, torch, dev, torch.cuda.Stream(device=dev), peak, n=args.n,
+                                              reps=args.steps)))
         return
     if args.batched_only:
         import torch

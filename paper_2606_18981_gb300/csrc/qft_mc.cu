@@ -282,6 +282,32 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// exp(DIR 2 pi i p / 2^n) for the integer phase p (only p mod 2^n matters),
+// n <= 40: the phase is reduced exactly in integers to the nearest quarter
+// turn and the remainder (22 bits of a quarter turn, |x| <= 1/4 half-turn) is
+// converted to FP32 by the 2^23-offset trick (an integer add and one FP32
+// subtraction, exact), so that no 64-bit integer conversion -- which runs on
+// the FP64 pipe -- is needed per pair; then sincospif.
+template <int DIR>
+__device__ __forceinline__ float2 mc_phase(uint64_t p, int n) {
+    const uint64_t b = (p << (64 - n)) >> 24;                  // p mod 2^n, 2^40 per turn
+    const uint64_t q4 = (b + (1ull << 37)) >> 38;              // nearest quarter turn
+    const int64_t rem = static_cast<int64_t>(b) - static_cast<int64_t>(q4 << 38);  // |rem| <= 2^37
+    const int32_t r = static_cast<int32_t>((rem + (1ll << 15)) >> 16);  // rounded, |r| <= 2^21
+    const float xr = __int_as_float(0x4B400000 + r) - 12582912.0f;  // = r exactly
+    float s, c;
+    sincospif(xr * (1.0f / 8388608.0f), &s, &c);              // r / 2^23 half-turns
+    float2 e;
+    switch (static_cast<int>(q4 & 3)) {
+        case 0: e.x = c; e.y = s; break;
+        case 1: e.x = -s; e.y = c; break;
+        case 2: e.x = -c; e.y = -s; break;
+        default: e.x = s; e.y = -c; break;
+    }
+    if (DIR < 0) e.y = -e.y;
+    return e;
+}
+
 // Bins: block (g, c) takes the kMcBinsPerBlock bins of group g and the
 // samples of chunk c; per sample it forms the integer phase of each bin
 // (exact: j y; range k: the windows of the set bits of y), the FP32
@@ -316,10 +342,21 @@ __global__ void __launch_bounds__(256)
         facc[b] = make_float2(0.f, 0.f);
     }
     int cnt = 0;
-    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-        const uint64_t j = static_cast<uint64_t>(idx[i]);
-        const double2 wd = w[i];
-        const float2 wf = make_float2(static_cast<float>(wd.x), static_cast<float>(wd.y));
+    // one sample ahead: its index and weight load while this one is evaluated
+    int64_t i = s0 + threadIdx.x;
+    uint64_t jn = 0;
+    double2 wn = make_double2(0.0, 0.0);
+    if (i < s1) {
+        jn = static_cast<uint64_t>(idx[i]);
+        wn = w[i];
+    }
+    for (; i < s1; i += blockDim.x) {
+        const uint64_t j = jn;
+        const float2 wf = make_float2(static_cast<float>(wn.x), static_cast<float>(wn.y));
+        if (i + blockDim.x < s1) {
+            jn = static_cast<uint64_t>(idx[i + blockDim.x]);
+            wn = w[i + blockDim.x];
+        }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             uint64_t p;
@@ -331,7 +368,7 @@ __global__ void __launch_bounds__(256)
                 for (int bit = 0; bit < n; ++bit)
                     if ((y[b] >> bit) & 1ull) p += (j & win[bit]) << bit;
             }
-            const float2 e = phase_turns<float, DIR>(p, n);
+            const float2 e = mc_phase<DIR>(p, n);
             facc[b].x += wf.x * e.x - wf.y * e.y;
             facc[b].y += wf.x * e.y + wf.y * e.x;
         }
@@ -486,7 +523,8 @@ int qft_mc_bins(int n, int k, int direction, const int64_t* d_index, const doubl
     const int kk = (k < 0 || k > n - 1) ? n - 1 : k;
     const bool exact = kk >= n - 1;
     const int groups = (nbins + kMcBinsPerBlock - 1) / kMcBinsPerBlock;
-    int split = (2 * 152 + groups - 1) / groups;
+    // about eight waves of two 256-thread blocks per SM, for balance
+    int split = (16 * 152 + groups - 1) / groups;
     if (split > kMcMaxSplit) split = kMcMaxSplit;
     if (int64_t(split) > (m + 255) / 256) split = static_cast<int>((m + 255) / 256);
     if (split < 1) split = 1;
