@@ -25,6 +25,9 @@ Functions:
                                few nonzeros, summed over the nonzeros only
   mc_sample(x, u)              Sec. 6 Monte Carlo backend: importance-sampled input
                                indices and weights for given uniforms
+  mc_sample_sparse(pos, vals, u), aqft_bins_sparse(pos, vals, n, ys, k, sign)
+                               the same for an input of few nonzeros in an n-wire
+                               register (n <= 62)
   mc_bins(idx, w, n, ys, k, sign)
                                per output bin: the sample mean of the path
                                amplitudes, the unbiased power estimate, the
@@ -99,6 +102,11 @@ def _load():
         lib.oracle_mc_sample.restype = ctypes.c_uint64
         lib.oracle_mc_bins.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p, dp, ctypes.c_int64, i64p,
                                        ctypes.c_int, dp]
+        lib.oracle_mc_sample_sparse.argtypes = [ctypes.c_int64, i64p, dp, dp, ctypes.c_int64, i64p, dp]
+        lib.oracle_mc_sample_sparse.restype = ctypes.c_uint64
+        lib.oracle_aqft_bins_sparse.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, i64p, dp,
+                                                i64p, ctypes.c_int, dp]
+        lib.oracle_aqft_bins_sparse.restype = None
         lib.oracle_mc_bins.restype = None
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
@@ -297,6 +305,37 @@ def mc_sample(x, u):
     T = lib.oracle_mc_sample(n, _dptr(x), u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(u.size),
                              idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(w))
     return idx, w, int(T)
+
+
+def mc_sample_sparse(pos, vals, u):
+    """mc_sample for a sparse input: amplitude vals[j] at input index pos[j] of
+    an n-wire register (any n <= 62); the proposal runs over the list (S from
+    ceil(log2 K)); returns (input indices int64, w complex128, T)."""
+    lib = _load()
+    pos = np.ascontiguousarray(np.asarray(pos, dtype=np.int64))
+    vals = _as_c128(vals)
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    idx = np.empty(u.size, dtype=np.int64)
+    w = np.empty(u.size, dtype=np.complex128)
+    T = lib.oracle_mc_sample_sparse(int(pos.size), pos.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(vals),
+                                    u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(u.size),
+                                    idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(w))
+    return idx, w, int(T)
+
+
+def aqft_bins_sparse(pos, vals, n: int, ys, k: int = -1, sign: int = FORWARD) -> np.ndarray:
+    """<y|U_k|x> (closed-form elements, natural order) for an input with
+    amplitudes vals at indices pos of an n-wire register (n <= 62), summed
+    over the nonzeros only."""
+    lib = _load()
+    pos = np.ascontiguousarray(np.asarray(pos, dtype=np.int64))
+    vals = _as_c128(vals)
+    ys = np.ascontiguousarray(np.asarray(ys, dtype=np.int64))
+    out = np.empty(ys.size, dtype=np.complex128)
+    lib.oracle_aqft_bins_sparse(int(n), int(k), int(sign), int(pos.size),
+                                pos.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(vals),
+                                ys.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(ys.size), _dptr(out))
+    return out
 
 
 def mc_bins(idx, w, n: int, ys, k: int = -1, sign: int = FORWARD):

@@ -384,12 +384,13 @@ static uint64_t mc_weight(uint64_t bits, int emax, int S)
     return (sh < 64 ? sig >> sh : 0) + 1;
 }
 
-/* Importance sampling of M input indices: idx[m] and the complex weight
- * w[2m], w[2m+1] for the uniform u[m].  Returns T (0 for a zero input: then
- * every index is 0 and every weight 0). */
-uint64_t oracle_mc_sample(int n, const double *x, const double *u, int64_t m, int64_t *idx, double *w)
+/* Importance sampling of M entries of a list of K amplitudes x (entry j at
+ * list position j): idx[m] = the drawn position and the complex weight w[2m],
+ * w[2m+1] for the uniform u[m]; S = min(62 - lg, 52) with K <= 2^lg.  Returns
+ * T (0 for an all-zero list: then every position is 0 and every weight 0). */
+static uint64_t mc_sample_list(int64_t N, int lg, const double *x, const double *u, int64_t m, int64_t *idx,
+                               double *w)
 {
-    const int64_t N = (int64_t)1 << n;
     uint64_t mb = 0;
     for (int64_t j = 0; j < N; j++) {
         const uint64_t b = mc_mag_bits(x, j);
@@ -400,7 +401,7 @@ uint64_t oracle_mc_sample(int n, const double *x, const double *u, int64_t m, in
         return 0;
     }
     const int emax = (int)(mb >> 52) > 0 ? (int)(mb >> 52) : 1;
-    const int S = 62 - n < 52 ? 62 - n : 52;
+    const int S = 62 - lg < 52 ? 62 - lg : 52;
     uint64_t *C = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
     if (!C) return 0;
     uint64_t acc = 0;
@@ -427,12 +428,33 @@ uint64_t oracle_mc_sample(int n, const double *x, const double *u, int64_t m, in
     return T;
 }
 
+/* The dense input x of 2^n amplitudes: positions are the input indices. */
+uint64_t oracle_mc_sample(int n, const double *x, const double *u, int64_t m, int64_t *idx, double *w)
+{
+    return mc_sample_list((int64_t)1 << n, n, x, u, m, idx, w);
+}
+
+/* A sparse input of K >= 1 nonzeros: amplitude vals[j] at input index pos[j]
+ * of an n-wire register (n <= 62, far beyond a state vector): the proposal
+ * runs over the list (S from lg = ceil(log2 K)), and idx[m] receives the
+ * drawn entry's input index pos[j]. */
+uint64_t oracle_mc_sample_sparse(int64_t K, const int64_t *pos, const double *vals, const double *u, int64_t m,
+                                 int64_t *idx, double *w)
+{
+    int lg = 0;
+    while (((int64_t)1 << lg) < K) lg++;
+    const uint64_t T = mc_sample_list(K, lg, vals, u, m, idx, w);
+    for (int64_t i = 0; i < m; i++) idx[i] = pos[idx[i]];
+    return T;
+}
+
 /* Per output bin ys[b] of the range-k transform with swaps (natural order):
  * out[4b..4b+3] = (Re mean, Im mean, power estimate, standard error) of the
  * M samples (idx, w) drawn by oracle_mc_sample. */
 void oracle_mc_bins(int n, int k, int sign, const int64_t *idx, const double *w, int64_t m, const int64_t *ys,
                     int nbins, double *out)
 {
+    /* n <= 62: phases mod 2^n in 64-bit integers */
     const int kk = effective_k(n, k);
     const double inv_root = 1.0 / sqrt(ldexp(1.0, n));
 #pragma omp parallel for schedule(dynamic)
@@ -455,5 +477,29 @@ void oracle_mc_bins(int n, int k, int sign, const int64_t *idx, const double *w,
         out[4 * b + 2] = m > 1 ? (sr * sr + si * si - sq) / (M * (M - 1.0)) : 0.0;
         const double v = m > 1 ? (sq / M - (mr * mr + mi * mi)) / (M - 1.0) : 0.0;
         out[4 * b + 3] = v > 0.0 ? sqrt(v) : 0.0;
+    }
+}
+
+/* A few output bins of the range-k AQFT with swaps of an input with K
+ * nonzero amplitudes vals[j] at indices pos[j] of an n-wire register
+ * (n <= 62): the closed-form matrix elements summed over the nonzeros only
+ * (no normalisation of x).  out[b] = <ys[b]| U_k |x>. */
+void oracle_aqft_bins_sparse(int n, int k, int sign, int64_t K, const int64_t *pos, const double *vals,
+                             const int64_t *ys, int nbins, double *out)
+{
+    const int kk = effective_k(n, k);
+    const double inv_root = 1.0 / sqrt(ldexp(1.0, n));
+#pragma omp parallel for schedule(dynamic)
+    for (int b = 0; b < nbins; b++) {
+        double sr = 0.0, si = 0.0;
+        for (int64_t j = 0; j < K; j++) {
+            const uint64_t p = aqft_phase(n, kk, (uint64_t)pos[j], (uint64_t)ys[b]);
+            const double th = sign * ORACLE_TWO_PI * ldexp((double)p, -n);
+            const double c = cos(th), s = sin(th);
+            sr += vals[2 * j] * c - vals[2 * j + 1] * s;
+            si += vals[2 * j] * s + vals[2 * j + 1] * c;
+        }
+        out[2 * b] = sr * inv_root;
+        out[2 * b + 1] = si * inv_root;
     }
 }

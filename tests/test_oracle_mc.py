@@ -120,3 +120,66 @@ def test_unbiased_mean_and_power_and_variance(oracle_mod, k):
     assert np.all(np.abs(pows.mean(0) - np.abs(ref) ** 2) <= 5 * pstd / np.sqrt(R))
     emp = np.mean(np.abs(amps - ref) ** 2, axis=0)
     assert np.all((emp > 0.75 * var) & (emp < 1.33 * var))
+
+
+# ------------------------------------------------- sparse inputs, n up to 62
+
+def test_sparse_bins_equal_dense_and_definition(oracle_mod):
+    """The sparse closed-form bins equal the dense ones on the scattered input
+    (every cutoff), and at n = 50 the exact ones equal the DFT definition
+    summed over the nonzeros with integer phases (an independent formula)."""
+    n = 9
+    rng = np.random.default_rng(9)
+    pos = np.unique(rng.integers(0, 1 << n, size=40))
+    vals = rng.standard_normal(pos.size) + 1j * rng.standard_normal(pos.size)
+    x = np.zeros(1 << n, complex)
+    x[pos] = vals
+    ys = np.arange(0, 1 << n, 5)
+    for k in (-1, 0, 2, 5):
+        assert np.max(np.abs(oracle_mod.aqft_bins_sparse(pos, vals, n, ys, k, -1) -
+                             oracle_mod.aqft_bins(x, ys, k, -1))) <= 1e-12
+    n = 50
+    pos = np.unique(rng.integers(0, 1 << n, size=300, dtype=np.int64))
+    vals = rng.standard_normal(pos.size) + 1j * rng.standard_normal(pos.size)
+    ys = rng.integers(0, 1 << n, size=20, dtype=np.int64)
+    got = oracle_mod.aqft_bins_sparse(pos, vals, n, ys, -1, 1)
+    ref = oracle_mod.dft_bins_sparse(pos, vals, n, ys, 1) / np.sqrt(2.0 ** n)
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_sparse_single_entry_is_exact(oracle_mod):
+    n = 48
+    j0 = (1 << 47) + 123456789
+    idx, w, T = oracle_mod.mc_sample_sparse([j0], [0.3 - 0.4j], _uniforms(np.random.default_rng(1), 50))
+    assert np.all(idx == j0)
+    ys = np.array([0, 1, 12345, (1 << 48) - 1])
+    amp, power, se = oracle_mod.mc_bins(idx, w, n, ys, 7, -1)
+    ref = oracle_mod.aqft_bins_sparse([j0], [0.3 - 0.4j], n, ys, 7, -1)
+    assert np.max(np.abs(amp - ref)) <= 1e-12 * 2.0 ** -24
+
+
+def test_sparse_draw_law_and_unbiased(oracle_mod):
+    """n = 40, 64 nonzeros: uniforms on a grid land on entry j in proportion to
+    q_j (S from ceil(log2 K)); over 300 runs of 32 samples the estimates of the
+    exact and the range-5 bins are unbiased within 5 standard errors."""
+    n, K = 40, 64
+    rng = np.random.default_rng(40)
+    pos = np.unique(rng.integers(0, 1 << n, size=K, dtype=np.int64))
+    vals = qft_inputs.gaussian(6, seed=6, normalise=False)[:pos.size]
+    G = 1 << 14
+    idx, w, T = oracle_mod.mc_sample_sparse(pos, vals, np.arange(G) / G)
+    qi = _q(vals, 6)
+    assert T == int(qi.sum())
+    q = qi.astype(np.float64)
+    where = {int(p): i for i, p in enumerate(pos)}
+    counts = np.bincount([where[int(j)] for j in idx], minlength=pos.size)
+    assert np.all(np.abs(counts - G * q / q.sum()) <= 1.0)
+    ys = np.concatenate([[0, 1], rng.integers(0, 1 << n, size=4, dtype=np.int64)])
+    for k in (-1, 5):
+        ref = oracle_mod.aqft_bins_sparse(pos, vals, n, ys, k, -1)
+        amps = []
+        for _ in range(300):
+            i2, w2, _ = oracle_mod.mc_sample_sparse(pos, vals, _uniforms(rng, 32))
+            amps.append(oracle_mod.mc_bins(i2, w2, n, ys, k, -1)[0])
+        amps = np.array(amps)
+        assert np.all(np.abs(amps.mean(0) - ref) <= 5 * amps.std(0) / np.sqrt(300))
