@@ -509,10 +509,24 @@ int qft_qpe_probabilities(const void* d_state, int m, int d_bits, int dtype, dou
  * samples and in FP64 beyond.  d_workspace must be the one the samples were
  * drawn with (it holds their sum of |w|^2).  k < 0 or k >= n - 1: exact.
  *
- * All three return QFT_ERR_BAD_ARG for null or misaligned pointers and out of
- * range sizes (1 <= n <= 34 complex64, 33 complex128), and are asynchronous
- * on the stream. */
+ * Sparse inputs (the backend's reach beyond a state vector): an input with K
+ * nonzero amplitudes d_vals[j] (K values of the dtype, 16-byte aligned) at
+ * input indices d_pos[j] (K int64, each < 2^n) of an n-wire register,
+ * n <= 62.  qft_mc_prepare_sparse builds the proposal over the K entries
+ * (S = min(62 - ceil(log2 K), 52); workspace qft_mc_sparse_workspace_size(K)
+ * bytes) and qft_mc_sample_sparse draws entries exactly as above but writes
+ * the drawn entry's input index d_pos[j] to d_index; qft_mc_bins then takes
+ * the register's n.  1 <= K <= 2^34.
+ *
+ * All return QFT_ERR_BAD_ARG for null or misaligned pointers and out of range
+ * sizes (dense: 1 <= n <= 34 complex64, 33 complex128; qft_mc_bins:
+ * 1 <= n <= 62), and are asynchronous on the stream. */
 size_t qft_mc_workspace_size(int n);
+size_t qft_mc_sparse_workspace_size(int64_t K);
+int qft_mc_prepare_sparse(int64_t K, int dtype, const void* d_vals, void* d_workspace, qft_stream_t stream);
+int qft_mc_sample_sparse(int64_t K, int dtype, const int64_t* d_pos, const void* d_vals, const void* d_workspace,
+                         const double* d_uniforms, int64_t m, int64_t* d_index, double* d_weight,
+                         qft_stream_t stream);
 int qft_mc_prepare(int n, int dtype, const void* d_x, void* d_workspace, qft_stream_t stream);
 int qft_mc_sample(int n, int dtype, const void* d_x, const void* d_workspace, const double* d_uniforms, int64_t m,
                   int64_t* d_index, double* d_weight, qft_stream_t stream);

@@ -94,6 +94,10 @@ _lib.qft_mc_prepare.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
 _lib.qft_mc_sample.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
 _lib.qft_mc_bins.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int,
                              _vp, _vp, _vp]
+_lib.qft_mc_sparse_workspace_size.argtypes = [ctypes.c_int64]
+_lib.qft_mc_sparse_workspace_size.restype = ctypes.c_size_t
+_lib.qft_mc_prepare_sparse.argtypes = [ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp]
+_lib.qft_mc_sample_sparse.argtypes = [ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
 _lib.qft_rplan_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts)]
 _lib.qft_rplan_destroy.argtypes = [_vp]
 _lib.qft_rplan_workspace_size.argtypes = [_vp]
@@ -543,32 +547,52 @@ class MonteCarlo:
     uniforms and evaluate any bins (qft_mc_prepare / qft_mc_sample /
     qft_mc_bins)."""
 
-    def __init__(self, x):
+    def __init__(self, x, pos=None, n: int | None = None):
+        """x: the dense input (length 2^n), or with pos (CUDA int64 input
+        indices < 2^n) and n the K nonzero amplitudes of a sparse input of an
+        n-wire register (n <= 62)."""
         import torch
 
         if not x.is_cuda or x.dtype not in (torch.complex64, torch.complex128):
             raise ValueError("MonteCarlo expects a CUDA complex64 or complex128 tensor")
-        N = x.numel()
-        n = N.bit_length() - 1
-        if (1 << n) != N:
-            raise QftError(ERR_SIZE, "MonteCarlo")
-        self.n = n
         self.dtype = C64 if x.dtype == torch.complex64 else C128
         self.x = x.contiguous()
-        self.ws = torch.empty(int(_lib.qft_mc_workspace_size(n)), dtype=torch.uint8, device=x.device)
-        _check(_lib.qft_mc_prepare(n, self.dtype, self.x.data_ptr(), self.ws.data_ptr(), _stream_handle(None)),
-               "qft_mc_prepare")
+        self.pos = None
+        if pos is None:
+            N = x.numel()
+            n = N.bit_length() - 1
+            if (1 << n) != N:
+                raise QftError(ERR_SIZE, "MonteCarlo")
+            self.n = n
+            self.ws = torch.empty(int(_lib.qft_mc_workspace_size(n)), dtype=torch.uint8, device=x.device)
+            _check(_lib.qft_mc_prepare(n, self.dtype, self.x.data_ptr(), self.ws.data_ptr(), _stream_handle(None)),
+                   "qft_mc_prepare")
+        else:
+            self.pos = pos.to(torch.int64).contiguous()
+            if n is None or self.pos.numel() != self.x.numel():
+                raise QftError(ERR_BAD_ARG, "MonteCarlo")
+            self.n = int(n)
+            K = self.x.numel()
+            self.ws = torch.empty(int(_lib.qft_mc_sparse_workspace_size(K)), dtype=torch.uint8, device=x.device)
+            _check(_lib.qft_mc_prepare_sparse(K, self.dtype, self.x.data_ptr(), self.ws.data_ptr(),
+                                              _stream_handle(None)), "qft_mc_prepare_sparse")
 
     def sample(self, u, stream=None):
-        """Indices (int64) and weights (complex128) for the uniforms u (CUDA float64)."""
+        """Input indices (int64) and weights (complex128) for the uniforms u (CUDA float64)."""
         import torch
 
         u = u.contiguous()
         m = u.numel()
         idx = torch.empty(m, dtype=torch.int64, device=u.device)
         w = torch.empty(m, dtype=torch.complex128, device=u.device)
-        _check(_lib.qft_mc_sample(self.n, self.dtype, self.x.data_ptr(), self.ws.data_ptr(), u.data_ptr(), m,
-                                  idx.data_ptr(), w.data_ptr(), _stream_handle(stream)), "qft_mc_sample")
+        if self.pos is None:
+            rc = _lib.qft_mc_sample(self.n, self.dtype, self.x.data_ptr(), self.ws.data_ptr(), u.data_ptr(), m,
+                                    idx.data_ptr(), w.data_ptr(), _stream_handle(stream))
+        else:
+            rc = _lib.qft_mc_sample_sparse(self.x.numel(), self.dtype, self.pos.data_ptr(), self.x.data_ptr(),
+                                           self.ws.data_ptr(), u.data_ptr(), m, idx.data_ptr(), w.data_ptr(),
+                                           _stream_handle(stream))
+        _check(rc, "qft_mc_sample")
         return idx, w
 
     def bins(self, idx, w, ys, k: int = -1, direction: int = FORWARD, stream=None):

@@ -54,17 +54,26 @@ struct McLayout {
 
 __host__ __device__ inline size_t mc_align(size_t b) { return (b + 255) / 256 * 256; }
 
-__host__ __device__ inline McLayout mc_layout(int n) {
-    const int64_t N = int64_t(1) << n;
-    const int64_t nb = (N + kMcChunk - 1) / kMcChunk;
+// Workspace of a proposal over K entries: the sections the bins read first,
+// at offsets that do not depend on K (so qft_mc_bins takes any workspace),
+// then the K-sized ones.
+__host__ __device__ inline McLayout mc_layout(int64_t K) {
+    const int64_t nb = (K + kMcChunk - 1) / kMcChunk;
     McLayout L;
     L.meta = 0;                                                         // T, max magnitude bits
-    L.bsum = 256;                                                       // nb block offsets
-    L.wpart = L.bsum + mc_align(size_t(nb) * 8);                        // sum |w|^2 per sampling block
+    L.wpart = 256;                                                      // sum |w|^2 per sampling block
     L.part = L.wpart + mc_align(size_t(kMcSampleBlocks) * 8);           // bin partial sums
-    L.cdf = L.part + mc_align(size_t(kMcMaxSplit) * kMcMaxBins * 16);  // local inclusive prefix sums
-    L.total = L.cdf + mc_align(size_t(N) * 8);
+    L.bsum = L.part + mc_align(size_t(kMcMaxSplit) * kMcMaxBins * 16);  // nb block offsets
+    L.cdf = L.bsum + mc_align(size_t(nb) * 8);                          // local inclusive prefix sums
+    L.total = L.cdf + mc_align(size_t(K) * 8);
     return L;
+}
+
+// ceil(log2 K), K >= 1: the proposal's S = min(62 - lg, 52) keeps T below 2^63.
+inline int mc_lg(int64_t K) {
+    int lg = 0;
+    while ((int64_t(1) << lg) < K) ++lg;
+    return lg;
 }
 
 // The bits of |f| as an FP64 number, by integer operations (the FP32 -> FP64
@@ -167,7 +176,7 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* w
 // per 16 so that those reads and writes are free of bank conflicts.
 template <typename V>
 __global__ void __launch_bounds__(kMcScanThreads)
-    mc_quant_scan_kernel(const V* __restrict__ x, int64_t N, int n, const unsigned long long* maxbits,
+    mc_quant_scan_kernel(const V* __restrict__ x, int64_t N, int lg, const unsigned long long* maxbits,
                          uint64_t* __restrict__ cdf, uint64_t* __restrict__ bsum) {
     constexpr int IT = kMcChunk / kMcScanThreads;
     constexpr int NT = kMcScanThreads;
@@ -175,7 +184,7 @@ __global__ void __launch_bounds__(kMcScanThreads)
     __shared__ uint64_t qs[kMcChunk + kMcChunk / 16];
     const uint64_t mb = *maxbits;
     const int emax = static_cast<int>(mb >> 52) > 0 ? static_cast<int>(mb >> 52) : 1;
-    const int S = 62 - n < 52 ? 62 - n : 52;
+    const int S = 62 - lg < 52 ? 62 - lg : 52;
     const int64_t base = blockIdx.x * int64_t(kMcChunk);
     const int t = threadIdx.x;
     auto pad = [](int e) { return e + (e >> 4); };
@@ -231,13 +240,14 @@ __global__ void __launch_bounds__(1024) mc_scan_offsets_kernel(uint64_t* bsum, i
     if (threadIdx.x == 0) meta[0] = carry;
 }
 
-// One draw per uniform: the index and its weight; per block the sum of |w|^2.
+// One draw per uniform: the entry's input index (pos[s] for a sparse list,
+// else s) and its weight; per block the sum of |w|^2.
 template <typename V>
 __global__ void __launch_bounds__(256)
-    mc_sample_kernel(const V* __restrict__ x, int64_t N, const uint64_t* __restrict__ cdf,
-                     const uint64_t* __restrict__ boff, int64_t nb, const uint64_t* __restrict__ meta,
-                     const double* __restrict__ u, int64_t m, int64_t* __restrict__ idx, double2* __restrict__ w,
-                     double* __restrict__ wpart) {
+    mc_sample_kernel(const V* __restrict__ x, int64_t N, const int64_t* __restrict__ pos,
+                     const uint64_t* __restrict__ cdf, const uint64_t* __restrict__ boff, int64_t nb,
+                     const uint64_t* __restrict__ meta, const double* __restrict__ u, int64_t m,
+                     int64_t* __restrict__ idx, double2* __restrict__ w, double* __restrict__ wpart) {
     __shared__ double red[8];
     const uint64_t T = meta[0];
     double acc = 0.0;
@@ -268,7 +278,7 @@ __global__ void __launch_bounds__(256)
         const double f = __ddiv_rn(__ull2double_rn(T), __ull2double_rn(q));
         const double2 v = as_d2(x[s]);
         const double2 wv = make_double2(__dmul_rn(v.x, f), __dmul_rn(v.y, f));
-        idx[i] = s;
+        idx[i] = pos ? pos[s] : s;
         w[i] = wv;
         acc = __dadd_rn(acc, __dadd_rn(__dmul_rn(wv.x, wv.x), __dmul_rn(wv.y, wv.y)));
     }
@@ -439,41 +449,82 @@ int mc_launch_error() {
 
 using namespace qft;
 
-extern "C" {
+namespace qft {
+namespace {
 
-size_t qft_mc_workspace_size(int n) {
-    if (n < 1 || n > 34) return 0;
-    return mc_layout(n).total;
-}
-
-int qft_mc_prepare(int n, int dtype, const void* d_x, void* d_workspace, qft_stream_t stream) {
-    if (!d_x || !d_workspace || n < 1 || n > (dtype == QFT_C64 ? 34 : 33)) return QFT_ERR_BAD_ARG;
-    if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
-    if ((reinterpret_cast<uintptr_t>(d_x) & 15) || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
-        return QFT_ERR_BAD_ARG;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const McLayout L = mc_layout(n);
+// The proposal over the K entries of x (dense: K = 2^n, lg = n).
+int mc_prepare_list(int64_t K, int lg, int dtype, const void* d_x, void* d_workspace, cudaStream_t st) {
+    const McLayout L = mc_layout(K);
     char* ws = static_cast<char*>(d_workspace);
     uint64_t* meta = reinterpret_cast<uint64_t*>(ws + L.meta);
     uint64_t* bsum = reinterpret_cast<uint64_t*>(ws + L.bsum);
     uint64_t* cdf = reinterpret_cast<uint64_t*>(ws + L.cdf);
-    const int64_t N = int64_t(1) << n;
-    const int64_t nb = (N + kMcChunk - 1) / kMcChunk;
+    const int64_t nb = (K + kMcChunk - 1) / kMcChunk;
     cudaError_t e = cudaMemsetAsync(meta, 0, 256, st);
     if (e != cudaSuccess) return set_cuda_error(e);
     auto* mx = reinterpret_cast<unsigned long long*>(meta + 1);
-    const int gmax = static_cast<int>(N / 256 < 152 * 16 ? (N + 255) / 256 : 152 * 16);
+    const int gmax = static_cast<int>(K / 256 < 152 * 16 ? (K + 255) / 256 : 152 * 16);
     if (dtype == QFT_C64) {
-        mc_max_kernel<<<gmax, 256, 0, st>>>(static_cast<const float2*>(d_x), N, mx);
-        mc_quant_scan_kernel<<<static_cast<unsigned>(nb), kMcScanThreads, 0, st>>>(static_cast<const float2*>(d_x), N, n,
-                                                                                   mx, cdf, bsum);
+        mc_max_kernel<<<gmax, 256, 0, st>>>(static_cast<const float2*>(d_x), K, mx);
+        mc_quant_scan_kernel<<<static_cast<unsigned>(nb), kMcScanThreads, 0, st>>>(static_cast<const float2*>(d_x), K,
+                                                                                   lg, mx, cdf, bsum);
     } else {
-        mc_max_kernel<<<gmax, 256, 0, st>>>(static_cast<const double2*>(d_x), N, mx);
-        mc_quant_scan_kernel<<<static_cast<unsigned>(nb), kMcScanThreads, 0, st>>>(static_cast<const double2*>(d_x), N,
-                                                                                   n, mx, cdf, bsum);
+        mc_max_kernel<<<gmax, 256, 0, st>>>(static_cast<const double2*>(d_x), K, mx);
+        mc_quant_scan_kernel<<<static_cast<unsigned>(nb), kMcScanThreads, 0, st>>>(static_cast<const double2*>(d_x), K,
+                                                                                   lg, mx, cdf, bsum);
     }
     mc_scan_offsets_kernel<<<1, 1024, 0, st>>>(bsum, nb, meta);
     return mc_launch_error();
+}
+
+int mc_sample_list(int64_t K, int dtype, const int64_t* d_pos, const void* d_x, const void* d_workspace,
+                   const double* d_u, int64_t m, int64_t* d_index, double* d_weight, cudaStream_t st) {
+    const McLayout L = mc_layout(K);
+    const char* ws = static_cast<const char*>(d_workspace);
+    const uint64_t* meta = reinterpret_cast<const uint64_t*>(ws + L.meta);
+    const uint64_t* boff = reinterpret_cast<const uint64_t*>(ws + L.bsum);
+    const uint64_t* cdf = reinterpret_cast<const uint64_t*>(ws + L.cdf);
+    double* wpart = reinterpret_cast<double*>(const_cast<char*>(ws) + L.wpart);
+    const int64_t nb = (K + kMcChunk - 1) / kMcChunk;
+    auto* w2 = reinterpret_cast<double2*>(d_weight);
+    if (dtype == QFT_C64)
+        mc_sample_kernel<<<kMcSampleBlocks, 256, 0, st>>>(static_cast<const float2*>(d_x), K, d_pos, cdf, boff, nb,
+                                                          meta, d_u, m, d_index, w2, wpart);
+    else
+        mc_sample_kernel<<<kMcSampleBlocks, 256, 0, st>>>(static_cast<const double2*>(d_x), K, d_pos, cdf, boff, nb,
+                                                          meta, d_u, m, d_index, w2, wpart);
+    return mc_launch_error();
+}
+
+bool misaligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
+
+}  // namespace
+}  // namespace qft
+
+extern "C" {
+
+size_t qft_mc_workspace_size(int n) {
+    if (n < 1 || n > 34) return 0;
+    return mc_layout(int64_t(1) << n).total;
+}
+
+size_t qft_mc_sparse_workspace_size(int64_t K) {
+    if (K < 1 || K > (int64_t(1) << 34)) return 0;
+    return mc_layout(K).total;
+}
+
+int qft_mc_prepare(int n, int dtype, const void* d_x, void* d_workspace, qft_stream_t stream) {
+    if (!d_x || !d_workspace || (dtype != QFT_C64 && dtype != QFT_C128)) return QFT_ERR_BAD_ARG;
+    if (n < 1 || n > (dtype == QFT_C64 ? 34 : 33)) return QFT_ERR_BAD_ARG;
+    if (misaligned(d_x, 16) || misaligned(d_workspace, 256)) return QFT_ERR_BAD_ARG;
+    return mc_prepare_list(int64_t(1) << n, n, dtype, d_x, d_workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int qft_mc_prepare_sparse(int64_t K, int dtype, const void* d_vals, void* d_workspace, qft_stream_t stream) {
+    if (!d_vals || !d_workspace || (dtype != QFT_C64 && dtype != QFT_C128)) return QFT_ERR_BAD_ARG;
+    if (K < 1 || K > (int64_t(1) << 34)) return QFT_ERR_BAD_ARG;
+    if (misaligned(d_vals, 16) || misaligned(d_workspace, 256)) return QFT_ERR_BAD_ARG;
+    return mc_prepare_list(K, mc_lg(K), dtype, d_vals, d_workspace, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int qft_mc_sample(int n, int dtype, const void* d_x, const void* d_workspace, const double* d_uniforms, int64_t m,
@@ -481,27 +532,24 @@ int qft_mc_sample(int n, int dtype, const void* d_x, const void* d_workspace, co
     if (!d_x || !d_workspace || !d_uniforms || !d_index || !d_weight || m < 1) return QFT_ERR_BAD_ARG;
     if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
     if (n < 1 || n > (dtype == QFT_C64 ? 34 : 33)) return QFT_ERR_BAD_ARG;
-    if ((reinterpret_cast<uintptr_t>(d_x) & 15) || (reinterpret_cast<uintptr_t>(d_workspace) & 255) ||
-        (reinterpret_cast<uintptr_t>(d_uniforms) & 7) || (reinterpret_cast<uintptr_t>(d_index) & 7) ||
-        (reinterpret_cast<uintptr_t>(d_weight) & 15))
+    if (misaligned(d_x, 16) || misaligned(d_workspace, 256) || misaligned(d_uniforms, 8) ||
+        misaligned(d_index, 8) || misaligned(d_weight, 16))
         return QFT_ERR_BAD_ARG;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const McLayout L = mc_layout(n);
-    const char* ws = static_cast<const char*>(d_workspace);
-    const uint64_t* meta = reinterpret_cast<const uint64_t*>(ws + L.meta);
-    const uint64_t* boff = reinterpret_cast<const uint64_t*>(ws + L.bsum);
-    const uint64_t* cdf = reinterpret_cast<const uint64_t*>(ws + L.cdf);
-    double* wpart = reinterpret_cast<double*>(const_cast<char*>(ws) + L.wpart);
-    const int64_t N = int64_t(1) << n;
-    const int64_t nb = (N + kMcChunk - 1) / kMcChunk;
-    auto* w2 = reinterpret_cast<double2*>(d_weight);
-    if (dtype == QFT_C64)
-        mc_sample_kernel<<<kMcSampleBlocks, 256, 0, st>>>(static_cast<const float2*>(d_x), N, cdf, boff, nb, meta,
-                                                          d_uniforms, m, d_index, w2, wpart);
-    else
-        mc_sample_kernel<<<kMcSampleBlocks, 256, 0, st>>>(static_cast<const double2*>(d_x), N, cdf, boff, nb, meta,
-                                                          d_uniforms, m, d_index, w2, wpart);
-    return mc_launch_error();
+    return mc_sample_list(int64_t(1) << n, dtype, nullptr, d_x, d_workspace, d_uniforms, m, d_index, d_weight,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+int qft_mc_sample_sparse(int64_t K, int dtype, const int64_t* d_pos, const void* d_vals, const void* d_workspace,
+                         const double* d_uniforms, int64_t m, int64_t* d_index, double* d_weight,
+                         qft_stream_t stream) {
+    if (!d_pos || !d_vals || !d_workspace || !d_uniforms || !d_index || !d_weight || m < 1) return QFT_ERR_BAD_ARG;
+    if (dtype != QFT_C64 && dtype != QFT_C128) return QFT_ERR_BAD_ARG;
+    if (K < 1 || K > (int64_t(1) << 34)) return QFT_ERR_BAD_ARG;
+    if (misaligned(d_pos, 8) || misaligned(d_vals, 16) || misaligned(d_workspace, 256) ||
+        misaligned(d_uniforms, 8) || misaligned(d_index, 8) || misaligned(d_weight, 16))
+        return QFT_ERR_BAD_ARG;
+    return mc_sample_list(K, dtype, d_pos, d_vals, d_workspace, d_uniforms, m, d_index, d_weight,
+                          reinterpret_cast<cudaStream_t>(stream));
 }
 
 int qft_mc_bins(int n, int k, int direction, const int64_t* d_index, const double* d_weight, int64_t m,
@@ -509,14 +557,13 @@ int qft_mc_bins(int n, int k, int direction, const int64_t* d_index, const doubl
     if (!d_index || !d_weight || !d_workspace || !d_out || m < 1 || nbins < 0 || nbins > kMcMaxBins)
         return QFT_ERR_BAD_ARG;
     if (nbins > 0 && !d_bins) return QFT_ERR_BAD_ARG;
-    if (n < 1 || n > 34 || (direction != QFT_FORWARD && direction != QFT_INVERSE)) return QFT_ERR_BAD_ARG;
-    if ((reinterpret_cast<uintptr_t>(d_index) & 7) || (reinterpret_cast<uintptr_t>(d_weight) & 15) ||
-        (reinterpret_cast<uintptr_t>(d_bins) & 7) || (reinterpret_cast<uintptr_t>(d_out) & 7) ||
-        (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+    if (n < 1 || n > 62 || (direction != QFT_FORWARD && direction != QFT_INVERSE)) return QFT_ERR_BAD_ARG;
+    if (misaligned(d_index, 8) || misaligned(d_weight, 16) || misaligned(d_bins, 8) || misaligned(d_out, 8) ||
+        misaligned(d_workspace, 256))
         return QFT_ERR_BAD_ARG;
     if (nbins == 0) return QFT_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const McLayout L = mc_layout(n);
+    const McLayout L = mc_layout(1);  // the sections the bins use sit at fixed offsets
     char* ws = static_cast<char*>(const_cast<void*>(d_workspace));
     auto* part = reinterpret_cast<double2*>(ws + L.part);
     const double* wpart = reinterpret_cast<const double*>(ws + L.wpart);
