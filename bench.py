@@ -729,6 +729,30 @@ def monte_carlo_workload(q, torch, dev, stream, peak, n=30, m=1 << 22, nbins=102
            "reference": "the state-vector transform of the same input"}
     del mc, idx, w, u, x
     torch.cuda.empty_cache()
+    # a sparse input of a 60-wire register (2^60 amplitudes: no state vector
+    # holds it): 2^20 nonzeros, the same draws and bins
+    K = 1 << 20
+    pos = torch.randint(0, 1 << 60, (K,), generator=g, device=dev, dtype=torch.int64)
+    vals = torch.randn(K, dtype=torch.complex64, generator=g, device=dev)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        mcs = q.MonteCarlo(vals, pos=pos, n=60)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_prep = a.elapsed_time(b)
+        u = torch.rand(m, dtype=torch.float64, device=dev, generator=g)
+        ys60 = torch.randint(0, 1 << 60, (nbins,), generator=g, device=dev, dtype=torch.int64)
+        a.record(stream)
+        idx, w = mcs.sample(u, stream=stream)
+        amp, power, se = mcs.bins(idx, w, ys60, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+    out["sparse_n60"] = {"nonzeros": K, "samples": m, "bins": nbins, "ms_prepare": t_prep,
+                         "ms_sample_and_bins": a.elapsed_time(b),
+                         "median_std_error_over_rms": float((se.median() / (vals.abs().pow(2).sum().sqrt() /
+                                                                             2.0 ** 30)).item())}
+    del mcs, idx, w, u, pos, vals
+    torch.cuda.empty_cache()
     return out
 
 
