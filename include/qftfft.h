@@ -487,7 +487,8 @@ int qft_qpe_probabilities(const void* d_state, int m, int d_bits, int dtype, dou
  * amplitude -- and their prefix sums, T = sum q, into
  * d_workspace (qft_mc_workspace_size(n) bytes of device memory, 256-byte
  * aligned; the workspace holds the proposal until the next prepare and also
- * the partial sums of qft_mc_sample and qft_mc_bins).
+ * the partial sums of qft_mc_sample and qft_mc_bins, so calls that overlap on
+ * the device with the same workspace race; use one workspace per stream).
  *
  * qft_mc_sample draws M >= 1 indices: for uniform u_i in [0, 1) (d_uniforms,
  * M doubles in device memory, drawn by the caller; u_i 2^53 is truncated to
