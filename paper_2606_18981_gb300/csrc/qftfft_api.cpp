@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -631,6 +632,38 @@ int plan_passes(qft_plan_s* pl) {
         } else {
             for (int j = 0; j < n % P; ++j) a[j] += 1;
         }
+        if (pl->df && P >= 2) {
+            // double-float plans are bound by the arithmetic per register
+            // stage (cross twiddles, shared-memory round trips, barriers):
+            // the pass widths with the fewest stages in all (multiples of the
+            // stage size where possible; every pass >= cmin wires so the last
+            // pass keeps full HBM runs), the wider passes first
+            auto stages = [&](const std::vector<int>& v) {
+                int t = 0;
+                for (int x : v) t += (x + pl->rmax - 1) / pl->rmax;
+                return t;
+            };
+            std::vector<int> cur(P), best = a;
+            int best_st = stages(a);
+            std::function<void(int, int)> rec = [&](int j, int left) {
+                if (j == P - 1) {
+                    if (left < std::min(cmin, n) || left > cap) return;
+                    cur[j] = left;
+                    const int st = stages(cur);
+                    if (st < best_st || (st == best_st && cur > best)) {
+                        best_st = st;
+                        best = cur;
+                    }
+                    return;
+                }
+                for (int x = std::min(cap, left - 1); x >= 1; --x) {
+                    cur[j] = x;
+                    rec(j + 1, left - x);
+                }
+            };
+            rec(0, n);
+            a = best;
+        }
     } else if (pl->precision) {
         // tensor tier: every pass is one block of <= cap wires
         P = (n + cap - 1) / cap;
@@ -667,11 +700,12 @@ int plan_passes(qft_plan_s* pl) {
         // the last pass's wires keep forming as few blocks as possible
         if (pl->pass_split == 1) ctop = std::min(ctop, pl->cmin);
         if (ctop < 1) return QFT_ERR_UNSUPPORTED;
-        if (pl->precision && ctop < a[P - 1]) {
-            // the tensor-core tier runs one block per pass, so the last pass's
-            // wires must sit on consecutive addresses: the top wires go
-            // (reversed) to the lowest addresses and every other wire moves
-            // up by ctop
+        if ((pl->precision || pl->df) && ctop < a[P - 1]) {
+            // the last pass's wires on consecutive addresses, so that they
+            // form as few blocks as possible (the tensor-core tier runs one
+            // block per pass; double-float plans pay per register stage): the
+            // top wires go (reversed) to the lowest addresses and every other
+            // wire moves up by ctop
             shift = ctop;
             for (int w = 0; w < n - ctop; ++w) L1[w] = w + ctop;
             for (int e = 0; e < ctop; ++e) L1[n - 1 - e] = e;
