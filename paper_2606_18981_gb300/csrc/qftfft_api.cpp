@@ -632,9 +632,10 @@ int plan_passes(qft_plan_s* pl) {
         } else {
             for (int j = 0; j < n % P; ++j) a[j] += 1;
         }
-        if (pl->df && P >= 2) {
-            // double-float plans are bound by the arithmetic per register
-            // stage (cross twiddles, shared-memory round trips, barriers):
+        if (pl->df && pl->threads == 512 && P >= 2) {
+            // double-float plans of 512 threads (blocks of <= 3 wires) are
+            // bound by the arithmetic per register stage (cross twiddles,
+            // shared-memory round trips, barriers):
             // the pass widths with the fewest stages in all (multiples of the
             // stage size where possible; every pass >= cmin wires so the last
             // pass keeps full HBM runs), the wider passes first
@@ -700,7 +701,7 @@ int plan_passes(qft_plan_s* pl) {
         // the last pass's wires keep forming as few blocks as possible
         if (pl->pass_split == 1) ctop = std::min(ctop, pl->cmin);
         if (ctop < 1) return QFT_ERR_UNSUPPORTED;
-        if ((pl->precision || pl->df) && ctop < a[P - 1]) {
+        if ((pl->precision || (pl->df && pl->threads == 512)) && ctop < a[P - 1]) {
             // the last pass's wires on consecutive addresses, so that they
             // form as few blocks as possible (the tensor-core tier runs one
             // block per pass; double-float plans pay per register stage): the
