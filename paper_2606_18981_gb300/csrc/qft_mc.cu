@@ -37,6 +37,7 @@
 #include "../../include/qftfft.h"
 #include "plan_host.hpp"
 #include "qft_device.cuh"
+#include "qft_phase64.cuh"
 
 namespace qft {
 namespace {
@@ -292,30 +293,29 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// exp(DIR 2 pi i p / 2^n) for the integer phase p (only p mod 2^n matters),
-// n <= 40: the phase is reduced exactly in integers to the nearest quarter
-// turn and the remainder (22 bits of a quarter turn, |x| <= 1/4 half-turn) is
-// converted to FP32 by the 2^23-offset trick (an integer add and one FP32
-// subtraction, exact), so that no 64-bit integer conversion -- which runs on
-// the FP64 pipe -- is needed per pair; then sincospif.
+// exp(DIR 2 pi i F / 2^64) from the top 32 bits fh of a 64-bit fixed-point
+// phase F (one turn = 2^64; the low word is below 2^-32 of a turn): the
+// nearest quarter turn exactly in 32-bit integers, the remainder rounded to
+// 22 bits (|x| <= 1/4 half-turn) and converted to FP32 by the 2^23-offset
+// trick (an integer add and an exact FP32 subtraction: no conversion
+// instruction, which for 64-bit integers runs on the FP64 pipe), then the
+// Taylor sine and cosine of qft_phase64.cuh (no range reduction needed).
 template <int DIR>
-__device__ __forceinline__ float2 mc_phase(uint64_t p, int n) {
-    const uint64_t b = (p << (64 - n)) >> 24;                  // p mod 2^n, 2^40 per turn
-    const uint64_t q4 = (b + (1ull << 37)) >> 38;              // nearest quarter turn
-    const int64_t rem = static_cast<int64_t>(b) - static_cast<int64_t>(q4 << 38);  // |rem| <= 2^37
-    const int32_t r = static_cast<int32_t>((rem + (1ll << 15)) >> 16);  // rounded, |r| <= 2^21
-    const float xr = __int_as_float(0x4B400000 + r) - 12582912.0f;  // = r exactly
-    float s, c;
-    sincospif(xr * (1.0f / 8388608.0f), &s, &c);              // r / 2^23 half-turns
-    float2 e;
-    switch (static_cast<int>(q4 & 3)) {
-        case 0: e.x = c; e.y = s; break;
-        case 1: e.x = -s; e.y = c; break;
-        case 2: e.x = -c; e.y = -s; break;
-        default: e.x = s; e.y = -c; break;
-    }
-    if (DIR < 0) e.y = -e.y;
-    return e;
+__device__ __forceinline__ float2 mc_phase_hi(uint32_t fh) {
+    const uint32_t q4 = (fh + (1u << 29)) >> 30;                       // nearest quarter turn (mod 4)
+    const int32_t rem = static_cast<int32_t>(fh - (q4 << 30));          // |rem| <= 2^29
+    const int32_t r = (rem + 128) >> 8;                                 // rounded, |r| <= 2^21
+    const float xr = __int_as_float(0x4B400000 + r) - 12582912.0f;      // = r exactly
+    float sn, cs;
+    sincospi_quarter(xr * (1.0f / 8388608.0f), sn, cs);                 // r / 2^23 half-turns
+    // q4 quarter turns more, without branches: (c, s) = (cs, sn), (-sn, cs),
+    // (-cs, -sn), (sn, -cs) for q4 mod 4 = 0, 1, 2, 3 (signs by the sign bit)
+    const uint32_t q = q4 & 3u;
+    const float tc = (q & 1u) ? sn : cs, ts = (q & 1u) ? cs : sn;
+    const float c = __int_as_float(__float_as_int(tc) ^ static_cast<int>(((q + 1u) & 2u) << 30));
+    const uint32_t sneg = (q & 2u) ^ (DIR < 0 ? 2u : 0u);
+    const float s = __int_as_float(__float_as_int(ts) ^ static_cast<int>(sneg << 30));
+    return make_float2(c, s);
 }
 
 // Bins: block (g, c) takes the kMcBinsPerBlock bins of group g and the
@@ -339,9 +339,14 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const int g0 = blockIdx.x * B;
+    // the bins as 64-bit fixed-point factors: the exact phase j y / 2^n turns
+    // is j (y << (64 - n)) mod 2^64
     uint64_t y[B];
 #pragma unroll
-    for (int b = 0; b < B; ++b) y[b] = g0 + b < nbins ? static_cast<uint64_t>(ys[g0 + b]) : 0ull;
+    for (int b = 0; b < B; ++b) {
+        y[b] = g0 + b < nbins ? static_cast<uint64_t>(ys[g0 + b]) : 0ull;
+        if (EXACT) y[b] <<= (64 - n);
+    }
     const int64_t per = (m + gridDim.y - 1) / gridDim.y;
     const int64_t s0 = blockIdx.y * per, s1 = s0 + per < m ? s0 + per : m;
     double2 dacc[B];
@@ -369,16 +374,20 @@ __global__ void __launch_bounds__(256)
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            uint64_t p;
+            uint32_t fh;
             if constexpr (EXACT) {
-                p = j * y[b];
+                // the high word of the low 64 bits of j * y'
+                const uint32_t jl = static_cast<uint32_t>(j), jh = static_cast<uint32_t>(j >> 32);
+                const uint32_t yl = static_cast<uint32_t>(y[b]), yh = static_cast<uint32_t>(y[b] >> 32);
+                fh = __umulhi(jl, yl) + jl * yh + jh * yl;
             } else {
-                p = 0;
+                uint64_t p = 0;
 #pragma unroll 1
                 for (int bit = 0; bit < n; ++bit)
                     if ((y[b] >> bit) & 1ull) p += (j & win[bit]) << bit;
+                fh = static_cast<uint32_t>((p << (64 - n)) >> 32);
             }
-            const float2 e = mc_phase<DIR>(p, n);
+            const float2 e = mc_phase_hi<DIR>(fh);
             facc[b].x += wf.x * e.x - wf.y * e.y;
             facc[b].y += wf.x * e.y + wf.y * e.x;
         }
