@@ -41,15 +41,16 @@ __host__ __device__ inline uint64_t phase64_quarter(uint64_t phase, int64_t& rem
     return q4;
 }
 
-// (c, s) = (cos, sin) of q4 quarter turns plus the angle whose (cos, sin) are (cs, sn).
+// (c, s) = (cos, sin) of q4 quarter turns plus the angle whose (cos, sin) are
+// (cs, sn): (cs, sn), (-sn, cs), (-cs, -sn), (sn, -cs) for q4 mod 4 = 0..3,
+// written as selects (a switch on a per-thread quarter made the warps branch).
 template <typename T>
 __host__ __device__ inline void rotate_quarters(uint64_t q4, T cs, T sn, T& c, T& s) {
-    switch (q4 & 3) {
-        case 0: c = cs; s = sn; break;
-        case 1: c = -sn; s = cs; break;
-        case 2: c = -cs; s = -sn; break;
-        default: c = sn; s = -cs; break;
-    }
+    const unsigned q = static_cast<unsigned>(q4 & 3u);
+    const T tc = (q & 1u) ? sn : cs;
+    const T ts = (q & 1u) ? cs : sn;
+    c = ((q + 1u) & 2u) ? -tc : tc;
+    s = (q & 2u) ? -ts : ts;
 }
 
 // complex64: exp(2 pi i phase / 2^64) with the rest of the reduction taken
