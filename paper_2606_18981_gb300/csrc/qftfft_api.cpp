@@ -317,13 +317,14 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
 // fit (more than 5 TMA dimensions, or store maps that would not coalesce).
 bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const std::vector<int>& Lin,
                      const std::vector<int>& Lout, bool first, bool last, bool top, int extra_mode) {
-    const int n = pl->n;
+    const int n = pl->n;       // transform wires: phases, normalisation
+    const int na = pl->n_addr; // address bits (> n: a subset plan's upper wires, a batch index)
     const int r1 = a - r0;
     if (r0 < 4 || r0 > 5 || r1 < 3 || r1 > 5) return false;
     const int E0 = 5 - r0, E1 = 5 - r1;
-    std::vector<int> wire_at(n);
-    for (int w = 0; w < n; ++w) wire_at[Lin[w]] = w;
-    std::vector<char> used(n, 0);
+    std::vector<int> wire_at(na);
+    for (int w = 0; w < na; ++w) wire_at[Lin[w]] = w;
+    std::vector<char> used(na, 0);
     for (int w = glo; w < glo + a; ++w) used[w] = 1;
     int xw[14];
     for (int b = 0; b < 4; ++b) {
@@ -342,7 +343,7 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
         for (int i = E0 + E1 - 1; i >= E1; --i) ex0.push_back(below[i]);
     } else {
         std::vector<int> cand;
-        for (int adr = 0; adr < n; ++adr)
+        for (int adr = 0; adr < na; ++adr)
             if (!used[wire_at[adr]]) cand.push_back(wire_at[adr]);
         if (static_cast<int>(cand.size()) < E0 + E1) return false;
         const int nfirst = extra_mode == 0 ? E1 : E0;
@@ -353,7 +354,7 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
     for (int w = glo; w < glo + r1; ++w) xw[x++] = w;
     for (int w : ex0) xw[x++] = w;
     for (int w = glo + r1; w < glo + a; ++w) xw[x++] = w;
-    std::vector<char> in_tile(n, 0);
+    std::vector<char> in_tile(na, 0);
     for (int b = 0; b < 14; ++b) in_tile[xw[b]] = 1;
 
     PassParams& P = ph.prm;
@@ -363,7 +364,7 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
     P.first = first;
     P.last = last;
     P.tb = 14;
-    P.num_tiles = int64_t(1) << (n - 14);
+    P.num_tiles = int64_t(1) << (na - 14);
     P.inv_root_n = std::ldexp(1.0, -n / 2) * ((n & 1) ? std::sqrt(0.5) : 1.0);
     ph.wires = a;
     for (int b = 0; b < 14; ++b) {
@@ -380,7 +381,7 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
     }
     // tile-coordinate wires in input address order -> segments
     std::vector<int> nt;
-    for (int adr = 0; adr < n; ++adr)
+    for (int adr = 0; adr < na; ++adr)
         if (!in_tile[wire_at[adr]]) nt.push_back(wire_at[adr]);
     P.nseg = 0;
     for (int m = 0; m < static_cast<int>(nt.size());) {
@@ -432,14 +433,14 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
     for (int d = nd; d < kMaxDims; ++d) {
         ph.gdim[d] = 1;
         ph.box[d] = 1;
-        ph.gstride[d - 1] = (cuuint64_t(1) << n) * 8;
+        ph.gstride[d - 1] = (cuuint64_t(1) << na) * 8;
         P.dim_src[d] = 0;
         P.dim_len[d] = 0;
         P.dim_scale[d] = 1;
     }
     P.load_mode = 0;
     ph.run_bits = 0;
-    while (ph.run_bits < n && in_tile[wire_at[ph.run_bits]]) ++ph.run_bits;
+    while (ph.run_bits < na && in_tile[wire_at[ph.run_bits]]) ++ph.run_bits;
     // the two register stages (also read by describe_pass and the CPU plan checks)
     const int rr[2] = {r0, r1}, qq[2] = {9 + E0, 4 + E1}, wl[2] = {glo + r1, glo};
     P.nstages = 2;
@@ -454,14 +455,14 @@ bool build_pass_wide(qft_plan_s* pl, PassHost& ph, int glo, int a, int r0, const
         S.ngbits = 14 - S.r;
         S.tile_above = 0;
         for (int w : nt)
-            if (w > hi) S.tile_above = 1;
+            if (w > hi && w < n) S.tile_above = 1;  // wires >= n: batch index, no phase
         S.uoff = s ? r0 : 0;
         int i = 0;
         for (int b = 0; b < 14; ++b)
             if (b < S.q || b >= S.q + S.r) S.gpos[i++] = b;
         S.lo_tw = S.hi_tw = 0;
         for (int g = 0; g < S.ngbits; ++g)
-            if (P.p_wire[S.gpos[g]] > hi) (g < 5 ? S.lo_tw : S.hi_tw) = 1;
+            if (P.p_wire[S.gpos[g]] > hi && P.p_wire[S.gpos[g]] < n) (g < 5 ? S.lo_tw : S.hi_tw) = 1;
         if (!S.lo_tw && !S.hi_tw) S.hi_tw = 1;
         P.tab_off[s] = ntab;
         ntab += 32 + (1 << (S.ngbits - 5));
@@ -511,10 +512,13 @@ int plan_passes_wide_split(qft_plan_s* pl, const std::vector<int>& a);
 // Natural-order complex64 plans on wide passes: P = ceil(n / 10) passes of
 // 7..10 wires each; the first pass moves the 4 top wires to the lowest
 // addresses (layout L1 below), the middle passes run in place on L1, the
-// last pass writes the bit-reversed order.
+// last pass writes the bit-reversed order.  Also subset plans on the low n
+// of n_addr address bits (w0 = 0): the upper wires keep their addresses in
+// every layout and act as a batch index (the kernel's phases read the
+// transform's n wires only).
 int plan_passes_wide(qft_plan_s* pl) {
     const int n = pl->n;
-    if (pl->dtype != QFT_C64 || pl->order != QFT_ORDER_NATURAL || pl->n_addr != n || pl->precision) return QFT_ERR_UNSUPPORTED;
+    if (pl->dtype != QFT_C64 || pl->order != QFT_ORDER_NATURAL || pl->w0 != 0 || pl->precision) return QFT_ERR_UNSUPPORTED;
     const int P = std::max(2, (n + 9) / 10);
     if (P > kMaxPasses) return QFT_ERR_UNSUPPORTED;
     // Pass widths: as even as possible.  The wider passes go first; if a pass
@@ -552,10 +556,11 @@ int plan_passes_wide_split(qft_plan_s* pl, const std::vector<int>& a) {
         int t = n;
         for (int j = 0; j < P; ++j) { t -= a[j]; glo[j] = t; }
     }
-    std::vector<int> ident(n), brev(n), L1(n);
-    for (int w = 0; w < n; ++w) {
+    const int na = pl->n_addr;
+    std::vector<int> ident(na), brev(na), L1(na);
+    for (int w = 0; w < na; ++w) {
         ident[w] = w;
-        brev[w] = n - 1 - w;
+        brev[w] = w < n ? n - 1 - w : w;
         L1[w] = w;
     }
     // Layout between the passes: the 4 top wires reversed at addresses 0..3
@@ -1010,8 +1015,9 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
         if (opts->order != QFT_ORDER_NATURAL && opts->order != QFT_ORDER_BITREV) { delete pl; return QFT_ERR_BAD_ARG; }
         pl->order = opts->order;
         if (opts->tile_bits == 14 && dtype == QFT_C64) {
-            // the wide pass kernel: natural order, complex64, the CUDA-core path, whole-register plans
-            if (opts->order != QFT_ORDER_NATURAL || subset || (opts->precision != QFT_PREC_NATIVE) ||
+            // the wide pass kernel: natural order, complex64, the CUDA-core path, the whole
+            // register or its low n wires (w0 = 0)
+            if (opts->order != QFT_ORDER_NATURAL || w0 != 0 || (opts->precision != QFT_PREC_NATIVE) ||
                 opts->threads || opts->max_stage_bits || opts->coalesce_bits) {
                 delete pl;
                 return QFT_ERR_UNSUPPORTED;
@@ -1080,11 +1086,12 @@ int create_plan(qft_plan_t* out, int n_addr, int w0, int n, int k, int direction
         if (!(opts && opts->pass_split)) pl->pass_split = 1;
     }
     if (!shape_given && dtype == QFT_C128 && !fp64 && n_addr >= 21) pl->threads = 512;
-    // complex64, natural order, whole-register plans from n = 23: the wide pass
-    // kernel where the planner finds wide shapes (2^14-amplitude tiles, so
-    // ceil(n / 10) passes), else the shapes above.
-    if (!shape_given && dtype == QFT_C64 && !pl->precision && !subset && pl->order == QFT_ORDER_NATURAL &&
-        n >= 23)
+    // complex64, natural order, arrays of >= 2^23 amplitudes (the whole register,
+    // or a transform of >= 14 wires on its low bits): the wide pass kernel where
+    // the planner finds wide shapes (2^14-amplitude tiles, so ceil(n / 10)
+    // passes), else the shapes above.
+    if (!shape_given && dtype == QFT_C64 && !pl->precision && w0 == 0 && pl->order == QFT_ORDER_NATURAL &&
+        n >= 14 && n_addr >= 23)
         pl->wide_tiles = 2;
     // complex64 tiles of <= 2^12 amplitudes fit two CTAs per SM; blocks of <= 4
     // wires keep the kernel within the 128 registers that needs.

@@ -32,7 +32,7 @@ def subset_reference(oracle_mod, x, n_addr, w0, m, k, sign, mode, natural):
 
 
 CASES = [(10, 0, 6), (12, 0, 8), (16, 0, 13), (11, 3, 5), (12, 4, 8), (14, 5, 9), (15, 4, 11), (13, 6, 7),
-         (12, 2, 6), (18, 4, 14)]
+         (12, 2, 6), (18, 4, 14), (23, 0, 16), (24, 0, 18)]
 
 
 @pytest.mark.parametrize("dt", ["c64", "c128"])

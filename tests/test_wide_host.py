@@ -76,3 +76,41 @@ def test_wide_dataflow_matches_oracle(oracle_mod, index_exe, n):
                 ref, _ = oracle_mod.qft(x, k=k, sign=direction, mode=mode, natural_order=True)
                 err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
                 assert err < 1e-12, (n, k, direction, mode, err)
+
+
+def _subset_reference(oracle_mod, x, n_addr, m, k, sign, mode):
+    """The oracle's m-wire transform of every length-2^m run of x (index bits
+    m .. n_addr-1 fixed)."""
+    a = np.asarray(x, dtype=np.complex128).reshape(1 << (n_addr - m), 1 << m)
+    return np.concatenate([oracle_mod.qft(r.copy(), k=k, sign=sign, mode=mode, natural_order=True)[0] for r in a])
+
+
+@pytest.mark.parametrize("n_addr,m", [(17, 16), (18, 16), (19, 17), (20, 18)])
+def test_wide_subset_plans_match_oracle(oracle_mod, index_exe, n_addr, m):
+    """Wide passes for a transform on the low m of n_addr index bits: the upper
+    bits keep their addresses in every layout (a batch index, no phases)."""
+    maps = thread_maps(index_exe)
+    x = qft_inputs.gaussian(n_addr, seed=70 + n_addr + m, normalise=False)
+    for k, direction in ((-1, q.FORWARD), (3, q.INVERSE)):
+        p = q.Plan(m, k, direction, "c64", q.ORDER_NATURAL, tile_bits=14, n_addr=n_addr)
+        assert p.info().passes == max(2, (m + 9) // 10)
+        for mode in (q.SCALE_UNNORM, q.SCALE_INV_N):
+            got = emulate_wide(p, x, maps, mode)
+            ref = _subset_reference(oracle_mod, x, n_addr, m, k, direction, mode)
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err < 1e-12, (n_addr, m, k, direction, mode, err)
+
+
+def test_default_subset_plans_take_wide_passes():
+    """Default complex64 natural-order plans on the low bits of an array of
+    >= 2^23 amplitudes run on wide passes; other subsets, and transforms of 14 or
+    15 wires under further index bits (six TMA dimensions), keep the 2^12 / 2^13 tiles."""
+    for n_addr, m in ((23, 16), (28, 24), (30, 20), (34, 30)):
+        d = q.Plan(m, -1, q.FORWARD, "c64", n_addr=n_addr)
+        assert d.info().passes == max(2, (m + 9) // 10)
+        assert all(parse(d.describe_pass(i))["wide"] == 1 for i in range(d.info().passes)), (n_addr, m)
+        for i in range(d.info().passes):
+            check_structure(parse(d.describe_pass(i)), 8)
+    for args in ((20, dict(n_addr=22)), (24, dict(n_addr=28, w0=4)), (13, dict(n_addr=28)), (14, dict(n_addr=28))):
+        d = q.Plan(args[0], -1, q.FORWARD, "c64", **args[1])
+        assert all(parse(d.describe_pass(i))["wide"] == 0 for i in range(d.info().passes))
