@@ -23,7 +23,8 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache
 
 # candidate plan shapes (qft_opts fields; 0 = planner default).  Complex64
 # tiles of 2^12 amplitudes run two CTAs per SM; tile bits 14 is the wide pass
-# kernel (2^14-amplitude tiles).
+# kernel (2^14-amplitude tiles); double-float tiles of 2^11 pairs with 256
+# threads and blocks of <= 3 wires run two CTAs per SM.
 _KEYS = ("tile_bits", "coalesce_bits", "max_stage_bits", "threads", "paired", "pass_split")
 CANDIDATES = {
     "c64": [dict(zip(_KEYS, c)) for c in (
@@ -34,7 +35,7 @@ CANDIDATES = {
     "c128": [dict(zip(_KEYS, c)) for c in (
         (0, 0, 0, 0, 0, 0), (12, 3, 4, 256, 0, 0), (11, 3, 4, 256, 0, 0), (12, 2, 4, 256, 0, 0),
         (12, 4, 4, 256, 0, 0), (12, 3, 4, 256, 0, 1), (12, 3, 3, 256, 0, 0), (12, 3, 3, 512, 0, 0),
-        (12, 4, 3, 512, 0, 0), (11, 3, 3, 512, 0, 0))],
+        (12, 4, 3, 512, 0, 0), (11, 3, 3, 512, 0, 0), (11, 3, 3, 256, 0, 0))],
 }
 
 _cache: dict | None = None

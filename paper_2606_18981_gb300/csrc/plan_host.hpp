@@ -22,8 +22,8 @@ cudaError_t launch_pass_wide(int dir, int r0, int r1, int top, const CUtensorMap
 cudaError_t launch_pass_wide_group(int dir, int r0, int r1, int top, const WideParams& P, int grid,
                                    cudaStream_t stream);
 constexpr size_t kWideSmem = 215032;  // dynamic shared memory of the wide kernel (checked in qft_wide_fwd.cu)
-cudaError_t launch_pass_df(int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
-                           cudaStream_t stream);
+cudaError_t launch_pass_df(int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P, int grid,
+                           size_t smem, cudaStream_t stream);
 cudaError_t launch_df_maxexp(const void* state, size_t n_amps, int* out, int num_sms, cudaStream_t stream);
 cudaError_t launch_tc_pass(int dir, int prec, const CUtensorMap& map, const PassParams& P, const void* a_hi,
                            const void* a_lo, int kpad, int ncols, int grid, size_t smem, cudaStream_t st);

@@ -264,11 +264,11 @@ __host__ __device__ __forceinline__ dfloat df_from_double_shift(double d, int k)
     return r;
 }
 
-// (a.hi + a.lo) * 2^k as FP64, for a pair normalised by fast_two_sum
-// (|lo| <= ulp(hi) / 2).  The two significands are added in a 64-bit integer
-// (lo's bits below the 53-bit significand are truncated); a result whose
-// exponent leaves the FP64 normal range becomes 0 (underflow) or infinity.
-__host__ __device__ __forceinline__ double df_to_double_shift(dfloat a, int k) {
+// (a.hi + a.lo) * 2^k as FP64, for any pair whose high part dominates.  The
+// two significands are added in a 64-bit integer (lo's bits below the 53-bit
+// significand are truncated); a result whose exponent leaves the FP64 normal
+// range becomes 0 (underflow) or infinity.
+__host__ __device__ __forceinline__ double df_to_double_shift_general(dfloat a, int k) {
     const uint32_t hb = f2u(a.hi);
     const int Eh = static_cast<int>((hb >> 23) & 0xFFu);
     if (Eh == 0) return 0.0;  // hi is zero (or subnormal, below any value that matters)
@@ -296,6 +296,40 @@ __host__ __device__ __forceinline__ double df_to_double_shift(dfloat a, int k) {
     if (Ed <= 0) return sh ? -0.0 : 0.0;
     if (Ed >= 2047) return u2d((sh << 63) | (uint64_t(0x7FF) << 52));
     return u2d((sh << 63) | (static_cast<uint64_t>(Ed) << 52) | (M & ((uint64_t(1) << 52) - 1)));
+}
+
+// The same conversion, bit for bit, written for the pairs the kernel stores
+// (normalised by fast_two_sum, so |lo| <= ulp(hi) / 2): lo's significand then
+// sits at most 5 bits above the 29 bits below hi's, its aligned value is
+// below 2^29 and fits a 32-bit word, and the 53-bit sum lies in
+// (2^52 - 2^29, 2^53), so it needs at most one left shift.  Every step is a
+// select on 32-bit words plus one 64-bit add; other pairs take the general
+// path above.
+__host__ __device__ __forceinline__ double df_to_double_shift(dfloat a, int k) {
+    const uint32_t hb = f2u(a.hi), lb = f2u(a.lo);
+    const int Eh = static_cast<int>((hb >> 23) & 0xFFu);
+    const int El = static_cast<int>((lb >> 23) & 0xFFu);
+    const int sa = El - Eh + 29;
+    if (sa > 5) return df_to_double_shift_general(a, k);
+    const uint32_t Ml = El ? ((lb & 0x7FFFFFu) | 0x800000u) : 0u;
+    const int rs = -sa < 31 ? -sa : 31;
+    const uint32_t add = sa >= 0 ? (Ml << sa) : (Ml >> rs);
+    const uint32_t sh = hb >> 31;
+    const int64_t sadd = ((lb >> 31) == sh) ? static_cast<int64_t>(add) : -static_cast<int64_t>(add);
+    uint64_t M = (static_cast<uint64_t>((hb & 0x7FFFFFu) | 0x800000u) << 29) + static_cast<uint64_t>(sadd);
+    const bool low = M < (uint64_t(1) << 52);
+    M = low ? (M << 1) : M;
+    const int Ed = Eh + 896 + k - (low ? 1 : 0);
+    const uint32_t mhi = static_cast<uint32_t>(M >> 32) & 0xFFFFFu;
+    uint32_t whi = (sh << 31) | (static_cast<uint32_t>(Ed) << 20) | mhi;
+    uint32_t wlo = static_cast<uint32_t>(M);
+    const bool zero = Ed <= 0;
+    const bool inf = Ed >= 2047;
+    whi = zero ? (sh << 31) : (inf ? ((sh << 31) | 0x7FF00000u) : whi);
+    wlo = (zero || inf) ? 0u : wlo;
+    whi = Eh == 0 ? 0u : whi;
+    wlo = Eh == 0 ? 0u : wlo;
+    return u2d((static_cast<uint64_t>(whi) << 32) | wlo);
 }
 
 }  // namespace qft

@@ -35,10 +35,15 @@ cudaError_t launch_df_maxexp(const void* state, size_t n_amps, int* out, int num
     return cudaGetLastError();
 }
 
-// 256 threads: blocks of <= 4 wires, up to 255 registers, 8 warps per SM.
+cudaError_t launch_pass_df_minb2(int dir, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
+                                 cudaStream_t stream);
+
+// 256 threads: blocks of <= 4 wires, up to 255 registers, 8 warps per SM; or
+// (minb = 2) blocks of <= 3 wires within 128 registers, two CTAs per SM.
 // 512 threads: blocks of <= 3 wires within 128 registers, 16 warps per SM.
-cudaError_t launch_pass_df(int dir, int threads, const CUtensorMap& map, const PassParams& P, int grid, size_t smem,
-                           cudaStream_t stream) {
+cudaError_t launch_pass_df(int dir, int threads, int minb, const CUtensorMap& map, const PassParams& P, int grid,
+                           size_t smem, cudaStream_t stream) {
+    if (threads == 256 && minb == 2) return launch_pass_df_minb2(dir, map, P, grid, smem, stream);
     if (threads == 512)
         return dir < 0 ? launch_pass_t<dfloat, -1, 512, 1>(map, P, grid, smem, stream)
                        : launch_pass_t<dfloat, +1, 512, 1>(map, P, grid, smem, stream);

@@ -183,6 +183,14 @@ __device__ __forceinline__ void dispatch_stage(const PassParams& P, int s, const
     else dispatch_r<T, DIR, K_MID, NT, MAXR>(P, s, tab, A, Bb, out_tile, scale, U, acc_norm, norm_acc, io);
 }
 
+// Widest register stage a kernel shape compiles: 5 wires for complex64 with
+// 256 threads and one CTA per SM; 3 where the registers are capped at 128
+// per thread with pair-of-pairs amplitudes (double-float with 512 threads, or
+// two CTAs per SM) or with 512 threads and two CTAs per SM; 4 otherwise.
+template <bool DF, int NT, int MINB>
+inline constexpr int kMaxStageWires =
+    (NT <= 256 && MINB == 1 && !DF) ? 5 : ((DF && (NT > 256 || MINB == 2)) || (MINB == 2 && NT > 256)) ? 3 : 4;
+
 // MINB = CTAs per SM the launch is built for: 2 caps registers at 65536 / (2 NT)
 // and is used only for passes whose stages hold <= 4 wires and whose buffers
 // fit twice in shared memory (tiles of <= 2^12 complex64 amplitudes).
@@ -282,7 +290,7 @@ __global__ void __launch_bounds__(NT, MINB)
             const bool from_A = (s == 0);
             if (ok)
                 dispatch_stage<T, DIR, NT,
-                               (NT <= 256 && MINB == 1 && !Tr::kDF) ? 5 : ((Tr::kDF || MINB == 2) && NT > 256) ? 3 : 4>(
+                               kMaxStageWires<Tr::kDF, NT, MINB>>(
                     P, s, tab, Ab, B, out_tile, scale, Ucur + P.st[s].uoff, P.first && !P.last, norm_acc, io);
             if (last_stage) compute_tile_twiddles<T, DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1]);
             if (from_A) {

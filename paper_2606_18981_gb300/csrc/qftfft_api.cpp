@@ -299,6 +299,8 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
     if (pl->dtype == QFT_C64 && pl->threads == 256 && maxr <= 4 &&
         2 * (ph.smem + 3 * 1024) <= 228 * 1024)
         ph.minb = 2;
+    // double-float: the same with blocks of <= 3 wires (tiles of <= 2^11 pairs)
+    if (pl->df && pl->threads == 256 && maxr <= 3 && 2 * (ph.smem + 3 * 1024) <= 228 * 1024) ph.minb = 2;
     const int64_t tiles = P.num_tiles;
     ph.grid = static_cast<int>(std::min<int64_t>(tiles, int64_t(pl->num_sms) * ph.minb));
     return true;
@@ -637,8 +639,9 @@ int plan_passes(qft_plan_s* pl) {
         } else {
             for (int j = 0; j < n % P; ++j) a[j] += 1;
         }
-        if (pl->df && pl->threads == 512 && P >= 2) {
-            // double-float plans of 512 threads (blocks of <= 3 wires) are
+        if (pl->df && pl->rmax <= 3 && P >= 2) {
+            // double-float plans with blocks of <= 3 wires (512 threads, or
+            // 256 threads two CTAs per SM) are
             // bound by the arithmetic per register stage (cross twiddles,
             // shared-memory round trips, barriers):
             // the pass widths with the fewest stages in all (multiples of the
@@ -706,7 +709,7 @@ int plan_passes(qft_plan_s* pl) {
         // the last pass's wires keep forming as few blocks as possible
         if (pl->pass_split == 1) ctop = std::min(ctop, pl->cmin);
         if (ctop < 1) return QFT_ERR_UNSUPPORTED;
-        if ((pl->precision || (pl->df && pl->threads == 512)) && ctop < a[P - 1]) {
+        if ((pl->precision || (pl->df && pl->rmax <= 3)) && ctop < a[P - 1]) {
             // the last pass's wires on consecutive addresses, so that they
             // form as few blocks as possible (the tensor-core tier runs one
             // block per pass; double-float plans pay per register stage): the
@@ -1286,7 +1289,7 @@ int execute_range(qft_plan_t pl, const void* d_in, void* d_state, void* d_worksp
             e = launch_tc_pass(pl->dir, pl->precision, pl->maps[i], P, ph.tc_a_hi, ph.tc_a_lo, ph.tc_kpad,
                                ph.tc_ncols, ph.grid, ph.smem, st);
         else if (pl->df)
-            e = launch_pass_df(pl->dir, pl->threads, pl->maps[i], P, ph.grid, ph.smem, st);
+            e = launch_pass_df(pl->dir, pl->threads, ph.minb, pl->maps[i], P, ph.grid, ph.smem, st);
         else
             e = launch_pass(pl->dtype, pl->dir, pl->threads, ph.minb, pl->maps[i], P, ph.grid, ph.smem, st);
         if (e != cudaSuccess) return cuda_fail(e);

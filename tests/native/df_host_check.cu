@@ -81,6 +81,33 @@ int main() {
         }
         check(worst <= std::ldexp(1.0, -52), "to_double_shift relative error", worst, std::ldexp(1.0, -52));
     }
+    // 4b. the kernel's conversion equals the general one bit for bit: pairs
+    //     normalised by fast_two_sum (random, powers of two with a negative low
+    //     part, zero / subnormal low parts, shifts that overflow or underflow)
+    //     and pairs that are not normalised (the general path)
+    {
+        long bad = 0, total = 0;
+        auto same = [&](dfloat a, int k) {
+            const double r = qft::df_to_double_shift(a, k), g = qft::df_to_double_shift_general(a, k);
+            ++total;
+            if (qft::d2u(r) != qft::d2u(g)) ++bad;
+        };
+        std::uniform_int_distribution<int> kk(-1200, 1200);
+        for (int i = 0; i < 400000; ++i) {
+            const int k = (i & 3) ? ex(rng) * 10 : kk(rng);
+            const float h = (float)std::ldexp(u(rng), ex(rng) * 2);
+            const float l = (float)(std::ldexp(u(rng), -(i % 40)) * h);
+            same(qft::fast_two_sum(h, l), k);                       // normalised
+            same(dfloat(h, l), k);                                  // as it comes
+            const float p2 = std::ldexp(1.0f, ex(rng));
+            same(qft::fast_two_sum(p2, -std::ldexp(p2, -25 - (i % 8))), k);  // borrow below a power of two
+            same(dfloat(h, 0.f), k);
+            same(dfloat(h, std::ldexp(1.0f, -140)), k);             // subnormal low part
+            same(dfloat(0.f, l), k);
+        }
+        check(bad == 0, "to_double_shift equals the general form", (double)bad, 0);
+        std::printf("  (%ld pairs)\n", total);
+    }
     // 5. round trip FP64 -> df -> FP64
     {
         double worst = 0;

@@ -28,8 +28,8 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def run(x, n, k=-1, direction=-1, order=0, mode=0, precision=0, threads=0):
-    p = q.Plan(n, k, direction, "c128", order, precision=precision, threads=threads)
+def run(x, n, k=-1, direction=-1, order=0, mode=0, precision=0, threads=0, **shape):
+    p = q.Plan(n, k, direction, "c128", order, precision=precision, threads=threads, **shape)
     state = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
     p.load(state, torch.from_numpy(np.ascontiguousarray(x)).pin_memory())
     ws = p.alloc_workspace()
@@ -108,3 +108,20 @@ def test_df_512_threads(oracle_mod, n, order):
         got, _ = run(x, n, k, direction, order, 0, 0, threads=512)
         ref, _ = oracle_mod.qft(x, k, direction, 0, order == 0)
         assert rel_l2(got, ref) <= tol(n)
+
+
+@pytest.mark.parametrize("n", [9, 14, 19, 23])
+@pytest.mark.parametrize("order", [0, 1])
+def test_df_two_ctas_per_sm(oracle_mod, n, order):
+    """The double-float kernel with two 256-thread CTAs per SM (2^11-pair
+    tiles, blocks of <= 3 wires within 128 registers) against the oracle."""
+    x = qft_inputs.tones(n, seed=450 + n)
+    shape = dict(threads=256, tile_bits=11, max_stage_bits=3)
+    p = q.Plan(n, -1, -1, "c128", order, **shape)
+    from plan_emulator import parse
+    assert all(parse(p.describe_pass(i))["minb"] == 2 for i in range(p.info().passes))
+    for direction, k in ((-1, -1), (+1, 5)):
+        for mode in (q.SCALE_STATE, q.SCALE_UNNORM):
+            got, _ = run(x, n, k, direction, order, mode, 0, **shape)
+            ref, _ = oracle_mod.qft(x, k, direction, mode, order == 0)
+            assert rel_l2(got, ref) <= tol(n), (n, order, direction, mode)

@@ -271,6 +271,23 @@ def test_512_thread_plans_match_oracle(oracle_mod, dt, order, n):
     assert rel_l2(got, ref) < 1e-12
 
 
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("n", [9, 14, 19])
+def test_df_two_cta_plans_match_oracle(oracle_mod, order, n):
+    """Double-float plans for two 256-thread CTAs per SM: 2^11-pair tiles,
+    blocks of <= 3 wires, the stage-minimising pass widths; replayed against
+    the oracle."""
+    x = qft_inputs.gaussian(n, seed=5100 + n, normalise=False)
+    p = q.Plan(n, -1, q.FORWARD, "c128", order, threads=256, tile_bits=11, max_stage_bits=3)
+    for i in range(p.info().passes):
+        P = parse(p.describe_pass(i))
+        check_structure(P, 16)
+        assert P["minb"] == 2 and P["tb"] <= 11 and all(s["r"] <= 3 for s in P["st"])
+    got = emulate(p, x, q.SCALE_UNITARY)
+    ref, _ = oracle_mod.qft(x, k=-1, sign=q.FORWARD, mode=q.SCALE_UNITARY, natural_order=(order == q.ORDER_NATURAL))
+    assert rel_l2(got, ref) < 1e-12
+
+
 def test_plan_info_fused_blocks():
     """Sec. 3.1's plan record: the fused blocks (register stages of all passes)
     cover every wire once, and max_fused_size is the widest block."""
