@@ -235,8 +235,9 @@ int batch_build(const qft_plan_t* plans, void* const* d_states, int count, void*
     }
     T.ncounters = ncounters;
     // two load buffers (the next item's tile loads while this one computes)
-    // when they fit, else one
-    constexpr size_t kSmemLimit = 227 * 1024 - 4096;
+    // when they fit, else one; the kernel's static shared memory takes 4 KB
+    // (6.1 KB for double-float, with its per-tile twiddle table)
+    const size_t kSmemLimit = 227 * 1024 - (T.df ? 7 : 4) * 1024;
     T.lay.nbuf = 2;
     T.smem = batch_smem_bytes(T.lay, plans[0]->esize);
     if (T.smem > kSmemLimit) {

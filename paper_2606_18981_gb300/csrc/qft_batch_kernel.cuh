@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(NT, MINB)
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ double red[NT / 32];
     __shared__ __align__(16) typename Vec2<T>::type Ubuf_raw[kMaxR * kMaxStages];
+    // double-float: the table of the FP32-only per-tile factors (phase_turns_df)
+    __shared__ __align__(16) V t40[AmpTraits<T>::kDF ? 129 : 1];
     __shared__ int s_first, s_next, s_pref, s_ok;
     __shared__ __align__(16) PassParams s_prm[2];  // this item's pass descriptor and the next one's
     __shared__ int s_nxdesc;
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(NT, MINB)
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
     }
+    if constexpr (Tr::kDF) build_turns40_table<NT>(t40);
     __syncthreads();
     uint32_t parity = 0;    // phase bit per load buffer (every thread)
     uint32_t inflight = 0;  // buffers with a load issued and not yet waited for (thread 0)
@@ -187,7 +190,8 @@ __global__ void __launch_bounds__(NT, MINB)
             build_group_tables_wide<T, DIR, NT>(P, tab);
             cached_shape = it.shape;
         }
-        compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
+        if constexpr (Tr::kDF) compute_tile_twiddles_df<DIR>(P, it.tile, Ubuf, t40);
+        else compute_tile_twiddles<T, DIR>(P, it.tile, Ubuf);
         __syncthreads();  // tables, twiddles, s_next, s_pref and s_nxdesc
         const int nx = s_next;
         const int pref = s_pref;

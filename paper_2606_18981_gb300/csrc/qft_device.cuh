@@ -561,6 +561,57 @@ __device__ __forceinline__ void compute_tile_twiddles(const PassParams& P, int64
     Ubuf[i] = phase_turns<T, DIR>(beta, P.n);
 }
 
+// exp(DIR * 2 pi i beta / 2^n) as a double-float pair with FP32 operations
+// only: the same exact reduction to the nearest quarter turn as phase_turns,
+// then df_turns40 on the rest (tab: its 129-entry table).
+template <int DIR>
+__device__ __forceinline__ dcomplex phase_turns_df(uint64_t beta, int n, const dcomplex* tab) {
+    const uint64_t b = (beta << (64 - n)) >> 24;  // beta mod 2^n, scaled to 2^40 per turn
+    const uint64_t q4 = (b + (1ull << 37)) >> 38;
+    const int64_t rem = static_cast<int64_t>(b) - static_cast<int64_t>(q4 << 38);
+    const dcomplex z = df_turns40(rem, tab);
+    const dfloat c = z.re(), s = z.im();
+    dfloat x, y;
+    switch (q4 & 3) {
+        case 0: x = c; y = s; break;
+        case 1: x = df_neg(s); y = c; break;
+        case 2: x = df_neg(c); y = df_neg(s); break;
+        default: x = s; y = df_neg(c); break;
+    }
+    if (DIR < 0) y = df_neg(y);
+    return dc_make(x, y);
+}
+
+// The table of df_turns40 ((cos, sin) of 2 pi k / 2^10, k = 0..128), by the
+// NT threads of a CTA (FP64 once per launch).
+template <int NT>
+__device__ __forceinline__ void build_turns40_table(dcomplex* tab) {
+    for (int k = threadIdx.x; k <= 128; k += NT) {
+        double s, c;
+        sincospi(k * (1.0 / 512.0), &s, &c);
+        tab[k] = dc_make(dfloat(c), dfloat(s));
+    }
+}
+
+// compute_tile_twiddles for double-float amplitudes: the per-tile factors come
+// from phase_turns_df, so that the FP64 pipe (1/64 of the FP32 rate) is off
+// the path every tile takes.
+template <int DIR>
+__device__ __forceinline__ void compute_tile_twiddles_df(const PassParams& P, int64_t tile, dcomplex* Ubuf,
+                                                         const dcomplex* tab) {
+    const int i = threadIdx.x;
+    if (i >= P.nU || tile >= P.num_tiles) return;
+    int s = 0;
+    while (s + 1 < P.nstages && P.st[s + 1].uoff <= i) ++s;
+    const StageDesc& S = P.st[s];
+    const int e = i - S.uoff;
+    uint64_t I_tile;
+    int64_t dummy;
+    tile_coords(P, tile, I_tile, dummy);
+    const uint64_t beta = cross_phase(I_tile, P.n, S.wlo + S.r - 1, S.wlo + e, P.kk);
+    Ubuf[i] = phase_turns_df<DIR>(beta, P.n, tab);
+}
+
 // Build the group tables (pb, ob, cross-twiddle factors of the group's tile
 // wires) of every stage of pass P into shared memory.
 template <typename T, int DIR, int NT>

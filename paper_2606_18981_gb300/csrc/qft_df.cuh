@@ -235,6 +235,44 @@ __host__ __device__ __forceinline__ dcomplex dc_norm(dcomplex a) {
 #endif
 }
 
+// ------------------------------------------- twiddles without FP64 work
+
+// (cos, sin) of 2 pi m / 2^40 as double-float pairs, for |m| <= 2^37 (at most
+// an eighth of a turn), with FP32 operations only: m = 2^30 k + r with k the
+// nearest integer to m / 2^30 (|k| <= 128) and |r| <= 2^29; the angle 2 pi k
+// / 2^10 comes from a table (tab[|k|] = (cos, sin) of 2 pi |k| / 2^10, k >= 0;
+// sin is odd), the rest t = 2 pi r / 2^40 (|t| < 3.1e-3) from the Taylor
+// series at 0 -- cos t = 1 - t^2/2 + t^4/24 and sin t = t (1 - t^2/6 +
+// t^4/120), the omitted terms below 2^-58 -- with t^2 as a pair and the
+// quartic terms in FP32 (they are below 4e-12).  The two rotations are then
+// combined as base + base (cos t - 1 + i sin t), so that the complex
+// product's rounding error scales with |t| < 3.1e-3.  Error a few units of
+// 2^-48.
+__host__ __device__ __forceinline__ dcomplex df_turns40(int64_t m, const dcomplex* tab) {
+    const int k = static_cast<int>((m + (int64_t(1) << 29)) >> 30);
+    const int64_t r = m - (static_cast<int64_t>(k) << 30);
+    // 2 pi / 2^40 as a pair
+    const dfloat c40(0x1.921fb6p-38f, -0x1.777a5cp-63f);
+    const float rh = static_cast<float>(r);
+    const dfloat rr(rh, static_cast<float>(r - static_cast<int64_t>(rh)));
+    const dfloat t = df_mul(rr, c40);
+    const dfloat t2 = df_mul(t, t);
+    const float q = t2.hi * t2.hi;
+    // 1 - t^2/6 + t^4/120 and 1 - t^2/2 + t^4/24
+    const dfloat sixth(0x1.555556p-3f, -0x1.555556p-28f);
+    const dfloat b = df_mul(t2, sixth);
+    dfloat ps = two_sum(1.0f, -b.hi);
+    ps.lo += q * (1.0f / 120.0f) - b.lo;
+    const dfloat sn = df_mul(t, fast_two_sum(ps.hi, ps.lo));
+    // cos t - 1 = -t^2/2 + t^4/24 (|.| < 5e-6)
+    const dfloat cm1 = fast_two_sum(-0.5f * t2.hi, q * (1.0f / 24.0f) - 0.5f * t2.lo);
+    dcomplex base = tab[k < 0 ? -k : k];
+    if (k < 0) base = dc_make(base.re(), df_neg(base.im()));
+    // base (cos t + i sin t) = base + base (cos t - 1 + i sin t): the product's
+    // rounding error is relative to its own small size
+    return dc_norm(dc_add(base, dc_mul(base, dc_make(cm1, sn))));
+}
+
 // ------------------------------------------------ FP64 <-> df conversions
 
 // FP64 value d times 2^-k as a df pair, by integer operations only.  The

@@ -202,6 +202,9 @@ __global__ void __launch_bounds__(NT, MINB)
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ double red[NT / 32];
     __shared__ __align__(16) V Ubuf[2][kMaxR * kMaxStages];
+    using Tr = AmpTraits<T>;
+    // double-float: the table of the FP32-only per-tile factors (phase_turns_df)
+    __shared__ __align__(16) V t40[Tr::kDF ? 129 : 1];
 
     const int tid = threadIdx.x;
     const uint32_t tile_elems = 1u << P.tb;
@@ -224,12 +227,17 @@ __global__ void __launch_bounds__(NT, MINB)
         mbar_init(&mbar[1], 1);
     }
     int64_t tile = blockIdx.x;
-    compute_tile_twiddles<T, DIR>(P, tile, Ubuf[0]);
+    if constexpr (Tr::kDF) {
+        build_turns40_table<NT>(t40);
+        __syncthreads();
+        compute_tile_twiddles_df<DIR>(P, tile, Ubuf[0], t40);
+    } else {
+        compute_tile_twiddles<T, DIR>(P, tile, Ubuf[0]);
+    }
     __syncthreads();
 
     // Amplitude I/O: the double-float kernel converts the caller's FP64 data
     // in the first pass and back in the last, with its exponent shift.
-    using Tr = AmpTraits<T>;
     AmpIO io{0, 0, 0, 0};
     if constexpr (Tr::kDF) {
         io.raw_in = P.first;
@@ -292,7 +300,10 @@ __global__ void __launch_bounds__(NT, MINB)
                 dispatch_stage<T, DIR, NT,
                                kMaxStageWires<Tr::kDF, NT, MINB>>(
                     P, s, tab, Ab, B, out_tile, scale, Ucur + P.st[s].uoff, P.first && !P.last, norm_acc, io);
-            if (last_stage) compute_tile_twiddles<T, DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1]);
+            if (last_stage) {
+                if constexpr (Tr::kDF) compute_tile_twiddles_df<DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1], t40);
+                else compute_tile_twiddles<T, DIR>(P, tile + gridDim.x, Ubuf[buf ^ 1]);
+            }
             if (from_A) {
                 if (__syncthreads_or(!ok)) {
                     aborted = true;

@@ -299,8 +299,9 @@ bool build_pass(qft_plan_s* pl, PassHost& ph, int glo, int a, const std::vector<
     if (pl->dtype == QFT_C64 && pl->threads == 256 && maxr <= 4 &&
         2 * (ph.smem + 3 * 1024) <= 228 * 1024)
         ph.minb = 2;
-    // double-float: the same with blocks of <= 3 wires (tiles of <= 2^11 pairs)
-    if (pl->df && pl->threads == 256 && maxr <= 3 && 2 * (ph.smem + 3 * 1024) <= 228 * 1024) ph.minb = 2;
+    // double-float: the same with blocks of <= 3 wires (tiles of <= 2^11 pairs;
+    // 4.1 KB of static shared memory plus the 1 KB reserve)
+    if (pl->df && pl->threads == 256 && maxr <= 3 && 2 * (ph.smem + 5 * 1024) <= 228 * 1024) ph.minb = 2;
     const int64_t tiles = P.num_tiles;
     ph.grid = static_cast<int>(std::min<int64_t>(tiles, int64_t(pl->num_sms) * ph.minb));
     return true;

@@ -108,6 +108,29 @@ int main() {
         check(bad == 0, "to_double_shift equals the general form", (double)bad, 0);
         std::printf("  (%ld pairs)\n", total);
     }
+    // 4c. df_turns40: (cos, sin) of 2 pi m / 2^40 for |m| <= 2^37 from the
+    //     129-entry table, against long double, relative to |z| = 1
+    {
+        qft::dcomplex tab[129];
+        for (int k = 0; k <= 128; ++k) {
+            const long double a = 2.0L * 3.14159265358979323846264338327950288L * k / 1024.0L;
+            const double c = (double)std::cos(a), s = (double)std::sin(a);
+            tab[k] = qft::dc_make(dfloat(c), dfloat(s));
+        }
+        std::uniform_int_distribution<int64_t> um(-(int64_t(1) << 37), int64_t(1) << 37);
+        double worst = 0;
+        auto one = [&](int64_t m) {
+            const qft::dcomplex z = qft::df_turns40(m, tab);
+            const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / 1099511627776.0L;
+            const long double ec = std::fabs(val(z.re()) - std::cos(a)), es = std::fabs(val(z.im()) - std::sin(a));
+            worst = std::fmax(worst, (double)std::fmax(ec, es));
+        };
+        for (int i = 0; i < 400000; ++i) one(um(rng));
+        const int64_t edges[] = {0, 1, -1, int64_t(1) << 37, -(int64_t(1) << 37), (int64_t(1) << 29), -(int64_t(1) << 29),
+                                 (int64_t(1) << 29) - 1, (int64_t(3) << 29), (int64_t(3) << 29) - 1, 12345678901LL};
+        for (int64_t m : edges) one(m);
+        check(worst <= std::ldexp(1.0, -47), "turns40 (cos, sin) error", worst, std::ldexp(1.0, -47));
+    }
     // 5. round trip FP64 -> df -> FP64
     {
         double worst = 0;
