@@ -90,10 +90,13 @@ typedef struct {
     int tile_bits;      /* log2(amplitudes per CTA tile); 0 = default (complex64 natural
                            order from n = 23: the wide pass kernel, 14; else 13 c64, 12
                            c128).  14 (complex64, NATURAL order, no other shape field, no
-                           precision tier, whole-register plans) asks for the wide pass
-                           kernel: tiles of 2^14 amplitudes (4 coalescing batch bits and
-                           two register stages of up to 5 wires), so ceil(n / 10) passes;
-                           QFT_ERR_UNSUPPORTED where the planner finds no wide shape.   */
+                           precision tier, the whole register or a subset plan with w0
+                           = 0) asks for the wide pass kernel: tiles of 2^14 amplitudes (4
+                           coalescing batch bits and two register stages of up to 5
+                           wires), so ceil(n / 10) passes; QFT_ERR_UNSUPPORTED where the
+                           planner finds no wide shape.  Default plans take it for
+                           complex64 natural order on arrays of >= 2^23 amplitudes
+                           (n >= 23, or w0 = 0 subsets of n >= 14 wires).               */
     int coalesce_bits;  /* min log2(contiguous amplitudes per HBM run); 0 = default         */
     int max_stage_bits; /* max wires per register stage (1..5; 1..4 with 512 threads); 0 =
                            default.  With a tensor-core tier (precision 1..5) it is f, the
@@ -106,7 +109,9 @@ typedef struct {
                                  reports QFT_ERR_TIMEOUT (exercises failure reporting
                                  without a fault; see also the test-hook section)       */
     int threads;        /* CTA size of the pass kernel: 256 (stages <= 5 wires) or 512
-                           (stages <= 4 wires); 0 = default                                 */
+                           (stages <= 4 wires); 0 = default.  Double-float complex128 with
+                           256 threads, tile_bits <= 11 and max_stage_bits <= 3 runs two
+                           CTAs per SM (128 registers per thread).                         */
     int precision;      /* QFT_PREC_*: 0 = the default CUDA-core path (complex64 in FP32;
                            complex128 in double-float, see QFT_PREC_FP64); 6 = complex128 in
                            IEEE FP64 arithmetic; 1..5 = complex64 only, each pass's fused
