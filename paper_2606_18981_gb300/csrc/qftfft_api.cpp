@@ -597,6 +597,39 @@ int plan_passes_wide_split(qft_plan_s* pl, const std::vector<int>& a) {
 
 int plan_passes_subset(qft_plan_s* pl);
 
+// The split of n wires into P passes of <= cap wires (the last >= cmin) with
+// the fewest register stages of <= rmax wires in all, the wider passes first
+// among equals; a holds a valid split on entry and the best one on return.
+// Returns its stage count.
+int df_stage_split(int n, int P, int cap, int cmin, int rmax, std::vector<int>& a) {
+    auto stages = [&](const std::vector<int>& v) {
+        int t = 0;
+        for (int x : v) t += (x + rmax - 1) / rmax;
+        return t;
+    };
+    std::vector<int> cur(P), best = a;
+    int best_st = stages(a);
+    std::function<void(int, int)> rec = [&](int j, int left) {
+        if (j == P - 1) {
+            if (left < std::min(cmin, n) || left > cap) return;
+            cur[j] = left;
+            const int st = stages(cur);
+            if (st < best_st || (st == best_st && cur > best)) {
+                best_st = st;
+                best = cur;
+            }
+            return;
+        }
+        for (int x = std::min(cap, left - 1); x >= 1; --x) {
+            cur[j] = x;
+            rec(j + 1, left - x);
+        }
+    };
+    rec(0, n);
+    a = best;
+    return best_st;
+}
+
 // The whole register, or (subset plans with w0 = 0) its low n bits with the
 // bits above as a batch index: logical wires n .. n_addr-1 stay at their own
 // addresses in every map.
@@ -621,6 +654,25 @@ int plan_passes(qft_plan_s* pl) {
         ph.in_buf = ph.out_buf = 0;
         pl->passes.push_back(ph);
         return QFT_OK;
+    }
+    if (natural && pl->df && pl->rmax <= 3 && !pl->shape_given && pl->cmin >= 3) {
+        // double-float plans pay per register stage and per pass: one
+        // coalescing bit less (64-byte HBM runs; the kernel is bound by its
+        // arithmetic, not HBM) where that saves a pass without adding a stage
+        // (n = 28: 3 passes of 10 / 9 / 9 wires in 10 stages instead of 4)
+        auto even = [&](int P) {
+            std::vector<int> v(P, n / P);
+            for (int j = 0; j < n % P; ++j) v[j] += 1;
+            return v;
+        };
+        const int cap1 = pl->TB - pl->cmin, cap2 = cap1 + 1;
+        const int P1 = (n + cap1 - 1) / cap1, P2 = (n + cap2 - 1) / cap2;
+        if (P2 >= 2 && P2 < P1) {
+            std::vector<int> v1 = even(P1), v2 = even(P2);
+            const int s1 = df_stage_split(n, P1, cap1, pl->cmin, pl->rmax, v1);
+            const int s2 = df_stage_split(n, P2, cap2, pl->cmin - 1, pl->rmax, v2);
+            if (s2 <= s1) pl->cmin -= 1;
+        }
     }
     const int TB = pl->TB, cmin = pl->cmin;
     const int cap = TB - cmin;
@@ -648,31 +700,7 @@ int plan_passes(qft_plan_s* pl) {
             // the pass widths with the fewest stages in all (multiples of the
             // stage size where possible; every pass >= cmin wires so the last
             // pass keeps full HBM runs), the wider passes first
-            auto stages = [&](const std::vector<int>& v) {
-                int t = 0;
-                for (int x : v) t += (x + pl->rmax - 1) / pl->rmax;
-                return t;
-            };
-            std::vector<int> cur(P), best = a;
-            int best_st = stages(a);
-            std::function<void(int, int)> rec = [&](int j, int left) {
-                if (j == P - 1) {
-                    if (left < std::min(cmin, n) || left > cap) return;
-                    cur[j] = left;
-                    const int st = stages(cur);
-                    if (st < best_st || (st == best_st && cur > best)) {
-                        best_st = st;
-                        best = cur;
-                    }
-                    return;
-                }
-                for (int x = std::min(cap, left - 1); x >= 1; --x) {
-                    cur[j] = x;
-                    rec(j + 1, left - x);
-                }
-            };
-            rec(0, n);
-            a = best;
+            df_stage_split(n, P, cap, cmin, pl->rmax, a);
         }
     } else if (pl->precision) {
         // tensor tier: every pass is one block of <= cap wires
