@@ -949,19 +949,31 @@ def run_ours(args, world, rank, local):
         computed = [torch.cuda.Event() for _ in range(depth)]
         done = [torch.cuda.Event() for _ in range(depth)]
 
-        def run_steps(count):
+        marks = []  # per timed step: (H2D start, H2D end, D2H start, D2H end) events
+
+        def run_steps(count, timeline=False):
             for kk in range(count):
                 bi = kk % depth
                 if kk >= depth:
                     s_in.wait_event(done[bi])  # buffer bi's previous result has been read back
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if timeline else None
+                if timeline:
+                    ev[0].record(s_in)
                 plan.load(states[bi], host_in, stream=s_in)
                 loaded[bi].record(s_in)
+                if timeline:
+                    ev[1].record(s_in)
                 stream.wait_event(loaded[bi])
                 plan.execute(states[bi], wss[bi], q.SCALE_STATE, stream=stream)
                 computed[bi].record(stream)
                 s_out.wait_event(computed[bi])
+                if timeline:
+                    ev[2].record(s_out)
                 plan.read(states[bi], host_out[bi], stream=s_out)
                 done[bi].record(s_out)
+                if timeline:
+                    ev[3].record(s_out)
+                    marks.append(ev)
 
         run_steps(depth)
         torch.cuda.synchronize()
@@ -970,12 +982,19 @@ def run_ours(args, world, rank, local):
         b = torch.cuda.Event(enable_timing=True)
         a.record(s_in)
         stream.wait_event(a)
-        run_steps(e_steps)
+        run_steps(e_steps, timeline=True)
         stream.wait_stream(s_out)
         b.record(stream)
         torch.cuda.synchronize()
         barrier()
         e_ms_max, e_value = whole_job_rate(a.elapsed_time(b) / e_steps, N, world, dev)
+        # the copies' own times and how much of each step's input copy ran while
+        # the previous step's read-back did (device events on the copy streams)
+        iv = [(a.elapsed_time(m[0]), a.elapsed_time(m[1]), a.elapsed_time(m[2]), a.elapsed_time(m[3])) for m in marks]
+        overlap = sum(max(0.0, min(iv[i + 1][1], iv[i][3]) - max(iv[i + 1][0], iv[i][2])) for i in range(len(iv) - 1))
+        copy_timeline = {"h2d_ms_mean": statistics.mean(t[1] - t[0] for t in iv),
+                         "d2h_ms_mean": statistics.mean(t[3] - t[2] for t in iv),
+                         "h2d_next_during_d2h_ms_mean": overlap / max(1, len(iv) - 1)}
         # the host link alone: one pinned copy of the state each way, and both at once
         link = {}
         for label, fn in (("h2d_gbs", lambda: states[1].copy_(host_in, non_blocking=True)),
@@ -1003,6 +1022,7 @@ def run_ours(args, world, rank, local):
         e2e = {"value": e_value, "unit": UNIT, "ms_per_step": e_ms_max,
                "h2d_bytes_per_step": N * eb, "d2h_bytes_per_step": N * eb, "steps": e_steps,
                "link_gbs_per_step": 2 * N * eb / (e_ms_max / 1e3) / 1e9, "host_link_alone": link,
+               "copy_timeline": copy_timeline,
                "pipeline": "three steps in flight (three device buffers) on three streams: H2D of step k+1 and D2H of step k-1 overlap the compute of step k"}
         del host_in, host_out, states, wss
 
