@@ -181,6 +181,16 @@ def ncu_traffic(n, dt):
         return None
 
 
+def copy_overlap(iv):
+    """Per-step copy intervals (H2D start, H2D end, D2H start, D2H end, in ms)
+    -> mean copy times and the mean time step k+1's input copy ran while step
+    k's read-back did."""
+    overlap = sum(max(0.0, min(iv[i + 1][1], iv[i][3]) - max(iv[i + 1][0], iv[i][2])) for i in range(len(iv) - 1))
+    return {"h2d_ms_mean": statistics.mean(t[1] - t[0] for t in iv),
+            "d2h_ms_mean": statistics.mean(t[3] - t[2] for t in iv),
+            "h2d_next_during_d2h_ms_mean": overlap / max(1, len(iv) - 1)}
+
+
 def whole_job_rate(ms_local, units_per_rank, world, device="cpu"):
     """Replicas: every rank processes units_per_rank in ms_local.  The job's time
     is the slowest rank's (all-reduce MAX over the ranks) and its rate is the
@@ -990,11 +1000,8 @@ def run_ours(args, world, rank, local):
         e_ms_max, e_value = whole_job_rate(a.elapsed_time(b) / e_steps, N, world, dev)
         # the copies' own times and how much of each step's input copy ran while
         # the previous step's read-back did (device events on the copy streams)
-        iv = [(a.elapsed_time(m[0]), a.elapsed_time(m[1]), a.elapsed_time(m[2]), a.elapsed_time(m[3])) for m in marks]
-        overlap = sum(max(0.0, min(iv[i + 1][1], iv[i][3]) - max(iv[i + 1][0], iv[i][2])) for i in range(len(iv) - 1))
-        copy_timeline = {"h2d_ms_mean": statistics.mean(t[1] - t[0] for t in iv),
-                         "d2h_ms_mean": statistics.mean(t[3] - t[2] for t in iv),
-                         "h2d_next_during_d2h_ms_mean": overlap / max(1, len(iv) - 1)}
+        copy_timeline = copy_overlap([(a.elapsed_time(m[0]), a.elapsed_time(m[1]), a.elapsed_time(m[2]),
+                                       a.elapsed_time(m[3])) for m in marks])
         # the host link alone: one pinned copy of the state each way, and both at once
         link = {}
         for label, fn in (("h2d_gbs", lambda: states[1].copy_(host_in, non_blocking=True)),

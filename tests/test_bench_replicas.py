@@ -66,3 +66,18 @@ def test_clock_record_rejection_rules():
         assert bench.clocks_rejected({**ok, "reasons": [r]})
     assert bench.clocks_rejected({**ok, "sm_mhz": 990.0})
     assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]})
+
+
+def test_copy_overlap_of_the_end_to_end_pipeline():
+    """The e2e record's copy timeline: mean copy times and how long each input
+    copy ran alongside the previous step's read-back (serial copies give 0)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    serial = [(0, 40, 50, 95), (95, 135, 145, 190), (190, 230, 240, 285)]
+    r = bench.copy_overlap(serial)
+    assert r["h2d_ms_mean"] == 40 and r["d2h_ms_mean"] == 45 and r["h2d_next_during_d2h_ms_mean"] == 0
+    overlapped = [(0, 41, 50, 105), (41, 95, 105, 160), (95, 150, 160, 215)]
+    r = bench.copy_overlap(overlapped)
+    # step 2's input copy [41, 95] against step 1's read-back [50, 105]: 45 ms; then [95, 150] vs [105, 160]: 45
+    assert r["h2d_next_during_d2h_ms_mean"] == 45

@@ -288,6 +288,26 @@ def test_df_two_cta_plans_match_oracle(oracle_mod, order, n):
     assert rel_l2(got, ref) < 1e-12
 
 
+def test_default_double_float_plan_shapes():
+    """Default double-float complex128 plans from n = 21 (512 threads, blocks of
+    <= 3 wires): the fewest register stages in all, and one coalescing bit less
+    only where that saves a pass without adding a stage (n = 28 alone up to 33)."""
+    expect = {21: (3, 7), 24: (3, 8), 27: (3, 9), 28: (3, 10), 29: (4, 10), 30: (4, 10), 33: (4, 11)}
+    for n in range(21, 34):
+        p = q.Plan(n, -1, q.FORWARD, "c128", q.ORDER_NATURAL)
+        ds = [parse(p.describe_pass(i)) for i in range(p.info().passes)]
+        for P in ds:
+            check_structure(P, 16)
+            assert all(s["r"] <= 3 for s in P["st"][:P["nstages"]])
+        stages = sum(P["nstages"] for P in ds)
+        # every pass but the last (the contiguous one) keeps >= 2 coalescing bits (64-byte runs)
+        assert all(P["run_bits"] >= 2 for P in ds), n
+        assert min(P["run_bits"] for P in ds[:-1]) == (2 if n == 28 else 3), n
+        assert stages >= -(-n // 3)  # blocks of <= 3 wires
+        if n in expect:
+            assert (len(ds), stages) == expect[n], (n, len(ds), stages)
+
+
 def test_plan_info_fused_blocks():
     """Sec. 3.1's plan record: the fused blocks (register stages of all passes)
     cover every wire once, and max_fused_size is the widest block."""
