@@ -114,3 +114,20 @@ def test_default_subset_plans_take_wide_passes():
     for args in ((20, dict(n_addr=22)), (24, dict(n_addr=28, w0=4)), (13, dict(n_addr=28)), (14, dict(n_addr=28))):
         d = q.Plan(args[0], -1, q.FORWARD, "c64", **args[1])
         assert all(parse(d.describe_pass(i))["wide"] == 0 for i in range(d.info().passes))
+
+
+def test_subset_plans_on_large_arrays_are_well_formed():
+    """Every default complex64 plan for the low m bits of a 2^23..2^34 array:
+    well-formed pass records (the address maps are permutations of all n_addr
+    bits, the TMA boxes fit); wide passes, ceil(m / 10) of them, except where
+    the upper wires would need a sixth TMA dimension (m = 14, 15, 21..23, 31)."""
+    for n_addr in range(23, 35):
+        for m in range(14, n_addr + 1):
+            p = q.Plan(m, -1, q.FORWARD, "c64", n_addr=n_addr)
+            ds = [parse(p.describe_pass(i)) for i in range(p.info().passes)]
+            for P in ds:
+                check_structure(P, 8)
+            if all(P["wide"] == 1 for P in ds):
+                assert p.info().passes == max(2, (m + 9) // 10), (n_addr, m)
+            else:
+                assert m in (14, 15, 21, 22, 23, 31), (n_addr, m)
