@@ -94,9 +94,10 @@ typedef struct {
                            = 0) asks for the wide pass kernel: tiles of 2^14 amplitudes (4
                            coalescing batch bits and two register stages of up to 5
                            wires), so ceil(n / 10) passes; QFT_ERR_UNSUPPORTED where the
-                           planner finds no wide shape.  Default plans take it for
-                           complex64 natural order on arrays of >= 2^23 amplitudes
-                           (n >= 23, or w0 = 0 subsets of n >= 14 wires).               */
+                           planner finds no wide shape.  Default plans take it, where
+                           the planner finds a wide shape, for complex64 natural order
+                           on arrays of >= 2^23 amplitudes (n >= 23, or w0 = 0 subsets
+                           of n >= 14 wires).                                           */
     int coalesce_bits;  /* min log2(contiguous amplitudes per HBM run); 0 = default         */
     int max_stage_bits; /* max wires per register stage (1..5; 1..4 with 512 threads); 0 =
                            default.  With a tensor-core tier (precision 1..5) it is f, the
